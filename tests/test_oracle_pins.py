@@ -1,0 +1,394 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle itself:
+library special cases, closed forms, invariants and brute force on tiny inputs.
+
+Each test targets a mistake that would otherwise go unseen (a dropped scale,
+a wrong sign or index, a transposed operand).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import hqs, kb, nudft, nufft, solvers, toeplitz
+import synth
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a - b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
+
+
+def rand_c(rng, shape):
+    return rng.normal(size=shape) + 1j * rng.normal(size=shape)
+
+
+# ---------------------------------------------------------------- Kaiser-Bessel
+def test_i0_series_matches_library():
+    special = pytest.importorskip("scipy.special")
+    z = np.linspace(0.0, 40.0, 401)
+    assert np.max(np.abs(kb.i0(z) / special.i0(z) - 1.0)) < 1e-14
+
+
+def test_i0_small_argument_closed_form():
+    # I0(z) = 1 + z^2/4 + z^4/64 + O(z^6): exact at tiny z
+    z = np.array([1e-4, 3e-4])
+    assert np.allclose(kb.i0(z), 1 + z ** 2 / 4 + z ** 4 / 64, rtol=1e-16, atol=0)
+
+
+@pytest.mark.parametrize("W,sigma", [(4, 2.0), (6, 2.0), (5, 1.5)])
+def test_phihat_matches_quadrature(W, sigma):
+    # int_{-W/2}^{W/2} phi(t) cos(2 pi nu t) dt with t = (W/2) sin(theta):
+    # the substitution removes the square-root edge, Gauss-Legendre converges fast.
+    b = kb.beta(W, sigma)
+    th, wq = np.polynomial.legendre.leggauss(400)
+    th = th * (math.pi / 2)
+    wq = wq * (math.pi / 2)
+    t = (W / 2) * np.sin(th)
+    jac = (W / 2) * np.cos(th)
+    for nu in [0.0, 0.05, 0.2, 0.37, 0.9, 1.7]:
+        quad = np.sum(wq * jac * kb.phi(t, W, b) * np.cos(2 * math.pi * nu * t))
+        got = kb.phihat(np.array([nu]), W, b)[0]
+        # relative to the value, or to the peak where the value is in a side lobe
+        # (the quadrature sums terms of the peak's size there)
+        scale = max(abs(quad), 1e-5 * kb.phihat(np.array([0.0]), W, b)[0])
+        assert abs(got - quad) < 1e-10 * scale
+
+
+def test_beta_formula_values():
+    # Beatty et al. (2005): W=6, sigma=2 -> pi*sqrt(9*2.25-0.8)
+    assert abs(kb.beta(6, 2.0) - math.pi * math.sqrt(19.45)) < 1e-14
+    assert abs(kb.beta(4, 2.0) - math.pi * math.sqrt(8.2)) < 1e-14
+
+
+# ---------------------------------------------------------------- exact NUDFT
+def test_nudft_matches_brute_force_loop():
+    rng = np.random.default_rng(1)
+    n, L, M = 8, 2, 20
+    x = rand_c(rng, (n, n))
+    S = rand_c(rng, (L, n, n))
+    traj = rng.uniform(-math.pi, math.pi, size=(M, 2)).astype(np.float32)
+    y = nudft.forward(x, S, traj)
+    ref = np.zeros((L, M), dtype=np.complex128)
+    k = traj.astype(np.float64)
+    for l in range(L):
+        for j in range(M):
+            acc = 0j
+            for iy in range(n):
+                for ix in range(n):
+                    ph = k[j, 0] * (ix - n // 2) + k[j, 1] * (iy - n // 2)
+                    acc += S[l, iy, ix] * x[iy, ix] * complex(math.cos(ph), -math.sin(ph))
+            ref[l, j] = acc / n
+    assert rel(y, ref) < 1e-14
+    # adjoint brute force
+    yy = rand_c(rng, (L, M))
+    xa = nudft.adjoint(yy, S, traj)
+    ref_a = np.zeros((n, n), dtype=np.complex128)
+    for l in range(L):
+        for iy in range(n):
+            for ix in range(n):
+                ph = k[:, 0] * (ix - n // 2) + k[:, 1] * (iy - n // 2)
+                ref_a[iy, ix] += np.conj(S[l, iy, ix]) * np.sum(yy[l] * np.exp(1j * ph))
+    assert rel(xa, ref_a / n) < 1e-14
+
+
+def cartesian_traj(n):
+    m = np.arange(n) - n // 2
+    MY, MX = np.meshgrid(m, m, indexing="ij")
+    return np.stack([2 * math.pi * MX.ravel() / n, 2 * math.pi * MY.ravel() / n], 1), MY, MX
+
+
+def test_nudft_cartesian_equals_library_fft():
+    n = 12
+    rng = np.random.default_rng(2)
+    x = rand_c(rng, (n, n))
+    S = np.ones((1, n, n), dtype=np.complex128)
+    traj, MY, MX = cartesian_traj(n)
+    y = nudft.forward(x, S, traj).reshape(n, n)
+    X = np.fft.fft2(np.fft.ifftshift(x), norm="ortho")
+    assert rel(y, X[np.mod(MY, n), np.mod(MX, n)]) < 1e-13
+
+
+def test_parseval_cartesian_rss_maps():
+    n, L = 16, 3
+    x = synth.phantom(3, n)
+    S = synth.coil_maps(3, n, L)
+    traj, _, _ = cartesian_traj(n)
+    y = nudft.forward(x, S, traj)
+    assert abs(np.linalg.norm(y) / np.linalg.norm(x) - 1) < 1e-13
+    yn = nufft.forward(x, S, traj, 4, 2.0)
+    assert abs(np.linalg.norm(yn) / np.linalg.norm(x) - 1) < 2e-3
+
+
+@pytest.mark.parametrize("op", ["nudft", "nufft4", "nufft6"])
+def test_adjointness(op):
+    rng = np.random.default_rng(4)
+    n, L, M = 16, 3, 150
+    x = rand_c(rng, (n, n))
+    y = rand_c(rng, (L, M))
+    S = rand_c(rng, (L, n, n))
+    traj = rng.uniform(-math.pi, math.pi, size=(M, 2)).astype(np.float32)
+    if op == "nudft":
+        Ax, Ahy = nudft.forward(x, S, traj), nudft.adjoint(y, S, traj)
+    else:
+        W = int(op[-1])
+        Ax, Ahy = nufft.forward(x, S, traj, W, 2.0), nufft.adjoint(y, S, traj, W, 2.0)
+    lhs = np.vdot(y, Ax)
+    rhs = np.vdot(Ahy, x)
+    assert abs(lhs - rhs) / abs(lhs) < 1e-12
+
+
+# ---------------------------------------------------------------- gridding accuracy
+def test_nufft_vs_nudft_error_bound_and_monotone_in_width():
+    c = synth.tiny_case(0)
+    x, S, traj = c["x"], c["smaps"], c["traj"]
+    ex = nudft.forward(x, S, traj)
+    errs = {W: rel(nufft.forward(x, S, traj, W, 2.0), ex) for W in (4, 6, 8)}
+    assert errs[4] <= 2e-3
+    assert errs[6] < errs[4] / 10 and errs[8] < errs[6]
+    y = c["noise"]
+    ea = rel(nufft.adjoint(y, S, traj, 4, 2.0), nudft.adjoint(y, S, traj))
+    assert ea <= 2e-3
+
+
+def test_nufft_odd_shapes_and_hot_centre():
+    c = synth.odd_case(0)
+    ex = nudft.forward(c["x"], c["smaps"], c["traj"])
+    assert rel(nufft.forward(c["x"], c["smaps"], c["traj"], 4, 2.0), ex) < 2e-3
+
+
+# ---------------------------------------------------------------- Toeplitz
+def test_toeplitz_embedding_equals_dense_normal_operator():
+    rng = np.random.default_rng(5)
+    n, L, M = 12, 2, 90
+    x = rand_c(rng, (n, n))
+    S = rand_c(rng, (L, n, n))
+    traj = rng.uniform(-math.pi, math.pi, size=(M, 2)).astype(np.float32)
+    c = toeplitz.kernel(traj, n, n)
+    Kh = toeplitz.khat(c)
+    assert np.max(np.abs(np.fft.fft2(c).imag)) < 1e-12 * np.max(np.abs(Kh))
+    assert rel(toeplitz.normal(x, S, Kh), nudft.normal(x, S, traj)) < 1e-12
+
+
+def test_toeplitz_kernel_brute_force_entry():
+    rng = np.random.default_rng(6)
+    n, M = 6, 11
+    traj = rng.uniform(-math.pi, math.pi, size=(M, 2)).astype(np.float32)
+    c = toeplitz.kernel(traj, n, n)
+    k = traj.astype(np.float64)
+    for (py, px) in [(0, 0), (1, 4), (7, 2), (11, 11), (n, 3)]:
+        dy = py if py < n else py - 2 * n
+        dx = px if px < n else px - 2 * n
+        want = 0.0 if (py == n or px == n) else np.sum(np.exp(1j * (k[:, 0] * dx + k[:, 1] * dy))) / n ** 2
+        assert abs(c[py, px] - want) < 1e-14
+
+
+def test_density_symbols_are_one_on_full_cartesian():
+    n = 16
+    traj, _, _ = cartesian_traj(n)
+    c = toeplitz.kernel(traj, n, n)
+    for lam in (toeplitz.strang_symbol(c, n, n), toeplitz.chan_symbol(c, n, n)):
+        assert np.max(np.abs(lam - 1.0)) < 1e-12
+    v = rand_c(np.random.default_rng(7), (n, n))
+    lam = toeplitz.chan_symbol(c, n, n)
+    assert rel(toeplitz.precond_apply(v, lam, 2.0, 0.5), v / math.sqrt(2.5)) < 1e-13
+
+
+def test_chan_circulant_averages_wrapped_diagonals():
+    # T. Chan (1988): the Frobenius-optimal circulant approximation of a matrix
+    # has first column c[q] = mean over n of T[(n + q) mod N, n].  Build the
+    # dense block-Toeplitz matrix of F^H F on a tiny grid and compare.
+    rng = np.random.default_rng(17)
+    n, M = 5, 23
+    traj = rng.uniform(-math.pi, math.pi, size=(M, 2)).astype(np.float32)
+    c = toeplitz.kernel(traj, n, n)
+    S = np.ones((1, n, n))
+    T = dense_matrix(lambda v: nudft.normal(v, S, traj), n)   # (n*n, n*n)
+    want = np.zeros((n, n), dtype=np.complex128)
+    for qy in range(n):
+        for qx in range(n):
+            acc = 0j
+            for my in range(n):
+                for mx in range(n):
+                    row = ((my + qy) % n) * n + (mx + qx) % n
+                    acc += T[row, my * n + mx]
+            want[qy, qx] = acc / (n * n)
+    assert rel(toeplitz.chan_column(c, n, n), want) < 1e-12
+    lam = toeplitz.chan_symbol(c, n, n)
+    assert lam.min() > -1e-12       # a PSD Toeplitz gives a PSD Chan circulant
+
+
+# ---------------------------------------------------------------- solvers
+def small_problem(seed=8, n=16, L=2, M=200):
+    rng = np.random.default_rng(seed)
+    x = synth.phantom(seed, n)
+    S = synth.coil_maps(seed, n, L)
+    traj = rng.uniform(-math.pi, math.pi, size=(M, 2)).astype(np.float32)
+    c = toeplitz.kernel(traj, n, n)
+    Kh = toeplitz.khat(c)
+    lam = toeplitz.chan_symbol(c, n, n)
+    AHA = lambda v: toeplitz.normal(v, S, Kh)
+    y = nudft.forward(x, S, traj) + 0.01 * rand_c(rng, (L, M))
+    b0 = nudft.adjoint(y, S, traj)
+    return dict(n=n, S=S, traj=traj, Kh=Kh, lam=lam, AHA=AHA, b0=b0, x=x)
+
+
+def dense_matrix(apply, n):
+    cols = []
+    for i in range(n * n):
+        e = np.zeros(n * n, dtype=np.complex128)
+        e[i] = 1
+        cols.append(apply(e.reshape(n, n)).ravel())
+    return np.stack(cols, axis=1)
+
+
+def test_pcg_matches_dense_solve():
+    P = small_problem()
+    n, mu = P["n"], 1e-2
+    H = lambda v: P["AHA"](v) + mu * v
+    Hd = dense_matrix(H, n)
+    assert np.allclose(Hd, Hd.conj().T, atol=1e-12)
+    ref = np.linalg.solve(Hd, P["b0"].ravel()).reshape(n, n)
+    x, info = solvers.pcg(H, P["b0"], np.zeros((n, n)), None, max_iter=500, tol=1e-12)
+    assert info["status"] == "ok" and rel(x, ref) < 1e-10
+    Minv = lambda v: toeplitz.precond_apply(v, P["lam"], 1.0, mu)
+    x2, info2 = solvers.pcg(H, P["b0"], np.zeros((n, n)), Minv, max_iter=500, tol=1e-12)
+    assert rel(x2, ref) < 1e-10
+    # true residual agrees with the recursive one at the end
+    assert rel(H(x2), P["b0"]) < 1e-11
+
+
+def test_cg_energy_decreases_monotonically():
+    P = small_problem(9)
+    n, mu = P["n"], 1e-3
+    H = lambda v: P["AHA"](v) + mu * v
+    Minv = lambda v: toeplitz.precond_apply(v, P["lam"], 1.0, mu)
+    energies = []
+    for it in range(0, 25):
+        x, _ = solvers.pcg(H, P["b0"], np.zeros((n, n)), Minv, max_iter=it, tol=0.0)
+        energies.append(solvers.cg_energy(H, P["b0"], x))
+    assert all(e2 <= e1 + 1e-12 * abs(e1) for e1, e2 in zip(energies, energies[1:]))
+
+
+def test_fcg_with_linear_preconditioner_matches_pcg():
+    P = small_problem(10)
+    n, mu = P["n"], 1e-2
+    H = lambda v: P["AHA"](v) + mu * v
+    Minv = lambda v: toeplitz.precond_apply(v, P["lam"], 1.0, mu)
+    x1, i1 = solvers.pcg(H, P["b0"], np.zeros((n, n)), Minv, max_iter=200, tol=1e-10)
+    x2, i2 = solvers.fcg(H, P["b0"], np.zeros((n, n)), Minv, Minv, max_iter=200, tol=1e-10)
+    assert rel(x2, x1) < 1e-8 and not i2["fallback"]
+    # a useless preconditioner (negated) must trigger the fallback and still converge
+    x3, i3 = solvers.fcg(H, P["b0"], np.zeros((n, n)), lambda v: -v, Minv,
+                         max_iter=200, tol=1e-10)
+    assert i3["fallback"] and rel(x3, x1) < 1e-8
+
+
+def test_pcg_zero_rhs_and_converged_start():
+    P = small_problem(11)
+    n = P["n"]
+    H = lambda v: P["AHA"](v) + 0.1 * v
+    x, info = solvers.pcg(H, np.zeros((n, n)), np.ones((n, n)), None, 10, 1e-4)
+    assert info["iters"] == 0 and np.all(x == 0)
+    ref, _ = solvers.pcg(H, P["b0"], np.zeros((n, n)), None, 500, 1e-12)
+    x, info = solvers.pcg(H, P["b0"], ref, None, 10, 1e-6)
+    assert info["iters"] == 0
+
+
+def test_power_iteration_matches_eigvalsh():
+    P = small_problem(12, n=10, M=80)
+    Nd = dense_matrix(P["AHA"], P["n"])
+    want = np.linalg.eigvalsh((Nd + Nd.conj().T) / 2).max()
+    got = solvers.power_iteration(P["AHA"], (P["n"], P["n"]), iters=3000, rtol=1e-13)
+    assert abs(got / want - 1) < 1e-6
+
+
+# ---------------------------------------------------------------- denoiser and HQS
+def test_gaussian_denoiser_matches_fft_convolution():
+    rng = np.random.default_rng(13)
+    v = rand_c(rng, (20, 24))
+    s = 1.3
+    g = hqs.gaussian_taps(s)
+    r = (len(g) - 1) // 2
+    ker = np.zeros((20, 24))
+    for i in range(-r, r + 1):
+        for j in range(-r, r + 1):
+            ker[i % 20, j % 24] += g[i + r] * g[j + r]
+    # correlation with a symmetric kernel equals convolution
+    want = np.fft.ifft2(np.fft.fft2(v) * np.fft.fft2(ker))
+    assert rel(hqs.gaussian_denoise(v, s), want) < 1e-13
+    assert np.allclose(hqs.gaussian_denoise(v, 0.05), v)
+    assert abs(hqs.gaussian_denoise(v, 2.0).sum() - v.sum()) < 1e-10
+
+
+def test_hqs_fixed_point_linear_shrink_prop1():
+    # D(v) = v/(1+tau) is the prox of (tau/2)||.||^2.  With P = Id and constant
+    # mu, HQS converges to u* solving (A^H A + mu tau/(1+tau) I) u = A^H y,
+    # x* = u*/(1+tau); PGD converges to (gamma A^H A + tau I) x = gamma A^H y.
+    P = small_problem(14)
+    n, mu, tau, K = P["n"], 0.05, 0.5, 120
+    D = lambda u, s: u / (1 + tau)
+    x, u, _ = hqs.hqs(P["AHA"], P["b0"], np.zeros((n, n)), [mu] * K, [1.0] * K, K,
+                      cg_iters=60, denoiser=D, lam=P["lam"])
+    Hd = dense_matrix(lambda v: P["AHA"](v) + mu * tau / (1 + tau) * v, n)
+    ustar = np.linalg.solve(Hd, P["b0"].ravel()).reshape(n, n)
+    assert rel(u, ustar) < 1e-8
+    assert rel(x, ustar / (1 + tau)) < 1e-8
+    gamma = 1.0 / mu
+    xp = hqs.pgd(P["AHA"], P["b0"], np.zeros((n, n)), [0.5] * 400, [1.0] * 400, 400,
+                 denoiser=D)
+    Hp = dense_matrix(lambda v: 0.5 * P["AHA"](v) + tau * v, n)
+    xpstar = np.linalg.solve(Hp, 0.5 * P["b0"].ravel()).reshape(n, n)
+    assert rel(xp, xpstar) < 1e-8
+    assert gamma > 0
+
+
+def test_hqs_fixed_point_gaussian_smoothing():
+    # circulant smoothing G: fixed point solves (A^H A + mu (I - G)) u = A^H y
+    P = small_problem(15)
+    n, mu, s, K = P["n"], 0.05, 0.8, 150
+    D = lambda u, _s: hqs.gaussian_denoise(u, s)
+    x, u, _ = hqs.hqs(P["AHA"], P["b0"], np.zeros((n, n)), [mu] * K, [1.0] * K, K,
+                      cg_iters=60, denoiser=D, lam=P["lam"])
+    Hd = dense_matrix(lambda v: P["AHA"](v) + mu * (v - hqs.gaussian_denoise(v, s)), n)
+    ustar = np.linalg.solve(Hd, P["b0"].ravel()).reshape(n, n)
+    assert rel(u, ustar) < 1e-7
+
+
+def test_hqs_pmetric_prox_is_argmin():
+    # one prox step with P = c0 I + c1 A^H A must satisfy the optimality
+    # condition gamma A^H (A u - y) + P (u - x) = 0 (Sec. 3.4 definition).
+    P = small_problem(16)
+    n, mu = P["n"], 0.05
+    alpha = 1.0 / solvers.power_iteration(P["AHA"], (n, n), iters=500, rtol=1e-12)
+    x0 = synth.phantom(99, n)
+    for c0, c1 in [(1.0, 0.0), (2.0, -alpha), (4.0, -10.0 * alpha / 3.0)]:
+        D = lambda u, s: u
+        _, u, _ = hqs.hqs(P["AHA"], P["b0"], x0, [mu], [1.0], 1, cg_iters=200,
+                          c0=c0, c1=c1, denoiser=D, lam=P["lam"])
+        gamma = 1.0 / mu
+        grad = gamma * (P["AHA"](u) - P["b0"]) + c0 * (u - x0) + c1 * P["AHA"](u - x0)
+        assert np.linalg.norm(grad) < 1e-8 * np.linalg.norm(gamma * P["b0"])
+
+
+def test_prox_coefficients():
+    assert hqs.prox_coefficients(0.1, 1.0, 0.0) == (1.0, 0.1)
+    a, b = hqs.prox_coefficients(0.1, 2.0, -0.5)
+    assert abs(a - 0.95) < 1e-15 and abs(b - 0.2) < 1e-15
+
+
+def test_density_preconditioner_cuts_iterations_on_vd_spiral():
+    # the design property the preconditioner is chosen for (not a parity pin)
+    n, L = 64, 4
+    traj = synth.traj_spiral(16, 512, n)
+    S = synth.coil_maps(0, n, L)
+    c = toeplitz.kernel(traj, n, n)
+    Kh = toeplitz.khat(c)
+    lam = toeplitz.chan_symbol(c, n, n)
+    AHA = lambda v: toeplitz.normal(v, S, Kh)
+    y = nudft.forward(synth.phantom(0, n), S, traj) + 0.01 * synth.complex_noise(0, (L, traj.shape[0]))
+    b0 = nudft.adjoint(y, S, traj)
+    mu = 1e-2
+    H = lambda v: AHA(v) + mu * v
+    _, i_plain = solvers.pcg(H, b0, np.zeros((n, n)), None, 300, 1e-4)
+    _, i_dc = solvers.pcg(H, b0, np.zeros((n, n)),
+                          lambda v: toeplitz.precond_apply(v, lam, 1.0, mu), 300, 1e-4)
+    assert i_dc["iters"] < 0.8 * i_plain["iters"]
