@@ -1,0 +1,205 @@
+/*
+ * hqs.h - C ABI of the GB300 (sm_103a) multicoil non-Cartesian MRI hot path
+ * of annealed plug-and-play HQS reconstruction (Comby, Lapostolle, Terris,
+ * Ciuciu, "Robust Plug-and-Play Methods for Highly Accelerated Non-Cartesian
+ * MRI Reconstruction", arXiv 2411.01955).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Complex arrays are interleaved float32 pairs (re, im) = hqs_c64.
+ * - Images are (ny, nx) row-major; pixel (iy, ix) has the centred coordinate
+ *   n = (ix - nx/2, iy - ny/2).  Only square images (ny == nx) are accepted.
+ * - Coil maps at the boundary are (L, ny, nx); k-space data are (L, M) in the
+ *   caller's point order; trajectories are (M, 2) float32 (kx, ky) in radians
+ *   per pixel (any real value; the grid is periodic in 2*pi).
+ * - Unless stated otherwise every array argument is a DEVICE pointer owned by
+ *   the caller, valid for the duration of the work the call enqueues.  The
+ *   plan copies what it keeps.
+ * - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
+ *   stream.  Calls enqueue work asynchronously on it unless documented as
+ *   blocking.
+ * - Every call returns an int status: HQS_OK (0) or a negative HQS_ERR_*
+ *   code.  No C++ exception and no abort crosses this boundary.  A plan must
+ *   not be used from two host threads at once (it owns its workspace).
+ */
+#ifndef HQS_GB300_H
+#define HQS_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define HQS_API __attribute__((visibility("default")))
+#else
+#define HQS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define HQS_OK                  0
+#define HQS_ERR_INVALID_ARG    (-1)  /* bad size, NULL pointer, unsupported shape */
+#define HQS_ERR_OOM            (-2)  /* device allocation failed */
+#define HQS_ERR_NOT_CONVERGED  (-3)  /* max_iter reached above rel_tol */
+#define HQS_ERR_BREAKDOWN      (-4)  /* CG curvature <= 0 or non-finite value */
+#define HQS_ERR_TIMEOUT        (-5)  /* a device-side wait exceeded its limit */
+#define HQS_ERR_CALLBACK       (-6)  /* the denoiser callback returned non-zero */
+#define HQS_ERR_CUDA           (-7)  /* a CUDA runtime call failed */
+#define HQS_ERR_UNSUPPORTED    (-8)  /* valid request this build does not implement */
+
+/* operator precision for hqs_toeplitz_normal / dc_solve */
+#define HQS_PREC_FP32    0
+#define HQS_PREC_BF16X3  1   /* DFT-GEMM FFT, bf16 hi/lo split operands, fp32 accumulate */
+#define HQS_PREC_FP16X3  2   /* same with fp16 hi/lo split operands */
+
+/* preconditioners for hqs_dc_solve */
+#define HQS_PRECOND_NONE     0
+#define HQS_PRECOND_DC       1   /* circulant density-compensation preconditioner */
+#define HQS_PRECOND_LEARNED  2   /* conv-net preconditioner in flexible CG */
+
+/* execution modes for hqs_dc_solve */
+#define HQS_SOLVE_PLAIN      0   /* one launch per stage, host checks the residual each iteration */
+#define HQS_SOLVE_FUSED      1   /* one persistent cooperative launch for the whole solve */
+
+#define HQS_MAX_ITERS 512
+
+typedef struct hqs_plan_s* hqs_plan;
+typedef struct { float re, im; } hqs_c64;
+
+typedef struct {
+    int     ny, nx, coils, kernel_width;
+    float   oversamp;
+    int     grid;             /* NUFFT grid size G = oversamp * n */
+    int64_t npoints;          /* M */
+    double  kb_beta;          /* Kaiser-Bessel shape parameter */
+    size_t  device_bytes;     /* device memory held by the plan */
+    int     nsub;             /* spreading sub-problems */
+    int     tile;             /* spreading tile edge on the grid */
+} hqs_plan_info;
+
+typedef struct {
+    int    iterations;        /* H applications inside the loop */
+    int    status;            /* HQS_OK, HQS_ERR_NOT_CONVERGED or HQS_ERR_BREAKDOWN */
+    int    fallback;          /* 1 if the learned preconditioner fell back to DC-PCG */
+    int    reserved;
+    double rhs_norm;          /* ||rhs|| (fp64) */
+    double rel_residual;      /* final ||r|| / ||rhs|| of the CG recursion */
+    double res_history[HQS_MAX_ITERS + 1];  /* ||r_i|| / ||rhs||, i = 0..iterations */
+} hqs_solve_info;
+
+/* Denoiser callback for hqs_run: D_sigma of the PnP-HQS update (Sec. 3.3).
+ * `in` and `out` are device (ny, nx) images borrowed for the call; the
+ * callback must only enqueue work on `stream` (or finish it) and return 0,
+ * any other value aborts hqs_run with HQS_ERR_CALLBACK. */
+typedef int (*hqs_denoiser_fn)(void* user, const hqs_c64* in, hqs_c64* out,
+                               int ny, int nx, float sigma, void* stream);
+
+/* Parameters of the built-in Gaussian-smoothing denoiser: blur std
+ * s = kappa * sigma / sigma0 pixels (sigma0 <= 0 means s = sigma). */
+typedef struct { float kappa; float sigma0; } hqs_gauss_params;
+
+/* ------------------------------------------------------------ plan (a1) */
+/* Builds the operator A = sampling o NUFFT o coil sensitivities of Eq. (1)
+ * (Sec. 2.1) for one trajectory: sorts the M points into grid tiles and
+ * spreading sub-problems, tabulates the Kaiser-Bessel deapodisation, copies
+ * the coil maps into the plan (coil-innermost), computes the Toeplitz kernel
+ * t(d) = Npix^-1 sum_j exp(i k_j.d) of A^H A on the 2N grid with its FFT, and
+ * the density symbol of the circulant CG preconditioner.
+ *   traj         (M, 2) float32 device, radians per pixel
+ *   smaps        (coils, ny, nx) complex device; Sum_l |S_l|^2 need not be 1
+ *   kernel_width W in [2, 8]; oversamp * ny must be a supported FFT size
+ *   (supported n: 16, 32, 64, 128, 256, 320, 384 with oversamp 2; any
+ *   oversamp giving G in {32, 64, 128, 256, 320, 384, 512, 640, 768}).
+ * BLOCKING: returns after the plan is ready.  On error *out is NULL. */
+HQS_API int hqs_plan_create(hqs_plan* out, const float* traj, int64_t M, int ny, int nx,
+                    int coils, const hqs_c64* smaps, int kernel_width,
+                    float oversamp, void* stream);
+HQS_API void hqs_plan_destroy(hqs_plan plan);
+HQS_API int hqs_plan_get_info(hqs_plan plan, hqs_plan_info* info);   /* host struct */
+
+/* --------------------------------------------------------- forward (a2) */
+/* y = A x, Eq. (1): y_l[j] = Npix^-1/2 sum_n S_l[n] x[n] exp(-i k_j.n),
+ * by gridding (apodised, zero-padded FFT on the oversampled grid, KB
+ * interpolation).  x: (ny, nx); y: (L, M). */
+HQS_API int hqs_forward(hqs_plan plan, const hqs_c64* x, hqs_c64* y, void* stream);
+
+/* --------------------------------------------------------- adjoint (a3) */
+/* x = A^H y (Sec. 3.4 uses A^H), the exact transpose of hqs_forward:
+ * KB spreading (shared-memory tiles), inverse FFT, deapodisation, coil
+ * combination with conj(S_l).  y: (L, M); x: (ny, nx). */
+HQS_API int hqs_adjoint(hqs_plan plan, const hqs_c64* y, hqs_c64* x, void* stream);
+
+/* ------------------------------------------------- Toeplitz normal (a4) */
+/* out = A^H A x (Sec. 3.4, A = F_Omega (x) S_l) through the exact 2N
+ * circulant embedding of F^H F; never touches the trajectory.
+ * precision: HQS_PREC_FP32 (in-house FFTs) or HQS_PREC_BF16X3 / _FP16X3
+ * (FFT stages as split hi/lo tensor-core DFT-GEMMs, fp32 accumulation). */
+HQS_API int hqs_toeplitz_normal(hqs_plan plan, const hqs_c64* x, hqs_c64* out,
+                        int precision, void* stream);
+
+/* ------------------------------------------- preconditioner apply (a5) */
+/* z = M^-1 r for H = a A^H A + b I: z = IFFT_N(FFT_N(r) * s^-1/2),
+ * s = max(a*max(lam,0) + b, b/4), lam the gridded sampling density
+ * (eigenvalues of T. Chan's circulant approximation of F^H F). b > 0. */
+HQS_API int hqs_precond_apply(hqs_plan plan, float a, float b, const hqs_c64* r,
+                      hqs_c64* z, void* stream);
+
+/* --------------------------------------------------- DC solve (a5, a7) */
+/* Solves (a A^H A + b I) x = rhs by preconditioned CG with fp64 inner
+ * products: the P-metric proximal step of Sec. 3.4 ("subiteration solver").
+ * For the HQS data-consistency step with P = Id: a = 1, b = mu_k,
+ * rhs = A^H y + mu_k z_k.  x holds the initial guess on entry and the
+ * solution on exit.  Stops when ||r|| <= rel_tol ||rhs|| or after max_iter
+ * (<= HQS_MAX_ITERS) iterations; rel_tol = 0 runs exactly max_iter.
+ * b must be > 0.  precond: HQS_PRECOND_*; mode: HQS_SOLVE_*; precision:
+ * HQS_PREC_*.  If info != NULL the call synchronises `stream` and fills it,
+ * returning HQS_ERR_NOT_CONVERGED / HQS_ERR_BREAKDOWN when applicable; with
+ * info == NULL it only enqueues (capturable in a CUDA graph when mode is
+ * HQS_SOLVE_FUSED) and the outcome is read later with hqs_last_solve_info. */
+HQS_API int hqs_dc_solve(hqs_plan plan, float a, float b, const hqs_c64* rhs, hqs_c64* x,
+                 int max_iter, double rel_tol, int precond, int mode, int precision,
+                 hqs_solve_info* info, void* stream);
+/* Synchronises `stream` and reports the last solve enqueued on this plan. */
+HQS_API int hqs_last_solve_info(hqs_plan plan, hqs_solve_info* info, void* stream);
+
+/* ------------------------------------------------ HQS outer loop (a6) */
+/* Annealed PnP-HQS (Sec. 3.3): for k = k0..K-1
+ *   u_k = prox^P_{gamma_k f}(x_k), P = c0 I + c1 A^H A (Sec. 3.4),
+ *         i.e. ((1 + c1 mu_k) A^H A + c0 mu_k I) u = A^H y + mu_k (c0 x_k + c1 A^H A x_k),
+ *         cg_iters DC-preconditioned CG iterations warm-started at x_k;
+ *   x_{k+1} = D_{sigma_k}(u_k).
+ * mu, sigma: HOST arrays of K floats (mu_k = 1/gamma_k).  y: (L, M) device;
+ * x: (ny, nx) device, x_{k0} on entry, x_K on exit.  denoiser NULL selects
+ * the built-in Gaussian smoothing with `user` pointing to hqs_gauss_params
+ * (NULL: kappa 1.5, sigma0 = sigma[0]).  Resuming from k0 with x_{k0} gives
+ * the same x_K as an uninterrupted run: the Toeplitz/CG iterations have no
+ * atomics and fixed-order reductions; only A^H y (float atomics in the
+ * spreading) may differ in the last bits between calls.
+ * The loop enqueues on `stream` and
+ * calls the callback from the calling thread between outer iterations; each
+ * DC step synchronises `stream` once per CG iteration (plain mode). */
+HQS_API int hqs_run(hqs_plan plan, const hqs_c64* y, hqs_c64* x, const float* mu,
+            const float* sigma, int K, int k0, int cg_iters, float c0, float c1,
+            hqs_denoiser_fn denoiser, void* user, void* stream);
+
+/* Built-in denoiser (stand-in for the trained prior of Sec. 4.2): separable
+ * Gaussian blur of real and imaginary parts, std s pixels (see
+ * hqs_gauss_params), radius ceil(3 s), taps normalised to sum 1, periodic
+ * boundary; copies in to out when s < 0.1.  Matches hqs_denoiser_fn. */
+HQS_API int hqs_gaussian_denoise(void* user, const hqs_c64* in, hqs_c64* out,
+                         int ny, int nx, float sigma, void* stream);
+
+/* --------------------------------------------------- power iteration */
+/* Largest eigenvalue of A^H A by `iters` power iterations from a fixed seed
+ * (alpha = 1/||A^H A|| for the F-1 and Chebyshev metrics of Sec. 3.4).
+ * BLOCKING; result in *lam_max (host). */
+HQS_API int hqs_power_iteration(hqs_plan plan, int iters, double* lam_max, void* stream);
+
+HQS_API const char* hqs_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HQS_GB300_H */

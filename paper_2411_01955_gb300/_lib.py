@@ -1,0 +1,277 @@
+"""ctypes binding of include/hqs.h (argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import torch
+
+HQS_OK = 0
+HQS_ERR_INVALID_ARG = -1
+HQS_ERR_OOM = -2
+HQS_ERR_NOT_CONVERGED = -3
+HQS_ERR_BREAKDOWN = -4
+HQS_ERR_TIMEOUT = -5
+HQS_ERR_CALLBACK = -6
+HQS_ERR_CUDA = -7
+HQS_ERR_UNSUPPORTED = -8
+
+HQS_PREC_FP32, HQS_PREC_BF16X3, HQS_PREC_FP16X3 = 0, 1, 2
+HQS_PRECOND_NONE, HQS_PRECOND_DC, HQS_PRECOND_LEARNED = 0, 1, 2
+HQS_SOLVE_PLAIN, HQS_SOLVE_FUSED = 0, 1
+HQS_MAX_ITERS = 512
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+
+
+def library_path() -> str:
+    return os.path.join(_PKG, "libhqs_gb300.so")
+
+
+class PlanInfo(C.Structure):
+    _fields_ = [("ny", C.c_int), ("nx", C.c_int), ("coils", C.c_int), ("kernel_width", C.c_int),
+                ("oversamp", C.c_float), ("grid", C.c_int), ("npoints", C.c_int64),
+                ("kb_beta", C.c_double), ("device_bytes", C.c_size_t), ("nsub", C.c_int),
+                ("tile", C.c_int)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("status", C.c_int), ("fallback", C.c_int),
+                ("reserved", C.c_int), ("rhs_norm", C.c_double), ("rel_residual", C.c_double),
+                ("res_history", C.c_double * (HQS_MAX_ITERS + 1))]
+
+    def history(self):
+        return [self.res_history[i] for i in range(self.iterations + 1)]
+
+
+class GaussParams(C.Structure):
+    _fields_ = [("kappa", C.c_float), ("sigma0", C.c_float)]
+
+
+DENOISER_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int,
+                          C.c_float, C.c_void_p)
+
+_lock = threading.Lock()
+_lib = None
+
+_SIGS = {
+    "hqs_plan_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_void_p, C.c_int64, C.c_int, C.c_int,
+                                  C.c_int, C.c_void_p, C.c_int, C.c_float, C.c_void_p]),
+    "hqs_plan_destroy": (None, [C.c_void_p]),
+    "hqs_plan_get_info": (C.c_int, [C.c_void_p, C.POINTER(PlanInfo)]),
+    "hqs_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "hqs_adjoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "hqs_toeplitz_normal": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "hqs_precond_apply": (C.c_int, [C.c_void_p, C.c_float, C.c_float, C.c_void_p, C.c_void_p,
+                                    C.c_void_p]),
+    "hqs_dc_solve": (C.c_int, [C.c_void_p, C.c_float, C.c_float, C.c_void_p, C.c_void_p, C.c_int,
+                               C.c_double, C.c_int, C.c_int, C.c_int, C.POINTER(SolveInfo),
+                               C.c_void_p]),
+    "hqs_last_solve_info": (C.c_int, [C.c_void_p, C.POINTER(SolveInfo), C.c_void_p]),
+    "hqs_run": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_float),
+                          C.POINTER(C.c_float), C.c_int, C.c_int, C.c_int, C.c_float, C.c_float,
+                          C.c_void_p, C.c_void_p, C.c_void_p]),
+    "hqs_gaussian_denoise": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int,
+                                       C.c_float, C.c_void_p]),
+    "hqs_power_iteration": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_void_p]),
+    "hqs_status_string": (C.c_char_p, [C.c_int]),
+}
+
+
+def library():
+    """Load the compiled library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = library_path()
+            if not os.path.exists(path):
+                raise RuntimeError(
+                    f"{path} is missing: build it with paper_2411_01955_gb300.build.build() "
+                    "(there is no CPU fallback)")
+            lib = C.CDLL(path)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+class HqsError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} ({status})")
+
+
+def status_string(status: int) -> str:
+    return library().hqs_status_string(int(status)).decode()
+
+
+def _check(rc: int, what: str):
+    if rc != HQS_OK:
+        raise HqsError(rc, what)
+
+
+def _ptr(t, dtype=None, name="tensor"):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+class Plan:
+    """Owns an hqs_plan (hqs_plan_create / hqs_plan_destroy)."""
+
+    def __init__(self, handle, ny, nx, coils, npoints):
+        self.handle = handle
+        self.ny, self.nx, self.coils, self.npoints = ny, nx, coils, npoints
+
+    def info(self) -> PlanInfo:
+        inf = PlanInfo()
+        _check(library().hqs_plan_get_info(self.handle, C.byref(inf)), "hqs_plan_get_info")
+        return inf
+
+    def close(self):
+        if self.handle:
+            library().hqs_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def plan_create(traj, ny, nx, smaps, kernel_width=6, oversamp=2.0, stream=None) -> Plan:
+    """traj (M, 2) float32 CUDA; smaps (L, ny, nx) complex64 CUDA."""
+    lib = library()
+    h = C.c_void_p()
+    M = int(traj.shape[0])
+    rc = lib.hqs_plan_create(C.byref(h), _ptr(traj, torch.float32, "traj"), M, int(ny), int(nx),
+                             int(smaps.shape[0]), _ptr(smaps, torch.complex64, "smaps"),
+                             int(kernel_width), float(oversamp), _stream(stream))
+    _check(rc, "hqs_plan_create")
+    return Plan(h, int(ny), int(nx), int(smaps.shape[0]), M)
+
+
+def forward(plan: Plan, x, y, stream=None):
+    _check(library().hqs_forward(plan.handle, _ptr(x, torch.complex64, "x"),
+                                 _ptr(y, torch.complex64, "y"), _stream(stream)), "hqs_forward")
+    return y
+
+
+def adjoint(plan: Plan, y, x, stream=None):
+    _check(library().hqs_adjoint(plan.handle, _ptr(y, torch.complex64, "y"),
+                                 _ptr(x, torch.complex64, "x"), _stream(stream)), "hqs_adjoint")
+    return x
+
+
+def toeplitz_normal(plan: Plan, x, out, precision=HQS_PREC_FP32, stream=None):
+    _check(library().hqs_toeplitz_normal(plan.handle, _ptr(x, torch.complex64, "x"),
+                                         _ptr(out, torch.complex64, "out"), int(precision),
+                                         _stream(stream)), "hqs_toeplitz_normal")
+    return out
+
+
+def precond_apply(plan: Plan, a, b, r, z, stream=None):
+    _check(library().hqs_precond_apply(plan.handle, float(a), float(b), _ptr(r, torch.complex64, "r"),
+                                       _ptr(z, torch.complex64, "z"), _stream(stream)),
+           "hqs_precond_apply")
+    return z
+
+
+def dc_solve(plan: Plan, a, b, rhs, x, max_iter=30, rel_tol=1e-4, precond=HQS_PRECOND_DC,
+             mode=HQS_SOLVE_PLAIN, precision=HQS_PREC_FP32, want_info=True, stream=None,
+             check=True):
+    """Solves (a A^H A + b I) x = rhs in place; returns SolveInfo (or None)."""
+    info = SolveInfo() if want_info else None
+    rc = library().hqs_dc_solve(plan.handle, float(a), float(b), _ptr(rhs, torch.complex64, "rhs"),
+                                _ptr(x, torch.complex64, "x"), int(max_iter), float(rel_tol),
+                                int(precond), int(mode), int(precision),
+                                C.byref(info) if info is not None else None, _stream(stream))
+    if check and rc not in (HQS_OK, HQS_ERR_NOT_CONVERGED):
+        raise HqsError(rc, "hqs_dc_solve")
+    if info is not None:
+        info.rc = rc
+    return info
+
+
+def last_solve_info(plan: Plan, stream=None) -> SolveInfo:
+    info = SolveInfo()
+    _check(library().hqs_last_solve_info(plan.handle, C.byref(info), _stream(stream)),
+           "hqs_last_solve_info")
+    return info
+
+
+def _wrap_device(ptr, shape):
+    class _Arr:
+        __cuda_array_interface__ = {"shape": tuple(shape), "typestr": "<c8", "data": (ptr, False),
+                                    "version": 3, "strides": None}
+    return torch.as_tensor(_Arr(), device="cuda")
+
+
+def hqs_run(plan: Plan, y, x, mu, sigma, K=None, k0=0, cg_iters=5, c0=1.0, c1=0.0,
+            denoiser=None, gauss=None, stream=None):
+    """Annealed PnP-HQS; `denoiser` is None (built-in Gaussian smoothing, with
+    optional gauss=(kappa, sigma0)) or a callable(in_tensor, out_tensor, sigma)
+    that enqueues work on the current stream and returns 0 on success."""
+    lib = library()
+    K = len(mu) if K is None else int(K)
+    mu_c = (C.c_float * K)(*[float(v) for v in mu[:K]])
+    sg_c = (C.c_float * K)(*[float(v) for v in sigma[:K]])
+    user = None
+    cb = None
+    keep = []
+    if denoiser is None:
+        if gauss is not None:
+            gp = GaussParams(float(gauss[0]), float(gauss[1]))
+            keep.append(gp)
+            user = C.cast(C.pointer(gp), C.c_void_p)
+    else:
+        ny, nx = plan.ny, plan.nx
+
+        def _cb(_user, pin, pout, h, w, s, _stream_ptr):
+            try:
+                tin = _wrap_device(pin, (h, w))
+                tout = _wrap_device(pout, (h, w))
+                return int(denoiser(tin, tout, float(s)) or 0)
+            except Exception:
+                return 1
+        cb = DENOISER_FN(_cb)
+        keep.append(cb)
+    rc = lib.hqs_run(plan.handle, _ptr(y, torch.complex64, "y"), _ptr(x, torch.complex64, "x"),
+                     mu_c, sg_c, K, int(k0), int(cg_iters), float(c0), float(c1),
+                     C.cast(cb, C.c_void_p) if cb is not None else None, user, _stream(stream))
+    _check(rc, "hqs_run")
+    return x
+
+
+def gaussian_denoise(x, out, sigma, gauss=None, stream=None):
+    gp = None
+    if gauss is not None:
+        gp = GaussParams(float(gauss[0]), float(gauss[1]))
+    ny, nx = x.shape[-2], x.shape[-1]
+    _check(library().hqs_gaussian_denoise(C.cast(C.pointer(gp), C.c_void_p) if gp else None,
+                                          _ptr(x, torch.complex64, "x"),
+                                          _ptr(out, torch.complex64, "out"), int(ny), int(nx),
+                                          float(sigma), _stream(stream)), "hqs_gaussian_denoise")
+    return out
+
+
+def power_iteration(plan: Plan, iters=50, stream=None) -> float:
+    lam = C.c_double()
+    _check(library().hqs_power_iteration(plan.handle, int(iters), C.byref(lam), _stream(stream)),
+           "hqs_power_iteration")
+    return lam.value

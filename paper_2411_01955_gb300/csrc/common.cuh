@@ -1,0 +1,51 @@
+// Shared device/host helpers for the sm_103a kernels of the HQS hot path.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hqs.h"
+
+#define HQS_DEV __device__ __forceinline__
+
+// ---------------------------------------------------------------- complex
+HQS_DEV float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+HQS_DEV float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+HQS_DEV float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+HQS_DEV float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// conj(a) * b
+HQS_DEV float2 cmulc(float2 a, float2 b) {
+    return make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+HQS_DEV float2 cfma(float2 a, float2 b, float2 acc) {   // acc + a*b
+    acc.x = fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x));
+    acc.y = fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y));
+    return acc;
+}
+// multiply by -i (forward) or +i (inverse)
+template <bool INV> HQS_DEV float2 mul_mi(float2 a) {
+    return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+// ---------------------------------------------------------------- errors
+#define HQS_CUDA_TRY(expr)                                   \
+    do {                                                     \
+        cudaError_t e_ = (expr);                             \
+        if (e_ != cudaSuccess) {                             \
+            hqs_note_cuda_error(e_, #expr, __FILE__, __LINE__); \
+            return (e_ == cudaErrorMemoryAllocation) ? HQS_ERR_OOM : HQS_ERR_CUDA; \
+        }                                                    \
+    } while (0)
+
+void hqs_note_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+
+// Device error word bits (per plan), read back at sync points.
+#define HQS_DEVERR_TIMEOUT   1u
+#define HQS_DEVERR_BREAKDOWN 2u
+#define HQS_DEVERR_BOUNDS    4u
+
+// ---------------------------------------------------------------- math
+static inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
+static inline int64_t ceil_div64(int64_t a, int64_t b) { return (a + b - 1) / b; }

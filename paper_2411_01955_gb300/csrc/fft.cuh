@@ -1,0 +1,269 @@
+// In-house batched FFT on shared memory for the sizes the hot path uses.
+//
+// A CTA transforms up to kLines lines of length N stored line-innermost in
+// shared memory (element (pos, line) at s[pos * kLines + line]), which is the
+// coil-innermost layout the grids use in global memory, so loads and stores
+// are contiguous over coils.  The transform is a mixed-radix Stockham
+// autosort FFT: stage with radix R after a product P of earlier radices reads
+// x[i + r*N/R], multiplies by w_{P R}^(r k) (k = i mod P), applies the
+// radix-R DFT and writes y[(i - k) R + k + s P].  Each thread owns E elements
+// of one line (E divisible by every radix of the size), holds them in
+// registers across the barrier, so the transform runs in place in one buffer.
+// Forward uses exp(-2 pi i m / N), inverse its conjugate; neither scales.
+#pragma once
+
+#include "common.cuh"
+
+namespace hqs {
+
+constexpr float kSqrtHalf = 0.70710678118654752440f;
+// Shared-memory stride between positions of a line: a compile-time constant
+// keeps the per-element address arithmetic out of the register budget.
+constexpr int kLines = 16;
+
+template <int R, bool INV> struct Dft;
+
+template <bool INV> struct Dft<2, INV> {
+    HQS_DEV static void run(float2* v) {
+        float2 a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    }
+};
+
+template <bool INV> struct Dft<3, INV> {
+    HQS_DEV static void run(float2* v) {
+        // w = exp(-+2 pi i / 3) = -1/2 -+ i sqrt(3)/2
+        const float h = 0.86602540378443864676f;
+        float2 t = cadd(v[1], v[2]);
+        float2 d = csub(v[1], v[2]);
+        float2 m = make_float2(v[0].x - 0.5f * t.x, v[0].y - 0.5f * t.y);
+        float2 j = mul_mi<INV>(cscale(d, h));      // -+ i * sqrt(3)/2 * d
+        v[0] = cadd(v[0], t);
+        v[1] = cadd(m, j);
+        v[2] = csub(m, j);
+    }
+};
+
+template <bool INV> struct Dft<4, INV> {
+    HQS_DEV static void run(float2* v) {
+        float2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+        float2 t2 = cadd(v[1], v[3]), t3 = mul_mi<INV>(csub(v[1], v[3]));
+        v[0] = cadd(t0, t2);
+        v[2] = csub(t0, t2);
+        v[1] = cadd(t1, t3);
+        v[3] = csub(t1, t3);
+    }
+};
+
+template <bool INV> struct Dft<5, INV> {
+    HQS_DEV static void run(float2* v) {
+        const float c1 = 0.30901699437494742410f;   // cos(2 pi / 5)
+        const float c2 = -0.80901699437494742410f;  // cos(4 pi / 5)
+        const float s1 = 0.95105651629515357212f;   // sin(2 pi / 5)
+        const float s2 = 0.58778525229247312917f;   // sin(4 pi / 5)
+        float2 a1 = cadd(v[1], v[4]), b1 = csub(v[1], v[4]);
+        float2 a2 = cadd(v[2], v[3]), b2 = csub(v[2], v[3]);
+        float2 x0 = v[0];
+        float2 m1 = make_float2(x0.x + c1 * a1.x + c2 * a2.x, x0.y + c1 * a1.y + c2 * a2.y);
+        float2 m2 = make_float2(x0.x + c2 * a1.x + c1 * a2.x, x0.y + c2 * a1.y + c1 * a2.y);
+        // forward: out1 = m1 - i(s1 b1 + s2 b2); out2 = m2 - i(s2 b1 - s1 b2)
+        float2 n1 = mul_mi<INV>(make_float2(s1 * b1.x + s2 * b2.x, s1 * b1.y + s2 * b2.y));
+        float2 n2 = mul_mi<INV>(make_float2(s2 * b1.x - s1 * b2.x, s2 * b1.y - s1 * b2.y));
+        v[0] = make_float2(x0.x + a1.x + a2.x, x0.y + a1.y + a2.y);
+        v[1] = cadd(m1, n1);
+        v[4] = csub(m1, n1);
+        v[2] = cadd(m2, n2);
+        v[3] = csub(m2, n2);
+    }
+};
+
+template <bool INV> struct Dft<8, INV> {
+    HQS_DEV static void run(float2* v) {
+        float2 e[4] = {v[0], v[2], v[4], v[6]};
+        float2 o[4] = {v[1], v[3], v[5], v[7]};
+        Dft<4, INV>::run(e);
+        Dft<4, INV>::run(o);
+        // w8^1, w8^2, w8^3 with w8 = exp(-+ i pi / 4)
+        float2 o1, o2, o3;
+        if (!INV) {
+            o1 = make_float2((o[1].x + o[1].y) * kSqrtHalf, (o[1].y - o[1].x) * kSqrtHalf);
+            o3 = make_float2((o[3].y - o[3].x) * kSqrtHalf, -(o[3].x + o[3].y) * kSqrtHalf);
+        } else {
+            o1 = make_float2((o[1].x - o[1].y) * kSqrtHalf, (o[1].x + o[1].y) * kSqrtHalf);
+            o3 = make_float2(-(o[3].x + o[3].y) * kSqrtHalf, (o[3].x - o[3].y) * kSqrtHalf);
+        }
+        o2 = mul_mi<INV>(o[2]);
+        v[0] = cadd(e[0], o[0]);
+        v[4] = csub(e[0], o[0]);
+        v[1] = cadd(e[1], o1);
+        v[5] = csub(e[1], o1);
+        v[2] = cadd(e[2], o2);
+        v[6] = csub(e[2], o2);
+        v[3] = cadd(e[3], o3);
+        v[7] = csub(e[3], o3);
+    }
+};
+
+// One Stockham stage.  `s` points at element (0, line); consecutive positions
+// are kLines float2 apart.  Threads with act == false only take the barriers.
+template <int N, int E, int R, int P, bool INV>
+HQS_DEV void fft_stage(float2* s, int t, bool act, const float2* __restrict__ tw) {
+    constexpr int st = kLines;
+    constexpr int TPL = N / E;
+    constexpr int NB = N / R;
+    constexpr int BPT = E / R;
+    static_assert(E % R == 0, "radix must divide elements per thread");
+    static_assert(NB == TPL * BPT, "butterfly split");
+    float2 v[E];
+    if (act) {
+#pragma unroll
+        for (int b = 0; b < BPT; ++b) {
+            const int i = t + b * TPL;
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[b * R + r] = s[(i + r * NB) * st];
+        }
+    }
+    __syncthreads();
+    if (act) {
+#pragma unroll
+        for (int b = 0; b < BPT; ++b) {
+            const int i = t + b * TPL;
+            const int k = i % P;
+            if (P > 1) {
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    float2 w = tw[r * k * (N / (P * R))];
+                    if (INV) w.y = -w.y;
+                    v[b * R + r] = cmul(v[b * R + r], w);
+                }
+            }
+            Dft<R, INV>::run(&v[b * R]);
+            const int j = (i - k) * R + k;
+#pragma unroll
+            for (int r = 0; r < R; ++r) s[(j + r * P) * st] = v[b * R + r];
+        }
+    }
+    __syncthreads();
+}
+
+// Size table: elements per thread and radix sequence.
+template <int N> struct FftSize;
+
+#define HQS_FFT_SIZE(NN, EE, ...)                                                     \
+    template <> struct FftSize<NN> {                                                  \
+        static constexpr int E = EE;                                                  \
+        static constexpr int TPL = NN / EE;                                           \
+        template <bool INV>                                                           \
+        HQS_DEV static void run(float2* s, int t, bool act, const float2* tw) {        \
+            __VA_ARGS__                                                               \
+        }                                                                             \
+    };
+
+#define ST(R, P) fft_stage<NN_, E_, R, P, INV>(s, t, act, tw);
+
+#define NN_ 16
+#define E_ 4
+HQS_FFT_SIZE(16, 4, ST(4, 1) ST(4, 4))
+#undef NN_
+#undef E_
+#define NN_ 32
+#define E_ 8
+HQS_FFT_SIZE(32, 8, ST(8, 1) ST(4, 8))
+#undef NN_
+#undef E_
+#define NN_ 64
+#define E_ 8
+HQS_FFT_SIZE(64, 8, ST(8, 1) ST(8, 8))
+#undef NN_
+#undef E_
+#define NN_ 128
+#define E_ 8
+HQS_FFT_SIZE(128, 8, ST(8, 1) ST(4, 8) ST(4, 32))
+#undef NN_
+#undef E_
+#define NN_ 256
+#define E_ 8
+HQS_FFT_SIZE(256, 8, ST(8, 1) ST(8, 8) ST(4, 64))
+#undef NN_
+#undef E_
+#define NN_ 320
+#define E_ 40
+HQS_FFT_SIZE(320, 40, ST(8, 1) ST(8, 8) ST(5, 64))
+#undef NN_
+#undef E_
+#define NN_ 384
+#define E_ 24
+HQS_FFT_SIZE(384, 24, ST(8, 1) ST(8, 8) ST(3, 64) ST(2, 192))
+#undef NN_
+#undef E_
+#define NN_ 512
+#define E_ 8
+HQS_FFT_SIZE(512, 8, ST(8, 1) ST(8, 8) ST(8, 64))
+#undef NN_
+#undef E_
+#define NN_ 640
+#define E_ 40
+HQS_FFT_SIZE(640, 40, ST(8, 1) ST(8, 8) ST(5, 64) ST(2, 320))
+#undef NN_
+#undef E_
+#define NN_ 768
+#define E_ 24
+HQS_FFT_SIZE(768, 24, ST(8, 1) ST(8, 8) ST(4, 64) ST(3, 256))
+#undef NN_
+#undef E_
+#undef ST
+#undef HQS_FFT_SIZE
+
+// Transform `nlines` (<= kLines) lines held at s[pos * kLines + line] with the
+// whole CTA: thread (line = tid % lpg, t = tid / lpg) owns E elements of one
+// line, lpg = blockDim.x / TPL >= nlines (launch with fft_threads).  The
+// caller synchronises before (after filling s); this routine ends with a
+// barrier.  (A loop over line groups here doubles register use, so the launch
+// shape covers every line at once instead.)
+template <int N, bool INV>
+HQS_DEV void block_fft(float2* s, int nlines, const float2* tw) {
+    constexpr int TPL = FftSize<N>::TPL;
+    const int lpg = blockDim.x / TPL;
+    int tid;
+    // The thread index is read through a volatile move so that the per-thread
+    // address and twiddle-index arithmetic of the stages (a function of the
+    // thread index only) is not hoisted out of a caller's loop, which would
+    // keep ~2E extra registers live across the loop and spill.
+    asm volatile("mov.u32 %0, %%tid.x;" : "=r"(tid));
+    const int ll = tid % lpg;
+    const int t = tid / lpg;
+    const bool act = (ll < nlines) && (t < TPL);
+    FftSize<N>::template run<INV>(s + (act ? ll : 0), t, act, tw);
+}
+
+// Threads per CTA for a pass over `nlines` (<= kLines) lines of size N: every
+// line in one group, rounded up to whole warps (TPL is a power of two).
+template <int N> inline int fft_threads(int nlines) {
+    constexpr int TPL = FftSize<N>::TPL;
+    return ((nlines * TPL + 31) / 32) * 32;
+}
+
+// Dispatch a functor templated on the FFT size.
+template <class F> inline int dispatch_fft_size(int n, F&& f) {
+    switch (n) {
+        case 16: return f.template operator()<16>();
+        case 32: return f.template operator()<32>();
+        case 64: return f.template operator()<64>();
+        case 128: return f.template operator()<128>();
+        case 256: return f.template operator()<256>();
+        case 320: return f.template operator()<320>();
+        case 384: return f.template operator()<384>();
+        case 512: return f.template operator()<512>();
+        case 640: return f.template operator()<640>();
+        case 768: return f.template operator()<768>();
+        default: return HQS_ERR_INVALID_ARG;
+    }
+}
+
+inline bool fft_size_supported(int n) {
+    return n == 16 || n == 32 || n == 64 || n == 128 || n == 256 || n == 320 || n == 384 ||
+           n == 512 || n == 640 || n == 768;
+}
+
+}  // namespace hqs

@@ -1,0 +1,190 @@
+// Single-image 2D FFT passes: in-place transforms used at plan time (the
+// Toeplitz kernel spectrum Khat and the density symbol) and the circulant
+// density-compensation preconditioner applied once per CG iteration:
+//   z = IFFT_N(FFT_N(r) * m),  m = s^-1/2,  s = max(a*max(lam,0) + b, b/4).
+#include "fft.cuh"
+#include "plan.cuh"
+
+using namespace hqs;
+
+// Q consecutive rows of a [rows][N] image per CTA, in place.
+template <int N, bool INV>
+__global__ void k_fft_rows(float2* __restrict__ data, int rows, int Q, const float2* __restrict__ tw) {
+    extern __shared__ float2 s[];
+    const int r0 = blockIdx.x * Q;
+    const int lines = min(Q, rows - r0);
+    for (int e = threadIdx.x; e < N * lines; e += blockDim.x) {
+        const int q = e / N, pos = e % N;
+        s[pos * kLines + q] = data[(int64_t)(r0 + q) * N + pos];
+    }
+    __syncthreads();
+    block_fft<N, INV>(s, lines, tw);
+    for (int e = threadIdx.x; e < N * lines; e += blockDim.x) {
+        const int q = e / N, pos = e % N;
+        data[(int64_t)(r0 + q) * N + pos] = s[pos * kLines + q];
+    }
+}
+
+// Q adjacent columns of a [N][cols] image per CTA, in place.
+template <int N, bool INV>
+__global__ void k_fft_cols(float2* __restrict__ data, int cols, int Q, const float2* __restrict__ tw) {
+    extern __shared__ float2 s[];
+    const int c0 = blockIdx.x * Q;
+    const int lines = min(Q, cols - c0);
+    for (int e = threadIdx.x; e < N * lines; e += blockDim.x) {
+        const int pos = e / lines, q = e % lines;
+        s[pos * kLines + q] = data[(int64_t)pos * cols + c0 + q];
+    }
+    __syncthreads();
+    block_fft<N, INV>(s, lines, tw);
+    for (int e = threadIdx.x; e < N * lines; e += blockDim.x) {
+        const int pos = e / lines, q = e % lines;
+        data[(int64_t)pos * cols + c0 + q] = s[pos * kLines + q];
+    }
+}
+
+template <int N, bool INV>
+static int fft2d_impl(const hqs_plan_s* p, float2* data, cudaStream_t st) {
+    const float2* tw = plan_twiddles(p, N);
+    if (!tw) return HQS_ERR_INVALID_ARG;
+    const int Q = 16;
+    const int th = fft_threads<N>(Q);
+    const size_t sm = (size_t)N * kLines * sizeof(float2);
+    HQS_CUDA_TRY(cudaFuncSetAttribute(k_fft_rows<N, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    HQS_CUDA_TRY(cudaFuncSetAttribute(k_fft_cols<N, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_fft_rows<N, INV><<<ceil_div(N, Q), th, sm, st>>>(data, N, Q, tw);
+    k_fft_cols<N, INV><<<ceil_div(N, Q), th, sm, st>>>(data, N, Q, tw);
+    HQS_CUDA_TRY(cudaGetLastError());
+    return HQS_OK;
+}
+
+int launch_fft2d(const hqs_plan_s* p, float2* data, int N, bool inverse, cudaStream_t st) {
+    return dispatch_fft_size(N, [&]<int NN>() {
+        return inverse ? fft2d_impl<NN, true>(p, data, st) : fft2d_impl<NN, false>(p, data, st);
+    });
+}
+
+// ------------------------------------------------------ preconditioner
+
+// rows: out[row][:] = FFT_N(in[row][:]) for Q rows per CTA
+template <int N>
+__global__ void k_pc_rows_fwd(const float2* __restrict__ in, float2* __restrict__ out, int Q,
+                              const float2* __restrict__ tw, const CgScalars* __restrict__ cg) {
+    if (cg && cg->done) return;
+    extern __shared__ float2 s[];
+    const int r0 = blockIdx.x * Q;
+    const int lines = min(Q, N - r0);
+    for (int e = threadIdx.x; e < N * lines; e += blockDim.x) {
+        const int q = e / N, pos = e % N;
+        s[pos * kLines + q] = in[(int64_t)(r0 + q) * N + pos];
+    }
+    __syncthreads();
+    block_fft<N, false>(s, lines, tw);
+    for (int e = threadIdx.x; e < N * lines; e += blockDim.x) {
+        const int q = e / N, pos = e % N;
+        out[(int64_t)(r0 + q) * N + pos] = s[pos * kLines + q];
+    }
+}
+
+// columns: FFT, multiply by m = s^-1/2, optional partial sum of |R|^2 m
+// (Parseval: N^2 <r, z>), inverse FFT; in place on buf.
+template <int N>
+__global__ void k_pc_cols(float2* __restrict__ buf, int Q, const float* __restrict__ lam, float a,
+                          float b, const float2* __restrict__ tw, const CgScalars* __restrict__ cg,
+                          double* __restrict__ part) {
+    if (cg && cg->done) return;
+    extern __shared__ float2 s[];
+    __shared__ double red[32];
+    const int c0 = blockIdx.x * Q;
+    const int lines = min(Q, N - c0);
+    for (int e = threadIdx.x; e < N * lines; e += blockDim.x) {
+        const int pos = e / lines, q = e % lines;
+        s[pos * kLines + q] = buf[(int64_t)pos * N + c0 + q];
+    }
+    __syncthreads();
+    block_fft<N, false>(s, lines, tw);
+    double acc = 0.0;
+    for (int e = threadIdx.x; e < N * lines; e += blockDim.x) {
+        const int pos = e / lines, q = e % lines;
+        const float l = lam[(int64_t)pos * N + c0 + q];
+        const float sv = fmaxf(fmaf(a, fmaxf(l, 0.f), b), 0.25f * b);
+        const float m = rsqrtf(sv);
+        const float2 v = s[pos * kLines + q];
+        acc += (double)(m * (v.x * v.x + v.y * v.y));
+        s[pos * kLines + q] = cscale(v, m);
+    }
+    if (part) {
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    }
+    __syncthreads();
+    if (part && threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) t += red[w];
+        part[blockIdx.x] = t;
+    }
+    block_fft<N, true>(s, lines, tw);
+    for (int e = threadIdx.x; e < N * lines; e += blockDim.x) {
+        const int pos = e / lines, q = e % lines;
+        buf[(int64_t)pos * N + c0 + q] = s[pos * kLines + q];
+    }
+}
+
+// rows: z[row][:] = IFFT_N(buf[row][:]) / N^2
+template <int N>
+__global__ void k_pc_rows_inv(const float2* __restrict__ buf, float2* __restrict__ z, int Q,
+                              const float2* __restrict__ tw, const CgScalars* __restrict__ cg) {
+    if (cg && cg->done) return;
+    extern __shared__ float2 s[];
+    const int r0 = blockIdx.x * Q;
+    const int lines = min(Q, N - r0);
+    for (int e = threadIdx.x; e < N * lines; e += blockDim.x) {
+        const int q = e / N, pos = e % N;
+        s[pos * kLines + q] = buf[(int64_t)(r0 + q) * N + pos];
+    }
+    __syncthreads();
+    block_fft<N, true>(s, lines, tw);
+    const float sc = 1.0f / ((float)N * (float)N);
+    for (int e = threadIdx.x; e < N * lines; e += blockDim.x) {
+        const int q = e / N, pos = e % N;
+        z[(int64_t)(r0 + q) * N + pos] = cscale(s[pos * kLines + q], sc);
+    }
+}
+
+template <int N>
+static int precond_impl(hqs_plan_s* p, float a, float b, const float2* r, float2* z, bool rows_done,
+                        const CgScalars* cg, double* part, cudaStream_t st) {
+    const float2* tw = plan_twiddles(p, N);
+    const int Q = p->q_rows;
+    const int th = fft_threads<N>(Q);
+    const size_t sm = (size_t)N * kLines * sizeof(float2);
+    const int nb = ceil_div(N, Q);
+    HQS_CUDA_TRY(cudaFuncSetAttribute(k_pc_rows_fwd<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    HQS_CUDA_TRY(cudaFuncSetAttribute(k_pc_cols<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    HQS_CUDA_TRY(cudaFuncSetAttribute(k_pc_rows_inv<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    if (!rows_done) k_pc_rows_fwd<N><<<nb, th, sm, st>>>(r, p->pc_buf, Q, tw, cg);
+    k_pc_cols<N><<<nb, th, sm, st>>>(p->pc_buf, Q, p->lam, a, b, tw, cg, part);
+    k_pc_rows_inv<N><<<nb, th, sm, st>>>(p->pc_buf, z, Q, tw, cg);
+    HQS_CUDA_TRY(cudaGetLastError());
+    return HQS_OK;
+}
+
+// Full preconditioner apply (standalone entry and solver use).  When
+// rows_done is set the forward row pass has already written pc_buf.
+int launch_precond_ex(hqs_plan_s* p, float a, float b, const float2* r, float2* z, bool rows_done,
+                      const CgScalars* cg, double* part, cudaStream_t st) {
+    return dispatch_fft_size(p->n, [&]<int NN>() {
+        return precond_impl<NN>(p, a, b, r, z, rows_done, cg, part, st);
+    });
+}
+
+int launch_precond(hqs_plan_s* p, float a, float b, const float2* r, float2* z, cudaStream_t st) {
+    return launch_precond_ex(p, a, b, r, z, false, nullptr, nullptr, st);
+}
+
+extern "C" int hqs_precond_apply(hqs_plan p, float a, float b, const hqs_c64* r, hqs_c64* z,
+                                 void* stream) {
+    if (!p || !r || !z || !(b > 0.f)) return HQS_ERR_INVALID_ARG;
+    return launch_precond(p, a, b, reinterpret_cast<const float2*>(r), reinterpret_cast<float2*>(z),
+                          (cudaStream_t)stream);
+}

@@ -1,0 +1,16 @@
+// Entry points of the solver variants that are declared in the C ABI but
+// not built yet: they fail loudly with HQS_ERR_UNSUPPORTED instead of
+// falling back to another path.
+#include "solve.cuh"
+
+int pcg_fused(hqs_plan_s*, float, float, const float2*, float2*, int, double, int, int, cudaStream_t) {
+    return HQS_ERR_UNSUPPORTED;
+}
+
+int fcg_learned(hqs_plan_s*, float, float, const float2*, float2*, int, double, int, cudaStream_t) {
+    return HQS_ERR_UNSUPPORTED;
+}
+
+int launch_toeplitz_mixed(hqs_plan_s*, const float2*, float2*, int, cudaStream_t) {
+    return HQS_ERR_UNSUPPORTED;
+}

@@ -1,0 +1,93 @@
+// Internal plan layout shared by the translation units of the library.
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+
+#define HQS_MAX_W 8
+#define HQS_MAX_LC 16          // coils per chunk in the FFT passes
+#define HQS_MAX_BLOCKS 2048    // partial-sum slots per reduction
+#define HQS_SPREAD_MAXPTS 256  // points per spreading sub-problem
+
+// CG scalars kept on the device so that the solve never needs the host
+// between iterations.
+struct CgScalars {
+    double rz;          // <r, z> of the current iterate
+    double pq;          // <p, H p>
+    double alpha, beta;
+    double bnorm;       // ||rhs||
+    double rr;          // ||r||^2
+    double tol2;        // (rel_tol * ||rhs||)^2
+    int it;             // completed iterations
+    int done;           // 1 once converged, failed or out of iterations
+    int status;         // HQS_OK / HQS_ERR_NOT_CONVERGED / HQS_ERR_BREAKDOWN
+    int zero_rhs;       // rhs == 0: solution is exactly 0
+    int max_iter;
+    int fallback;
+};
+
+enum PartialSlot { SLOT_PQ = 0, SLOT_RR = 1, SLOT_BB = 2, SLOT_RZ = 3, SLOT_AUX = 4, NSLOTS = 6 };
+
+struct hqs_plan_s {
+    int device = 0;
+    int n = 0;          // ny == nx
+    int L = 0;          // coils
+    int G = 0;          // NUFFT grid
+    int n2 = 0;         // Toeplitz grid (2n)
+    int W = 0;
+    float oversamp = 2.f;
+    double beta = 0.0;
+    int64_t M = 0;
+    float scale = 1.f;  // Npix^-1/2
+    int LC = 1, nchunk = 1;
+    int tile = 16, nbx = 0, nsub = 0;
+    int q_rows = 8;     // lines per CTA in the single-image FFT passes
+
+    // constant tables and plan data (device)
+    float2* smaps = nullptr;    // [n][n][L]
+    float* apod = nullptr;      // [n] 1/phihat((i - n/2)/G)
+    int4* pts = nullptr;        // sorted points: (i0x, i0y, bits(dx), bits(dy)), i0 in [0, G)
+    int* perm = nullptr;        // sorted -> caller index
+    int4* subs = nullptr;       // (bin, start, count, 0)
+    float* khat = nullptr;      // [n2][n2], includes 1/n2^2
+    float* lam = nullptr;       // [n][n] density symbol
+    float2* tw = nullptr;       // twiddle bank
+    int tw_sizes[4] = {0, 0, 0, 0};
+    int tw_offs[4] = {0, 0, 0, 0};
+
+    // workspace
+    float2* grid = nullptr;     // [G][G][L]
+    float2* work = nullptr;     // [n][max(G, n2)][L]
+    float2* cg_r = nullptr;     // CG vectors, [n][n] each
+    float2* cg_z = nullptr;
+    float2* cg_p = nullptr;
+    float2* cg_q = nullptr;
+    float2* img_tmp = nullptr;  // [n][n] scratch image
+    float2* img_tmp2 = nullptr; // [n][n] scratch image
+    float2* pc_buf = nullptr;   // [n][n] preconditioner spectrum
+    float2* img_b0 = nullptr;   // [n][n] A^H y of the outer loop
+    float2* img_rhs = nullptr;  // [n][n] right-hand side of the outer loop
+    float2* img_u = nullptr;    // [n][n] prox output of the outer loop
+    float2* chunk_buf = nullptr; // [nchunk][n][n] per-coil-chunk partial sums (nchunk > 1)
+    double* partials = nullptr; // [NSLOTS][HQS_MAX_BLOCKS]
+    CgScalars* cg = nullptr;
+    double* hist = nullptr;     // [HQS_MAX_ITERS + 1] ||r_i||^2
+    CgScalars* h_cg = nullptr;  // pinned host mirror
+    double* h_hist = nullptr;
+    unsigned* dev_err = nullptr;
+    unsigned* barrier = nullptr; // grid barrier words for the persistent solve
+    float2* smaps_user = nullptr;
+
+    size_t bytes = 0;
+    std::vector<void*> allocs;
+};
+
+const float2* plan_twiddles(const hqs_plan_s* p, int N);
+
+// launchers implemented in the kernel translation units
+int launch_fwd(hqs_plan_s* p, const float2* x, float2* y, cudaStream_t s);
+int launch_adj(hqs_plan_s* p, const float2* y, float2* x, cudaStream_t s);
+int launch_toeplitz(hqs_plan_s* p, const float2* x, float2* out, cudaStream_t s);
+int launch_fft2d(const hqs_plan_s* p, float2* data, int N, bool inverse, cudaStream_t s);
+int launch_precond(hqs_plan_s* p, float a, float b, const float2* r, float2* z, cudaStream_t s);

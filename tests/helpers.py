@@ -1,0 +1,44 @@
+"""Shared helpers for the GPU parity tests (inputs from synth, expected values
+from the oracle, results from the CUDA library through its C ABI)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+
+def rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+def to_dev(a, dtype=None):
+    a = np.ascontiguousarray(a)
+    if np.iscomplexobj(a):
+        return torch.from_numpy(a.astype(np.complex64)).cuda()
+    return torch.from_numpy(a.astype(dtype or np.float32)).cuda()
+
+
+def to_host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy().astype(np.complex128)
+
+
+def make_plan(case, kernel_width=None, oversamp=None):
+    import paper_2411_01955_gb300 as hq
+    n = case["n"]
+    W = kernel_width or case["W"]
+    sg = oversamp or case["sigma"]
+    traj = to_dev(case["traj"], np.float32)
+    smaps = to_dev(case["smaps"])
+    return hq.plan_create(traj, n, n, smaps, W, sg), traj, smaps
+
+
+def quantised(case):
+    """The case's arrays rounded to what the GPU sees (float32 / complex64),
+    as float64 / complex128 for the oracle."""
+    out = dict(case)
+    out["x"] = case["x"].astype(np.complex64).astype(np.complex128)
+    out["smaps"] = case["smaps"].astype(np.complex64).astype(np.complex128)
+    out["traj"] = case["traj"].astype(np.float32)
+    return out

@@ -1,0 +1,271 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
+same seeded inputs.  Bar (float32 path vs float64 oracle, equal parameters):
+relative L2 <= 1e-5; against the exact NUDFT at width 4, sigma 2: <= 2e-3."""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from helpers import make_plan, quantised, rel, to_dev, to_host
+from oracle import hqs as ohqs
+from oracle import nudft, nufft, solvers, toeplitz
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+def hq():
+    import paper_2411_01955_gb300 as m
+    return m
+
+
+def cases():
+    return {
+        "tiny": synth.tiny_case(0),
+        "odd": synth.odd_case(0),
+        "odd_w6": dict(synth.odd_case(1, n=32, L=5, M=301, W=6)),
+    }
+
+
+@pytest.fixture(scope="module", params=["tiny", "odd", "odd_w6"])
+def case(request):
+    return quantised(cases()[request.param])
+
+
+def test_forward_matches_oracle(case):
+    plan, traj, smaps = make_plan(case)
+    x = to_dev(case["x"])
+    y = torch.empty((case["smaps"].shape[0], case["traj"].shape[0]), dtype=torch.complex64, device="cuda")
+    hq().forward(plan, x, y)
+    got = to_host(y)
+    want = nufft.forward(case["x"], case["smaps"], case["traj"], case["W"], case["sigma"])
+    assert rel(got, want) <= TOL
+    if case["W"] == 4:
+        assert rel(got, nudft.forward(case["x"], case["smaps"], case["traj"])) <= 2e-3
+
+
+def test_adjoint_matches_oracle(case):
+    plan, traj, smaps = make_plan(case)
+    yv = case["noise"].astype(np.complex64).astype(np.complex128)
+    y = to_dev(yv)
+    x = torch.empty((case["n"], case["n"]), dtype=torch.complex64, device="cuda")
+    hq().adjoint(plan, y, x)
+    got = to_host(x)
+    want = nufft.adjoint(yv, case["smaps"], case["traj"], case["W"], case["sigma"])
+    assert rel(got, want) <= TOL
+    if case["W"] == 4:
+        assert rel(got, nudft.adjoint(yv, case["smaps"], case["traj"])) <= 2e-3
+
+
+def test_gpu_operator_pair_is_adjoint(case):
+    plan, _, _ = make_plan(case)
+    rng = np.random.default_rng(3)
+    n, L, M = case["n"], case["smaps"].shape[0], case["traj"].shape[0]
+    xv = rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n))
+    yv = rng.normal(size=(L, M)) + 1j * rng.normal(size=(L, M))
+    Ax = torch.empty((L, M), dtype=torch.complex64, device="cuda")
+    Ahy = torch.empty((n, n), dtype=torch.complex64, device="cuda")
+    hq().forward(plan, to_dev(xv), Ax)
+    hq().adjoint(plan, to_dev(yv), Ahy)
+    x32 = xv.astype(np.complex64).astype(np.complex128)
+    y32 = yv.astype(np.complex64).astype(np.complex128)
+    lhs = np.vdot(y32, to_host(Ax))
+    rhs = np.vdot(to_host(Ahy), x32)
+    assert abs(lhs - rhs) / abs(lhs) < 1e-5
+
+
+def oracle_toeplitz(case):
+    n = case["n"]
+    c = toeplitz.kernel(case["traj"], n, n)
+    return toeplitz.khat(c), toeplitz.chan_symbol(c, n, n)
+
+
+def test_toeplitz_normal_matches_oracle(case):
+    plan, _, _ = make_plan(case)
+    Kh, _ = oracle_toeplitz(case)
+    out = torch.empty((case["n"], case["n"]), dtype=torch.complex64, device="cuda")
+    hq().toeplitz_normal(plan, to_dev(case["x"]), out)
+    want = toeplitz.normal(case["x"], case["smaps"], Kh)
+    assert rel(to_host(out), want) <= TOL
+
+
+def test_precond_apply_matches_oracle(case):
+    plan, _, _ = make_plan(case)
+    _, lam = oracle_toeplitz(case)
+    r = case["x"]
+    z = torch.empty_like(to_dev(r))
+    for a, b in [(1.0, 1e-2), (0.8, 0.05), (-0.3, 2.0)]:
+        hq().precond_apply(plan, a, b, to_dev(r), z)
+        want = toeplitz.precond_apply(r, lam, a, b)
+        assert rel(to_host(z), want) <= TOL, (a, b)
+
+
+def test_dc_solve_fixed_iterations_matches_oracle(case):
+    plan, _, _ = make_plan(case)
+    Kh, lam = oracle_toeplitz(case)
+    n = case["n"]
+    mu = 1e-2
+    rhs = nufft.adjoint(case["noise"], case["smaps"], case["traj"], case["W"], case["sigma"])
+    rhs = rhs.astype(np.complex64).astype(np.complex128)
+    H = lambda v: toeplitz.normal(v, case["smaps"], Kh) + mu * v
+    for precond in (hq().HQS_PRECOND_DC, hq().HQS_PRECOND_NONE):
+        Minv = (lambda v: toeplitz.precond_apply(v, lam, 1.0, mu)) if precond else None
+        want, winfo = solvers.pcg(H, rhs, np.zeros((n, n)), Minv, max_iter=5, tol=0.0)
+        x = torch.zeros((n, n), dtype=torch.complex64, device="cuda")
+        info = hq().dc_solve(plan, 1.0, mu, to_dev(rhs), x, max_iter=5, rel_tol=0.0, precond=precond)
+        assert info.iterations == 5 and info.status == 0
+        assert rel(to_host(x), want) <= TOL
+        got_hist = np.array(info.history())
+        assert np.allclose(got_hist, winfo["res_hist"], rtol=1e-4, atol=0)
+
+
+def test_dc_solve_converges_to_tolerance(case):
+    plan, _, _ = make_plan(case)
+    Kh, lam = oracle_toeplitz(case)
+    n, mu = case["n"], 1e-2
+    rhs = nufft.adjoint(case["noise"], case["smaps"], case["traj"], case["W"], case["sigma"])
+    rhs = rhs.astype(np.complex64).astype(np.complex128)
+    x = torch.zeros((n, n), dtype=torch.complex64, device="cuda")
+    info = hq().dc_solve(plan, 1.0, mu, to_dev(rhs), x, max_iter=200, rel_tol=1e-4)
+    assert info.status == 0 and info.rel_residual <= 1e-4
+    H = lambda v: toeplitz.normal(v, case["smaps"], Kh) + mu * v
+    true_res = np.linalg.norm(rhs - H(to_host(x))) / np.linalg.norm(rhs)
+    assert true_res <= 1.2e-4
+    hist = info.history()
+    assert len(hist) == info.iterations + 1
+
+
+def test_dc_solve_edge_cases():
+    case = quantised(synth.tiny_case(1))
+    plan, _, _ = make_plan(case)
+    n = case["n"]
+    # zero right-hand side: exact zero solution, no iterations
+    x = to_dev(np.ones((n, n), dtype=np.complex64))
+    info = hq().dc_solve(plan, 1.0, 0.1, torch.zeros_like(x), x, max_iter=10, rel_tol=1e-4)
+    assert info.iterations == 0 and info.status == 0
+    assert float(torch.abs(x).max()) == 0.0
+    # max_iter = 0 returns the start point untouched
+    x0 = to_dev(case["x"])
+    x = x0.clone()
+    info = hq().dc_solve(plan, 1.0, 0.1, to_dev(case["x"] * 2), x, max_iter=0, rel_tol=1e-4,
+                         check=False)
+    assert info.iterations == 0 and torch.equal(x, x0)
+    # non-positive b is rejected
+    with pytest.raises(hq().HqsError):
+        hq().dc_solve(plan, 1.0, 0.0, x0, x, max_iter=5)
+    # non-finite input is reported as breakdown, not a fault
+    bad = case["x"].copy()
+    bad[3, 4] = np.nan
+    info = hq().dc_solve(plan, 1.0, 0.1, to_dev(bad), torch.zeros_like(x0), max_iter=5,
+                         rel_tol=1e-4, check=False)
+    assert info.status == hq().HQS_ERR_BREAKDOWN
+
+
+def test_empty_trajectory():
+    case = quantised(synth.tiny_case(2))
+    case["traj"] = np.zeros((0, 2), dtype=np.float32)
+    plan, _, _ = make_plan(case)
+    n = case["n"]
+    x = torch.empty((n, n), dtype=torch.complex64, device="cuda")
+    hq().adjoint(plan, torch.zeros((case["smaps"].shape[0], 0), dtype=torch.complex64, device="cuda"), x)
+    assert float(torch.abs(x).max()) == 0.0
+    out = torch.empty_like(x)
+    hq().toeplitz_normal(plan, to_dev(case["x"]), out)
+    assert float(torch.abs(out).max()) == 0.0
+    # H = b I: one CG step solves it
+    xs = torch.zeros_like(x)
+    info = hq().dc_solve(plan, 1.0, 0.5, to_dev(case["x"]), xs, max_iter=5, rel_tol=1e-6)
+    assert rel(to_host(xs), case["x"] / 0.5) < 1e-6
+
+
+def test_gaussian_denoiser_matches_oracle():
+    rng = np.random.default_rng(5)
+    v = (rng.normal(size=(64, 96)) + 1j * rng.normal(size=(64, 96))).astype(np.complex64)
+    v = v.astype(np.complex128)
+    out = torch.empty((64, 96), dtype=torch.complex64, device="cuda")
+    for s in [0.05, 0.5, 1.5, 4.0]:
+        hq().gaussian_denoise(to_dev(v), out, s)
+        assert rel(to_host(out), ohqs.gaussian_denoise(v, s)) <= TOL, s
+    hq().gaussian_denoise(to_dev(v), out, 0.3, gauss=(1.5, 0.1))   # s = 1.5*0.3/0.1
+    assert rel(to_host(out), ohqs.gaussian_denoise(v, 4.5)) <= TOL
+
+
+def test_hqs_run_matches_oracle_tiny_config():
+    """Annealed HQS, 10 outer x 5 CG iterations, Gaussian-smoothing denoiser.
+
+    Each outer step, started on the GPU from the oracle's x_k, must match the
+    oracle's x_{k+1} to 1e-5.  The whole run amplifies rounding: truncated,
+    warm-started CG with mu falling to 1e-3 multiplies a relative input
+    perturbation by ~3e3 over ten steps, so the end-to-end bound is 4x the
+    oracle's own deviation when its A^H y is perturbed by the float32 unit
+    roundoff 2^-24 (measured here, not assumed)."""
+    case = quantised(synth.tiny_case(0))
+    plan, _, _ = make_plan(case)
+    n, K = case["n"], case["K"]
+    Kh, lam = oracle_toeplitz(case)
+    y = nufft.forward(case["x"], case["smaps"], case["traj"], case["W"], case["sigma"])
+    sd = synth.noise_scale_snr(float(np.sum(np.abs(y) ** 2)), y.size, case["snr_db"])
+    y = (y + sd * case["noise"]).astype(np.complex64).astype(np.complex128)
+    mu = case["mu"].astype(np.float32)
+    sigma = mu.copy()   # sigma_k tied to mu_k
+    mu64, sg64 = mu.astype(np.float64), sigma.astype(np.float64)
+    b0 = nufft.adjoint(y, case["smaps"], case["traj"], case["W"], case["sigma"])
+    AHA = lambda v: toeplitz.normal(v, case["smaps"], Kh)
+    want, _, hist = ohqs.hqs(AHA, b0, np.zeros((n, n)), mu64, sg64, K, cg_iters=case["cg_iters"], lam=lam)
+    gauss = (1.5, float(sigma[0]))
+    # per outer step from the oracle's iterate
+    xk = np.zeros((n, n))
+    for k in range(K):
+        xg = to_dev(xk)
+        hq().hqs_run(plan, to_dev(y), xg, mu, sigma, K=k + 1, k0=k, cg_iters=case["cg_iters"], gauss=gauss)
+        assert rel(to_host(xg), hist[k]) <= TOL, k
+        xk = hist[k].astype(np.complex64).astype(np.complex128)
+    # whole run
+    x = torch.zeros((n, n), dtype=torch.complex64, device="cuda")
+    hq().hqs_run(plan, to_dev(y), x, mu, sigma, K=K, cg_iters=case["cg_iters"])
+    rng = np.random.default_rng(0)
+    b0p = b0 * (1 + 2.0 ** -24 * rng.normal(size=b0.shape))
+    pert, _, _ = ohqs.hqs(AHA, b0p, np.zeros((n, n)), mu64, sg64, K, cg_iters=case["cg_iters"], lam=lam)
+    bound = 4 * rel(pert, want)
+    err = rel(to_host(x), want)
+    assert err <= bound, (err, bound)
+    # resume: 5 + 5 iterations reproduce the straight run (up to the float-atomic
+    # summation order of A^H y, recomputed by each call)
+    xa = torch.zeros((n, n), dtype=torch.complex64, device="cuda")
+    hq().hqs_run(plan, to_dev(y), xa, mu, sigma, K=5, cg_iters=case["cg_iters"], gauss=gauss)
+    hq().hqs_run(plan, to_dev(y), xa, mu, sigma, K=K, k0=5, cg_iters=case["cg_iters"], gauss=gauss)
+    assert rel(to_host(xa), to_host(x)) <= bound
+
+
+def test_hqs_denoiser_callback_and_failure():
+    case = quantised(synth.tiny_case(0))
+    plan, _, _ = make_plan(case)
+    n = case["n"]
+    y = to_dev(case["noise"])
+    calls = []
+
+    def shrink(tin, tout, s):
+        calls.append(s)
+        tout.copy_(tin * 0.5)
+        return 0
+
+    x = torch.zeros((n, n), dtype=torch.complex64, device="cuda")
+    hq().hqs_run(plan, y, x, [0.1, 0.05], [1.0, 0.5], cg_iters=3, denoiser=shrink)
+    assert calls == [1.0, 0.5]
+    with pytest.raises(hq().HqsError) as ei:
+        hq().hqs_run(plan, y, x, [0.1], [1.0], cg_iters=3, denoiser=lambda a, b, s: 7)
+    assert ei.value.status == hq().HQS_ERR_CALLBACK
+
+
+def test_power_iteration_matches_oracle():
+    case = quantised(synth.tiny_case(0))
+    plan, _, _ = make_plan(case)
+    Kh, _ = oracle_toeplitz(case)
+    n = case["n"]
+    want = solvers.power_iteration(lambda v: toeplitz.normal(v, case["smaps"], Kh), (n, n),
+                                   iters=200, rtol=1e-9)
+    got = hq().power_iteration(plan, iters=200)
+    assert abs(got / want - 1) < 1e-3
