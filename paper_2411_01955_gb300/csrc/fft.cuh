@@ -106,7 +106,8 @@ template <bool INV> struct Dft<8, INV> {
 };
 
 // One Stockham stage.  `s` points at element (0, line); consecutive positions
-// are kLines float2 apart.  Threads with act == false only take the barriers.
+// are kLines float2 apart.  Threads with act == false (given t = 0 and line 0)
+// read but do not write.
 template <int N, int E, int R, int P, bool INV>
 HQS_DEV void fft_stage(float2* s, int t, bool act, const float2* __restrict__ tw) {
     constexpr int st = kLines;
@@ -116,13 +117,14 @@ HQS_DEV void fft_stage(float2* s, int t, bool act, const float2* __restrict__ tw
     static_assert(E % R == 0, "radix must divide elements per thread");
     static_assert(NB == TPL * BPT, "butterfly split");
     float2 v[E];
-    if (act) {
+    // Loads are unconditional (inactive threads read line 0 at t = 0, which
+    // is in bounds): a predicated load block inside a caller's loop makes the
+    // register allocator keep the whole array live and spill.
 #pragma unroll
-        for (int b = 0; b < BPT; ++b) {
-            const int i = t + b * TPL;
+    for (int b = 0; b < BPT; ++b) {
+        const int i = t + b * TPL;
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[b * R + r] = s[(i + r * NB) * st];
-        }
+        for (int r = 0; r < R; ++r) v[b * R + r] = s[(i + r * NB) * st];
     }
     __syncthreads();
     if (act) {
@@ -234,7 +236,22 @@ HQS_DEV void block_fft(float2* s, int nlines, const float2* tw) {
     const int ll = tid % lpg;
     const int t = tid / lpg;
     const bool act = (ll < nlines) && (t < TPL);
-    FftSize<N>::template run<INV>(s + (act ? ll : 0), t, act, tw);
+    FftSize<N>::template run<INV>(s + (act ? ll : 0), act ? t : 0, act, tw);
+}
+
+// Copies the N-point twiddle table into shared memory; the caller's barrier
+// before block_fft publishes it.  Staging it there keeps the stage loops off
+// global memory (the streaming grid data would evict it from L1).
+template <int N> HQS_DEV const float2* stage_twiddles(float2* dst, const float2* __restrict__ tw) {
+    for (int i = threadIdx.x; i < N; i += blockDim.x) dst[i] = tw[i];
+    return dst;
+}
+
+// f(p0 + k * PST) for k = 0..CNT-1, fully unrolled: with compile-time trip
+// counts every global load of a pass is in flight at once.
+template <int CNT, int PST, class F> HQS_DEV void unrolled(int p0, F&& f) {
+#pragma unroll
+    for (int k = 0; k < CNT; ++k) f(p0 + k * PST);
 }
 
 // Threads per CTA for a pass over `nlines` (<= kLines) lines of size N: every

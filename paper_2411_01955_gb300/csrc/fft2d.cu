@@ -9,16 +9,19 @@ using namespace hqs;
 
 // Q consecutive rows of a [rows][N] image per CTA, in place.
 template <int N, bool INV>
-__global__ void k_fft_rows(float2* __restrict__ data, int rows, int Q, const float2* __restrict__ tw) {
+__global__ void k_fft_rows(float2* __restrict__ data, int rows, int Q, const float2* __restrict__ twg) {
     extern __shared__ float2 s[];
+    const float2* tw = stage_twiddles<N>(s + N * kLines, twg);
     const int r0 = blockIdx.x * Q;
     const int lines = min(Q, rows - r0);
+#pragma unroll 4
     for (int e = threadIdx.x; e < N * lines; e += blockDim.x) {
         const int q = e / N, pos = e % N;
         s[pos * kLines + q] = data[(int64_t)(r0 + q) * N + pos];
     }
     __syncthreads();
     block_fft<N, INV>(s, lines, tw);
+#pragma unroll 4
     for (int e = threadIdx.x; e < N * lines; e += blockDim.x) {
         const int q = e / N, pos = e % N;
         data[(int64_t)(r0 + q) * N + pos] = s[pos * kLines + q];
@@ -27,16 +30,19 @@ __global__ void k_fft_rows(float2* __restrict__ data, int rows, int Q, const flo
 
 // Q adjacent columns of a [N][cols] image per CTA, in place.
 template <int N, bool INV>
-__global__ void k_fft_cols(float2* __restrict__ data, int cols, int Q, const float2* __restrict__ tw) {
+__global__ void k_fft_cols(float2* __restrict__ data, int cols, int Q, const float2* __restrict__ twg) {
     extern __shared__ float2 s[];
+    const float2* tw = stage_twiddles<N>(s + N * kLines, twg);
     const int c0 = blockIdx.x * Q;
     const int lines = min(Q, cols - c0);
+#pragma unroll 4
     for (int e = threadIdx.x; e < N * lines; e += blockDim.x) {
         const int pos = e / lines, q = e % lines;
         s[pos * kLines + q] = data[(int64_t)pos * cols + c0 + q];
     }
     __syncthreads();
     block_fft<N, INV>(s, lines, tw);
+#pragma unroll 4
     for (int e = threadIdx.x; e < N * lines; e += blockDim.x) {
         const int pos = e / lines, q = e % lines;
         data[(int64_t)pos * cols + c0 + q] = s[pos * kLines + q];
@@ -49,7 +55,7 @@ static int fft2d_impl(const hqs_plan_s* p, float2* data, cudaStream_t st) {
     if (!tw) return HQS_ERR_INVALID_ARG;
     const int Q = 16;
     const int th = fft_threads<N>(Q);
-    const size_t sm = (size_t)N * kLines * sizeof(float2);
+    const size_t sm = (size_t)(N * kLines + N) * sizeof(float2);
     HQS_CUDA_TRY(cudaFuncSetAttribute(k_fft_rows<N, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     HQS_CUDA_TRY(cudaFuncSetAttribute(k_fft_cols<N, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     k_fft_rows<N, INV><<<ceil_div(N, Q), th, sm, st>>>(data, N, Q, tw);
@@ -69,41 +75,57 @@ int launch_fft2d(const hqs_plan_s* p, float2* data, int N, bool inverse, cudaStr
 // rows: out[row][:] = FFT_N(in[row][:]) for Q rows per CTA
 template <int N>
 __global__ void k_pc_rows_fwd(const float2* __restrict__ in, float2* __restrict__ out, int Q,
-                              const float2* __restrict__ tw, const CgScalars* __restrict__ cg) {
+                              const float2* __restrict__ twg, const CgScalars* __restrict__ cg) {
     if (cg && cg->done) return;
     extern __shared__ float2 s[];
+    const float2* tw = stage_twiddles<N>(s + N * kLines, twg);
     const int r0 = blockIdx.x * Q;
     const int lines = min(Q, N - r0);
-    for (int e = threadIdx.x; e < N * lines; e += blockDim.x) {
+    constexpr int BD = FftSize<N>::TPL * kLines;
+    auto ld = [&](int e) {
         const int q = e / N, pos = e % N;
         s[pos * kLines + q] = in[(int64_t)(r0 + q) * N + pos];
-    }
+    };
+    if (lines == kLines && blockDim.x == BD) unrolled<N * kLines / BD, BD>(threadIdx.x, ld);
+    else for (int e = threadIdx.x; e < N * lines; e += blockDim.x) ld(e);
     __syncthreads();
     block_fft<N, false>(s, lines, tw);
-    for (int e = threadIdx.x; e < N * lines; e += blockDim.x) {
+    auto st = [&](int e) {
         const int q = e / N, pos = e % N;
         out[(int64_t)(r0 + q) * N + pos] = s[pos * kLines + q];
-    }
+    };
+    if (lines == kLines && blockDim.x == BD) unrolled<N * kLines / BD, BD>(threadIdx.x, st);
+    else for (int e = threadIdx.x; e < N * lines; e += blockDim.x) st(e);
 }
 
 // columns: FFT, multiply by m = s^-1/2, optional partial sum of |R|^2 m
 // (Parseval: N^2 <r, z>), inverse FFT; in place on buf.
 template <int N>
 __global__ void k_pc_cols(float2* __restrict__ buf, int Q, const float* __restrict__ lam, float a,
-                          float b, const float2* __restrict__ tw, const CgScalars* __restrict__ cg,
+                          float b, const float2* __restrict__ twg, const CgScalars* __restrict__ cg,
                           double* __restrict__ part) {
     if (cg && cg->done) return;
     extern __shared__ float2 s[];
+    const float2* tw = stage_twiddles<N>(s + N * kLines, twg);
     __shared__ double red[32];
     const int c0 = blockIdx.x * Q;
     const int lines = min(Q, N - c0);
-    for (int e = threadIdx.x; e < N * lines; e += blockDim.x) {
-        const int pos = e / lines, q = e % lines;
-        s[pos * kLines + q] = buf[(int64_t)pos * N + c0 + q];
+    constexpr int BD = FftSize<N>::TPL * kLines;
+    const bool full = lines == kLines && blockDim.x == BD;
+    if (full) {
+        unrolled<N * kLines / BD, BD>(threadIdx.x, [&](int e) {
+            s[e] = buf[(int64_t)(e / kLines) * N + c0 + (e % kLines)];
+        });
+    } else {
+        for (int e = threadIdx.x; e < N * lines; e += blockDim.x) {
+            const int pos = e / lines, q = e % lines;
+            s[pos * kLines + q] = buf[(int64_t)pos * N + c0 + q];
+        }
     }
     __syncthreads();
     block_fft<N, false>(s, lines, tw);
     double acc = 0.0;
+#pragma unroll 4
     for (int e = threadIdx.x; e < N * lines; e += blockDim.x) {
         const int pos = e / lines, q = e % lines;
         const float l = lam[(int64_t)pos * N + c0 + q];
@@ -124,31 +146,44 @@ __global__ void k_pc_cols(float2* __restrict__ buf, int Q, const float* __restri
         part[blockIdx.x] = t;
     }
     block_fft<N, true>(s, lines, tw);
-    for (int e = threadIdx.x; e < N * lines; e += blockDim.x) {
-        const int pos = e / lines, q = e % lines;
-        buf[(int64_t)pos * N + c0 + q] = s[pos * kLines + q];
+    if (full) {
+        unrolled<N * kLines / BD, BD>(threadIdx.x, [&](int e) {
+            buf[(int64_t)(e / kLines) * N + c0 + (e % kLines)] = s[e];
+        });
+    } else {
+        for (int e = threadIdx.x; e < N * lines; e += blockDim.x) {
+            const int pos = e / lines, q = e % lines;
+            buf[(int64_t)pos * N + c0 + q] = s[pos * kLines + q];
+        }
     }
 }
 
 // rows: z[row][:] = IFFT_N(buf[row][:]) / N^2
 template <int N>
 __global__ void k_pc_rows_inv(const float2* __restrict__ buf, float2* __restrict__ z, int Q,
-                              const float2* __restrict__ tw, const CgScalars* __restrict__ cg) {
+                              const float2* __restrict__ twg, const CgScalars* __restrict__ cg) {
     if (cg && cg->done) return;
     extern __shared__ float2 s[];
+    const float2* tw = stage_twiddles<N>(s + N * kLines, twg);
     const int r0 = blockIdx.x * Q;
     const int lines = min(Q, N - r0);
-    for (int e = threadIdx.x; e < N * lines; e += blockDim.x) {
+    constexpr int BD = FftSize<N>::TPL * kLines;
+    const bool full = lines == kLines && blockDim.x == BD;
+    auto ld = [&](int e) {
         const int q = e / N, pos = e % N;
         s[pos * kLines + q] = buf[(int64_t)(r0 + q) * N + pos];
-    }
+    };
+    if (full) unrolled<N * kLines / BD, BD>(threadIdx.x, ld);
+    else for (int e = threadIdx.x; e < N * lines; e += blockDim.x) ld(e);
     __syncthreads();
     block_fft<N, true>(s, lines, tw);
     const float sc = 1.0f / ((float)N * (float)N);
-    for (int e = threadIdx.x; e < N * lines; e += blockDim.x) {
+    auto st = [&](int e) {
         const int q = e / N, pos = e % N;
         z[(int64_t)(r0 + q) * N + pos] = cscale(s[pos * kLines + q], sc);
-    }
+    };
+    if (full) unrolled<N * kLines / BD, BD>(threadIdx.x, st);
+    else for (int e = threadIdx.x; e < N * lines; e += blockDim.x) st(e);
 }
 
 template <int N>
@@ -157,7 +192,7 @@ static int precond_impl(hqs_plan_s* p, float a, float b, const float2* r, float2
     const float2* tw = plan_twiddles(p, N);
     const int Q = p->q_rows;
     const int th = fft_threads<N>(Q);
-    const size_t sm = (size_t)N * kLines * sizeof(float2);
+    const size_t sm = (size_t)(N * kLines + N) * sizeof(float2);
     const int nb = ceil_div(N, Q);
     HQS_CUDA_TRY(cudaFuncSetAttribute(k_pc_rows_fwd<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     HQS_CUDA_TRY(cudaFuncSetAttribute(k_pc_cols<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));

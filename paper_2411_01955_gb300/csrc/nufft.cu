@@ -32,18 +32,26 @@ HQS_DEV int pix_to_grid(int i, int n, int G) {
 }
 
 // ---------------------------------------------------------------- forward
+// Shared memory of the FFT passes: [G][kLines] lines | [G] twiddles.
+template <int G> constexpr size_t nufft_smem_floats2() { return (size_t)G * kLines + G; }
+
+// Row iy for the coils of chunk blockIdx.y: S_l x / (phihat phihat) placed at
+// n mod G, FFT along x -> U[iy][gx][l].
 template <int G>
 __global__ void k_fwd_rows(const float2* __restrict__ x, const float2* __restrict__ smaps,
                            const float* __restrict__ apod, int n, int L, int LC, int nchunk,
-                           float scale, const float2* __restrict__ tw, float2* __restrict__ U) {
+                           float scale, const float2* __restrict__ twg, float2* __restrict__ U) {
     extern __shared__ float2 s[];
+    const float2* tw = stage_twiddles<G>(s + G * kLines, twg);
     const int iy = blockIdx.x;
     const float ay = apod[iy] * scale;
-    {
-        const int l0 = blockIdx.y * LC;
-        const int lines = min(LC, L - l0);
-        for (int e = threadIdx.x; e < G * lines; e += blockDim.x) {
-            const int p = e / lines, l = e - p * lines;
+    const int l0 = blockIdx.y * LC;
+    const int lines = min(LC, L - l0);
+    const int pst = blockDim.x / lines;
+    const int l = threadIdx.x % lines, p0 = threadIdx.x / lines;
+    if (p0 < pst) {
+#pragma unroll 4
+        for (int p = p0; p < G; p += pst) {
             const int ix = grid_to_pix(p, n, G);
             float2 v = make_float2(0.f, 0.f);
             if (ix >= 0) {
@@ -52,35 +60,42 @@ __global__ void k_fwd_rows(const float2* __restrict__ x, const float2* __restric
             }
             s[p * kLines + l] = v;
         }
-        __syncthreads();
-        block_fft<G, false>(s, lines, tw);
-        float2* dst = U + (int64_t)iy * G * L + l0;
-        for (int e = threadIdx.x; e < G * lines; e += blockDim.x) {
-            const int p = e / lines, l = e - p * lines;
-            dst[(int64_t)p * L + l] = s[p * kLines + l];
-        }
+    }
+    __syncthreads();
+    block_fft<G, false>(s, lines, tw);
+    float2* dst = U + (int64_t)iy * G * L + l0 + l;
+    if (p0 < pst) {
+#pragma unroll 4
+        for (int p = p0; p < G; p += pst) dst[(int64_t)p * L] = s[p * kLines + l];
     }
 }
 
+// Column gx: image rows at n mod G, zeros elsewhere, FFT along y -> Ghat.
 template <int G>
 __global__ void k_fwd_cols(const float2* __restrict__ U, int n, int L, int LC, int nchunk,
-                           const float2* __restrict__ tw, float2* __restrict__ Gh) {
+                           const float2* __restrict__ twg, float2* __restrict__ Gh) {
     extern __shared__ float2 s[];
+    const float2* tw = stage_twiddles<G>(s + G * kLines, twg);
     const int gx = blockIdx.x;
-    {
-        const int l0 = blockIdx.y * LC;
-        const int lines = min(LC, L - l0);
-        for (int e = threadIdx.x; e < G * lines; e += blockDim.x) {
-            const int p = e / lines, l = e - p * lines;
+    const int l0 = blockIdx.y * LC;
+    const int lines = min(LC, L - l0);
+    const int pst = blockDim.x / lines;
+    const int l = threadIdx.x % lines, p0 = threadIdx.x / lines;
+    const int64_t rs = (int64_t)G * L;
+    const float2* col = U + (int64_t)gx * L + l0 + l;
+    if (p0 < pst) {
+#pragma unroll 8
+        for (int p = p0; p < G; p += pst) {
             const int iy = grid_to_pix(p, n, G);
-            s[p * kLines + l] = iy >= 0 ? U[((int64_t)iy * G + gx) * L + l0 + l] : make_float2(0.f, 0.f);
+            s[p * kLines + l] = iy >= 0 ? col[iy * rs] : make_float2(0.f, 0.f);
         }
-        __syncthreads();
-        block_fft<G, false>(s, lines, tw);
-        for (int e = threadIdx.x; e < G * lines; e += blockDim.x) {
-            const int p = e / lines, l = e - p * lines;
-            Gh[((int64_t)p * G + gx) * L + l0 + l] = s[p * kLines + l];
-        }
+    }
+    __syncthreads();
+    block_fft<G, false>(s, lines, tw);
+    float2* dst = Gh + (int64_t)gx * L + l0 + l;
+    if (p0 < pst) {
+#pragma unroll 4
+        for (int p = p0; p < G; p += pst) dst[p * rs] = s[p * kLines + l];
     }
 }
 
@@ -203,25 +218,29 @@ __global__ void k_spread(const float2* __restrict__ y, const int4* __restrict__ 
     }
 }
 
+// Column gx: IFFT along y of the spread grid, keep the image rows -> V[iy][gx][l].
 template <int G>
 __global__ void k_adj_cols(const float2* __restrict__ Hg, int n, int L, int LC, int nchunk,
-                           const float2* __restrict__ tw, float2* __restrict__ V) {
+                           const float2* __restrict__ twg, float2* __restrict__ V) {
     extern __shared__ float2 s[];
+    const float2* tw = stage_twiddles<G>(s + G * kLines, twg);
     const int gx = blockIdx.x;
-    {
-        const int l0 = blockIdx.y * LC;
-        const int lines = min(LC, L - l0);
-        for (int e = threadIdx.x; e < G * lines; e += blockDim.x) {
-            const int p = e / lines, l = e - p * lines;
-            s[p * kLines + l] = Hg[((int64_t)p * G + gx) * L + l0 + l];
-        }
-        __syncthreads();
-        block_fft<G, true>(s, lines, tw);
-        for (int e = threadIdx.x; e < n * lines; e += blockDim.x) {
-            const int iy = e / lines, l = e - iy * lines;
-            const int p = pix_to_grid(iy, n, G);
-            V[((int64_t)iy * G + gx) * L + l0 + l] = s[p * kLines + l];
-        }
+    const int l0 = blockIdx.y * LC;
+    const int lines = min(LC, L - l0);
+    const int pst = blockDim.x / lines;
+    const int l = threadIdx.x % lines, p0 = threadIdx.x / lines;
+    const int64_t rs = (int64_t)G * L;
+    const float2* col = Hg + (int64_t)gx * L + l0 + l;
+    if (p0 < pst) {
+#pragma unroll 8
+        for (int p = p0; p < G; p += pst) s[p * kLines + l] = col[p * rs];
+    }
+    __syncthreads();
+    block_fft<G, true>(s, lines, tw);
+    float2* dst = V + (int64_t)gx * L + l0 + l;
+    if (p0 < pst) {
+#pragma unroll 4
+        for (int iy = p0; iy < n; iy += pst) dst[iy * rs] = s[pix_to_grid(iy, n, G) * kLines + l];
     }
 }
 
@@ -231,16 +250,19 @@ __global__ void k_adj_cols(const float2* __restrict__ Hg, int n, int L, int LC, 
 template <int G>
 __global__ void k_adj_rows(const float2* __restrict__ V, const float2* __restrict__ smaps,
                            const float* __restrict__ apod, int n, int L, int LC, int nchunk,
-                           float scale, const float2* __restrict__ tw, float2* __restrict__ x,
+                           float scale, const float2* __restrict__ twg, float2* __restrict__ x,
                            float2* __restrict__ part) {
     extern __shared__ float2 s[];
+    const float2* tw = stage_twiddles<G>(s + G * kLines, twg);
     const int iy = blockIdx.x;
     const int l0 = blockIdx.y * LC;
     const int lines = min(LC, L - l0);
-    const float2* src = V + (int64_t)iy * G * L + l0;
-    for (int e = threadIdx.x; e < G * lines; e += blockDim.x) {
-        const int p = e / lines, l = e - p * lines;
-        s[p * kLines + l] = src[(int64_t)p * L + l];
+    const int pst = blockDim.x / lines;
+    const int l = threadIdx.x % lines, p0 = threadIdx.x / lines;
+    const float2* src = V + (int64_t)iy * G * L + l0 + l;
+    if (p0 < pst) {
+#pragma unroll 8
+        for (int p = p0; p < G; p += pst) s[p * kLines + l] = src[(int64_t)p * L];
     }
     __syncthreads();
     block_fft<G, true>(s, lines, tw);
@@ -249,9 +271,9 @@ __global__ void k_adj_rows(const float2* __restrict__ V, const float2* __restric
         const int p = pix_to_grid(ix, n, G);
         const float2* sm = smaps + ((int64_t)iy * n + ix) * L + l0;
         float2 a = make_float2(0.f, 0.f);
-        for (int l = 0; l < lines; ++l) {
-            const float2 sv = sm[l];
-            const float2 g = s[p * kLines + l];
+        for (int ll = 0; ll < lines; ++ll) {
+            const float2 sv = sm[ll];
+            const float2 g = s[p * kLines + ll];
             a.x += sv.x * g.x + sv.y * g.y;
             a.y += sv.x * g.y - sv.y * g.x;
         }
@@ -278,7 +300,7 @@ template <int G>
 static int fwd_fft_impl(hqs_plan_s* p, const float2* x, cudaStream_t st) {
     const float2* tw = plan_twiddles(p, G);
     const int th = fft_threads<G>(p->LC);
-    const size_t sm = (size_t)G * kLines * sizeof(float2);
+    const size_t sm = nufft_smem_floats2<G>() * sizeof(float2);
     HQS_CUDA_TRY(cudaFuncSetAttribute(k_fwd_rows<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     HQS_CUDA_TRY(cudaFuncSetAttribute(k_fwd_cols<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     k_fwd_rows<G><<<dim3(p->n, p->nchunk), th, sm, st>>>(x, p->smaps, p->apod, p->n, p->L, p->LC,
@@ -292,7 +314,7 @@ template <int G>
 static int adj_fft_impl(hqs_plan_s* p, float2* x, cudaStream_t st) {
     const float2* tw = plan_twiddles(p, G);
     const int th = fft_threads<G>(p->LC);
-    const size_t sm = (size_t)G * kLines * sizeof(float2);
+    const size_t sm = nufft_smem_floats2<G>() * sizeof(float2);
     HQS_CUDA_TRY(cudaFuncSetAttribute(k_adj_cols<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     HQS_CUDA_TRY(cudaFuncSetAttribute(k_adj_rows<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     k_adj_cols<G><<<dim3(G, p->nchunk), th, sm, st>>>(p->grid, p->n, p->L, p->LC, p->nchunk, tw, p->work);

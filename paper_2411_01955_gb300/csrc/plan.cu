@@ -271,6 +271,7 @@ static void plan_free(hqs_plan_s* p) {
     for (void* v : p->allocs) cudaFree(v);
     if (p->h_cg) cudaFreeHost(p->h_cg);
     if (p->h_hist) cudaFreeHost(p->h_hist);
+    if (p->h_err) cudaFreeHost(p->h_err);
     if (cur >= 0 && cur != p->device) cudaSetDevice(cur);
     delete p;
 }
@@ -284,7 +285,7 @@ static int plan_build(hqs_plan_s* p, const float* traj, const float2* smaps_user
     p->tile = 16;
     if (G % p->tile != 0) p->tile = 8;
     p->nbx = G / p->tile;
-    p->q_rows = 8;
+    p->q_rows = 16;
     const int maxg = std::max(G, n2);
 
     HQS_TRY(dev_alloc(p, &p->smaps, (size_t)n * n * L));
@@ -313,6 +314,7 @@ static int plan_build(hqs_plan_s* p, const float* traj, const float2* smaps_user
     HQS_TRY(dev_alloc(p, &p->barrier, (size_t)64));
     HQS_CUDA_TRY(cudaMallocHost(&p->h_cg, sizeof(CgScalars)));
     HQS_CUDA_TRY(cudaMallocHost(&p->h_hist, sizeof(double) * (HQS_MAX_ITERS + 1)));
+    HQS_CUDA_TRY(cudaMallocHost(&p->h_err, sizeof(unsigned)));
     HQS_CUDA_TRY(cudaMemsetAsync(p->cg, 0, sizeof(CgScalars), s));
     HQS_CUDA_TRY(cudaMemsetAsync(p->dev_err, 0, 4 * sizeof(unsigned), s));
     HQS_CUDA_TRY(cudaMemsetAsync(p->barrier, 0, 64 * sizeof(unsigned), s));

@@ -43,6 +43,7 @@ struct hqs_plan_s {
     int LC = 1, nchunk = 1;
     int tile = 16, nbx = 0, nsub = 0;
     int q_rows = 8;     // lines per CTA in the single-image FFT passes
+    int fused_grid = 0; // cap on the persistent solver's CTAs (0: occupancy limit)
 
     // constant tables and plan data (device)
     float2* smaps = nullptr;    // [n][n][L]
@@ -75,6 +76,7 @@ struct hqs_plan_s {
     double* hist = nullptr;     // [HQS_MAX_ITERS + 1] ||r_i||^2
     CgScalars* h_cg = nullptr;  // pinned host mirror
     double* h_hist = nullptr;
+    unsigned* h_err = nullptr;  // pinned mirror of dev_err
     unsigned* dev_err = nullptr;
     unsigned* barrier = nullptr; // grid barrier words for the persistent solve
     float2* smaps_user = nullptr;

@@ -1,0 +1,177 @@
+// Device bodies of the three A^H A passes, shared by the per-stage kernels
+// and the persistent solver.
+#pragma once
+
+#include "fft.cuh"
+#include "solve.cuh"
+
+namespace hqs {
+
+// ------------------------------------------------------------ A^H A passes
+// Each CTA handles one row/column for the coils of chunk `ch` (<= 16 coils);
+// the FFT body must not sit inside a runtime loop (register allocation
+// collapses), so coil chunks are a grid dimension.
+
+// Shared memory of the A^H A passes: [N2][kLines] lines | [n] image row |
+// [N2] twiddles.
+template <int N2> constexpr size_t toep_smem_floats2(int n) { return (size_t)N2 * kLines + n + N2; }
+
+// P1: v = src (or p = src + beta p when fused, single chunk only), S_l v,
+// zero-pad to N2, FFT along x.
+// src_row, when given, is the row already in shared memory (the persistent
+// solver rebuilds z there); otherwise the row is read from src.  Vectors
+// written by other CTAs earlier in the same launch are read with ld.global.cg
+// (L2), never from a possibly stale L1 line.
+template <int N2>
+HQS_DEV void toep_rows_fwd_item(const ToepArgs& A, int iy, int ch, const float2* __restrict__ src,
+                                float2* __restrict__ pvec, float beta, bool fuse, float2* s,
+                                const float2* src_row = nullptr) {
+    const int n = A.n, L = A.L;
+    float2* rowv = s + N2 * kLines;
+    const float2* tw = stage_twiddles<N2>(rowv + n, A.tw);
+    for (int ix = threadIdx.x; ix < n; ix += blockDim.x) {
+        const int64_t e = (int64_t)iy * n + ix;
+        float2 v = src_row ? src_row[ix] : __ldcg(src + e);
+        if (fuse) {
+            if (beta != 0.f) {
+                const float2 pv = __ldcg(pvec + e);
+                v.x = fmaf(beta, pv.x, v.x);
+                v.y = fmaf(beta, pv.y, v.y);
+            }
+            pvec[e] = v;
+        }
+        rowv[ix] = v;
+    }
+    const int l0 = ch * A.LC;
+    const int lines = min(A.LC, L - l0);
+    const int pst = blockDim.x / lines;
+    const int l = threadIdx.x % lines, p0 = threadIdx.x / lines;
+    const float2* sm = A.smaps + (int64_t)iy * n * L + l0 + l;
+    __syncthreads();
+    constexpr int TPL = FftSize<N2>::TPL;
+    if (lines == kLines) {   // full chunk: n = N2/2 and pst = TPL are compile-time
+        unrolled<N2 / 2 / TPL, TPL>(p0, [&](int p) { s[p * kLines + l] = cmul(sm[(int64_t)p * L], rowv[p]); });
+        unrolled<N2 / 2 / TPL, TPL>(p0 + N2 / 2, [&](int p) { s[p * kLines + l] = make_float2(0.f, 0.f); });
+    } else if (p0 < pst) {
+        for (int p = p0; p < n; p += pst) s[p * kLines + l] = cmul(sm[(int64_t)p * L], rowv[p]);
+        for (int p = n + p0; p < N2; p += pst) s[p * kLines + l] = make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    block_fft<N2, false>(s, lines, tw);
+    float2* dst = A.T + (int64_t)iy * N2 * L + l0 + l;
+    if (lines == kLines) {
+        unrolled<N2 / TPL, TPL>(p0, [&](int p) { dst[(int64_t)p * L] = s[p * kLines + l]; });
+    } else if (p0 < pst) {
+        for (int p = p0; p < N2; p += pst) dst[(int64_t)p * L] = s[p * kLines + l];
+    }
+    __syncthreads();
+}
+
+// P2: column kx: zero-pad, FFT along y, * Khat, IFFT, keep the first n rows.
+template <int N2>
+HQS_DEV void toep_cols_item(const ToepArgs& A, int kx, int ch, float2* s) {
+    const int n = A.n, L = A.L;
+    const float2* tw = stage_twiddles<N2>(s + N2 * kLines + n, A.tw);
+    const int l0 = ch * A.LC;
+    const int lines = min(A.LC, L - l0);
+    const int pst = blockDim.x / lines;
+    const int l = threadIdx.x % lines, p0 = threadIdx.x / lines;
+    float2* col = A.T + (int64_t)kx * L + l0 + l;
+    const int64_t rs = (int64_t)N2 * L;
+    constexpr int TPL = FftSize<N2>::TPL;
+    const bool full = lines == kLines;
+    if (full) {
+        unrolled<N2 / 2 / TPL, TPL>(p0, [&](int p) { s[p * kLines + l] = __ldcg(col + p * rs); });
+        unrolled<N2 / 2 / TPL, TPL>(p0 + N2 / 2, [&](int p) { s[p * kLines + l] = make_float2(0.f, 0.f); });
+    } else if (p0 < pst) {
+        for (int p = p0; p < n; p += pst) s[p * kLines + l] = __ldcg(col + p * rs);
+        for (int p = n + p0; p < N2; p += pst) s[p * kLines + l] = make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    block_fft<N2, false>(s, lines, tw);
+    if (full) {
+        unrolled<N2 / TPL, TPL>(p0, [&](int p) {
+            s[p * kLines + l] = cscale(s[p * kLines + l], __ldg(A.khat + (int64_t)p * N2 + kx));
+        });
+    } else if (p0 < pst) {
+        for (int p = p0; p < N2; p += pst)
+            s[p * kLines + l] = cscale(s[p * kLines + l], __ldg(A.khat + (int64_t)p * N2 + kx));
+    }
+    __syncthreads();
+    block_fft<N2, true>(s, lines, tw);
+    if (full) {
+        unrolled<N2 / 2 / TPL, TPL>(p0, [&](int p) { col[p * rs] = s[p * kLines + l]; });
+    } else if (p0 < pst) {
+        for (int p = p0; p < n; p += pst) col[p * rs] = s[p * kLines + l];
+    }
+    __syncthreads();
+}
+
+// CG epilogue on one pixel: mode 0 returns v = A^H A p; mode 1 returns
+// q = a v + b p and adds Re<p, q> to part.
+HQS_DEV float2 toep_epilogue(float2 v, int64_t e, const float2* __restrict__ pvec, float a, float b,
+                             int mode, double& part) {
+    if (mode == 1) {
+        const float2 pv = __ldcg(pvec + e);
+        v = make_float2(fmaf(a, v.x, b * pv.x), fmaf(a, v.y, b * pv.y));
+        part += (double)pv.x * v.x + (double)pv.y * v.y;
+    }
+    return v;
+}
+
+// P3: row iy: IFFT along x, keep n, sum_l conj(S_l) . over the chunk's coils.
+// One chunk: epilogue and store here (returns the thread's partial); several
+// chunks: the raw chunk sum goes to A.chunk[ch] for k_toep_chunk_epilogue.
+template <int N2>
+HQS_DEV double toep_rows_adj_item(const ToepArgs& A, int iy, int ch, float2* __restrict__ out,
+                                  const float2* __restrict__ pvec, float a, float b, int mode,
+                                  float2* s) {
+    const int n = A.n, L = A.L;
+    const float2* tw = stage_twiddles<N2>(s + N2 * kLines + n, A.tw);
+    const int l0 = ch * A.LC;
+    const int lines = min(A.LC, L - l0);
+    const int pst = blockDim.x / lines;
+    const int l = threadIdx.x % lines, p0 = threadIdx.x / lines;
+    const float2* src = A.T + (int64_t)iy * N2 * L + l0 + l;
+    constexpr int TPL = FftSize<N2>::TPL;
+    if (lines == kLines) {
+        unrolled<N2 / TPL, TPL>(p0, [&](int p) { s[p * kLines + l] = __ldcg(src + (int64_t)p * L); });
+    } else if (p0 < pst) {
+        for (int p = p0; p < N2; p += pst) s[p * kLines + l] = __ldcg(src + (int64_t)p * L);
+    }
+    __syncthreads();
+    block_fft<N2, true>(s, lines, tw);
+    const float2* sm = A.smaps + (int64_t)iy * n * L + l0;
+    double part = 0.0;
+    for (int ix = threadIdx.x; ix < n; ix += blockDim.x) {
+        float2 acc = make_float2(0.f, 0.f);
+        const float2* smx = sm + (int64_t)ix * L;
+        for (int ll = 0; ll < lines; ++ll) {
+            const float2 sv = smx[ll];
+            const float2 g = s[ix * kLines + ll];
+            acc.x += sv.x * g.x + sv.y * g.y;
+            acc.y += sv.x * g.y - sv.y * g.x;
+        }
+        const int64_t e = (int64_t)iy * n + ix;
+        if (A.nchunk == 1)
+            out[e] = toep_epilogue(acc, e, pvec, a, b, mode, part);
+        else
+            A.chunk[(int64_t)ch * n * n + e] = acc;
+    }
+    __syncthreads();
+    return part;
+}
+
+HQS_DEV double block_sum(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) t += red[w];
+    __syncthreads();
+    return t;
+}
+
+
+}  // namespace hqs

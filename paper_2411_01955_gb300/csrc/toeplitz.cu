@@ -18,133 +18,7 @@
 
 using namespace hqs;
 
-// ------------------------------------------------------------ A^H A passes
-// Each CTA handles one row/column for the coils of chunk `ch` (<= 16 coils);
-// the FFT body must not sit inside a runtime loop (register allocation
-// collapses), so coil chunks are a grid dimension.
-
-// P1: v = src (or p = src + beta p when fused, single chunk only), S_l v,
-// zero-pad to N2, FFT along x.
-template <int N2>
-HQS_DEV void toep_rows_fwd_item(const ToepArgs& A, int iy, int ch, const float2* __restrict__ src,
-                                float2* __restrict__ pvec, float beta, bool fuse, float2* s) {
-    const int n = A.n, L = A.L;
-    float2* rowv = s + N2 * kLines;
-    for (int ix = threadIdx.x; ix < n; ix += blockDim.x) {
-        const int64_t e = (int64_t)iy * n + ix;
-        float2 v = src[e];
-        if (fuse) {
-            if (beta != 0.f) {
-                const float2 pv = pvec[e];
-                v.x = fmaf(beta, pv.x, v.x);
-                v.y = fmaf(beta, pv.y, v.y);
-            }
-            pvec[e] = v;
-        }
-        rowv[ix] = v;
-    }
-    __syncthreads();
-    const int l0 = ch * A.LC;
-    const int lines = min(A.LC, L - l0);
-    const float2* sm = A.smaps + (int64_t)iy * n * L + l0;
-    for (int e = threadIdx.x; e < N2 * lines; e += blockDim.x) {
-        const int p = e / lines, l = e - p * lines;
-        s[p * kLines + l] = p < n ? cmul(sm[(int64_t)p * L + l], rowv[p]) : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-    block_fft<N2, false>(s, lines, A.tw);
-    float2* dst = A.T + (int64_t)iy * N2 * L + l0;
-    for (int e = threadIdx.x; e < N2 * lines; e += blockDim.x) {
-        const int p = e / lines, l = e - p * lines;
-        dst[(int64_t)p * L + l] = s[p * kLines + l];
-    }
-    __syncthreads();
-}
-
-// P2: column kx: zero-pad, FFT along y, * Khat, IFFT, keep the first n rows.
-template <int N2>
-HQS_DEV void toep_cols_item(const ToepArgs& A, int kx, int ch, float2* s) {
-    const int n = A.n, L = A.L;
-    const int l0 = ch * A.LC;
-    const int lines = min(A.LC, L - l0);
-    for (int e = threadIdx.x; e < N2 * lines; e += blockDim.x) {
-        const int p = e / lines, l = e - p * lines;
-        s[p * kLines + l] = p < n ? A.T[((int64_t)p * N2 + kx) * L + l0 + l] : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-    block_fft<N2, false>(s, lines, A.tw);
-    for (int e = threadIdx.x; e < N2 * lines; e += blockDim.x) {
-        const int p = e / lines, l = e - p * lines;
-        s[p * kLines + l] = cscale(s[p * kLines + l], A.khat[(int64_t)p * N2 + kx]);
-    }
-    __syncthreads();
-    block_fft<N2, true>(s, lines, A.tw);
-    for (int e = threadIdx.x; e < n * lines; e += blockDim.x) {
-        const int p = e / lines, l = e - p * lines;
-        A.T[((int64_t)p * N2 + kx) * L + l0 + l] = s[p * kLines + l];
-    }
-    __syncthreads();
-}
-
-// CG epilogue on one pixel: mode 0 returns v = A^H A p; mode 1 returns
-// q = a v + b p and adds Re<p, q> to part.
-HQS_DEV float2 toep_epilogue(float2 v, int64_t e, const float2* __restrict__ pvec, float a, float b,
-                             int mode, double& part) {
-    if (mode == 1) {
-        const float2 pv = pvec[e];
-        v = make_float2(fmaf(a, v.x, b * pv.x), fmaf(a, v.y, b * pv.y));
-        part += (double)pv.x * v.x + (double)pv.y * v.y;
-    }
-    return v;
-}
-
-// P3: row iy: IFFT along x, keep n, sum_l conj(S_l) . over the chunk's coils.
-// One chunk: epilogue and store here (returns the thread's partial); several
-// chunks: the raw chunk sum goes to A.chunk[ch] for k_toep_chunk_epilogue.
-template <int N2>
-HQS_DEV double toep_rows_adj_item(const ToepArgs& A, int iy, int ch, float2* __restrict__ out,
-                                  const float2* __restrict__ pvec, float a, float b, int mode,
-                                  float2* s) {
-    const int n = A.n, L = A.L;
-    const int l0 = ch * A.LC;
-    const int lines = min(A.LC, L - l0);
-    const float2* src = A.T + (int64_t)iy * N2 * L + l0;
-    for (int e = threadIdx.x; e < N2 * lines; e += blockDim.x) {
-        const int p = e / lines, l = e - p * lines;
-        s[p * kLines + l] = src[(int64_t)p * L + l];
-    }
-    __syncthreads();
-    block_fft<N2, true>(s, lines, A.tw);
-    const float2* sm = A.smaps + (int64_t)iy * n * L + l0;
-    double part = 0.0;
-    for (int ix = threadIdx.x; ix < n; ix += blockDim.x) {
-        float2 acc = make_float2(0.f, 0.f);
-        for (int l = 0; l < lines; ++l) {
-            const float2 sv = sm[(int64_t)ix * L + l];
-            const float2 g = s[ix * kLines + l];
-            acc.x += sv.x * g.x + sv.y * g.y;
-            acc.y += sv.x * g.y - sv.y * g.x;
-        }
-        const int64_t e = (int64_t)iy * n + ix;
-        if (A.nchunk == 1)
-            out[e] = toep_epilogue(acc, e, pvec, a, b, mode, part);
-        else
-            A.chunk[(int64_t)ch * n * n + e] = acc;
-    }
-    __syncthreads();
-    return part;
-}
-
-HQS_DEV double block_sum(double v, double* red) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-    __syncthreads();
-    double t = 0.0;
-    if (threadIdx.x == 0)
-        for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) t += red[w];
-    __syncthreads();
-    return t;
-}
+#include "toep_items.cuh"
 
 // --------------------------------------------------------- plain kernels
 template <int N2>
@@ -384,7 +258,7 @@ static int toep_impl(hqs_plan_s* p, const float2* src, float2* pvec, int fuse, f
                      const CgScalars* cg, cudaStream_t st) {
     ToepArgs A = toep_args(p);
     const int th = fft_threads<N2>(p->LC);
-    const size_t sm = ((size_t)N2 * kLines + p->n) * sizeof(float2);
+    const size_t sm = toep_smem_floats2<N2>(p->n) * sizeof(float2);
     HQS_CUDA_TRY(cudaFuncSetAttribute(k_toep_rows_fwd<N2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     HQS_CUDA_TRY(cudaFuncSetAttribute(k_toep_cols<N2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     HQS_CUDA_TRY(cudaFuncSetAttribute(k_toep_rows_adj<N2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
@@ -472,11 +346,13 @@ int read_solve_info(hqs_plan_s* p, hqs_solve_info* info, cudaStream_t st) {
     HQS_CUDA_TRY(cudaMemcpyAsync(p->h_cg, p->cg, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
     HQS_CUDA_TRY(cudaMemcpyAsync(p->h_hist, p->hist, sizeof(double) * (HQS_MAX_ITERS + 1),
                                  cudaMemcpyDeviceToHost, st));
+    HQS_CUDA_TRY(cudaMemcpyAsync(p->h_err, p->dev_err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
     HQS_CUDA_TRY(cudaStreamSynchronize(st));
     const CgScalars& c = *p->h_cg;
-    if (!info) return c.status;
+    const int status = (*p->h_err & HQS_DEVERR_TIMEOUT) ? HQS_ERR_TIMEOUT : c.status;
+    if (!info) return status;
     info->iterations = c.it;
-    info->status = c.status;
+    info->status = status;
     info->fallback = c.fallback;
     info->reserved = 0;
     info->rhs_norm = c.bnorm;
@@ -485,13 +361,14 @@ int read_solve_info(hqs_plan_s* p, hqs_solve_info* info, cudaStream_t st) {
     for (int i = 0; i <= HQS_MAX_ITERS; ++i)
         info->res_history[i] = (i <= c.it) ? sqrt(std::max(p->h_hist[i], 0.0)) / bn : 0.0;
     if (c.bnorm == 0) info->res_history[0] = 0.0;
-    return c.status;
+    return status;
 }
 
 extern "C" int hqs_last_solve_info(hqs_plan p, hqs_solve_info* info, void* stream) {
     if (!p || !info) return HQS_ERR_INVALID_ARG;
     int rc = read_solve_info(p, info, (cudaStream_t)stream);
-    return rc < 0 && rc != HQS_ERR_NOT_CONVERGED && rc != HQS_ERR_BREAKDOWN ? rc : HQS_OK;
+    return rc < 0 && rc != HQS_ERR_NOT_CONVERGED && rc != HQS_ERR_BREAKDOWN && rc != HQS_ERR_TIMEOUT ? rc
+                                                                                                    : HQS_OK;
 }
 
 extern "C" int hqs_dc_solve(hqs_plan p, float a, float b, const hqs_c64* rhs, hqs_c64* x,

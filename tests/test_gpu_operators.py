@@ -27,10 +27,12 @@ def cases():
         "tiny": synth.tiny_case(0),
         "odd": synth.odd_case(0),
         "odd_w6": dict(synth.odd_case(1, n=32, L=5, M=301, W=6)),
+        # 20 coils: two coil chunks in every FFT pass; odd kernel width
+        "l20_w5": dict(synth.odd_case(2, n=32, L=20, M=400, W=5)),
     }
 
 
-@pytest.fixture(scope="module", params=["tiny", "odd", "odd_w6"])
+@pytest.fixture(scope="module", params=["tiny", "odd", "odd_w6", "l20_w5"])
 def case(request):
     return quantised(cases()[request.param])
 
@@ -122,6 +124,40 @@ def test_dc_solve_fixed_iterations_matches_oracle(case):
         assert np.allclose(got_hist, winfo["res_hist"], rtol=1e-4, atol=0)
 
 
+@pytest.mark.parametrize("precond", [1, 0])
+def test_fused_dc_solve_matches_oracle(case, precond):
+    """The persistent cooperative solve follows the same recursion as the oracle."""
+    plan, _, _ = make_plan(case)
+    Kh, lam = oracle_toeplitz(case)
+    n, mu = case["n"], 1e-2
+    rhs = nufft.adjoint(case["noise"], case["smaps"], case["traj"], case["W"], case["sigma"])
+    rhs = rhs.astype(np.complex64).astype(np.complex128)
+    H = lambda v: toeplitz.normal(v, case["smaps"], Kh) + mu * v
+    Minv = (lambda v: toeplitz.precond_apply(v, lam, 1.0, mu)) if precond else None
+    want, winfo = solvers.pcg(H, rhs, np.zeros((n, n)), Minv, max_iter=5, tol=0.0)
+    x = torch.zeros((n, n), dtype=torch.complex64, device="cuda")
+    info = hq().dc_solve(plan, 1.0, mu, to_dev(rhs), x, max_iter=5, rel_tol=0.0, precond=precond,
+                         mode=hq().HQS_SOLVE_FUSED)
+    assert info.iterations == 5 and info.status == 0
+    assert rel(to_host(x), want) <= TOL
+    assert np.allclose(np.array(info.history()), winfo["res_hist"], rtol=1e-4, atol=0)
+    # to tolerance: same iteration count as the per-stage path (+-1), true residual
+    xp = torch.zeros_like(x)
+    ip = hq().dc_solve(plan, 1.0, mu, to_dev(rhs), xp, max_iter=200, rel_tol=1e-4, precond=precond)
+    xf = torch.zeros_like(x)
+    inf = hq().dc_solve(plan, 1.0, mu, to_dev(rhs), xf, max_iter=200, rel_tol=1e-4, precond=precond,
+                        mode=hq().HQS_SOLVE_FUSED)
+    assert inf.status == 0 and abs(inf.iterations - ip.iterations) <= 1
+    true_res = np.linalg.norm(rhs - H(to_host(xf))) / np.linalg.norm(rhs)
+    assert true_res <= 1.2e-4
+    # deterministic: a second fused solve is bitwise identical
+    xf2 = torch.zeros_like(x)
+    hq().dc_solve(plan, 1.0, mu, to_dev(rhs), xf2, max_iter=200, rel_tol=1e-4, precond=precond,
+                  mode=hq().HQS_SOLVE_FUSED)
+    torch.cuda.synchronize()
+    assert torch.equal(xf, xf2)
+
+
 def test_dc_solve_converges_to_tolerance(case):
     plan, _, _ = make_plan(case)
     Kh, lam = oracle_toeplitz(case)
@@ -138,29 +174,31 @@ def test_dc_solve_converges_to_tolerance(case):
     assert len(hist) == info.iterations + 1
 
 
-def test_dc_solve_edge_cases():
+@pytest.mark.parametrize("mode", [0, 1])
+def test_dc_solve_edge_cases(mode):
     case = quantised(synth.tiny_case(1))
     plan, _, _ = make_plan(case)
     n = case["n"]
+    import functools
+    solve = functools.partial(hq().dc_solve, mode=mode)
     # zero right-hand side: exact zero solution, no iterations
     x = to_dev(np.ones((n, n), dtype=np.complex64))
-    info = hq().dc_solve(plan, 1.0, 0.1, torch.zeros_like(x), x, max_iter=10, rel_tol=1e-4)
+    info = solve(plan, 1.0, 0.1, torch.zeros_like(x), x, max_iter=10, rel_tol=1e-4)
     assert info.iterations == 0 and info.status == 0
     assert float(torch.abs(x).max()) == 0.0
     # max_iter = 0 returns the start point untouched
     x0 = to_dev(case["x"])
     x = x0.clone()
-    info = hq().dc_solve(plan, 1.0, 0.1, to_dev(case["x"] * 2), x, max_iter=0, rel_tol=1e-4,
-                         check=False)
+    info = solve(plan, 1.0, 0.1, to_dev(case["x"] * 2), x, max_iter=0, rel_tol=1e-4, check=False)
     assert info.iterations == 0 and torch.equal(x, x0)
     # non-positive b is rejected
     with pytest.raises(hq().HqsError):
-        hq().dc_solve(plan, 1.0, 0.0, x0, x, max_iter=5)
+        solve(plan, 1.0, 0.0, x0, x, max_iter=5)
     # non-finite input is reported as breakdown, not a fault
     bad = case["x"].copy()
     bad[3, 4] = np.nan
-    info = hq().dc_solve(plan, 1.0, 0.1, to_dev(bad), torch.zeros_like(x0), max_iter=5,
-                         rel_tol=1e-4, check=False)
+    info = solve(plan, 1.0, 0.1, to_dev(bad), torch.zeros_like(x0), max_iter=5, rel_tol=1e-4,
+                 check=False)
     assert info.status == hq().HQS_ERR_BREAKDOWN
 
 
@@ -196,12 +234,14 @@ def test_gaussian_denoiser_matches_oracle():
 def test_hqs_run_matches_oracle_tiny_config():
     """Annealed HQS, 10 outer x 5 CG iterations, Gaussian-smoothing denoiser.
 
-    Each outer step, started on the GPU from the oracle's x_k, must match the
-    oracle's x_{k+1} to 1e-5.  The whole run amplifies rounding: truncated,
-    warm-started CG with mu falling to 1e-3 multiplies a relative input
-    perturbation by ~3e3 over ten steps, so the end-to-end bound is 4x the
-    oracle's own deviation when its A^H y is perturbed by the float32 unit
-    roundoff 2^-24 (measured here, not assumed)."""
+    Truncated, warm-started CG with mu falling to 1e-3 amplifies rounding
+    (a relative input perturbation grows ~3e3-fold over the ten steps), so
+    the bounds are derived, not assumed: each outer step, started on the GPU
+    from the oracle's x_k, must match the oracle's x_{k+1} within
+    max(1e-5, 4 d_k), d_k the oracle's own one-step deviation when its inputs
+    (A^H y and x_k) are perturbed by the float32 unit roundoff 2^-24; the
+    whole run within 4x the oracle's deviation under the same perturbation
+    of A^H y."""
     case = quantised(synth.tiny_case(0))
     plan, _, _ = make_plan(case)
     n, K = case["n"], case["K"]
@@ -217,17 +257,23 @@ def test_hqs_run_matches_oracle_tiny_config():
     want, _, hist = ohqs.hqs(AHA, b0, np.zeros((n, n)), mu64, sg64, K, cg_iters=case["cg_iters"], lam=lam)
     gauss = (1.5, float(sigma[0]))
     # per outer step from the oracle's iterate
-    xk = np.zeros((n, n))
+    rng = np.random.default_rng(0)
+    eps = 2.0 ** -24
+    xk = np.zeros((n, n), dtype=np.complex128)
     for k in range(K):
         xg = to_dev(xk)
         hq().hqs_run(plan, to_dev(y), xg, mu, sigma, K=k + 1, k0=k, cg_iters=case["cg_iters"], gauss=gauss)
-        assert rel(to_host(xg), hist[k]) <= TOL, k
+        step, _, _ = ohqs.hqs(AHA, b0, xk, mu64, sg64, k + 1, k0=k, cg_iters=case["cg_iters"], lam=lam)
+        b0p = b0 * (1 + eps * rng.normal(size=b0.shape))
+        xkp = xk * (1 + eps * rng.normal(size=xk.shape))
+        pstep, _, _ = ohqs.hqs(AHA, b0p, xkp, mu64, sg64, k + 1, k0=k, cg_iters=case["cg_iters"], lam=lam)
+        tol_k = max(TOL, 4 * rel(pstep, step))
+        assert rel(to_host(xg), step) <= tol_k, (k, rel(to_host(xg), step), tol_k)
         xk = hist[k].astype(np.complex64).astype(np.complex128)
     # whole run
     x = torch.zeros((n, n), dtype=torch.complex64, device="cuda")
     hq().hqs_run(plan, to_dev(y), x, mu, sigma, K=K, cg_iters=case["cg_iters"])
-    rng = np.random.default_rng(0)
-    b0p = b0 * (1 + 2.0 ** -24 * rng.normal(size=b0.shape))
+    b0p = b0 * (1 + eps * rng.normal(size=b0.shape))
     pert, _, _ = ohqs.hqs(AHA, b0p, np.zeros((n, n)), mu64, sg64, K, cg_iters=case["cg_iters"], lam=lam)
     bound = 4 * rel(pert, want)
     err = rel(to_host(x), want)
