@@ -62,6 +62,8 @@ extern "C" {
 /* execution modes for hqs_dc_solve */
 #define HQS_SOLVE_PLAIN      0   /* one launch per stage, host checks the residual each iteration */
 #define HQS_SOLVE_FUSED      1   /* one persistent cooperative launch for the whole solve */
+#define HQS_SOLVE_X0_ZERO    16  /* flag (OR with the mode): start from x = 0, ignoring x on entry;
+                                    saves the initial A^H A apply */
 
 #define HQS_MAX_ITERS 512
 
@@ -131,6 +133,13 @@ HQS_API int hqs_forward(hqs_plan plan, const hqs_c64* x, hqs_c64* y, void* strea
  * combination with conj(S_l).  y: (L, M); x: (ny, nx). */
 HQS_API int hqs_adjoint(hqs_plan plan, const hqs_c64* y, hqs_c64* x, void* stream);
 
+/* x = A^H y + c z: the data-consistency right-hand side of the HQS step
+ * (Sec. 3.3/3.4, rhs = A^H y + mu_k z_k for P = Id), with the axpy fused into
+ * the adjoint's last pass.  z: (ny, nx) device; z may be the same buffer as
+ * x (each pixel is read before it is written). */
+HQS_API int hqs_adjoint_axpy(hqs_plan plan, const hqs_c64* y, float c, const hqs_c64* z,
+                             hqs_c64* x, void* stream);
+
 /* ------------------------------------------------- Toeplitz normal (a4) */
 /* out = A^H A x (Sec. 3.4, A = F_Omega (x) S_l) through the exact 2N
  * circulant embedding of F^H F; never touches the trajectory.
@@ -198,6 +207,23 @@ HQS_API int hqs_gaussian_denoise(void* user, const hqs_c64* in, hqs_c64* out,
 HQS_API int hqs_power_iteration(hqs_plan plan, int iters, double* lam_max, void* stream);
 
 HQS_API const char* hqs_status_string(int status);
+
+/* Tuning knobs (no counterpart in the paper), set per plan by the autotuner:
+ *   HQS_TUNE_FUSED_GRID  cap on the persistent solve's CTAs (0 = all resident)
+ *   HQS_TUNE_PC_LINES    preconditioner rows/columns per work item (1..16) */
+#define HQS_TUNE_FUSED_GRID   1
+#define HQS_TUNE_PC_LINES     2
+#define HQS_TUNE_SPREAD_TILE  3
+HQS_API int hqs_plan_set_tuning(hqs_plan plan, int key, int value);
+
+/* Diagnostics (no counterpart in the paper): phase trace of the persistent
+ * solve.  enable = 1 allocates a trace buffer on the plan (returns 0); later
+ * calls with enable = 0 synchronise `stream` and copy up to max_out
+ * globaltimer stamps (ns) of the last fused solve into out (host): the start,
+ * one stamp after every grid barrier, and the end.  Returns the number of
+ * stamps (or a negative status). */
+HQS_API int hqs_debug_phase_trace(hqs_plan plan, int enable, unsigned long long* out, int max_out,
+                                  void* stream);
 
 #ifdef __cplusplus
 }

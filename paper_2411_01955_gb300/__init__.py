@@ -12,8 +12,9 @@ from ._lib import (  # noqa: F401
     HQS_ERR_TIMEOUT, HQS_ERR_CALLBACK, HQS_ERR_CUDA, HQS_ERR_UNSUPPORTED,
     HQS_PREC_FP32, HQS_PREC_BF16X3, HQS_PREC_FP16X3,
     HQS_PRECOND_NONE, HQS_PRECOND_DC, HQS_PRECOND_LEARNED,
-    HQS_SOLVE_PLAIN, HQS_SOLVE_FUSED, HQS_MAX_ITERS,
+    HQS_SOLVE_PLAIN, HQS_SOLVE_FUSED, HQS_SOLVE_X0_ZERO, HQS_MAX_ITERS,
     HqsError, Plan, SolveInfo, library, library_path,
-    plan_create, forward, adjoint, toeplitz_normal, precond_apply, dc_solve,
+    plan_create, forward, adjoint, adjoint_axpy, toeplitz_normal, precond_apply, dc_solve,
     last_solve_info, hqs_run, gaussian_denoise, power_iteration, status_string,
+    debug_phase_trace, plan_set_tuning, HQS_TUNE_FUSED_GRID, HQS_TUNE_PC_LINES,
 )

@@ -20,6 +20,8 @@ HQS_ERR_UNSUPPORTED = -8
 HQS_PREC_FP32, HQS_PREC_BF16X3, HQS_PREC_FP16X3 = 0, 1, 2
 HQS_PRECOND_NONE, HQS_PRECOND_DC, HQS_PRECOND_LEARNED = 0, 1, 2
 HQS_SOLVE_PLAIN, HQS_SOLVE_FUSED = 0, 1
+HQS_SOLVE_X0_ZERO = 16
+HQS_TUNE_FUSED_GRID, HQS_TUNE_PC_LINES, HQS_TUNE_SPREAD_TILE = 1, 2, 3
 HQS_MAX_ITERS = 512
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -62,6 +64,8 @@ _SIGS = {
     "hqs_plan_get_info": (C.c_int, [C.c_void_p, C.POINTER(PlanInfo)]),
     "hqs_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "hqs_adjoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "hqs_adjoint_axpy": (C.c_int, [C.c_void_p, C.c_void_p, C.c_float, C.c_void_p, C.c_void_p,
+                                   C.c_void_p]),
     "hqs_toeplitz_normal": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "hqs_precond_apply": (C.c_int, [C.c_void_p, C.c_float, C.c_float, C.c_void_p, C.c_void_p,
                                     C.c_void_p]),
@@ -76,6 +80,9 @@ _SIGS = {
                                        C.c_float, C.c_void_p]),
     "hqs_power_iteration": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_void_p]),
     "hqs_status_string": (C.c_char_p, [C.c_int]),
+    "hqs_plan_set_tuning": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "hqs_debug_phase_trace": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_ulonglong), C.c_int,
+                                        C.c_void_p]),
 }
 
 
@@ -178,6 +185,14 @@ def adjoint(plan: Plan, y, x, stream=None):
     return x
 
 
+def adjoint_axpy(plan: Plan, y, c, z, x, stream=None):
+    """x = A^H y + c z (the HQS data-consistency right-hand side)."""
+    _check(library().hqs_adjoint_axpy(plan.handle, _ptr(y, torch.complex64, "y"), float(c),
+                                      _ptr(z, torch.complex64, "z"), _ptr(x, torch.complex64, "x"),
+                                      _stream(stream)), "hqs_adjoint_axpy")
+    return x
+
+
 def toeplitz_normal(plan: Plan, x, out, precision=HQS_PREC_FP32, stream=None):
     _check(library().hqs_toeplitz_normal(plan.handle, _ptr(x, torch.complex64, "x"),
                                          _ptr(out, torch.complex64, "out"), int(precision),
@@ -275,3 +290,17 @@ def power_iteration(plan: Plan, iters=50, stream=None) -> float:
     _check(library().hqs_power_iteration(plan.handle, int(iters), C.byref(lam), _stream(stream)),
            "hqs_power_iteration")
     return lam.value
+
+
+def debug_phase_trace(plan: Plan, enable=False, stream=None):
+    """enable=True arms the persistent solve's phase trace; enable=False
+    returns the globaltimer stamps (ns) of the last fused solve."""
+    buf = (C.c_ulonglong * 4096)()
+    rc = library().hqs_debug_phase_trace(plan.handle, 1 if enable else 0, buf, 4096, _stream(stream))
+    if rc < 0:
+        raise HqsError(rc, "hqs_debug_phase_trace")
+    return [buf[i] for i in range(rc)]
+
+
+def plan_set_tuning(plan: Plan, key: int, value: int):
+    _check(library().hqs_plan_set_tuning(plan.handle, int(key), int(value)), "hqs_plan_set_tuning")

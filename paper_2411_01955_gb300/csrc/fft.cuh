@@ -105,10 +105,98 @@ template <bool INV> struct Dft<8, INV> {
     }
 };
 
+// Composite radix R = R1 R2 with gcd(R1, R2) = 1 by the prime-factor
+// (Good-Thomas) mapping: input index n = (R2 n1 + R1 n2) mod R, output index
+// k with k = k1 (mod R1), k = k2 (mod R2); then
+// X[k] = sum_n1 w_R1^(n1 k1) sum_n2 w_R2^(n2 k2) x[n], with no twiddles
+// between the two small DFTs.  All indices are compile-time register names.
+template <int R1, int R2> struct Crt {
+    // k in [0, R) with k % R1 == k1 and k % R2 == k2
+    static constexpr int out(int k1, int k2) {
+        for (int k = 0; k < R1 * R2; ++k)
+            if (k % R1 == k1 && k % R2 == k2) return k;
+        return -1;
+    }
+};
+
+template <int R1, int R2, bool INV> struct DftPfa {
+    HQS_DEV static void run(float2* v) {
+        constexpr int R = R1 * R2;
+        float2 a[R1][R2];
+#pragma unroll
+        for (int n1 = 0; n1 < R1; ++n1)
+#pragma unroll
+            for (int n2 = 0; n2 < R2; ++n2) a[n1][n2] = v[(R2 * n1 + R1 * n2) % R];
+#pragma unroll
+        for (int n1 = 0; n1 < R1; ++n1) Dft<R2, INV>::run(a[n1]);
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) {
+            float2 c[R1];
+#pragma unroll
+            for (int n1 = 0; n1 < R1; ++n1) c[n1] = a[n1][k2];
+            Dft<R1, INV>::run(c);
+#pragma unroll
+            for (int k1 = 0; k1 < R1; ++k1) v[Crt<R1, R2>::out(k1, k2)] = c[k1];
+        }
+    }
+};
+
+template <bool INV> struct Dft<6, INV> : DftPfa<2, 3, INV> {};
+template <bool INV> struct Dft<10, INV> : DftPfa<2, 5, INV> {};
+template <bool INV> struct Dft<12, INV> : DftPfa<4, 3, INV> {};
+template <bool INV> struct Dft<40, INV> : DftPfa<8, 5, INV> {};
+
+// First-stage DFT when the upper half of the line is known to be zero
+// (zero padding): inputs r >= R/2 are not read and not added.
+template <int R, bool INV> struct DftHalfIn {
+    HQS_DEV static void run(float2* v) {
+#pragma unroll
+        for (int r = R / 2; r < R; ++r) v[r] = make_float2(0.f, 0.f);
+        Dft<R, INV>::run(v);
+    }
+};
+template <bool INV> struct DftHalfIn<4, INV> {
+    HQS_DEV static void run(float2* v) {   // inputs (a, b, 0, 0)
+        const float2 a = v[0], b = v[1];
+        const float2 jb = mul_mi<INV>(b);
+        v[0] = cadd(a, b);
+        v[1] = cadd(a, jb);
+        v[2] = csub(a, b);
+        v[3] = csub(a, jb);
+    }
+};
+template <bool INV> struct DftHalfIn<8, INV> {
+    HQS_DEV static void run(float2* v) {   // inputs (v0..v3, 0, 0, 0, 0)
+        float2 e[4] = {v[0], v[2], make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+        float2 o[4] = {v[1], v[3], make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+        DftHalfIn<4, INV>::run(e);
+        DftHalfIn<4, INV>::run(o);
+        float2 o1, o3;
+        if (!INV) {
+            o1 = make_float2((o[1].x + o[1].y) * kSqrtHalf, (o[1].y - o[1].x) * kSqrtHalf);
+            o3 = make_float2((o[3].y - o[3].x) * kSqrtHalf, -(o[3].x + o[3].y) * kSqrtHalf);
+        } else {
+            o1 = make_float2((o[1].x - o[1].y) * kSqrtHalf, (o[1].x + o[1].y) * kSqrtHalf);
+            o3 = make_float2(-(o[3].x + o[3].y) * kSqrtHalf, (o[3].x - o[3].y) * kSqrtHalf);
+        }
+        const float2 o2 = mul_mi<INV>(o[2]);
+        v[0] = cadd(e[0], o[0]);
+        v[4] = csub(e[0], o[0]);
+        v[1] = cadd(e[1], o1);
+        v[5] = csub(e[1], o1);
+        v[2] = cadd(e[2], o2);
+        v[6] = csub(e[2], o2);
+        v[3] = cadd(e[3], o3);
+        v[7] = csub(e[3], o3);
+    }
+};
+
 // One Stockham stage.  `s` points at element (0, line); consecutive positions
 // are kLines float2 apart.  Threads with act == false (given t = 0 and line 0)
-// read but do not write.
-template <int N, int E, int R, int P, bool INV>
+// read but do not write.  ZIN (first stage only): the line's upper half is
+// zero and is neither read nor added.  HOUT (last stage only): only the lower
+// half of the output is wanted and the upper half is not written.
+template <int N, int E, int R, int P, bool INV, bool ZIN = false, bool HOUT = false>
 HQS_DEV void fft_stage(float2* s, int t, bool act, const float2* __restrict__ tw) {
     constexpr int st = kLines;
     constexpr int TPL = N / E;
@@ -116,6 +204,10 @@ HQS_DEV void fft_stage(float2* s, int t, bool act, const float2* __restrict__ tw
     constexpr int BPT = E / R;
     static_assert(E % R == 0, "radix must divide elements per thread");
     static_assert(NB == TPL * BPT, "butterfly split");
+    static_assert(!ZIN || (P == 1 && R % 2 == 0), "zero-input pruning is for an even first stage");
+    static_assert(!HOUT || (P * R == N && R % 2 == 0), "half-output pruning is for an even last stage");
+    constexpr int RIN = ZIN ? R / 2 : R;
+    constexpr int ROUT = HOUT ? R / 2 : R;
     float2 v[E];
     // Loads are unconditional (inactive threads read line 0 at t = 0, which
     // is in bounds): a predicated load block inside a caller's loop makes the
@@ -124,7 +216,7 @@ HQS_DEV void fft_stage(float2* s, int t, bool act, const float2* __restrict__ tw
     for (int b = 0; b < BPT; ++b) {
         const int i = t + b * TPL;
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[b * R + r] = s[(i + r * NB) * st];
+        for (int r = 0; r < RIN; ++r) v[b * R + r] = s[(i + r * NB) * st];
     }
     __syncthreads();
     if (act) {
@@ -140,10 +232,13 @@ HQS_DEV void fft_stage(float2* s, int t, bool act, const float2* __restrict__ tw
                     v[b * R + r] = cmul(v[b * R + r], w);
                 }
             }
-            Dft<R, INV>::run(&v[b * R]);
+            if (ZIN)
+                DftHalfIn<R, INV>::run(&v[b * R]);
+            else
+                Dft<R, INV>::run(&v[b * R]);
             const int j = (i - k) * R + k;
 #pragma unroll
-            for (int r = 0; r < R; ++r) s[(j + r * P) * st] = v[b * R + r];
+            for (int r = 0; r < ROUT; ++r) s[(j + r * P) * st] = v[b * R + r];
         }
     }
     __syncthreads();
@@ -156,13 +251,13 @@ template <int N> struct FftSize;
     template <> struct FftSize<NN> {                                                  \
         static constexpr int E = EE;                                                  \
         static constexpr int TPL = NN / EE;                                           \
-        template <bool INV>                                                           \
+        template <bool INV, bool ZIN, bool HOUT>                                      \
         HQS_DEV static void run(float2* s, int t, bool act, const float2* tw) {        \
             __VA_ARGS__                                                               \
         }                                                                             \
     };
 
-#define ST(R, P) fft_stage<NN_, E_, R, P, INV>(s, t, act, tw);
+#define ST(R, P) fft_stage<NN_, E_, R, P, INV, ZIN && (P == 1), HOUT && (P * R == NN_)>(s, t, act, tw);
 
 #define NN_ 16
 #define E_ 4
@@ -191,12 +286,12 @@ HQS_FFT_SIZE(256, 8, ST(8, 1) ST(8, 8) ST(4, 64))
 #undef E_
 #define NN_ 320
 #define E_ 40
-HQS_FFT_SIZE(320, 40, ST(8, 1) ST(8, 8) ST(5, 64))
+HQS_FFT_SIZE(320, 40, ST(8, 1) ST(40, 8))
 #undef NN_
 #undef E_
 #define NN_ 384
 #define E_ 24
-HQS_FFT_SIZE(384, 24, ST(8, 1) ST(8, 8) ST(3, 64) ST(2, 192))
+HQS_FFT_SIZE(384, 24, ST(8, 1) ST(8, 8) ST(6, 64))
 #undef NN_
 #undef E_
 #define NN_ 512
@@ -206,12 +301,12 @@ HQS_FFT_SIZE(512, 8, ST(8, 1) ST(8, 8) ST(8, 64))
 #undef E_
 #define NN_ 640
 #define E_ 40
-HQS_FFT_SIZE(640, 40, ST(8, 1) ST(8, 8) ST(5, 64) ST(2, 320))
+HQS_FFT_SIZE(640, 40, ST(8, 1) ST(8, 8) ST(10, 64))
 #undef NN_
 #undef E_
 #define NN_ 768
 #define E_ 24
-HQS_FFT_SIZE(768, 24, ST(8, 1) ST(8, 8) ST(4, 64) ST(3, 256))
+HQS_FFT_SIZE(768, 24, ST(8, 1) ST(8, 8) ST(12, 64))
 #undef NN_
 #undef E_
 #undef ST
@@ -223,7 +318,7 @@ HQS_FFT_SIZE(768, 24, ST(8, 1) ST(8, 8) ST(4, 64) ST(3, 256))
 // caller synchronises before (after filling s); this routine ends with a
 // barrier.  (A loop over line groups here doubles register use, so the launch
 // shape covers every line at once instead.)
-template <int N, bool INV>
+template <int N, bool INV, bool ZIN = false, bool HOUT = false>
 HQS_DEV void block_fft(float2* s, int nlines, const float2* tw) {
     constexpr int TPL = FftSize<N>::TPL;
     const int lpg = blockDim.x / TPL;
@@ -236,7 +331,7 @@ HQS_DEV void block_fft(float2* s, int nlines, const float2* tw) {
     const int ll = tid % lpg;
     const int t = tid / lpg;
     const bool act = (ll < nlines) && (t < TPL);
-    FftSize<N>::template run<INV>(s + (act ? ll : 0), act ? t : 0, act, tw);
+    FftSize<N>::template run<INV, ZIN, HOUT>(s + (act ? ll : 0), act ? t : 0, act, tw);
 }
 
 // Copies the N-point twiddle table into shared memory; the caller's barrier

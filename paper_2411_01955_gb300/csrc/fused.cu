@@ -37,6 +37,7 @@ struct FusedArgs {
     const float2* twN;  // n-point twiddles
     int Q;              // preconditioner lines per item
     int precond;
+    int x0_zero;        // start from x = 0 (no initial A^H A apply)
     int max_iter;
     double rel_tol2;
     double* part;       // [NSLOTS][HQS_MAX_BLOCKS]
@@ -44,7 +45,15 @@ struct FusedArgs {
     double* hist;
     unsigned* bar;      // [0] arrivals, [1] generation
     unsigned* err;
+    unsigned long long* trace;  // optional: globaltimer stamp after each barrier
+    int trace_max;
 };
+
+HQS_DEV unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 // Grid-wide barrier (cooperative launch: all CTAs are resident).  Returns
 // false when the wait exceeded its limit or another CTA reported an error.
@@ -220,7 +229,8 @@ template <int N2, int N> constexpr size_t fused_smem_floats2() {
 }
 
 template <int N2, int N>
-__global__ void __launch_bounds__(FftSize<N2>::TPL * kLines)
+__global__ void __launch_bounds__(FftSize<N2>::TPL * kLines,
+                                  (512 / (FftSize<N2>::TPL * kLines)) > 1 ? 512 / (FftSize<N2>::TPL * kLines) : 1)
     k_pcg_persistent(FusedArgs F) {
     extern __shared__ float2 s[];
     __shared__ double red[33];
@@ -238,32 +248,39 @@ __global__ void __launch_bounds__(FftSize<N2>::TPL * kLines)
     double* P_BB = F.part + SLOT_BB * HQS_MAX_BLOCKS;
     double* P_RZ = F.part + SLOT_RZ * HQS_MAX_BLOCKS;
     const bool lead = bid == 0 && threadIdx.x == 0;
-#define BARRIER()                                  \
-    do {                                           \
-        if (!grid_barrier(F.bar, F.err)) return;   \
+    int ntrace = 0;
+    if (lead && F.trace && F.trace_max > 0) F.trace[ntrace++] = global_ns();
+#define BARRIER()                                                            \
+    do {                                                                     \
+        if (!grid_barrier(F.bar, F.err)) return;                             \
+        if (lead && F.trace && ntrace < F.trace_max) F.trace[ntrace++] = global_ns(); \
     } while (0)
 
-    // ---- r = rhs - H x
-    for (int it = bid; it < n * nch; it += G) toep_rows_fwd_item<N2>(A, it % n, it / n, F.x, nullptr, 0.f, false, s);
-    BARRIER();
-    for (int it = bid; it < N2 * nch; it += G) toep_cols_item<N2>(A, it % N2, it / N2, s);
-    BARRIER();
-    for (int it = bid; it < n * nch; it += G) toep_rows_adj_item<N2>(A, it % n, it / n, F.q, F.x, F.a, F.b, 1, s);
-    if (nch > 1) {
+    // ---- r = rhs - H x  (x = 0: r = rhs without an A^H A apply)
+    if (!F.x0_zero) {
+        for (int it = bid; it < n * nch; it += G) toep_rows_fwd_item<N2>(A, it % n, it / n, F.x, nullptr, 0.f, false, s);
         BARRIER();
-        double dummy = 0.0;
-        for (int e = bid * blockDim.x + threadIdx.x; e < count; e += G * blockDim.x) {
-            float2 v = make_float2(0.f, 0.f);
-            for (int c = 0; c < nch; ++c) v = cadd(v, __ldcg(A.chunk + (int64_t)c * count + e));
-            F.q[e] = toep_epilogue(v, e, F.x, F.a, F.b, 1, dummy);
+        for (int it = bid; it < N2 * nch; it += G) toep_cols_item<N2>(A, it % N2, it / N2, s);
+        BARRIER();
+        for (int it = bid; it < n * nch; it += G) toep_rows_adj_item<N2>(A, it % n, it / n, F.q, F.x, F.a, F.b, 1, s);
+        if (nch > 1) {
+            BARRIER();
+            double dummy = 0.0;
+            for (int e = bid * blockDim.x + threadIdx.x; e < count; e += G * blockDim.x) {
+                float2 v = make_float2(0.f, 0.f);
+                for (int c = 0; c < nch; ++c) v = cadd(v, __ldcg(A.chunk + (int64_t)c * count + e));
+                F.q[e] = toep_epilogue(v, e, F.x, F.a, F.b, 1, dummy);
+            }
         }
+        BARRIER();
     }
-    BARRIER();
     {
         double rr = 0.0, bb = 0.0;
         for (int e = bid * blockDim.x + threadIdx.x; e < count; e += G * blockDim.x) {
             const float2 bv = F.rhs[e];
-            const float2 v = csub(bv, __ldcg(F.q + e));
+            float2 v = bv;
+            if (F.x0_zero) F.x[e] = make_float2(0.f, 0.f);
+            else v = csub(bv, __ldcg(F.q + e));
             F.r[e] = v;
             rr += (double)v.x * v.x + (double)v.y * v.y;
             bb += (double)bv.x * bv.x + (double)bv.y * bv.y;
@@ -402,12 +419,14 @@ __global__ void __launch_bounds__(FftSize<N2>::TPL * kLines)
         c->zero_rhs = zero_rhs;
         c->max_iter = F.max_iter;
         c->fallback = 0;
+        if (F.trace && ntrace < F.trace_max) F.trace[ntrace++] = global_ns();
+        if (F.trace) F.trace[F.trace_max] = ntrace;
     }
 }
 
 template <int N2, int N>
 static int pcg_fused_impl(hqs_plan_s* p, float a, float b, const float2* rhs, float2* x, int max_iter,
-                          double rel_tol, int precond, cudaStream_t st) {
+                          double rel_tol, int precond, bool x0_zero, cudaStream_t st) {
     FusedArgs F;
     F.A = toep_args(p);
     F.a = a;
@@ -420,8 +439,9 @@ static int pcg_fused_impl(hqs_plan_s* p, float a, float b, const float2* rhs, fl
     F.pcb = p->pc_buf;
     F.lam = p->lam;
     F.twN = plan_twiddles(p, N);
-    F.Q = kLines;
+    F.Q = std::max(1, std::min(p->pc_lines, kLines));
     F.precond = precond == HQS_PRECOND_DC ? 1 : 0;
+    F.x0_zero = x0_zero ? 1 : 0;
     F.max_iter = max_iter;
     F.rel_tol2 = rel_tol * rel_tol;
     F.part = p->partials;
@@ -429,6 +449,8 @@ static int pcg_fused_impl(hqs_plan_s* p, float a, float b, const float2* rhs, fl
     F.hist = p->hist;
     F.bar = p->barrier;
     F.err = p->dev_err;
+    F.trace = p->trace;
+    F.trace_max = p->trace ? HQS_TRACE_MAX : 0;
     auto kern = k_pcg_persistent<N2, N>;
     const int threads = FftSize<N2>::TPL * kLines;
     const size_t sm = fused_smem_floats2<N2, N>() * sizeof(float2);
@@ -449,16 +471,52 @@ static int pcg_fused_impl(hqs_plan_s* p, float a, float b, const float2* rhs, fl
 }
 
 int pcg_fused(hqs_plan_s* p, float a, float b, const float2* rhs, float2* x, int max_iter, double rel_tol,
-              int precond, int precision, cudaStream_t st) {
+              int precond, int precision, bool x0_zero, cudaStream_t st) {
     if (precision != HQS_PREC_FP32) return HQS_ERR_UNSUPPORTED;
     switch (p->n) {
-        case 16: return pcg_fused_impl<32, 16>(p, a, b, rhs, x, max_iter, rel_tol, precond, st);
-        case 32: return pcg_fused_impl<64, 32>(p, a, b, rhs, x, max_iter, rel_tol, precond, st);
-        case 64: return pcg_fused_impl<128, 64>(p, a, b, rhs, x, max_iter, rel_tol, precond, st);
-        case 128: return pcg_fused_impl<256, 128>(p, a, b, rhs, x, max_iter, rel_tol, precond, st);
-        case 256: return pcg_fused_impl<512, 256>(p, a, b, rhs, x, max_iter, rel_tol, precond, st);
-        case 320: return pcg_fused_impl<640, 320>(p, a, b, rhs, x, max_iter, rel_tol, precond, st);
-        case 384: return pcg_fused_impl<768, 384>(p, a, b, rhs, x, max_iter, rel_tol, precond, st);
+        case 16: return pcg_fused_impl<32, 16>(p, a, b, rhs, x, max_iter, rel_tol, precond, x0_zero, st);
+        case 32: return pcg_fused_impl<64, 32>(p, a, b, rhs, x, max_iter, rel_tol, precond, x0_zero, st);
+        case 64: return pcg_fused_impl<128, 64>(p, a, b, rhs, x, max_iter, rel_tol, precond, x0_zero, st);
+        case 128: return pcg_fused_impl<256, 128>(p, a, b, rhs, x, max_iter, rel_tol, precond, x0_zero, st);
+        case 256: return pcg_fused_impl<512, 256>(p, a, b, rhs, x, max_iter, rel_tol, precond, x0_zero, st);
+        case 320: return pcg_fused_impl<640, 320>(p, a, b, rhs, x, max_iter, rel_tol, precond, x0_zero, st);
+        case 384: return pcg_fused_impl<768, 384>(p, a, b, rhs, x, max_iter, rel_tol, precond, x0_zero, st);
         default: return HQS_ERR_INVALID_ARG;
+    }
+}
+
+extern "C" int hqs_debug_phase_trace(hqs_plan p, int enable, unsigned long long* out, int max_out,
+                                     void* stream) {
+    if (!p) return HQS_ERR_INVALID_ARG;
+    if (enable && !p->trace) {
+        HQS_CUDA_TRY(cudaMalloc(&p->trace, (HQS_TRACE_MAX + 1) * sizeof(unsigned long long)));
+        HQS_CUDA_TRY(cudaMemset(p->trace, 0, (HQS_TRACE_MAX + 1) * sizeof(unsigned long long)));
+        return 0;
+    }
+    if (!p->trace) return 0;
+    unsigned long long h[HQS_TRACE_MAX + 1];
+    HQS_CUDA_TRY(cudaMemcpyAsync(h, p->trace, sizeof(h), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    HQS_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    const int cnt = (int)std::min<unsigned long long>(h[HQS_TRACE_MAX], HQS_TRACE_MAX);
+    if (out)
+        for (int i = 0; i < cnt && i < max_out; ++i) out[i] = h[i];
+    return cnt;
+}
+
+extern "C" int hqs_plan_set_tuning(hqs_plan p, int key, int value) {
+    if (!p) return HQS_ERR_INVALID_ARG;
+    switch (key) {
+        case HQS_TUNE_FUSED_GRID:
+            if (value < 0) return HQS_ERR_INVALID_ARG;
+            p->fused_grid = value;
+            return HQS_OK;
+        case HQS_TUNE_PC_LINES:
+            if (value < 1 || value > kLines) return HQS_ERR_INVALID_ARG;
+            p->pc_lines = value;
+            return HQS_OK;
+        case HQS_TUNE_SPREAD_TILE:
+            return HQS_ERR_UNSUPPORTED;   // fixed at plan creation
+        default:
+            return HQS_ERR_INVALID_ARG;
     }
 }

@@ -250,8 +250,8 @@ __global__ void k_adj_cols(const float2* __restrict__ Hg, int n, int L, int LC, 
 template <int G>
 __global__ void k_adj_rows(const float2* __restrict__ V, const float2* __restrict__ smaps,
                            const float* __restrict__ apod, int n, int L, int LC, int nchunk,
-                           float scale, const float2* __restrict__ twg, float2* __restrict__ x,
-                           float2* __restrict__ part) {
+                           float scale, const float2* __restrict__ twg, float2* x,
+                           float2* __restrict__ part, float zc, const float2* z) {
     extern __shared__ float2 s[];
     const float2* tw = stage_twiddles<G>(s + G * kLines, twg);
     const int iy = blockIdx.x;
@@ -277,21 +277,35 @@ __global__ void k_adj_rows(const float2* __restrict__ V, const float2* __restric
             a.x += sv.x * g.x + sv.y * g.y;
             a.y += sv.x * g.y - sv.y * g.x;
         }
-        if (nchunk == 1)
-            x[(int64_t)iy * n + ix] = cscale(a, ay * apod[ix]);
-        else
+        if (nchunk == 1) {
+            const int64_t e = (int64_t)iy * n + ix;
+            float2 v = cscale(a, ay * apod[ix]);
+            if (z) {
+                const float2 zv = z[e];
+                v.x = fmaf(zc, zv.x, v.x);
+                v.y = fmaf(zc, zv.y, v.y);
+            }
+            x[e] = v;
+        } else {
             part[((int64_t)blockIdx.y * n + iy) * n + ix] = a;
+        }
     }
 }
 
 __global__ void k_adj_chunk_sum(const float2* __restrict__ part, const float* __restrict__ apod, int n,
-                                int nchunk, float scale, float2* __restrict__ x) {
+                                int nchunk, float scale, float2* x, float zc, const float2* z) {
     const int count = n * n;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x) {
         float2 a = make_float2(0.f, 0.f);
         for (int c = 0; c < nchunk; ++c) a = cadd(a, part[(int64_t)c * count + e]);
         const int iy = e / n, ix = e - iy * n;
-        x[e] = cscale(a, apod[iy] * apod[ix] * scale);
+        float2 v = cscale(a, apod[iy] * apod[ix] * scale);
+        if (z) {
+            const float2 zv = z[e];
+            v.x = fmaf(zc, zv.x, v.x);
+            v.y = fmaf(zc, zv.y, v.y);
+        }
+        x[e] = v;
     }
 }
 
@@ -311,7 +325,7 @@ static int fwd_fft_impl(hqs_plan_s* p, const float2* x, cudaStream_t st) {
 }
 
 template <int G>
-static int adj_fft_impl(hqs_plan_s* p, float2* x, cudaStream_t st) {
+static int adj_fft_impl(hqs_plan_s* p, float2* x, float zc, const float2* z, cudaStream_t st) {
     const float2* tw = plan_twiddles(p, G);
     const int th = fft_threads<G>(p->LC);
     const size_t sm = nufft_smem_floats2<G>() * sizeof(float2);
@@ -319,10 +333,10 @@ static int adj_fft_impl(hqs_plan_s* p, float2* x, cudaStream_t st) {
     HQS_CUDA_TRY(cudaFuncSetAttribute(k_adj_rows<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     k_adj_cols<G><<<dim3(G, p->nchunk), th, sm, st>>>(p->grid, p->n, p->L, p->LC, p->nchunk, tw, p->work);
     k_adj_rows<G><<<dim3(p->n, p->nchunk), th, sm, st>>>(p->work, p->smaps, p->apod, p->n, p->L, p->LC,
-                                                         p->nchunk, p->scale, tw, x, p->chunk_buf);
+                                                         p->nchunk, p->scale, tw, x, p->chunk_buf, zc, z);
     if (p->nchunk > 1)
         k_adj_chunk_sum<<<std::min(ceil_div(p->n * p->n, 256), 1024), 256, 0, st>>>(
-            p->chunk_buf, p->apod, p->n, p->nchunk, p->scale, x);
+            p->chunk_buf, p->apod, p->n, p->nchunk, p->scale, x, zc, z);
     HQS_CUDA_TRY(cudaGetLastError());
     return HQS_OK;
 }
@@ -369,11 +383,15 @@ int launch_fwd(hqs_plan_s* p, const float2* x, float2* y, cudaStream_t st) {
     return dispatch_w(p->W, [&]<int WW>() { return interp_impl<WW>(p, y, st); });
 }
 
-int launch_adj(hqs_plan_s* p, const float2* y, float2* x, cudaStream_t st) {
+int launch_adj_axpy(hqs_plan_s* p, const float2* y, float zc, const float2* z, float2* x, cudaStream_t st) {
     HQS_CUDA_TRY(cudaMemsetAsync(p->grid, 0, (size_t)p->G * p->G * p->L * sizeof(float2), st));
     int rc = dispatch_w(p->W, [&]<int WW>() { return spread_impl<WW>(p, y, st); });
     if (rc != HQS_OK) return rc;
-    return dispatch_fft_size(p->G, [&]<int GG>() { return adj_fft_impl<GG>(p, x, st); });
+    return dispatch_fft_size(p->G, [&]<int GG>() { return adj_fft_impl<GG>(p, x, zc, z, st); });
+}
+
+int launch_adj(hqs_plan_s* p, const float2* y, float2* x, cudaStream_t st) {
+    return launch_adj_axpy(p, y, 0.f, nullptr, x, st);
 }
 
 extern "C" int hqs_forward(hqs_plan p, const hqs_c64* x, hqs_c64* y, void* stream) {
@@ -386,4 +404,11 @@ extern "C" int hqs_adjoint(hqs_plan p, const hqs_c64* y, hqs_c64* x, void* strea
     if (!p || !x || (!y && p->M > 0)) return HQS_ERR_INVALID_ARG;
     return launch_adj(p, reinterpret_cast<const float2*>(y), reinterpret_cast<float2*>(x),
                       (cudaStream_t)stream);
+}
+
+extern "C" int hqs_adjoint_axpy(hqs_plan p, const hqs_c64* y, float c, const hqs_c64* z, hqs_c64* x,
+                                void* stream) {
+    if (!p || !x || !z || (!y && p->M > 0)) return HQS_ERR_INVALID_ARG;
+    return launch_adj_axpy(p, reinterpret_cast<const float2*>(y), c, reinterpret_cast<const float2*>(z),
+                           reinterpret_cast<float2*>(x), (cudaStream_t)stream);
 }

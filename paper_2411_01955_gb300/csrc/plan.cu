@@ -227,6 +227,16 @@ __global__ void k_real_scaled(const float2* __restrict__ in, float* __restrict__
     if (e < count) out[e] = in[e].x * scale;
 }
 
+// out[c][r] = Re in[r][c] * scale (Khat kept transposed so that a column of
+// the Toeplitz spectrum is contiguous for the column pass)
+__global__ void k_real_scaled_T(const float2* __restrict__ in, float* __restrict__ out, int nn,
+                                float scale) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nn * nn) return;
+    const int r = e / nn, c = e - r * nn;
+    out[(int64_t)c * nn + r] = in[e].x * scale;
+}
+
 // ------------------------------------------------------------- host side
 
 // Continuous transform of the KB kernel: W sinh(r)/r, r = sqrt(beta^2 - (pi W nu)^2).
@@ -269,6 +279,7 @@ static void plan_free(hqs_plan_s* p) {
     cudaGetDevice(&cur);
     if (cur != p->device) cudaSetDevice(p->device);
     for (void* v : p->allocs) cudaFree(v);
+    if (p->trace) cudaFree(p->trace);
     if (p->h_cg) cudaFreeHost(p->h_cg);
     if (p->h_hist) cudaFreeHost(p->h_hist);
     if (p->h_err) cudaFreeHost(p->h_err);
@@ -420,8 +431,8 @@ static int plan_build(hqs_plan_s* p, const float* traj, const float2* smaps_user
         }
         k_chan_column<<<ceil_div(n * n, 256), 256, 0, s>>>(cbuf, n, n2, chan);
         if ((rc = launch_fft2d(p, cbuf, n2, false, s)) != HQS_OK) break;
-        k_real_scaled<<<ceil_div(n2 * n2, 256), 256, 0, s>>>(cbuf, p->khat, n2 * n2,
-                                                             1.0f / ((float)n2 * (float)n2));
+        k_real_scaled_T<<<ceil_div(n2 * n2, 256), 256, 0, s>>>(cbuf, p->khat, n2,
+                                                               1.0f / ((float)n2 * (float)n2));
         if ((rc = launch_fft2d(p, chan, n, false, s)) != HQS_OK) break;
         k_real_scaled<<<ceil_div(n * n, 256), 256, 0, s>>>(chan, p->lam, n * n, 1.0f);
         if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {

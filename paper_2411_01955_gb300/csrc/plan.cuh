@@ -9,6 +9,7 @@
 #define HQS_MAX_LC 16          // coils per chunk in the FFT passes
 #define HQS_MAX_BLOCKS 2048    // partial-sum slots per reduction
 #define HQS_SPREAD_MAXPTS 256  // points per spreading sub-problem
+#define HQS_TRACE_MAX 4096     // phase-trace stamps kept per persistent solve
 
 // CG scalars kept on the device so that the solve never needs the host
 // between iterations.
@@ -44,6 +45,7 @@ struct hqs_plan_s {
     int tile = 16, nbx = 0, nsub = 0;
     int q_rows = 8;     // lines per CTA in the single-image FFT passes
     int fused_grid = 0; // cap on the persistent solver's CTAs (0: occupancy limit)
+    int pc_lines = 4;   // preconditioner lines per item in the persistent solver (1..16)
 
     // constant tables and plan data (device)
     float2* smaps = nullptr;    // [n][n][L]
@@ -51,7 +53,7 @@ struct hqs_plan_s {
     int4* pts = nullptr;        // sorted points: (i0x, i0y, bits(dx), bits(dy)), i0 in [0, G)
     int* perm = nullptr;        // sorted -> caller index
     int4* subs = nullptr;       // (bin, start, count, 0)
-    float* khat = nullptr;      // [n2][n2], includes 1/n2^2
+    float* khat = nullptr;      // [n2][n2] transposed (khat[kx][ky]), includes 1/n2^2
     float* lam = nullptr;       // [n][n] density symbol
     float2* tw = nullptr;       // twiddle bank
     int tw_sizes[4] = {0, 0, 0, 0};
@@ -79,7 +81,7 @@ struct hqs_plan_s {
     unsigned* h_err = nullptr;  // pinned mirror of dev_err
     unsigned* dev_err = nullptr;
     unsigned* barrier = nullptr; // grid barrier words for the persistent solve
-    float2* smaps_user = nullptr;
+    unsigned long long* trace = nullptr;  // optional phase trace of the persistent solve
 
     size_t bytes = 0;
     std::vector<void*> allocs;
@@ -90,6 +92,7 @@ const float2* plan_twiddles(const hqs_plan_s* p, int N);
 // launchers implemented in the kernel translation units
 int launch_fwd(hqs_plan_s* p, const float2* x, float2* y, cudaStream_t s);
 int launch_adj(hqs_plan_s* p, const float2* y, float2* x, cudaStream_t s);
+int launch_adj_axpy(hqs_plan_s* p, const float2* y, float zc, const float2* z, float2* x, cudaStream_t s);
 int launch_toeplitz(hqs_plan_s* p, const float2* x, float2* out, cudaStream_t s);
 int launch_fft2d(const hqs_plan_s* p, float2* data, int N, bool inverse, cudaStream_t s);
 int launch_precond(hqs_plan_s* p, float a, float b, const float2* r, float2* z, cudaStream_t s);

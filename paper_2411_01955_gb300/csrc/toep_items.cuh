@@ -51,13 +51,11 @@ HQS_DEV void toep_rows_fwd_item(const ToepArgs& A, int iy, int ch, const float2*
     constexpr int TPL = FftSize<N2>::TPL;
     if (lines == kLines) {   // full chunk: n = N2/2 and pst = TPL are compile-time
         unrolled<N2 / 2 / TPL, TPL>(p0, [&](int p) { s[p * kLines + l] = cmul(sm[(int64_t)p * L], rowv[p]); });
-        unrolled<N2 / 2 / TPL, TPL>(p0 + N2 / 2, [&](int p) { s[p * kLines + l] = make_float2(0.f, 0.f); });
     } else if (p0 < pst) {
         for (int p = p0; p < n; p += pst) s[p * kLines + l] = cmul(sm[(int64_t)p * L], rowv[p]);
-        for (int p = n + p0; p < N2; p += pst) s[p * kLines + l] = make_float2(0.f, 0.f);
     }
     __syncthreads();
-    block_fft<N2, false>(s, lines, tw);
+    block_fft<N2, false, true>(s, lines, tw);   // upper half is the zero padding
     float2* dst = A.T + (int64_t)iy * N2 * L + l0 + l;
     if (lines == kLines) {
         unrolled<N2 / TPL, TPL>(p0, [&](int p) { dst[(int64_t)p * L] = s[p * kLines + l]; });
@@ -80,25 +78,21 @@ HQS_DEV void toep_cols_item(const ToepArgs& A, int kx, int ch, float2* s) {
     const int64_t rs = (int64_t)N2 * L;
     constexpr int TPL = FftSize<N2>::TPL;
     const bool full = lines == kLines;
+    const float* kh = A.khat + (int64_t)kx * N2;   // Khat stored transposed: column kx contiguous
     if (full) {
         unrolled<N2 / 2 / TPL, TPL>(p0, [&](int p) { s[p * kLines + l] = __ldcg(col + p * rs); });
-        unrolled<N2 / 2 / TPL, TPL>(p0 + N2 / 2, [&](int p) { s[p * kLines + l] = make_float2(0.f, 0.f); });
     } else if (p0 < pst) {
         for (int p = p0; p < n; p += pst) s[p * kLines + l] = __ldcg(col + p * rs);
-        for (int p = n + p0; p < N2; p += pst) s[p * kLines + l] = make_float2(0.f, 0.f);
     }
     __syncthreads();
-    block_fft<N2, false>(s, lines, tw);
+    block_fft<N2, false, true>(s, lines, tw);   // zero-padded upper half
     if (full) {
-        unrolled<N2 / TPL, TPL>(p0, [&](int p) {
-            s[p * kLines + l] = cscale(s[p * kLines + l], __ldg(A.khat + (int64_t)p * N2 + kx));
-        });
+        unrolled<N2 / TPL, TPL>(p0, [&](int p) { s[p * kLines + l] = cscale(s[p * kLines + l], __ldg(kh + p)); });
     } else if (p0 < pst) {
-        for (int p = p0; p < N2; p += pst)
-            s[p * kLines + l] = cscale(s[p * kLines + l], __ldg(A.khat + (int64_t)p * N2 + kx));
+        for (int p = p0; p < N2; p += pst) s[p * kLines + l] = cscale(s[p * kLines + l], __ldg(kh + p));
     }
     __syncthreads();
-    block_fft<N2, true>(s, lines, tw);
+    block_fft<N2, true, false, true>(s, lines, tw);   // only the first n rows are kept
     if (full) {
         unrolled<N2 / 2 / TPL, TPL>(p0, [&](int p) { col[p * rs] = s[p * kLines + l]; });
     } else if (p0 < pst) {
@@ -140,17 +134,31 @@ HQS_DEV double toep_rows_adj_item(const ToepArgs& A, int iy, int ch, float2* __r
         for (int p = p0; p < N2; p += pst) s[p * kLines + l] = __ldcg(src + (int64_t)p * L);
     }
     __syncthreads();
-    block_fft<N2, true>(s, lines, tw);
+    block_fft<N2, true, false, true>(s, lines, tw);   // only the first n columns are kept
     const float2* sm = A.smaps + (int64_t)iy * n * L + l0;
     double part = 0.0;
     for (int ix = threadIdx.x; ix < n; ix += blockDim.x) {
         float2 acc = make_float2(0.f, 0.f);
         const float2* smx = sm + (int64_t)ix * L;
-        for (int ll = 0; ll < lines; ++ll) {
-            const float2 sv = smx[ll];
-            const float2 g = s[ix * kLines + ll];
-            acc.x += sv.x * g.x + sv.y * g.y;
-            acc.y += sv.x * g.y - sv.y * g.x;
+        if (lines == kLines) {
+            // a full chunk of 16 coils is 128 contiguous, 16-byte aligned bytes
+            const float4* s4 = reinterpret_cast<const float4*>(smx);
+            float4 sv4[kLines / 2];
+#pragma unroll
+            for (int h = 0; h < kLines / 2; ++h) sv4[h] = __ldg(s4 + h);
+#pragma unroll
+            for (int h = 0; h < kLines / 2; ++h) {
+                const float2 g0 = s[ix * kLines + 2 * h], g1 = s[ix * kLines + 2 * h + 1];
+                acc.x += sv4[h].x * g0.x + sv4[h].y * g0.y + sv4[h].z * g1.x + sv4[h].w * g1.y;
+                acc.y += sv4[h].x * g0.y - sv4[h].y * g0.x + sv4[h].z * g1.y - sv4[h].w * g1.x;
+            }
+        } else {
+            for (int ll = 0; ll < lines; ++ll) {
+                const float2 sv = smx[ll];
+                const float2 g = s[ix * kLines + ll];
+                acc.x += sv.x * g.x + sv.y * g.y;
+                acc.y += sv.x * g.y - sv.y * g.x;
+            }
         }
         const int64_t e = (int64_t)iy * n + ix;
         if (A.nchunk == 1)

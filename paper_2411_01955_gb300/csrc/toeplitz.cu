@@ -87,15 +87,18 @@ __global__ void k_cg_pupdate(const float2* __restrict__ z, float2* __restrict__ 
     }
 }
 
-// r = rhs - q; partials ||r||^2 and ||rhs||^2
+// r = rhs - q (q == nullptr: the start is x = 0, written here, and r = rhs);
+// partials ||r||^2 and ||rhs||^2
 __global__ void k_cg_init_r(const float2* __restrict__ rhs, const float2* __restrict__ q,
-                            float2* __restrict__ r, int count, double* __restrict__ part_rr,
-                            double* __restrict__ part_bb) {
+                            float2* __restrict__ r, float2* __restrict__ x, int count,
+                            double* __restrict__ part_rr, double* __restrict__ part_bb) {
     __shared__ double red[32];
     double rr = 0.0, bb = 0.0;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x) {
         const float2 b = rhs[e];
-        const float2 v = csub(b, q[e]);
+        float2 v = b;
+        if (q) v = csub(b, q[e]);
+        else x[e] = make_float2(0.f, 0.f);
         r[e] = v;
         rr += (double)v.x * v.x + (double)v.y * v.y;
         bb += (double)b.x * b.x + (double)b.y * b.y;
@@ -304,7 +307,7 @@ extern "C" int hqs_toeplitz_normal(hqs_plan p, const hqs_c64* x, hqs_c64* out, i
 // ------------------------------------------------------- plain PCG driver
 // One launch per stage; the host reads the stop flag after every iteration.
 int pcg_plain(hqs_plan_s* p, float a, float b, const float2* rhs, float2* x, int max_iter,
-              double rel_tol, int precond, cudaStream_t st) {
+              double rel_tol, int precond, bool x0_zero, cudaStream_t st) {
     const int n = p->n, count = n * n;
     const int nb_vec = std::min(ceil_div(count, 256), HQS_MAX_BLOCKS);
     double* part = p->partials;
@@ -318,9 +321,10 @@ int pcg_plain(hqs_plan_s* p, float a, float b, const float2* rhs, float2* x, int
     const float2* zsrc = dc ? p->cg_z : p->cg_r;
 
     k_cg_setup<<<1, 1, 0, st>>>(p->cg, max_iter, rel_tol);
-    // q = H x
-    HQS_TRY_RC(launch_toeplitz_ex(p, x, nullptr, 0, p->cg_q, x, a, b, 1, nullptr, nullptr, st));
-    k_cg_init_r<<<nb_vec, 256, 0, st>>>(rhs, p->cg_q, p->cg_r, count, P_RR, P_BB);
+    // q = H x (skipped for a zero start)
+    if (!x0_zero)
+        HQS_TRY_RC(launch_toeplitz_ex(p, x, nullptr, 0, p->cg_q, x, a, b, 1, nullptr, nullptr, st));
+    k_cg_init_r<<<nb_vec, 256, 0, st>>>(rhs, x0_zero ? nullptr : p->cg_q, p->cg_r, x, count, P_RR, P_BB);
     k_cg_scalar<<<1, 256, 0, st>>>(p->cg, part, CG_INIT, nb_vec, rz_scale, 0, p->hist);
     if (dc) HQS_TRY_RC(launch_precond_ex(p, a, b, p->cg_r, p->cg_z, false, p->cg, P_RZ, st));
     k_cg_scalar<<<1, 256, 0, st>>>(p->cg, part, CG_BETA0, dc ? nb_pc : nb_vec, rz_scale, dc ? 1 : 0, p->hist);
@@ -379,6 +383,8 @@ extern "C" int hqs_dc_solve(hqs_plan p, float a, float b, const hqs_c64* rhs, hq
         return HQS_ERR_INVALID_ARG;
     if (precond != HQS_PRECOND_NONE && precond != HQS_PRECOND_DC && precond != HQS_PRECOND_LEARNED)
         return HQS_ERR_INVALID_ARG;
+    const bool x0_zero = (mode & HQS_SOLVE_X0_ZERO) != 0;
+    mode &= ~HQS_SOLVE_X0_ZERO;
     if (mode != HQS_SOLVE_PLAIN && mode != HQS_SOLVE_FUSED) return HQS_ERR_INVALID_ARG;
     if (precision != HQS_PREC_FP32 && precision != HQS_PREC_BF16X3 && precision != HQS_PREC_FP16X3)
         return HQS_ERR_INVALID_ARG;
@@ -389,9 +395,9 @@ extern "C" int hqs_dc_solve(hqs_plan p, float a, float b, const hqs_c64* rhs, hq
     if (precond == HQS_PRECOND_LEARNED) {
         rc = fcg_learned(p, a, b, r, xx, max_iter, rel_tol, precision, st);
     } else if (mode == HQS_SOLVE_FUSED || precision != HQS_PREC_FP32) {
-        rc = pcg_fused(p, a, b, r, xx, max_iter, rel_tol, precond, precision, st);
+        rc = pcg_fused(p, a, b, r, xx, max_iter, rel_tol, precond, precision, x0_zero, st);
     } else {
-        rc = pcg_plain(p, a, b, r, xx, max_iter, rel_tol, precond, st);
+        rc = pcg_plain(p, a, b, r, xx, max_iter, rel_tol, precond, x0_zero, st);
     }
     if (rc != HQS_OK) return rc;
     if (info) return read_solve_info(p, info, st);

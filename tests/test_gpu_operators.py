@@ -62,6 +62,29 @@ def test_adjoint_matches_oracle(case):
         assert rel(got, nudft.adjoint(yv, case["smaps"], case["traj"])) <= 2e-3
 
 
+def test_adjoint_axpy_and_zero_start(case):
+    plan, _, _ = make_plan(case)
+    n = case["n"]
+    yv = case["noise"].astype(np.complex64).astype(np.complex128)
+    z = case["x"]
+    x = torch.empty((n, n), dtype=torch.complex64, device="cuda")
+    hq().adjoint_axpy(plan, to_dev(yv), 0.3, to_dev(z), x)
+    want = nufft.adjoint(yv, case["smaps"], case["traj"], case["W"], case["sigma"]) + 0.3 * z
+    assert rel(to_host(x), want) <= TOL
+    zz = to_dev(z)                        # in place: z and x the same buffer
+    hq().adjoint_axpy(plan, to_dev(yv), 0.3, zz, zz)
+    assert rel(to_host(zz), want) <= TOL
+    # zero start ignores the incoming x and matches a solve from zeros
+    for mode in (0, 1):
+        a = to_dev(np.full((n, n), 7.0 + 1j))
+        b = torch.zeros_like(a)
+        ia = hq().dc_solve(plan, 1.0, 1e-2, x, a, max_iter=6, rel_tol=0.0,
+                           mode=mode | hq().HQS_SOLVE_X0_ZERO)
+        ib = hq().dc_solve(plan, 1.0, 1e-2, x, b, max_iter=6, rel_tol=0.0, mode=mode)
+        assert ia.iterations == ib.iterations == 6
+        assert rel(to_host(a), to_host(b)) <= 1e-6
+
+
 def test_gpu_operator_pair_is_adjoint(case):
     plan, _, _ = make_plan(case)
     rng = np.random.default_rng(3)
