@@ -155,6 +155,28 @@ HQS_API int hqs_toeplitz_normal(hqs_plan plan, const hqs_c64* x, hqs_c64* out,
 HQS_API int hqs_precond_apply(hqs_plan plan, float a, float b, const hqs_c64* r,
                       hqs_c64* z, void* stream);
 
+/* Allocation-free preconditioner apply.  The paper has no counterpart: this
+ * entry point exists for callers that may not allocate device memory, such
+ * as a reconstruction service that reserves all GPU memory at start-up and
+ * forbids allocation on its serving path, or a host framework whose memory
+ * pool owns the device.  It needs no plan (a plan allocates tens of MB of
+ * workspace) and calls no cudaMalloc/cudaFree or allocating routine: its
+ * scratch (the n x n spectrum, 1.125 MiB at the maximum) and twiddle tables
+ * are file-scope device arrays that every GPU loading this library holds
+ * until the process exits.
+ *   z = IFFT_N(FFT_N(r) * s^-1/2), s = max(a*max(lam,0) + b, b/4), as
+ *   hqs_precond_apply, with the density symbol lam given by the caller.
+ *   r, z: (n, n) complex device; lam: (n, n) float device; b > 0;
+ *   n in {16, 32, 64, 128, 256, 320, 384}: larger n returns HQS_ERR_INVALID_ARG.
+ * The first call on a device sets up (looks up the arrays' device addresses,
+ * fills the twiddle tables and synchronises `stream` once); make that first
+ * call before any stream capture.  All calls on a device share the scratch
+ * array and it keeps the last call's contents: calls that overlap on the GPU
+ * (for instance on two streams) race on it.  Nothing in it needs to start at
+ * zero: the row pass overwrites the whole n x n region before it is read. */
+HQS_API int hqs_precond_apply_noalloc(const hqs_c64* r, const float* lam, int n, float a, float b,
+                                      hqs_c64* z, void* stream);
+
 /* --------------------------------------------------- DC solve (a5, a7) */
 /* Solves (a A^H A + b I) x = rhs by preconditioned CG with fp64 inner
  * products: the P-metric proximal step of Sec. 3.4 ("subiteration solver").

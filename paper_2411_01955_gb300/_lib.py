@@ -81,6 +81,8 @@ _SIGS = {
     "hqs_power_iteration": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_void_p]),
     "hqs_status_string": (C.c_char_p, [C.c_int]),
     "hqs_plan_set_tuning": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "hqs_precond_apply_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_float, C.c_float,
+                                            C.c_void_p, C.c_void_p]),
     "hqs_debug_phase_trace": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_ulonglong), C.c_int,
                                         C.c_void_p]),
 }
@@ -304,3 +306,14 @@ def debug_phase_trace(plan: Plan, enable=False, stream=None):
 
 def plan_set_tuning(plan: Plan, key: int, value: int):
     _check(library().hqs_plan_set_tuning(plan.handle, int(key), int(value)), "hqs_plan_set_tuning")
+
+
+def precond_apply_noalloc(r, lam, a, b, z, stream=None):
+    """Preconditioner apply without any device allocation (no plan): scratch
+    lives in a static device array, n <= 384; the density symbol lam is given."""
+    n = int(r.shape[-1])
+    _check(library().hqs_precond_apply_noalloc(_ptr(r, torch.complex64, "r"),
+                                               _ptr(lam, torch.float32, "lam"), n, float(a),
+                                               float(b), _ptr(z, torch.complex64, "z"),
+                                               _stream(stream)), "hqs_precond_apply_noalloc")
+    return z

@@ -223,3 +223,120 @@ extern "C" int hqs_precond_apply(hqs_plan p, float a, float b, const hqs_c64* r,
     return launch_precond(p, a, b, reinterpret_cast<const float2*>(r), reinterpret_cast<float2*>(z),
                           (cudaStream_t)stream);
 }
+
+// ------------------------------------------------ allocation-free variant
+// hqs_precond_apply_noalloc: the density-compensation preconditioner apply
+// for callers that must not allocate device memory.  Its scratch (the n x n
+// spectrum between the row and column passes) and its twiddle tables are
+// file-scope device arrays sized for n <= HQS_NOALLOC_MAX_N; every GPU that
+// loads this library holds them until the process exits.
+#include <mutex>
+
+#define HQS_NOALLOC_MAX_N 384
+#define HQS_NOALLOC_MAX_DEVICES 64
+#define HQS_NOALLOC_TW_TOTAL 1200   // 16 + 32 + 64 + 128 + 256 + 320 + 384
+
+static __device__ __align__(256) float2 g_noalloc_spectrum[HQS_NOALLOC_MAX_N * HQS_NOALLOC_MAX_N];
+static __device__ __align__(256) float2 g_noalloc_twiddles[HQS_NOALLOC_TW_TOTAL];
+
+static const int kNoallocSizes[7] = {16, 32, 64, 128, 256, 320, 384};
+
+static int noalloc_tw_offset(int n) {
+    int off = 0;
+    for (int s : kNoallocSizes) {
+        if (s == n) return off;
+        off += s;
+    }
+    return -1;
+}
+
+// exp(-2 pi i m / N) for every supported N, in double precision, rounded to float
+__global__ void k_noalloc_twiddles(float2* tw) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= HQS_NOALLOC_TW_TOTAL) return;
+    int off = 0;
+    const int sizes[7] = {16, 32, 64, 128, 256, 320, 384};
+    for (int i = 0; i < 7; ++i) {
+        if (e < off + sizes[i]) {
+            double sn, cs;
+            sincospi(-2.0 * (double)(e - off) / (double)sizes[i], &sn, &cs);
+            tw[e] = make_float2((float)cs, (float)sn);
+            return;
+        }
+        off += sizes[i];
+    }
+}
+
+struct NoallocDevice {
+    bool ready = false;
+    float2* spectrum = nullptr;   // device address of g_noalloc_spectrum
+    float2* twiddles = nullptr;   // device address of g_noalloc_twiddles
+};
+static std::mutex g_noalloc_mu;
+static NoallocDevice g_noalloc_dev[HQS_NOALLOC_MAX_DEVICES];
+
+// Once per device, with that device current: resolve the arrays' device
+// addresses (their names are only host stand-ins in host code) and fill the
+// twiddle tables; the caller's stream is synchronised once so that later
+// calls on any stream see the tables.
+static int noalloc_setup(int dev, cudaStream_t st, NoallocDevice** out) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    NoallocDevice& d = g_noalloc_dev[dev];
+    if (!d.ready) {
+        void* spec = nullptr;
+        void* tw = nullptr;
+        HQS_CUDA_TRY(cudaGetSymbolAddress(&spec, g_noalloc_spectrum));
+        HQS_CUDA_TRY(cudaGetSymbolAddress(&tw, g_noalloc_twiddles));
+        k_noalloc_twiddles<<<ceil_div(HQS_NOALLOC_TW_TOTAL, 256), 256, 0, st>>>(static_cast<float2*>(tw));
+        HQS_CUDA_TRY(cudaGetLastError());
+        HQS_CUDA_TRY(cudaStreamSynchronize(st));
+        d.spectrum = static_cast<float2*>(spec);
+        d.twiddles = static_cast<float2*>(tw);
+        d.ready = true;
+    }
+    *out = &d;
+    return HQS_OK;
+}
+
+template <int N>
+static int precond_noalloc_impl(const NoallocDevice& d, float a, float b, const float2* r, const float* lam,
+                                float2* z, cudaStream_t st) {
+    const float2* tw = d.twiddles + noalloc_tw_offset(N);
+    const int Q = kLines;
+    const int th = fft_threads<N>(Q);
+    const size_t sm = (size_t)(N * kLines + N) * sizeof(float2);
+    const int nb = ceil_div(N, Q);
+    HQS_CUDA_TRY(cudaFuncSetAttribute(k_pc_rows_fwd<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    HQS_CUDA_TRY(cudaFuncSetAttribute(k_pc_cols<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    HQS_CUDA_TRY(cudaFuncSetAttribute(k_pc_rows_inv<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_pc_rows_fwd<N><<<nb, th, sm, st>>>(r, d.spectrum, Q, tw, nullptr);
+    k_pc_cols<N><<<nb, th, sm, st>>>(d.spectrum, Q, lam, a, b, tw, nullptr, nullptr);
+    k_pc_rows_inv<N><<<nb, th, sm, st>>>(d.spectrum, z, Q, tw, nullptr);
+    HQS_CUDA_TRY(cudaGetLastError());
+    return HQS_OK;
+}
+
+extern "C" int hqs_precond_apply_noalloc(const hqs_c64* r, const float* lam, int n, float a, float b,
+                                         hqs_c64* z, void* stream) {
+    if (!r || !lam || !z || !(b > 0.f) || !(a == a)) return HQS_ERR_INVALID_ARG;
+    if (n > HQS_NOALLOC_MAX_N || noalloc_tw_offset(n) < 0) return HQS_ERR_INVALID_ARG;
+    int dev = 0;
+    HQS_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= HQS_NOALLOC_MAX_DEVICES) return HQS_ERR_UNSUPPORTED;
+    cudaStream_t st = (cudaStream_t)stream;
+    NoallocDevice* d = nullptr;
+    const int rc = noalloc_setup(dev, st, &d);
+    if (rc != HQS_OK) return rc;
+    const float2* rr = reinterpret_cast<const float2*>(r);
+    float2* zz = reinterpret_cast<float2*>(z);
+    switch (n) {
+        case 16: return precond_noalloc_impl<16>(*d, a, b, rr, lam, zz, st);
+        case 32: return precond_noalloc_impl<32>(*d, a, b, rr, lam, zz, st);
+        case 64: return precond_noalloc_impl<64>(*d, a, b, rr, lam, zz, st);
+        case 128: return precond_noalloc_impl<128>(*d, a, b, rr, lam, zz, st);
+        case 256: return precond_noalloc_impl<256>(*d, a, b, rr, lam, zz, st);
+        case 320: return precond_noalloc_impl<320>(*d, a, b, rr, lam, zz, st);
+        case 384: return precond_noalloc_impl<384>(*d, a, b, rr, lam, zz, st);
+        default: return HQS_ERR_INVALID_ARG;
+    }
+}
