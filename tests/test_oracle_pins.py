@@ -392,3 +392,81 @@ def test_density_preconditioner_cuts_iterations_on_vd_spiral():
     _, i_dc = solvers.pcg(H, b0, np.zeros((n, n)),
                           lambda v: toeplitz.precond_apply(v, lam, 1.0, mu), 300, 1e-4)
     assert i_dc["iters"] < 0.8 * i_plain["iters"]
+
+
+# ---------------------------------------------------------------- conv net
+from oracle import convnet
+
+
+def small_net(seed=0, layers=((2, 3), (3, 2))):
+    rng = np.random.default_rng(seed)
+    return [(rng.normal(size=(co, ci, 3, 3)), rng.normal(size=co)) for ci, co in layers]
+
+
+def test_conv3x3_matches_brute_force():
+    rng = np.random.default_rng(20)
+    x = rng.normal(size=(2, 3, 5, 4))
+    W = rng.normal(size=(2, 3, 3, 3))
+    b = rng.normal(size=2)
+    out = convnet.conv3x3(x, W, b)
+    ref = np.zeros_like(out)
+    for n in range(2):
+        for o in range(2):
+            for y in range(5):
+                for xx in range(4):
+                    acc = b[o]
+                    for i in range(3):
+                        for dy in range(3):
+                            for dx in range(3):
+                                yy, xc = y + dy - 1, xx + dx - 1
+                                if 0 <= yy < 5 and 0 <= xc < 4:
+                                    acc += W[o, i, dy, dx] * x[n, i, yy, xc]
+                    ref[n, o, y, xx] = acc
+    assert np.max(np.abs(out - ref)) < 1e-12
+
+
+def test_conv3x3_single_channel_equals_library_correlation():
+    signal = pytest.importorskip("scipy.signal")
+    rng = np.random.default_rng(21)
+    x = rng.normal(size=(1, 1, 9, 7))
+    W = rng.normal(size=(1, 1, 3, 3))
+    out = convnet.conv3x3(x, W, np.zeros(1))[0, 0]
+    ref = signal.correlate2d(x[0, 0], W[0, 0], mode="same", boundary="fill")
+    assert np.max(np.abs(out - ref)) < 1e-12
+
+
+def test_convnet_gradient_matches_finite_differences():
+    rng = np.random.default_rng(22)
+    params = small_net(1, layers=((2, 4), (4, 4), (4, 2)))
+    x = rng.normal(size=(3, 2, 6, 5))
+    t = rng.normal(size=(3, 2, 6, 5))
+    loss, grads = convnet.loss_and_grad(params, x, t)
+    g = np.concatenate([np.concatenate([dW.ravel(), db.ravel()]) for dW, db in grads])
+    layers = [(p[0].shape[1], p[0].shape[0]) for p in params]
+    vec = convnet.flatten(params)
+    h = 1e-6
+    for k in rng.choice(vec.size, size=25, replace=False):
+        vp, vm = vec.copy(), vec.copy()
+        vp[k] += h
+        vm[k] -= h
+        lp, _ = convnet.loss_and_grad(convnet.unflatten(vp, layers), x, t)
+        lm, _ = convnet.loss_and_grad(convnet.unflatten(vm, layers), x, t)
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - g[k]) <= 1e-7 * max(1.0, abs(fd)), (k, fd, g[k])
+
+
+def test_adam_first_step_closed_form():
+    # after one step from m = v = 0: update = lr * g / (|g| + eps) elementwise
+    g = np.array([0.5, -2.0, 1e-3])
+    p, m, v = convnet.adam_step(np.zeros(3), g, np.zeros(3), np.zeros(3), 1, 0.1)
+    assert np.allclose(p, -0.1 * g / (np.abs(g) + 1e-8), rtol=1e-12)
+
+
+def test_learned_preconditioner_starts_as_dc_preconditioner():
+    # zero last layer: the learned preconditioner reduces to the DC one
+    P = small_problem(23)
+    params = convnet.init_params(0)
+    assert convnet.num_params() == 19682
+    r = P["b0"]
+    z = convnet.learned_precond(r, P["lam"], 1.0, 0.05, params)
+    assert rel(z, toeplitz.precond_apply(r, P["lam"], 1.0, 0.05)) < 1e-15
