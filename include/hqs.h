@@ -68,6 +68,7 @@ extern "C" {
 #define HQS_MAX_ITERS 512
 
 typedef struct hqs_plan_s* hqs_plan;
+typedef struct hqs_net_s* hqs_net;
 typedef struct { float re, im; } hqs_c64;
 
 typedef struct {
@@ -194,6 +195,41 @@ HQS_API int hqs_dc_solve(hqs_plan plan, float a, float b, const hqs_c64* rhs, hq
                  hqs_solve_info* info, void* stream);
 /* Synchronises `stream` and reports the last solve enqueued on this plan. */
 HQS_API int hqs_last_solve_info(hqs_plan plan, hqs_solve_info* info, void* stream);
+
+/* ------------------------------------- learned preconditioner (a10) */
+/* A 4-layer 3x3 convolutional network (2 -> 32 -> 32 -> 32 -> 2 channels,
+ * ReLU, 19,682 float parameters; no counterpart in the paper, whose networks
+ * are its denoisers) used as a nonlinear CG preconditioner:
+ *   z = zdc + s * net(zdc / s),  zdc = M_DC^-1 r (hqs_precond_apply),
+ *   s = root-mean-square of zdc, channels = (Re, Im).
+ * With a zero last layer it equals the DC preconditioner.  Activations are
+ * planar float [N][C][H][W] device arrays; the parameter vector is
+ * [W1 b1 W2 b2 W3 b3 W4 b4], W[out][in][3][3] (cross-correlation, one pixel
+ * of zero padding).  Training minimises the mean over samples of
+ * ||net(x_n) - t_n||^2 / ||t_n||^2 with Adam (0.9, 0.999, 1e-8). */
+HQS_API int hqs_net_create(hqs_net* out);                  /* parameters zero */
+HQS_API void hqs_net_destroy(hqs_net net);
+HQS_API int hqs_net_num_params(void);
+HQS_API int hqs_net_set_params(hqs_net net, const float* host, int count);  /* resets Adam */
+HQS_API int hqs_net_get_params(hqs_net net, float* host, int count);
+HQS_API int hqs_net_forward(hqs_net net, const float* x, float* y, int N, int H, int W, void* stream);
+/* loss (host, blocking) and gradient (device, num_params floats; may be NULL) */
+HQS_API int hqs_net_gradient(hqs_net net, const float* x, const float* target, int N, int H, int W,
+                             float* grad, double* loss, void* stream);
+/* one Adam step on a batch; loss before the step (host, blocking) */
+HQS_API int hqs_net_train_step(hqs_net net, const float* x, const float* target, int N, int H, int W,
+                               float lr, double* loss, void* stream);
+HQS_API int hqs_net_save(hqs_net net, const char* path);
+HQS_API int hqs_net_load(hqs_net net, const char* path);
+/* attach (or detach with NULL) the network used by HQS_PRECOND_LEARNED; the
+ * plan does not own it.  The solve is Notay's flexible CG (alpha =
+ * <p,r>/<p,Hp>, Polak-Ribiere beta); when Re<z, r> <= 0 or ||r|| fails to
+ * drop 10% over 5 iterations it restarts as DC-preconditioned CG from the
+ * current iterate (info->fallback = 1). */
+HQS_API int hqs_plan_set_net(hqs_plan plan, hqs_net net);
+/* z = learned preconditioner applied to r (n x n complex device arrays). */
+HQS_API int hqs_learned_precond_apply(hqs_plan plan, float a, float b, const hqs_c64* r, hqs_c64* z,
+                                      void* stream);
 
 /* ------------------------------------------------ HQS outer loop (a6) */
 /* Annealed PnP-HQS (Sec. 3.3): for k = k0..K-1

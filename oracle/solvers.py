@@ -67,14 +67,18 @@ def pcg(apply_H, rhs, x0, apply_Minv=None, max_iter=30, tol=0.0):
 
 
 def fcg(apply_H, rhs, x0, apply_B, apply_Minv=None, max_iter=100, tol=1e-4,
-        stall_window=3, stall_factor=0.9):
+        stall_window=5, stall_factor=0.9):
     """Flexible CG with a (possibly nonlinear) preconditioner B and fallback.
 
-    beta_k = Re<z_{k+1}, r_{k+1} - r_k> / Re<z_k, r_k> (Polak-Ribiere form of
-    Notay's truncated FCG).  If Re<z, r> <= 0, or the residual has not dropped
-    by the factor stall_factor over the last stall_window iterations, the
-    method restarts as plain PCG with apply_Minv from the current iterate for
-    the remaining iterations.  Returns (x, info) with info['fallback'].
+    Notay's truncated flexible CG (one direction kept): alpha_k =
+    Re<p_k, r_k> / Re<p_k, H p_k> (exact line search along p_k, which keeps
+    r_{k+1} orthogonal to p_k whatever B is), beta_k = Re<z_{k+1}, r_{k+1} -
+    r_k> / Re<z_k, r_k> (Polak-Ribiere form), p_{k+1} = z_{k+1} + beta_k p_k.
+    If Re<z, r> <= 0, Re<p, Hp> <= 0, or ||r|| has not dropped by the factor
+    stall_factor over the last stall_window iterations (CG residual norms are
+    not monotone, so the window is several iterations), the method restarts
+    as plain PCG with apply_Minv from the current iterate for the remaining
+    iterations.  Returns (x, info) with info['fallback'].
     """
     rhs = np.asarray(rhs, dtype=np.complex128)
     x = np.array(x0, dtype=np.complex128, copy=True)
@@ -97,7 +101,7 @@ def fcg(apply_H, rhs, x0, apply_B, apply_Minv=None, max_iter=100, tol=1e-4,
             if not pq > 0.0:
                 fallback = True
                 break
-            alpha = rz / pq
+            alpha = vdot_re(p, r) / pq
             x = x + alpha * p
             r_old = r
             r = r - alpha * q
@@ -105,10 +109,10 @@ def fcg(apply_H, rhs, x0, apply_B, apply_Minv=None, max_iter=100, tol=1e-4,
             hist.append(float(np.linalg.norm(r)) / bnorm)
             if hist[-1] <= tol:
                 return x, dict(iters=it, res_hist=hist, status="ok", fallback=False)
+            if it == max_iter:
+                break
             if it >= stall_window and hist[-1] > stall_factor * hist[-1 - stall_window]:
                 fallback = True
-                break
-            if it == max_iter:
                 break
             z = apply_B(r)
             rz_new = vdot_re(r, z)

@@ -81,6 +81,22 @@ _SIGS = {
     "hqs_power_iteration": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_void_p]),
     "hqs_status_string": (C.c_char_p, [C.c_int]),
     "hqs_plan_set_tuning": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "hqs_net_create": (C.c_int, [C.POINTER(C.c_void_p)]),
+    "hqs_net_destroy": (None, [C.c_void_p]),
+    "hqs_net_num_params": (C.c_int, []),
+    "hqs_net_set_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "hqs_net_get_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "hqs_net_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,
+                                  C.c_void_p]),
+    "hqs_net_gradient": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,
+                                   C.c_void_p, C.POINTER(C.c_double), C.c_void_p]),
+    "hqs_net_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,
+                                     C.c_float, C.POINTER(C.c_double), C.c_void_p]),
+    "hqs_net_save": (C.c_int, [C.c_void_p, C.c_char_p]),
+    "hqs_net_load": (C.c_int, [C.c_void_p, C.c_char_p]),
+    "hqs_plan_set_net": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "hqs_learned_precond_apply": (C.c_int, [C.c_void_p, C.c_float, C.c_float, C.c_void_p,
+                                            C.c_void_p, C.c_void_p]),
     "hqs_precond_apply_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_float, C.c_float,
                                             C.c_void_p, C.c_void_p]),
     "hqs_debug_phase_trace": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_ulonglong), C.c_int,
@@ -316,4 +332,85 @@ def precond_apply_noalloc(r, lam, a, b, z, stream=None):
                                                _ptr(lam, torch.float32, "lam"), n, float(a),
                                                float(b), _ptr(z, torch.complex64, "z"),
                                                _stream(stream)), "hqs_precond_apply_noalloc")
+    return z
+
+
+class Net:
+    """The conv-net preconditioner (hqs_net_*); activations are planar float
+    CUDA tensors (N, 2, H, W)."""
+
+    def __init__(self):
+        h = C.c_void_p()
+        _check(library().hqs_net_create(C.byref(h)), "hqs_net_create")
+        self.handle = h
+        self.num_params = library().hqs_net_num_params()
+
+    def set_params(self, vec):
+        import numpy as np
+        v = np.ascontiguousarray(np.asarray(vec, dtype=np.float32))
+        _check(library().hqs_net_set_params(self.handle, v.ctypes.data_as(C.c_void_p), v.size),
+               "hqs_net_set_params")
+
+    def get_params(self):
+        import numpy as np
+        v = np.empty(self.num_params, dtype=np.float32)
+        _check(library().hqs_net_get_params(self.handle, v.ctypes.data_as(C.c_void_p), v.size),
+               "hqs_net_get_params")
+        return v
+
+    def forward(self, x, y=None, stream=None):
+        y = torch.empty_like(x) if y is None else y
+        N, _, H, W = x.shape
+        _check(library().hqs_net_forward(self.handle, _ptr(x, torch.float32, "x"),
+                                         _ptr(y, torch.float32, "y"), N, H, W, _stream(stream)),
+               "hqs_net_forward")
+        return y
+
+    def gradient(self, x, t, stream=None):
+        g = torch.empty(self.num_params, dtype=torch.float32, device=x.device)
+        loss = C.c_double()
+        N, _, H, W = x.shape
+        _check(library().hqs_net_gradient(self.handle, _ptr(x, torch.float32, "x"),
+                                          _ptr(t, torch.float32, "t"), N, H, W,
+                                          _ptr(g, torch.float32, "grad"), C.byref(loss),
+                                          _stream(stream)), "hqs_net_gradient")
+        return g, loss.value
+
+    def train_step(self, x, t, lr, stream=None):
+        loss = C.c_double()
+        N, _, H, W = x.shape
+        _check(library().hqs_net_train_step(self.handle, _ptr(x, torch.float32, "x"),
+                                            _ptr(t, torch.float32, "t"), N, H, W, float(lr),
+                                            C.byref(loss), _stream(stream)), "hqs_net_train_step")
+        return loss.value
+
+    def save(self, path):
+        _check(library().hqs_net_save(self.handle, str(path).encode()), "hqs_net_save")
+
+    def load(self, path):
+        _check(library().hqs_net_load(self.handle, str(path).encode()), "hqs_net_load")
+
+    def close(self):
+        if self.handle:
+            library().hqs_net_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def plan_set_net(plan: Plan, net):
+    _check(library().hqs_plan_set_net(plan.handle, net.handle if net is not None else None),
+           "hqs_plan_set_net")
+    plan._net = net
+
+
+def learned_precond_apply(plan: Plan, a, b, r, z, stream=None):
+    _check(library().hqs_learned_precond_apply(plan.handle, float(a), float(b),
+                                               _ptr(r, torch.complex64, "r"),
+                                               _ptr(z, torch.complex64, "z"), _stream(stream)),
+           "hqs_learned_precond_apply")
     return z

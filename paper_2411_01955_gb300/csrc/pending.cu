@@ -3,10 +3,6 @@
 // falling back to another path.
 #include "solve.cuh"
 
-int fcg_learned(hqs_plan_s*, float, float, const float2*, float2*, int, double, int, cudaStream_t) {
-    return HQS_ERR_UNSUPPORTED;
-}
-
 int launch_toeplitz_mixed(hqs_plan_s*, const float2*, float2*, int, cudaStream_t) {
     return HQS_ERR_UNSUPPORTED;
 }

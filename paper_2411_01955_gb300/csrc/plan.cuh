@@ -7,7 +7,7 @@
 
 #define HQS_MAX_W 8
 #define HQS_MAX_LC 16          // coils per chunk in the FFT passes
-#define HQS_MAX_BLOCKS 2048    // partial-sum slots per reduction
+#define HQS_MAX_BLOCKS 2048    // partial-sum slots per reduction (and >= 3 x 256 for the FCG dots)
 #define HQS_SPREAD_MAXPTS 256  // points per spreading sub-problem
 #define HQS_TRACE_MAX 4096     // phase-trace stamps kept per persistent solve
 
@@ -82,6 +82,7 @@ struct hqs_plan_s {
     unsigned* dev_err = nullptr;
     unsigned* barrier = nullptr; // grid barrier words for the persistent solve
     unsigned long long* trace = nullptr;  // optional phase trace of the persistent solve
+    struct hqs_net_s* net = nullptr;      // learned preconditioner (not owned)
 
     size_t bytes = 0;
     std::vector<void*> allocs;

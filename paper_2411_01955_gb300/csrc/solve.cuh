@@ -36,5 +36,5 @@ int pcg_plain(hqs_plan_s* p, float a, float b, const float2* rhs, float2* x, int
 int pcg_fused(hqs_plan_s* p, float a, float b, const float2* rhs, float2* x, int max_iter,
               double rel_tol, int precond, int precision, bool x0_zero, cudaStream_t st);
 int fcg_learned(hqs_plan_s* p, float a, float b, const float2* rhs, float2* x, int max_iter,
-                double rel_tol, int precision, cudaStream_t st);
+                double rel_tol, bool x0_zero, cudaStream_t st);
 int read_solve_info(hqs_plan_s* p, hqs_solve_info* info, cudaStream_t st);

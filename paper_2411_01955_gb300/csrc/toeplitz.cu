@@ -393,7 +393,8 @@ extern "C" int hqs_dc_solve(hqs_plan p, float a, float b, const hqs_c64* rhs, hq
     float2* xx = reinterpret_cast<float2*>(x);
     int rc;
     if (precond == HQS_PRECOND_LEARNED) {
-        rc = fcg_learned(p, a, b, r, xx, max_iter, rel_tol, precision, st);
+        if (precision != HQS_PREC_FP32) return HQS_ERR_UNSUPPORTED;
+        rc = fcg_learned(p, a, b, r, xx, max_iter, rel_tol, x0_zero, st);
     } else if (mode == HQS_SOLVE_FUSED || precision != HQS_PREC_FP32) {
         rc = pcg_fused(p, a, b, r, xx, max_iter, rel_tol, precond, precision, x0_zero, st);
     } else {

@@ -1,0 +1,190 @@
+"""GPU tests of the learned preconditioner: the network's forward pass,
+gradients and Adam step against the FP64 oracle; flexible CG with the trained
+network (convergence, held-out gain over the DC preconditioner alone) and its
+fallback to DC-preconditioned CG."""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from helpers import make_plan, quantised, rel, to_dev, to_host
+from oracle import convnet, toeplitz
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+def hq():
+    import paper_2411_01955_gb300 as m
+    return m
+
+
+def random_params(seed, scale_last=0.3):
+    rng = np.random.default_rng(seed)
+    params = convnet.init_params(seed)
+    W4 = rng.normal(size=params[-1][0].shape) * scale_last * math.sqrt(2.0 / (32 * 9))
+    params[-1] = (W4, rng.normal(size=2) * 0.1)
+    params = [(W, b + 0.05 * rng.normal(size=b.shape)) for W, b in params]
+    return params
+
+
+def f32(params):
+    return [(W.astype(np.float32).astype(np.float64), b.astype(np.float32).astype(np.float64))
+            for W, b in params]
+
+
+def test_net_forward_and_gradient_match_oracle():
+    rng = np.random.default_rng(0)
+    params = f32(random_params(1))
+    net = hq().Net()
+    assert net.num_params == convnet.num_params() == 19682
+    net.set_params(convnet.flatten(params))
+    assert np.array_equal(net.get_params(), convnet.flatten(params).astype(np.float32))
+    # odd spatial sizes: partial 16x16 tiles on both axes
+    x = rng.normal(size=(2, 2, 20, 19)).astype(np.float32)
+    t = rng.normal(size=(2, 2, 20, 19)).astype(np.float32)
+    xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+    out = net.forward(xd).cpu().numpy()
+    want, _ = convnet.forward(params, x.astype(np.float64))
+    assert rel(out, want) <= TOL
+    g, loss = net.gradient(xd, td)
+    wloss, wgrads = convnet.loss_and_grad(params, x.astype(np.float64), t.astype(np.float64))
+    wg = np.concatenate([np.concatenate([dW.ravel(), db.ravel()]) for dW, db in wgrads])
+    assert abs(loss / wloss - 1) <= TOL
+    assert rel(g.cpu().numpy(), wg) <= TOL
+    # per layer as well (a wrong layer offset would hide in the global norm)
+    k = 0
+    for dW, db in wgrads:
+        m = dW.size + db.size
+        assert rel(g.cpu().numpy()[k:k + m], wg[k:k + m]) <= 1e-4
+        k += m
+
+
+def test_adam_step_matches_its_definition():
+    rng = np.random.default_rng(2)
+    params = f32(random_params(3))
+    net = hq().Net()
+    p0 = convnet.flatten(params).astype(np.float32)
+    net.set_params(p0)
+    x = torch.from_numpy(rng.normal(size=(2, 2, 16, 16)).astype(np.float32)).cuda()
+    t = torch.from_numpy(rng.normal(size=(2, 2, 16, 16)).astype(np.float32)).cuda()
+    g, _ = net.gradient(x, t)
+    g = g.cpu().numpy().astype(np.float64)
+    lr = 1e-3
+    net.train_step(x, t, lr)
+    want, _, _ = convnet.adam_step(p0.astype(np.float64), g, np.zeros_like(g), np.zeros_like(g), 1, lr)
+    got = net.get_params().astype(np.float64)
+    assert np.max(np.abs(got - want)) <= 1e-6 * lr * 10 + 1e-7
+
+
+def make_slices(seeds, n=128, L=8):
+    traj = synth.traj_spiral(8, 1024, n)
+    out = []
+    for sd in seeds:
+        case = quantised(dict(n=n, L=L, W=6, sigma=2.0, x=synth.phantom(sd, n),
+                              smaps=synth.coil_maps(sd, n, L), traj=traj))
+        plan, _, _ = make_plan(case)
+        x = to_dev(case["x"])
+        y = torch.empty((L, traj.shape[0]), dtype=torch.complex64, device="cuda")
+        hq().forward(plan, x, y)
+        noise = torch.from_numpy(synth.complex_noise(sd, (L, traj.shape[0])).astype(np.complex64)).cuda()
+        y = y + 0.02 * float(torch.sqrt(torch.mean(torch.abs(y) ** 2))) * noise
+        rhs = torch.empty_like(x)
+        hq().adjoint(plan, y.contiguous(), rhs)
+        out.append((plan, rhs))
+    return out
+
+
+def test_learned_fcg_trains_converges_and_falls_back():
+    from paper_2411_01955_gb300 import learned
+    mu = 1e-2
+    train_slices = make_slices(range(1000, 1006))
+    test_slices = make_slices(range(5000, 5002))
+    examples = []
+    for plan, rhs in train_slices:
+        for r, e in learned.solve_pairs(plan, rhs, mu, iterates=24):
+            examples.append(learned.network_example(plan, mu, r, e))
+    held = []
+    for plan, rhs in test_slices:
+        for r, e in learned.solve_pairs(plan, rhs, mu, iterates=12):
+            held.append(learned.network_example(plan, mu, r, e))
+    net = hq().Net()
+    net.set_params(convnet.flatten(convnet.init_params(0)))
+    base = learned.heldout_loss(net, held)
+    assert abs(base - 1.0) < 1e-6          # zero last layer: exactly the DC preconditioner
+    losses = learned.train(net, examples, steps=600, batch=16, crop=48, lr=1e-3)
+    trained = learned.heldout_loss(net, held)
+    print(f"held-out relative error of the correction: {base:.3f} -> {trained:.3f}; "
+          f"train loss {losses[0]:.3f} -> {np.mean(losses[-20:]):.3f}")
+    assert trained < base                   # the trained network gains over DC alone
+    # flexible CG with the trained network, and DC-PCG, on held-out slices
+    for plan, rhs in test_slices:
+        hq().plan_set_net(plan, net)
+        xl = torch.zeros_like(rhs)
+        il = hq().dc_solve(plan, 1.0, mu, rhs, xl, max_iter=300, rel_tol=1e-4,
+                           precond=hq().HQS_PRECOND_LEARNED)
+        xd = torch.zeros_like(rhs)
+        idc = hq().dc_solve(plan, 1.0, mu, rhs, xd, max_iter=300, rel_tol=1e-4)
+        print(f"iterations to 1e-4: learned {il.iterations} (fallback {il.fallback}), DC {idc.iterations}")
+        assert il.status == 0 and il.rel_residual <= 1e-4
+        r = learned.residual(plan, mu, rhs, xl)
+        assert float(torch.linalg.vector_norm(r) / torch.linalg.vector_norm(rhs)) <= 1.5e-4
+    # a sabotaged network (negated correction, 30x) must trigger the fallback and still converge
+    bad = hq().Net()
+    vec = net.get_params().astype(np.float64)
+    k = convnet.num_params() - (2 * 32 * 9 + 2)
+    vec[k:] *= -30.0
+    bad.set_params(vec)
+    plan, rhs = test_slices[0]
+    hq().plan_set_net(plan, bad)
+    xb = torch.zeros_like(rhs)
+    ib = hq().dc_solve(plan, 1.0, mu, rhs, xb, max_iter=300, rel_tol=1e-4, precond=hq().HQS_PRECOND_LEARNED)
+    assert ib.status == 0 and ib.rel_residual <= 1e-4
+    print(f"sabotaged network: fallback {ib.fallback}, iterations {ib.iterations}")
+    hq().plan_set_net(plan, None)
+
+
+def test_learned_precond_apply_matches_oracle():
+    case = quantised(synth.tiny_case(0))
+    plan, _, _ = make_plan(case)
+    n = case["n"]
+    params = f32(random_params(5))
+    net = hq().Net()
+    net.set_params(convnet.flatten(params))
+    hq().plan_set_net(plan, net)
+    lam = toeplitz.chan_symbol(toeplitz.kernel(case["traj"], n, n), n, n)
+    r = case["x"]
+    z = torch.empty((n, n), dtype=torch.complex64, device="cuda")
+    hq().learned_precond_apply(plan, 1.0, 0.05, to_dev(r), z)
+    want = convnet.learned_precond(r, lam, 1.0, 0.05, params)
+    assert rel(to_host(z), want) <= 1e-4
+    hq().plan_set_net(plan, None)
+
+
+def test_learned_fcg_iterates_match_oracle():
+    from oracle import solvers
+    case = quantised(synth.tiny_case(0))
+    plan, _, _ = make_plan(case)
+    n, mu = case["n"], 1e-2
+    params = f32(random_params(7, scale_last=0.1))
+    net = hq().Net()
+    net.set_params(convnet.flatten(params))
+    hq().plan_set_net(plan, net)
+    c = toeplitz.kernel(case["traj"], n, n)
+    Kh, lam = toeplitz.khat(c), toeplitz.chan_symbol(c, n, n)
+    from oracle import nufft
+    rhs = nufft.adjoint(case["noise"], case["smaps"], case["traj"], case["W"], case["sigma"])
+    rhs = rhs.astype(np.complex64).astype(np.complex128)
+    H = lambda v: toeplitz.normal(v, case["smaps"], Kh) + mu * v
+    B = lambda v: convnet.learned_precond(v, lam, 1.0, mu, params)
+    want, winfo = solvers.fcg(H, rhs, np.zeros((n, n)), B, None, max_iter=4, tol=0.0)
+    x = torch.zeros((n, n), dtype=torch.complex64, device="cuda")
+    info = hq().dc_solve(plan, 1.0, mu, to_dev(rhs), x, max_iter=4, rel_tol=0.0,
+                         precond=hq().HQS_PRECOND_LEARNED)
+    assert info.iterations == 4 and not info.fallback and not winfo["fallback"]
+    assert rel(to_host(x), want) <= 1e-4
+    assert np.allclose(np.array(info.history()), winfo["res_hist"], rtol=1e-3, atol=0)
+    hq().plan_set_net(plan, None)
