@@ -69,6 +69,7 @@ extern "C" {
 
 typedef struct hqs_plan_s* hqs_plan;
 typedef struct hqs_net_s* hqs_net;
+typedef struct hqs_batch_s* hqs_batch;
 typedef struct { float re, im; } hqs_c64;
 
 typedef struct {
@@ -250,6 +251,31 @@ HQS_API int hqs_learned_precond_apply(hqs_plan plan, float a, float b, const hqs
 HQS_API int hqs_run(hqs_plan plan, const hqs_c64* y, hqs_c64* x, const float* mu,
             const float* sigma, int K, int k0, int cg_iters, float c0, float c1,
             hqs_denoiser_fn denoiser, void* user, void* stream);
+
+/* --------------------------------------- batched persistent HQS (a9) */
+/* Annealed PnP-HQS (Sec. 3.3, P = Id) for many slices of uneven size at once:
+ * one persistent cooperative launch runs, for every slice and k = k0..K-1,
+ * rhs = A^H y + mu_k c0 x_k, cg_iters DC-preconditioned CG iterations on
+ * (A^H A + c0 mu_k I) u = rhs from u = x_k, then x_{k+1} = Gaussian
+ * smoothing of u (std kappa sigma_k / sigma0 px; the built-in denoiser).
+ * Work items of all slices share every phase.  Plans: n in {64, 128, 256,
+ * 320, 384}, any coil count, <= 64 slices; each plan may belong to one batch
+ * at a time (its workspace is used).  hqs_batch_create allocates;
+ * hqs_batch_run enqueues on `stream` the per-slice adjoints and the
+ * persistent kernel, recorded once into a CUDA graph and replayed when
+ * use_graph != 0 (re-recorded when y/x pointers, K, k0, cg_iters or c0
+ * change; mu, sigma may change freely); it synchronises `stream` first.
+ * y[i]: (L_i, M_i) device; x[i]: (n_i, n_i) device, x_{k0} in, x_K out.
+ * c1 != 0 (F-1 / Chebyshev metrics) returns HQS_ERR_UNSUPPORTED here (use
+ * hqs_run).  hqs_batch_status synchronises and reports, per slice, the
+ * relative CG residual of the last data-consistency step. */
+HQS_API int hqs_batch_create(hqs_batch* out, hqs_plan* plans, int n, int max_outer);
+HQS_API void hqs_batch_destroy(hqs_batch batch);
+HQS_API int hqs_batch_run(hqs_batch batch, const hqs_c64* const* y, hqs_c64* const* x,
+                          const float* mu, const float* sigma, int K, int k0, int cg_iters,
+                          float c0, float c1, const hqs_gauss_params* gauss, int use_graph,
+                          void* stream);
+HQS_API int hqs_batch_status(hqs_batch batch, double* rel_residual, void* stream);
 
 /* Built-in denoiser (stand-in for the trained prior of Sec. 4.2): separable
  * Gaussian blur of real and imaginary parts, std s pixels (see

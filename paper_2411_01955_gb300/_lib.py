@@ -97,6 +97,12 @@ _SIGS = {
     "hqs_plan_set_net": (C.c_int, [C.c_void_p, C.c_void_p]),
     "hqs_learned_precond_apply": (C.c_int, [C.c_void_p, C.c_float, C.c_float, C.c_void_p,
                                             C.c_void_p, C.c_void_p]),
+    "hqs_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int, C.c_int]),
+    "hqs_batch_destroy": (None, [C.c_void_p]),
+    "hqs_batch_run": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_int, C.c_int, C.c_int,
+                                C.c_float, C.c_float, C.c_void_p, C.c_int, C.c_void_p]),
+    "hqs_batch_status": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_void_p]),
     "hqs_precond_apply_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_float, C.c_float,
                                             C.c_void_p, C.c_void_p]),
     "hqs_debug_phase_trace": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_ulonglong), C.c_int,
@@ -414,3 +420,46 @@ def learned_precond_apply(plan: Plan, a, b, r, z, stream=None):
                                                _ptr(z, torch.complex64, "z"), _stream(stream)),
            "hqs_learned_precond_apply")
     return z
+
+
+class Batch:
+    """Batched annealed HQS over plans of uneven size (hqs_batch_*)."""
+
+    def __init__(self, plans, max_outer=64):
+        self.plans = list(plans)
+        arr = (C.c_void_p * len(self.plans))(*[p.handle for p in self.plans])
+        h = C.c_void_p()
+        _check(library().hqs_batch_create(C.byref(h), arr, len(self.plans), int(max_outer)),
+               "hqs_batch_create")
+        self.handle = h
+
+    def run(self, ys, xs, mu, sigma, K=None, k0=0, cg_iters=5, c0=1.0, c1=0.0, gauss=None,
+            use_graph=True, stream=None):
+        K = len(mu) if K is None else int(K)
+        n = len(self.plans)
+        yp = (C.c_void_p * n)(*[_ptr(y, torch.complex64, "y") for y in ys])
+        xp = (C.c_void_p * n)(*[_ptr(x, torch.complex64, "x") for x in xs])
+        mu_c = (C.c_float * K)(*[float(v) for v in mu[:K]])
+        sg_c = (C.c_float * K)(*[float(v) for v in sigma[:K]])
+        gp = GaussParams(float(gauss[0]), float(gauss[1])) if gauss is not None else None
+        _check(library().hqs_batch_run(self.handle, yp, xp, mu_c, sg_c, K, int(k0), int(cg_iters),
+                                       float(c0), float(c1),
+                                       C.cast(C.pointer(gp), C.c_void_p) if gp else None,
+                                       1 if use_graph else 0, _stream(stream)), "hqs_batch_run")
+        return xs
+
+    def status(self, stream=None):
+        res = (C.c_double * len(self.plans))()
+        _check(library().hqs_batch_status(self.handle, res, _stream(stream)), "hqs_batch_status")
+        return [res[i] for i in range(len(self.plans))]
+
+    def close(self):
+        if self.handle:
+            library().hqs_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

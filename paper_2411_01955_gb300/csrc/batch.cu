@@ -1,0 +1,693 @@
+// Batched annealed PnP-HQS over slices of uneven size (a9): one persistent
+// cooperative launch runs, for every slice s and outer iteration k
+// (Sec. 3.3, P = Id in the metric of Sec. 3.4),
+//   u = x_k;  rhs = A^H y + mu_k c0 x_k;  cg_iters DC-preconditioned CG
+//   iterations on (A^H A + c0 mu_k I) u = rhs from u;  x_{k+1} = G_{s_k} u
+// with the Gaussian-smoothing denoiser of std s_k = kappa sigma_k / sigma_0.
+// The work items of all slices (rows, columns, preconditioner row blocks,
+// denoiser tiles) are dealt to the CTAs together in every phase, so slices of
+// 256^2, 320^2 and 384^2 with 8-20 coils share the GPU without per-slice
+// launches.  Every CTA reduces the per-slice partials in the same fixed order,
+// so the per-slice scalars agree everywhere.  hqs_batch_run records the
+// per-slice adjoints (A^H y) and the persistent kernel into one CUDA graph.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "persist.cuh"
+#include "plan.cuh"
+#include "solve.cuh"
+#include "toep_items.cuh"
+
+using namespace hqs;
+
+#define HQS_BATCH_MAX 64
+#define HQS_BATCH_BD 512
+#define HQS_BATCH_MAXR 24
+#define HQS_BATCH_Q 4
+
+namespace {
+
+enum BatchSlot { BS_PQ = 0, BS_RR = 1, BS_BB = 2, BS_RZ = 3, BS_N = 4 };
+enum BatchList { BL_ROWS = 0, BL_COLS = 1, BL_PC = 2, BL_IMG = 3, BL_BLUR = 4, BL_EPI = 5, BL_N = 6 };
+
+struct BatchSlice {
+    ToepArgs A;
+    const float2* twN;
+    const float* lam;
+    const float2* b0;
+    float2* x;
+    float2* u;
+    float2* rhs;
+    float2* r;
+    float2* p;
+    float2* q;
+    float2* pcb;
+};
+
+struct BatchArgs {
+    const BatchSlice* sl;
+    int ns;
+    const int* off;      // [BL_N][ns + 1] prefix item counts
+    int K, k0, cg_iters;
+    float c0;
+    const float* mu;     // [K]
+    const float* taps;   // [K][2 MAXR + 1], normalised
+    const int* radius;   // [K], -1: identity
+    double* part;        // [BS_N][ns][gridDim]
+    double* res;         // [ns] final ||r||^2 / ||rhs||^2 of the last DC step
+    unsigned* bar;
+    unsigned* err;
+};
+
+HQS_DEV int find_slice(const int* off, int ns, int g) {
+    int s = 0;
+    while (s + 1 < ns && off[s + 1] <= g) ++s;
+    return s;
+}
+
+// per-slice totals of a slot, identical in every CTA (fixed order)
+HQS_DEV void slice_totals(const double* part, int ns, double* out) {
+    const int G = gridDim.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int s = warp; s < ns; s += nw) {
+        double v = 0.0;
+        for (int c = lane; c < G; c += 32) v += __ldcg(part + (size_t)s * G + c);
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) out[s] = v;
+    }
+    __syncthreads();
+}
+
+HQS_DEV void put_slice_partials(double* part, int ns, const double* acc) {
+    for (int s = threadIdx.x; s < ns; s += blockDim.x) part[(size_t)s * gridDim.x + blockIdx.x] = acc[s];
+}
+
+// ---- per-size item bodies (BD = HQS_BATCH_BD)
+template <int N2, int N>
+HQS_DEV void z_and_p_row(const BatchSlice& S, int iy, float beta, bool first, float2* s, float2* zs,
+                         const float2* twN) {
+    const int n = N;
+    for (int pos = threadIdx.x; pos < N; pos += blockDim.x) s[pos * kLines] = __ldcg(S.pcb + (size_t)iy * N + pos);
+    __syncthreads();
+    block_fft<N, true>(s, 1, twN);
+    const float sc = 1.0f / ((float)N * (float)N);
+    for (int ix = threadIdx.x; ix < n; ix += blockDim.x) {
+        const size_t e = (size_t)iy * n + ix;
+        float2 v = cscale(s[ix * kLines], sc);
+        if (!first && beta != 0.f) {
+            const float2 pv = __ldcg(S.p + e);
+            v.x = fmaf(beta, pv.x, v.x);
+            v.y = fmaf(beta, pv.y, v.y);
+        }
+        S.p[e] = v;
+    }
+    __syncthreads();
+    (void)zs;
+}
+
+template <int N>
+HQS_DEV double pc_rows(const BatchSlice& S, int r0, float alpha, bool update, float2* s, const float2* twN) {
+    const int lines = min(HQS_BATCH_Q, N - r0);
+    double rr = 0.0;
+    for (int e = threadIdx.x; e < lines * N; e += blockDim.x) {
+        const int q_ = e / N, ix = e - q_ * N;
+        const size_t idx = (size_t)(r0 + q_) * N + ix;
+        float2 rv = __ldcg(S.r + idx);
+        if (update) {
+            const float2 pv = __ldcg(S.p + idx), qv = __ldcg(S.q + idx);
+            float2 uv = __ldcg(S.u + idx);
+            uv.x = fmaf(alpha, pv.x, uv.x);
+            uv.y = fmaf(alpha, pv.y, uv.y);
+            rv.x = fmaf(-alpha, qv.x, rv.x);
+            rv.y = fmaf(-alpha, qv.y, rv.y);
+            S.u[idx] = uv;
+            S.r[idx] = rv;
+        }
+        rr += (double)rv.x * rv.x + (double)rv.y * rv.y;
+        s[ix * kLines + q_] = rv;
+    }
+    __syncthreads();
+    block_fft<N, false>(s, lines, twN);
+    for (int e = threadIdx.x; e < lines * N; e += blockDim.x) {
+        const int q_ = e / N, pos = e - q_ * N;
+        S.pcb[(size_t)(r0 + q_) * N + pos] = s[pos * kLines + q_];
+    }
+    __syncthreads();
+    return rr;
+}
+
+template <int N>
+HQS_DEV double pc_cols(const BatchSlice& S, int c0, float a, float b, float2* s, const float2* twN) {
+    const int lines = min(HQS_BATCH_Q, N - c0);
+    for (int e = threadIdx.x; e < N * lines; e += blockDim.x) {
+        const int pos = e / lines, q_ = e - pos * lines;
+        s[pos * kLines + q_] = __ldcg(S.pcb + (size_t)pos * N + c0 + q_);
+    }
+    __syncthreads();
+    block_fft<N, false>(s, lines, twN);
+    double acc = 0.0;
+    for (int e = threadIdx.x; e < N * lines; e += blockDim.x) {
+        const int pos = e / lines, q_ = e - pos * lines;
+        const float l = S.lam[(size_t)pos * N + c0 + q_];
+        const float m = rsqrtf(fmaxf(fmaf(a, fmaxf(l, 0.f), b), 0.25f * b));
+        const float2 v = s[pos * kLines + q_];
+        acc += (double)(m * (v.x * v.x + v.y * v.y));
+        s[pos * kLines + q_] = cscale(v, m);
+    }
+    __syncthreads();
+    block_fft<N, true>(s, lines, twN);
+    for (int e = threadIdx.x; e < N * lines; e += blockDim.x) {
+        const int pos = e / lines, q_ = e - pos * lines;
+        S.pcb[(size_t)pos * N + c0 + q_] = s[pos * kLines + q_];
+    }
+    __syncthreads();
+    return acc;
+}
+
+#define HQS_BATCH_DISPATCH(n, ...)                                         \
+    switch (n) {                                                           \
+        case 64: { constexpr int N2 = 128, N = 64; __VA_ARGS__; break; }   \
+        case 128: { constexpr int N2 = 256, N = 128; __VA_ARGS__; break; } \
+        case 256: { constexpr int N2 = 512, N = 256; __VA_ARGS__; break; } \
+        case 320: { constexpr int N2 = 640, N = 320; __VA_ARGS__; break; } \
+        default: { constexpr int N2 = 768, N = 384; __VA_ARGS__; break; }  \
+    }
+
+// Gaussian blur of one 32x32 tile of u into x (periodic), radius r >= 0
+HQS_DEV void blur_tile(const BatchSlice& S, int tile, const float* g, int r, float2* sb) {
+    const int n = S.A.n;
+    const int tpr = (n + 31) / 32;
+    const int y0 = (tile / tpr) * 32, x0 = (tile % tpr) * 32;
+    const int E = 32 + 2 * r;
+    float2* t = sb;
+    float2* mid = sb + E * E;
+    for (int e = threadIdx.x; e < E * E; e += blockDim.x) {
+        const int ty = e / E, tx = e - ty * E;
+        int gy = (y0 + ty - r) % n, gx = (x0 + tx - r) % n;
+        if (gy < 0) gy += n;
+        if (gx < 0) gx += n;
+        t[e] = __ldcg(S.u + (size_t)gy * n + gx);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < E * 32; e += blockDim.x) {
+        const int ty = e / 32, tx = e - ty * 32;
+        float2 acc = make_float2(0.f, 0.f);
+        for (int i = 0; i <= 2 * r; ++i) {
+            const float2 v = t[ty * E + tx + i];
+            acc.x = fmaf(g[i], v.x, acc.x);
+            acc.y = fmaf(g[i], v.y, acc.y);
+        }
+        mid[e] = acc;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+        const int ty = e / 32, tx = e - ty * 32;
+        const int gy = y0 + ty, gx = x0 + tx;
+        if (gy >= n || gx >= n) continue;
+        float2 acc = make_float2(0.f, 0.f);
+        for (int i = 0; i <= 2 * r; ++i) {
+            const float2 v = mid[(ty + i) * 32 + tx];
+            acc.x = fmaf(g[i], v.x, acc.x);
+            acc.y = fmaf(g[i], v.y, acc.y);
+        }
+        S.x[(size_t)gy * n + gx] = acc;
+    }
+    __syncthreads();
+}
+
+// smem: lines buffer [768][16] | row [384] | tw 2n [768] | tw n [384] | scalars
+constexpr size_t kBatchSmemF2 = (size_t)768 * kLines + 384 + 768 + 384;
+
+__global__ void __launch_bounds__(HQS_BATCH_BD, 1) k_hqs_batch(BatchArgs B) {
+    extern __shared__ float2 s[];
+    __shared__ double red[33];
+    __shared__ double acc[2][HQS_BATCH_MAX];
+    __shared__ double tot[2][HQS_BATCH_MAX];
+    __shared__ double rzs[HQS_BATCH_MAX], alphas[HQS_BATCH_MAX], betas[HQS_BATCH_MAX];
+    __shared__ int sl_cache;
+    const int ns = B.ns, G = gridDim.x, bid = blockIdx.x;
+    float2* twN = s + (size_t)768 * kLines + 384 + 768;
+    int cur_twn = -1;   // slice whose n-point twiddles are staged
+#define BB_BARRIER()                                \
+    do {                                            \
+        if (!grid_barrier(B.bar, B.err)) return;    \
+    } while (0)
+#define FOR_ITEMS(list, ...)                                                               \
+    {                                                                                      \
+        const int* off_ = B.off + (list) * (ns + 1);                                       \
+        for (int g_ = bid; g_ < off_[ns]; g_ += G) {                                       \
+            const int si = find_slice(off_, ns, g_);                                       \
+            const int it_ = g_ - off_[si];                                                 \
+            const BatchSlice& S = B.sl[si];                                                \
+            __VA_ARGS__;                                                                   \
+        }                                                                                  \
+    }
+#define STAGE_TWN(S, si)                                                                  \
+    if (cur_twn != (si)) {                                                                \
+        __syncthreads();                                                                  \
+        for (int i_ = threadIdx.x; i_ < (S).A.n; i_ += blockDim.x) twN[i_] = (S).twN[i_]; \
+        __syncthreads();                                                                  \
+        cur_twn = (si);                                                                   \
+    }
+#define CLEAR_ACC()                                                      \
+    for (int i_ = threadIdx.x; i_ < 2 * HQS_BATCH_MAX; i_ += blockDim.x) \
+        (&acc[0][0])[i_] = 0.0;                                          \
+    __syncthreads();
+
+    (void)sl_cache;
+    for (int k = B.k0; k < B.K; ++k) {
+        const float muk = B.mu[k];
+        const float bcoef = B.c0 * muk;
+        // PREP: u = x, rhs = A^H y + mu c0 x
+        FOR_ITEMS(BL_IMG, {
+            const int n = S.A.n;
+            for (int ix = threadIdx.x; ix < n; ix += blockDim.x) {
+                const size_t e = (size_t)it_ * n + ix;
+                const float2 xv = __ldcg(S.x + e), bv = S.b0[e];
+                S.u[e] = xv;
+                S.rhs[e] = make_float2(fmaf(bcoef, xv.x, bv.x), fmaf(bcoef, xv.y, bv.y));
+            }
+        });
+        BB_BARRIER();
+        // q = H u
+        FOR_ITEMS(BL_ROWS, {
+            const int n = S.A.n, ch = it_ / n, iy = it_ - ch * n;
+            HQS_BATCH_DISPATCH(n, (toep_rows_fwd_item<N2, HQS_BATCH_BD>(S.A, iy, ch, S.u, nullptr, 0.f, false, s)));
+        });
+        BB_BARRIER();
+        FOR_ITEMS(BL_COLS, {
+            const int n = S.A.n, N2v = 2 * n, ch = it_ / N2v, kx = it_ - ch * N2v;
+            HQS_BATCH_DISPATCH(n, (toep_cols_item<N2, HQS_BATCH_BD>(S.A, kx, ch, s)));
+        });
+        BB_BARRIER();
+        FOR_ITEMS(BL_ROWS, {
+            const int n = S.A.n, ch = it_ / n, iy = it_ - ch * n;
+            HQS_BATCH_DISPATCH(n, (toep_rows_adj_item<N2, HQS_BATCH_BD>(S.A, iy, ch, S.q, S.u, 1.f, bcoef, 1, s)));
+        });
+        BB_BARRIER();
+        FOR_ITEMS(BL_EPI, {   // several coil chunks: fixed-order chunk sum + epilogue
+            const int n = S.A.n, cnt = n * n;
+            for (int ix = threadIdx.x; ix < n; ix += blockDim.x) {
+                const size_t e = (size_t)it_ * n + ix;
+                float2 v = make_float2(0.f, 0.f);
+                for (int c = 0; c < S.A.nchunk; ++c) v = cadd(v, __ldcg(S.A.chunk + (size_t)c * cnt + e));
+                double dummy = 0.0;
+                S.q[e] = toep_epilogue(v, e, S.u, 1.f, bcoef, 1, dummy);
+            }
+        });
+        BB_BARRIER();
+        // r = rhs - q; ||r||^2, ||rhs||^2 per slice
+        CLEAR_ACC();
+        FOR_ITEMS(BL_IMG, {
+            const int n = S.A.n;
+            double a1 = 0.0, a2 = 0.0;
+            for (int ix = threadIdx.x; ix < n; ix += blockDim.x) {
+                const size_t e = (size_t)it_ * n + ix;
+                const float2 bv = __ldcg(S.rhs + e);
+                const float2 v = csub(bv, __ldcg(S.q + e));
+                S.r[e] = v;
+                a1 += (double)v.x * v.x + (double)v.y * v.y;
+                a2 += (double)bv.x * bv.x + (double)bv.y * bv.y;
+            }
+            a1 = cta_sum(a1, red);
+            a2 = cta_sum(a2, red);
+            if (threadIdx.x == 0) {
+                acc[0][si] += a1;
+                acc[1][si] += a2;
+            }
+        });
+        __syncthreads();
+        put_slice_partials(B.part + (size_t)BS_RR * ns * G, ns, acc[0]);
+        put_slice_partials(B.part + (size_t)BS_BB * ns * G, ns, acc[1]);
+        BB_BARRIER();
+        slice_totals(B.part + (size_t)BS_BB * ns * G, ns, tot[1]);
+        // preconditioner of the initial residual
+        FOR_ITEMS(BL_PC, {
+            STAGE_TWN(S, si);
+            HQS_BATCH_DISPATCH(S.A.n, (pc_rows<N>(S, it_ * HQS_BATCH_Q, 0.f, false, s, twN)));
+        });
+        BB_BARRIER();
+        CLEAR_ACC();
+        FOR_ITEMS(BL_PC, {
+            STAGE_TWN(S, si);
+            double v = 0.0;
+            HQS_BATCH_DISPATCH(S.A.n, (v = pc_cols<N>(S, it_ * HQS_BATCH_Q, 1.f, bcoef, s, twN)));
+            v = cta_sum(v, red);
+            if (threadIdx.x == 0) acc[0][si] += v;
+        });
+        __syncthreads();
+        put_slice_partials(B.part + (size_t)BS_RZ * ns * G, ns, acc[0]);
+        BB_BARRIER();
+        slice_totals(B.part + (size_t)BS_RZ * ns * G, ns, tot[0]);
+        for (int i = threadIdx.x; i < ns; i += blockDim.x) {
+            const int n = B.sl[i].A.n;
+            rzs[i] = tot[0][i] / ((double)n * n);
+            betas[i] = 0.0;
+        }
+        __syncthreads();
+        for (int cg = 0; cg < B.cg_iters; ++cg) {
+            // A0: z rows and p = z + beta p
+            FOR_ITEMS(BL_IMG, {
+                STAGE_TWN(S, si);
+                HQS_BATCH_DISPATCH(S.A.n, (z_and_p_row<N2, N>(S, it_, (float)betas[si], cg == 0, s, nullptr, twN)));
+            });
+            BB_BARRIER();
+            FOR_ITEMS(BL_ROWS, {
+                const int n = S.A.n, ch = it_ / n, iy = it_ - ch * n;
+                HQS_BATCH_DISPATCH(n, (toep_rows_fwd_item<N2, HQS_BATCH_BD>(S.A, iy, ch, S.p, nullptr, 0.f, false, s)));
+            });
+            BB_BARRIER();
+            FOR_ITEMS(BL_COLS, {
+                const int n = S.A.n, N2v = 2 * n, ch = it_ / N2v, kx = it_ - ch * N2v;
+                HQS_BATCH_DISPATCH(n, (toep_cols_item<N2, HQS_BATCH_BD>(S.A, kx, ch, s)));
+            });
+            BB_BARRIER();
+            CLEAR_ACC();
+            FOR_ITEMS(BL_ROWS, {
+                const int n = S.A.n, ch = it_ / n, iy = it_ - ch * n;
+                double v = 0.0;
+                HQS_BATCH_DISPATCH(n, (v = toep_rows_adj_item<N2, HQS_BATCH_BD>(S.A, iy, ch, S.q, S.p, 1.f, bcoef, 1, s)));
+                v = cta_sum(v, red);
+                if (threadIdx.x == 0) acc[0][si] += v;
+            });
+            BB_BARRIER();
+            FOR_ITEMS(BL_EPI, {
+                const int n = S.A.n, cnt = n * n;
+                double v = 0.0;
+                for (int ix = threadIdx.x; ix < n; ix += blockDim.x) {
+                    const size_t e = (size_t)it_ * n + ix;
+                    float2 w = make_float2(0.f, 0.f);
+                    for (int c = 0; c < S.A.nchunk; ++c) w = cadd(w, __ldcg(S.A.chunk + (size_t)c * cnt + e));
+                    S.q[e] = toep_epilogue(w, e, S.p, 1.f, bcoef, 1, v);
+                }
+                v = cta_sum(v, red);
+                if (threadIdx.x == 0) acc[0][si] += v;
+            });
+            __syncthreads();
+            put_slice_partials(B.part + (size_t)BS_PQ * ns * G, ns, acc[0]);
+            BB_BARRIER();
+            slice_totals(B.part + (size_t)BS_PQ * ns * G, ns, tot[0]);
+            for (int i = threadIdx.x; i < ns; i += blockDim.x) {
+                const double pq = tot[0][i];
+                alphas[i] = (pq > 0.0 && !isinf(pq)) ? rzs[i] / pq : 0.0;
+            }
+            __syncthreads();
+            // D: u, r update, ||r||^2, row FFTs of r
+            CLEAR_ACC();
+            FOR_ITEMS(BL_PC, {
+                STAGE_TWN(S, si);
+                double v = 0.0;
+                HQS_BATCH_DISPATCH(S.A.n, (v = pc_rows<N>(S, it_ * HQS_BATCH_Q, (float)alphas[si], true, s, twN)));
+                v = cta_sum(v, red);
+                if (threadIdx.x == 0) acc[1][si] += v;
+            });
+            __syncthreads();
+            put_slice_partials(B.part + (size_t)BS_RR * ns * G, ns, acc[1]);
+            BB_BARRIER();
+            if (cg == B.cg_iters - 1) break;
+            // E: preconditioner columns, <r, z>
+            CLEAR_ACC();
+            FOR_ITEMS(BL_PC, {
+                STAGE_TWN(S, si);
+                double v = 0.0;
+                HQS_BATCH_DISPATCH(S.A.n, (v = pc_cols<N>(S, it_ * HQS_BATCH_Q, 1.f, bcoef, s, twN)));
+                v = cta_sum(v, red);
+                if (threadIdx.x == 0) acc[0][si] += v;
+            });
+            __syncthreads();
+            put_slice_partials(B.part + (size_t)BS_RZ * ns * G, ns, acc[0]);
+            BB_BARRIER();
+            slice_totals(B.part + (size_t)BS_RZ * ns * G, ns, tot[0]);
+            for (int i = threadIdx.x; i < ns; i += blockDim.x) {
+                const int n = B.sl[i].A.n;
+                const double rz_new = tot[0][i] / ((double)n * n);
+                betas[i] = rzs[i] > 0.0 ? rz_new / rzs[i] : 0.0;
+                rzs[i] = rz_new;
+            }
+            __syncthreads();
+        }
+        if (k == B.K - 1) {
+            slice_totals(B.part + (size_t)BS_RR * ns * G, ns, tot[0]);
+            if (bid == 0)
+                for (int i = threadIdx.x; i < ns; i += blockDim.x)
+                    B.res[i] = tot[1][i] > 0.0 ? tot[0][i] / tot[1][i] : 0.0;
+        }
+        // denoiser: x = G(u)
+        const int rk = B.radius[k];
+        const float* gk = B.taps + (size_t)k * (2 * HQS_BATCH_MAXR + 1);
+        FOR_ITEMS(BL_BLUR, {
+            if (rk < 0) {
+                const int n = S.A.n, tpr = (n + 31) / 32;
+                const int y0 = (it_ / tpr) * 32, x0 = (it_ % tpr) * 32;
+                for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
+                    const int gy = y0 + e / 32, gx = x0 + e % 32;
+                    if (gy < n && gx < n) S.x[(size_t)gy * n + gx] = __ldcg(S.u + (size_t)gy * n + gx);
+                }
+            } else {
+                blur_tile(S, it_, gk, rk, s);
+            }
+        });
+        BB_BARRIER();
+    }
+#undef BB_BARRIER
+#undef FOR_ITEMS
+#undef STAGE_TWN
+#undef CLEAR_ACC
+}
+
+}  // namespace
+
+struct hqs_batch_s {
+    int device = 0;
+    int ns = 0;
+    int K = 0;
+    std::vector<hqs_plan_s*> plans;
+    BatchSlice* d_slices = nullptr;
+    int* d_off = nullptr;
+    float* d_mu = nullptr;
+    float* d_taps = nullptr;
+    int* d_radius = nullptr;
+    double* d_part = nullptr;
+    double* d_res = nullptr;
+    unsigned* d_bar = nullptr;
+    unsigned* d_err = nullptr;
+    float* h_mu = nullptr;        // pinned staging (read when the graph replays)
+    float* h_taps = nullptr;
+    int* h_radius = nullptr;
+    int grid = 0;
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<const void*> key;  // y / x pointers the graph was recorded with
+    int key_K = -1, key_k0 = -1, key_cg = -1;
+    float key_c0 = 0.f;
+};
+
+static void batch_free(hqs_batch_s* b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    cudaFree(b->d_slices);
+    cudaFree(b->d_off);
+    cudaFree(b->d_mu);
+    cudaFree(b->d_taps);
+    cudaFree(b->d_radius);
+    cudaFree(b->d_part);
+    cudaFree(b->d_res);
+    cudaFree(b->d_bar);
+    cudaFree(b->d_err);
+    cudaFreeHost(b->h_mu);
+    cudaFreeHost(b->h_taps);
+    cudaFreeHost(b->h_radius);
+    delete b;
+}
+
+extern "C" void hqs_batch_destroy(hqs_batch b) { batch_free(b); }
+
+extern "C" int hqs_batch_create(hqs_batch* out, hqs_plan* plans, int n, int max_outer) {
+    if (!out || !plans || n <= 0 || n > HQS_BATCH_MAX || max_outer <= 0 || max_outer > 4096)
+        return HQS_ERR_INVALID_ARG;
+    *out = nullptr;
+    for (int i = 0; i < n; ++i) {
+        const hqs_plan_s* p = plans[i];
+        if (!p) return HQS_ERR_INVALID_ARG;
+        if (p->n != 64 && p->n != 128 && p->n != 256 && p->n != 320 && p->n != 384) return HQS_ERR_UNSUPPORTED;
+    }
+    hqs_batch_s* b = new (std::nothrow) hqs_batch_s();
+    if (!b) return HQS_ERR_OOM;
+    cudaGetDevice(&b->device);
+    b->ns = n;
+    b->K = max_outer;
+    b->plans.assign(plans, plans + n);
+    auto fail = [&](int rc) {
+        batch_free(b);
+        return rc;
+    };
+    // slice table and item lists
+    std::vector<BatchSlice> hs(n);
+    std::vector<int> off((size_t)BL_N * (n + 1), 0);
+    for (int i = 0; i < n; ++i) {
+        hqs_plan_s* p = plans[i];
+        BatchSlice& S = hs[i];
+        S.A = toep_args(p);
+        S.twN = plan_twiddles(p, p->n);
+        S.lam = p->lam;
+        S.b0 = p->img_b0;
+        S.x = nullptr;   // set per run
+        S.u = p->img_u;
+        S.rhs = p->img_rhs;
+        S.r = p->cg_r;
+        S.p = p->cg_p;
+        S.q = p->cg_q;
+        S.pcb = p->pc_buf;
+        const int cnt[BL_N] = {p->n * p->nchunk, 2 * p->n * p->nchunk, ceil_div(p->n, HQS_BATCH_Q), p->n,
+                               ceil_div(p->n, 32) * ceil_div(p->n, 32), p->nchunk > 1 ? p->n : 0};
+        for (int l = 0; l < BL_N; ++l) off[(size_t)l * (n + 1) + i + 1] = off[(size_t)l * (n + 1) + i] + cnt[l];
+    }
+    const size_t sm = kBatchSmemF2 * sizeof(float2);
+    int per_sm = 0, nsm = 0;
+    if (cudaFuncSetAttribute(k_hqs_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hqs_batch, HQS_BATCH_BD, sm) ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->device) || per_sm < 1)
+        return fail(HQS_ERR_CUDA);
+    b->grid = per_sm * nsm;
+    if (cudaMalloc(&b->d_slices, n * sizeof(BatchSlice)) || cudaMalloc(&b->d_off, off.size() * sizeof(int)) ||
+        cudaMalloc(&b->d_mu, max_outer * sizeof(float)) ||
+        cudaMalloc(&b->d_taps, (size_t)max_outer * (2 * HQS_BATCH_MAXR + 1) * sizeof(float)) ||
+        cudaMalloc(&b->d_radius, max_outer * sizeof(int)) ||
+        cudaMalloc(&b->d_part, (size_t)BS_N * n * b->grid * sizeof(double)) ||
+        cudaMalloc(&b->d_res, n * sizeof(double)) || cudaMalloc(&b->d_bar, 2 * sizeof(unsigned)) ||
+        cudaMalloc(&b->d_err, sizeof(unsigned)) || cudaMallocHost(&b->h_mu, max_outer * sizeof(float)) ||
+        cudaMallocHost(&b->h_taps, (size_t)max_outer * (2 * HQS_BATCH_MAXR + 1) * sizeof(float)) ||
+        cudaMallocHost(&b->h_radius, max_outer * sizeof(int)) ||
+        cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking))
+        return fail(HQS_ERR_OOM);
+    if (cudaMemcpy(b->d_slices, hs.data(), n * sizeof(BatchSlice), cudaMemcpyHostToDevice) ||
+        cudaMemcpy(b->d_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice))
+        return fail(HQS_ERR_CUDA);
+    *out = b;
+    return HQS_OK;
+}
+
+// Everything one batch step enqueues (recorded into the graph).
+static int batch_enqueue(hqs_batch_s* b, const hqs_c64* const* y, hqs_c64* const* x, int K, int k0, int cg_iters,
+                         float c0, cudaStream_t st) {
+    const int n = b->ns;
+    for (int i = 0; i < n; ++i)
+        HQS_TRY_RC(launch_adj(b->plans[i], reinterpret_cast<const float2*>(y[i]), b->plans[i]->img_b0, st));
+    HQS_CUDA_TRY(cudaMemcpyAsync(b->d_mu, b->h_mu, K * sizeof(float), cudaMemcpyHostToDevice, st));
+    HQS_CUDA_TRY(cudaMemcpyAsync(b->d_taps, b->h_taps, (size_t)K * (2 * HQS_BATCH_MAXR + 1) * sizeof(float),
+                                 cudaMemcpyHostToDevice, st));
+    HQS_CUDA_TRY(cudaMemcpyAsync(b->d_radius, b->h_radius, K * sizeof(int), cudaMemcpyHostToDevice, st));
+    HQS_CUDA_TRY(cudaMemsetAsync(b->d_bar, 0, 2 * sizeof(unsigned), st));
+    HQS_CUDA_TRY(cudaMemsetAsync(b->d_err, 0, sizeof(unsigned), st));
+    BatchArgs A;
+    A.sl = b->d_slices;
+    A.ns = n;
+    A.off = b->d_off;
+    A.K = K;
+    A.k0 = k0;
+    A.cg_iters = cg_iters;
+    A.c0 = c0;
+    A.mu = b->d_mu;
+    A.taps = b->d_taps;
+    A.radius = b->d_radius;
+    A.part = b->d_part;
+    A.res = b->d_res;
+    A.bar = b->d_bar;
+    A.err = b->d_err;
+    void* args[] = {&A};
+    HQS_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_hqs_batch, dim3(b->grid), dim3(HQS_BATCH_BD), args,
+                                             kBatchSmemF2 * sizeof(float2), st));
+    return HQS_OK;
+}
+
+extern "C" int hqs_batch_run(hqs_batch b, const hqs_c64* const* y, hqs_c64* const* x, const float* mu,
+                             const float* sigma, int K, int k0, int cg_iters, float c0, float c1,
+                             const hqs_gauss_params* gauss, int use_graph, void* stream) {
+    if (!b || !y || !x || !mu || !sigma || K <= 0 || K > b->K || k0 < 0 || k0 >= K || cg_iters < 1 ||
+        cg_iters > HQS_MAX_ITERS || !(c0 > 0.f))
+        return HQS_ERR_INVALID_ARG;
+    if (c1 != 0.f) return HQS_ERR_UNSUPPORTED;
+    for (int i = 0; i < b->ns; ++i)
+        if (!x[i] || (!y[i] && b->plans[i]->M > 0)) return HQS_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    // a previous step may still read the slice table and the staging buffers
+    HQS_CUDA_TRY(cudaStreamSynchronize(st));
+    // the x pointers live in the device slice table
+    std::vector<BatchSlice> hs(b->ns);
+    HQS_CUDA_TRY(cudaMemcpy(hs.data(), b->d_slices, b->ns * sizeof(BatchSlice), cudaMemcpyDeviceToHost));
+    bool xchg = false;
+    for (int i = 0; i < b->ns; ++i) {
+        float2* xi = reinterpret_cast<float2*>(x[i]);
+        if (hs[i].x != xi) xchg = true;
+        hs[i].x = xi;
+    }
+    if (xchg) HQS_CUDA_TRY(cudaMemcpy(b->d_slices, hs.data(), b->ns * sizeof(BatchSlice), cudaMemcpyHostToDevice));
+    // schedules and denoiser taps (host, into pinned staging)
+    const float kappa = gauss ? gauss->kappa : 1.5f;
+    const float s0 = gauss ? gauss->sigma0 : sigma[0];
+    for (int k = 0; k < K; ++k) {
+        if (!(mu[k] > 0.f) || !(sigma[k] >= 0.f)) return HQS_ERR_INVALID_ARG;
+        b->h_mu[k] = mu[k];
+        const double sd = s0 > 0.f ? (double)kappa * sigma[k] / s0 : (double)sigma[k];
+        float* g = b->h_taps + (size_t)k * (2 * HQS_BATCH_MAXR + 1);
+        if (sd < 0.1) {
+            b->h_radius[k] = -1;
+            continue;
+        }
+        const int r = (int)std::ceil(3.0 * sd);
+        if (r > HQS_BATCH_MAXR) return HQS_ERR_INVALID_ARG;
+        b->h_radius[k] = r;
+        double sum = 0.0;
+        std::vector<double> gg(2 * r + 1);
+        for (int i = -r; i <= r; ++i) sum += gg[i + r] = std::exp(-(double)i * i / (2.0 * sd * sd));
+        for (int i = 0; i <= 2 * r; ++i) g[i] = (float)(gg[i] / sum);
+    }
+    if (!use_graph) return batch_enqueue(b, y, x, K, k0, cg_iters, c0, st);
+    std::vector<const void*> key;
+    for (int i = 0; i < b->ns; ++i) {
+        key.push_back(y[i]);
+        key.push_back(x[i]);
+    }
+    if (!b->exec || key != b->key || K != b->key_K || k0 != b->key_k0 || cg_iters != b->key_cg || c0 != b->key_c0) {
+        if (b->exec) cudaGraphExecDestroy(b->exec);
+        if (b->graph) cudaGraphDestroy(b->graph);
+        b->exec = nullptr;
+        b->graph = nullptr;
+        HQS_CUDA_TRY(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+        const int rc = batch_enqueue(b, y, x, K, k0, cg_iters, c0, b->cap);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(b->cap, &g);
+        if (rc != HQS_OK) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        HQS_CUDA_TRY(e);
+        b->graph = g;
+        HQS_CUDA_TRY(cudaGraphInstantiate(&b->exec, g, 0));
+        b->key = key;
+        b->key_K = K;
+        b->key_k0 = k0;
+        b->key_cg = cg_iters;
+        b->key_c0 = c0;
+    }
+    HQS_CUDA_TRY(cudaGraphLaunch(b->exec, st));
+    return HQS_OK;
+}
+
+extern "C" int hqs_batch_status(hqs_batch b, double* rel_res, void* stream) {
+    if (!b) return HQS_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned err = 0;
+    HQS_CUDA_TRY(cudaMemcpyAsync(&err, b->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    std::vector<double> r(b->ns);
+    HQS_CUDA_TRY(cudaMemcpyAsync(r.data(), b->d_res, b->ns * sizeof(double), cudaMemcpyDeviceToHost, st));
+    HQS_CUDA_TRY(cudaStreamSynchronize(st));
+    if (rel_res)
+        for (int i = 0; i < b->ns; ++i) rel_res[i] = std::sqrt(std::max(r[i], 0.0));
+    return (err & HQS_DEVERR_TIMEOUT) ? HQS_ERR_TIMEOUT : HQS_OK;
+}

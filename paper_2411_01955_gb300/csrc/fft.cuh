@@ -295,8 +295,8 @@ HQS_FFT_SIZE(384, 24, ST(8, 1) ST(8, 8) ST(6, 64))
 #undef NN_
 #undef E_
 #define NN_ 512
-#define E_ 8
-HQS_FFT_SIZE(512, 8, ST(8, 1) ST(8, 8) ST(8, 64))
+#define E_ 16
+HQS_FFT_SIZE(512, 16, ST(8, 1) ST(8, 8) ST(8, 64))
 #undef NN_
 #undef E_
 #define NN_ 640

@@ -22,7 +22,7 @@ template <int N2> constexpr size_t toep_smem_floats2(int n) { return (size_t)N2 
 // solver rebuilds z there); otherwise the row is read from src.  Vectors
 // written by other CTAs earlier in the same launch are read with ld.global.cg
 // (L2), never from a possibly stale L1 line.
-template <int N2>
+template <int N2, int BD = FftSize<N2>::TPL * kLines>
 HQS_DEV void toep_rows_fwd_item(const ToepArgs& A, int iy, int ch, const float2* __restrict__ src,
                                 float2* __restrict__ pvec, float beta, bool fuse, float2* s,
                                 const float2* src_row = nullptr) {
@@ -48,8 +48,10 @@ HQS_DEV void toep_rows_fwd_item(const ToepArgs& A, int iy, int ch, const float2*
     const int l = threadIdx.x % lines, p0 = threadIdx.x / lines;
     const float2* sm = A.smaps + (int64_t)iy * n * L + l0 + l;
     __syncthreads();
-    constexpr int TPL = FftSize<N2>::TPL;
-    if (lines == kLines) {   // full chunk: n = N2/2 and pst = TPL are compile-time
+    // full chunk with the block size BD: n = N2/2 and pst = BD/16 are compile-time
+    constexpr int TPL = BD / kLines;
+    const bool full = lines == kLines && (int)blockDim.x == BD;
+    if (full) {
         unrolled<N2 / 2 / TPL, TPL>(p0, [&](int p) { s[p * kLines + l] = cmul(sm[(int64_t)p * L], rowv[p]); });
     } else if (p0 < pst) {
         for (int p = p0; p < n; p += pst) s[p * kLines + l] = cmul(sm[(int64_t)p * L], rowv[p]);
@@ -57,7 +59,7 @@ HQS_DEV void toep_rows_fwd_item(const ToepArgs& A, int iy, int ch, const float2*
     __syncthreads();
     block_fft<N2, false, true>(s, lines, tw);   // upper half is the zero padding
     float2* dst = A.T + (int64_t)iy * N2 * L + l0 + l;
-    if (lines == kLines) {
+    if (full) {
         unrolled<N2 / TPL, TPL>(p0, [&](int p) { dst[(int64_t)p * L] = s[p * kLines + l]; });
     } else if (p0 < pst) {
         for (int p = p0; p < N2; p += pst) dst[(int64_t)p * L] = s[p * kLines + l];
@@ -66,7 +68,7 @@ HQS_DEV void toep_rows_fwd_item(const ToepArgs& A, int iy, int ch, const float2*
 }
 
 // P2: column kx: zero-pad, FFT along y, * Khat, IFFT, keep the first n rows.
-template <int N2>
+template <int N2, int BD = FftSize<N2>::TPL * kLines>
 HQS_DEV void toep_cols_item(const ToepArgs& A, int kx, int ch, float2* s) {
     const int n = A.n, L = A.L;
     const float2* tw = stage_twiddles<N2>(s + N2 * kLines + n, A.tw);
@@ -76,8 +78,8 @@ HQS_DEV void toep_cols_item(const ToepArgs& A, int kx, int ch, float2* s) {
     const int l = threadIdx.x % lines, p0 = threadIdx.x / lines;
     float2* col = A.T + (int64_t)kx * L + l0 + l;
     const int64_t rs = (int64_t)N2 * L;
-    constexpr int TPL = FftSize<N2>::TPL;
-    const bool full = lines == kLines;
+    constexpr int TPL = BD / kLines;
+    const bool full = lines == kLines && (int)blockDim.x == BD;
     const float* kh = A.khat + (int64_t)kx * N2;   // Khat stored transposed: column kx contiguous
     if (full) {
         unrolled<N2 / 2 / TPL, TPL>(p0, [&](int p) { s[p * kLines + l] = __ldcg(col + p * rs); });
@@ -116,7 +118,7 @@ HQS_DEV float2 toep_epilogue(float2 v, int64_t e, const float2* __restrict__ pve
 // P3: row iy: IFFT along x, keep n, sum_l conj(S_l) . over the chunk's coils.
 // One chunk: epilogue and store here (returns the thread's partial); several
 // chunks: the raw chunk sum goes to A.chunk[ch] for k_toep_chunk_epilogue.
-template <int N2>
+template <int N2, int BD = FftSize<N2>::TPL * kLines>
 HQS_DEV double toep_rows_adj_item(const ToepArgs& A, int iy, int ch, float2* __restrict__ out,
                                   const float2* __restrict__ pvec, float a, float b, int mode,
                                   float2* s) {
@@ -127,8 +129,8 @@ HQS_DEV double toep_rows_adj_item(const ToepArgs& A, int iy, int ch, float2* __r
     const int pst = blockDim.x / lines;
     const int l = threadIdx.x % lines, p0 = threadIdx.x / lines;
     const float2* src = A.T + (int64_t)iy * N2 * L + l0 + l;
-    constexpr int TPL = FftSize<N2>::TPL;
-    if (lines == kLines) {
+    constexpr int TPL = BD / kLines;
+    if (lines == kLines && (int)blockDim.x == BD) {
         unrolled<N2 / TPL, TPL>(p0, [&](int p) { s[p * kLines + l] = __ldcg(src + (int64_t)p * L); });
     } else if (p0 < pst) {
         for (int p = p0; p < N2; p += pst) s[p * kLines + l] = __ldcg(src + (int64_t)p * L);

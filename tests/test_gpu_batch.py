@@ -1,0 +1,93 @@
+"""Batched persistent HQS over slices of uneven size, coil count and
+trajectory: every slice must match the FP64 oracle's annealed HQS, and the
+graph replay must reproduce the direct launch bit for bit."""
+import numpy as np
+import pytest
+
+import synth
+from helpers import make_plan, quantised, rel, to_dev, to_host
+from oracle import hqs as ohqs
+from oracle import nufft, toeplitz
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def hq():
+    import paper_2411_01955_gb300 as m
+    return m
+
+
+def slice_cases():
+    return [
+        dict(n=64, L=3, W=4, traj=synth.traj_radial(24, 128), seed=1),
+        dict(n=128, L=20, W=6, traj=synth.traj_spiral(12, 1024, 128), seed=2),   # two coil chunks
+        dict(n=64, L=8, W=6, traj=synth.traj_spiral(8, 512, 64), seed=3),
+        dict(n=128, L=5, W=4, traj=synth.traj_radial(40, 256), seed=4),
+    ]
+
+
+def build(cases):
+    out = []
+    for c in cases:
+        case = quantised(dict(n=c["n"], L=c["L"], W=c["W"], sigma=2.0, x=synth.phantom(c["seed"], c["n"]),
+                              smaps=synth.coil_maps(c["seed"], c["n"], c["L"]), traj=c["traj"]))
+        plan, _, _ = make_plan(case)
+        y = nufft.forward(case["x"], case["smaps"], case["traj"], case["W"], case["sigma"])
+        y = (y + 0.01 * np.sqrt(np.mean(np.abs(y) ** 2)) *
+             synth.complex_noise(c["seed"], y.shape)).astype(np.complex64).astype(np.complex128)
+        out.append((case, plan, y))
+    return out
+
+
+def test_batched_hqs_matches_oracle_per_slice_and_graph_replay():
+    slices = build(slice_cases())
+    K, cg = 3, 3
+    mu = np.array([0.1, 0.03, 0.01], dtype=np.float32)
+    sigma = mu.copy()
+    batch = hq().Batch([p for _, p, _ in slices], max_outer=8)
+    ys = [to_dev(y) for _, _, y in slices]
+    xs = [torch.zeros((c["n"], c["n"]), dtype=torch.complex64, device="cuda") for c, _, _ in slices]
+    batch.run(ys, xs, mu, sigma, cg_iters=cg, use_graph=False)
+    res = batch.status()
+    got = [to_host(x) for x in xs]
+    rng = np.random.default_rng(0)
+    tols = []
+    for (case, plan, y), g, r in zip(slices, got, res):
+        n = case["n"]
+        c = toeplitz.kernel(case["traj"], n, n)
+        Kh, lam = toeplitz.khat(c), toeplitz.chan_symbol(c, n, n)
+        b0 = nufft.adjoint(y, case["smaps"], case["traj"], case["W"], case["sigma"])
+        AHA = lambda v: toeplitz.normal(v, case["smaps"], Kh)
+        want, _, _ = ohqs.hqs(AHA, b0, np.zeros((n, n)), mu.astype(np.float64), sigma.astype(np.float64),
+                              K, cg_iters=cg, lam=lam)
+        b0p = b0 * (1 + 2.0 ** -24 * rng.normal(size=b0.shape))
+        pert, _, _ = ohqs.hqs(AHA, b0p, np.zeros((n, n)), mu.astype(np.float64), sigma.astype(np.float64),
+                              K, cg_iters=cg, lam=lam)
+        tol = max(1e-5, 4 * rel(pert, want))
+        tols.append(tol)
+        assert rel(g, want) <= tol, (n, case["L"], rel(g, want), tol)
+        assert 0.0 < r < 1.0
+    # graph replay (recorded on the first call, replayed on the second) = direct launch
+    for x in xs:
+        x.zero_()
+    batch.run(ys, xs, mu, sigma, cg_iters=cg, use_graph=True)
+    for x in xs:
+        x.zero_()
+    batch.run(ys, xs, mu, sigma, cg_iters=cg, use_graph=True)
+    torch.cuda.synchronize()
+    for x, g, tol in zip(xs, got, tols):
+        d = to_host(x)
+        # A^H y uses float atomics: replays agree to rounding (amplified by the
+        # annealed loop like any input perturbation), not bit for bit
+        assert rel(d, g) <= tol
+
+
+def test_batched_hqs_rejects_unsupported_metric():
+    slices = build(slice_cases()[:1])
+    batch = hq().Batch([p for _, p, _ in slices], max_outer=4)
+    ys = [to_dev(y) for _, _, y in slices]
+    xs = [torch.zeros((64, 64), dtype=torch.complex64, device="cuda")]
+    with pytest.raises(hq().HqsError) as ei:
+        batch.run(ys, xs, [0.1], [0.1], c1=-0.5)
+    assert ei.value.status == hq().HQS_ERR_UNSUPPORTED
