@@ -294,11 +294,17 @@ HQS_API const char* hqs_status_string(int status);
 
 /* Tuning knobs (no counterpart in the paper), set per plan by the autotuner:
  *   HQS_TUNE_FUSED_GRID  cap on the persistent solve's CTAs (0 = all resident)
- *   HQS_TUNE_PC_LINES    preconditioner rows/columns per work item (1..16) */
+ *   HQS_TUNE_PC_LINES    preconditioner rows/columns per work item (1..16)
+ *   HQS_TUNE_SPREAD_TILE spreading tile edge (8, 16 or 32): re-bins the
+ *                        plan's points (hqs_plan_retile on the default stream) */
 #define HQS_TUNE_FUSED_GRID   1
 #define HQS_TUNE_PC_LINES     2
 #define HQS_TUNE_SPREAD_TILE  3
 HQS_API int hqs_plan_set_tuning(hqs_plan plan, int key, int value);
+/* Re-sorts the plan's points into tile x tile spreading bins (8, 16, 32);
+ * BLOCKING on `stream`.  The result of hqs_adjoint does not depend on the tile
+ * beyond float rounding order. */
+HQS_API int hqs_plan_retile(hqs_plan plan, int tile, void* stream);
 
 /* Diagnostics (no counterpart in the paper): phase trace of the persistent
  * solve.  enable = 1 allocates a trace buffer on the plan (returns 0); later

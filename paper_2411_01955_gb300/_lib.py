@@ -81,6 +81,7 @@ _SIGS = {
     "hqs_power_iteration": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_void_p]),
     "hqs_status_string": (C.c_char_p, [C.c_int]),
     "hqs_plan_set_tuning": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "hqs_plan_retile": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "hqs_net_create": (C.c_int, [C.POINTER(C.c_void_p)]),
     "hqs_net_destroy": (None, [C.c_void_p]),
     "hqs_net_num_params": (C.c_int, []),
@@ -324,6 +325,10 @@ def debug_phase_trace(plan: Plan, enable=False, stream=None):
     if rc < 0:
         raise HqsError(rc, "hqs_debug_phase_trace")
     return [buf[i] for i in range(rc)]
+
+
+def plan_retile(plan: Plan, tile: int, stream=None):
+    _check(library().hqs_plan_retile(plan.handle, int(tile), _stream(stream)), "hqs_plan_retile")
 
 
 def plan_set_tuning(plan: Plan, key: int, value: int):

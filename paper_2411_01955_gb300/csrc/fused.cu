@@ -460,7 +460,7 @@ extern "C" int hqs_plan_set_tuning(hqs_plan p, int key, int value) {
             p->pc_lines = value;
             return HQS_OK;
         case HQS_TUNE_SPREAD_TILE:
-            return HQS_ERR_UNSUPPORTED;   // fixed at plan creation
+            return hqs_plan_retile(p, value, nullptr);
         default:
             return HQS_ERR_INVALID_ARG;
     }

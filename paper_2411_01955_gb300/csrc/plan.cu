@@ -481,6 +481,96 @@ extern "C" int hqs_plan_create(hqs_plan* out, const float* traj, int64_t M, int 
     return HQS_OK;
 }
 
+// Re-binning of the already sorted points for another spreading tile size.
+__global__ void k_rebin(const int4* __restrict__ pts, int M, int G, int W, int TB, int nbx,
+                        int* __restrict__ bin, int* __restrict__ counts) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= M) return;
+    const int4 pt = pts[j];
+    int cx = pt.x + W / 2, cy = pt.y + W / 2;
+    if (cx >= G) cx -= G;
+    if (cy >= G) cy -= G;
+    const int b = (cy / TB) * nbx + cx / TB;
+    bin[j] = b;
+    atomicAdd(&counts[b], 1);
+}
+
+__global__ void k_rebin_scatter(const int4* __restrict__ pts, const int* __restrict__ perm,
+                                const int* __restrict__ bin, int M, int* __restrict__ cursor,
+                                int4* __restrict__ pts_out, int* __restrict__ perm_out) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= M) return;
+    const int pos = atomicAdd(&cursor[bin[j]], 1);
+    pts_out[pos] = pts[j];
+    perm_out[pos] = perm[j];
+}
+
+extern "C" int hqs_plan_retile(hqs_plan p, int tile, void* stream) {
+    if (!p || (tile != 8 && tile != 16 && tile != 32) || p->G % tile != 0 || tile + p->W - 1 > p->G)
+        return HQS_ERR_INVALID_ARG;
+    const size_t smem = (size_t)(tile + p->W - 1) * (tile + p->W - 1) * p->LC * sizeof(float2) +
+                        HQS_SPREAD_MAXPTS * (2 * p->W * sizeof(float) + sizeof(int2));
+    if (smem > 220 * 1024) return HQS_ERR_UNSUPPORTED;
+    if (tile == p->tile) return HQS_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int M = (int)p->M;
+    const int nbx = p->G / tile, nbins = nbx * nbx;
+    int *bin = nullptr, *counts = nullptr, *perm2 = nullptr;
+    int4* pts2 = nullptr;
+    int4* subs2 = nullptr;
+    int rc = HQS_OK;
+    do {
+        const int Mp = std::max(M, 1);
+        if (cudaMalloc(&bin, Mp * sizeof(int)) || cudaMalloc(&counts, nbins * sizeof(int)) ||
+            cudaMalloc(&perm2, Mp * sizeof(int)) || cudaMalloc(&pts2, Mp * sizeof(int4))) {
+            rc = HQS_ERR_OOM;
+            break;
+        }
+        if (cudaMemsetAsync(counts, 0, nbins * sizeof(int), s)) { rc = HQS_ERR_CUDA; break; }
+        if (M > 0) k_rebin<<<ceil_div(M, 256), 256, 0, s>>>(p->pts, M, p->G, p->W, tile, nbx, bin, counts);
+        std::vector<int> hc(nbins), offs(nbins);
+        if (cudaMemcpyAsync(hc.data(), counts, nbins * sizeof(int), cudaMemcpyDeviceToHost, s) ||
+            cudaStreamSynchronize(s)) { rc = HQS_ERR_CUDA; break; }
+        std::vector<int4> subs;
+        int acc = 0;
+        for (int b = 0; b < nbins; ++b) {
+            offs[b] = acc;
+            for (int st = 0; st < hc[b]; st += HQS_SPREAD_MAXPTS)
+                subs.push_back(make_int4(b, acc + st, std::min(HQS_SPREAD_MAXPTS, hc[b] - st), 0));
+            acc += hc[b];
+        }
+        if (cudaMalloc(&subs2, std::max<size_t>(subs.size(), 1) * sizeof(int4))) { rc = HQS_ERR_OOM; break; }
+        if ((!subs.empty() && cudaMemcpyAsync(subs2, subs.data(), subs.size() * sizeof(int4),
+                                              cudaMemcpyHostToDevice, s)) ||
+            cudaMemcpyAsync(counts, offs.data(), nbins * sizeof(int), cudaMemcpyHostToDevice, s)) {
+            rc = HQS_ERR_CUDA;
+            break;
+        }
+        if (M > 0) k_rebin_scatter<<<ceil_div(M, 256), 256, 0, s>>>(p->pts, p->perm, bin, M, counts, pts2, perm2);
+        if (M > 0 && (cudaMemcpyAsync(p->pts, pts2, M * sizeof(int4), cudaMemcpyDeviceToDevice, s) ||
+                      cudaMemcpyAsync(p->perm, perm2, M * sizeof(int), cudaMemcpyDeviceToDevice, s))) {
+            rc = HQS_ERR_CUDA;
+            break;
+        }
+        if (cudaStreamSynchronize(s)) { rc = HQS_ERR_CUDA; break; }
+        // swap in the new sub-problem list (owned by the plan's allocation list)
+        for (auto& v : p->allocs)
+            if (v == p->subs) v = subs2;
+        cudaFree(p->subs);
+        p->subs = subs2;
+        subs2 = nullptr;
+        p->nsub = (int)subs.size();
+        p->tile = tile;
+        p->nbx = nbx;
+    } while (0);
+    cudaFree(bin);
+    cudaFree(counts);
+    cudaFree(perm2);
+    cudaFree(pts2);
+    cudaFree(subs2);
+    return rc;
+}
+
 extern "C" void hqs_plan_destroy(hqs_plan plan) { plan_free(plan); }
 
 extern "C" int hqs_plan_get_info(hqs_plan p, hqs_plan_info* info) {

@@ -1,6 +1,7 @@
 """Batched persistent HQS over slices of uneven size, coil count and
 trajectory: every slice must match the FP64 oracle's annealed HQS, and the
-graph replay must reproduce the direct launch bit for bit."""
+graph replay must reproduce the direct launch within the same derived bound
+(the adjoint's float atomics make replays differ in rounding order only)."""
 import numpy as np
 import pytest
 
