@@ -12,6 +12,7 @@ ellipse phantoms, Gaussian-bump coil maps, spiral trajectory).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B] [--impl ours|reference]
   python bench.py --workload batch64     # 64 uneven slices, batched HQS 20 x 5
+  python bench.py --workload mixed320    # A^H A and DC solves at FP32 / BF16x3 / FP16x3
 
 The batch64 workload runs annealed HQS (20 outer x 5 CG iterations, Gaussian
 smoothing denoiser) over 64 slices of mixed size {256, 320, 384}^2, 8-20
@@ -56,7 +57,7 @@ def parse():
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="fused", choices=["fused", "plain"])
-    ap.add_argument("--workload", default="dc320", choices=["dc320", "batch64"])
+    ap.add_argument("--workload", default="dc320", choices=["dc320", "batch64", "mixed320"])
     return ap.parse_args()
 
 
@@ -466,6 +467,96 @@ def run_batch64(args, rank, world, dist):
     print(json.dumps(line), flush=True)
 
 
+def run_mixed320(args, rank, world, dist):
+    """A^H A applies/s and DC solves/s (plain PCG, DC preconditioner, 1e-4) of
+    the 320^2 x 16-coil workload with the Toeplitz passes in FP32 (in-house
+    FFTs) and as BF16x3 / FP16x3 tensor-core DFT-GEMMs."""
+    import torch
+    import paper_2411_01955_gb300 as hq
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    B = args.batch
+    n, L, traj_np, sl = make_slices(B, rank)
+    traj = torch.from_numpy(traj_np).cuda()
+    plans, rhss, xs = [], [], []
+    for s in sl:
+        plan = hq.plan_create(traj, n, n, torch.from_numpy(s["smaps"].astype(np.complex64)).cuda(), 6, 2.0)
+        x = torch.from_numpy(s["x"].astype(np.complex64)).cuda()
+        y = torch.empty((L, traj.shape[0]), dtype=torch.complex64, device="cuda")
+        hq.forward(plan, x, y)
+        rhs = torch.empty_like(x)
+        hq.adjoint(plan, y, rhs)
+        plans.append(plan)
+        rhss.append(rhs)
+        xs.append(torch.zeros_like(x))
+    stream = torch.cuda.current_stream()
+    outs = [torch.empty_like(x) for x in xs]
+
+    def timed(fn, steps):
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        if dist is not None:
+            tt = torch.tensor([ms], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ms = float(tt.item())
+        return ms
+
+    res = {}
+    clk = ClockSampler(dev)
+    clk.start()
+    for name, prec in (("fp32", hq.HQS_PREC_FP32), ("bf16x3", hq.HQS_PREC_BF16X3), ("fp16x3", hq.HQS_PREC_FP16X3)):
+        def applies():
+            for i in range(B):
+                hq.toeplitz_normal(plans[i], rhss[i], outs[i], precision=prec)
+
+        def solves():
+            for i in range(B):
+                hq.dc_solve(plans[i], 1.0, MU, rhss[i], xs[i], max_iter=MAX_ITER, rel_tol=TOL, precision=prec,
+                            mode=hq.HQS_SOLVE_X0_ZERO, want_info=False)
+        iters = [hq.dc_solve(plans[i], 1.0, MU, rhss[i], xs[i], max_iter=MAX_ITER, rel_tol=TOL, precision=prec,
+                             mode=hq.HQS_SOLVE_X0_ZERO).iterations for i in range(B)]
+        for _ in range(max(args.warmup, 3)):
+            applies()
+        ms_a = timed(applies, args.steps)
+        solves()
+        ms_s = timed(solves, max(1, args.steps // 2))
+        res[name] = {"aha_applies_per_s": B * args.steps * world / (ms_a / 1e3),
+                     "aha_us": ms_a * 1e3 / (B * args.steps),
+                     "dc_solves_per_s": B * max(1, args.steps // 2) * world / (ms_s / 1e3),
+                     "mean_cg_iterations": float(np.mean(iters))}
+    clocks = clk.stop()
+    if rank != 0:
+        return
+    # tensor-pipe work of one mixed A^H A: 4 real GEMMs x 3 products
+    gemm_flops = 3 * 2 * (L * n * 4 * n * 2 * n + L * 2 * n * 4 * n * 2 * n + L * 2 * n * 2 * n * 4 * n
+                          + n * L * 2 * n * 4 * n)
+    peak = 1880.3
+    for name in ("bf16x3", "fp16x3"):
+        res[name]["tensor_tflops"] = gemm_flops / (res[name]["aha_us"] * 1e-6) / 1e12
+        res[name]["tensor_frac_of_measured_bf16_peak"] = res[name]["tensor_tflops"] / peak
+    line = {
+        "metric": "A^H A applies/s and DC solves/s at 320^2, 16 coils: FP32 vs BF16x3 / FP16x3 DFT-GEMM",
+        "value": res["bf16x3"]["dc_solves_per_s"], "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16x3", "data": "synthetic (seeded ellipse phantoms, Gaussian-bump coil maps, VD spiral)",
+        "config": {"workload": "320x320, 16 coils, spiral 16x2048, KB W=6, sigma=2, mu=1e-2, rel. residual 1e-4, "
+                               "plain PCG with DC preconditioner",
+                   "batch_per_gpu": B, "l2": "inputs larger than L2 (batch of distinct slices), no flush"},
+        "precisions": res, "gemm_flops_per_aha": gemm_flops,
+        "gpu_launches_per_mixed_aha": 6, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def fft_flops(N):
     return 5.0 * N * math.log2(N)
 
@@ -497,6 +588,8 @@ def main():
         run_reference(args, rank, world)
     elif args.workload == "batch64":
         run_batch64(args, rank, world, dist)
+    elif args.workload == "mixed320":
+        run_mixed320(args, rank, world, dist)
     else:
         run_ours(args, rank, world, dist)
     if dist is not None:

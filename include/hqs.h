@@ -146,7 +146,10 @@ HQS_API int hqs_adjoint_axpy(hqs_plan plan, const hqs_c64* y, float c, const hqs
 /* out = A^H A x (Sec. 3.4, A = F_Omega (x) S_l) through the exact 2N
  * circulant embedding of F^H F; never touches the trajectory.
  * precision: HQS_PREC_FP32 (in-house FFTs) or HQS_PREC_BF16X3 / _FP16X3
- * (FFT stages as split hi/lo tensor-core DFT-GEMMs, fp32 accumulation). */
+ * (the four pruned 2N-point DFT passes as tcgen05 GEMMs on split hi/lo
+ * 16-bit operands, fp32 accumulation; needs n % 64 == 0, n <= 512, coils
+ * <= 32, else HQS_ERR_UNSUPPORTED).  The first mixed-precision call of a plan
+ * allocates its workspace and synchronises `stream`. */
 HQS_API int hqs_toeplitz_normal(hqs_plan plan, const hqs_c64* x, hqs_c64* out,
                         int precision, void* stream);
 
@@ -187,7 +190,8 @@ HQS_API int hqs_precond_apply_noalloc(const hqs_c64* r, const float* lam, int n,
  * solution on exit.  Stops when ||r|| <= rel_tol ||rhs|| or after max_iter
  * (<= HQS_MAX_ITERS) iterations; rel_tol = 0 runs exactly max_iter.
  * b must be > 0.  precond: HQS_PRECOND_*; mode: HQS_SOLVE_*; precision:
- * HQS_PREC_*.  If info != NULL the call synchronises `stream` and fills it,
+ * HQS_PREC_* (the mixed precisions run with HQS_SOLVE_PLAIN and the DC or no
+ * preconditioner; inner products and norms stay fp64).  If info != NULL the call synchronises `stream` and fills it,
  * returning HQS_ERR_NOT_CONVERGED / HQS_ERR_BREAKDOWN when applicable; with
  * info == NULL it only enqueues (capturable in a CUDA graph when mode is
  * HQS_SOLVE_FUSED) and the outcome is read later with hqs_last_solve_info. */
@@ -305,6 +309,20 @@ HQS_API int hqs_plan_set_tuning(hqs_plan plan, int key, int value);
  * BLOCKING on `stream`.  The result of hqs_adjoint does not depend on the tile
  * beyond float rounding order. */
 HQS_API int hqs_plan_retile(hqs_plan plan, int tile, void* stream);
+
+/* Per-pass view of the mixed-precision A^H A (HQS_PREC_BF16X3 / _FP16X3):
+ * runs the DFT-GEMM passes 1..stage on x (device, n x n) and writes the
+ * intermediate, unscaled, as complex64 to out (device):
+ *   stage 1: [L][n][2n]   row DFT of pad(S_l x)             (y, kx)
+ *   stage 2: [L][2n][2n]  Khat . 2D DFT of pad(S_l x)        (ky, kx)
+ *   stage 3: [L][n][2n]   column IDFT of stage 2, rows y < n (y, kx)
+ *   stage 4: [n][n]       A^H A x (same as hqs_toeplitz_normal)
+ * DFTs unnormalised with e^{-i} forward; the inverse carries 1/(2n) per axis.
+ * The first mixed-precision call of a plan allocates its workspace and
+ * synchronises `stream`.  HQS_ERR_UNSUPPORTED unless n % 64 == 0, n <= 512
+ * and coils <= 32. */
+HQS_API int hqs_debug_toeplitz_stage(hqs_plan plan, const hqs_c64* x, int precision, int stage,
+                                     hqs_c64* out, void* stream);
 
 /* Diagnostics (no counterpart in the paper): phase trace of the persistent
  * solve.  enable = 1 allocates a trace buffer on the plan (returns 0); later

@@ -82,6 +82,7 @@ _SIGS = {
     "hqs_status_string": (C.c_char_p, [C.c_int]),
     "hqs_plan_set_tuning": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "hqs_plan_retile": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "hqs_debug_toeplitz_stage": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
     "hqs_net_create": (C.c_int, [C.POINTER(C.c_void_p)]),
     "hqs_net_destroy": (None, [C.c_void_p]),
     "hqs_net_num_params": (C.c_int, []),
@@ -325,6 +326,15 @@ def debug_phase_trace(plan: Plan, enable=False, stream=None):
     if rc < 0:
         raise HqsError(rc, "hqs_debug_phase_trace")
     return [buf[i] for i in range(rc)]
+
+
+def toeplitz_stage(plan: Plan, x, precision: int, stage: int, out, stream=None):
+    """Intermediate of the mixed-precision A^H A after DFT-GEMM pass `stage`
+    (1..3, complex64, natural layout; 4 = the result)."""
+    _check(library().hqs_debug_toeplitz_stage(plan.handle, _ptr(x, torch.complex64, "x"), int(precision),
+                                              int(stage), _ptr(out, torch.complex64, "out"),
+                                              _stream(stream)), "hqs_debug_toeplitz_stage")
+    return out
 
 
 def plan_retile(plan: Plan, tile: int, stream=None):

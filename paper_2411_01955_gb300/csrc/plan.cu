@@ -278,6 +278,7 @@ static void plan_free(hqs_plan_s* p) {
     int cur = -1;
     cudaGetDevice(&cur);
     if (cur != p->device) cudaSetDevice(p->device);
+    mixed_free(p);
     for (void* v : p->allocs) cudaFree(v);
     if (p->trace) cudaFree(p->trace);
     if (p->h_cg) cudaFreeHost(p->h_cg);

@@ -83,12 +83,14 @@ struct hqs_plan_s {
     unsigned* barrier = nullptr; // grid barrier words for the persistent solve
     unsigned long long* trace = nullptr;  // optional phase trace of the persistent solve
     struct hqs_net_s* net = nullptr;      // learned preconditioner (not owned)
+    struct hqs_mixed_s* mixed = nullptr;  // tensor-core Toeplitz workspace (built on first use)
 
     size_t bytes = 0;
     std::vector<void*> allocs;
 };
 
 const float2* plan_twiddles(const hqs_plan_s* p, int N);
+void mixed_free(hqs_plan_s* p);
 
 // launchers implemented in the kernel translation units
 int launch_fwd(hqs_plan_s* p, const float2* x, float2* y, cudaStream_t s);

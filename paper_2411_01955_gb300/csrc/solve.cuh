@@ -28,11 +28,14 @@ int launch_toeplitz_ex(hqs_plan_s* p, const float2* src, float2* pvec, int fuse,
                        const float2* pmul, float a, float b, int mode, double* part,
                        const CgScalars* cg, cudaStream_t st);
 int launch_toeplitz_mixed(hqs_plan_s* p, const float2* x, float2* out, int precision, cudaStream_t st);
+int launch_toeplitz_mixed_ex(hqs_plan_s* p, const float2* x, float2* out, const float2* pmul, float a, float b,
+                             int mode, double* part, int precision, cudaStream_t st);
+int mixed_partial_count(const hqs_plan_s* p);
 int launch_precond_ex(hqs_plan_s* p, float a, float b, const float2* r, float2* z, bool rows_done,
                       const CgScalars* cg, double* part, cudaStream_t st);
 
 int pcg_plain(hqs_plan_s* p, float a, float b, const float2* rhs, float2* x, int max_iter,
-              double rel_tol, int precond, bool x0_zero, cudaStream_t st);
+              double rel_tol, int precond, bool x0_zero, cudaStream_t st, int precision = HQS_PREC_FP32);
 int pcg_fused(hqs_plan_s* p, float a, float b, const float2* rhs, float2* x, int max_iter,
               double rel_tol, int precond, int precision, bool x0_zero, cudaStream_t st);
 int fcg_learned(hqs_plan_s* p, float a, float b, const float2* rhs, float2* x, int max_iter,

@@ -306,8 +306,26 @@ extern "C" int hqs_toeplitz_normal(hqs_plan p, const hqs_c64* x, hqs_c64* out, i
 
 // ------------------------------------------------------- plain PCG driver
 // One launch per stage; the host reads the stop flag after every iteration.
+// H p with the CG epilogue (q = a A^H A p + b p, partials of <p, q>); FP32
+// in-house FFTs, or the tensor-core DFT-GEMM passes for the mixed precisions
+// (p = z + beta p then runs as its own kernel).  Returns the partial count.
+static int toep_apply(hqs_plan_s* p, int precision, const float2* src, float2* pvec, int fuse, float2* out,
+                      const float2* pmul, float a, float b, double* part, const CgScalars* cg,
+                      cudaStream_t st, int* nparts) {
+    if (precision == HQS_PREC_FP32) {
+        *nparts = toep_partial_count(p);
+        return launch_toeplitz_ex(p, src, pvec, fuse, out, pmul, a, b, 1, part, cg, st);
+    }
+    if (fuse) {
+        k_cg_pupdate<<<std::min(ceil_div(p->n * p->n, 256), 1024), 256, 0, st>>>(src, pvec, p->n * p->n, cg);
+        src = pvec;
+    }
+    *nparts = mixed_partial_count(p);
+    return launch_toeplitz_mixed_ex(p, src, out, pmul, a, b, 1, part, precision, st);
+}
+
 int pcg_plain(hqs_plan_s* p, float a, float b, const float2* rhs, float2* x, int max_iter,
-              double rel_tol, int precond, bool x0_zero, cudaStream_t st) {
+              double rel_tol, int precond, bool x0_zero, cudaStream_t st, int precision) {
     const int n = p->n, count = n * n;
     const int nb_vec = std::min(ceil_div(count, 256), HQS_MAX_BLOCKS);
     double* part = p->partials;
@@ -321,9 +339,10 @@ int pcg_plain(hqs_plan_s* p, float a, float b, const float2* rhs, float2* x, int
     const float2* zsrc = dc ? p->cg_z : p->cg_r;
 
     k_cg_setup<<<1, 1, 0, st>>>(p->cg, max_iter, rel_tol);
+    int nparts = 0;
     // q = H x (skipped for a zero start)
     if (!x0_zero)
-        HQS_TRY_RC(launch_toeplitz_ex(p, x, nullptr, 0, p->cg_q, x, a, b, 1, nullptr, nullptr, st));
+        HQS_TRY_RC(toep_apply(p, precision, x, nullptr, 0, p->cg_q, x, a, b, nullptr, nullptr, st, &nparts));
     k_cg_init_r<<<nb_vec, 256, 0, st>>>(rhs, x0_zero ? nullptr : p->cg_q, p->cg_r, x, count, P_RR, P_BB);
     k_cg_scalar<<<1, 256, 0, st>>>(p->cg, part, CG_INIT, nb_vec, rz_scale, 0, p->hist);
     if (dc) HQS_TRY_RC(launch_precond_ex(p, a, b, p->cg_r, p->cg_z, false, p->cg, P_RZ, st));
@@ -335,8 +354,8 @@ int pcg_plain(hqs_plan_s* p, float a, float b, const float2* rhs, float2* x, int
         HQS_CUDA_TRY(cudaStreamSynchronize(st));
         if (p->h_cg->done) break;
         // p = z + beta p; q = H p; <p, q>
-        HQS_TRY_RC(launch_toeplitz_ex(p, zsrc, p->cg_p, 1, p->cg_q, p->cg_p, a, b, 1, P_PQ, p->cg, st));
-        k_cg_scalar<<<1, 256, 0, st>>>(p->cg, part, CG_ALPHA, toep_partial_count(p), rz_scale, 0, p->hist);
+        HQS_TRY_RC(toep_apply(p, precision, zsrc, p->cg_p, 1, p->cg_q, p->cg_p, a, b, P_PQ, p->cg, st, &nparts));
+        k_cg_scalar<<<1, 256, 0, st>>>(p->cg, part, CG_ALPHA, nparts, rz_scale, 0, p->hist);
         k_cg_update<<<nb_vec, 256, 0, st>>>(x, p->cg_r, p->cg_p, p->cg_q, count, P_RR, p->cg);
         k_cg_scalar<<<1, 256, 0, st>>>(p->cg, part, CG_RES, nb_vec, rz_scale, 0, p->hist);
         if (dc) HQS_TRY_RC(launch_precond_ex(p, a, b, p->cg_r, p->cg_z, false, p->cg, P_RZ, st));
@@ -395,10 +414,10 @@ extern "C" int hqs_dc_solve(hqs_plan p, float a, float b, const hqs_c64* rhs, hq
     if (precond == HQS_PRECOND_LEARNED) {
         if (precision != HQS_PREC_FP32) return HQS_ERR_UNSUPPORTED;
         rc = fcg_learned(p, a, b, r, xx, max_iter, rel_tol, x0_zero, st);
-    } else if (mode == HQS_SOLVE_FUSED || precision != HQS_PREC_FP32) {
+    } else if (mode == HQS_SOLVE_FUSED) {
         rc = pcg_fused(p, a, b, r, xx, max_iter, rel_tol, precond, precision, x0_zero, st);
     } else {
-        rc = pcg_plain(p, a, b, r, xx, max_iter, rel_tol, precond, x0_zero, st);
+        rc = pcg_plain(p, a, b, r, xx, max_iter, rel_tol, precond, x0_zero, st, precision);
     }
     if (rc != HQS_OK) return rc;
     if (info) return read_solve_info(p, info, st);
