@@ -47,6 +47,9 @@ UNIT = "solves/s"
 MU = 1e-2
 TOL = 1e-4
 MAX_ITER = 200
+# DRAM bytes (read + write) of one k_pcg_persistent<640,320> launch (one 36-iteration
+# solve), from the ncu capture summarised in profiles/pcg_persistent_320x16.md.
+PERSISTENT_TRAFFIC_BYTES = 16413184 + 2091008
 
 
 def parse():
@@ -333,7 +336,7 @@ def run_ours(args, rank, world, dist):
         "speedup_vs_plain_pcg": value / plain_value,
         "mean_cg_iterations": mean_iters,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": PERSISTENT_TRAFFIC_BYTES,
                      "kernel": "k_pcg_persistent<640,320>",
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock (unit counts and clocks)"},
         "cpu_baseline": {"value": cpu_value, "unit": UNIT, "cores": threads_used(), "kind": "oracle",

@@ -18,8 +18,12 @@ namespace hqs {
 
 constexpr float kSqrtHalf = 0.70710678118654752440f;
 // Shared-memory stride between positions of a line: a compile-time constant
-// keeps the per-element address arithmetic out of the register budget.
-constexpr int kLines = 16;
+// keeps the per-element address arithmetic out of the register budget.  It
+// is also the coil-chunk size of the FFT passes (lines per CTA).
+#ifndef HQS_KLINES
+#define HQS_KLINES 16
+#endif
+constexpr int kLines = HQS_KLINES;
 
 template <int R, bool INV> struct Dft;
 

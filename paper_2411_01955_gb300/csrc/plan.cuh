@@ -6,7 +6,10 @@
 #include "common.cuh"
 
 #define HQS_MAX_W 8
-#define HQS_MAX_LC 16          // coils per chunk in the FFT passes
+#ifndef HQS_KLINES
+#define HQS_KLINES 16
+#endif
+#define HQS_MAX_LC HQS_KLINES  // coils per chunk in the FFT passes
 #define HQS_MAX_BLOCKS 2048    // partial-sum slots per reduction (and >= 3 x 256 for the FCG dots)
 #define HQS_SPREAD_MAXPTS 256  // points per spreading sub-problem
 #define HQS_TRACE_MAX 4096     // phase-trace stamps kept per persistent solve

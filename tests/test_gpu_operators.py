@@ -338,3 +338,31 @@ def test_power_iteration_matches_oracle():
                                    iters=200, rtol=1e-9)
     got = hq().power_iteration(plan, iters=200)
     assert abs(got / want - 1) < 1e-3
+
+
+@pytest.mark.parametrize("grid", [0, 37, 100])
+def test_fused_line_balanced_passes(grid):
+    """16 coils: the persistent solve deals (row, coil) and (column, coil)
+    lines to the CTAs in contiguous ranges that straddle rows and columns
+    (uneven for 37 and 100 CTAs); it must follow the oracle's recursion."""
+    case = quantised(dict(synth.odd_case(3, n=64, L=16, M=1500, W=6)))
+    plan, _, _ = make_plan(case)
+    hq().plan_set_tuning(plan, hq().HQS_TUNE_FUSED_GRID, grid)
+    Kh, lam = oracle_toeplitz(case)
+    n, mu = case["n"], 1e-2
+    rhs = nufft.adjoint(case["noise"], case["smaps"], case["traj"], case["W"], case["sigma"])
+    rhs = rhs.astype(np.complex64).astype(np.complex128)
+    H = lambda v: toeplitz.normal(v, case["smaps"], Kh) + mu * v
+    Minv = lambda v: toeplitz.precond_apply(v, lam, 1.0, mu)
+    want, winfo = solvers.pcg(H, rhs, np.zeros((n, n)), Minv, max_iter=6, tol=0.0)
+    x = torch.zeros((n, n), dtype=torch.complex64, device="cuda")
+    info = hq().dc_solve(plan, 1.0, mu, to_dev(rhs), x, max_iter=6, rel_tol=0.0,
+                         mode=hq().HQS_SOLVE_FUSED)
+    assert info.iterations == 6 and info.status == 0
+    assert rel(to_host(x), want) <= TOL
+    assert np.allclose(np.array(info.history()), winfo["res_hist"], rtol=1e-4, atol=0)
+    xf = torch.zeros_like(x)
+    inf = hq().dc_solve(plan, 1.0, mu, to_dev(rhs), xf, max_iter=200, rel_tol=1e-4,
+                        mode=hq().HQS_SOLVE_FUSED | hq().HQS_SOLVE_X0_ZERO)
+    assert inf.status == 0
+    assert np.linalg.norm(rhs - H(to_host(xf))) / np.linalg.norm(rhs) <= 1.2e-4
