@@ -23,7 +23,7 @@
 using namespace hqs;
 
 #define HQS_BATCH_MAX 64
-#define HQS_BATCH_BD 512
+#define HQS_BATCH_BD 256
 #define HQS_BATCH_MAXR 24
 #define HQS_BATCH_Q 4
 
@@ -217,10 +217,12 @@ HQS_DEV void blur_tile(const BatchSlice& S, int tile, const float* g, int r, flo
     __syncthreads();
 }
 
-// smem: lines buffer [768][16] | row [384] | tw 2n [768] | tw n [384] | scalars
-constexpr size_t kBatchSmemF2 = (size_t)768 * kLines + 384 + 768 + 384;
+// smem: lines buffer [768][16] | row [384] | tw 2n [768]; the n-point twiddles
+// of the preconditioner FFTs are read from global memory (L1), which keeps two
+// CTAs resident per SM.
+constexpr size_t kBatchSmemF2 = (size_t)768 * kLines + 384 + 768;
 
-__global__ void __launch_bounds__(HQS_BATCH_BD, 1) k_hqs_batch(BatchArgs B) {
+__global__ void __launch_bounds__(HQS_BATCH_BD, 2) k_hqs_batch(BatchArgs B) {
     extern __shared__ float2 s[];
     __shared__ double red[33];
     __shared__ double acc[2][HQS_BATCH_MAX];
@@ -228,8 +230,7 @@ __global__ void __launch_bounds__(HQS_BATCH_BD, 1) k_hqs_batch(BatchArgs B) {
     __shared__ double rzs[HQS_BATCH_MAX], alphas[HQS_BATCH_MAX], betas[HQS_BATCH_MAX];
     __shared__ int sl_cache;
     const int ns = B.ns, G = gridDim.x, bid = blockIdx.x;
-    float2* twN = s + (size_t)768 * kLines + 384 + 768;
-    int cur_twn = -1;   // slice whose n-point twiddles are staged
+    const float2* twN = nullptr;   // n-point twiddles of the current slice (global)
 #define BB_BARRIER()                                \
     do {                                            \
         if (!grid_barrier(B.bar, B.err)) return;    \
@@ -244,13 +245,7 @@ __global__ void __launch_bounds__(HQS_BATCH_BD, 1) k_hqs_batch(BatchArgs B) {
             __VA_ARGS__;                                                                   \
         }                                                                                  \
     }
-#define STAGE_TWN(S, si)                                                                  \
-    if (cur_twn != (si)) {                                                                \
-        __syncthreads();                                                                  \
-        for (int i_ = threadIdx.x; i_ < (S).A.n; i_ += blockDim.x) twN[i_] = (S).twN[i_]; \
-        __syncthreads();                                                                  \
-        cur_twn = (si);                                                                   \
-    }
+#define STAGE_TWN(S, si) twN = (S).twN;
 #define CLEAR_ACC()                                                      \
     for (int i_ = threadIdx.x; i_ < 2 * HQS_BATCH_MAX; i_ += blockDim.x) \
         (&acc[0][0])[i_] = 0.0;                                          \
@@ -483,6 +478,7 @@ struct hqs_batch_s {
     std::vector<const void*> key;  // y / x pointers the graph was recorded with
     int key_K = -1, key_k0 = -1, key_cg = -1;
     float key_c0 = 0.f;
+    std::vector<float2*> chunks;   // per-slice coil-chunk partial sums
 };
 
 static void batch_free(hqs_batch_s* b) {
@@ -502,6 +498,7 @@ static void batch_free(hqs_batch_s* b) {
     cudaFreeHost(b->h_mu);
     cudaFreeHost(b->h_taps);
     cudaFreeHost(b->h_radius);
+    for (float2* c : b->chunks) cudaFree(c);
     delete b;
 }
 
@@ -533,6 +530,20 @@ extern "C" int hqs_batch_create(hqs_batch* out, hqs_plan* plans, int n, int max_
         hqs_plan_s* p = plans[i];
         BatchSlice& S = hs[i];
         S.A = toep_args(p);
+        // coil chunk: as many lines as fill the CTA at this FFT size (16 lines of
+        // 640 points, 8 of 512 or 768), chunks of equal size
+        const int tpl = dispatch_fft_size(p->n2, [&]<int NN>() { return FftSize<NN>::TPL; });
+        const int lcmax = std::max(1, std::min(kLines, HQS_BATCH_BD / tpl));
+        const int nch = ceil_div(p->L, lcmax);
+        S.A.nchunk = nch;
+        S.A.LC = ceil_div(p->L, nch);
+        S.A.chunk = nullptr;
+        if (nch > 1) {
+            float2* cb = nullptr;
+            if (cudaMalloc(&cb, (size_t)nch * p->n * p->n * sizeof(float2))) return fail(HQS_ERR_OOM);
+            b->chunks.push_back(cb);
+            S.A.chunk = cb;
+        }
         S.twN = plan_twiddles(p, p->n);
         S.lam = p->lam;
         S.b0 = p->img_b0;
@@ -543,8 +554,8 @@ extern "C" int hqs_batch_create(hqs_batch* out, hqs_plan* plans, int n, int max_
         S.p = p->cg_p;
         S.q = p->cg_q;
         S.pcb = p->pc_buf;
-        const int cnt[BL_N] = {p->n * p->nchunk, 2 * p->n * p->nchunk, ceil_div(p->n, HQS_BATCH_Q), p->n,
-                               ceil_div(p->n, 32) * ceil_div(p->n, 32), p->nchunk > 1 ? p->n : 0};
+        const int cnt[BL_N] = {p->n * nch, 2 * p->n * nch, ceil_div(p->n, HQS_BATCH_Q), p->n,
+                               ceil_div(p->n, 32) * ceil_div(p->n, 32), nch > 1 ? p->n : 0};
         for (int l = 0; l < BL_N; ++l) off[(size_t)l * (n + 1) + i + 1] = off[(size_t)l * (n + 1) + i] + cnt[l];
     }
     const size_t sm = kBatchSmemF2 * sizeof(float2);

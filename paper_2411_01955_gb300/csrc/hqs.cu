@@ -138,7 +138,12 @@ extern "C" int hqs_run(hqs_plan p, const hqs_c64* y, hqs_c64* x, const float* mu
         }
         k_axpbypcz<<<nb, 256, 0, st>>>(p->img_rhs, p->img_b0, 1.0f, xx, m * c0, w, m * c1, count);
         HQS_CUDA_TRY(cudaMemcpyAsync(p->img_u, xx, (size_t)count * sizeof(float2), cudaMemcpyDeviceToDevice, st));
-        HQS_TRY_RC(pcg_plain(p, a, b, p->img_rhs, p->img_u, cg_iters, 0.0, HQS_PRECOND_DC, false, st));
+        // the persistent solve (one launch per outer step); per-stage launches for
+        // sizes it does not cover
+        int rc = pcg_fused(p, a, b, p->img_rhs, p->img_u, cg_iters, 0.0, HQS_PRECOND_DC, HQS_PREC_FP32, false, st);
+        if (rc == HQS_ERR_INVALID_ARG || rc == HQS_ERR_UNSUPPORTED)
+            rc = pcg_plain(p, a, b, p->img_rhs, p->img_u, cg_iters, 0.0, HQS_PRECOND_DC, false, st);
+        HQS_TRY_RC(rc);
         const int drc = denoiser(user, reinterpret_cast<const hqs_c64*>(p->img_u), x, n, n, sigma[k], stream);
         if (drc != 0) return HQS_ERR_CALLBACK;
     }
