@@ -37,6 +37,10 @@ namespace {
 constexpr int kBM = 128;           // GEMM rows per tile = TMEM lanes
 constexpr int kBK = 64;            // 16-bit elements per k-block (one 128-byte swizzle row)
 constexpr int kThreads = 192;      // warp 0 TMA, warp 1 MMA + TMEM owner, warps 2-5 epilogue
+constexpr int kEpiWarps = 4;
+constexpr uint32_t kTmemCols = 512;   // two accumulator buffers of 256 columns
+constexpr uint32_t kAccStride = 256;
+constexpr int kCorrOff = 128;         // FP16: correction accumulator (tiles of <= 128 columns)
 constexpr float kLoScale = 2048.f;       // FP16 lo parts are stored x 2^11
 constexpr long long kWaitCycles = 2000000000LL;   // ~1 s at 2 GHz
 constexpr size_t kSmemLimit = 232448;
@@ -48,6 +52,7 @@ struct MixedArgs {
     int cb;                 // complex columns per N tile; the tile is [Re cb | Im cb]
     int BN;                 // = 2 cb
     int M, KB, stages;
+    int MT, NT;             // tiles along M and N (persistent tile loop)
     uint16_t* out_hi;       // next pass's operand
     uint16_t* out_lo;
     const float* khat;      // S2: [n2][n2] (kx-major) scaled by 1/kp
@@ -93,7 +98,6 @@ template <bool F16> HQS_DEV void acc_ld16(uint32_t tl, int col, int corr_off, fl
         for (int i = 0; i < 16; ++i) v[i] = fmaf(c[i], 1.f / kLoScale, v[i]);
     }
 }
-template <bool F16> constexpr uint32_t tmem_cols() { return F16 ? 512u : 256u; }
 
 // ------------------------------------------------------------ the GEMM pass
 template <int STAGE, bool F16>
@@ -105,8 +109,8 @@ HQS_DEV void pass_epilogue(const MixedArgs& P, uint32_t tl, int m, int nt, int l
         const float f = P.kp / input_scale(P.amax);
         for (int w = 0; w < cb; w += 16) {
             float re[16], im[16];
-            acc_ld16<F16>(tl, w, 256, re);
-            acc_ld16<F16>(tl, cb + w, 256, im);
+            acc_ld16<F16>(tl, w, kCorrOff, re);
+            acc_ld16<F16>(tl, cb + w, kCorrOff, im);
             const int x0 = nt * cb + w;
             float2 acc[16];
 #pragma unroll
@@ -136,7 +140,7 @@ HQS_DEV void pass_epilogue(const MixedArgs& P, uint32_t tl, int m, int nt, int l
     } else {
         for (int w = 0; w < P.BN; w += 16) {
             float v[16];
-            acc_ld16<F16>(tl, w, 256, v);
+            acc_ld16<F16>(tl, w, kCorrOff, v);
             if (!valid) continue;
             const int part = w >= cb ? 1 : 0;
             const int c0 = nt * cb + w - part * cb;
@@ -194,6 +198,10 @@ HQS_DEV void pass_epilogue(const MixedArgs& P, uint32_t tl, int m, int nt, int l
     }
 }
 
+// Persistent: one CTA per SM walks the tiles t = blockIdx.x + i gridDim.x
+// (N tile fastest, so CTAs running together share A rows in L2).  The
+// shared-memory ring continues across tiles, and the accumulator is double
+// buffered in TMEM, so the epilogue of tile i overlaps the MMAs of tile i+1.
 template <int STAGE, bool F16>
 __global__ void __launch_bounds__(kThreads, 1)
     k_dft_gemm(const __grid_constant__ CUtensorMap tA_hi, const __grid_constant__ CUtensorMap tA_lo,
@@ -207,22 +215,27 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int ST = P.stages;
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + ST * stage_bytes);
     uint64_t* empty = full + ST;
-    uint64_t* accf = empty + ST;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accf + 1);
+    uint64_t* tfull = empty + ST;     // [2] accumulator buffer ready for the epilogue
+    uint64_t* tempty = tfull + 2;     // [2] accumulator buffer drained by the epilogue
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
     __shared__ int s_fail;
+    const volatile int* fail = &s_fail;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nt = blockIdx.x, m0 = blockIdx.y * kBM, n0 = nt * P.BN;
+    const int tiles = P.MT * P.NT;
     if (threadIdx.x == 0) {
         for (int s = 0; s < ST; ++s) {
             tc::mbar_init(&full[s], 1);
             tc::mbar_init(&empty[s], 1);
         }
-        tc::mbar_init(accf, 1);
+        for (int b = 0; b < 2; ++b) {
+            tc::mbar_init(&tfull[b], 1);
+            tc::mbar_init(&tempty[b], kEpiWarps);
+        }
         s_fail = 0;
         tc::fence_mbar_init();
     }
-    if (warp == 1) tc::tmem_alloc(tmem_slot, tmem_cols<F16>());
+    if (warp == 1) tc::tmem_alloc(tmem_slot, kTmemCols);
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
@@ -230,72 +243,97 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     if (warp == 0) {
         if (lane == 0) {
-            int issued = 0;
-            for (int kb = 0; kb < P.KB; ++kb) {
-                const int s = kb % ST;
-                if (kb >= ST && !tc::mbar_wait(&empty[s], ((kb / ST) - 1) & 1, kWaitCycles)) {
-                    atomicOr(P.err, HQS_DEVERR_TIMEOUT);
-                    s_fail = 1;
-                    break;
+            int c = 0;
+            for (int t = blockIdx.x; t < tiles && !*fail; t += gridDim.x) {
+                const int m0 = (t / P.NT) * kBM, n0 = (t % P.NT) * P.BN;
+                for (int kb = 0; kb < P.KB; ++kb, ++c) {
+                    const int s = c % ST;
+                    if (c >= ST && !tc::mbar_wait(&empty[s], ((c / ST) - 1) & 1, kWaitCycles, fail)) {
+                        atomicOr(P.err, HQS_DEVERR_TIMEOUT);
+                        s_fail = 1;
+                        break;
+                    }
+                    uint8_t* st = smem + s * stage_bytes;
+                    tc::mbar_expect_tx(&full[s], stage_bytes);
+                    tc::tma_load_2d(st, &tA_hi, &full[s], kb * kBK, m0);
+                    tc::tma_load_2d(st + a_bytes, &tA_lo, &full[s], kb * kBK, m0);
+                    tc::tma_load_2d(st + 2 * a_bytes, &tB_hi, &full[s], kb * kBK, n0);
+                    tc::tma_load_2d(st + 2 * a_bytes + b_bytes, &tB_lo, &full[s], kb * kBK, n0);
                 }
-                uint8_t* st = smem + s * stage_bytes;
-                tc::mbar_expect_tx(&full[s], stage_bytes);
-                tc::tma_load_2d(st, &tA_hi, &full[s], kb * kBK, m0);
-                tc::tma_load_2d(st + a_bytes, &tA_lo, &full[s], kb * kBK, m0);
-                tc::tma_load_2d(st + 2 * a_bytes, &tB_hi, &full[s], kb * kBK, n0);
-                tc::tma_load_2d(st + 2 * a_bytes + b_bytes, &tB_lo, &full[s], kb * kBK, n0);
-                ++issued;
             }
             // on failure, let the copies in flight land before the CTA leaves
-            if (s_fail)
-                for (int kb = max(0, issued - ST); kb < issued; ++kb)
-                    tc::mbar_wait(&full[kb % ST], (kb / ST) & 1, kWaitCycles);
+            if (*fail)
+                for (int k = max(0, c - ST); k < c; ++k) tc::mbar_wait(&full[k % ST], (k / ST) & 1, kWaitCycles);
         }
     } else if (warp == 1) {
         if (lane == 0) {
             const uint32_t idesc = tc::idesc_f16(kBM, P.BN, F16);
-            for (int kb = 0; kb < P.KB; ++kb) {
-                const int s = kb % ST;
-                if (!tc::mbar_wait(&full[s], (kb / ST) & 1, kWaitCycles)) {
+            int c = 0, i = 0;
+            for (int t = blockIdx.x; t < tiles && !*fail; t += gridDim.x, ++i) {
+                const int buf = i & 1;
+                if (i >= 2 && !tc::mbar_wait(&tempty[buf], ((i >> 1) - 1) & 1, kWaitCycles, fail)) {
                     atomicOr(P.err, HQS_DEVERR_TIMEOUT);
                     s_fail = 1;
                     break;
                 }
                 tc::fence_after();
-                const uint32_t base = tc::smem_u32(smem + s * stage_bytes);
-#pragma unroll
-                for (int kk = 0; kk < kBK / 16; ++kk) {
-                    const uint64_t ah = tc::sdesc_sw128(base + kk * 32);
-                    const uint64_t al = tc::sdesc_sw128(base + a_bytes + kk * 32);
-                    const uint64_t bh = tc::sdesc_sw128(base + 2 * a_bytes + kk * 32);
-                    const uint64_t bl = tc::sdesc_sw128(base + 2 * a_bytes + b_bytes + kk * 32);
-                    const uint32_t acc = (kb | kk) != 0 ? 1u : 0u;
-                    tc::mma_f16(tmem, ah, bh, idesc, acc);
-                    if constexpr (F16) {
-                        tc::mma_f16(tmem + 256, al, bh, idesc, acc);
-                        tc::mma_f16(tmem + 256, ah, bl, idesc, 1u);
-                    } else {
-                        tc::mma_f16(tmem, al, bh, idesc, 1u);
-                        tc::mma_f16(tmem, ah, bl, idesc, 1u);
+                const uint32_t d = tmem + buf * kAccStride;
+                for (int kb = 0; kb < P.KB; ++kb, ++c) {
+                    const int s = c % ST;
+                    if (!tc::mbar_wait(&full[s], (c / ST) & 1, kWaitCycles, fail)) {
+                        atomicOr(P.err, HQS_DEVERR_TIMEOUT);
+                        s_fail = 1;
+                        break;
                     }
+                    tc::fence_after();
+                    const uint32_t base = tc::smem_u32(smem + s * stage_bytes);
+#pragma unroll
+                    for (int kk = 0; kk < kBK / 16; ++kk) {
+                        const uint64_t ah = tc::sdesc_sw128(base + kk * 32);
+                        const uint64_t al = tc::sdesc_sw128(base + a_bytes + kk * 32);
+                        const uint64_t bh = tc::sdesc_sw128(base + 2 * a_bytes + kk * 32);
+                        const uint64_t bl = tc::sdesc_sw128(base + 2 * a_bytes + b_bytes + kk * 32);
+                        const uint32_t acc = (kb | kk) != 0 ? 1u : 0u;
+                        tc::mma_f16(d, ah, bh, idesc, acc);
+                        if constexpr (F16) {
+                            tc::mma_f16(d + kCorrOff, al, bh, idesc, acc);
+                            tc::mma_f16(d + kCorrOff, ah, bl, idesc, 1u);
+                        } else {
+                            tc::mma_f16(d, al, bh, idesc, 1u);
+                            tc::mma_f16(d, ah, bl, idesc, 1u);
+                        }
+                    }
+                    tc::mma_commit(&empty[s]);
                 }
-                tc::mma_commit(&empty[s]);
+                tc::mma_commit(&tfull[buf]);
             }
-            tc::mma_commit(accf);
         }
     } else {
-        const bool ok = tc::mbar_wait(accf, 0, kWaitCycles);
-        tc::fence_after();
-        if (!ok) atomicOr(P.err, HQS_DEVERR_TIMEOUT);
         const int q = warp & 3;   // TMEM lane quarter this warp may read
-        const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16);
-        if (__all_sync(0xffffffffu, ok)) pass_epilogue<STAGE, F16>(P, tl, m0 + 32 * q + lane, nt, lane);
+        int i = 0;
+        for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++i) {
+            const int buf = i & 1;
+            const bool ok = tc::mbar_wait(&tfull[buf], (i >> 1) & 1, kWaitCycles, fail);
+            if (!__all_sync(0xffffffffu, ok)) {
+                if (lane == 0) {
+                    atomicOr(P.err, HQS_DEVERR_TIMEOUT);
+                    s_fail = 1;
+                }
+                break;
+            }
+            tc::fence_after();
+            const uint32_t tl = tmem + buf * kAccStride + ((uint32_t)(32 * q) << 16);
+            pass_epilogue<STAGE, F16>(P, tl, (t / P.NT) * kBM + 32 * q + lane, t % P.NT, lane);
+            tc::fence_before();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&tempty[buf]);
+        }
     }
     tc::fence_before();
     __syncthreads();
     if (warp == 1) {
         tc::fence_after();
-        tc::tmem_dealloc(tmem, tmem_cols<F16>());
+        tc::tmem_dealloc(tmem, kTmemCols);
     }
 }
 
@@ -442,13 +480,14 @@ __global__ void k_mx_dump(const uint16_t* __restrict__ hi, const uint16_t* __res
 // ------------------------------------------------------------ plan workspace
 struct MixedPrec {
     bool ready = false;
+    int cb = 0, BN = 0;     // complex columns per N tile, tile width (2 cb)
     uint16_t *bf_hi = nullptr, *bf_lo = nullptr;   // F: [4n][2n]
     uint16_t *bg_hi = nullptr, *bg_lo = nullptr;   // G: [2n][4n]
     CUtensorMap maps[4][4];                         // [pass][A_hi, A_lo, B_hi, B_lo]
 };
 
 struct hqs_mixed_s {
-    int n = 0, n2 = 0, L = 0, Lp = 0, cb = 0, BN = 0;
+    int n = 0, n2 = 0, L = 0, Lp = 0;
     uint16_t* x_hi[4] = {nullptr, nullptr, nullptr, nullptr};   // operands of S1..S4
     uint16_t* x_lo[4] = {nullptr, nullptr, nullptr, nullptr};
     int64_t x_rows[4] = {0, 0, 0, 0};
@@ -536,9 +575,6 @@ int mixed_workspace_fill(hqs_plan_s* p, hqs_mixed_s* w, cudaStream_t st) {
     w->L = L;
     w->Lp = 1;
     while (w->Lp < L) w->Lp <<= 1;
-    w->cb = n / 4;
-    w->BN = n / 2;
-    if (pipeline_stages(w->BN) < 2) return HQS_ERR_UNSUPPORTED;
     const int n2 = w->n2;
     w->x_rows[0] = (int64_t)L * n;       w->x_k[0] = 2 * n;
     w->x_rows[1] = (int64_t)L * n2;      w->x_k[1] = 2 * n;
@@ -578,16 +614,24 @@ int mixed_precision_ready(hqs_plan_s* p, int pi, cudaStream_t st) {
     if (m.ready) return HQS_OK;
     const int n = w->n, n2 = w->n2;
     const bool f16 = pi == 1;
+    // widest N tile whose half divides n in multiples of 16: two accumulator
+    // buffers of 256 TMEM columns hold BN (BF16) or 2 BN (FP16: main + correction)
+    const int cbmax = f16 ? kCorrOff / 2 : (int)kAccStride / 2;
+    m.cb = 0;
+    for (int c = 16; c <= std::min(cbmax, n); c += 16)
+        if (n % c == 0) m.cb = c;
+    m.BN = 2 * m.cb;
+    if (m.cb == 0 || pipeline_stages(m.BN) < 2) return HQS_ERR_UNSUPPORTED;
     HQS_TRY_RC(ws_alloc(p, &m.bf_hi, (size_t)4 * n * 2 * n));
     HQS_TRY_RC(ws_alloc(p, &m.bf_lo, (size_t)4 * n * 2 * n));
     HQS_TRY_RC(ws_alloc(p, &m.bg_hi, (size_t)2 * n * 4 * n));
     HQS_TRY_RC(ws_alloc(p, &m.bg_lo, (size_t)2 * n * 4 * n));
     if (f16) {
-        k_mx_build_b<true><<<1024, 256, 0, st>>>(m.bf_hi, m.bf_lo, 0, n, w->cb);
-        k_mx_build_b<true><<<1024, 256, 0, st>>>(m.bg_hi, m.bg_lo, 1, n, w->cb);
+        k_mx_build_b<true><<<1024, 256, 0, st>>>(m.bf_hi, m.bf_lo, 0, n, m.cb);
+        k_mx_build_b<true><<<1024, 256, 0, st>>>(m.bg_hi, m.bg_lo, 1, n, m.cb);
     } else {
-        k_mx_build_b<false><<<1024, 256, 0, st>>>(m.bf_hi, m.bf_lo, 0, n, w->cb);
-        k_mx_build_b<false><<<1024, 256, 0, st>>>(m.bg_hi, m.bg_lo, 1, n, w->cb);
+        k_mx_build_b<false><<<1024, 256, 0, st>>>(m.bf_hi, m.bf_lo, 0, n, m.cb);
+        k_mx_build_b<false><<<1024, 256, 0, st>>>(m.bg_hi, m.bg_lo, 1, n, m.cb);
     }
     HQS_CUDA_TRY(cudaGetLastError());
     for (int s = 0; s < 4; ++s) {
@@ -595,9 +639,9 @@ int mixed_precision_ready(hqs_plan_s* p, int pi, cudaStream_t st) {
         HQS_TRY_RC(make_map(&m.maps[s][1], w->x_lo[s], w->x_rows[s], w->x_k[s], kBM, f16));
         const bool fmat = s < 2;
         HQS_TRY_RC(make_map(&m.maps[s][2], fmat ? m.bf_hi : m.bg_hi, fmat ? 4 * n : n2, fmat ? 2 * n : 4 * n,
-                            w->BN, f16));
+                            m.BN, f16));
         HQS_TRY_RC(make_map(&m.maps[s][3], fmat ? m.bf_lo : m.bg_lo, fmat ? 4 * n : n2, fmat ? 2 * n : 4 * n,
-                            w->BN, f16));
+                            m.BN, f16));
     }
     m.ready = true;
     return HQS_OK;
@@ -605,14 +649,17 @@ int mixed_precision_ready(hqs_plan_s* p, int pi, cudaStream_t st) {
 
 template <int STAGE, bool F16>
 int launch_pass(hqs_plan_s* p, const MixedPrec& m, MixedArgs P, int Nreal, cudaStream_t st) {
-    const size_t smem = (size_t)P.stages * stage_bytes(P.BN) + 1024 + 64 + (2 * P.stages + 1) * 8 + 16;
+    const size_t smem = (size_t)P.stages * stage_bytes(P.BN) + 1024 + (2 * P.stages + 4) * 8 + 64;
     HQS_CUDA_TRY(cudaFuncSetAttribute(k_dft_gemm<STAGE, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
-    const dim3 grid(Nreal / P.BN, ceil_div(P.M, kBM));
+    P.MT = ceil_div(P.M, kBM);
+    P.NT = Nreal / P.BN;
+    int nsm = 0;
+    HQS_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device));
+    const int grid = std::min(P.MT * P.NT, nsm);
     k_dft_gemm<STAGE, F16><<<grid, kThreads, smem, st>>>(m.maps[STAGE][0], m.maps[STAGE][1], m.maps[STAGE][2],
                                                           m.maps[STAGE][3], P);
     HQS_CUDA_TRY(cudaGetLastError());
-    (void)p;
     return HQS_OK;
 }
 
@@ -630,9 +677,9 @@ int run_passes(hqs_plan_s* p, const float2* x, float2* out, int upto, cudaStream
     P.n2 = n2;
     P.L = L;
     P.Lp = w->Lp;
-    P.cb = w->cb;
-    P.BN = w->BN;
-    P.stages = pipeline_stages(w->BN);
+    P.cb = m.cb;
+    P.BN = m.BN;
+    P.stages = pipeline_stages(m.BN);
     P.khat = w->khat;
     P.smaps = p->smaps;
     P.out = out;

@@ -33,12 +33,18 @@ HQS_DEV bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Waits for the phase with the given parity to complete; false after `limit` cycles.
-HQS_DEV bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit) {
+// Waits for the phase with the given parity to complete; false after `limit`
+// cycles, or as soon as *abort (a CTA-wide failure flag) is set.
+HQS_DEV bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit, const volatile int* abort = nullptr) {
     const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity))
+    while (!mbar_try_wait(bar, parity)) {
         if (clock64() - t0 > limit) return false;
+        if (abort && *abort) return false;
+    }
     return true;
+}
+HQS_DEV void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 // ---------------------------------------------------------------- TMA
