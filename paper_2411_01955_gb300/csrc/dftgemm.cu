@@ -36,8 +36,8 @@ namespace {
 
 constexpr int kBM = 128;           // GEMM rows per tile = TMEM lanes
 constexpr int kBK = 64;            // 16-bit elements per k-block (one 128-byte swizzle row)
-constexpr int kThreads = 192;      // warp 0 TMA, warp 1 MMA + TMEM owner, warps 2-5 epilogue
-constexpr int kEpiWarps = 4;
+constexpr int kThreads = 320;      // warp 0 TMA, warp 1 MMA + TMEM owner, warps 2-9 epilogue
+constexpr int kEpiWarps = 8;       // two per TMEM lane quarter, alternating 16-column chunks
 constexpr uint32_t kTmemCols = 512;   // two accumulator buffers of 256 columns
 constexpr uint32_t kAccStride = 256;
 constexpr int kCorrOff = 128;         // FP16: correction accumulator (tiles of <= 128 columns)
@@ -99,15 +99,37 @@ template <bool F16> HQS_DEV void acc_ld16(uint32_t tl, int col, int corr_off, fl
     }
 }
 
+// Transposing store of 16 accumulator columns: lanes 2k and 2k+1 hold two rows
+// that are adjacent elements of the destination, so the pair is written as one
+// 32-bit word per column (even lanes take even columns, odd lanes odd ones);
+// idx(i) is the element index of column i at the pair's even row.
+template <bool F16, class Idx>
+HQS_DEV void store_pairs(const float* v, int lane, uint16_t* __restrict__ hi, uint16_t* __restrict__ lo, Idx idx) {
+    const int odd = lane & 1;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const float send = odd ? v[2 * j] : v[2 * j + 1];
+        const float recv = __shfl_xor_sync(0xffffffffu, send, 1);
+        const float r0 = odd ? recv : v[2 * j];
+        const float r1 = odd ? v[2 * j + 1] : recv;
+        uint16_t h0, l0, h1, l1;
+        split16<F16>(r0, h0, l0);
+        split16<F16>(r1, h1, l1);
+        const size_t e = idx(2 * j + odd);
+        *reinterpret_cast<uint32_t*>(hi + e) = (uint32_t)h0 | ((uint32_t)h1 << 16);
+        *reinterpret_cast<uint32_t*>(lo + e) = (uint32_t)l0 | ((uint32_t)l1 << 16);
+    }
+}
+
 // ------------------------------------------------------------ the GEMM pass
 template <int STAGE, bool F16>
-HQS_DEV void pass_epilogue(const MixedArgs& P, uint32_t tl, int m, int nt, int lane) {
+HQS_DEV void pass_epilogue(const MixedArgs& P, uint32_t tl, int m, int nt, int lane, int h) {
     const int n = P.n, n2 = P.n2, cb = P.cb;
     const bool valid = m < P.M;
     if constexpr (STAGE == MX_S4) {
         const int Lp = P.Lp, y = m / Lp, l = m - y * Lp;
         const float f = P.kp / input_scale(P.amax);
-        for (int w = 0; w < cb; w += 16) {
+        for (int w = 16 * h; w < cb; w += 32) {
             float re[16], im[16];
             acc_ld16<F16>(tl, w, kCorrOff, re);
             acc_ld16<F16>(tl, cb + w, kCorrOff, im);
@@ -138,23 +160,18 @@ HQS_DEV void pass_epilogue(const MixedArgs& P, uint32_t tl, int m, int nt, int l
         }
         (void)lane;
     } else {
-        for (int w = 0; w < P.BN; w += 16) {
+        for (int w = 16 * h; w < P.BN; w += 32) {
             float v[16];
             acc_ld16<F16>(tl, w, kCorrOff, v);
-            if (!valid) continue;
+            if (!valid) continue;   // warp-uniform: M and the warp's 32 rows are multiples of 32
             const int part = w >= cb ? 1 : 0;
             const int c0 = nt * cb + w - part * cb;
             if constexpr (STAGE == MX_S1) {
-                // rows (l, y) -> next operand rows (l, kx), K = (part, y)
+                // rows (l, y) -> next operand rows (l, kx), K = (part, y); lanes 2k, 2k+1
+                // hold y, y+1 (a warp's 32 rows lie in one coil since 32 | n)
                 const int l = m / n, y = m - l * n;
-#pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const size_t idx = (size_t)(l * n2 + c0 + i) * (2 * n) + part * n + y;
-                    uint16_t h, o;
-                    split16<F16>(v[i], h, o);
-                    P.out_hi[idx] = h;
-                    P.out_lo[idx] = o;
-                }
+                store_pairs<F16>(v, lane, P.out_hi, P.out_lo,
+                                 [&](int i) { return (size_t)(l * n2 + c0 + i) * (2 * n) + part * n + (y & ~1); });
             } else if constexpr (STAGE == MX_S2) {
                 // * Khat[kx][ky], same rows (l, kx), K = (part, ky)
                 const int kx = m % n2;
@@ -183,16 +200,12 @@ HQS_DEV void pass_epilogue(const MixedArgs& P, uint32_t tl, int m, int nt, int l
                     dl[j] = make_uint4(b[0], b[1], b[2], b[3]);
                 }
             } else {
-                // rows (l, kx) -> next operand rows (y, l) (coil-padded to Lp), K = (part, kx)
+                // rows (l, kx) -> next operand rows (y, l) (coil-padded to Lp), K = (part, kx);
+                // lanes 2k, 2k+1 hold kx, kx+1
                 const int l = m / n2, kx = m - l * n2;
-#pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const size_t idx = (size_t)((c0 + i) * P.Lp + l) * (4 * n) + part * n2 + kx;
-                    uint16_t h, o;
-                    split16<F16>(v[i], h, o);
-                    P.out_hi[idx] = h;
-                    P.out_lo[idx] = o;
-                }
+                store_pairs<F16>(v, lane, P.out_hi, P.out_lo, [&](int i) {
+                    return (size_t)((c0 + i) * P.Lp + l) * (4 * n) + part * n2 + (kx & ~1);
+                });
             }
         }
     }
@@ -310,6 +323,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else {
         const int q = warp & 3;   // TMEM lane quarter this warp may read
+        const int h = (warp - 2) >> 2;   // which half of the 16-column chunks
         int i = 0;
         for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++i) {
             const int buf = i & 1;
@@ -323,7 +337,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             tc::fence_after();
             const uint32_t tl = tmem + buf * kAccStride + ((uint32_t)(32 * q) << 16);
-            pass_epilogue<STAGE, F16>(P, tl, (t / P.NT) * kBM + 32 * q + lane, t % P.NT, lane);
+            pass_epilogue<STAGE, F16>(P, tl, (t / P.NT) * kBM + 32 * q + lane, t % P.NT, lane, h);
             tc::fence_before();
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(&tempty[buf]);
