@@ -47,9 +47,10 @@ UNIT = "solves/s"
 MU = 1e-2
 TOL = 1e-4
 MAX_ITER = 200
-# DRAM bytes (read + write) of one k_pcg_persistent<640,320> launch (one 36-iteration
-# solve), from the ncu capture summarised in profiles/pcg_persistent_320x16.md.
-PERSISTENT_TRAFFIC_BYTES = 16413184 + 2091008
+# DRAM bytes (read + write) of one k_pcg_persistent<640,320> launch from an ncu
+# capture of the current kernel (profiles/pcg_persistent_320x16.md); None while
+# the kernel has changed since the last capture.
+PERSISTENT_TRAFFIC_BYTES = None
 
 
 def parse():

@@ -12,6 +12,8 @@
 // Forward uses exp(-2 pi i m / N), inverse its conjugate; neither scales.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace hqs {
@@ -248,6 +250,79 @@ HQS_DEV void fft_stage(float2* s, int t, bool act, const float2* __restrict__ tw
     __syncthreads();
 }
 
+// No-op marker for the I/O hooks of fft_stage_io.
+struct NoIO {};
+
+// fft_stage with I/O hooks for the first and last stage of a transform:
+//   FIRST and LD != NoIO: the stage reads its inputs through ld(pos) (global
+//     memory of this thread's line) instead of shared memory, so the caller's
+//     separate load pass and one barrier disappear;
+//   LAST and XF != NoIO: outputs pass through xf(pos, v) before the shared
+//     memory store (a pointwise multiply fused into the stage);
+//   LAST and STF != NoIO: outputs go to stf(pos, v) (global memory) instead of
+//     shared memory, with no barrier between the stage's loads and stores.
+template <int N, int E, int R, int P, bool INV, bool ZIN, bool HOUT, bool FIRST, bool LAST, class LD, class XF,
+          class STF>
+HQS_DEV void fft_stage_io(float2* s, int t, bool act, const float2* __restrict__ tw, LD& ld, XF& xf, STF& stf) {
+    constexpr int st = kLines;
+    constexpr int TPL = N / E;
+    constexpr int NB = N / R;
+    constexpr int BPT = E / R;
+    constexpr bool GIN = FIRST && !std::is_same_v<LD, NoIO>;
+    constexpr bool GOUT = LAST && !std::is_same_v<STF, NoIO>;
+    constexpr bool XOUT = LAST && !std::is_same_v<XF, NoIO>;
+    static_assert(E % R == 0, "radix must divide elements per thread");
+    static_assert(NB == TPL * BPT, "butterfly split");
+    static_assert(!ZIN || (P == 1 && R % 2 == 0), "zero-input pruning is for an even first stage");
+    static_assert(!HOUT || (P * R == N && R % 2 == 0), "half-output pruning is for an even last stage");
+    constexpr int RIN = ZIN ? R / 2 : R;
+    constexpr int ROUT = HOUT ? R / 2 : R;
+    float2 v[E];
+#pragma unroll
+    for (int b = 0; b < BPT; ++b) {
+        const int i = t + b * TPL;
+#pragma unroll
+        for (int r = 0; r < RIN; ++r) {
+            if constexpr (GIN) v[b * R + r] = ld(i + r * NB);
+            else v[b * R + r] = s[(i + r * NB) * st];
+        }
+    }
+    // in place through shared memory: every read lands before any write
+    if constexpr (!GIN && !GOUT) __syncthreads();
+    if (act) {
+#pragma unroll
+        for (int b = 0; b < BPT; ++b) {
+            const int i = t + b * TPL;
+            const int k = i % P;
+            if (P > 1) {
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    float2 w = tw[r * k * (N / (P * R))];
+                    if (INV) w.y = -w.y;
+                    v[b * R + r] = cmul(v[b * R + r], w);
+                }
+            }
+            if (ZIN)
+                DftHalfIn<R, INV>::run(&v[b * R]);
+            else
+                Dft<R, INV>::run(&v[b * R]);
+            const int j = (i - k) * R + k;
+#pragma unroll
+            for (int r = 0; r < ROUT; ++r) {
+                const int pos = j + r * P;
+                if constexpr (GOUT) {
+                    stf(pos, v[b * R + r]);
+                } else if constexpr (XOUT) {
+                    s[pos * st] = xf(pos, v[b * R + r]);
+                } else {
+                    s[pos * st] = v[b * R + r];
+                }
+            }
+        }
+    }
+    if constexpr (!GOUT) __syncthreads();
+}
+
 // Size table: elements per thread and radix sequence.
 template <int N> struct FftSize;
 
@@ -257,11 +332,19 @@ template <int N> struct FftSize;
         static constexpr int TPL = NN / EE;                                           \
         template <bool INV, bool ZIN, bool HOUT>                                      \
         HQS_DEV static void run(float2* s, int t, bool act, const float2* tw) {        \
+            NoIO ld, xf, stf;                                                         \
+            __VA_ARGS__                                                               \
+        }                                                                             \
+        template <bool INV, bool ZIN, bool HOUT, class LD, class XF, class STF>       \
+        HQS_DEV static void run_io(float2* s, int t, bool act, const float2* tw, LD& ld, \
+                                   XF& xf, STF& stf) {                                \
             __VA_ARGS__                                                               \
         }                                                                             \
     };
 
-#define ST(R, P) fft_stage<NN_, E_, R, P, INV, ZIN && (P == 1), HOUT && (P * R == NN_)>(s, t, act, tw);
+#define ST(R, P)                                                                              \
+    fft_stage_io<NN_, E_, R, P, INV, ZIN && (P == 1), HOUT && (P * R == NN_), P == 1, P * R == NN_>( \
+        s, t, act, tw, ld, xf, stf);
 
 #define NN_ 16
 #define E_ 4
@@ -336,6 +419,38 @@ HQS_DEV void block_fft(float2* s, int nlines, const float2* tw) {
     const int t = tid / lpg;
     const bool act = (ll < nlines) && (t < TPL);
     FftSize<N>::template run<INV, ZIN, HOUT>(s + (act ? ll : 0), act ? t : 0, act, tw);
+}
+
+// block_fft with I/O hooks (see fft_stage_io).  The hooks receive this
+// thread's line (line 0 for threads without a line, which read in-bounds data
+// and store nothing) and a position; ld(line, pos) feeds the first stage,
+// xf(line, pos, v) transforms the last stage's outputs before they go to
+// shared memory, stf(line, pos, v) takes them instead of shared memory.  With
+// a loader the caller need not synchronise before (nothing is read from
+// shared memory); with a store hook the routine ends without a barrier.
+template <int N, bool INV, bool ZIN, bool HOUT, class LD, class XF, class STF>
+HQS_DEV void block_fft_io(float2* s, int nlines, const float2* tw, LD&& ld, XF&& xf, STF&& stf) {
+    constexpr int TPL = FftSize<N>::TPL;
+    const int lpg = blockDim.x / TPL;
+    int tid;
+    asm volatile("mov.u32 %0, %%tid.x;" : "=r"(tid));
+    const int ll = tid % lpg;
+    const int t = tid / lpg;
+    const bool act = (ll < nlines) && (t < TPL);
+    const int line = act ? ll : 0;
+    auto bind_ld = [&]() {
+        if constexpr (std::is_same_v<std::decay_t<LD>, NoIO>) return NoIO{};
+        else return [&, line](int pos) { return ld(line, pos); };
+    }();
+    auto bind_xf = [&]() {
+        if constexpr (std::is_same_v<std::decay_t<XF>, NoIO>) return NoIO{};
+        else return [&, line](int pos, float2 v) { return xf(line, pos, v); };
+    }();
+    auto bind_st = [&]() {
+        if constexpr (std::is_same_v<std::decay_t<STF>, NoIO>) return NoIO{};
+        else return [&, line](int pos, float2 v) { stf(line, pos, v); };
+    }();
+    FftSize<N>::template run_io<INV, ZIN, HOUT>(s + line, act ? t : 0, act, tw, bind_ld, bind_xf, bind_st);
 }
 
 // Copies the N-point twiddle table into shared memory; the caller's barrier

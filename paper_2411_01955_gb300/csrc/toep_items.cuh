@@ -44,26 +44,14 @@ HQS_DEV void toep_rows_fwd_item(const ToepArgs& A, int iy, int ch, const float2*
     }
     const int l0 = ch * A.LC;
     const int lines = min(A.LC, L - l0);
-    const int pst = blockDim.x / lines;
-    const int l = threadIdx.x % lines, p0 = threadIdx.x / lines;
-    const float2* sm = A.smaps + (int64_t)iy * n * L + l0 + l;
+    const float2* sm = A.smaps + (int64_t)iy * n * L + l0;
+    float2* dst = A.T + (int64_t)iy * N2 * L + l0;
     __syncthreads();
-    // full chunk with the block size BD: n = N2/2 and pst = BD/16 are compile-time
-    constexpr int TPL = BD / kLines;
-    const bool full = lines == kLines && (int)blockDim.x == BD;
-    if (full) {
-        unrolled<N2 / 2 / TPL, TPL>(p0, [&](int p) { s[p * kLines + l] = cmul(sm[(int64_t)p * L], rowv[p]); });
-    } else if (p0 < pst) {
-        for (int p = p0; p < n; p += pst) s[p * kLines + l] = cmul(sm[(int64_t)p * L], rowv[p]);
-    }
-    __syncthreads();
-    block_fft<N2, false, true>(s, lines, tw);   // upper half is the zero padding
-    float2* dst = A.T + (int64_t)iy * N2 * L + l0 + l;
-    if (full) {
-        unrolled<N2 / TPL, TPL>(p0, [&](int p) { dst[(int64_t)p * L] = s[p * kLines + l]; });
-    } else if (p0 < pst) {
-        for (int p = p0; p < N2; p += pst) dst[(int64_t)p * L] = s[p * kLines + l];
-    }
+    // S_l v straight into the first radix stage (upper half is the zero
+    // padding), last stage straight to T
+    block_fft_io<N2, false, true, false>(
+        s, lines, tw, [&](int line, int p) { return cmul(sm[(int64_t)p * L + line], rowv[p]); }, NoIO{},
+        [&](int line, int p, float2 v) { dst[(int64_t)p * L + line] = v; });
     __syncthreads();
 }
 
@@ -74,32 +62,17 @@ HQS_DEV void toep_cols_item(const ToepArgs& A, int kx, int ch, float2* s) {
     const float2* tw = stage_twiddles<N2>(s + N2 * kLines + n, A.tw);
     const int l0 = ch * A.LC;
     const int lines = min(A.LC, L - l0);
-    const int pst = blockDim.x / lines;
-    const int l = threadIdx.x % lines, p0 = threadIdx.x / lines;
-    float2* col = A.T + (int64_t)kx * L + l0 + l;
+    float2* col = A.T + (int64_t)kx * L + l0;
     const int64_t rs = (int64_t)N2 * L;
-    constexpr int TPL = BD / kLines;
-    const bool full = lines == kLines && (int)blockDim.x == BD;
     const float* kh = A.khat + (int64_t)kx * N2;   // Khat stored transposed: column kx contiguous
-    if (full) {
-        unrolled<N2 / 2 / TPL, TPL>(p0, [&](int p) { s[p * kLines + l] = __ldcg(col + p * rs); });
-    } else if (p0 < pst) {
-        for (int p = p0; p < n; p += pst) s[p * kLines + l] = __ldcg(col + p * rs);
-    }
     __syncthreads();
-    block_fft<N2, false, true>(s, lines, tw);   // zero-padded upper half
-    if (full) {
-        unrolled<N2 / TPL, TPL>(p0, [&](int p) { s[p * kLines + l] = cscale(s[p * kLines + l], __ldg(kh + p)); });
-    } else if (p0 < pst) {
-        for (int p = p0; p < N2; p += pst) s[p * kLines + l] = cscale(s[p * kLines + l], __ldg(kh + p));
-    }
-    __syncthreads();
-    block_fft<N2, true, false, true>(s, lines, tw);   // only the first n rows are kept
-    if (full) {
-        unrolled<N2 / 2 / TPL, TPL>(p0, [&](int p) { col[p * rs] = s[p * kLines + l]; });
-    } else if (p0 < pst) {
-        for (int p = p0; p < n; p += pst) col[p * rs] = s[p * kLines + l];
-    }
+    // column straight into the first stage (zero-padded upper half), * Khat in
+    // the last forward stage, IFFT, first n rows straight back to T
+    block_fft_io<N2, false, true, false>(
+        s, lines, tw, [&](int line, int p) { return __ldcg(col + line + p * rs); },
+        [&](int, int p, float2 v) { return cscale(v, __ldg(kh + p)); }, NoIO{});
+    block_fft_io<N2, true, false, true>(s, lines, tw, NoIO{}, NoIO{},
+                                        [&](int line, int p, float2 v) { col[line + p * rs] = v; });
     __syncthreads();
 }
 
@@ -126,17 +99,11 @@ HQS_DEV double toep_rows_adj_item(const ToepArgs& A, int iy, int ch, float2* __r
     const float2* tw = stage_twiddles<N2>(s + N2 * kLines + n, A.tw);
     const int l0 = ch * A.LC;
     const int lines = min(A.LC, L - l0);
-    const int pst = blockDim.x / lines;
-    const int l = threadIdx.x % lines, p0 = threadIdx.x / lines;
-    const float2* src = A.T + (int64_t)iy * N2 * L + l0 + l;
-    constexpr int TPL = BD / kLines;
-    if (lines == kLines && (int)blockDim.x == BD) {
-        unrolled<N2 / TPL, TPL>(p0, [&](int p) { s[p * kLines + l] = __ldcg(src + (int64_t)p * L); });
-    } else if (p0 < pst) {
-        for (int p = p0; p < N2; p += pst) s[p * kLines + l] = __ldcg(src + (int64_t)p * L);
-    }
+    const float2* src = A.T + (int64_t)iy * N2 * L + l0;
     __syncthreads();
-    block_fft<N2, true, false, true>(s, lines, tw);   // only the first n columns are kept
+    // row straight from T into the first stage; only the first n columns are kept
+    block_fft_io<N2, true, false, true>(
+        s, lines, tw, [&](int line, int p) { return __ldcg(src + (int64_t)p * L + line); }, NoIO{}, NoIO{});
     const float2* sm = A.smaps + (int64_t)iy * n * L + l0;
     double part = 0.0;
     for (int ix = threadIdx.x; ix < n; ix += blockDim.x) {
