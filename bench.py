@@ -50,7 +50,7 @@ MAX_ITER = 200
 # DRAM bytes (read + write) of one k_pcg_persistent<640,320> launch from an ncu
 # capture of the current kernel (profiles/pcg_persistent_320x16.md); None while
 # the kernel has changed since the last capture.
-PERSISTENT_TRAFFIC_BYTES = None
+PERSISTENT_TRAFFIC_BYTES = 16408576 + 2208768
 
 
 def parse():

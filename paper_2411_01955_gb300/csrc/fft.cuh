@@ -423,7 +423,9 @@ HQS_DEV void block_fft(float2* s, int nlines, const float2* tw) {
 
 // block_fft with I/O hooks (see fft_stage_io).  The hooks receive this
 // thread's line (line 0 for threads without a line, which read in-bounds data
-// and store nothing) and a position; ld(line, pos) feeds the first stage,
+// and store nothing) and a position; ld(line, pos, act) feeds the first stage
+// (act false: a thread without a line, whose value is discarded, so a loader
+// with side effects must skip them),
 // xf(line, pos, v) transforms the last stage's outputs before they go to
 // shared memory, stf(line, pos, v) takes them instead of shared memory.  With
 // a loader the caller need not synchronise before (nothing is read from
@@ -440,7 +442,7 @@ HQS_DEV void block_fft_io(float2* s, int nlines, const float2* tw, LD&& ld, XF&&
     const int line = act ? ll : 0;
     auto bind_ld = [&]() {
         if constexpr (std::is_same_v<std::decay_t<LD>, NoIO>) return NoIO{};
-        else return [&, line](int pos) { return ld(line, pos); };
+        else return [&, line, act](int pos) { return ld(line, pos, act); };
     }();
     auto bind_xf = [&]() {
         if constexpr (std::is_same_v<std::decay_t<XF>, NoIO>) return NoIO{};

@@ -73,12 +73,14 @@ HQS_DEV void z_row(const FusedArgs& F, int iy, float2* s, const float2* twN, flo
         __syncthreads();
         return;
     }
-    for (int pos = threadIdx.x; pos < N; pos += blockDim.x) s[pos * kLines] = __ldcg(F.pcb + (int64_t)iy * N + pos);
-    __syncthreads();
-    block_fft<N, true>(s, 1, twN);
     const float sc = 1.0f / ((float)N * (float)N);
-    for (int ix = threadIdx.x; ix < n; ix += blockDim.x) zs[ix] = cscale(s[ix * kLines], sc);
+    const float2* row = F.pcb + (int64_t)iy * N;
     __syncthreads();
+    block_fft_io<N, true, false, false>(
+        s, 1, twN, [&](int, int pos, bool) { return __ldcg(row + pos); }, NoIO{},
+        [&](int, int pos, float2 v) { zs[pos] = cscale(v, sc); });
+    __syncthreads();
+    (void)n;
 }
 
 // Row block [r0, r0+Q): optional CG update, ||r||^2, FFT of the r rows -> pcb.
@@ -111,17 +113,11 @@ HQS_DEV double update_rows(const FusedArgs& F, int r0, float alpha, bool update,
         for (int e = threadIdx.x; e < lines * n; e += blockDim.x) body(e);
     }
     if (F.precond) {
+        // row FFTs, the last stage stores the spectra straight to pcb
         __syncthreads();
-        block_fft<N, false>(s, lines, twN);
-        auto st = [&](int e) {
-            const int q_ = e / N, pos = e - q_ * N;
-            F.pcb[(int64_t)(r0 + q_) * N + pos] = s[pos * kLines + q_];
-        };
-        if (lines == kLines) {
-            unrolled<kLines * N / BD, BD>(threadIdx.x, st);
-        } else {
-            for (int e = threadIdx.x; e < lines * N; e += blockDim.x) st(e);
-        }
+        block_fft_io<N, false, false, false>(
+            s, lines, twN, NoIO{}, NoIO{},
+            [&](int line, int pos, float2 v) { F.pcb[(int64_t)(r0 + line) * N + pos] = v; });
     }
     __syncthreads();
     return rr;

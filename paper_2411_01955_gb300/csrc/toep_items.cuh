@@ -50,7 +50,7 @@ HQS_DEV void toep_rows_fwd_item(const ToepArgs& A, int iy, int ch, const float2*
     // S_l v straight into the first radix stage (upper half is the zero
     // padding), last stage straight to T
     block_fft_io<N2, false, true, false>(
-        s, lines, tw, [&](int line, int p) { return cmul(sm[(int64_t)p * L + line], rowv[p]); }, NoIO{},
+        s, lines, tw, [&](int line, int p, bool) { return cmul(sm[(int64_t)p * L + line], rowv[p]); }, NoIO{},
         [&](int line, int p, float2 v) { dst[(int64_t)p * L + line] = v; });
     __syncthreads();
 }
@@ -69,7 +69,7 @@ HQS_DEV void toep_cols_item(const ToepArgs& A, int kx, int ch, float2* s) {
     // column straight into the first stage (zero-padded upper half), * Khat in
     // the last forward stage, IFFT, first n rows straight back to T
     block_fft_io<N2, false, true, false>(
-        s, lines, tw, [&](int line, int p) { return __ldcg(col + line + p * rs); },
+        s, lines, tw, [&](int line, int p, bool) { return __ldcg(col + line + p * rs); },
         [&](int, int p, float2 v) { return cscale(v, __ldg(kh + p)); }, NoIO{});
     block_fft_io<N2, true, false, true>(s, lines, tw, NoIO{}, NoIO{},
                                         [&](int line, int p, float2 v) { col[line + p * rs] = v; });
@@ -103,7 +103,7 @@ HQS_DEV double toep_rows_adj_item(const ToepArgs& A, int iy, int ch, float2* __r
     __syncthreads();
     // row straight from T into the first stage; only the first n columns are kept
     block_fft_io<N2, true, false, true>(
-        s, lines, tw, [&](int line, int p) { return __ldcg(src + (int64_t)p * L + line); }, NoIO{}, NoIO{});
+        s, lines, tw, [&](int line, int p, bool) { return __ldcg(src + (int64_t)p * L + line); }, NoIO{}, NoIO{});
     const float2* sm = A.smaps + (int64_t)iy * n * L + l0;
     double part = 0.0;
     for (int ix = threadIdx.x; ix < n; ix += blockDim.x) {
