@@ -130,19 +130,19 @@ HQS_DEV void pass_epilogue(const MixedArgs& P, uint32_t tl, int m, int nt, int l
         const int Lp = P.Lp, y = m / Lp, l = m - y * Lp;
         const float f = P.kp / input_scale(P.amax);
         for (int w = 16 * h; w < cb; w += 32) {
+            const int x0 = nt * cb + w;
+            // coil-map values first: their latency overlaps the TMEM loads
+            float2 sv[16];
+            const bool own = valid && l < P.L;
+#pragma unroll
+            for (int i = 0; i < 16; ++i)
+                sv[i] = own ? P.smaps[((size_t)y * n + x0 + i) * P.L + l] : make_float2(0.f, 0.f);
             float re[16], im[16];
             acc_ld16<F16>(tl, w, kCorrOff, re);
             acc_ld16<F16>(tl, cb + w, kCorrOff, im);
-            const int x0 = nt * cb + w;
             float2 acc[16];
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                acc[i] = make_float2(0.f, 0.f);
-                if (valid && l < P.L) {
-                    const float2 s = P.smaps[((size_t)y * n + x0 + i) * P.L + l];
-                    acc[i] = cmulc(s, make_float2(re[i], im[i]));
-                }
-            }
+            for (int i = 0; i < 16; ++i) acc[i] = cmulc(sv[i], make_float2(re[i], im[i]));
             for (int off = Lp >> 1; off > 0; off >>= 1) {
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
@@ -161,11 +161,18 @@ HQS_DEV void pass_epilogue(const MixedArgs& P, uint32_t tl, int m, int nt, int l
         (void)lane;
     } else {
         for (int w = 16 * h; w < P.BN; w += 32) {
+            const int part = w >= cb ? 1 : 0;
+            const int c0 = nt * cb + w - part * cb;
+            float4 k4[4];
+            if constexpr (STAGE == MX_S2) {
+                // Khat row values first: their latency overlaps the TMEM loads
+                const float4* kr = reinterpret_cast<const float4*>(P.khat + (size_t)(m % n2) * n2 + c0);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) k4[i] = valid ? __ldg(kr + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
             float v[16];
             acc_ld16<F16>(tl, w, kCorrOff, v);
             if (!valid) continue;   // warp-uniform: M and the warp's 32 rows are multiples of 32
-            const int part = w >= cb ? 1 : 0;
-            const int c0 = nt * cb + w - part * cb;
             if constexpr (STAGE == MX_S1) {
                 // rows (l, y) -> next operand rows (l, kx), K = (part, y); lanes 2k, 2k+1
                 // hold y, y+1 (a warp's 32 rows lie in one coil since 32 | n)
@@ -174,16 +181,13 @@ HQS_DEV void pass_epilogue(const MixedArgs& P, uint32_t tl, int m, int nt, int l
                                  [&](int i) { return (size_t)(l * n2 + c0 + i) * (2 * n) + part * n + (y & ~1); });
             } else if constexpr (STAGE == MX_S2) {
                 // * Khat[kx][ky], same rows (l, kx), K = (part, ky)
-                const int kx = m % n2;
-                const float4* kr = reinterpret_cast<const float4*>(P.khat + (size_t)kx * n2 + c0);
                 uint16_t hs[16], ls[16];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
-                    const float4 k4 = kr[i];
-                    split16<F16>(v[4 * i] * k4.x, hs[4 * i], ls[4 * i]);
-                    split16<F16>(v[4 * i + 1] * k4.y, hs[4 * i + 1], ls[4 * i + 1]);
-                    split16<F16>(v[4 * i + 2] * k4.z, hs[4 * i + 2], ls[4 * i + 2]);
-                    split16<F16>(v[4 * i + 3] * k4.w, hs[4 * i + 3], ls[4 * i + 3]);
+                    split16<F16>(v[4 * i] * k4[i].x, hs[4 * i], ls[4 * i]);
+                    split16<F16>(v[4 * i + 1] * k4[i].y, hs[4 * i + 1], ls[4 * i + 1]);
+                    split16<F16>(v[4 * i + 2] * k4[i].z, hs[4 * i + 2], ls[4 * i + 2]);
+                    split16<F16>(v[4 * i + 3] * k4[i].w, hs[4 * i + 3], ls[4 * i + 3]);
                 }
                 const size_t idx = (size_t)m * (4 * n) + part * n2 + c0;
                 uint4* dh = reinterpret_cast<uint4*>(P.out_hi + idx);
