@@ -118,6 +118,23 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# --------------------------------------------------------------- ranks
+def max_over_ranks(value: float, dist, device: str = "cuda") -> float:
+    """The slowest rank's time (every rank gets it); the value itself at N = 1."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, ms_max: float) -> float:
+    """Units all ranks processed (each rank the same number: weak scaling)
+    per second of the slowest rank."""
+    return units_per_rank * world / (ms_max / 1e3)
+
+
 # --------------------------------------------------------------- workload
 def make_slices(B, rank=0):
     import synth
@@ -240,11 +257,7 @@ def run_ours(args, rank, world, dist):
         e1.record(stream)
         barrier()
         ms = e0.elapsed_time(e1)
-        if dist is not None:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return max_over_ranks(ms, dist)
 
     # iteration counts and residuals (untimed)
     iters = []
@@ -261,7 +274,7 @@ def run_ours(args, rank, world, dist):
     clk.start()
     ms = timed(step, args.steps)
     clocks = clk.stop()
-    value = B * args.steps * world / (ms / 1e3)
+    value = whole_job_rate(B * args.steps, world, ms)
 
     # the dominant kernel: the persistent solve, timed alone on the launching stream
     e_solve = []
@@ -423,11 +436,7 @@ def run_batch64(args, rank, world, dist):
         e1.record(stream)
         barrier()
         ms = e0.elapsed_time(e1)
-        if dist is not None:
-            tt = torch.tensor([ms], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ms = float(tt.item())
-        return ms
+        return max_over_ranks(ms, dist)
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -436,7 +445,7 @@ def run_batch64(args, rank, world, dist):
     clk.start()
     ms = timed(step, args.steps)
     clocks = clk.stop()
-    value = len(sl) * args.steps * world / (ms / 1e3)
+    value = whole_job_rate(len(sl) * args.steps, world, ms)
 
     def per_slice():
         for i, p in enumerate(plans):
@@ -508,11 +517,7 @@ def run_mixed320(args, rank, world, dist):
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
-        if dist is not None:
-            tt = torch.tensor([ms], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ms = float(tt.item())
-        return ms
+        return max_over_ranks(ms, dist)
 
     res = {}
     clk = ClockSampler(dev)
