@@ -47,6 +47,20 @@ UNIT = "solves/s"
 MU = 1e-2
 TOL = 1e-4
 MAX_ITER = 200
+# Measured copy bandwidth of the GB300s (MEASURED_PEAKS.json, hbm_gbs).
+HBM_PEAK_GBS = 6768.8
+# Algorithmic bytes of one forward / adjoint at 320^2, 16 coils, G = 640, M = 32768
+# (complex64 = 8 B): forward = x + S (fused apodise/coil/pad/row-FFT pass) + grid
+# write, column FFT read + write, interpolation read + points + y write;
+# adjoint = y + points + grid write (spreading), column IFFT read + write of the
+# n kept rows, row IFFT read + S + x write.
+_G2L = 640 * 640 * 16 * 8
+_ROWS = 320 * 640 * 16 * 8
+_S = 320 * 320 * 16 * 8
+_Y = 32768 * 16 * 8
+_PTS = 32768 * 16 + 32768 * 4
+FWD_BYTES = (320 * 320 * 8 + _S + _ROWS) + (_ROWS + _G2L) + (_G2L + _PTS + _Y)
+ADJ_BYTES = (_Y + _PTS + _G2L) + (_G2L + _ROWS) + (_ROWS + _S + 320 * 320 * 8)
 # DRAM bytes (read + write) of one k_pcg_persistent<640,320> launch from an ncu
 # capture of the current kernel (profiles/pcg_persistent_320x16.md); None while
 # the kernel has changed since the last capture.
@@ -307,6 +321,26 @@ def run_ours(args, rank, world, dist):
     ms_aha = timed(applies, reps)
     aha_per_s = B * reps * world / (ms_aha / 1e3)
 
+    # forward A and adjoint A^H of the NUFFT (each slice its own plan and data)
+    xs_img = [torch.from_numpy(s["x"].astype(np.complex64)).cuda() for s in sl]
+    ys_out = [torch.empty_like(y) for y in ys]
+
+    def forwards():
+        for i in range(B):
+            hq.forward(plans[i], xs_img[i], ys_out[i])
+
+    def adjoints():
+        for i in range(B):
+            hq.adjoint(plans[i], ys[i], outs[i])
+    forwards()
+    adjoints()
+    ms_fwd = timed(forwards, reps)
+    ms_adj = timed(adjoints, reps)
+    fwd_per_s = B * reps * world / (ms_fwd / 1e3)
+    adj_per_s = B * reps * world / (ms_adj / 1e3)
+    # measured FP32 FMA throughput: the ALU roofline's denominator
+    fp32_peak = hq.probe_fp32_peak()
+
     # end to end through the public API with host buffers: H2D of y, D2H of x
     y_host = [y.cpu().pin_memory() for y in ys]
     x_host = [torch.empty(x.shape, dtype=x.dtype).pin_memory() for x in xs]
@@ -332,7 +366,8 @@ def run_ours(args, rank, world, dist):
     flops_launch = flops_iter * mean_iters
     achieved = flops_launch / (solve_ms / 1e3) / 1e12
     sm_max = clocks.get("sm_max_mhz") or 2070.0
-    peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+    nominal = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+    peak = fp32_peak
     cpu_t_it, cpu_plan = cpu_oracle_sample(1)
     cpu_value = 1.0 / (cpu_t_it * mean_iters)
     launches_per_solve = 4   # spread, column IFFT, row IFFT + axpy, persistent solve
@@ -346,13 +381,22 @@ def run_ours(args, rank, world, dist):
                    "batch_per_gpu": B, "solver": args.mode, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (batch of distinct slices), no flush"},
         "aha_applies_per_s": aha_per_s,
+        "forward_per_s": fwd_per_s,
+        "adjoint_per_s": adj_per_s,
+        "nufft_hbm": {"unit": "GB/s", "peak": HBM_PEAK_GBS,
+                      "forward": FWD_BYTES * fwd_per_s / world / 1e9,
+                      "adjoint": ADJ_BYTES * adj_per_s / world / 1e9,
+                      "bytes": "per operator, algorithmic bytes of the multi-pass design (x or y, S, the "
+                               "oversampled grid written and read per pass, points)"},
         "plain_pcg_solves_per_s": plain_value,
         "speedup_vs_plain_pcg": value / plain_value,
         "mean_cg_iterations": mean_iters,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": PERSISTENT_TRAFFIC_BYTES,
                      "kernel": "k_pcg_persistent<640,320>",
-                     "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock (unit counts and clocks)"},
+                     "peak_source": "measured: FP32 FMA probe (hqs_probe_fp32_peak, 8 independent chains per "
+                                    "thread, full occupancy) on this GPU after the timed region",
+                     "nominal": nominal},
         "cpu_baseline": {"value": cpu_value, "unit": UNIT, "cores": threads_used(), "kind": "oracle",
                          "sample": f"1 FP64 oracle PCG iteration (+ initial residual) on one slice, "
                                    f"scaled to {mean_iters:.1f} iterations per solve; oracle plan "

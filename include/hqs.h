@@ -296,6 +296,12 @@ HQS_API int hqs_power_iteration(hqs_plan plan, int iters, double* lam_max, void*
 
 HQS_API const char* hqs_status_string(int status);
 
+/* Measured FP32 FMA throughput of the current GPU in TFLOP/s (no counterpart
+ * in the paper: the denominator of the ALU roofline of the L2-resident
+ * persistent solve).  BLOCKING on `stream`: 4 launches of 8 independent FMA
+ * chains per thread at full occupancy, median of the last 3. */
+HQS_API int hqs_probe_fp32_peak(double* tflops, void* stream);
+
 /* Tuning knobs (no counterpart in the paper), set per plan by the autotuner:
  *   HQS_TUNE_FUSED_GRID  cap on the persistent solve's CTAs (0 = all resident)
  *   HQS_TUNE_PC_LINES    preconditioner rows/columns per work item (1..16)

@@ -80,6 +80,7 @@ _SIGS = {
                                        C.c_float, C.c_void_p]),
     "hqs_power_iteration": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_void_p]),
     "hqs_status_string": (C.c_char_p, [C.c_int]),
+    "hqs_probe_fp32_peak": (C.c_int, [C.POINTER(C.c_double), C.c_void_p]),
     "hqs_plan_set_tuning": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "hqs_plan_retile": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "hqs_debug_toeplitz_stage": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
@@ -135,6 +136,13 @@ class HqsError(RuntimeError):
     def __init__(self, status: int, what: str):
         self.status = status
         super().__init__(f"{what}: {status_string(status)} ({status})")
+
+
+def probe_fp32_peak(stream=None) -> float:
+    """Measured FP32 FMA throughput of the current GPU, TFLOP/s."""
+    v = C.c_double()
+    _check(library().hqs_probe_fp32_peak(C.byref(v), _stream(stream)), "hqs_probe_fp32_peak")
+    return v.value
 
 
 def status_string(status: int) -> str:

@@ -366,3 +366,11 @@ def test_fused_line_balanced_passes(grid):
                         mode=hq().HQS_SOLVE_FUSED | hq().HQS_SOLVE_X0_ZERO)
     assert inf.status == 0
     assert np.linalg.norm(rhs - H(to_host(xf))) / np.linalg.norm(rhs) <= 1.2e-4
+
+
+def test_fp32_peak_probe_is_plausible():
+    """The measured FP32 FMA rate sits below the unit-count bound (152 SMs x
+    128 lanes x 2 flop x at most 2.1 GHz = 81.7 TFLOP/s) and well above a
+    small fraction of it."""
+    t = hq().probe_fp32_peak()
+    assert 20.0 < t < 82.0, t
