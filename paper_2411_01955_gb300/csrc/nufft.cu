@@ -180,7 +180,7 @@ __global__ void k_spread(const float2* __restrict__ y, const int4* __restrict__ 
         if (cy >= G) cy -= G;
         loc[i] = make_int2(cx - bx * TB, cy - by * TB);
     }
-    for (int ch = 0; ch < nchunk; ++ch) {
+    for (int ch = blockIdx.y; ch < nchunk; ch += gridDim.y) {
         const int l0 = ch * LC;
         const int lines = min(LC, L - l0);
         for (int e = threadIdx.x; e < P * P * lines; e += blockDim.x) patch[e] = make_float2(0.f, 0.f);
@@ -355,11 +355,15 @@ template <int W>
 static int spread_impl(hqs_plan_s* p, const float2* y, cudaStream_t st) {
     if (p->nsub == 0) return HQS_OK;
     const int P = p->tile + W - 1;
-    const size_t sm = (size_t)P * P * p->LC * sizeof(float2) + HQS_SPREAD_MAXPTS * 2 * W * sizeof(float) +
+    // coil chunks of <= 8 on the grid's y dimension: a smaller shared patch per
+    // CTA keeps more CTAs resident to hide the shared-atomic latency
+    const int nch = ceil_div(p->L, 8);
+    const int lc = ceil_div(p->L, nch);
+    const size_t sm = (size_t)P * P * lc * sizeof(float2) + HQS_SPREAD_MAXPTS * 2 * W * sizeof(float) +
                       HQS_SPREAD_MAXPTS * sizeof(int2);
     HQS_CUDA_TRY(cudaFuncSetAttribute(k_spread<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_spread<W><<<p->nsub, 256, sm, st>>>(y, p->pts, p->perm, p->subs, (int)p->M, p->G, p->L, p->LC,
-                                          p->nchunk, p->tile, p->nbx, (float)p->beta, p->grid);
+    k_spread<W><<<dim3(p->nsub, nch), 256, sm, st>>>(y, p->pts, p->perm, p->subs, (int)p->M, p->G, p->L, lc,
+                                                     nch, p->tile, p->nbx, (float)p->beta, p->grid);
     HQS_CUDA_TRY(cudaGetLastError());
     return HQS_OK;
 }
