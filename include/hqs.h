@@ -224,6 +224,16 @@ HQS_API int hqs_net_gradient(hqs_net net, const float* x, const float* target, i
 /* one Adam step on a batch; loss before the step (host, blocking) */
 HQS_API int hqs_net_train_step(hqs_net net, const float* x, const float* target, int N, int H, int W,
                                float lr, double* loss, void* stream);
+/* Gradient for a loss given through its gradient dy = dL/dy with respect to
+ * the network output (N x 2 x H x W, device): the preconditioner is trained on
+ * the residual r - H z it leaves, whose gradient needs the operator H (A^H A
+ * applies done by the caller).  hqs_net_backward writes the parameter
+ * gradient to grad (device, optional); hqs_net_train_step_dy also takes one
+ * Adam step (same rule as hqs_net_train_step). */
+HQS_API int hqs_net_backward(hqs_net net, const float* x, const float* dy, int N, int H, int W,
+                             float* grad, void* stream);
+HQS_API int hqs_net_train_step_dy(hqs_net net, const float* x, const float* dy, int N, int H, int W,
+                                  float lr, void* stream);
 HQS_API int hqs_net_save(hqs_net net, const char* path);
 HQS_API int hqs_net_load(hqs_net net, const char* path);
 /* attach (or detach with NULL) the network used by HQS_PRECOND_LEARNED; the

@@ -95,6 +95,10 @@ _SIGS = {
                                    C.c_void_p, C.POINTER(C.c_double), C.c_void_p]),
     "hqs_net_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,
                                      C.c_float, C.POINTER(C.c_double), C.c_void_p]),
+    "hqs_net_backward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,
+                                   C.c_void_p, C.c_void_p]),
+    "hqs_net_train_step_dy": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,
+                                        C.c_float, C.c_void_p]),
     "hqs_net_save": (C.c_int, [C.c_void_p, C.c_char_p]),
     "hqs_net_load": (C.c_int, [C.c_void_p, C.c_char_p]),
     "hqs_plan_set_net": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -412,6 +416,21 @@ class Net:
                                             _ptr(t, torch.float32, "t"), N, H, W, float(lr),
                                             C.byref(loss), _stream(stream)), "hqs_net_train_step")
         return loss.value
+
+    def backward(self, x, dy, stream=None):
+        """Parameter gradient for a loss with output gradient dy."""
+        g = torch.empty(self.num_params, dtype=torch.float32, device=x.device)
+        N, _, H, W = x.shape
+        _check(library().hqs_net_backward(self.handle, _ptr(x, torch.float32, "x"), _ptr(dy, torch.float32, "dy"),
+                                          N, H, W, _ptr(g, torch.float32, "grad"), _stream(stream)),
+               "hqs_net_backward")
+        return g
+
+    def train_step_dy(self, x, dy, lr, stream=None):
+        N, _, H, W = x.shape
+        _check(library().hqs_net_train_step_dy(self.handle, _ptr(x, torch.float32, "x"),
+                                               _ptr(dy, torch.float32, "dy"), N, H, W, float(lr),
+                                               _stream(stream)), "hqs_net_train_step_dy")
 
     def save(self, path):
         _check(library().hqs_net_save(self.handle, str(path).encode()), "hqs_net_save")

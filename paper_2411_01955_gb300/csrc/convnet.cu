@@ -269,18 +269,13 @@ int net_forward(hqs_net_s* net, const float* x, float* out, int N, int H, int Wd
     return HQS_OK;
 }
 
-// loss and gradient into net->grads; loss per sample into net->loss_n
-static int net_backward(hqs_net_s* net, const float* x, const float* target, int N, int H, int Wd,
-                        cudaStream_t st) {
-    HQS_TRY_RC(net_forward(net, x, nullptr, N, H, Wd, st));
-    const int Hd = HQS_NET_HIDDEN;
+// Back-propagation from the output gradient in net->dbuf[0] (activations of
+// the last forward in net->act) into net->grads.
+static int net_backprop(hqs_net_s* net, const float* x, int N, int H, int Wd, cudaStream_t st) {
     const float* P = net->params;
     float* G = net->grads;
     float* dz = net->dbuf[0];
     float* da = net->dbuf[1];
-    const int per = 2 * H * Wd;
-    k_rel_mse<<<N, 256, 0, st>>>(net->act[3], target, per, N, dz, net->loss_n);
-    HQS_CUDA_TRY(cudaGetLastError());
     // layer 4 (H -> 2)
     HQS_TRY_RC((wgrad_launch<HQS_NET_HIDDEN, 2>(net->act[2], dz, net->part, G + layer_offset(3), N, H, Wd, st)));
     HQS_TRY_RC((conv_launch<2, HQS_NET_HIDDEN, CONV_DGRAD_MASK>(dz, P + layer_offset(3), nullptr, net->act[2], da, N,
@@ -300,7 +295,36 @@ static int net_backward(hqs_net_s* net, const float* x, const float* target, int
     std::swap(dz, da);
     // layer 1 (2 -> H)
     HQS_TRY_RC((wgrad_launch<2, HQS_NET_HIDDEN>(x, dz, net->part, G + layer_offset(0), N, H, Wd, st)));
-    (void)Hd;
+    return HQS_OK;
+}
+
+// loss and gradient into net->grads; loss per sample into net->loss_n
+static int net_backward(hqs_net_s* net, const float* x, const float* target, int N, int H, int Wd,
+                        cudaStream_t st) {
+    HQS_TRY_RC(net_forward(net, x, nullptr, N, H, Wd, st));
+    const int per = 2 * H * Wd;
+    k_rel_mse<<<N, 256, 0, st>>>(net->act[3], target, per, N, net->dbuf[0], net->loss_n);
+    HQS_CUDA_TRY(cudaGetLastError());
+    return net_backprop(net, x, N, H, Wd, st);
+}
+
+// gradient into net->grads for a loss whose gradient with respect to the
+// network output is dy (N x 2 x H x W)
+static int net_backward_dy(hqs_net_s* net, const float* x, const float* dy, int N, int H, int Wd, cudaStream_t st) {
+    HQS_TRY_RC(net_forward(net, x, nullptr, N, H, Wd, st));
+    HQS_CUDA_TRY(cudaMemcpyAsync(net->dbuf[0], dy, (size_t)N * 2 * H * Wd * sizeof(float), cudaMemcpyDeviceToDevice,
+                                 st));
+    return net_backprop(net, x, N, H, Wd, st);
+}
+
+static int adam_update(hqs_net_s* net, float lr, cudaStream_t st) {
+    net->adam_t += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = (float)(1.0 - std::pow(0.9, net->adam_t));
+    const float c2 = (float)(1.0 - std::pow(0.999, net->adam_t));
+    const int np = net_num_params();
+    k_adam<<<ceil_div(np, 256), 256, 0, st>>>(net->params, net->grads, net->m, net->v, np, lr, b1, b2, 1e-8f, c1, c2);
+    HQS_CUDA_TRY(cudaGetLastError());
     return HQS_OK;
 }
 
@@ -392,14 +416,26 @@ extern "C" int hqs_net_train_step(hqs_net net, const float* x, const float* targ
     if (!net || !x || !target || N <= 0 || H <= 0 || Wd <= 0 || !(lr > 0.f)) return HQS_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     HQS_TRY_RC(net_backward(net, x, target, N, H, Wd, st));
-    net->adam_t += 1;
-    const float b1 = 0.9f, b2 = 0.999f;
-    const float c1 = (float)(1.0 - std::pow(0.9, net->adam_t));
-    const float c2 = (float)(1.0 - std::pow(0.999, net->adam_t));
-    const int np = net_num_params();
-    k_adam<<<ceil_div(np, 256), 256, 0, st>>>(net->params, net->grads, net->m, net->v, np, lr, b1, b2, 1e-8f, c1, c2);
-    HQS_CUDA_TRY(cudaGetLastError());
+    HQS_TRY_RC(adam_update(net, lr, st));
     return read_loss(net, N, loss, st);
+}
+
+extern "C" int hqs_net_backward(hqs_net net, const float* x, const float* dy, int N, int H, int Wd, float* grad,
+                                void* stream) {
+    if (!net || !x || !dy || N <= 0 || H <= 0 || Wd <= 0) return HQS_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    HQS_TRY_RC(net_backward_dy(net, x, dy, N, H, Wd, st));
+    if (grad)
+        HQS_CUDA_TRY(cudaMemcpyAsync(grad, net->grads, net_num_params() * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    return HQS_OK;
+}
+
+extern "C" int hqs_net_train_step_dy(hqs_net net, const float* x, const float* dy, int N, int H, int Wd, float lr,
+                                     void* stream) {
+    if (!net || !x || !dy || N <= 0 || H <= 0 || Wd <= 0 || !(lr > 0.f)) return HQS_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    HQS_TRY_RC(net_backward_dy(net, x, dy, N, H, Wd, st));
+    return adam_update(net, lr, st);
 }
 
 extern "C" int hqs_net_save(hqs_net net, const char* path) {

@@ -81,3 +81,72 @@ def heldout_loss(net, examples):
         out = net.forward(inp[None].contiguous())[0]
         vals.append(float(torch.sum((out - tgt) ** 2) / torch.sum(tgt ** 2)))
     return float(np.mean(vals))
+
+
+# ---------------------------------------------------------------- residual loss
+# The flexible CG this preconditioner serves converges fast when ||I - H M||
+# is small on the residuals it meets, so the second training mode minimises
+# the preconditioned residual itself: for z = zdc + s net(zdc / s),
+#     loss = ||r - H z||^2 / ||r||^2,   dloss/dz = -2 H (r - H z) / ||r||^2
+# (H Hermitian), and dloss/d(net output) = s dloss/dz.  Full images are used
+# (H is a global operator); the two A^H A applies per example run in the
+# library, the network's backward in the library from that output gradient.
+
+def from_planar(p):
+    return torch.complex(p[0], p[1])
+
+
+def apply_H(plan, mu, v):
+    out = torch.empty_like(v)
+    hq.toeplitz_normal(plan, v, out)
+    return out + mu * v
+
+
+def residual_example(plan, mu, r):
+    """Example of the residual-loss mode: the DC-preconditioned residual zdc,
+    its RMS s and the network input zdc / s (planar)."""
+    zdc = torch.empty_like(r)
+    hq.precond_apply(plan, 1.0, mu, r, zdc)
+    s = float(torch.sqrt(torch.mean(torch.abs(zdc) ** 2)))
+    s = s if s > 0 else 1.0
+    return dict(plan=plan, mu=mu, r=r, zdc=zdc, s=s, inp=to_planar(zdc / s))
+
+
+def residual_loss(net, ex, out=None):
+    """Preconditioned residual ||r - H z||^2 / ||r||^2 of one example, and the
+    gradient with respect to the network output (planar)."""
+    if out is None:
+        out = net.forward(ex["inp"][None].contiguous())[0]
+    z = ex["zdc"] + ex["s"] * from_planar(out)
+    res = ex["r"] - apply_H(ex["plan"], ex["mu"], z)
+    rn = float(torch.sum(torch.abs(ex["r"]) ** 2))
+    loss = float(torch.sum(torch.abs(res) ** 2)) / rn
+    g = -2.0 * apply_H(ex["plan"], ex["mu"], res) / rn
+    return loss, ex["s"] * to_planar(g)
+
+
+def train_residual(net, examples, steps=300, batch=8, lr=5e-4, seed=0, log_every=0):
+    """Adam on the mean preconditioned residual over random batches of
+    full-size examples (all of one image size)."""
+    rng = np.random.default_rng(seed)
+    losses = []
+    for it in range(steps):
+        idx = rng.integers(len(examples), size=batch)
+        exs = [examples[int(i)] for i in idx]
+        x = torch.stack([e["inp"] for e in exs]).contiguous()
+        out = net.forward(x)
+        dys, ls = [], []
+        for k, e in enumerate(exs):
+            l, dy = residual_loss(net, e, out[k])
+            ls.append(l)
+            dys.append(dy / batch)
+        net.train_step_dy(x, torch.stack(dys).contiguous(), lr)
+        losses.append(float(np.mean(ls)))
+        if log_every and it % log_every == 0:
+            print(f"step {it} residual loss {losses[-1]:.4f}", flush=True)
+    return losses
+
+
+def heldout_residual(net, examples):
+    """Mean ||r - H M r||^2 / ||r||^2 over examples (M: DC + network)."""
+    return float(np.mean([residual_loss(net, e)[0] for e in examples]))
