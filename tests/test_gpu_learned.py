@@ -188,3 +188,57 @@ def test_learned_fcg_iterates_match_oracle():
     assert rel(to_host(x), want) <= 1e-4
     assert np.allclose(np.array(info.history()), winfo["res_hist"], rtol=1e-3, atol=0)
     hq().plan_set_net(plan, None)
+
+
+def test_backward_from_output_gradient_matches_loss_gradient():
+    """hqs_net_backward seeded with the relative-MSE output gradient
+    2 (y - t) / (N ||t_k||^2) reproduces hqs_net_gradient (itself pinned to
+    the oracle)."""
+    rng = np.random.default_rng(8)
+    net = hq().Net()
+    net.set_params(convnet.flatten(f32(random_params(9))))
+    x = torch.from_numpy(rng.normal(size=(3, 2, 24, 17)).astype(np.float32)).cuda()
+    t = torch.from_numpy(rng.normal(size=(3, 2, 24, 17)).astype(np.float32)).cuda()
+    g_ref, _ = net.gradient(x, t)
+    y = net.forward(x)
+    tn = torch.sum(t.double() ** 2, dim=(1, 2, 3)).view(3, 1, 1, 1)
+    dy = (2.0 * (y.double() - t.double()) / (3 * tn)).float().contiguous()
+    g = net.backward(x, dy)
+    assert rel(g.cpu().numpy(), g_ref.cpu().numpy()) <= 1e-5
+
+
+def test_residual_trained_net_in_flexible_cg():
+    """Trained on the preconditioned residual ||r - H M r||^2 / ||r||^2 of
+    DC-PCG residuals, the network lowers it on held-out slices below the DC
+    preconditioner's; flexible CG with it converges (falling back if it
+    stalls), and its iteration count is reported beside DC-PCG's."""
+    from paper_2411_01955_gb300 import learned
+    mu = 1e-2
+    train_slices = make_slices(range(1000, 1008))
+    test_slices = make_slices(range(5000, 5003))
+
+    def residuals(slices, its):
+        out = []
+        for plan, rhs in slices:
+            for r, _ in learned.solve_pairs(plan, rhs, mu, iterates=its):
+                out.append(learned.residual_example(plan, mu, r))
+        return out
+    examples = residuals(train_slices, 20)
+    held = residuals(test_slices, 12)
+    net = hq().Net()
+    net.set_params(convnet.flatten(convnet.init_params(0)))
+    base = learned.heldout_residual(net, held)
+    losses = learned.train_residual(net, examples, steps=300, batch=8, lr=5e-4)
+    trained = learned.heldout_residual(net, held)
+    print(f"held-out ||r - H M r||^2/||r||^2: DC {base:.4f} -> learned {trained:.4f}; "
+          f"train {losses[0]:.4f} -> {np.mean(losses[-20:]):.4f}")
+    assert trained < base
+    for plan, rhs in test_slices:
+        hq().plan_set_net(plan, net)
+        xl = torch.zeros_like(rhs)
+        il = hq().dc_solve(plan, 1.0, mu, rhs, xl, max_iter=300, rel_tol=1e-4, precond=hq().HQS_PRECOND_LEARNED)
+        xd = torch.zeros_like(rhs)
+        idc = hq().dc_solve(plan, 1.0, mu, rhs, xd, max_iter=300, rel_tol=1e-4)
+        print(f"iterations to 1e-4: learned {il.iterations} (fallback {il.fallback}), DC {idc.iterations}")
+        assert il.status == 0 and il.rel_residual <= 1e-4
+        hq().plan_set_net(plan, None)
