@@ -13,6 +13,8 @@ ellipse phantoms, Gaussian-bump coil maps, spiral trajectory).
   python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B] [--impl ours|reference]
   python bench.py --workload batch64     # 64 uneven slices, batched HQS 20 x 5
   python bench.py --workload mixed320    # A^H A and DC solves at FP32 / BF16x3 / FP16x3
+  python bench.py --workload hqs320      # annealed HQS 10 x 5 with the Id, F-1, Chebyshev metrics
+  python bench.py --workload learned320  # learned-preconditioned flexible CG vs DC-PCG
 
 The batch64 workload runs annealed HQS (20 outer x 5 CG iterations, Gaussian
 smoothing denoiser) over 64 slices of mixed size {256, 320, 384}^2, 8-20
@@ -75,7 +77,8 @@ def parse():
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="fused", choices=["fused", "plain"])
-    ap.add_argument("--workload", default="dc320", choices=["dc320", "batch64", "mixed320"])
+    ap.add_argument("--workload", default="dc320",
+                    choices=["dc320", "batch64", "mixed320", "hqs320", "learned320"])
     return ap.parse_args()
 
 
@@ -610,6 +613,151 @@ def run_mixed320(args, rank, world, dist):
     print(json.dumps(line), flush=True)
 
 
+def run_hqs320(args, rank, world, dist):
+    """Annealed PnP-HQS on the 320^2 x 16-coil workload (10 outer steps x 5 CG
+    iterations, mu 1e-1 -> 1e-3, Gaussian smoothing denoiser) in the metric
+    P = c0 I + c1 A^H A: Id (1, 0), F-1 (2, -alpha), Chebyshev (4, -10 alpha / 3),
+    alpha = 1 / ||A^H A|| by power iteration; HQS runs per second."""
+    import torch
+    import paper_2411_01955_gb300 as hq
+    import synth
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    B = args.batch
+    n, L, traj_np, sl = make_slices(B, rank)
+    traj = torch.from_numpy(traj_np).cuda()
+    K, CG = 10, 5
+    mu = synth.mu_schedule_geometric(1e-1, 1e-3, K).astype(np.float32)
+    plans, ys, xs = [], [], []
+    for s in sl:
+        plan = hq.plan_create(traj, n, n, torch.from_numpy(s["smaps"].astype(np.complex64)).cuda(), 6, 2.0)
+        x = torch.from_numpy(s["x"].astype(np.complex64)).cuda()
+        y = torch.empty((L, traj.shape[0]), dtype=torch.complex64, device="cuda")
+        hq.forward(plan, x, y)
+        sd = math.sqrt(1e-4 * float(np.max(np.sum(np.abs(s["smaps"] * s["x"]) ** 2, axis=0))))
+        y = (y + sd * torch.from_numpy(s["noise"].astype(np.complex64)).cuda()).contiguous()
+        plans.append(plan)
+        ys.append(y)
+        xs.append(torch.zeros_like(x))
+    alpha = 1.0 / hq.power_iteration(plans[0], 50)
+    metrics = {"id": (1.0, 0.0), "f1": (2.0, -alpha), "chebyshev": (4.0, -10.0 * alpha / 3.0)}
+    stream = torch.cuda.current_stream()
+    res = {}
+    clk = ClockSampler(dev)
+    clk.start()
+    for name, (c0, c1) in metrics.items():
+        def runs():
+            for i in range(B):
+                xs[i].zero_()
+                hq.hqs_run(plans[i], ys[i], xs[i], mu, mu, cg_iters=CG, c0=c0, c1=c1)
+        for _ in range(max(args.warmup, 3)):
+            runs()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            runs()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = max_over_ranks(e0.elapsed_time(e1), dist)
+        res[name] = {"hqs_runs_per_s": whole_job_rate(B * args.steps, world, ms),
+                     "ms_per_run": ms / (B * args.steps), "c0": c0, "c1": c1}
+    clocks = clk.stop()
+    if rank != 0:
+        return
+    line = {
+        "metric": "annealed PnP-HQS runs/s at 320^2, 16 coils (10 outer x 5 CG), Id / F-1 / Chebyshev metrics",
+        "value": res["id"]["hqs_runs_per_s"], "unit": "HQS runs/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (seeded ellipse phantoms, Gaussian-bump coil maps, VD spiral)",
+        "config": {"workload": "320x320, 16 coils, spiral 16x2048, KB W=6, sigma=2, HQS 10 x 5 CG, "
+                               "mu 1e-1 -> 1e-3, Gaussian smoothing denoiser, DC-preconditioned CG",
+                   "batch_per_gpu": B, "alpha": alpha},
+        "metrics": res, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_learned320(args, rank, world, dist):
+    """Learned preconditioner at 320^2 x 16 coils: the network is trained on the
+    GPU (library kernels) on DC-PCG iterates of training seeds 1000+ (mu
+    log-uniform in [1e-3, 1e-1]), then flexible CG with it and DC-PCG solve
+    held-out seeds 5000+ to relative residual 1e-4: iterations, solve time,
+    fallback counts."""
+    import time as _time
+    import torch
+    import paper_2411_01955_gb300 as hq
+    from paper_2411_01955_gb300 import learned
+    import synth
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    n, L = 320, 16
+    traj_np = synth.traj_spiral(16, 2048, n)
+    traj = torch.from_numpy(traj_np).cuda()
+    rng = np.random.default_rng(77)
+
+    def slice_(seed):
+        plan = hq.plan_create(traj, n, n, torch.from_numpy(synth.coil_maps(seed, n, L).astype(np.complex64)).cuda(),
+                              6, 2.0)
+        x = torch.from_numpy(synth.phantom(seed, n).astype(np.complex64)).cuda()
+        y = torch.empty((L, traj.shape[0]), dtype=torch.complex64, device="cuda")
+        hq.forward(plan, x, y)
+        rhs = torch.empty_like(x)
+        hq.adjoint(plan, y, rhs)
+        return plan, rhs
+    t0 = _time.time()
+    examples = []
+    for seed in range(1000, 1000 + args.batch):
+        plan, rhs = slice_(seed)
+        mu = float(10 ** rng.uniform(-3, -1))
+        for r, e in learned.solve_pairs(plan, rhs, mu, iterates=16):
+            examples.append(learned.network_example(plan, mu, r, e))
+    net = hq.Net()
+    net.set_params(learned.initial_params(0))   # zero last layer: the untrained network is DC-PCG
+    losses = learned.train(net, examples, steps=400, batch=16, crop=64, lr=1e-3)
+    train_s = _time.time() - t0
+    rows = []
+    for seed in range(5000, 5000 + 4):
+        plan, rhs = slice_(seed)
+        mu = float(10 ** rng.uniform(-3, -1))
+        out = {}
+        for name, pc in (("dc", hq.HQS_PRECOND_DC), ("learned", hq.HQS_PRECOND_LEARNED)):
+            hq.plan_set_net(plan, net if name == "learned" else None)
+            x = torch.zeros_like(rhs)
+            hq.dc_solve(plan, 1.0, mu, rhs, x, max_iter=400, rel_tol=1e-4, precond=pc)   # warm-up
+            x.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            info = hq.dc_solve(plan, 1.0, mu, rhs, x, max_iter=400, rel_tol=1e-4, precond=pc)
+            e1.record()
+            torch.cuda.synchronize()
+            out[name] = {"iterations": info.iterations, "ms": e0.elapsed_time(e1), "fallback": info.fallback,
+                         "rel_residual": info.rel_residual}
+        hq.plan_set_net(plan, None)
+        rows.append({"seed": seed, "mu": mu, **out})
+    if rank != 0:
+        return
+    line = {
+        "metric": "DC solves to 1e-4 at 320^2, 16 coils: learned-preconditioned flexible CG vs DC-PCG",
+        "value": float(np.mean([r["learned"]["iterations"] for r in rows])), "unit": "CG iterations (mean)",
+        "n_gpus": world, "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded ellipse phantoms, Gaussian-bump coil maps, VD spiral)",
+        "config": {"workload": "320x320, 16 coils, spiral 16x2048, KB W=6, sigma=2, mu log-uniform [1e-3, 1e-1]; "
+                               f"training: {args.batch} seeds x 16 DC-PCG iterates, 400 Adam steps on 64x64 crops",
+                   "train_pairs": len(examples)},
+        "dc_mean_iterations": float(np.mean([r["dc"]["iterations"] for r in rows])),
+        "learned_fallbacks": int(sum(r["learned"]["fallback"] for r in rows)),
+        "train_seconds": train_s, "train_loss_first_last": [losses[0], float(np.mean(losses[-20:]))],
+        "held_out": rows,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def fft_flops(N):
     return 5.0 * N * math.log2(N)
 
@@ -643,6 +791,10 @@ def main():
         run_batch64(args, rank, world, dist)
     elif args.workload == "mixed320":
         run_mixed320(args, rank, world, dist)
+    elif args.workload == "hqs320":
+        run_hqs320(args, rank, world, dist)
+    elif args.workload == "learned320":
+        run_learned320(args, rank, world, dist)
     else:
         run_ours(args, rank, world, dist)
     if dist is not None:

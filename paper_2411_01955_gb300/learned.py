@@ -17,6 +17,24 @@ import torch
 from . import _lib as hq
 
 
+LAYERS = ((2, 32), (32, 32), (32, 32), (32, 2))   # (in, out) channels of the 3x3 convolutions
+
+
+def initial_params(seed=0):
+    """Flat float32 parameters in the library's layout (per layer: weights
+    [out][in][3][3], then biases): He-normal hidden layers, zero biases, and a
+    zero last layer, so the untrained network adds nothing to the DC
+    preconditioner."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for k, (ci, co) in enumerate(LAYERS):
+        w = rng.normal(size=(co, ci, 3, 3)) * np.sqrt(2.0 / (ci * 9))
+        if k == len(LAYERS) - 1:
+            w = np.zeros_like(w)
+        parts += [w.ravel(), np.zeros(co)]
+    return np.concatenate(parts).astype(np.float32)
+
+
 def residual(plan, mu, rhs, x):
     """r = rhs - (A^H A + mu I) x."""
     ax = torch.empty_like(x)
