@@ -13,7 +13,7 @@ ellipse phantoms, Gaussian-bump coil maps, spiral trajectory).
   python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B] [--impl ours|reference]
   python bench.py --workload batch64     # 64 uneven slices, batched HQS 20 x 5
   python bench.py --workload mixed320    # A^H A and DC solves at FP32 / BF16x3 / FP16x3
-  python bench.py --workload hqs320      # annealed HQS 10 x 5 with the Id, F-1, Chebyshev metrics
+  python bench.py --workload hqs320      # annealed HQS 10 x 5 and PnP-PGD 10 steps, Id / F-1 / Chebyshev
   python bench.py --workload learned320  # learned-preconditioned flexible CG vs DC-PCG
 
 The batch64 workload runs annealed HQS (20 outer x 5 CG iterations, Gaussian
@@ -677,6 +677,28 @@ def run_hqs320(args, rank, world, dist):
         ms = max_over_ranks(e0.elapsed_time(e1), dist)
         res[name] = {"hqs_runs_per_s": whole_job_rate(B * args.steps, world, ms),
                      "ms_per_run": ms / (B * args.steps), "c0": c0, "c1": c1}
+    # PnP-PGD, 10 steps, gamma = 0.9 / (c0 ||A^H A||), same metrics
+    gam_base = 0.9 * alpha
+    for name, (c0, c1) in metrics.items():
+        gam = np.full(K, gam_base / c0, dtype=np.float32)
+        sg = np.full(K, 0.5, dtype=np.float32)
+
+        def pruns():
+            for i in range(B):
+                xs[i].zero_()
+                hq.pgd_run(plans[i], ys[i], xs[i], gam, sg, c0=c0, c1=c1)
+        for _ in range(max(args.warmup, 3)):
+            pruns()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            pruns()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = max_over_ranks(e0.elapsed_time(e1), dist)
+        res["pgd_" + name] = {"pgd_runs_per_s": whole_job_rate(B * args.steps, world, ms),
+                              "ms_per_run": ms / (B * args.steps), "c0": c0, "c1": c1}
     clocks = clk.stop()
     if rank != 0:
         return

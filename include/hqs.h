@@ -267,6 +267,16 @@ HQS_API int hqs_run(hqs_plan plan, const hqs_c64* y, hqs_c64* x, const float* mu
             hqs_denoiser_fn denoiser, void* user, void* stream);
 
 /* --------------------------------------- batched persistent HQS (a9) */
+/* PnP-PGD (Sec. 3.3) with the gradient step in the metric P = c0 I + c1 A^H A
+ * of Sec. 3.4: for k = 0..K-1,
+ *     g = A^H A x - A^H y,  u = x - gamma[k] (c0 g + c1 A^H A g),  x = D_{sigma[k]}(u);
+ * x (device, n x n) is x_0 in, x_K out; gamma[k] > 0 and sigma[k] >= 0 are host
+ * arrays; denoiser / user as in hqs_run (NULL: the built-in Gaussian smoothing).
+ * One A^H A per step for P = Id, two otherwise; enqueued on `stream`. */
+HQS_API int hqs_pgd_run(hqs_plan plan, const hqs_c64* y, hqs_c64* x, const float* gamma,
+                        const float* sigma, int K, float c0, float c1, hqs_denoiser_fn denoiser,
+                        void* user, void* stream);
+
 /* Annealed PnP-HQS (Sec. 3.3, P = Id) for many slices of uneven size at once:
  * one persistent cooperative launch runs, for every slice and k = k0..K-1,
  * rhs = A^H y + mu_k c0 x_k, cg_iters DC-preconditioned CG iterations on

@@ -76,6 +76,9 @@ _SIGS = {
     "hqs_run": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_float),
                           C.POINTER(C.c_float), C.c_int, C.c_int, C.c_int, C.c_float, C.c_float,
                           C.c_void_p, C.c_void_p, C.c_void_p]),
+    "hqs_pgd_run": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_float),
+                          C.POINTER(C.c_float), C.c_int, C.c_float, C.c_float,
+                          C.c_void_p, C.c_void_p, C.c_void_p]),
     "hqs_gaussian_denoise": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int,
                                        C.c_float, C.c_void_p]),
     "hqs_power_iteration": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_void_p]),
@@ -308,6 +311,22 @@ def hqs_run(plan: Plan, y, x, mu, sigma, K=None, k0=0, cg_iters=5, c0=1.0, c1=0.
                      mu_c, sg_c, K, int(k0), int(cg_iters), float(c0), float(c1),
                      C.cast(cb, C.c_void_p) if cb is not None else None, user, _stream(stream))
     _check(rc, "hqs_run")
+    return x
+
+
+def pgd_run(plan: Plan, y, x, gamma, sigma, K=None, c0=1.0, c1=0.0, gauss=None, stream=None):
+    """PnP-PGD with the gradient step in the metric P = c0 I + c1 A^H A and the
+    built-in Gaussian smoothing denoiser (optional gauss=(kappa, sigma0))."""
+    K = len(gamma) if K is None else int(K)
+    g_c = (C.c_float * max(K, 1))(*[float(v) for v in gamma[:K]])
+    s_c = (C.c_float * max(K, 1))(*[float(v) for v in sigma[:K]])
+    user, keep = None, []
+    if gauss is not None:
+        gp = GaussParams(float(gauss[0]), float(gauss[1]))
+        keep.append(gp)
+        user = C.cast(C.pointer(gp), C.c_void_p)
+    _check(library().hqs_pgd_run(plan.handle, _ptr(y, torch.complex64, "y"), _ptr(x, torch.complex64, "x"),
+                                 g_c, s_c, K, float(c0), float(c1), None, user, _stream(stream)), "hqs_pgd_run")
     return x
 
 

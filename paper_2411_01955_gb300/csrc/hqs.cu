@@ -151,6 +151,37 @@ extern "C" int hqs_run(hqs_plan p, const hqs_c64* y, hqs_c64* x, const float* mu
     return HQS_OK;
 }
 
+// PnP-PGD (Sec. 3.3) in the metric P = c0 I + c1 A^H A of Sec. 3.4:
+//   g = A^H A x - A^H y;  u = x - gamma_k (c0 g + c1 A^H A g);  x = D_{sigma_k}(u)
+extern "C" int hqs_pgd_run(hqs_plan p, const hqs_c64* y, hqs_c64* x, const float* gamma, const float* sigma,
+                           int K, float c0, float c1, hqs_denoiser_fn denoiser, void* user, void* stream) {
+    if (!p || !x || (!y && p->M > 0) || !gamma || !sigma || K < 0) return HQS_ERR_INVALID_ARG;
+    for (int k = 0; k < K; ++k)
+        if (!(gamma[k] > 0.f) || !(sigma[k] >= 0.f)) return HQS_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = p->n, count = n * n;
+    const int nb = std::min(ceil_div(count, 256), 1024);
+    float2* xx = reinterpret_cast<float2*>(x);
+    hqs_gauss_params gp_default = {1.5f, K > 0 ? sigma[0] : 1.f};
+    if (!denoiser && !user) user = &gp_default;
+    if (!denoiser) denoiser = hqs_gaussian_denoise;
+    HQS_TRY_RC(launch_adj(p, reinterpret_cast<const float2*>(y), p->img_b0, st));
+    for (int k = 0; k < K; ++k) {
+        HQS_TRY_RC(launch_toeplitz(p, xx, p->img_tmp, st));
+        k_axpbypcz<<<nb, 256, 0, st>>>(p->img_rhs, p->img_tmp, 1.0f, p->img_b0, -1.0f, nullptr, 0.f, count);
+        const float2* h = nullptr;
+        if (c1 != 0.f) {
+            HQS_TRY_RC(launch_toeplitz(p, p->img_rhs, p->img_tmp2, st));
+            h = p->img_tmp2;
+        }
+        k_axpbypcz<<<nb, 256, 0, st>>>(p->img_u, xx, 1.0f, p->img_rhs, -gamma[k] * c0, h, -gamma[k] * c1, count);
+        const int drc = denoiser(user, reinterpret_cast<const hqs_c64*>(p->img_u), x, n, n, sigma[k], stream);
+        if (drc != 0) return HQS_ERR_CALLBACK;
+    }
+    HQS_CUDA_TRY(cudaGetLastError());
+    return HQS_OK;
+}
+
 // ------------------------------------------------------ power iteration
 __global__ void k_dot_norm(const float2* __restrict__ v, const float2* __restrict__ w, int count,
                            double* __restrict__ part) {

@@ -374,3 +374,40 @@ def test_fp32_peak_probe_is_plausible():
     small fraction of it."""
     t = hq().probe_fp32_peak()
     assert 20.0 < t < 82.0, t
+
+
+@pytest.mark.parametrize("metric", ["id", "f1", "chebyshev"])
+def test_pgd_run_matches_oracle(metric):
+    """PnP-PGD, 10 steps, gamma = 0.9 / ||A^H A||, Gaussian-smoothing denoiser,
+    gradient step in the metric P = c0 I + c1 A^H A (Id, F-1, Chebyshev with
+    alpha = 1 / ||A^H A||).  Bound derived as for HQS: 4x the oracle's own
+    deviation when A^H y is perturbed by the float32 unit roundoff, at least
+    1e-5."""
+    from oracle import hqs as ohqs
+    from oracle import solvers as osolvers
+    case = quantised(synth.tiny_case(0))
+    plan, _, _ = make_plan(case)
+    n, K = case["n"], 10
+    Kh, _ = oracle_toeplitz(case)
+    AHA = lambda v: toeplitz.normal(v, case["smaps"], Kh)
+    lmax = osolvers.power_iteration(AHA, (n, n), iters=200, rtol=1e-10)
+    alpha = 1.0 / lmax
+    c0, c1 = {"id": (1.0, 0.0), "f1": (2.0, -alpha), "chebyshev": (4.0, -10.0 * alpha / 3.0)}[metric]
+    gamma = np.full(K, 0.9 / lmax / c0, dtype=np.float32)
+    sigma = np.full(K, 0.5, dtype=np.float32)
+    y = nufft.forward(case["x"], case["smaps"], case["traj"], case["W"], case["sigma"])
+    y = (y + 0.02 * np.sqrt(np.mean(np.abs(y) ** 2)) * case["noise"]).astype(np.complex64).astype(np.complex128)
+    b0 = nufft.adjoint(y, case["smaps"], case["traj"], case["W"], case["sigma"])
+    c1f = float(np.float32(c1))
+    want = ohqs.pgd(AHA, b0, np.zeros((n, n)), gamma.astype(np.float64), sigma.astype(np.float64), K,
+                    c0=c0, c1=c1f)
+    rng = np.random.default_rng(1)
+    b0p = b0 * (1 + 2.0 ** -24 * rng.normal(size=b0.shape))
+    pert = ohqs.pgd(AHA, b0p, np.zeros((n, n)), gamma.astype(np.float64), sigma.astype(np.float64), K,
+                    c0=c0, c1=c1f)
+    tol = max(TOL, 4 * rel(pert, want))
+    x = torch.zeros((n, n), dtype=torch.complex64, device="cuda")
+    hq().pgd_run(plan, to_dev(y), x, gamma, sigma, c0=c0, c1=c1f)
+    err = rel(to_host(x), want)
+    print(f"PGD {metric}: rel err {err:.2e} (bound {tol:.2e})")
+    assert err <= tol
