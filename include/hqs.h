@@ -300,6 +300,19 @@ HQS_API int hqs_batch_run(hqs_batch batch, const hqs_c64* const* y, hqs_c64* con
                           float c0, float c1, const hqs_gauss_params* gauss, int use_graph,
                           void* stream);
 HQS_API int hqs_batch_status(hqs_batch batch, double* rel_residual, void* stream);
+/* Batched data-consistency solve (Sec. 3.4's system, P = Id form): for every
+ * slice i of the batch, DC-preconditioned CG on (a A^H A + b I) x[i] = rhs[i]
+ * from x[i] = 0 until ||r|| <= rel_tol ||rhs[i]|| or max_iter iterations, all
+ * slices in one cooperative launch (a slice that converges drops out).
+ * rhs[i], x[i]: device (n_i x n_i) of the i-th plan; b > 0.  Enqueued on
+ * `stream`; synchronises it first when the pointers differ from the last
+ * call.  hqs_batch_dc_info (blocking) returns per slice the iterations, the
+ * relative residual of the CG recursion and the status (HQS_OK,
+ * HQS_ERR_NOT_CONVERGED, HQS_ERR_BREAKDOWN); NULL outputs are skipped. */
+HQS_API int hqs_batch_dc_solve(hqs_batch batch, const hqs_c64* const* rhs, hqs_c64* const* x, float a, float b,
+                               int max_iter, double rel_tol, void* stream);
+HQS_API int hqs_batch_dc_info(hqs_batch batch, int* iterations, double* rel_residual, int* status,
+                              void* stream);
 
 /* Built-in denoiser (stand-in for the trained prior of Sec. 4.2): separable
  * Gaussian blur of real and imaginary parts, std s pixels (see

@@ -113,6 +113,10 @@ _SIGS = {
                                 C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_int, C.c_int, C.c_int,
                                 C.c_float, C.c_float, C.c_void_p, C.c_int, C.c_void_p]),
     "hqs_batch_status": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_void_p]),
+    "hqs_batch_dc_solve": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_float,
+                                     C.c_float, C.c_int, C.c_double, C.c_void_p]),
+    "hqs_batch_dc_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_int),
+                                    C.c_void_p]),
     "hqs_precond_apply_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_float, C.c_float,
                                             C.c_void_p, C.c_void_p]),
     "hqs_debug_phase_trace": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_ulonglong), C.c_int,
@@ -508,6 +512,24 @@ class Batch:
                                        C.cast(C.pointer(gp), C.c_void_p) if gp else None,
                                        1 if use_graph else 0, _stream(stream)), "hqs_batch_run")
         return xs
+
+    def dc_solve(self, rhs, xs, a, b, max_iter=200, rel_tol=1e-4, stream=None):
+        """Solves (a A^H A + b I) x_i = rhs_i for every slice from x_i = 0 in one launch."""
+        n = len(self.plans)
+        rp = (C.c_void_p * n)(*[_ptr(r, torch.complex64, "rhs") for r in rhs])
+        xp = (C.c_void_p * n)(*[_ptr(x, torch.complex64, "x") for x in xs])
+        _check(library().hqs_batch_dc_solve(self.handle, rp, xp, float(a), float(b), int(max_iter),
+                                            float(rel_tol), _stream(stream)), "hqs_batch_dc_solve")
+        return xs
+
+    def dc_info(self, stream=None):
+        """Per slice (iterations, relative residual, status) of the last batched solve."""
+        n = len(self.plans)
+        it = (C.c_int * n)()
+        rr = (C.c_double * n)()
+        st = (C.c_int * n)()
+        _check(library().hqs_batch_dc_info(self.handle, it, rr, st, _stream(stream)), "hqs_batch_dc_info")
+        return [(it[i], rr[i], st[i]) for i in range(n)]
 
     def status(self, stream=None):
         res = (C.c_double * len(self.plans))()

@@ -452,6 +452,260 @@ __global__ void __launch_bounds__(HQS_BATCH_BD, 2) k_hqs_batch(BatchArgs B) {
 #undef CLEAR_ACC
 }
 
+
+// ---------------------------------------------------------------------------
+// Batched data-consistency solve: DC-preconditioned CG on (a A^H A + b I) x =
+// rhs for every slice from x = 0 to its own relative tolerance, in one
+// cooperative launch (the same per-slice work items as the HQS kernel, so the
+// phases of all slices share the GPU and one slice's phase tail is filled by
+// the others' items).  A slice that converges (or breaks down) drops out of
+// the item lists; every CTA takes the same decisions from the same totals.
+struct DcBatchArgs {
+    const BatchSlice* sl;   // u = caller's x, rhs = caller's right-hand side
+    int ns;
+    const int* off;
+    float a, b;
+    int max_iter;
+    double tol2;            // rel_tol^2
+    double* part;           // [BS_N][ns][gridDim]
+    double* res;            // [ns] final ||r||^2 / ||rhs||^2
+    int* iters;             // [ns]
+    int* status;            // [ns] HQS_OK / HQS_ERR_NOT_CONVERGED / HQS_ERR_BREAKDOWN
+    unsigned* bar;
+    unsigned* err;
+};
+
+__global__ void __launch_bounds__(HQS_BATCH_BD, 2) k_pcg_batch(DcBatchArgs B) {
+    extern __shared__ float2 s[];
+    __shared__ double red[33];
+    __shared__ double acc[2][HQS_BATCH_MAX];
+    __shared__ double tot[2][HQS_BATCH_MAX];
+    __shared__ double rzs[HQS_BATCH_MAX], alphas[HQS_BATCH_MAX], betas[HQS_BATCH_MAX];
+    __shared__ double bbs[HQS_BATCH_MAX], rrs[HQS_BATCH_MAX];
+    __shared__ int active[HQS_BATCH_MAX], its[HQS_BATCH_MAX], stat[HQS_BATCH_MAX];
+    __shared__ int nact;
+    const int ns = B.ns, G = gridDim.x, bid = blockIdx.x;
+    const float a = B.a, bcoef = B.b;
+    const float2* twN = nullptr;
+#define BB_BARRIER()                                \
+    do {                                            \
+        if (!grid_barrier(B.bar, B.err)) return;    \
+    } while (0)
+#define FOR_ITEMS(list, ...)                                                               \
+    {                                                                                      \
+        const int* off_ = B.off + (list) * (ns + 1);                                       \
+        for (int g_ = bid; g_ < off_[ns]; g_ += G) {                                       \
+            const int si = find_slice(off_, ns, g_);                                       \
+            if (!active[si]) continue;                                                     \
+            const int it_ = g_ - off_[si];                                                 \
+            const BatchSlice& S = B.sl[si];                                                \
+            __VA_ARGS__;                                                                   \
+        }                                                                                  \
+    }
+#define STAGE_TWN(S, si) twN = (S).twN;
+#define CLEAR_ACC()                                                      \
+    for (int i_ = threadIdx.x; i_ < 2 * HQS_BATCH_MAX; i_ += blockDim.x) \
+        (&acc[0][0])[i_] = 0.0;                                          \
+    __syncthreads();
+#define COUNT_ACTIVE()                                               \
+    if (threadIdx.x == 0) {                                          \
+        int c_ = 0;                                                  \
+        for (int i_ = 0; i_ < ns; ++i_) c_ += active[i_];            \
+        nact = c_;                                                   \
+    }                                                                \
+    __syncthreads();
+
+    for (int i = threadIdx.x; i < ns; i += blockDim.x) {
+        active[i] = 1;
+        its[i] = 0;
+        stat[i] = HQS_OK;
+        betas[i] = 0.0;
+    }
+    __syncthreads();
+    // x = 0, r = rhs, ||rhs||^2
+    CLEAR_ACC();
+    FOR_ITEMS(BL_IMG, {
+        const int n = S.A.n;
+        double a1 = 0.0;
+        for (int ix = threadIdx.x; ix < n; ix += blockDim.x) {
+            const size_t e = (size_t)it_ * n + ix;
+            const float2 bv = S.rhs[e];
+            S.u[e] = make_float2(0.f, 0.f);
+            S.r[e] = bv;
+            a1 += (double)bv.x * bv.x + (double)bv.y * bv.y;
+        }
+        a1 = cta_sum(a1, red);
+        if (threadIdx.x == 0) acc[0][si] += a1;
+    });
+    __syncthreads();
+    put_slice_partials(B.part + (size_t)BS_BB * ns * G, ns, acc[0]);
+    BB_BARRIER();
+    slice_totals(B.part + (size_t)BS_BB * ns * G, ns, tot[0]);
+    for (int i = threadIdx.x; i < ns; i += blockDim.x) {
+        const double bb = tot[0][i];
+        bbs[i] = bb;
+        rrs[i] = bb;
+        if (!(bb == bb) || isinf(bb)) {
+            stat[i] = HQS_ERR_BREAKDOWN;
+            active[i] = 0;
+        } else if (bb == 0.0 || B.tol2 >= 1.0) {
+            active[i] = 0;
+        } else if (B.max_iter == 0) {
+            stat[i] = HQS_ERR_NOT_CONVERGED;
+            active[i] = 0;
+        }
+    }
+    __syncthreads();
+    // preconditioner of the initial residual, <r, z>
+    FOR_ITEMS(BL_PC, {
+        STAGE_TWN(S, si);
+        HQS_BATCH_DISPATCH(S.A.n, (pc_rows<N>(S, it_ * HQS_BATCH_Q, 0.f, false, s, twN)));
+    });
+    BB_BARRIER();
+    CLEAR_ACC();
+    FOR_ITEMS(BL_PC, {
+        STAGE_TWN(S, si);
+        double v = 0.0;
+        HQS_BATCH_DISPATCH(S.A.n, (v = pc_cols<N>(S, it_ * HQS_BATCH_Q, a, bcoef, s, twN)));
+        v = cta_sum(v, red);
+        if (threadIdx.x == 0) acc[0][si] += v;
+    });
+    __syncthreads();
+    put_slice_partials(B.part + (size_t)BS_RZ * ns * G, ns, acc[0]);
+    BB_BARRIER();
+    slice_totals(B.part + (size_t)BS_RZ * ns * G, ns, tot[0]);
+    for (int i = threadIdx.x; i < ns; i += blockDim.x) {
+        const int n = B.sl[i].A.n;
+        rzs[i] = tot[0][i] / ((double)n * n);
+        if (active[i] && !(rzs[i] > 0.0 && !isinf(rzs[i]))) {
+            stat[i] = HQS_ERR_BREAKDOWN;
+            active[i] = 0;
+        }
+    }
+    __syncthreads();
+    COUNT_ACTIVE();
+    for (int cg = 0; cg < B.max_iter && nact > 0; ++cg) {
+        // p = z + beta p
+        FOR_ITEMS(BL_IMG, {
+            STAGE_TWN(S, si);
+            HQS_BATCH_DISPATCH(S.A.n, (z_and_p_row<N2, N>(S, it_, (float)betas[si], cg == 0, s, nullptr, twN)));
+        });
+        BB_BARRIER();
+        // q = a A^H A p + b p, <p, q>
+        FOR_ITEMS(BL_ROWS, {
+            const int n = S.A.n, ch = it_ / n, iy = it_ - ch * n;
+            HQS_BATCH_DISPATCH(n, (toep_rows_fwd_item<N2, HQS_BATCH_BD>(S.A, iy, ch, S.p, nullptr, 0.f, false, s)));
+        });
+        BB_BARRIER();
+        FOR_ITEMS(BL_COLS, {
+            const int n = S.A.n, N2v = 2 * n, ch = it_ / N2v, kx = it_ - ch * N2v;
+            HQS_BATCH_DISPATCH(n, (toep_cols_item<N2, HQS_BATCH_BD>(S.A, kx, ch, s)));
+        });
+        BB_BARRIER();
+        CLEAR_ACC();
+        FOR_ITEMS(BL_ROWS, {
+            const int n = S.A.n, ch = it_ / n, iy = it_ - ch * n;
+            double v = 0.0;
+            HQS_BATCH_DISPATCH(n, (v = toep_rows_adj_item<N2, HQS_BATCH_BD>(S.A, iy, ch, S.q, S.p, a, bcoef, 1, s)));
+            v = cta_sum(v, red);
+            if (threadIdx.x == 0) acc[0][si] += v;
+        });
+        BB_BARRIER();
+        FOR_ITEMS(BL_EPI, {   // several coil chunks: fixed-order chunk sum + epilogue
+            const int n = S.A.n, cnt = n * n;
+            double v = 0.0;
+            for (int ix = threadIdx.x; ix < n; ix += blockDim.x) {
+                const size_t e = (size_t)it_ * n + ix;
+                float2 w = make_float2(0.f, 0.f);
+                for (int c = 0; c < S.A.nchunk; ++c) w = cadd(w, __ldcg(S.A.chunk + (size_t)c * cnt + e));
+                S.q[e] = toep_epilogue(w, e, S.p, a, bcoef, 1, v);
+            }
+            v = cta_sum(v, red);
+            if (threadIdx.x == 0) acc[0][si] += v;
+        });
+        __syncthreads();
+        put_slice_partials(B.part + (size_t)BS_PQ * ns * G, ns, acc[0]);
+        BB_BARRIER();
+        slice_totals(B.part + (size_t)BS_PQ * ns * G, ns, tot[0]);
+        for (int i = threadIdx.x; i < ns; i += blockDim.x) {
+            const double pq = tot[0][i];
+            alphas[i] = (pq > 0.0 && !isinf(pq)) ? rzs[i] / pq : 0.0;
+            if (active[i] && !(pq > 0.0 && !isinf(pq))) {
+                stat[i] = HQS_ERR_BREAKDOWN;
+                active[i] = 0;
+            }
+        }
+        __syncthreads();
+        // x += alpha p, r -= alpha q, ||r||^2, row FFTs of r
+        CLEAR_ACC();
+        FOR_ITEMS(BL_PC, {
+            STAGE_TWN(S, si);
+            double v = 0.0;
+            HQS_BATCH_DISPATCH(S.A.n, (v = pc_rows<N>(S, it_ * HQS_BATCH_Q, (float)alphas[si], true, s, twN)));
+            v = cta_sum(v, red);
+            if (threadIdx.x == 0) acc[1][si] += v;
+        });
+        __syncthreads();
+        put_slice_partials(B.part + (size_t)BS_RR * ns * G, ns, acc[1]);
+        BB_BARRIER();
+        slice_totals(B.part + (size_t)BS_RR * ns * G, ns, tot[1]);
+        for (int i = threadIdx.x; i < ns; i += blockDim.x) {
+            if (!active[i]) continue;
+            const double rr = tot[1][i];
+            its[i] += 1;
+            rrs[i] = rr;
+            if (!(rr == rr) || isinf(rr)) {
+                stat[i] = HQS_ERR_BREAKDOWN;
+                active[i] = 0;
+            } else if (rr <= B.tol2 * bbs[i]) {
+                active[i] = 0;
+            } else if (its[i] >= B.max_iter) {
+                if (B.tol2 > 0.0) stat[i] = HQS_ERR_NOT_CONVERGED;
+                active[i] = 0;
+            }
+        }
+        __syncthreads();
+        COUNT_ACTIVE();
+        if (nact == 0) break;
+        // preconditioner columns, <r, z>, beta
+        CLEAR_ACC();
+        FOR_ITEMS(BL_PC, {
+            STAGE_TWN(S, si);
+            double v = 0.0;
+            HQS_BATCH_DISPATCH(S.A.n, (v = pc_cols<N>(S, it_ * HQS_BATCH_Q, a, bcoef, s, twN)));
+            v = cta_sum(v, red);
+            if (threadIdx.x == 0) acc[0][si] += v;
+        });
+        __syncthreads();
+        put_slice_partials(B.part + (size_t)BS_RZ * ns * G, ns, acc[0]);
+        BB_BARRIER();
+        slice_totals(B.part + (size_t)BS_RZ * ns * G, ns, tot[0]);
+        for (int i = threadIdx.x; i < ns; i += blockDim.x) {
+            const int n = B.sl[i].A.n;
+            const double rz_new = tot[0][i] / ((double)n * n);
+            if (active[i] && !(rz_new > 0.0 && !isinf(rz_new))) {
+                stat[i] = HQS_ERR_BREAKDOWN;
+                active[i] = 0;
+            }
+            betas[i] = rzs[i] > 0.0 ? rz_new / rzs[i] : 0.0;
+            rzs[i] = rz_new;
+        }
+        __syncthreads();
+        COUNT_ACTIVE();
+    }
+    if (bid == 0)
+        for (int i = threadIdx.x; i < ns; i += blockDim.x) {
+            B.res[i] = bbs[i] > 0.0 ? rrs[i] / bbs[i] : 0.0;
+            B.iters[i] = its[i];
+            B.status[i] = stat[i];
+        }
+#undef BB_BARRIER
+#undef FOR_ITEMS
+#undef STAGE_TWN
+#undef CLEAR_ACC
+#undef COUNT_ACTIVE
+}
+
 }  // namespace
 
 struct hqs_batch_s {
@@ -479,6 +733,13 @@ struct hqs_batch_s {
     int key_K = -1, key_k0 = -1, key_cg = -1;
     float key_c0 = 0.f;
     std::vector<float2*> chunks;   // per-slice coil-chunk partial sums
+    // batched data-consistency solve: its own slice table (u = x, rhs = the
+    // caller's), rebuilt when the caller's pointers change
+    std::vector<BatchSlice> dc_host;
+    BatchSlice* d_slices_dc = nullptr;
+    int* d_iters = nullptr;
+    int* d_status = nullptr;
+    std::vector<const void*> dc_key;
 };
 
 static void batch_free(hqs_batch_s* b) {
@@ -499,6 +760,9 @@ static void batch_free(hqs_batch_s* b) {
     cudaFreeHost(b->h_taps);
     cudaFreeHost(b->h_radius);
     for (float2* c : b->chunks) cudaFree(c);
+    cudaFree(b->d_slices_dc);
+    cudaFree(b->d_iters);
+    cudaFree(b->d_status);
     delete b;
 }
 
@@ -575,6 +839,10 @@ extern "C" int hqs_batch_create(hqs_batch* out, hqs_plan* plans, int n, int max_
         cudaMallocHost(&b->h_taps, (size_t)max_outer * (2 * HQS_BATCH_MAXR + 1) * sizeof(float)) ||
         cudaMallocHost(&b->h_radius, max_outer * sizeof(int)) ||
         cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking))
+        return fail(HQS_ERR_OOM);
+    b->dc_host = hs;
+    if (cudaMalloc(&b->d_slices_dc, n * sizeof(BatchSlice)) || cudaMalloc(&b->d_iters, n * sizeof(int)) ||
+        cudaMalloc(&b->d_status, n * sizeof(int)))
         return fail(HQS_ERR_OOM);
     if (cudaMemcpy(b->d_slices, hs.data(), n * sizeof(BatchSlice), cudaMemcpyHostToDevice) ||
         cudaMemcpy(b->d_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice))
@@ -700,5 +968,77 @@ extern "C" int hqs_batch_status(hqs_batch b, double* rel_res, void* stream) {
     HQS_CUDA_TRY(cudaStreamSynchronize(st));
     if (rel_res)
         for (int i = 0; i < b->ns; ++i) rel_res[i] = std::sqrt(std::max(r[i], 0.0));
+    return (err & HQS_DEVERR_TIMEOUT) ? HQS_ERR_TIMEOUT : HQS_OK;
+}
+
+extern "C" int hqs_batch_dc_solve(hqs_batch b, const hqs_c64* const* rhs, hqs_c64* const* x, float a, float bcoef,
+                                  int max_iter, double rel_tol, void* stream) {
+    if (!b || !rhs || !x || !(a == a) || !(bcoef > 0.f) || max_iter < 0 || max_iter > HQS_MAX_ITERS ||
+        !(rel_tol >= 0.0))
+        return HQS_ERR_INVALID_ARG;
+    for (int i = 0; i < b->ns; ++i)
+        if (!rhs[i] || !x[i]) return HQS_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<const void*> key;
+    for (int i = 0; i < b->ns; ++i) {
+        key.push_back(rhs[i]);
+        key.push_back(x[i]);
+    }
+    if (key != b->dc_key) {
+        // a previous solve may still read the table
+        HQS_CUDA_TRY(cudaStreamSynchronize(st));
+        for (int i = 0; i < b->ns; ++i) {
+            b->dc_host[i].u = reinterpret_cast<float2*>(x[i]);
+            b->dc_host[i].rhs = const_cast<float2*>(reinterpret_cast<const float2*>(rhs[i]));
+            b->dc_host[i].x = nullptr;
+        }
+        HQS_CUDA_TRY(cudaMemcpy(b->d_slices_dc, b->dc_host.data(), b->ns * sizeof(BatchSlice),
+                                cudaMemcpyHostToDevice));
+        b->dc_key = key;
+    }
+    HQS_CUDA_TRY(cudaMemsetAsync(b->d_bar, 0, 2 * sizeof(unsigned), st));
+    HQS_CUDA_TRY(cudaMemsetAsync(b->d_err, 0, sizeof(unsigned), st));
+    DcBatchArgs A;
+    A.sl = b->d_slices_dc;
+    A.ns = b->ns;
+    A.off = b->d_off;
+    A.a = a;
+    A.b = bcoef;
+    A.max_iter = max_iter;
+    A.tol2 = rel_tol * rel_tol;
+    A.part = b->d_part;
+    A.res = b->d_res;
+    A.iters = b->d_iters;
+    A.status = b->d_status;
+    A.bar = b->d_bar;
+    A.err = b->d_err;
+    const size_t sm = kBatchSmemF2 * sizeof(float2);
+    HQS_CUDA_TRY(cudaFuncSetAttribute(k_pcg_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    int per_sm = 0, nsm = 0;
+    HQS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_batch, HQS_BATCH_BD, sm));
+    HQS_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->device));
+    if (per_sm < 1) return HQS_ERR_UNSUPPORTED;
+    const int grid = std::min(b->grid, per_sm * nsm);   // d_part holds b->grid partials per slot
+    void* args[] = {&A};
+    HQS_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_pcg_batch, dim3(grid), dim3(HQS_BATCH_BD), args, sm, st));
+    return HQS_OK;
+}
+
+extern "C" int hqs_batch_dc_info(hqs_batch b, int* iterations, double* rel_residual, int* status, void* stream) {
+    if (!b) return HQS_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned err = 0;
+    std::vector<int> it(b->ns), stt(b->ns);
+    std::vector<double> r(b->ns);
+    HQS_CUDA_TRY(cudaMemcpyAsync(&err, b->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    HQS_CUDA_TRY(cudaMemcpyAsync(it.data(), b->d_iters, b->ns * sizeof(int), cudaMemcpyDeviceToHost, st));
+    HQS_CUDA_TRY(cudaMemcpyAsync(stt.data(), b->d_status, b->ns * sizeof(int), cudaMemcpyDeviceToHost, st));
+    HQS_CUDA_TRY(cudaMemcpyAsync(r.data(), b->d_res, b->ns * sizeof(double), cudaMemcpyDeviceToHost, st));
+    HQS_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int i = 0; i < b->ns; ++i) {
+        if (iterations) iterations[i] = it[i];
+        if (rel_residual) rel_residual[i] = std::sqrt(std::max(r[i], 0.0));
+        if (status) status[i] = stt[i];
+    }
     return (err & HQS_DEVERR_TIMEOUT) ? HQS_ERR_TIMEOUT : HQS_OK;
 }

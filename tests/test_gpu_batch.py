@@ -92,3 +92,62 @@ def test_batched_hqs_rejects_unsupported_metric():
     with pytest.raises(hq().HqsError) as ei:
         batch.run(ys, xs, [0.1], [0.1], c1=-0.5)
     assert ei.value.status == hq().HQS_ERR_UNSUPPORTED
+
+
+def test_batched_dc_solve_matches_oracle_and_per_slice_solves():
+    """One launch, DC-preconditioned CG for every slice: 5 fixed iterations
+    match the oracle's PCG per slice within max(1e-5, 4x the oracle's own
+    deviation under a 2^-24 perturbation of the right-hand side); to
+    tolerance 1e-4 every slice
+    stops on its own (iterations within 1 of the per-slice persistent solve),
+    with the true residual checked in fp64; a zero right-hand side gives
+    x = 0 after no iterations while the other slices still run."""
+    from oracle import solvers
+    slices = build(slice_cases())
+    batch = hq().Batch([p for _, p, _ in slices], max_outer=2)
+    mu = 1e-2
+    rhs_np, Hs, Ms = [], [], []
+    for case, _, y in slices:
+        n = case["n"]
+        c = toeplitz.kernel(case["traj"], n, n)
+        Kh, lam = toeplitz.khat(c), toeplitz.chan_symbol(c, n, n)
+        b = nufft.adjoint(y, case["smaps"], case["traj"], case["W"], case["sigma"])
+        rhs_np.append(b.astype(np.complex64).astype(np.complex128))
+        Hs.append(lambda v, S=case["smaps"], Kh=Kh: toeplitz.normal(v, S, Kh) + mu * v)
+        Ms.append(lambda v, lam=lam: toeplitz.precond_apply(v, lam, 1.0, mu))
+    rhs = [to_dev(b) for b in rhs_np]
+    xs = [torch.full(r.shape, 3.0 + 1j, dtype=torch.complex64, device="cuda") for r in rhs]
+    batch.dc_solve(rhs, xs, 1.0, mu, max_iter=5, rel_tol=0.0)
+    info = batch.dc_info()
+    rng = np.random.default_rng(3)
+    for i, (x, b) in enumerate(zip(xs, rhs_np)):
+        want, _ = solvers.pcg(Hs[i], b, np.zeros_like(b), Ms[i], max_iter=5, tol=0.0)
+        bp = b * (1 + 2.0 ** -24 * rng.normal(size=b.shape))
+        pert, _ = solvers.pcg(Hs[i], bp, np.zeros_like(b), Ms[i], max_iter=5, tol=0.0)
+        tol = max(1e-5, 4 * rel(pert, want))
+        xf = torch.zeros_like(x)
+        hq().dc_solve(slices[i][1], 1.0, mu, rhs[i], xf, max_iter=5, rel_tol=0.0, mode=hq().HQS_SOLVE_FUSED)
+        print(f"slice {i}, 5 iterations: batched {rel(to_host(x), want):.2e}, per-slice fused "
+              f"{rel(to_host(xf), want):.2e}, bound {tol:.2e}")
+        assert info[i][0] == 5 and info[i][2] == 0
+        assert rel(to_host(x), want) <= tol, (i, rel(to_host(x), want), tol)
+    # to tolerance, against the per-slice persistent solve
+    for x in xs:
+        x.zero_()
+    batch.dc_solve(rhs, xs, 1.0, mu, max_iter=200, rel_tol=1e-4)
+    info = batch.dc_info()
+    for i, ((case, plan, _), x, b) in enumerate(zip(slices, xs, rhs_np)):
+        xf = torch.zeros_like(x)
+        inf = hq().dc_solve(plan, 1.0, mu, rhs[i], xf, max_iter=200, rel_tol=1e-4, mode=hq().HQS_SOLVE_FUSED)
+        its, rr, st = info[i]
+        print(f"slice {i}: batched {its} iterations (rel {rr:.2e}), per-slice {inf.iterations}")
+        assert st == 0 and rr <= 1e-4 and abs(its - inf.iterations) <= 1
+        assert np.linalg.norm(b - Hs[i](to_host(x))) / np.linalg.norm(b) <= 1.2e-4
+    # a zero right-hand side in the batch
+    rhs[2] = torch.zeros_like(rhs[2])
+    for x in xs:
+        x.fill_(1.0)
+    batch.dc_solve(rhs, xs, 1.0, mu, max_iter=200, rel_tol=1e-4)
+    info = batch.dc_info()
+    assert info[2][0] == 0 and float(torch.abs(xs[2]).max()) == 0.0
+    assert all(info[i][2] == 0 and info[i][1] <= 1e-4 for i in range(len(xs)))
