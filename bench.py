@@ -6,11 +6,15 @@ with A^H A applies per second and the per-stage (plain) PCG path beside it.
 A step is one DC solve for each slice of a batch of B slices: A^H y
 (adjoint NUFFT), rhs = A^H y + mu z, and the preconditioned CG solve of
 (A^H A + mu I) x = rhs, each slice with its own phantom and coil maps (one
-plan per slice).  The batch's resident inputs exceed the 129 MB L2, so no
+plan per slice).  By default (--mode batched) the B solves run in one
+cooperative launch (hqs_batch_dc_solve), each slice to its own tolerance;
+--mode fused launches the persistent solve once per slice, --mode plain
+the per-stage PCG.  The batch's resident inputs exceed the 129 MB L2, so no
 explicit flush is needed between steps.  Inputs are synthetic (seeded
 ellipse phantoms, Gaussian-bump coil maps, spiral trajectory).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B] [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B] [--mode batched|fused|plain]
+                  [--impl ours|reference]
   python bench.py --workload batch64     # 64 uneven slices, batched HQS 20 x 5
   python bench.py --workload mixed320    # A^H A and DC solves at FP32 / BF16x3 / FP16x3
   python bench.py --workload hqs320      # annealed HQS 10 x 5 and PnP-PGD 10 steps, Id / F-1 / Chebyshev
@@ -71,6 +75,8 @@ ADJ_BYTES = (_Y + _PTS + _G2L) + (_G2L + _ROWS) + (_ROWS + _S + 320 * 320 * 8)
 # capture of the current kernel (profiles/pcg_persistent_320x16.md); None while
 # the kernel has changed since the last capture.
 PERSISTENT_TRAFFIC_BYTES = 16408576 + 2208768
+# The same for one k_pcg_batch launch (all 8 slices of a step); None until captured.
+BATCH_TRAFFIC_BYTES = None
 
 
 def parse():
@@ -80,7 +86,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="fused", choices=["fused", "plain"])
+    ap.add_argument("--mode", default="batched", choices=["batched", "fused", "plain"])
     ap.add_argument("--workload", default="dc320",
                     choices=["dc320", "batch64", "mixed320", "hqs320", "learned320"])
     return ap.parse_args()
@@ -260,15 +266,22 @@ def run_ours(args, rank, world, dist):
         zs.append(z)
         rhss.append(torch.empty_like(x))
         xs.append(torch.zeros_like(x))
-    mode = hq.HQS_SOLVE_FUSED if args.mode == "fused" else hq.HQS_SOLVE_PLAIN
+    batch = hq.Batch(plans, max_outer=1) if args.mode == "batched" else None
     stream = torch.cuda.current_stream()
 
-    def step(mode_=mode, ys_=None):
+    def solve_all(mode_):
+        if mode_ == "batched":
+            batch.dc_solve(rhss, xs, 1.0, MU, max_iter=MAX_ITER, rel_tol=TOL)
+            return
+        flag = hq.HQS_SOLVE_FUSED if mode_ == "fused" else hq.HQS_SOLVE_PLAIN
+        for i in range(B):
+            hq.dc_solve(plans[i], 1.0, MU, rhss[i], xs[i], max_iter=MAX_ITER, rel_tol=TOL,
+                        precond=hq.HQS_PRECOND_DC, mode=flag | hq.HQS_SOLVE_X0_ZERO, want_info=False)
+
+    def step(mode_=args.mode, ys_=None):
         for i in range(B):
             hq.adjoint_axpy(plans[i], ys[i] if ys_ is None else ys_[i], MU, zs[i], rhss[i])
-            hq.dc_solve(plans[i], 1.0, MU, rhss[i], xs[i], max_iter=MAX_ITER, rel_tol=TOL,
-                        precond=hq.HQS_PRECOND_DC, mode=mode_ | hq.HQS_SOLVE_X0_ZERO,
-                        want_info=False)
+        solve_all(mode_)
 
     def barrier():
         if dist is not None:
@@ -287,13 +300,21 @@ def run_ours(args, rank, world, dist):
         return max_over_ranks(ms, dist)
 
     # iteration counts and residuals (untimed)
-    iters = []
     for i in range(B):
         hq.adjoint_axpy(plans[i], ys[i], MU, zs[i], rhss[i])
-        inf = hq.dc_solve(plans[i], 1.0, MU, rhss[i], xs[i], max_iter=MAX_ITER, rel_tol=TOL,
-                          mode=mode | hq.HQS_SOLVE_X0_ZERO)
-        iters.append(inf.iterations)
-        assert inf.rel_residual <= TOL
+    if args.mode == "batched":
+        batch.dc_solve(rhss, xs, 1.0, MU, max_iter=MAX_ITER, rel_tol=TOL)
+        info = batch.dc_info()
+        iters = [it for it, _, _ in info]
+        assert all(st == 0 and rr <= TOL for _, rr, st in info)
+    else:
+        iters = []
+        flag = hq.HQS_SOLVE_FUSED if args.mode == "fused" else hq.HQS_SOLVE_PLAIN
+        for i in range(B):
+            inf = hq.dc_solve(plans[i], 1.0, MU, rhss[i], xs[i], max_iter=MAX_ITER, rel_tol=TOL,
+                              mode=flag | hq.HQS_SOLVE_X0_ZERO)
+            iters.append(inf.iterations)
+            assert inf.rel_residual <= TOL
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -303,25 +324,26 @@ def run_ours(args, rank, world, dist):
     clocks = clk.stop()
     value = whole_job_rate(B * args.steps, world, ms)
 
-    # the dominant kernel: the persistent solve, timed alone on the launching stream
-    e_solve = []
+    # the dominant kernel, timed alone on the launching stream: the batched solve
+    # (one launch for all B slices) or the persistent solve (one launch per slice)
     for i in range(B):
         hq.adjoint_axpy(plans[i], ys[i], MU, zs[i], rhss[i])
     torch.cuda.synchronize()
-    for rep in range(2):
-        for i in range(B):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            hq.dc_solve(plans[i], 1.0, MU, rhss[i], xs[i], max_iter=MAX_ITER, rel_tol=TOL,
-                        precond=hq.HQS_PRECOND_DC, mode=mode | hq.HQS_SOLVE_X0_ZERO, want_info=False)
-            e1.record(stream)
-            e_solve.append((e0, e1))
+    e_solve = []
+    for rep in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        solve_all(args.mode if args.mode != "plain" else "fused")
+        e1.record(stream)
+        e_solve.append((e0, e1))
     torch.cuda.synchronize()
-    solve_ms = float(np.mean([a.elapsed_time(b) for a, b in e_solve[B:]]))
+    launch_ms = float(np.mean([a.elapsed_time(b) for a, b in e_solve[1:]]))
+    solves_per_launch = B if args.mode == "batched" else 1
+    solve_ms = launch_ms / (1 if args.mode == "batched" else B)   # per launch
     mean_iters = float(np.mean(iters))
 
     # plain PCG (per-stage launches, host-checked residual) and A^H A applies/s
-    ms_plain = timed(lambda: step(hq.HQS_SOLVE_PLAIN), max(1, args.steps // 2))
+    ms_plain = timed(lambda: step("plain"), max(1, args.steps // 2))
     plain_value = B * max(1, args.steps // 2) * world / (ms_plain / 1e3)
     outs = [torch.empty_like(x) for x in xs]
     reps = 10
@@ -376,14 +398,15 @@ def run_ours(args, rank, world, dist):
         return
     # roofline of the persistent solve: FP32 ALU work per launch / duration
     flops_iter = aha_flops(n, L) + precond_flops(n) + 12 * 8 * n * n
-    flops_launch = flops_iter * mean_iters
+    flops_launch = flops_iter * mean_iters * solves_per_launch
     achieved = flops_launch / (solve_ms / 1e3) / 1e12
     sm_max = clocks.get("sm_max_mhz") or 2070.0
     nominal = 152 * 128 * 2 * sm_max * 1e6 / 1e12
     peak = fp32_peak
     cpu_t_it, cpu_plan = cpu_oracle_sample(1)
     cpu_value = 1.0 / (cpu_t_it * mean_iters)
-    launches_per_solve = 4   # spread, column IFFT, row IFFT + axpy, persistent solve
+    # per step: spread, column IFFT, row IFFT + axpy per slice, then the solve launch(es)
+    launches_per_step = 3 * B + (1 if args.mode == "batched" else B)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -407,8 +430,10 @@ def run_ours(args, rank, world, dist):
         "speedup_vs_plain_pcg": value / plain_value,
         "mean_cg_iterations": mean_iters,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": PERSISTENT_TRAFFIC_BYTES,
-                     "kernel": "k_pcg_persistent<640,320>",
+                     "frac": achieved / peak,
+                     "traffic": BATCH_TRAFFIC_BYTES if args.mode == "batched" else PERSISTENT_TRAFFIC_BYTES,
+                     "kernel": (f"k_pcg_batch ({B} slices per launch)" if args.mode == "batched"
+                                else "k_pcg_persistent<640,320>"),
                      "peak_source": "measured: FP32 FMA probe (hqs_probe_fp32_peak, 8 independent chains per "
                                     "thread, full occupancy) on this GPU after the timed region",
                      "nominal": nominal},
@@ -417,7 +442,7 @@ def run_ours(args, rank, world, dist):
                                    f"scaled to {mean_iters:.1f} iterations per solve; oracle plan "
                                    f"{cpu_plan:.1f} s not included"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": launches_per_solve * B * args.steps,
+        "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
