@@ -75,8 +75,8 @@ ADJ_BYTES = (_Y + _PTS + _G2L) + (_G2L + _ROWS) + (_ROWS + _S + 320 * 320 * 8)
 # capture of the current kernel (profiles/pcg_persistent_320x16.md); None while
 # the kernel has changed since the last capture.
 PERSISTENT_TRAFFIC_BYTES = 16408576 + 2208768
-# The same for one k_pcg_batch launch (all 8 slices of a step); None until captured.
-BATCH_TRAFFIC_BYTES = None
+# The same for one k_pcg_batch launch (all 16 slices of a default step); None until captured.
+BATCH_TRAFFIC_BYTES = 49974686464 + 33292417280
 
 
 def parse():
@@ -84,9 +84,10 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--batch", type=int, default=16)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="batched", choices=["batched", "fused", "plain"])
+    ap.add_argument("--group", type=int, default=64, help="slices per batched launch (at most 64)")
     ap.add_argument("--workload", default="dc320",
                     choices=["dc320", "batch64", "mixed320", "hqs320", "learned320"])
     return ap.parse_args()
@@ -266,12 +267,15 @@ def run_ours(args, rank, world, dist):
         zs.append(z)
         rhss.append(torch.empty_like(x))
         xs.append(torch.zeros_like(x))
-    batch = hq.Batch(plans, max_outer=1) if args.mode == "batched" else None
+    G_ = max(1, min(args.group, B))
+    groups = [list(range(i, min(i + G_, B))) for i in range(0, B, G_)]
+    batches = [hq.Batch([plans[i] for i in g], max_outer=1) for g in groups] if args.mode == "batched" else []
     stream = torch.cuda.current_stream()
 
     def solve_all(mode_):
         if mode_ == "batched":
-            batch.dc_solve(rhss, xs, 1.0, MU, max_iter=MAX_ITER, rel_tol=TOL)
+            for g, bt in zip(groups, batches):
+                bt.dc_solve([rhss[i] for i in g], [xs[i] for i in g], 1.0, MU, max_iter=MAX_ITER, rel_tol=TOL)
             return
         flag = hq.HQS_SOLVE_FUSED if mode_ == "fused" else hq.HQS_SOLVE_PLAIN
         for i in range(B):
@@ -303,8 +307,8 @@ def run_ours(args, rank, world, dist):
     for i in range(B):
         hq.adjoint_axpy(plans[i], ys[i], MU, zs[i], rhss[i])
     if args.mode == "batched":
-        batch.dc_solve(rhss, xs, 1.0, MU, max_iter=MAX_ITER, rel_tol=TOL)
-        info = batch.dc_info()
+        solve_all("batched")
+        info = [t for bt in batches for t in bt.dc_info()]
         iters = [it for it, _, _ in info]
         assert all(st == 0 and rr <= TOL for _, rr, st in info)
     else:
@@ -338,8 +342,8 @@ def run_ours(args, rank, world, dist):
         e_solve.append((e0, e1))
     torch.cuda.synchronize()
     launch_ms = float(np.mean([a.elapsed_time(b) for a, b in e_solve[1:]]))
-    solves_per_launch = B if args.mode == "batched" else 1
-    solve_ms = launch_ms / (1 if args.mode == "batched" else B)   # per launch
+    solves_per_launch = len(groups[0]) if args.mode == "batched" else 1
+    solve_ms = launch_ms / (len(groups) if args.mode == "batched" else B)   # per launch
     mean_iters = float(np.mean(iters))
 
     # plain PCG (per-stage launches, host-checked residual) and A^H A applies/s
@@ -406,7 +410,7 @@ def run_ours(args, rank, world, dist):
     cpu_t_it, cpu_plan = cpu_oracle_sample(1)
     cpu_value = 1.0 / (cpu_t_it * mean_iters)
     # per step: spread, column IFFT, row IFFT + axpy per slice, then the solve launch(es)
-    launches_per_step = 3 * B + (1 if args.mode == "batched" else B)
+    launches_per_step = 3 * B + (len(groups) if args.mode == "batched" else B)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -414,7 +418,8 @@ def run_ours(args, rank, world, dist):
         "data": "synthetic (seeded ellipse phantoms, Gaussian-bump coil maps, VD spiral)",
         "config": {"workload": "brain-sized DC solve: 320x320, 16 coils, spiral 16x2048 (32768 pts), "
                                "KB W=6, sigma=2, mu=1e-2, rel. residual 1e-4, DC-preconditioned CG",
-                   "batch_per_gpu": B, "solver": args.mode, "parallelism": f"replicas x{world}",
+                   "batch_per_gpu": B, "solver": args.mode,
+                   "slices_per_launch": len(groups[0]) if args.mode == "batched" else 1, "parallelism": f"replicas x{world}",
                    "tuning": {"spread_tile": tuned.spread_tile, "pc_lines": tuned.pc_lines,
                               "fused_grid": tuned.fused_grid},
                    "l2": "inputs larger than L2 (batch of distinct slices), no flush"},
@@ -432,7 +437,7 @@ def run_ours(args, rank, world, dist):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
                      "traffic": BATCH_TRAFFIC_BYTES if args.mode == "batched" else PERSISTENT_TRAFFIC_BYTES,
-                     "kernel": (f"k_pcg_batch ({B} slices per launch)" if args.mode == "batched"
+                     "kernel": (f"k_pcg_batch ({len(groups[0])} slices per launch)" if args.mode == "batched"
                                 else "k_pcg_persistent<640,320>"),
                      "peak_source": "measured: FP32 FMA probe (hqs_probe_fp32_peak, 8 independent chains per "
                                     "thread, full occupancy) on this GPU after the timed region",
