@@ -25,7 +25,7 @@ using namespace hqs;
 #define HQS_BATCH_MAX 64
 #define HQS_BATCH_BD 256
 #define HQS_BATCH_MAXR 24
-#define HQS_BATCH_Q 4
+#define HQS_BATCH_Q 8   // preconditioner lines per item: Q x TPL(n) <= block size for every n
 
 namespace {
 
@@ -109,6 +109,7 @@ HQS_DEV void z_and_p_row(const BatchSlice& S, int iy, float beta, bool first, fl
 
 template <int N>
 HQS_DEV double pc_rows(const BatchSlice& S, int r0, float alpha, bool update, float2* s, const float2* twN) {
+    static_assert(HQS_BATCH_Q * FftSize<N>::TPL <= HQS_BATCH_BD, "a preconditioner item needs more threads");
     const int lines = min(HQS_BATCH_Q, N - r0);
     double rr = 0.0;
     for (int e = threadIdx.x; e < lines * N; e += blockDim.x) {
@@ -140,6 +141,7 @@ HQS_DEV double pc_rows(const BatchSlice& S, int r0, float alpha, bool update, fl
 
 template <int N>
 HQS_DEV double pc_cols(const BatchSlice& S, int c0, float a, float b, float2* s, const float2* twN) {
+    static_assert(HQS_BATCH_Q * FftSize<N>::TPL <= HQS_BATCH_BD, "a preconditioner item needs more threads");
     const int lines = min(HQS_BATCH_Q, N - c0);
     for (int e = threadIdx.x; e < N * lines; e += blockDim.x) {
         const int pos = e / lines, q_ = e - pos * lines;

@@ -25,6 +25,8 @@ def slice_cases():
         dict(n=128, L=20, W=6, traj=synth.traj_spiral(12, 1024, 128), seed=2),   # two coil chunks
         dict(n=64, L=8, W=6, traj=synth.traj_spiral(8, 512, 64), seed=3),
         dict(n=128, L=5, W=4, traj=synth.traj_radial(40, 256), seed=4),
+        # 256^2: 512-point row FFTs (8 lines per item) and 256-point preconditioner items
+        dict(n=256, L=6, W=4, traj=synth.traj_radial(48, 512), seed=5),
     ]
 
 
