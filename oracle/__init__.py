@@ -17,6 +17,7 @@ nudft     exact non-uniform DFT forward/adjoint (the definition of A in Eq. (1))
 nufft     gridding NUFFT with the same kernel parameters as the GPU path.
 toeplitz  Toeplitz embedding of A^H A and the Strang circulant preconditioner.
 solvers   PCG, flexible CG, CG energy, power iteration.
+smaps     S-map estimation from the windowed k-space centre (Sec. 4.1).
 hqs       PnP-HQS / PnP-PGD loops (Sec. 3.3), Gaussian-smoothing denoiser,
           P-metric prox coefficients (Sec. 3.4).
 convnet   small 2-channel conv net: forward, backward, Adam.

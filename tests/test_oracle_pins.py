@@ -470,3 +470,57 @@ def test_learned_preconditioner_starts_as_dc_preconditioner():
     r = P["b0"]
     z = convnet.learned_precond(r, P["lam"], 1.0, 0.05, params)
     assert rel(z, toeplitz.precond_apply(r, P["lam"], 1.0, 0.05)) < 1e-15
+
+
+# ------------------------------------------------------------------ S-maps (Sec. 4.1)
+def test_smaps_window_closed_form():
+    from oracle import smaps
+    n = 64
+    # u = 0, +-5, +-10, 12 Cartesian units on each axis
+    us = np.array([0.0, 5.0, -5.0, 10.0, -10.0, 12.0])
+    traj = np.stack([us * 2 * np.pi / n, np.zeros_like(us)], axis=1)
+    w = smaps.hamming_centre(traj, n, 20)
+    assert np.allclose(w, [1.0, 0.54, 0.54, 0.08, 0.08, 0.0], atol=1e-12)
+
+
+def test_smaps_estimate_normalised_masked_and_phase_covariant():
+    from oracle import nufft as onufft, smaps
+    n, L = 48, 4
+    traj = synth.traj_radial(32, 96)
+    x = synth.phantom(2, n)
+    S = synth.coil_maps(2, n, L)
+    y = onufft.forward(x, S, traj, 4, 2.0)
+    est, mask = smaps.estimate(y, traj, n, 4, 2.0, thresh=0.3)
+    rss = np.sqrt(np.sum(np.abs(est) ** 2, axis=0))
+    assert mask.any() and not mask.all()
+    assert np.allclose(rss[mask], 1.0, atol=1e-12) and np.all(rss[~mask] == 0.0)
+    # a common complex factor on the data only rotates every map by its phase
+    c = 3.0 * np.exp(0.7j)
+    est2, mask2 = smaps.estimate(c * y, traj, n, 4, 2.0, thresh=0.3)
+    assert np.array_equal(mask, mask2)
+    assert np.allclose(est2, np.exp(0.7j) * est, atol=1e-12)
+    # one coil: unit modulus on the mask
+    est1, m1 = smaps.estimate(y[:1], traj, n, 4, 2.0, thresh=0.3)
+    assert np.allclose(np.abs(est1[0][m1]), 1.0, atol=1e-12)
+
+
+def test_smaps_estimate_recovers_smooth_maps_of_a_smooth_object():
+    """For a smooth positive object and maps with root-sum-of-squares 1, the
+    windowed, density-compensated low-resolution coil images are ~ S_l times
+    a positive blur of the object, so the normalised estimate returns S_l on
+    the object; without the density weights the radial centre dominates and
+    the estimate is much worse."""
+    from oracle import nufft as onufft, smaps
+    n, L = 64, 6
+    yy, xx = np.mgrid[0:n, 0:n] - n / 2
+    x = np.exp(-(xx ** 2 + yy ** 2) / (2 * (0.3 * n) ** 2)).astype(np.complex128)
+    S = synth.coil_maps(5, n, L)
+    traj = synth.traj_radial(64, 2 * n)
+    y = onufft.forward(x, S, traj, 6, 2.0)
+    dcf = synth.dcf_voronoi(traj)
+    est, mask = smaps.estimate(y, traj, n, 6, 2.0, thresh=0.3, dcf=dcf)
+    err = np.linalg.norm((est - S)[:, mask]) / np.linalg.norm(S[:, mask])
+    raw, mraw = smaps.estimate(y, traj, n, 6, 2.0, thresh=0.3)
+    err_raw = np.linalg.norm((raw - S)[:, mraw]) / np.linalg.norm(S[:, mraw])
+    print(f"S-map recovery: {err:.3f} with density weights, {err_raw:.3f} without")
+    assert err < 0.1 and err < err_raw, (err, err_raw)
