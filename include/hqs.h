@@ -142,6 +142,19 @@ HQS_API int hqs_adjoint(hqs_plan plan, const hqs_c64* y, hqs_c64* x, void* strea
 HQS_API int hqs_adjoint_axpy(hqs_plan plan, const hqs_c64* y, float c, const hqs_c64* z,
                              hqs_c64* x, void* stream);
 
+/* S-map estimation (Sec. 4.1): c_l = A_1^H (w d y_l), the single-coil adjoint
+ * NUFFT of coil l's samples under the separable Hamming window
+ * w = h(u_x) h(u_y), h(u) = 0.54 + 0.46 cos(2 pi u / width) for |u| <= width/2
+ * (u = k n / 2 pi, Cartesian grid units; width 20 in the paper), times the
+ * optional per-sample density weights d (dcf, device M floats, or NULL);
+ * then S_l = c_l / sqrt(sum_l |c_l|^2) where that root-sum-of-squares is at
+ * least thresh times its maximum, S_l = 0 elsewhere.  traj: device M x 2
+ * (radians), y: device (coils, M), smaps: device (coils, n, n) out.  Builds
+ * and frees a one-coil plan and scratch: BLOCKING on `stream`. */
+HQS_API int hqs_estimate_smaps(const float* traj, int64_t M, const hqs_c64* y, const float* dcf, int n,
+                               int coils, int kernel_width, float oversamp, float width, float thresh,
+                               hqs_c64* smaps, void* stream);
+
 /* ------------------------------------------------- Toeplitz normal (a4) */
 /* out = A^H A x (Sec. 3.4, A = F_Omega (x) S_l) through the exact 2N
  * circulant embedding of F^H F; never touches the trajectory.

@@ -84,6 +84,8 @@ _SIGS = {
     "hqs_power_iteration": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_void_p]),
     "hqs_status_string": (C.c_char_p, [C.c_int]),
     "hqs_probe_fp32_peak": (C.c_int, [C.POINTER(C.c_double), C.c_void_p]),
+    "hqs_estimate_smaps": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,
+                                     C.c_float, C.c_float, C.c_float, C.c_void_p, C.c_void_p]),
     "hqs_plan_set_tuning": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "hqs_plan_retile": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "hqs_debug_toeplitz_stage": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
@@ -147,6 +149,18 @@ class HqsError(RuntimeError):
     def __init__(self, status: int, what: str):
         self.status = status
         super().__init__(f"{what}: {status_string(status)} ({status})")
+
+
+def estimate_smaps(traj, y, n, out, dcf=None, kernel_width=6, oversamp=2.0, width=20.0, thresh=0.05,
+                   stream=None):
+    """S-maps (coils, n, n) from the windowed k-space centre of y (coils, M)."""
+    coils, M = y.shape
+    _check(library().hqs_estimate_smaps(_ptr(traj, torch.float32, "traj"), int(M), _ptr(y, torch.complex64, "y"),
+                                        _ptr(dcf, torch.float32, "dcf") if dcf is not None else None, int(n),
+                                        int(coils), int(kernel_width), float(oversamp), float(width),
+                                        float(thresh), _ptr(out, torch.complex64, "smaps"), _stream(stream)),
+           "hqs_estimate_smaps")
+    return out
 
 
 def probe_fp32_peak(stream=None) -> float:

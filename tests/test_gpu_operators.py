@@ -411,3 +411,30 @@ def test_pgd_run_matches_oracle(metric):
     err = rel(to_host(x), want)
     print(f"PGD {metric}: rel err {err:.2e} (bound {tol:.2e})")
     assert err <= tol
+
+
+@pytest.mark.parametrize("use_dcf", [True, False], ids=["dcf", "no_dcf"])
+def test_estimate_smaps_matches_oracle(use_dcf):
+    """S-map estimation (Sec. 4.1) against the oracle: the mask agrees except
+    for pixels whose root-sum-of-squares lies within 1e-4 of the threshold
+    (a float decision), and the maps on the common mask to 1e-5."""
+    from oracle import smaps as osmaps
+    n, L = 64, 4
+    traj = synth.traj_radial(32, 128).astype(np.float32)
+    x = synth.phantom(4, n).astype(np.complex64).astype(np.complex128)
+    S = synth.coil_maps(4, n, L).astype(np.complex64).astype(np.complex128)
+    y = nufft.forward(x, S, traj, 6, 2.0).astype(np.complex64).astype(np.complex128)
+    dcf = synth.dcf_voronoi(traj).astype(np.float32) if use_dcf else None
+    want, mask = osmaps.estimate(y, traj, n, 6, 2.0, thresh=0.3, dcf=dcf)
+    out = torch.empty((L, n, n), dtype=torch.complex64, device="cuda")
+    hq().estimate_smaps(to_dev(traj, np.float32), to_dev(y), n, out,
+                        dcf=to_dev(dcf, np.float32) if use_dcf else None, kernel_width=6, thresh=0.3)
+    got = to_host(out)
+    gmask = np.sum(np.abs(got) ** 2, axis=0) > 0
+    c = osmaps.coil_images(y, traj, n, 6, 2.0, dcf=dcf)
+    rss = np.sqrt(np.sum(np.abs(c) ** 2, axis=0))
+    band = np.abs(rss - 0.3 * rss.max()) <= 1e-4 * rss.max()
+    assert np.all((gmask == mask) | band)
+    both = gmask & mask
+    assert rel(got[:, both], want[:, both]) <= 1e-5
+    assert np.allclose(np.sqrt(np.sum(np.abs(got[:, both]) ** 2, axis=0)), 1.0, atol=1e-5)
