@@ -247,6 +247,13 @@ HQS_API int hqs_net_backward(hqs_net net, const float* x, const float* dy, int N
                              float* grad, void* stream);
 HQS_API int hqs_net_train_step_dy(hqs_net net, const float* x, const float* dy, int N, int H, int W,
                                   float lr, void* stream);
+/* Conv-net denoiser with the hqs_denoiser_fn signature (user = the hqs_net):
+ * out = in - sigma net(in / sigma), the network predicting the noise of an
+ * image whose noise standard deviation (per real / imaginary part) is
+ * normalised to 1; sigma = 0 copies.  A sigma-conditioned stand-in for the
+ * paper's trained prior (Sec. 4.2) that hqs_run can call directly. */
+HQS_API int hqs_net_denoise(void* user, const hqs_c64* in, hqs_c64* out, int ny, int nx, float sigma,
+                            void* stream);
 HQS_API int hqs_net_save(hqs_net net, const char* path);
 HQS_API int hqs_net_load(hqs_net net, const char* path);
 /* attach (or detach with NULL) the network used by HQS_PRECOND_LEARNED; the

@@ -104,6 +104,7 @@ _SIGS = {
                                    C.c_void_p, C.c_void_p]),
     "hqs_net_train_step_dy": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,
                                         C.c_float, C.c_void_p]),
+    "hqs_net_denoise": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_float, C.c_void_p]),
     "hqs_net_save": (C.c_int, [C.c_void_p, C.c_char_p]),
     "hqs_net_load": (C.c_int, [C.c_void_p, C.c_char_p]),
     "hqs_plan_set_net": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -308,7 +309,12 @@ def hqs_run(plan: Plan, y, x, mu, sigma, K=None, k0=0, cg_iters=5, c0=1.0, c1=0.
     user = None
     cb = None
     keep = []
-    if denoiser is None:
+    if isinstance(denoiser, Net):
+        # the library's conv-net denoiser, called natively with the network as user data
+        cb = C.cast(lib.hqs_net_denoise, DENOISER_FN)
+        user = denoiser.handle
+        keep.append(denoiser)
+    elif denoiser is None:
         if gauss is not None:
             gp = GaussParams(float(gauss[0]), float(gauss[1]))
             keep.append(gp)
@@ -468,6 +474,13 @@ class Net:
         _check(library().hqs_net_train_step_dy(self.handle, _ptr(x, torch.float32, "x"),
                                                _ptr(dy, torch.float32, "dy"), N, H, W, float(lr),
                                                _stream(stream)), "hqs_net_train_step_dy")
+
+    def denoise(self, v, out, sigma, stream=None):
+        """out = v - sigma net(v / sigma) (complex64 image)."""
+        ny, nx = v.shape[-2], v.shape[-1]
+        _check(library().hqs_net_denoise(self.handle, _ptr(v, torch.complex64, "v"), _ptr(out, torch.complex64, "out"),
+                                         int(ny), int(nx), float(sigma), _stream(stream)), "hqs_net_denoise")
+        return out
 
     def save(self, path):
         _check(library().hqs_net_save(self.handle, str(path).encode()), "hqs_net_save")

@@ -360,3 +360,56 @@ extern "C" int hqs_learned_precond_apply(hqs_plan p, float a, float b, const hqs
     return learned_apply(p, a, b, reinterpret_cast<const float2*>(r), reinterpret_cast<float2*>(z),
                          (cudaStream_t)stream);
 }
+
+// ------------------------------------------------------------ conv denoiser
+// D_sigma(v) = v - sigma net(v / sigma): the network predicts the noise of an
+// image whose noise level is normalised to 1, which conditions it on sigma
+// (the paper's prior is a sigma-conditioned 2-channel network, Sec. 4.2; this
+// is a small stand-in built from the same convolution kernels).
+namespace {
+
+__global__ void k_denoise_split(const float2* __restrict__ v, int count, float inv_sigma, float* __restrict__ planar) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x) {
+        const float2 a = v[e];
+        planar[e] = a.x * inv_sigma;
+        planar[count + e] = a.y * inv_sigma;
+    }
+}
+
+__global__ void k_denoise_combine(const float2* __restrict__ v, const float* __restrict__ noise, int count,
+                                  float sigma, float2* __restrict__ out) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x) {
+        const float2 a = v[e];
+        out[e] = make_float2(fmaf(-sigma, noise[e], a.x), fmaf(-sigma, noise[count + e], a.y));
+    }
+}
+
+__global__ void k_copy_c64(const float2* __restrict__ a, float2* __restrict__ b, int count) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x) b[e] = a[e];
+}
+
+}  // namespace
+
+extern "C" int hqs_net_denoise(void* user, const hqs_c64* in, hqs_c64* out, int ny, int nx, float sigma,
+                               void* stream) {
+    hqs_net_s* net = reinterpret_cast<hqs_net_s*>(user);
+    if (!net || !in || !out || ny <= 0 || nx <= 0 || !(sigma >= 0.f)) return HQS_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int count = ny * nx;
+    const int nb = std::min(ceil_div(count, 256), 1024);
+    const float2* v = reinterpret_cast<const float2*>(in);
+    float2* o = reinterpret_cast<float2*>(out);
+    if (sigma == 0.f) {
+        if (v != o) k_copy_c64<<<nb, 256, 0, st>>>(v, o, count);
+        HQS_CUDA_TRY(cudaGetLastError());
+        return HQS_OK;
+    }
+    HQS_TRY_RC(ensure_net_buffers(net, std::max(ny, nx)));
+    float* x = net->planar;
+    float* noise = net->planar + 2 * (size_t)count;
+    k_denoise_split<<<nb, 256, 0, st>>>(v, count, 1.f / sigma, x);
+    HQS_TRY_RC(net_forward(net, x, noise, 1, ny, nx, st));
+    k_denoise_combine<<<nb, 256, 0, st>>>(v, noise, count, sigma, o);
+    HQS_CUDA_TRY(cudaGetLastError());
+    return HQS_OK;
+}

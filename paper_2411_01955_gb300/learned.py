@@ -168,3 +168,18 @@ def train_residual(net, examples, steps=300, batch=8, lr=5e-4, seed=0, log_every
 def heldout_residual(net, examples):
     """Mean ||r - H M r||^2 / ||r||^2 over examples (M: DC + network)."""
     return float(np.mean([residual_loss(net, e)[0] for e in examples]))
+
+
+# ---------------------------------------------------------------- conv denoiser
+def denoiser_examples(images, sigmas, seed=0):
+    """(input, target) pairs for D_sigma(v) = v - sigma net(v / sigma): v = x + sigma n
+    with complex Gaussian n (unit variance per part); input v / sigma, target n."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for x in images:
+        s = float(rng.choice(sigmas)) if np.ndim(sigmas) else float(sigmas)
+        noise = torch.complex(torch.from_numpy(rng.normal(size=x.shape).astype(np.float32)),
+                              torch.from_numpy(rng.normal(size=x.shape).astype(np.float32))).to(x.device)
+        v = x + s * noise
+        out.append((to_planar(v / s), to_planar(noise)))
+    return out
