@@ -535,6 +535,15 @@ def run_batch64(args, rank, world, dist):
     ms = timed(step, args.steps)
     clocks = clk.stop()
     value = whole_job_rate(len(sl) * args.steps, world, ms)
+    # per-step latency (every slice of a step finishes with the step's one launch)
+    lat = []
+    for _ in range(max(args.steps, 5)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        lat.append(e0.elapsed_time(e1))
 
     def per_slice():
         for i, p in enumerate(plans):
@@ -560,6 +569,7 @@ def run_batch64(args, rank, world, dist):
                    "spread_tiles_picked": {str(k): v for k, v in sorted(tuned.items())},
                    "l2": "inputs larger than L2 (64 distinct slices), no flush"},
         "batch_latency_ms": ms / args.steps,
+        "slice_latency_ms_p50_p95": [float(np.percentile(lat, 50)), float(np.percentile(lat, 95))],
         "per_slice_hqs_run_slices_per_s": len(sl) * world / (ms_seq / 1e3),
         "speedup_vs_per_slice": (ms_seq) / (ms / args.steps),
         "max_final_rel_residual_sq": float(max(res)),
