@@ -30,7 +30,7 @@ using namespace hqs;
 namespace {
 
 enum BatchSlot { BS_PQ = 0, BS_RR = 1, BS_BB = 2, BS_RZ = 3, BS_N = 4 };
-enum BatchList { BL_ROWS = 0, BL_COLS = 1, BL_PC = 2, BL_IMG = 3, BL_BLUR = 4, BL_EPI = 5, BL_N = 6 };
+enum BatchList { BL_ROWS = 0, BL_COLS = 1, BL_PC = 2, BL_IMG = 3, BL_BLUR = 4, BL_EPI = 5, BL_ZP = 6, BL_N = 7 };
 
 struct BatchSlice {
     ToepArgs A;
@@ -85,17 +85,27 @@ HQS_DEV void put_slice_partials(double* part, int ns, const double* acc) {
 }
 
 // ---- per-size item bodies (BD = HQS_BATCH_BD)
+// z rows per item in the p-update phase: as many n-point lines as the CTA holds
+template <int N> constexpr int batch_zq() {
+    return (HQS_BATCH_BD / FftSize<N>::TPL) < kLines ? HQS_BATCH_BD / FftSize<N>::TPL : kLines;
+}
+
+// rows [r0, r0 + lines): z = IFFT_N(pc spectrum rows) / N^2, p = z + beta p
 template <int N2, int N>
-HQS_DEV void z_and_p_row(const BatchSlice& S, int iy, float beta, bool first, float2* s, float2* zs,
-                         const float2* twN) {
-    const int n = N;
-    for (int pos = threadIdx.x; pos < N; pos += blockDim.x) s[pos * kLines] = __ldcg(S.pcb + (size_t)iy * N + pos);
+HQS_DEV void z_and_p_rows(const BatchSlice& S, int r0, float beta, bool first, float2* s, const float2* twN) {
+    constexpr int n = N;
+    const int lines = min(batch_zq<N>(), n - r0);
+    for (int e = threadIdx.x; e < lines * N; e += blockDim.x) {
+        const int q = e / N, pos = e - q * N;
+        s[pos * kLines + q] = __ldcg(S.pcb + (size_t)(r0 + q) * N + pos);
+    }
     __syncthreads();
-    block_fft<N, true>(s, 1, twN);
+    block_fft<N, true>(s, lines, twN);
     const float sc = 1.0f / ((float)N * (float)N);
-    for (int ix = threadIdx.x; ix < n; ix += blockDim.x) {
-        const size_t e = (size_t)iy * n + ix;
-        float2 v = cscale(s[ix * kLines], sc);
+    for (int e2 = threadIdx.x; e2 < lines * n; e2 += blockDim.x) {
+        const int q = e2 / n, ix = e2 - q * n;
+        const size_t e = (size_t)(r0 + q) * n + ix;
+        float2 v = cscale(s[ix * kLines + q], sc);
         if (!first && beta != 0.f) {
             const float2 pv = __ldcg(S.p + e);
             v.x = fmaf(beta, pv.x, v.x);
@@ -104,7 +114,6 @@ HQS_DEV void z_and_p_row(const BatchSlice& S, int iy, float beta, bool first, fl
         S.p[e] = v;
     }
     __syncthreads();
-    (void)zs;
 }
 
 template <int N>
@@ -346,9 +355,9 @@ __global__ void __launch_bounds__(HQS_BATCH_BD, 2) k_hqs_batch(BatchArgs B) {
         __syncthreads();
         for (int cg = 0; cg < B.cg_iters; ++cg) {
             // A0: z rows and p = z + beta p
-            FOR_ITEMS(BL_IMG, {
+            FOR_ITEMS(BL_ZP, {
                 STAGE_TWN(S, si);
-                HQS_BATCH_DISPATCH(S.A.n, (z_and_p_row<N2, N>(S, it_, (float)betas[si], cg == 0, s, nullptr, twN)));
+                HQS_BATCH_DISPATCH(S.A.n, (z_and_p_rows<N2, N>(S, it_ * batch_zq<N>(), (float)betas[si], cg == 0, s, twN)));
             });
             BB_BARRIER();
             FOR_ITEMS(BL_ROWS, {
@@ -588,9 +597,9 @@ __global__ void __launch_bounds__(HQS_BATCH_BD, 2) k_pcg_batch(DcBatchArgs B) {
     COUNT_ACTIVE();
     for (int cg = 0; cg < B.max_iter && nact > 0; ++cg) {
         // p = z + beta p
-        FOR_ITEMS(BL_IMG, {
+        FOR_ITEMS(BL_ZP, {
             STAGE_TWN(S, si);
-            HQS_BATCH_DISPATCH(S.A.n, (z_and_p_row<N2, N>(S, it_, (float)betas[si], cg == 0, s, nullptr, twN)));
+            HQS_BATCH_DISPATCH(S.A.n, (z_and_p_rows<N2, N>(S, it_ * batch_zq<N>(), (float)betas[si], cg == 0, s, twN)));
         });
         BB_BARRIER();
         // q = a A^H A p + b p, <p, q>
@@ -820,8 +829,9 @@ extern "C" int hqs_batch_create(hqs_batch* out, hqs_plan* plans, int n, int max_
         S.p = p->cg_p;
         S.q = p->cg_q;
         S.pcb = p->pc_buf;
+        const int zq = dispatch_fft_size(p->n, [&]<int NN>() { return batch_zq<NN>(); });
         const int cnt[BL_N] = {p->n * nch, 2 * p->n * nch, ceil_div(p->n, HQS_BATCH_Q), p->n,
-                               ceil_div(p->n, 32) * ceil_div(p->n, 32), nch > 1 ? p->n : 0};
+                               ceil_div(p->n, 32) * ceil_div(p->n, 32), nch > 1 ? p->n : 0, ceil_div(p->n, zq)};
         for (int l = 0; l < BL_N; ++l) off[(size_t)l * (n + 1) + i + 1] = off[(size_t)l * (n + 1) + i] + cnt[l];
     }
     const size_t sm = kBatchSmemF2 * sizeof(float2);
