@@ -16,6 +16,7 @@ kb        Kaiser-Bessel kernel, its own I0 power series and closed-form transfor
 nudft     exact non-uniform DFT forward/adjoint (the definition of A in Eq. (1)).
 nufft     gridding NUFFT with the same kernel parameters as the GPU path.
 toeplitz  Toeplitz embedding of A^H A and the Strang circulant preconditioner.
+nufft3d   volumetric operator: exact 3D NUDFT, 3D gridding, 2N^3 Toeplitz embedding.
 solvers   PCG, flexible CG, CG energy, power iteration.
 smaps     S-map estimation from the windowed k-space centre (Sec. 4.1).
 hqs       PnP-HQS / PnP-PGD loops (Sec. 3.3), Gaussian-smoothing denoiser,
@@ -23,6 +24,7 @@ hqs       PnP-HQS / PnP-PGD loops (Sec. 3.3), Gaussian-smoothing denoiser,
 convnet   small 2-channel conv net: forward, backward, Adam.
 
 Parity status: every function has an independent pin in tests/test_oracle_pins.py
+(tests/test_oracle_pins_3d.py for nufft3d)
 except the annealed HQS run with a non-proximal denoiser, which has no closed
 form: there only iterate-level agreement is checked ("parity unpinned" beyond that).
 """

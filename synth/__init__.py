@@ -28,7 +28,7 @@ __all__ = [
     "phantom", "coil_maps", "traj_radial", "traj_spiral", "dcf_voronoi",
     "complex_noise", "noise_scale_snr", "noise_scale_image_rule",
     "mu_schedule_geometric", "paper_schedule", "tiny_case", "brain_case",
-    "odd_case",
+    "odd_case", "phantom3d", "coil_maps3d", "traj_stack_of_spirals", "volume_case",
 ]
 
 
@@ -227,3 +227,83 @@ def odd_case(seed: int = 0, n: int = 16, L: int = 3, M: int = 37, W: int = 4):
     return dict(n=n, L=L, W=W, sigma=2.0, x=phantom(seed, n),
                 smaps=coil_maps(seed, n, L), traj=k.astype(np.float32),
                 noise=complex_noise(seed, (L, M)))
+
+
+# ------------------------------------------------------------------ volumes
+def phantom3d(seed: int, shape) -> np.ndarray:
+    """Random-ellipsoid phantom with a smooth random phase, complex128 (nz, ny, nx).
+
+    An outer ellipsoid (semi-axes 0.9, 0.8, 0.85 of the half field of view in
+    x, y, z) holds 8-12 random axis-aligned ellipsoids: centres U(-0.5, 0.5),
+    semi-axes U(0.08, 0.4), amplitude U(0.1, 1); the phase is exp(i*pi*p) with p
+    a random linear-plus-quadratic polynomial scaled to max|p| <= 1.
+    """
+    nz, ny, nx = shape
+    rng = np.random.default_rng(seed + 104729)
+    Z, Y, X = np.meshgrid(_grid_coords(nz), _grid_coords(ny), _grid_coords(nx), indexing="ij")
+    head = (X / 0.9) ** 2 + (Y / 0.8) ** 2 + (Z / 0.85) ** 2 <= 1.0
+    mag = 0.25 * head.astype(np.float64)
+    for _ in range(int(rng.integers(8, 13))):
+        c = rng.uniform(-0.5, 0.5, size=3)
+        a = rng.uniform(0.08, 0.4, size=3)
+        amp = rng.uniform(0.1, 1.0)
+        mag += amp * ((((X - c[0]) / a[0]) ** 2 + ((Y - c[1]) / a[1]) ** 2
+                       + ((Z - c[2]) / a[2]) ** 2) <= 1.0)
+    mag *= head
+    coef = rng.normal(size=7)
+    p = (coef[0] + coef[1] * X + coef[2] * Y + coef[3] * Z + coef[4] * X * X
+         + coef[5] * Y * Y + coef[6] * Z * Z)
+    p /= max(np.abs(p).max(), 1e-12)
+    return mag * np.exp(1j * math.pi * p)
+
+
+def coil_maps3d(seed: int, shape, L: int) -> np.ndarray:
+    """Smooth coil sensitivities, complex128 (L, nz, ny, nx), RSS = 1 per voxel.
+
+    Coil l is a Gaussian bump (std 0.9 half-FOV units) centred on a ring of
+    radius 1.4 at angle 2*pi*l/L, alternately raised to z = +-0.5, with phase
+    2*pi*l/L plus a small random linear ramp.
+    """
+    nz, ny, nx = shape
+    rng = np.random.default_rng(seed + 15485863)
+    Z, Y, X = np.meshgrid(_grid_coords(nz), _grid_coords(ny), _grid_coords(nx), indexing="ij")
+    maps = np.empty((L,) + tuple(shape), dtype=np.complex128)
+    for l in range(L):
+        ang = 2 * math.pi * l / L + rng.uniform(-0.2, 0.2)
+        cx, cy, cz = 1.4 * math.cos(ang), 1.4 * math.sin(ang), 0.5 * (-1) ** l
+        amp = np.exp(-((X - cx) ** 2 + (Y - cy) ** 2 + (Z - cz) ** 2) / (2 * 0.9 ** 2))
+        r = rng.uniform(-0.5, 0.5, size=3)
+        maps[l] = amp * np.exp(1j * (2 * math.pi * l / L + r[0] * X + r[1] * Y + r[2] * Z))
+    rss = np.sqrt((np.abs(maps) ** 2).sum(axis=0))
+    return maps / rss[None]
+
+
+def traj_stack_of_spirals(n_planes: int, n_interleaves: int, n_samples: int, n: int,
+                          accel: float = 8.0) -> np.ndarray:
+    """Stack of variable-density spirals, float32 (n_planes*n_interleaves*n_samples, 3).
+
+    Plane p sits at kz = 2*pi*(p - n_planes/2)/n_planes (Cartesian along z,
+    Nyquist-spaced when n_planes equals the slice count) and holds the
+    traj_spiral pattern for an n-wide field of view, rotated by p times the
+    golden angle so that neighbouring planes interleave.  Columns (kx, ky, kz).
+    """
+    base = traj_spiral(n_interleaves, n_samples, n, accel).astype(np.float64)
+    kxy = base[:, 0] + 1j * base[:, 1]
+    golden = math.pi * (3.0 - math.sqrt(5.0))
+    out = []
+    for p in range(n_planes):
+        r = kxy * np.exp(1j * golden * p)
+        kz = 2 * math.pi * (p - n_planes / 2) / n_planes
+        out.append(np.stack([_wrap_pi(r.real), _wrap_pi(r.imag), np.full(r.shape, kz)], axis=1))
+    return np.concatenate(out).astype(np.float32)
+
+
+def volume_case(seed: int = 0, shape=(64, 64, 64), L: int = 16, n_interleaves: int = 8,
+                n_samples: int = 1024, W: int = 6):
+    """Volume of shape (nz, ny, nx), L coils, stack of nz spirals of
+    n_interleaves x n_samples each (8-fold undersampled in-plane), KB width W,
+    oversampling 2."""
+    nz, ny, nx = shape
+    traj = traj_stack_of_spirals(nz, n_interleaves, n_samples, max(ny, nx))
+    return dict(shape=tuple(shape), L=L, W=W, sigma=2.0, x=phantom3d(seed, shape),
+                smaps=coil_maps3d(seed, shape, L), traj=traj)

@@ -1,0 +1,147 @@
+"""Pins of the volumetric (3D) oracle against facts that do not come from it:
+brute-force loops on tiny volumes, the 2D operator (pinned on its own) as the
+one-slice special case, the library FFT on Cartesian samples, adjointness, and
+the Kaiser-Bessel error decreasing with the kernel width.  Shapes are
+anisotropic throughout so that a transposed axis fails.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import nudft, nufft3d, toeplitz
+import synth
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a - b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
+
+
+def rand_c(rng, shape):
+    return rng.normal(size=shape) + 1j * rng.normal(size=shape)
+
+
+def rand_traj(rng, M):
+    return rng.uniform(-math.pi, math.pi, size=(M, 3)).astype(np.float32)
+
+
+def test_nudft3d_matches_brute_force_loop():
+    rng = np.random.default_rng(11)
+    nz, ny, nx, L, M = 3, 4, 5, 2, 7
+    x = rand_c(rng, (nz, ny, nx))
+    S = rand_c(rng, (L, nz, ny, nx))
+    traj = rand_traj(rng, M)
+    k = traj.astype(np.float64)
+    ref = np.zeros((L, M), dtype=np.complex128)
+    for l in range(L):
+        for j in range(M):
+            acc = 0j
+            for iz in range(nz):
+                for iy in range(ny):
+                    for ix in range(nx):
+                        ph = (k[j, 0] * (ix - nx // 2) + k[j, 1] * (iy - ny // 2)
+                              + k[j, 2] * (iz - nz // 2))
+                        acc += S[l, iz, iy, ix] * x[iz, iy, ix] * complex(math.cos(ph), -math.sin(ph))
+            ref[l, j] = acc / math.sqrt(nz * ny * nx)
+    assert rel(nufft3d.nudft_forward(x, S, traj), ref) < 1e-14
+    yy = rand_c(rng, (L, M))
+    ref_a = np.zeros((nz, ny, nx), dtype=np.complex128)
+    for l in range(L):
+        for iz in range(nz):
+            for iy in range(ny):
+                for ix in range(nx):
+                    ph = k[:, 0] * (ix - nx // 2) + k[:, 1] * (iy - ny // 2) + k[:, 2] * (iz - nz // 2)
+                    ref_a[iz, iy, ix] += np.conj(S[l, iz, iy, ix]) * np.sum(yy[l] * np.exp(1j * ph))
+    assert rel(nufft3d.nudft_adjoint(yy, S, traj), ref_a / math.sqrt(nz * ny * nx)) < 1e-14
+
+
+def test_nudft3d_one_slice_is_the_2d_operator():
+    rng = np.random.default_rng(12)
+    ny, nx, L, M = 6, 10, 3, 40
+    x = rand_c(rng, (ny, nx))
+    S = rand_c(rng, (L, ny, nx))
+    traj = rand_traj(rng, M)                      # any kz: the one slice sits at n_z = 0
+    y3 = nufft3d.nudft_forward(x[None], S[:, None], traj)
+    assert rel(y3, nudft.forward(x, S, traj[:, :2])) < 1e-14
+    yy = rand_c(rng, (L, M))
+    assert rel(nufft3d.nudft_adjoint(yy, S[:, None], traj)[0], nudft.adjoint(yy, S, traj[:, :2])) < 1e-14
+
+
+def test_nudft3d_cartesian_equals_library_fft():
+    nz, ny, nx = 4, 6, 8
+    rng = np.random.default_rng(13)
+    x = rand_c(rng, (nz, ny, nx))
+    mz, my, mx = (np.arange(n) - n // 2 for n in (nz, ny, nx))
+    MZ, MY, MX = np.meshgrid(mz, my, mx, indexing="ij")
+    traj = np.stack([2 * math.pi * MX.ravel() / nx, 2 * math.pi * MY.ravel() / ny,
+                     2 * math.pi * MZ.ravel() / nz], 1)
+    y = nufft3d.nudft_forward(x, np.ones((1, nz, ny, nx)), traj).reshape(nz, ny, nx)
+    X = np.fft.fftn(np.fft.ifftshift(x), norm="ortho")
+    assert rel(y, X[np.mod(MZ, nz), np.mod(MY, ny), np.mod(MX, nx)]) < 1e-13
+
+
+@pytest.mark.parametrize("op", ["nudft", "nufft4", "nufft6"])
+def test_adjointness_3d(op):
+    rng = np.random.default_rng(14)
+    shape, L, M = (8, 12, 10), 2, 300
+    x = rand_c(rng, shape)
+    y = rand_c(rng, (L, M))
+    S = rand_c(rng, (L,) + shape)
+    traj = rand_traj(rng, M)
+    if op == "nudft":
+        Ax, Ahy = nufft3d.nudft_forward(x, S, traj), nufft3d.nudft_adjoint(y, S, traj)
+    else:
+        W = int(op[-1])
+        Ax, Ahy = nufft3d.forward(x, S, traj, W, 2.0), nufft3d.adjoint(y, S, traj, W, 2.0)
+    lhs, rhs = np.vdot(y, Ax), np.vdot(Ahy, x)
+    assert abs(lhs - rhs) / abs(lhs) < 1e-12
+
+
+def test_nufft3d_vs_nudft_error_bound_and_monotone_in_width():
+    c = synth.volume_case(0, (8, 16, 12), 3, 4, 128)
+    x, S, traj = c["x"], c["smaps"], c["traj"]
+    ex = nufft3d.nudft_forward(x, S, traj)
+    errs = {W: rel(nufft3d.forward(x, S, traj, W, 2.0), ex) for W in (4, 6, 8)}
+    # one-dimensional KB aliasing error at W = 4, sigma = 2 is ~2e-4 per axis
+    assert errs[4] <= 2e-3
+    assert errs[6] < errs[4] / 10 and errs[8] < errs[6]
+    y = synth.complex_noise(1, ex.shape)
+    ea = {W: rel(nufft3d.adjoint(y, S, traj, W, 2.0), nufft3d.nudft_adjoint(y, S, traj)) for W in (4, 6)}
+    assert ea[4] <= 2e-3 and ea[6] < ea[4] / 10
+
+
+def test_toeplitz3d_equals_dense_normal_operator():
+    rng = np.random.default_rng(15)
+    shape, L, M = (4, 6, 5), 2, 80
+    x = rand_c(rng, shape)
+    S = rand_c(rng, (L,) + shape)
+    traj = rand_traj(rng, M)
+    c = nufft3d.kernel(traj, shape)
+    Kh = nufft3d.khat(c)
+    assert np.max(np.abs(np.fft.fftn(c).imag)) < 1e-12 * np.max(np.abs(Kh))
+    assert rel(nufft3d.normal(x, S, Kh), nufft3d.nudft_normal(x, S, traj)) < 1e-12
+
+
+def test_toeplitz3d_kernel_brute_force_entries():
+    rng = np.random.default_rng(16)
+    shape, M = (3, 4, 5), 9
+    traj = rand_traj(rng, M)
+    c = nufft3d.kernel(traj, shape)
+    k = traj.astype(np.float64)
+    nz, ny, nx = shape
+    for p in [(0, 0, 0), (1, 2, 3), (5, 7, 9), (4, 1, 6), (nz, 2, 2), (1, ny, 2), (2, 1, nx)]:
+        d = [q if q < n else q - 2 * n for q, n in zip(p, shape)]
+        zero = any(q == n for q, n in zip(p, shape))
+        want = 0.0 if zero else np.sum(np.exp(1j * (k[:, 0] * d[2] + k[:, 1] * d[1] + k[:, 2] * d[0]))) / (nz * ny * nx)
+        assert abs(c[p] - want) < 1e-14
+
+
+def test_toeplitz3d_one_slice_is_the_2d_embedding():
+    rng = np.random.default_rng(17)
+    ny, nx, L, M = 6, 8, 2, 50
+    x = rand_c(rng, (ny, nx))
+    S = rand_c(rng, (L, ny, nx))
+    traj = rand_traj(rng, M)
+    K3 = nufft3d.khat(nufft3d.kernel(traj, (1, ny, nx)))
+    K2 = toeplitz.khat(toeplitz.kernel(traj[:, :2], ny, nx))
+    assert rel(nufft3d.normal(x[None], S[:, None], K3)[0], toeplitz.normal(x, S, K2)) < 1e-13
