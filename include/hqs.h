@@ -8,7 +8,8 @@
  * ---------------------------------------
  * - Complex arrays are interleaved float32 pairs (re, im) = hqs_c64.
  * - Images are (ny, nx) row-major; pixel (iy, ix) has the centred coordinate
- *   n = (ix - nx/2, iy - ny/2).  Only square images (ny == nx) are accepted.
+ *   n = (ix - nx/2, iy - ny/2).  Only square images (ny == nx) are accepted
+ *   (the volumetric entry points below take (nz, ny, nx) volumes).
  * - Coil maps at the boundary are (L, ny, nx); k-space data are (L, M) in the
  *   caller's point order; trajectories are (M, 2) float32 (kx, ky) in radians
  *   per pixel (any real value; the grid is periodic in 2*pi).
@@ -70,6 +71,7 @@ extern "C" {
 typedef struct hqs_plan_s* hqs_plan;
 typedef struct hqs_net_s* hqs_net;
 typedef struct hqs_batch_s* hqs_batch;
+typedef struct hqs_plan3d_s* hqs_plan3d;
 typedef struct { float re, im; } hqs_c64;
 
 typedef struct {
@@ -382,6 +384,50 @@ HQS_API int hqs_plan_retile(hqs_plan plan, int tile, void* stream);
  * and coils <= 32. */
 HQS_API int hqs_debug_toeplitz_stage(hqs_plan plan, const hqs_c64* x, int precision, int stage,
                                      hqs_c64* out, void* stream);
+
+/* ------------------------------------------------ volumetric operator (3D) */
+/* Eq. (1) on volumes, the extension Sec. 5 names as future work: voxel
+ * (iz, iy, ix) of an (nz, ny, nx) row-major volume has the centred coordinate
+ * n = (ix - nx/2, iy - ny/2, iz - nz/2); trajectories are (M, 3) float32
+ * (kx, ky, kz) in radians per voxel (any real value, periodic in 2*pi); coil
+ * maps are (L, nz, ny, nx); k-space data (L, M) in the caller's point order.
+ *
+ * hqs_plan3d_create copies the maps, sorts the points into 8^3 spreading bins
+ * and builds the Toeplitz kernel of A^H A on the 2N^3 grid (blocking: it
+ * synchronises `stream`).  Each of nz, ny, nx must be one of
+ * {8, 16, 32, 64, 128, 160, 192}; coils 1..64; kernel_width 4..8; oversamp
+ * must be 2 (the NUFFT grid is then also the 2N Toeplitz grid).  Invalid
+ * arguments return HQS_ERR_INVALID_ARG with *out = NULL.  The plan holds
+ * about (13 L + 8) * 8 * nz*ny*nx bytes of device memory. */
+HQS_API int hqs_plan3d_create(hqs_plan3d* out, const float* traj, int64_t M, int nz, int ny, int nx,
+                              int coils, const hqs_c64* smaps, int kernel_width, float oversamp,
+                              void* stream);
+HQS_API void hqs_plan3d_destroy(hqs_plan3d plan);
+/* Host outputs (NULL skipped): point count, spreading sub-problems, device bytes held. */
+HQS_API int hqs_plan3d_get_info(hqs_plan3d plan, int64_t* npoints, int* nsub, size_t* device_bytes);
+
+/* y = A x by 3D gridding: apodise, zero-pad to the 2N grid, 3D FFT, W^3
+ * Kaiser-Bessel interpolation.  x: (nz, ny, nx); y: (L, M). */
+HQS_API int hqs_forward3d(hqs_plan3d plan, const hqs_c64* x, hqs_c64* y, void* stream);
+/* x = A^H y, the exact transpose of hqs_forward3d (tiled spreading, inverse
+ * 3D FFT, crop, deapodisation, conj(S_l) coil sum). */
+HQS_API int hqs_adjoint3d(hqs_plan3d plan, const hqs_c64* y, hqs_c64* x, void* stream);
+/* out = A^H A x by the 2N^3 circulant embedding (the normal operator of
+ * Sec. 3.4 in 3D): out = sum_l conj(S_l) crop(IFFT(Khat * FFT(pad(S_l x)))).
+ * The kernel t(d) = Nvox^-1 sum_j exp(+i k_j . d) is gridded with an
+ * 8-wide Kaiser-Bessel kernel on a 4N grid (relative error ~1e-7).
+ * x and out: (nz, ny, nx), distinct buffers. */
+HQS_API int hqs_toeplitz_normal3d(hqs_plan3d plan, const hqs_c64* x, hqs_c64* out, void* stream);
+/* Khat (2nz, 2ny, 2nx) float32 = Re FFT_2N(t) / (8 nz ny nx), copied to out (device). */
+HQS_API int hqs_plan3d_get_khat(hqs_plan3d plan, float* out, void* stream);
+/* Data-consistency solve of the HQS step on a volume: CG on
+ * (a A^H A + b I) x = rhs, starting from x on entry, fp64 inner products,
+ * stopping at ||r|| <= rel_tol ||rhs|| or after max_iter (<= HQS_MAX_ITERS)
+ * iterations; the host checks the residual each iteration (blocking).
+ * Returns HQS_OK, HQS_ERR_NOT_CONVERGED or HQS_ERR_BREAKDOWN; info (host,
+ * optional) as for hqs_dc_solve.  rhs and x distinct (nz, ny, nx). */
+HQS_API int hqs_dc_solve3d(hqs_plan3d plan, float a, float b, const hqs_c64* rhs, hqs_c64* x,
+                           int max_iter, double rel_tol, hqs_solve_info* info, void* stream);
 
 /* Diagnostics (no counterpart in the paper): phase trace of the persistent
  * solve.  enable = 1 allocates a trace buffer on the plan (returns 0); later

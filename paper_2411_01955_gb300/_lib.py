@@ -124,6 +124,17 @@ _SIGS = {
                                             C.c_void_p, C.c_void_p]),
     "hqs_debug_phase_trace": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_ulonglong), C.c_int,
                                         C.c_void_p]),
+    "hqs_plan3d_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_int,
+                                    C.c_int, C.c_void_p, C.c_int, C.c_float, C.c_void_p]),
+    "hqs_plan3d_destroy": (None, [C.c_void_p]),
+    "hqs_plan3d_get_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int),
+                                      C.POINTER(C.c_size_t)]),
+    "hqs_plan3d_get_khat": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "hqs_forward3d": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "hqs_adjoint3d": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "hqs_toeplitz_normal3d": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "hqs_dc_solve3d": (C.c_int, [C.c_void_p, C.c_float, C.c_float, C.c_void_p, C.c_void_p, C.c_int,
+                                 C.c_double, C.POINTER(SolveInfo), C.c_void_p]),
 }
 
 
@@ -573,3 +584,79 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------------ volumes
+class Plan3d:
+    """Owns an hqs_plan3d (hqs_plan3d_create / hqs_plan3d_destroy)."""
+
+    def __init__(self, handle, shape, coils, npoints):
+        self.handle = handle
+        self.shape, self.coils, self.npoints = tuple(shape), coils, npoints
+
+    def info(self):
+        M, nsub, nbytes = C.c_int64(), C.c_int(), C.c_size_t()
+        _check(library().hqs_plan3d_get_info(self.handle, C.byref(M), C.byref(nsub), C.byref(nbytes)),
+               "hqs_plan3d_get_info")
+        return {"npoints": M.value, "nsub": nsub.value, "device_bytes": nbytes.value}
+
+    def close(self):
+        if self.handle:
+            library().hqs_plan3d_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def plan3d_create(traj, shape, smaps, kernel_width=6, oversamp=2.0, stream=None) -> Plan3d:
+    """traj (M, 3) float32 CUDA; shape (nz, ny, nx); smaps (L, nz, ny, nx) complex64 CUDA."""
+    nz, ny, nx = (int(v) for v in shape)
+    h = C.c_void_p()
+    M = int(traj.shape[0])
+    rc = library().hqs_plan3d_create(C.byref(h), _ptr(traj, torch.float32, "traj"), M, nz, ny, nx,
+                                     int(smaps.shape[0]), _ptr(smaps, torch.complex64, "smaps"),
+                                     int(kernel_width), float(oversamp), _stream(stream))
+    _check(rc, "hqs_plan3d_create")
+    return Plan3d(h, (nz, ny, nx), int(smaps.shape[0]), M)
+
+
+def forward3d(plan: Plan3d, x, y, stream=None):
+    _check(library().hqs_forward3d(plan.handle, _ptr(x, torch.complex64, "x"), _ptr(y, torch.complex64, "y"),
+                                   _stream(stream)), "hqs_forward3d")
+    return y
+
+
+def adjoint3d(plan: Plan3d, y, x, stream=None):
+    _check(library().hqs_adjoint3d(plan.handle, _ptr(y, torch.complex64, "y"), _ptr(x, torch.complex64, "x"),
+                                   _stream(stream)), "hqs_adjoint3d")
+    return x
+
+
+def toeplitz_normal3d(plan: Plan3d, x, out, stream=None):
+    _check(library().hqs_toeplitz_normal3d(plan.handle, _ptr(x, torch.complex64, "x"),
+                                           _ptr(out, torch.complex64, "out"), _stream(stream)),
+           "hqs_toeplitz_normal3d")
+    return out
+
+
+def plan3d_khat(plan: Plan3d, out, stream=None):
+    """Khat (2nz, 2ny, 2nx) float32, scaled by 1 / (8 nz ny nx)."""
+    _check(library().hqs_plan3d_get_khat(plan.handle, _ptr(out, torch.float32, "out"), _stream(stream)),
+           "hqs_plan3d_get_khat")
+    return out
+
+
+def dc_solve3d(plan: Plan3d, a, b, rhs, x, max_iter=30, rel_tol=1e-4, stream=None, check=True) -> SolveInfo:
+    """Solves (a A^H A + b I) x = rhs in place (CG, blocking); returns SolveInfo."""
+    info = SolveInfo()
+    rc = library().hqs_dc_solve3d(plan.handle, float(a), float(b), _ptr(rhs, torch.complex64, "rhs"),
+                                  _ptr(x, torch.complex64, "x"), int(max_iter), float(rel_tol), C.byref(info),
+                                  _stream(stream))
+    if check and rc not in (HQS_OK, HQS_ERR_NOT_CONVERGED):
+        raise HqsError(rc, "hqs_dc_solve3d")
+    info.rc = rc
+    return info

@@ -1,0 +1,1124 @@
+// Volumetric (3D) multicoil operator of Eq. (1): the paper's conclusion
+// (Sec. 5) names 3D data as the next target, and the operator changes only
+// by one more axis.
+//
+//   forward : apodise + coil-multiply fused into the x-axis FFT of the
+//             centred, sigma-oversampled grid, then the y and z FFTs, then
+//             W^3-tap Kaiser-Bessel interpolation (gather, one half-warp per
+//             point, lanes over coils);
+//   adjoint : shared-memory tiled spreading (TB^3 bins), z / y / x inverse
+//             FFTs with crop, conj(S_l) per coil, coil sum + deapodisation;
+//   A^H A   : the 2N^3 circulant embedding (Sec. 3.4 form of the normal
+//             operator): pad(S_l x) -> FFT_x, FFT_y, FFT_z * Khat * IFFT_z,
+//             IFFT_y, IFFT_x -> crop, conj(S_l) sum.  Zero-padded inputs use
+//             the pruned first stage, cropped outputs the pruned last stage.
+//   kernel  : t(d) = Nvox^-1 sum_j exp(+i k_j . d) on d in [-N, N)^3 by the
+//             adjoint gridding of unit data onto a 4N grid with an 8-wide
+//             kernel (an M-independent cost; the exact sum costs M (2N)^3),
+//             then Khat = Re FFT_2N(t) / (2N)^3.
+//   DC solve: CG on (a A^H A + b I) x = rhs with fp64 inner products.
+//
+// Grids and per-coil volumes are coil-innermost ([z][y][x][l]); every FFT
+// pass is one kernel over lines (a, p, b) at base + a*sA + p*sP + b with b
+// the contiguous index, 16 lines per CTA, so loads and stores are coalesced
+// over b.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "fft.cuh"
+#include "plan.cuh"
+
+using namespace hqs;
+
+#define HQS3_TILE 8           // spreading bin edge on the grid
+#define HQS3_MAXPTS 256       // points per spreading sub-problem
+#define HQS3_KERNEL_W 8       // KB width used to grid the Toeplitz kernel
+#define HQS3_PATCH_BYTES (96 * 1024)
+
+struct Cg3 {
+    double rr, pq, alpha, beta, bnorm2, tol2;
+    int it, done, status, max_iter;
+};
+
+struct hqs_plan3d_s {
+    int device = 0;
+    int n[3] = {0, 0, 0};     // nx, ny, nz
+    int G[3] = {0, 0, 0};     // oversampled NUFFT grid (= 2n: also the Toeplitz grid)
+    int L = 0, W = 0;
+    double beta = 0.0;
+    int64_t M = 0;
+    float scale = 1.f;        // Nvox^-1/2
+    int nb[3] = {0, 0, 0};
+    int nsub = 0;
+    float2* smaps = nullptr;  // [nz][ny][nx][L]
+    float* apod[3] = {nullptr, nullptr, nullptr};
+    int4* pti = nullptr;      // sorted points: (i0x, i0y, i0z, caller index)
+    float4* ptd = nullptr;    // (dx, dy, dz, 0)
+    int4* subs = nullptr;     // (bin, start, count, 0)
+    float* khat = nullptr;    // [2nz][2ny][2nx], includes 1 / (8 Nvox)
+    float2* tw = nullptr;     // twiddle bank
+    int tw_sizes[6] = {0, 0, 0, 0, 0, 0};
+    int tw_offs[6] = {0, 0, 0, 0, 0, 0};
+    float2* bufA = nullptr;   // 8 Nvox L
+    float2* bufB = nullptr;   // 4 Nvox L
+    float2* bufC = nullptr;   // Nvox L
+    float2* cg_r = nullptr;
+    float2* cg_p = nullptr;
+    float2* cg_q = nullptr;
+    double* partials = nullptr;
+    Cg3* cg = nullptr;
+    Cg3* h_cg = nullptr;
+    double* hist = nullptr;
+    size_t bytes = 0;
+    std::vector<void*> allocs;
+};
+
+namespace {
+
+// ---------------------------------------------------------------- helpers
+HQS_DEV float kb_phi3(float t, float W, float beta) {
+    const float z = 2.0f * t / W;
+    const float s = 1.0f - z * z;
+    return s >= 0.f ? cyl_bessel_i0f(beta * sqrtf(s)) : 0.f;
+}
+HQS_DEV int wrap(int i, int G) { return i < 0 ? i + G : (i >= G ? i - G : i); }
+// grid position of centred image index i (image size n on grid G)
+HQS_DEV int centred_pos(int i, int n, int G) {
+    const int c = i - (n >> 1);
+    return c >= 0 ? c : c + G;
+}
+// grid position of circulant index p in [0, 2h) (offset d = p or p - 2h) on grid G
+HQS_DEV int circ_pos(int p, int h, int G) { return p < h ? p : p - 2 * h + G; }
+
+// ------------------------------------------------------------ point setup
+__global__ void k_points3(const float* __restrict__ traj, int M, int Gx, int Gy, int Gz, int W, int TB,
+                          int nbx, int nby, int4* __restrict__ rawi, float4* __restrict__ rawd,
+                          int* __restrict__ bin, int* __restrict__ counts) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= M) return;
+    const int Gs[3] = {Gx, Gy, Gz};
+    int i0v[3], cb[3];
+    float dv[3];
+    for (int ax = 0; ax < 3; ++ax) {
+        const double G = (double)Gs[ax];
+        double u = ((double)traj[3 * (int64_t)j + ax] * G) / (2.0 * 3.141592653589793);
+        u -= G * floor(u / G);
+        const double i0 = ceil(u - 0.5 * (double)W);
+        dv[ax] = (float)(u - i0);
+        int ii = (int)i0;
+        if (ii < 0) ii += Gs[ax];
+        if (ii >= Gs[ax]) ii -= Gs[ax];
+        i0v[ax] = ii;
+        int c = ii + W / 2;
+        if (c >= Gs[ax]) c -= Gs[ax];
+        cb[ax] = c / TB;
+    }
+    rawi[j] = make_int4(i0v[0], i0v[1], i0v[2], j);
+    rawd[j] = make_float4(dv[0], dv[1], dv[2], 0.f);
+    const int b = (cb[2] * nby + cb[1]) * nbx + cb[0];
+    bin[j] = b;
+    atomicAdd(&counts[b], 1);
+}
+
+__global__ void k_points3_scatter(const int4* __restrict__ rawi, const float4* __restrict__ rawd,
+                                  const int* __restrict__ bin, int M, int* __restrict__ cursor,
+                                  int4* __restrict__ pti, float4* __restrict__ ptd) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= M) return;
+    const int pos = atomicAdd(&cursor[bin[j]], 1);
+    pti[pos] = rawi[j];
+    ptd[pos] = rawd[j];
+}
+
+__global__ void k_smaps3_coil_inner(const float2* __restrict__ in, float2* __restrict__ out, int64_t nvox,
+                                    int L) {
+    const int64_t total = nvox * L;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = e / L;
+        const int l = (int)(e - v * L);
+        out[e] = in[(int64_t)l * nvox + v];
+    }
+}
+
+// ------------------------------------------------------ interpolation
+// Type-2 interpolation: a half-warp per point, lane = coil (looping beyond
+// 16 coils).  The 3W separable weights are computed once per point by the
+// lanes (index q on lane q and q - 16) and broadcast with shuffles.
+template <int W>
+__global__ void __launch_bounds__(256) k_interp3(const float2* __restrict__ Gh, const int4* __restrict__ pti,
+                                                 const float4* __restrict__ ptd, int M, int Gx, int Gy,
+                                                 int Gz, int L, float beta, float2* __restrict__ y) {
+    const int64_t j = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 4;
+    const int h = threadIdx.x & 15;
+    const int base = threadIdx.x & 16;
+    const bool valid = j < M;
+    const int4 pi = valid ? pti[j] : make_int4(0, 0, 0, 0);
+    const float4 pd = valid ? ptd[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float w0 = 0.f, w1 = 0.f;
+    if (valid) {
+        const float dd[3] = {pd.x, pd.y, pd.z};
+        if (h < 3 * W) w0 = kb_phi3(dd[h / W] - (float)(h % W), (float)W, beta);
+        const int q = h + 16;
+        if (q < 3 * W) w1 = kb_phi3(dd[q / W] - (float)(q % W), (float)W, beta);
+    }
+    float wx[W], wy[W], wz[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        const int qx = w, qy = W + w, qz = 2 * W + w;
+        wx[w] = qx < 16 ? __shfl_sync(0xffffffffu, w0, base + qx) : __shfl_sync(0xffffffffu, w1, base + qx - 16);
+        wy[w] = qy < 16 ? __shfl_sync(0xffffffffu, w0, base + qy) : __shfl_sync(0xffffffffu, w1, base + qy - 16);
+        wz[w] = qz < 16 ? __shfl_sync(0xffffffffu, w0, base + qz) : __shfl_sync(0xffffffffu, w1, base + qz - 16);
+    }
+    if (!valid) return;
+    int gx[W];
+#pragma unroll
+    for (int b = 0; b < W; ++b) gx[b] = wrap(pi.x + b, Gx);
+    for (int l = h; l < L; l += 16) {
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll 1
+        for (int c = 0; c < W; ++c) {
+            const int gz = wrap(pi.z + c, Gz);
+            float2 az = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int a = 0; a < W; ++a) {
+                const int gy = wrap(pi.y + a, Gy);
+                const float2* row = Gh + ((int64_t)gz * Gy + gy) * Gx * L + l;
+                float2 ra = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int b = 0; b < W; ++b) {
+                    const float2 g = __ldg(row + (int64_t)gx[b] * L);
+                    ra.x = fmaf(wx[b], g.x, ra.x);
+                    ra.y = fmaf(wx[b], g.y, ra.y);
+                }
+                az.x = fmaf(wy[a], ra.x, az.x);
+                az.y = fmaf(wy[a], ra.y, az.y);
+            }
+            acc.x = fmaf(wz[c], az.x, acc.x);
+            acc.y = fmaf(wz[c], az.y, acc.y);
+        }
+        y[(int64_t)l * M + pi.w] = acc;
+    }
+}
+
+// ------------------------------------------------------------ spreading
+// One sub-problem (<= HQS3_MAXPTS points of one TB^3 bin) is spread into a
+// (TB+W-1)^3 x LC patch in shared memory with shared atomics, then added to
+// the global grid with one float2 atomic per nonzero patch cell.  `unit`
+// spreads the value 1 for every point (the Toeplitz-kernel gridding).
+template <int W>
+__global__ void k_spread3(const float2* __restrict__ y, const int4* __restrict__ pti,
+                          const float4* __restrict__ ptd, const int4* __restrict__ subs, int64_t M, int Gx,
+                          int Gy, int Gz, int L, int LC, int nchunk, int TB, int nbx, int nby, float beta,
+                          int unit, float2* __restrict__ grid) {
+    extern __shared__ float4 smem4[];
+    const int P = TB + W - 1;
+    const int P3 = P * P * P;
+    int4* loc = reinterpret_cast<int4*>(smem4);
+    float* wts = reinterpret_cast<float*>(loc + HQS3_MAXPTS);
+    float2* patch = reinterpret_cast<float2*>(wts + HQS3_MAXPTS * 3 * W);
+    const int4 sb = subs[blockIdx.x];
+    const int bin = sb.x, start = sb.y, cnt = sb.z;
+    const int bx = bin % nbx, by = (bin / nbx) % nby, bz = bin / (nbx * nby);
+    for (int i = threadIdx.x; i < cnt * 3 * W; i += blockDim.x) {
+        const int q = i / (3 * W), hh = i - q * 3 * W;
+        const float4 pd = ptd[start + q];
+        const int ax = hh / W;
+        const float d = ax == 0 ? pd.x : (ax == 1 ? pd.y : pd.z);
+        wts[i] = kb_phi3(d - (float)(hh - ax * W), (float)W, beta);
+    }
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+        const int4 pi = pti[start + i];
+        const int cx = wrap(pi.x + W / 2, Gx), cy = wrap(pi.y + W / 2, Gy), cz = wrap(pi.z + W / 2, Gz);
+        loc[i] = make_int4(cx - bx * TB, cy - by * TB, cz - bz * TB, pi.w);
+    }
+    const int ox = bx * TB - W / 2, oy = by * TB - W / 2, oz = bz * TB - W / 2;
+    for (int ch = blockIdx.y; ch < nchunk; ch += gridDim.y) {
+        const int l0 = ch * LC;
+        const int lines = min(LC, L - l0);
+        for (int e = threadIdx.x; e < P3 * lines; e += blockDim.x) patch[e] = make_float2(0.f, 0.f);
+        __syncthreads();
+        for (int wi = threadIdx.x; wi < cnt * lines; wi += blockDim.x) {
+            const int i = wi / lines, l = wi - i * lines;
+            const int4 c0 = loc[i];
+            const float2 v = unit ? make_float2(1.f, 0.f) : y[(int64_t)(l0 + l) * M + c0.w];
+            const float* wv = wts + i * 3 * W;
+#pragma unroll 1
+            for (int c = 0; c < W; ++c) {
+                const float wzv = wv[2 * W + c];
+#pragma unroll
+                for (int a = 0; a < W; ++a) {
+                    const float wya = wzv * wv[W + a];
+                    const float2 va = make_float2(v.x * wya, v.y * wya);
+                    float2* prow = patch + (((c0.z + c) * P + c0.y + a) * P + c0.x) * lines + l;
+#pragma unroll
+                    for (int b = 0; b < W; ++b) {
+                        atomicAdd(&prow[b * lines].x, va.x * wv[b]);
+                        atomicAdd(&prow[b * lines].y, va.y * wv[b]);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < P3 * lines; e += blockDim.x) {
+            const float2 v = patch[e];
+            if (v.x == 0.f && v.y == 0.f) continue;
+            const int l = e % lines, cell = e / lines;
+            const int cx = cell % P, cy = (cell / P) % P, cz = cell / (P * P);
+            const int gx = wrap(ox + cx, Gx), gy = wrap(oy + cy, Gy), gz = wrap(oz + cz, Gz);
+            atomicAdd(&grid[(((int64_t)gz * Gy + gy) * Gx + gx) * L + l0 + l], v);
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------ FFT passes
+// Line (a, b) of a pass: element p at base + a*sA + p*sP + b.
+struct Lines {
+    int64_t sA, sP;
+};
+
+// plain line load: positions < count read, the rest zero
+struct LdLine {
+    const float2* src;
+    Lines g;
+    int count;
+    HQS_DEV float2 operator()(int64_t a, int64_t b, int p) const {
+        return p < count ? src[a * g.sA + (int64_t)p * g.sP + b] : make_float2(0.f, 0.f);
+    }
+};
+// centred placement: grid position p holds image index grid->image (n on G)
+struct LdCentred {
+    const float2* src;
+    Lines g;
+    int n, G;
+    HQS_DEV float2 operator()(int64_t a, int64_t b, int p) const {
+        const int h = n >> 1;
+        const int i = p < h ? p + h : (p >= G - h ? p - G + h : -1);
+        return i >= 0 ? src[a * g.sA + (int64_t)i * g.sP + b] : make_float2(0.f, 0.f);
+    }
+};
+// first forward pass of the NUFFT: S_l x / (phihat^3) at centred positions,
+// a = z * ny + y, b = coil
+struct LdImageX {
+    const float2* x;
+    const float2* S;
+    const float *apx, *apy, *apz;
+    int nx, ny, G, L;
+    float scale;
+    HQS_DEV float2 operator()(int64_t a, int64_t b, int p) const {
+        const int h = nx >> 1;
+        const int ix = p < h ? p + h : (p >= G - h ? p - G + h : -1);
+        if (ix < 0) return make_float2(0.f, 0.f);
+        const int z = (int)(a / ny), yy = (int)(a - (int64_t)z * ny);
+        const int64_t v = a * nx + ix;
+        return cscale(cmul(S[v * L + b], x[v]), scale * apz[z] * apy[yy] * apx[ix]);
+    }
+};
+// first pass of the Toeplitz product: S_l x in [0, n) (the upper half is zero)
+struct LdToepX {
+    const float2* x;
+    const float2* S;
+    int nx, L;
+    HQS_DEV float2 operator()(int64_t a, int64_t b, int p) const {
+        const int64_t v = a * nx + p;
+        return cmul(S[v * L + b], x[v]);
+    }
+};
+
+// store positions o < count: dst[a*sA + o*sP + b] = line[pos(o)]
+// mode 0: pos = o; mode 1: centred crop (image n = count on grid G);
+// mode 2: circulant crop (count = 2h on grid G)
+struct StLine {
+    float2* dst;
+    Lines g;
+    int count, mode, G;
+    HQS_DEV int pos(int o) const {
+        if (mode == 1) return centred_pos(o, count, G);
+        if (mode == 2) return circ_pos(o, count >> 1, G);
+        return o;
+    }
+    HQS_DEV void operator()(int64_t a, int64_t b, int li, int p0, int pst, const float2* s) const {
+        float2* d = dst + a * g.sA + b;
+        for (int o = p0; o < count; o += pst) d[(int64_t)o * g.sP] = s[pos(o) * kLines + li];
+    }
+};
+// last pass with coil weighting: P[(a*nx + o)*L + b] = conj(S) * line[pos(o)]
+struct StCoil {
+    float2* dst;
+    const float2* S;
+    int nx, L, centred, G;
+    HQS_DEV void operator()(int64_t a, int64_t b, int li, int p0, int pst, const float2* s) const {
+        for (int o = p0; o < nx; o += pst) {
+            const int p = centred ? centred_pos(o, nx, G) : o;
+            const int64_t e = (a * nx + o) * L + b;
+            dst[e] = cmulc(S[e], s[p * kLines + li]);
+        }
+    }
+};
+
+struct NoMid {};
+// Khat multiply between the forward and inverse z transforms: b = (ky*Tx + kx)*L + l
+struct MidKhat {
+    const float* khat;
+    int64_t plane;   // Ty * Tx
+    int L;
+    HQS_DEV float2 operator()(int64_t, int64_t b, int p, float2 v) const {
+        return cscale(v, khat[(int64_t)p * plane + b / L]);
+    }
+};
+
+template <int N> constexpr size_t pass_smem() { return ((size_t)N * kLines + N) * sizeof(float2); }
+
+// One FFT pass over `nlines` lines (a = line / B, b = line % B), kLines per
+// CTA: load (ld), transform (INV, ZIN, HOUT as in block_fft), and store (st).
+// With a MID functor the pass is FFT -> mid -> inverse FFT (HOUT applies to
+// the inverse).
+template <int N, bool INV, bool ZIN, bool HOUT, class LD, class ST, class MID>
+__global__ void k_pass3(LD ld, ST st, MID mid, int64_t nlines, int64_t B, const float2* __restrict__ twg) {
+    extern __shared__ float2 s[];
+    const float2* tw = stage_twiddles<N>(s + N * kLines, twg);
+    const int64_t l0 = (int64_t)blockIdx.x * kLines;
+    const int lines = (int)min((int64_t)kLines, nlines - l0);
+    const int pst = blockDim.x / lines;
+    const int li = threadIdx.x % lines, p0 = threadIdx.x / lines;
+    const int64_t line = l0 + li;
+    const int64_t a = line / B, b = line - a * B;
+    constexpr int NIN = ZIN ? N / 2 : N;
+    if (p0 < pst) {
+        for (int p = p0; p < NIN; p += pst) s[p * kLines + li] = ld(a, b, p);
+    }
+    __syncthreads();
+    if constexpr (std::is_same_v<MID, NoMid>) {
+        block_fft<N, INV, ZIN, HOUT>(s, lines, tw);
+    } else {
+        block_fft<N, false, ZIN, false>(s, lines, tw);
+        if (p0 < pst) {
+            for (int p = p0; p < N; p += pst) s[p * kLines + li] = mid(a, b, p, s[p * kLines + li]);
+        }
+        __syncthreads();
+        block_fft<N, true, false, HOUT>(s, lines, tw);
+    }
+    if (p0 < pst) st(a, b, li, p0, pst, s);
+}
+
+template <class F> int dispatch3(int n, F&& f) { return dispatch_fft_size(n, std::forward<F>(f)); }
+
+const float2* tw3(const hqs_plan3d_s* p, int N) {
+    for (int i = 0; i < 6; ++i)
+        if (p->tw_sizes[i] == N) return p->tw + p->tw_offs[i];
+    return nullptr;
+}
+
+template <bool INV, bool ZIN, bool HOUT, class LD, class ST, class MID = NoMid>
+int run_pass(const hqs_plan3d_s* p, int N, LD ld, ST st, int64_t nlines, int64_t B, cudaStream_t s,
+             MID mid = MID{}) {
+    if (nlines <= 0) return HQS_OK;
+    const float2* tw = tw3(p, N);
+    if (!tw) return HQS_ERR_INVALID_ARG;
+    return dispatch3(N, [&]<int NN>() {
+        auto kern = k_pass3<NN, INV, ZIN, HOUT, LD, ST, MID>;
+        const size_t sm = pass_smem<NN>();
+        HQS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        const int64_t nblk = ceil_div64(nlines, kLines);
+        if (nblk > 0x7fffffff) return HQS_ERR_INVALID_ARG;
+        kern<<<(unsigned)nblk, fft_threads<NN>(kLines), sm, s>>>(ld, st, mid, nlines, B, tw);
+        HQS_CUDA_TRY(cudaGetLastError());
+        return HQS_OK;
+    });
+}
+
+// out[v] = ca * apod(v) * sum_l P[v*L + l] + cb * z[v]   (apod optional, z optional)
+__global__ void k_coil_sum3(const float2* __restrict__ P, int L, int nx, int ny, int64_t nvox,
+                            const float* __restrict__ apx, const float* __restrict__ apy,
+                            const float* __restrict__ apz, float ca, float cb, const float2* z,
+                            float2* out) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nvox;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        float2 a = make_float2(0.f, 0.f);
+        const float2* pv = P + v * L;
+        for (int l = 0; l < L; ++l) a = cadd(a, pv[l]);
+        float f = ca;
+        if (apx) {
+            const int ix = (int)(v % nx);
+            const int64_t r = v / nx;
+            const int iy = (int)(r % ny), iz = (int)(r / ny);
+            f *= apx[ix] * apy[iy] * apz[iz];
+        }
+        float2 o = cscale(a, f);
+        if (z) {
+            const float2 zv = z[v];
+            o.x = fmaf(cb, zv.x, o.x);
+            o.y = fmaf(cb, zv.y, o.y);
+        }
+        out[v] = o;
+    }
+}
+
+// circulant column: c[p] *= prod_axis 1/phihat(d/G') / Nvox, zero on every d = -N plane
+__global__ void k_kernel_deapod(float2* __restrict__ c, int Tx, int Ty, int Tz, const float* __restrict__ ax,
+                                const float* __restrict__ ay, const float* __restrict__ az, float inv_nvox) {
+    const int64_t total = (int64_t)Tx * Ty * Tz;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int px = (int)(e % Tx);
+        const int64_t r = e / Tx;
+        const int py = (int)(r % Ty), pz = (int)(r / Ty);
+        const bool zero = px == Tx / 2 || py == Ty / 2 || pz == Tz / 2;
+        c[e] = zero ? make_float2(0.f, 0.f) : cscale(c[e], ax[px] * ay[py] * az[pz] * inv_nvox);
+    }
+}
+
+__global__ void k_real_part3(const float2* __restrict__ in, float* __restrict__ out, int64_t count, float s) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
+         e += (int64_t)gridDim.x * blockDim.x)
+        out[e] = in[e].x * s;
+}
+
+// ------------------------------------------------------------ CG kernels
+#define CG3_BLOCKS 1024
+enum { CG3_INIT = 0, CG3_ALPHA = 1, CG3_BETA = 2 };
+
+HQS_DEV double block_sum(double v, double* sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    __syncthreads();
+    return t;
+}
+
+// partials[blk] = Re <a, b> over this block's grid-stride share (fp64)
+__global__ void k_dot3(const float2* __restrict__ a, const float2* __restrict__ b, int64_t count,
+                       double* __restrict__ part) {
+    __shared__ double sh[32];
+    double acc = 0.0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const float2 u = a[e], v = b[e];
+        acc += (double)u.x * v.x + (double)u.y * v.y;
+    }
+    const double t = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+// r = rhs - q (q optional), p = r; partials: <r, r> (slot 0) and <rhs, rhs> (slot 1)
+__global__ void k_cg3_init(const float2* __restrict__ rhs, const float2* __restrict__ q, float2* __restrict__ r,
+                           float2* __restrict__ p, int64_t count, double* __restrict__ part) {
+    __shared__ double sh[32];
+    double rr = 0.0, bb = 0.0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const float2 b = rhs[e];
+        const float2 v = q ? csub(b, q[e]) : b;
+        r[e] = v;
+        p[e] = v;
+        rr += (double)v.x * v.x + (double)v.y * v.y;
+        bb += (double)b.x * b.x + (double)b.y * b.y;
+    }
+    const double t0 = block_sum(rr, sh);
+    const double t1 = block_sum(bb, sh);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = t0;
+        part[CG3_BLOCKS + blockIdx.x] = t1;
+    }
+}
+
+__global__ void k_cg3_scalar(Cg3* cg, const double* __restrict__ part, int nparts, int mode, double* hist,
+                             double rel_tol, int max_iter) {
+    if (threadIdx.x != 0) return;
+    double s = 0.0;
+    for (int i = 0; i < nparts; ++i) s += part[i];
+    if (mode == CG3_INIT) {
+        double bb = 0.0;
+        for (int i = 0; i < nparts; ++i) bb += part[CG3_BLOCKS + i];
+        cg->rr = s;
+        cg->bnorm2 = bb;
+        cg->tol2 = rel_tol * rel_tol * bb;
+        cg->it = 0;
+        cg->max_iter = max_iter;
+        cg->status = HQS_OK;
+        cg->done = (bb == 0.0 || s <= cg->tol2) ? 1 : 0;
+        if (!cg->done && max_iter <= 0) {
+            cg->done = 1;
+            cg->status = HQS_ERR_NOT_CONVERGED;
+        }
+        hist[0] = s;
+        return;
+    }
+    if (cg->done) return;
+    if (mode == CG3_ALPHA) {
+        cg->pq = s;
+        if (!(s > 0.0) || !isfinite(s)) {
+            cg->done = 1;
+            cg->status = HQS_ERR_BREAKDOWN;
+            cg->alpha = 0.0;
+            return;
+        }
+        cg->alpha = cg->rr / s;
+    } else {
+        cg->it += 1;
+        cg->beta = s / cg->rr;
+        cg->rr = s;
+        if (cg->it <= HQS_MAX_ITERS) hist[cg->it] = s;
+        if (!isfinite(s)) {
+            cg->done = 1;
+            cg->status = HQS_ERR_BREAKDOWN;
+        } else if (s <= cg->tol2) {
+            cg->done = 1;
+        } else if (cg->it >= cg->max_iter) {
+            cg->done = 1;
+            cg->status = HQS_ERR_NOT_CONVERGED;
+        }
+    }
+}
+
+// x += alpha p, r -= alpha q; partials <r, r>
+__global__ void k_cg3_update(float2* __restrict__ x, float2* __restrict__ r, const float2* __restrict__ p,
+                             const float2* __restrict__ q, int64_t count, const Cg3* __restrict__ cg,
+                             double* __restrict__ part) {
+    __shared__ double sh[32];
+    const bool skip = cg->done != 0;
+    const float al = (float)cg->alpha;
+    double rr = 0.0;
+    if (!skip) {
+        for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
+             e += (int64_t)gridDim.x * blockDim.x) {
+            const float2 pv = p[e], qv = q[e];
+            float2 xv = x[e], rv = r[e];
+            xv.x = fmaf(al, pv.x, xv.x);
+            xv.y = fmaf(al, pv.y, xv.y);
+            rv.x = fmaf(-al, qv.x, rv.x);
+            rv.y = fmaf(-al, qv.y, rv.y);
+            x[e] = xv;
+            r[e] = rv;
+            rr += (double)rv.x * rv.x + (double)rv.y * rv.y;
+        }
+    }
+    const double t = block_sum(rr, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+// p = r + beta p (after the BETA scalar step; skipped once done)
+__global__ void k_cg3_pupdate(float2* __restrict__ p, const float2* __restrict__ r, int64_t count,
+                              const Cg3* __restrict__ cg) {
+    if (cg->done) return;
+    const float be = (float)cg->beta;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const float2 rv = r[e], pv = p[e];
+        p[e] = make_float2(fmaf(be, pv.x, rv.x), fmaf(be, pv.y, rv.y));
+    }
+}
+
+// ------------------------------------------------------------ host side
+double kb_phihat3(double nu, int W, double beta) {
+    const double r2 = beta * beta - (M_PI * W * nu) * (M_PI * W * nu);
+    if (r2 > 1e-300) {
+        const double r = sqrt(r2);
+        return W * sinh(r) / r;
+    }
+    if (r2 < -1e-300) {
+        const double r = sqrt(-r2);
+        return W * sin(r) / r;
+    }
+    return (double)W;
+}
+double kb_beta3(int W, double sigma) {
+    return M_PI * sqrt((double)W * W / (sigma * sigma) * (sigma - 0.5) * (sigma - 0.5) - 0.8);
+}
+
+template <class T> int alloc3(hqs_plan3d_s* p, T** ptr, size_t count) {
+    void* v = nullptr;
+    cudaError_t e = cudaMalloc(&v, std::max<size_t>(count, 1) * sizeof(T));
+    if (e != cudaSuccess) {
+        hqs_note_cuda_error(e, "cudaMalloc", __FILE__, __LINE__);
+        return HQS_ERR_OOM;
+    }
+    p->allocs.push_back(v);
+    p->bytes += count * sizeof(T);
+    *ptr = static_cast<T*>(v);
+    return HQS_OK;
+}
+
+void plan3d_free(hqs_plan3d_s* p) {
+    if (!p) return;
+    for (void* v : p->allocs) cudaFree(v);
+    if (p->h_cg) cudaFreeHost(p->h_cg);
+    delete p;
+}
+
+#define TRY3(expr)                   \
+    do {                             \
+        const int rc_ = (expr);      \
+        if (rc_ != HQS_OK) return rc_; \
+    } while (0)
+
+bool size3_ok(int n) {
+    // n even, 2n and 4n transform sizes of the library
+    return n >= 8 && n % 2 == 0 && fft_size_supported(2 * n) && fft_size_supported(4 * n);
+}
+
+// Sorted points and spreading sub-problems for grid G with kernel width W.
+struct Points3 {
+    int4* pti = nullptr;
+    float4* ptd = nullptr;
+    int4* subs = nullptr;
+    int nsub = 0;
+    int nb[3] = {0, 0, 0};
+};
+
+int build_points(hqs_plan3d_s* p, const float* traj, int64_t M, const int G[3], int W, Points3* out,
+                 bool owned, cudaStream_t s) {
+    for (int a = 0; a < 3; ++a) out->nb[a] = G[a] / HQS3_TILE;
+    const int nbins = out->nb[0] * out->nb[1] * out->nb[2];
+    int4* rawi = nullptr;
+    float4* rawd = nullptr;
+    int* bin = nullptr;
+    int* counts = nullptr;
+    auto cleanup = [&]() {
+        cudaFree(rawi);
+        cudaFree(rawd);
+        cudaFree(bin);
+        cudaFree(counts);
+    };
+    const int64_t Mp = std::max<int64_t>(M, 1);
+    if (cudaMalloc(&rawi, Mp * sizeof(int4)) || cudaMalloc(&rawd, Mp * sizeof(float4)) ||
+        cudaMalloc(&bin, Mp * sizeof(int)) || cudaMalloc(&counts, nbins * sizeof(int))) {
+        cleanup();
+        return HQS_ERR_OOM;
+    }
+    int rc = HQS_OK;
+    do {
+        if (owned) {
+            if ((rc = alloc3(p, &out->pti, (size_t)Mp)) != HQS_OK) break;
+            if ((rc = alloc3(p, &out->ptd, (size_t)Mp)) != HQS_OK) break;
+        } else if (cudaMalloc(&out->pti, Mp * sizeof(int4)) || cudaMalloc(&out->ptd, Mp * sizeof(float4))) {
+            rc = HQS_ERR_OOM;
+            break;
+        }
+        if (cudaMemsetAsync(counts, 0, nbins * sizeof(int), s)) { rc = HQS_ERR_CUDA; break; }
+        if (M > 0)
+            k_points3<<<(unsigned)ceil_div64(M, 256), 256, 0, s>>>(traj, (int)M, G[0], G[1], G[2], W, HQS3_TILE,
+                                                                  out->nb[0], out->nb[1], rawi, rawd, bin, counts);
+        std::vector<int> hc(nbins);
+        if (cudaMemcpyAsync(hc.data(), counts, nbins * sizeof(int), cudaMemcpyDeviceToHost, s) ||
+            cudaStreamSynchronize(s)) { rc = HQS_ERR_CUDA; break; }
+        std::vector<int> offs(nbins);
+        std::vector<int4> subs;
+        int acc = 0;
+        for (int b = 0; b < nbins; ++b) {
+            offs[b] = acc;
+            for (int st = 0; st < hc[b]; st += HQS3_MAXPTS)
+                subs.push_back(make_int4(b, acc + st, std::min(HQS3_MAXPTS, hc[b] - st), 0));
+            acc += hc[b];
+        }
+        out->nsub = (int)subs.size();
+        if (owned) {
+            if ((rc = alloc3(p, &out->subs, subs.size())) != HQS_OK) break;
+        } else if (cudaMalloc(&out->subs, std::max<size_t>(subs.size(), 1) * sizeof(int4))) {
+            rc = HQS_ERR_OOM;
+            break;
+        }
+        if (!subs.empty() &&
+            cudaMemcpyAsync(out->subs, subs.data(), subs.size() * sizeof(int4), cudaMemcpyHostToDevice, s)) {
+            rc = HQS_ERR_CUDA;
+            break;
+        }
+        if (cudaMemcpyAsync(counts, offs.data(), nbins * sizeof(int), cudaMemcpyHostToDevice, s)) {
+            rc = HQS_ERR_CUDA;
+            break;
+        }
+        if (M > 0)
+            k_points3_scatter<<<(unsigned)ceil_div64(M, 256), 256, 0, s>>>(rawi, rawd, bin, (int)M, counts,
+                                                                          out->pti, out->ptd);
+        if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) rc = HQS_ERR_CUDA;
+    } while (0);
+    cleanup();
+    return rc;
+}
+
+template <class F> int dispatch_w3(int W, F&& f) {
+    switch (W) {
+        case 4: return f.template operator()<4>();
+        case 5: return f.template operator()<5>();
+        case 6: return f.template operator()<6>();
+        case 7: return f.template operator()<7>();
+        case 8: return f.template operator()<8>();
+        default: return HQS_ERR_INVALID_ARG;
+    }
+}
+
+// Spread y (or unit data) onto `grid` (zeroed here) of size G with L coils.
+int spread3(const Points3& pts, const float2* y, int64_t M, const int G[3], int L, int W, double beta,
+            bool unit, float2* grid, cudaStream_t s) {
+    const size_t cells = (size_t)G[0] * G[1] * G[2] * L;
+    HQS_CUDA_TRY(cudaMemsetAsync(grid, 0, cells * sizeof(float2), s));
+    if (pts.nsub == 0) return HQS_OK;
+    return dispatch_w3(W, [&]<int WW>() {
+        const int P = HQS3_TILE + WW - 1;
+        const size_t cell_bytes = (size_t)P * P * P * sizeof(float2);
+        const int lc_max = std::max(1, (int)(HQS3_PATCH_BYTES / cell_bytes));
+        const int nch = ceil_div(L, std::min(L, lc_max));
+        const int lc = ceil_div(L, nch);
+        const size_t sm = HQS3_MAXPTS * sizeof(int4) + HQS3_MAXPTS * 3 * WW * sizeof(float) + cell_bytes * lc;
+        HQS_CUDA_TRY(cudaFuncSetAttribute(k_spread3<WW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_spread3<WW><<<dim3(pts.nsub, nch), 256, sm, s>>>(y, pts.pti, pts.ptd, pts.subs, M, G[0], G[1], G[2], L,
+                                                           lc, nch, HQS3_TILE, pts.nb[0], pts.nb[1], (float)beta,
+                                                           unit ? 1 : 0, grid);
+        HQS_CUDA_TRY(cudaGetLastError());
+        return HQS_OK;
+    });
+}
+
+int vec_blocks(int64_t count) { return (int)std::min<int64_t>(ceil_div64(count, 256), CG3_BLOCKS); }
+
+// -------- operators
+int fwd3(hqs_plan3d_s* p, const float2* x, float2* y, cudaStream_t s) {
+    const int nx = p->n[0], ny = p->n[1], nz = p->n[2];
+    const int Gx = p->G[0], Gy = p->G[1], Gz = p->G[2], L = p->L;
+    // x pass: [nz][ny][Gx][L] in bufA
+    TRY3((run_pass<false, false, false>(
+        p, Gx, LdImageX{x, p->smaps, p->apod[0], p->apod[1], p->apod[2], nx, ny, Gx, L, p->scale},
+        StLine{p->bufA, {(int64_t)Gx * L, L}, Gx, 0, Gx}, (int64_t)nz * ny * L, L, s)));
+    // y pass: [nz][Gy][Gx][L] in bufB
+    const int64_t row = (int64_t)Gx * L;
+    TRY3((run_pass<false, false, false>(p, Gy, LdCentred{p->bufA, {(int64_t)ny * row, row}, ny, Gy},
+                                        StLine{p->bufB, {(int64_t)Gy * row, row}, Gy, 0, Gy},
+                                        (int64_t)nz * row, row, s)));
+    // z pass: [Gz][Gy][Gx][L] in bufA
+    const int64_t plane = (int64_t)Gy * row;
+    TRY3((run_pass<false, false, false>(p, Gz, LdCentred{p->bufB, {0, plane}, nz, Gz},
+                                        StLine{p->bufA, {0, plane}, Gz, 0, Gz}, plane, plane, s)));
+    if (p->M == 0) return HQS_OK;
+    return dispatch_w3(p->W, [&]<int WW>() {
+        const int64_t threads = p->M * 16;
+        k_interp3<WW><<<(unsigned)ceil_div64(threads, 256), 256, 0, s>>>(p->bufA, p->pti, p->ptd, (int)p->M, Gx,
+                                                                        Gy, Gz, L, (float)p->beta, y);
+        HQS_CUDA_TRY(cudaGetLastError());
+        return HQS_OK;
+    });
+}
+
+int adj3(hqs_plan3d_s* p, const float2* y, float2* x, cudaStream_t s) {
+    const int nx = p->n[0], ny = p->n[1], nz = p->n[2];
+    const int Gx = p->G[0], Gy = p->G[1], Gz = p->G[2], L = p->L;
+    Points3 pts;
+    pts.pti = p->pti;
+    pts.ptd = p->ptd;
+    pts.subs = p->subs;
+    pts.nsub = p->nsub;
+    for (int a = 0; a < 3; ++a) pts.nb[a] = p->nb[a];
+    TRY3(spread3(pts, y, p->M, p->G, L, p->W, p->beta, false, p->bufA, s));
+    const int64_t row = (int64_t)Gx * L, plane = (int64_t)Gy * row;
+    // z: [nz][Gy][Gx][L] in bufB
+    TRY3((run_pass<true, false, false>(p, Gz, LdLine{p->bufA, {0, plane}, Gz},
+                                       StLine{p->bufB, {0, plane}, nz, 1, Gz}, plane, plane, s)));
+    // y: [nz][ny][Gx][L] in bufA
+    TRY3((run_pass<true, false, false>(p, Gy, LdLine{p->bufB, {plane, row}, Gy},
+                                       StLine{p->bufA, {(int64_t)ny * row, row}, ny, 1, Gy}, (int64_t)nz * row,
+                                       row, s)));
+    // x: conj(S_l) per coil, [nz][ny][nx][L] in bufC
+    TRY3((run_pass<true, false, false>(p, Gx, LdLine{p->bufA, {row, L}, Gx},
+                                       StCoil{p->bufC, p->smaps, nx, L, 1, Gx}, (int64_t)nz * ny * L, L, s)));
+    const int64_t nvox = (int64_t)nx * ny * nz;
+    k_coil_sum3<<<vec_blocks(nvox), 256, 0, s>>>(p->bufC, L, nx, ny, nvox, p->apod[0], p->apod[1], p->apod[2],
+                                                 p->scale, 0.f, nullptr, x);
+    HQS_CUDA_TRY(cudaGetLastError());
+    return HQS_OK;
+}
+
+// out = ca * A^H A x + cb * z (z optional)
+int toep3(hqs_plan3d_s* p, const float2* x, float2* out, float ca, float cb, const float2* z, cudaStream_t s) {
+    const int nx = p->n[0], ny = p->n[1], nz = p->n[2];
+    const int Tx = p->G[0], Ty = p->G[1], Tz = p->G[2], L = p->L;
+    const int64_t row = (int64_t)Tx * L, plane = (int64_t)Ty * row;
+    // x: [nz][ny][Tx][L] in bufA
+    TRY3((run_pass<false, true, false>(p, Tx, LdToepX{x, p->smaps, nx, L}, StLine{p->bufA, {row, L}, Tx, 0, Tx},
+                                       (int64_t)nz * ny * L, L, s)));
+    // y: [nz][Ty][Tx][L] in bufB
+    TRY3((run_pass<false, true, false>(p, Ty, LdLine{p->bufA, {(int64_t)ny * row, row}, ny},
+                                       StLine{p->bufB, {plane, row}, Ty, 0, Ty}, (int64_t)nz * row, row, s)));
+    // z: FFT, Khat, IFFT, rows z < nz, in place in bufB
+    TRY3((run_pass<true, true, true>(p, Tz, LdLine{p->bufB, {0, plane}, nz}, StLine{p->bufB, {0, plane}, nz, 0, Tz},
+                                     plane, plane, s, MidKhat{p->khat, (int64_t)Ty * Tx, L})));
+    // y inverse: [nz][ny][Tx][L] in bufA
+    TRY3((run_pass<true, false, true>(p, Ty, LdLine{p->bufB, {plane, row}, Ty},
+                                      StLine{p->bufA, {(int64_t)ny * row, row}, ny, 0, Ty}, (int64_t)nz * row, row,
+                                      s)));
+    // x inverse: conj(S_l) per coil in bufC
+    TRY3((run_pass<true, false, true>(p, Tx, LdLine{p->bufA, {row, L}, Tx}, StCoil{p->bufC, p->smaps, nx, L, 0, Tx},
+                                      (int64_t)nz * ny * L, L, s)));
+    const int64_t nvox = (int64_t)nx * ny * nz;
+    k_coil_sum3<<<vec_blocks(nvox), 256, 0, s>>>(p->bufC, L, nx, ny, nvox, nullptr, nullptr, nullptr, ca, cb, z,
+                                                 out);
+    HQS_CUDA_TRY(cudaGetLastError());
+    return HQS_OK;
+}
+
+// Khat from the gridded kernel: unit data spread on the 4N grid (width 8),
+// inverse transforms cropped to the 2N circulant, deapodised, FFT_2N.
+int build_khat(hqs_plan3d_s* p, const float* traj, cudaStream_t s) {
+    const int T[3] = {p->G[0], p->G[1], p->G[2]};
+    const int G4[3] = {2 * T[0], 2 * T[1], 2 * T[2]};
+    const int Wk = HQS3_KERNEL_W;
+    const double bk = kb_beta3(Wk, 2.0);
+    Points3 pts;
+    float2* grid = nullptr;
+    float2* mid = nullptr;
+    float* ap[3] = {nullptr, nullptr, nullptr};
+    auto cleanup = [&]() {
+        cudaFree(pts.pti);
+        cudaFree(pts.ptd);
+        cudaFree(pts.subs);
+        cudaFree(grid);
+        cudaFree(mid);
+        for (int a = 0; a < 3; ++a) cudaFree(ap[a]);
+    };
+    int rc = HQS_OK;
+    do {
+        const size_t g4 = (size_t)G4[0] * G4[1] * G4[2];
+        const size_t m2 = (size_t)T[2] * G4[1] * G4[0];   // [2nz][4ny][4nx]
+        if (cudaMalloc(&grid, g4 * sizeof(float2)) || cudaMalloc(&mid, m2 * sizeof(float2))) {
+            rc = HQS_ERR_OOM;
+            break;
+        }
+        for (int a = 0; a < 3; ++a) {
+            std::vector<float> h(T[a]);
+            const int hn = T[a] / 2;
+            for (int q = 0; q < T[a]; ++q) {
+                const int d = q < hn ? q : q - T[a];
+                h[q] = (float)(1.0 / kb_phihat3((double)d / G4[a], Wk, bk));
+            }
+            if (cudaMalloc(&ap[a], T[a] * sizeof(float)) ||
+                cudaMemcpyAsync(ap[a], h.data(), T[a] * sizeof(float), cudaMemcpyHostToDevice, s) ||
+                cudaStreamSynchronize(s)) {
+                rc = HQS_ERR_CUDA;
+                break;
+            }
+        }
+        if (rc != HQS_OK) break;
+        if ((rc = build_points(p, traj, p->M, G4, Wk, &pts, false, s)) != HQS_OK) break;
+        if ((rc = spread3(pts, nullptr, p->M, G4, 1, Wk, bk, true, grid, s)) != HQS_OK) break;
+        // z: [2nz][4ny][4nx] in mid (circulant crop)
+        const int64_t row4 = G4[0], plane4 = (int64_t)G4[1] * G4[0];
+        if ((rc = run_pass<true, false, false>(p, G4[2], LdLine{grid, {0, plane4}, G4[2]},
+                                               StLine{mid, {0, plane4}, T[2], 2, G4[2]}, plane4, plane4, s)))
+            break;
+        // y: [2nz][2ny][4nx] in grid
+        if ((rc = run_pass<true, false, false>(p, G4[1], LdLine{mid, {plane4, row4}, G4[1]},
+                                               StLine{grid, {(int64_t)T[1] * row4, row4}, T[1], 2, G4[1]},
+                                               (int64_t)T[2] * row4, row4, s)))
+            break;
+        // x: [2nz][2ny][2nx] in mid
+        if ((rc = run_pass<true, false, false>(p, G4[0], LdLine{grid, {row4, 1}, G4[0]},
+                                               StLine{mid, {T[0], 1}, T[0], 2, G4[0]}, (int64_t)T[2] * T[1], 1, s)))
+            break;
+        const int64_t t3 = (int64_t)T[0] * T[1] * T[2];
+        const double nvox = (double)p->n[0] * p->n[1] * p->n[2];
+        k_kernel_deapod<<<vec_blocks(t3), 256, 0, s>>>(mid, T[0], T[1], T[2], ap[0], ap[1], ap[2],
+                                                        (float)(1.0 / nvox));
+        // forward FFT of the circulant column, in place (x, y, z)
+        const int64_t rowT = T[0], planeT = (int64_t)T[1] * T[0];
+        if ((rc = run_pass<false, false, false>(p, T[0], LdLine{mid, {rowT, 1}, T[0]}, StLine{mid, {rowT, 1}, T[0], 0, T[0]},
+                                                (int64_t)T[2] * T[1], 1, s)))
+            break;
+        if ((rc = run_pass<false, false, false>(p, T[1], LdLine{mid, {planeT, rowT}, T[1]},
+                                                StLine{mid, {planeT, rowT}, T[1], 0, T[1]}, (int64_t)T[2] * rowT,
+                                                rowT, s)))
+            break;
+        if ((rc = run_pass<false, false, false>(p, T[2], LdLine{mid, {0, planeT}, T[2]},
+                                                StLine{mid, {0, planeT}, T[2], 0, T[2]}, planeT, planeT, s)))
+            break;
+        k_real_part3<<<vec_blocks(t3), 256, 0, s>>>(mid, p->khat, t3, (float)(1.0 / (double)t3));
+        if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) rc = HQS_ERR_CUDA;
+    } while (0);
+    cleanup();
+    return rc;
+}
+
+int plan3d_build(hqs_plan3d_s* p, const float* traj, const float2* smaps_user, cudaStream_t s) {
+    const int nx = p->n[0], ny = p->n[1], nz = p->n[2], L = p->L;
+    const int64_t nvox = (int64_t)nx * ny * nz;
+    const int64_t gvox = (int64_t)p->G[0] * p->G[1] * p->G[2];
+    TRY3(alloc3(p, &p->smaps, (size_t)(nvox * L)));
+    for (int a = 0; a < 3; ++a) TRY3(alloc3(p, &p->apod[a], (size_t)p->n[a]));
+    TRY3(alloc3(p, &p->khat, (size_t)gvox));
+    TRY3(alloc3(p, &p->bufA, (size_t)(gvox * L)));
+    TRY3(alloc3(p, &p->bufB, (size_t)(gvox / 2 * L)));
+    TRY3(alloc3(p, &p->bufC, (size_t)(nvox * L)));
+    TRY3(alloc3(p, &p->cg_r, (size_t)nvox));
+    TRY3(alloc3(p, &p->cg_p, (size_t)nvox));
+    TRY3(alloc3(p, &p->cg_q, (size_t)nvox));
+    TRY3(alloc3(p, &p->partials, (size_t)2 * CG3_BLOCKS));
+    TRY3(alloc3(p, &p->cg, 1));
+    TRY3(alloc3(p, &p->hist, HQS_MAX_ITERS + 1));
+    HQS_CUDA_TRY(cudaMallocHost(&p->h_cg, sizeof(Cg3)));
+    // twiddles for 2n and 4n per axis
+    {
+        int ns = 0, total = 0;
+        for (int a = 0; a < 3; ++a)
+            for (int m = 2; m <= 4; m += 2) {
+                const int N = m * p->n[a];
+                bool seen = false;
+                for (int k = 0; k < ns; ++k) seen |= p->tw_sizes[k] == N;
+                if (!seen) {
+                    p->tw_sizes[ns] = N;
+                    p->tw_offs[ns] = total;
+                    total += N;
+                    ++ns;
+                }
+            }
+        std::vector<float2> h(total);
+        for (int k = 0; k < ns; ++k)
+            for (int m = 0; m < p->tw_sizes[k]; ++m) {
+                const double ang = -2.0 * M_PI * (double)m / (double)p->tw_sizes[k];
+                h[p->tw_offs[k] + m] = make_float2((float)cos(ang), (float)sin(ang));
+            }
+        TRY3(alloc3(p, &p->tw, (size_t)total));
+        HQS_CUDA_TRY(cudaMemcpyAsync(p->tw, h.data(), total * sizeof(float2), cudaMemcpyHostToDevice, s));
+        HQS_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    for (int a = 0; a < 3; ++a) {
+        std::vector<float> h(p->n[a]);
+        for (int i = 0; i < p->n[a]; ++i)
+            h[i] = (float)(1.0 / kb_phihat3((double)(i - p->n[a] / 2) / p->G[a], p->W, p->beta));
+        HQS_CUDA_TRY(cudaMemcpyAsync(p->apod[a], h.data(), p->n[a] * sizeof(float), cudaMemcpyHostToDevice, s));
+        HQS_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    k_smaps3_coil_inner<<<(unsigned)std::min<int64_t>(ceil_div64(nvox * L, 256), 8192), 256, 0, s>>>(
+        smaps_user, p->smaps, nvox, L);
+    HQS_CUDA_TRY(cudaGetLastError());
+    Points3 pts;
+    TRY3(build_points(p, traj, p->M, p->G, p->W, &pts, true, s));
+    p->pti = pts.pti;
+    p->ptd = pts.ptd;
+    p->subs = pts.subs;
+    p->nsub = pts.nsub;
+    for (int a = 0; a < 3; ++a) p->nb[a] = pts.nb[a];
+    if (p->M > 0) {
+        TRY3(build_khat(p, traj, s));
+    } else {
+        HQS_CUDA_TRY(cudaMemsetAsync(p->khat, 0, gvox * sizeof(float), s));
+    }
+    HQS_CUDA_TRY(cudaStreamSynchronize(s));
+    return HQS_OK;
+}
+
+}  // namespace
+
+// ================================================================ C ABI
+extern "C" int hqs_plan3d_create(hqs_plan3d* out, const float* traj, int64_t M, int nz, int ny, int nx, int coils,
+                                 const hqs_c64* smaps, int kernel_width, float oversamp, void* stream) {
+    if (!out) return HQS_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (M < 0 || M > 0x7fffffffLL || (M > 0 && !traj) || !smaps || coils < 1 || coils > 64) return HQS_ERR_INVALID_ARG;
+    if (kernel_width < 4 || kernel_width > 8 || oversamp != 2.0f) return HQS_ERR_INVALID_ARG;
+    if (!size3_ok(nx) || !size3_ok(ny) || !size3_ok(nz)) return HQS_ERR_INVALID_ARG;
+    auto* p = new (std::nothrow) hqs_plan3d_s;
+    if (!p) return HQS_ERR_OOM;
+    cudaGetDevice(&p->device);
+    p->n[0] = nx;
+    p->n[1] = ny;
+    p->n[2] = nz;
+    for (int a = 0; a < 3; ++a) p->G[a] = 2 * p->n[a];
+    p->L = coils;
+    p->W = kernel_width;
+    p->beta = kb_beta3(kernel_width, 2.0);
+    p->M = M;
+    p->scale = (float)(1.0 / sqrt((double)nx * ny * nz));
+    const int rc = plan3d_build(p, traj, reinterpret_cast<const float2*>(smaps), (cudaStream_t)stream);
+    if (rc != HQS_OK) {
+        cudaStreamSynchronize((cudaStream_t)stream);
+        plan3d_free(p);
+        return rc;
+    }
+    *out = p;
+    return HQS_OK;
+}
+
+extern "C" void hqs_plan3d_destroy(hqs_plan3d plan) {
+    if (plan) cudaDeviceSynchronize();
+    plan3d_free(plan);
+}
+
+extern "C" int hqs_plan3d_get_khat(hqs_plan3d p, float* out, void* stream) {
+    if (!p || !out) return HQS_ERR_INVALID_ARG;
+    const size_t n = (size_t)p->G[0] * p->G[1] * p->G[2];
+    HQS_CUDA_TRY(cudaMemcpyAsync(out, p->khat, n * sizeof(float), cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    return HQS_OK;
+}
+
+extern "C" int hqs_forward3d(hqs_plan3d p, const hqs_c64* x, hqs_c64* y, void* stream) {
+    if (!p || !x || (!y && p->M > 0)) return HQS_ERR_INVALID_ARG;
+    return fwd3(p, reinterpret_cast<const float2*>(x), reinterpret_cast<float2*>(y), (cudaStream_t)stream);
+}
+
+extern "C" int hqs_adjoint3d(hqs_plan3d p, const hqs_c64* y, hqs_c64* x, void* stream) {
+    if (!p || !x || (!y && p->M > 0)) return HQS_ERR_INVALID_ARG;
+    return adj3(p, reinterpret_cast<const float2*>(y), reinterpret_cast<float2*>(x), (cudaStream_t)stream);
+}
+
+extern "C" int hqs_toeplitz_normal3d(hqs_plan3d p, const hqs_c64* x, hqs_c64* out, void* stream) {
+    if (!p || !x || !out || x == out) return HQS_ERR_INVALID_ARG;
+    return toep3(p, reinterpret_cast<const float2*>(x), reinterpret_cast<float2*>(out), 1.f, 0.f, nullptr,
+                 (cudaStream_t)stream);
+}
+
+extern "C" int hqs_dc_solve3d(hqs_plan3d p, float a, float b, const hqs_c64* rhs_c, hqs_c64* x_c, int max_iter,
+                              double rel_tol, hqs_solve_info* info, void* stream) {
+    if (!p || !rhs_c || !x_c || max_iter < 0 || max_iter > HQS_MAX_ITERS || !(rel_tol >= 0.0) ||
+        reinterpret_cast<const void*>(rhs_c) == reinterpret_cast<const void*>(x_c))
+        return HQS_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const float2* rhs = reinterpret_cast<const float2*>(rhs_c);
+    float2* x = reinterpret_cast<float2*>(x_c);
+    const int64_t nvox = (int64_t)p->n[0] * p->n[1] * p->n[2];
+    const int nb = vec_blocks(nvox);
+    // q = H x for the initial residual
+    TRY3(toep3(p, x, p->cg_q, a, b, x, s));
+    k_cg3_init<<<nb, 256, 0, s>>>(rhs, p->cg_q, p->cg_r, p->cg_p, nvox, p->partials);
+    k_cg3_scalar<<<1, 32, 0, s>>>(p->cg, p->partials, nb, CG3_INIT, p->hist, rel_tol, max_iter);
+    HQS_CUDA_TRY(cudaGetLastError());
+    for (int it = 0; it < max_iter; ++it) {
+        HQS_CUDA_TRY(cudaMemcpyAsync(p->h_cg, p->cg, sizeof(Cg3), cudaMemcpyDeviceToHost, s));
+        HQS_CUDA_TRY(cudaStreamSynchronize(s));
+        if (p->h_cg->done) break;
+        TRY3(toep3(p, p->cg_p, p->cg_q, a, b, p->cg_p, s));
+        k_dot3<<<nb, 256, 0, s>>>(p->cg_p, p->cg_q, nvox, p->partials);
+        k_cg3_scalar<<<1, 32, 0, s>>>(p->cg, p->partials, nb, CG3_ALPHA, p->hist, rel_tol, max_iter);
+        k_cg3_update<<<nb, 256, 0, s>>>(x, p->cg_r, p->cg_p, p->cg_q, nvox, p->cg, p->partials);
+        k_cg3_scalar<<<1, 32, 0, s>>>(p->cg, p->partials, nb, CG3_BETA, p->hist, rel_tol, max_iter);
+        k_cg3_pupdate<<<nb, 256, 0, s>>>(p->cg_p, p->cg_r, nvox, p->cg);
+        HQS_CUDA_TRY(cudaGetLastError());
+    }
+    HQS_CUDA_TRY(cudaMemcpyAsync(p->h_cg, p->cg, sizeof(Cg3), cudaMemcpyDeviceToHost, s));
+    HQS_CUDA_TRY(cudaStreamSynchronize(s));
+    const Cg3 c = *p->h_cg;
+    if (info) {
+        std::vector<double> h(HQS_MAX_ITERS + 1);
+        HQS_CUDA_TRY(cudaMemcpy(h.data(), p->hist, h.size() * sizeof(double), cudaMemcpyDeviceToHost));
+        info->iterations = c.it;
+        info->status = c.status;
+        info->fallback = 0;
+        info->reserved = 0;
+        info->rhs_norm = sqrt(c.bnorm2);
+        const double bn = c.bnorm2 > 0.0 ? sqrt(c.bnorm2) : 1.0;
+        info->rel_residual = c.bnorm2 > 0.0 ? sqrt(std::max(c.rr, 0.0)) / bn : 0.0;
+        for (int i = 0; i <= HQS_MAX_ITERS; ++i)
+            info->res_history[i] = i <= c.it ? sqrt(std::max(h[i], 0.0)) / bn : 0.0;
+    }
+    if (c.bnorm2 == 0.0) HQS_CUDA_TRY(cudaMemsetAsync(x, 0, nvox * sizeof(float2), s));
+    return c.status;
+}
+
+extern "C" int hqs_plan3d_get_info(hqs_plan3d p, int64_t* npoints, int* nsub, size_t* device_bytes) {
+    if (!p) return HQS_ERR_INVALID_ARG;
+    if (npoints) *npoints = p->M;
+    if (nsub) *nsub = p->nsub;
+    if (device_bytes) *device_bytes = p->bytes;
+    return HQS_OK;
+}

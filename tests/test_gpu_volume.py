@@ -1,0 +1,219 @@
+"""Volumetric (3D) operator on the GPU against the FP64 oracle.
+
+Tolerances.  The GPU and the oracle grid with the same Kaiser-Bessel kernel,
+so they differ by float32 rounding only: a 3D transform of size G^3 adds about
+log2(G^3) * 2^-24 relative error per pass and the W^3-tap sums about
+2^-24 sqrt(W^3); with four passes that is ~1e-6, and the checks allow 1e-5.
+The GPU's Toeplitz kernel is gridded with an 8-wide kernel on a 4N grid,
+whose relative error is ~1e-7 (the oracle pins show 7e-8 for the operator at
+W = 8), so the Toeplitz product against the exact oracle embedding is held to
+the same 1e-5.  At the benchmark size the oracle cannot run whole: there the
+forward and adjoint are checked at sampled points/voxels against the exact
+NUDFT (difference = the W = 6 gridding error, ~1e-5), the Toeplitz kernel at
+sampled offsets against its defining sum, and A^H A against the GPU's own
+adjoint of its forward (two independent code paths, equal up to the gridding
+error).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from helpers import rel, to_dev, to_host
+from oracle import nufft3d, solvers
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def hq():
+    import paper_2411_01955_gb300 as m
+    return m
+
+
+def q(case):
+    out = dict(case)
+    out["x"] = case["x"].astype(np.complex64).astype(np.complex128)
+    out["smaps"] = case["smaps"].astype(np.complex64).astype(np.complex128)
+    out["traj"] = case["traj"].astype(np.float32)
+    return out
+
+
+CASES = {
+    # anisotropic, 3 coils (a ragged coil chunk), 8 planes of 4 x 256 samples
+    "aniso": lambda: q(synth.volume_case(1, (8, 16, 32), 3, 4, 256)),
+    # 32^3 with 8 coils, width 4
+    "cube32": lambda: q(dict(synth.volume_case(2, (32, 32, 32), 8, 4, 128), W=4)),
+}
+
+
+def plan_of(case, W=None):
+    traj = to_dev(case["traj"], np.float32)
+    smaps = to_dev(case["smaps"])
+    return hq().plan3d_create(traj, case["shape"], smaps, W or case["W"], 2.0), traj, smaps
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_forward_adjoint_3d_match_oracle(name):
+    c = CASES[name]()
+    plan, _, _ = plan_of(c)
+    L, M = c["L"], c["traj"].shape[0]
+    x = to_dev(c["x"])
+    y = torch.empty((L, M), dtype=torch.complex64, device="cuda")
+    hq().forward3d(plan, x, y)
+    want = nufft3d.forward(c["x"], c["smaps"], c["traj"], c["W"], c["sigma"])
+    ef = rel(to_host(y), want)
+    yin = synth.complex_noise(5, (L, M)).astype(np.complex64).astype(np.complex128)
+    xa = torch.empty(c["shape"], dtype=torch.complex64, device="cuda")
+    hq().adjoint3d(plan, to_dev(yin), xa)
+    ea = rel(to_host(xa), nufft3d.adjoint(yin, c["smaps"], c["traj"], c["W"], c["sigma"]))
+    print(f"{name}: forward {ef:.2e}, adjoint {ea:.2e}")
+    assert ef <= 1e-5 and ea <= 1e-5
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_toeplitz_3d_matches_exact_embedding(name):
+    c = CASES[name]()
+    plan, _, _ = plan_of(c)
+    K = nufft3d.khat(nufft3d.kernel(c["traj"], c["shape"]))
+    T = [2 * v for v in c["shape"]]
+    kg = torch.empty(T, dtype=torch.float32, device="cuda")
+    hq().plan3d_khat(plan, kg)
+    torch.cuda.synchronize()
+    ek = rel(kg.cpu().numpy().astype(np.float64) * np.prod(T), K)
+    out = torch.empty(c["shape"], dtype=torch.complex64, device="cuda")
+    hq().toeplitz_normal3d(plan, to_dev(c["x"]), out)
+    et = rel(to_host(out), nufft3d.normal(c["x"], c["smaps"], K))
+    print(f"{name}: Khat {ek:.2e}, A^H A {et:.2e}")
+    assert ek <= 1e-5 and et <= 1e-5
+
+
+def test_adjointness_3d_on_gpu():
+    c = CASES["aniso"]()
+    plan, _, _ = plan_of(c)
+    L, M = c["L"], c["traj"].shape[0]
+    rng = np.random.default_rng(3)
+    xv = (rng.normal(size=c["shape"]) + 1j * rng.normal(size=c["shape"])).astype(np.complex64)
+    yv = (rng.normal(size=(L, M)) + 1j * rng.normal(size=(L, M))).astype(np.complex64)
+    Ax = torch.empty((L, M), dtype=torch.complex64, device="cuda")
+    Ahy = torch.empty(c["shape"], dtype=torch.complex64, device="cuda")
+    hq().forward3d(plan, to_dev(xv), Ax)
+    hq().adjoint3d(plan, to_dev(yv), Ahy)
+    lhs = np.vdot(yv.astype(np.complex128), to_host(Ax))
+    rhs = np.vdot(to_host(Ahy), xv.astype(np.complex128))
+    assert abs(lhs - rhs) / abs(lhs) < 1e-5
+
+
+def test_dc_solve_3d_matches_oracle_cg():
+    c = CASES["aniso"]()
+    plan, _, _ = plan_of(c)
+    mu = 1e-2
+    K = nufft3d.khat(nufft3d.kernel(c["traj"], c["shape"]))
+    y = nufft3d.forward(c["x"], c["smaps"], c["traj"], c["W"], c["sigma"])
+    rhs = nufft3d.adjoint(y, c["smaps"], c["traj"], c["W"], c["sigma"])
+    rhs = rhs.astype(np.complex64).astype(np.complex128)
+    H = lambda v: nufft3d.normal(v, c["smaps"], K) + mu * v
+    xo, io = solvers.pcg(H, rhs, np.zeros_like(rhs), max_iter=200, tol=1e-4)
+    x = torch.zeros(c["shape"], dtype=torch.complex64, device="cuda")
+    info = hq().dc_solve3d(plan, 1.0, mu, to_dev(rhs), x, max_iter=200, rel_tol=1e-4)
+    got = to_host(x)
+    true_res = float(np.linalg.norm(rhs - H(got)) / np.linalg.norm(rhs))
+    print(f"3D DC solve: {info.iterations} iterations (oracle {io['iters']}), recursion {info.rel_residual:.2e}, "
+          f"true {true_res:.2e}, vs oracle solution {rel(got, xo):.2e}")
+    assert info.rc == hq().HQS_OK and info.rel_residual <= 1e-4
+    assert abs(info.iterations - io["iters"]) <= max(2, io["iters"] // 10)
+    assert true_res <= 2e-4
+    # the CG recursion history starts at 1 for a zero start and decreases overall
+    h = info.history()
+    assert abs(h[0] - 1.0) < 1e-6 and h[-1] <= 1e-4
+
+
+def test_dc_solve_3d_zero_rhs_and_start_at_solution():
+    c = CASES["aniso"]()
+    plan, _, _ = plan_of(c)
+    x = torch.full(c["shape"], 1 + 1j, dtype=torch.complex64, device="cuda")
+    info = hq().dc_solve3d(plan, 1.0, 1e-2, torch.zeros_like(x), x, max_iter=10, rel_tol=1e-4)
+    assert info.rc == hq().HQS_OK and info.iterations == 0
+    assert float(x.abs().max()) == 0.0
+
+
+def test_volume_edge_cases():
+    c = CASES["aniso"]()
+    smaps = to_dev(c["smaps"])
+    empty = torch.zeros((0, 3), dtype=torch.float32, device="cuda")
+    plan = hq().plan3d_create(empty, c["shape"], smaps, 6, 2.0)
+    x = to_dev(c["x"])
+    out = torch.full(c["shape"], 7.0, dtype=torch.complex64, device="cuda")
+    hq().adjoint3d(plan, torch.zeros((c["L"], 0), dtype=torch.complex64, device="cuda"), out)
+    assert float(out.abs().max()) == 0.0
+    out.fill_(7.0)
+    hq().toeplitz_normal3d(plan, x, out)
+    assert float(out.abs().max()) == 0.0
+    traj = to_dev(c["traj"], np.float32)
+    for shape, W, sg in [((8, 16, 24), 6, 2.0), ((8, 16, 32), 3, 2.0), ((8, 16, 32), 6, 1.5),
+                         ((4, 16, 32), 6, 2.0)]:
+        with pytest.raises(hq().HqsError) as e:
+            hq().plan3d_create(traj, shape, to_dev(np.ones((c["L"],) + shape, np.complex64)), W, sg)
+        assert e.value.status == hq().HQS_ERR_INVALID_ARG
+
+
+# ------------------------------------------------------------ benchmark size
+def test_volume_benchmark_size_sampled():
+    shape, L = (64, 64, 64), 16
+    c = q(synth.volume_case(0, shape, L, 8, 1024))
+    plan, _, _ = plan_of(c)
+    M = c["traj"].shape[0]
+    x = to_dev(c["x"])
+    y = torch.empty((L, M), dtype=torch.complex64, device="cuda")
+    hq().forward3d(plan, x, y)
+    yh = to_host(y)
+    rng = np.random.default_rng(9)
+    k = c["traj"].astype(np.float64)
+    nz, ny, nx = shape
+    ez, ey, ex = (np.arange(n) - n // 2 for n in shape)
+    # forward: 48 sampled points, all coils, against the exact NUDFT sum
+    js = rng.choice(M, 48, replace=False)
+    Ex = np.exp(-1j * np.outer(k[js, 0], ex))
+    Ey = np.exp(-1j * np.outer(k[js, 1], ey))
+    Ez = np.exp(-1j * np.outer(k[js, 2], ez))
+    phase = Ez[:, :, None, None] * Ey[:, None, :, None] * Ex[:, None, None, :]   # (48, nz, ny, nx)
+    want = np.einsum("jzyx,lzyx->lj", phase, c["smaps"] * c["x"]) / math.sqrt(nz * ny * nx)
+    ef = rel(yh[:, js], want)
+    # adjoint: 32 sampled voxels against the exact sum over every point
+    yin = synth.complex_noise(6, (L, M)).astype(np.complex64).astype(np.complex128)
+    xa = torch.empty(shape, dtype=torch.complex64, device="cuda")
+    hq().adjoint3d(plan, to_dev(yin), xa)
+    xah = to_host(xa)
+    vs = [tuple(int(rng.integers(0, shape[a])) for a in range(3)) for _ in range(32)]
+    got, exp_ = [], []
+    for (iz, iy, ix) in vs:
+        ph = np.exp(1j * (k[:, 0] * (ix - nx // 2) + k[:, 1] * (iy - ny // 2) + k[:, 2] * (iz - nz // 2)))
+        s = (yin @ ph)                                    # per coil
+        exp_.append(np.sum(np.conj(c["smaps"][:, iz, iy, ix]) * s) / math.sqrt(nz * ny * nx))
+        got.append(xah[iz, iy, ix])
+    ea = rel(np.array(got), np.array(exp_))
+    # Toeplitz kernel: sampled offsets of IFFT(Khat) against the defining sum
+    T = [2 * v for v in shape]
+    kg = torch.empty(T, dtype=torch.float32, device="cuda")
+    hq().plan3d_khat(plan, kg)
+    torch.cuda.synchronize()
+    cfull = np.fft.ifftn(kg.cpu().numpy().astype(np.float64)) * np.prod(T)
+    got_t, want_t = [], []
+    for _ in range(24):
+        p = tuple(int(rng.integers(0, t)) for t in T)
+        d = [pp if pp < t // 2 else pp - t for pp, t in zip(p, T)]
+        zero = any(pp == t // 2 for pp, t in zip(p, T))
+        w = 0.0 if zero else np.sum(np.exp(1j * (k[:, 0] * d[2] + k[:, 1] * d[1] + k[:, 2] * d[0]))) / (nz * ny * nx)
+        got_t.append(cfull[p])
+        want_t.append(w)
+    et = np.max(np.abs(np.array(got_t) - np.array(want_t))) / np.abs(cfull[0, 0, 0])
+    # A^H A against the GPU adjoint of the GPU forward
+    out = torch.empty(shape, dtype=torch.complex64, device="cuda")
+    hq().toeplitz_normal3d(plan, x, out)
+    ref = torch.empty(shape, dtype=torch.complex64, device="cuda")
+    hq().adjoint3d(plan, y, ref)
+    en = rel(to_host(out), to_host(ref))
+    print(f"64^3 x 16 coils, {M} points: forward {ef:.2e}, adjoint {ea:.2e}, kernel {et:.2e}, "
+          f"Toeplitz vs A^H(A x) {en:.2e}")
+    assert ef <= 1e-4 and ea <= 1e-4 and et <= 1e-5 and en <= 1e-4
