@@ -34,7 +34,6 @@ using namespace hqs;
 #define HQS3_TILE 8           // spreading bin edge on the grid
 #define HQS3_MAXPTS 256       // points per spreading sub-problem
 #define HQS3_KERNEL_W 8       // KB width used to grid the Toeplitz kernel
-#define HQS3_PATCH_BYTES (96 * 1024)
 
 struct Cg3 {
     double rr, pq, alpha, beta, bnorm2, tol2;
@@ -204,20 +203,28 @@ __global__ void __launch_bounds__(256) k_interp3(const float2* __restrict__ Gh, 
 
 // ------------------------------------------------------------ spreading
 // One sub-problem (<= HQS3_MAXPTS points of one TB^3 bin) is spread into a
-// (TB+W-1)^3 x LC patch in shared memory with shared atomics, then added to
-// the global grid with one float2 atomic per nonzero patch cell.  `unit`
-// spreads the value 1 for every point (the Toeplitz-kernel gridding).
+// (TB+W-1)^3 patch of LC coils (a power of two) in shared memory, then added
+// to the global grid with one float2 atomic per nonzero patch cell.  The
+// patch has no shared atomics: warp w owns the patch planes z = w (mod 8), so
+// for each point the (at most one) footprint plane of a warp is updated by
+// that warp alone, lanes over (cell, coil) entries of the plane, with a warp
+// barrier between points.  `unit` spreads the value 1 for every point (the
+// Toeplitz-kernel gridding).
+#define HQS3_SPREAD_WARPS 8
 template <int W>
-__global__ void k_spread3(const float2* __restrict__ y, const int4* __restrict__ pti,
-                          const float4* __restrict__ ptd, const int4* __restrict__ subs, int64_t M, int Gx,
-                          int Gy, int Gz, int L, int LC, int nchunk, int TB, int nbx, int nby, float beta,
-                          int unit, float2* __restrict__ grid) {
+__global__ void __launch_bounds__(HQS3_SPREAD_WARPS * 32)
+    k_spread3(const float2* __restrict__ y, const int4* __restrict__ pti, const float4* __restrict__ ptd,
+              const int4* __restrict__ subs, int64_t M, int Gx, int Gy, int Gz, int L, int lcs, int nchunk,
+              int TB, int nbx, int nby, float beta, int unit, float2* __restrict__ grid) {
+    static_assert(W <= HQS3_SPREAD_WARPS, "one footprint plane per warp and point");
     extern __shared__ float4 smem4[];
+    const int LC = 1 << lcs;
     const int P = TB + W - 1;
     const int P3 = P * P * P;
     int4* loc = reinterpret_cast<int4*>(smem4);
     float* wts = reinterpret_cast<float*>(loc + HQS3_MAXPTS);
-    float2* patch = reinterpret_cast<float2*>(wts + HQS3_MAXPTS * 3 * W);
+    float2* vals = reinterpret_cast<float2*>(wts + HQS3_MAXPTS * 3 * W);
+    float2* patch = vals + HQS3_MAXPTS * LC;
     const int4 sb = subs[blockIdx.x];
     const int bin = sb.x, start = sb.y, cnt = sb.z;
     const int bx = bin % nbx, by = (bin / nbx) % nby, bz = bin / (nbx * nby);
@@ -233,38 +240,50 @@ __global__ void k_spread3(const float2* __restrict__ y, const int4* __restrict__
         const int cx = wrap(pi.x + W / 2, Gx), cy = wrap(pi.y + W / 2, Gy), cz = wrap(pi.z + W / 2, Gz);
         loc[i] = make_int4(cx - bx * TB, cy - by * TB, cz - bz * TB, pi.w);
     }
+    __syncthreads();   // loc and wts are read by other threads below
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ox = bx * TB - W / 2, oy = by * TB - W / 2, oz = bz * TB - W / 2;
+    constexpr int W2 = W * W;
+    const int E = W2 << lcs;     // (cell, coil) entries of one footprint plane
     for (int ch = blockIdx.y; ch < nchunk; ch += gridDim.y) {
         const int l0 = ch * LC;
         const int lines = min(LC, L - l0);
-        for (int e = threadIdx.x; e < P3 * lines; e += blockDim.x) patch[e] = make_float2(0.f, 0.f);
-        __syncthreads();
-        for (int wi = threadIdx.x; wi < cnt * lines; wi += blockDim.x) {
-            const int i = wi / lines, l = wi - i * lines;
-            const int4 c0 = loc[i];
-            const float2 v = unit ? make_float2(1.f, 0.f) : y[(int64_t)(l0 + l) * M + c0.w];
-            const float* wv = wts + i * 3 * W;
-#pragma unroll 1
-            for (int c = 0; c < W; ++c) {
-                const float wzv = wv[2 * W + c];
-#pragma unroll
-                for (int a = 0; a < W; ++a) {
-                    const float wya = wzv * wv[W + a];
-                    const float2 va = make_float2(v.x * wya, v.y * wya);
-                    float2* prow = patch + (((c0.z + c) * P + c0.y + a) * P + c0.x) * lines + l;
-#pragma unroll
-                    for (int b = 0; b < W; ++b) {
-                        atomicAdd(&prow[b * lines].x, va.x * wv[b]);
-                        atomicAdd(&prow[b * lines].y, va.y * wv[b]);
-                    }
-                }
-            }
+        for (int e = threadIdx.x; e < P3 * LC; e += blockDim.x) patch[e] = make_float2(0.f, 0.f);
+        for (int e = threadIdx.x; e < cnt * LC; e += blockDim.x) {
+            const int i = e >> lcs, l = e & (LC - 1);
+            float2 v = make_float2(0.f, 0.f);
+            if (l < lines) v = unit ? make_float2(1.f, 0.f) : y[(int64_t)(l0 + l) * M + loc[i].w];
+            vals[e] = v;
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < P3 * lines; e += blockDim.x) {
+        for (int i = 0; i < cnt; ++i) {
+            const int4 c0 = loc[i];
+            const int c = ((warp - c0.z) % HQS3_SPREAD_WARPS + HQS3_SPREAD_WARPS) % HQS3_SPREAD_WARPS;
+            if (c < W) {
+                const float* wv = wts + i * 3 * W;
+                const float wz = wv[2 * W + c];
+                float2* plane = patch + (((c0.z + c) * P + c0.y) * P + c0.x) * LC;
+                for (int e = lane; e < E; e += 32) {
+                    const int l = e & (LC - 1), cell = e >> lcs;
+                    const int a = cell / W, b = cell - a * W;
+                    const float w = wz * wv[W + a] * wv[b];
+                    const float2 v = vals[(i << lcs) + l];
+                    float2* dst = plane + ((a * P + b) << lcs) + l;
+                    float2 acc = *dst;
+                    acc.x = fmaf(w, v.x, acc.x);
+                    acc.y = fmaf(w, v.y, acc.y);
+                    *dst = acc;
+                }
+            }
+            __syncwarp();
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < P3 * LC; e += blockDim.x) {
+            const int l = e & (LC - 1);
+            if (l >= lines) continue;
             const float2 v = patch[e];
             if (v.x == 0.f && v.y == 0.f) continue;
-            const int l = e % lines, cell = e / lines;
+            const int cell = e >> lcs;
             const int cx = cell % P, cy = (cell / P) % P, cz = cell / (P * P);
             const int gx = wrap(ox + cx, Gx), gy = wrap(oy + cy, Gy), gz = wrap(oz + cz, Gz);
             atomicAdd(&grid[(((int64_t)gz * Gy + gy) * Gx + gx) * L + l0 + l], v);
@@ -761,14 +780,16 @@ int spread3(const Points3& pts, const float2* y, int64_t M, const int G[3], int 
     return dispatch_w3(W, [&]<int WW>() {
         const int P = HQS3_TILE + WW - 1;
         const size_t cell_bytes = (size_t)P * P * P * sizeof(float2);
-        const int lc_max = std::max(1, (int)(HQS3_PATCH_BYTES / cell_bytes));
-        const int nch = ceil_div(L, std::min(L, lc_max));
-        const int lc = ceil_div(L, nch);
-        const size_t sm = HQS3_MAXPTS * sizeof(int4) + HQS3_MAXPTS * 3 * WW * sizeof(float) + cell_bytes * lc;
+        // coils per chunk: 4, or 2 where a 4-coil patch would exceed 72 KB, or 1 for one coil
+        int lcs = cell_bytes * 4 <= 72 * 1024 ? 2 : 1;
+        while (lcs > 0 && (1 << (lcs - 1)) >= L) --lcs;
+        const int nch = ceil_div(L, 1 << lcs);
+        const size_t sm = HQS3_MAXPTS * sizeof(int4) + HQS3_MAXPTS * 3 * WW * sizeof(float) +
+                          (size_t)HQS3_MAXPTS * (1 << lcs) * sizeof(float2) + cell_bytes * (1 << lcs);
         HQS_CUDA_TRY(cudaFuncSetAttribute(k_spread3<WW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_spread3<WW><<<dim3(pts.nsub, nch), 256, sm, s>>>(y, pts.pti, pts.ptd, pts.subs, M, G[0], G[1], G[2], L,
-                                                           lc, nch, HQS3_TILE, pts.nb[0], pts.nb[1], (float)beta,
-                                                           unit ? 1 : 0, grid);
+        k_spread3<WW><<<dim3(pts.nsub, nch), HQS3_SPREAD_WARPS * 32, sm, s>>>(
+            y, pts.pti, pts.ptd, pts.subs, M, G[0], G[1], G[2], L, lcs, nch, HQS3_TILE, pts.nb[0], pts.nb[1],
+            (float)beta, unit ? 1 : 0, grid);
         HQS_CUDA_TRY(cudaGetLastError());
         return HQS_OK;
     });
