@@ -14,6 +14,12 @@ iz - nz//2) and trajectory rows k_j = (kx, ky, kz) in radians per voxel:
                    t(d) = Nvox^(-1) sum_j exp(+i k_j . d), d in (-N, N)^3,
                    embedded in a 2N circulant per axis with every d = -N
                    plane set to zero; Khat = FFT_2N(c) is real.
+  preconditioner   the density-compensation preconditioner of Sec. 3.4 on
+                   volumes: T. Chan's optimal circulant of the N^3 Toeplitz
+                   part of F^H F (first column: the wrapped diagonals
+                   averaged, per axis d in {q, q - N} with weights (N - q)/N
+                   and q/N), eigenvalues lam = Re FFT_N(column), and
+                   M^-1 v = IFFT_N(FFT_N(v) s^(-1/2)), s = max(a max(lam, 0) + b, b/4).
 
 Every formula is evaluated as written, axis by axis, with NumPy products as
 the only library steps.
@@ -193,3 +199,31 @@ def normal(x, smaps, Kh) -> np.ndarray:
         w = np.fft.ifftn(Kh * np.fft.fftn(pad))[:nz, :ny, :nx]
         out += np.conj(smaps[l]) * w
     return out
+
+
+# ------------------------------------------------- density preconditioner
+def chan_column(c, shape) -> np.ndarray:
+    """First column (nz, ny, nx) of Chan's optimal circulant for the N^3
+    Toeplitz operator with kernel t (given as the 2N circulant column c)."""
+    nz, ny, nx = shape
+    choices = []
+    for n in (nz, ny, nx):
+        q = np.arange(n)
+        choices.append(((np.mod(q, 2 * n), (n - q) / n), (np.mod(q - n, 2 * n), q / n)))
+    out = np.zeros(shape, dtype=np.complex128)
+    for pz, wz in choices[0]:
+        for py, wy in choices[1]:
+            for px, wx in choices[2]:
+                out += (wz[:, None, None] * wy[None, :, None] * wx[None, None, :]) * c[np.ix_(pz, py, px)]
+    return out
+
+
+def chan_symbol(c, shape) -> np.ndarray:
+    """Eigenvalues of the Chan circulant: Re FFT_N(chan_column)."""
+    return np.fft.fftn(chan_column(c, shape)).real
+
+
+def precond_apply(v, lam, a: float, b: float) -> np.ndarray:
+    """M^-1 v for H = a A^H A + b I on volumes."""
+    s = a * np.maximum(lam, 0.0) + b
+    return np.fft.ifftn(np.fft.fftn(v) / np.sqrt(np.maximum(s, 0.25 * b)))

@@ -9,7 +9,7 @@ import math
 import numpy as np
 import pytest
 
-from oracle import nudft, nufft3d, toeplitz
+from oracle import nudft, nufft3d, solvers, toeplitz
 import synth
 
 
@@ -145,3 +145,66 @@ def test_toeplitz3d_one_slice_is_the_2d_embedding():
     K3 = nufft3d.khat(nufft3d.kernel(traj, (1, ny, nx)))
     K2 = toeplitz.khat(toeplitz.kernel(traj[:, :2], ny, nx))
     assert rel(nufft3d.normal(x[None], S[:, None], K3)[0], toeplitz.normal(x, S, K2)) < 1e-13
+
+
+# ------------------------------------------------- density preconditioner
+def test_chan3d_averages_wrapped_diagonals_of_the_dense_normal_matrix():
+    # T. Chan (1988): the Frobenius-optimal (three-level) circulant has first
+    # column c[q] = mean over m of T[(m + q) mod N, m], T the dense matrix of F^H F.
+    rng = np.random.default_rng(18)
+    shape, M = (2, 3, 4), 17
+    nvox = int(np.prod(shape))
+    traj = rand_traj(rng, M)
+    S = np.ones((1,) + shape)
+    T = np.zeros((nvox, nvox), dtype=np.complex128)
+    for i in range(nvox):
+        e = np.zeros(nvox, dtype=np.complex128)
+        e[i] = 1
+        T[:, i] = nufft3d.nudft_normal(e.reshape(shape), S, traj).ravel()
+    nz, ny, nx = shape
+    want = np.zeros(shape, dtype=np.complex128)
+    for q in np.ndindex(*shape):
+        acc = 0j
+        for m in np.ndindex(*shape):
+            r = [(mm + qq) % n for mm, qq, n in zip(m, q, shape)]
+            acc += T[(r[0] * ny + r[1]) * nx + r[2], (m[0] * ny + m[1]) * nx + m[2]]
+        want[q] = acc / nvox
+    c = nufft3d.kernel(traj, shape)
+    assert rel(nufft3d.chan_column(c, shape), want) < 1e-12
+    assert nufft3d.chan_symbol(c, shape).min() > -1e-12
+
+
+def test_chan3d_one_slice_is_the_2d_symbol():
+    rng = np.random.default_rng(19)
+    ny, nx, M = 6, 8, 60
+    traj = rand_traj(rng, M)
+    lam3 = nufft3d.chan_symbol(nufft3d.kernel(traj, (1, ny, nx)), (1, ny, nx))[0]
+    lam2 = toeplitz.chan_symbol(toeplitz.kernel(traj[:, :2], ny, nx), ny, nx)
+    assert rel(lam3, lam2) < 1e-13
+
+
+def test_chan3d_symbol_is_one_on_full_cartesian_sampling():
+    shape = (4, 6, 8)
+    mz, my, mx = (np.arange(n) - n // 2 for n in shape)
+    MZ, MY, MX = np.meshgrid(mz, my, mx, indexing="ij")
+    traj = np.stack([2 * math.pi * MX.ravel() / shape[2], 2 * math.pi * MY.ravel() / shape[1],
+                     2 * math.pi * MZ.ravel() / shape[0]], 1)
+    lam = nufft3d.chan_symbol(nufft3d.kernel(traj, shape), shape)
+    assert np.max(np.abs(lam - 1.0)) < 1e-12
+    v = rand_c(np.random.default_rng(20), shape)
+    assert rel(nufft3d.precond_apply(v, lam, 2.0, 0.5), v / math.sqrt(2.5)) < 1e-13
+
+
+def test_density_preconditioner_cuts_3d_iterations_on_stacked_spirals():
+    # the design property the preconditioner is chosen for (not a parity pin)
+    c = synth.volume_case(3, (8, 32, 32), 4, 8, 256)
+    K = nufft3d.khat(nufft3d.kernel(c["traj"], c["shape"]))
+    lam = nufft3d.chan_symbol(nufft3d.kernel(c["traj"], c["shape"]), c["shape"])
+    y = nufft3d.nudft_forward(c["x"], c["smaps"], c["traj"])
+    b0 = nufft3d.nudft_adjoint(y, c["smaps"], c["traj"])
+    mu = 1e-2
+    H = lambda v: nufft3d.normal(v, c["smaps"], K) + mu * v
+    z0 = np.zeros(c["shape"])
+    _, i_plain = solvers.pcg(H, b0, z0, None, 300, 1e-4)
+    _, i_dc = solvers.pcg(H, b0, z0, lambda v: nufft3d.precond_apply(v, lam, 1.0, mu), 300, 1e-4)
+    assert i_dc["iters"] < 0.8 * i_plain["iters"], (i_dc["iters"], i_plain["iters"])
