@@ -420,14 +420,25 @@ HQS_API int hqs_adjoint3d(hqs_plan3d plan, const hqs_c64* y, hqs_c64* x, void* s
 HQS_API int hqs_toeplitz_normal3d(hqs_plan3d plan, const hqs_c64* x, hqs_c64* out, void* stream);
 /* Khat (2nz, 2ny, 2nx) float32 = Re FFT_2N(t) / (8 nz ny nx), copied to out (device). */
 HQS_API int hqs_plan3d_get_khat(hqs_plan3d plan, float* out, void* stream);
+/* Density-compensation preconditioner of Sec. 3.4 on volumes: z = M^-1 r =
+ * IFFT_N(FFT_N(r) s^-1/2), s = max(a max(lam, 0) + b, b/4), lam the
+ * eigenvalues of T. Chan's optimal circulant of the N^3 Toeplitz part of
+ * A^H A / S (built with the plan).  b > 0.  HQS_ERR_UNSUPPORTED unless each
+ * of nz, ny, nx is also a transform size (16, 32, 64, 128). */
+HQS_API int hqs_precond_apply3d(hqs_plan3d plan, float a, float b, const hqs_c64* r, hqs_c64* z,
+                                void* stream);
 /* Data-consistency solve of the HQS step on a volume: CG on
- * (a A^H A + b I) x = rhs, starting from x on entry, fp64 inner products,
- * stopping at ||r|| <= rel_tol ||rhs|| or after max_iter (<= HQS_MAX_ITERS)
- * iterations; the host checks the residual each iteration (blocking).
- * Returns HQS_OK, HQS_ERR_NOT_CONVERGED or HQS_ERR_BREAKDOWN; info (host,
- * optional) as for hqs_dc_solve.  rhs and x distinct (nz, ny, nx). */
+ * (a A^H A + b I) x = rhs (precond HQS_PRECOND_NONE) or PCG with the
+ * density preconditioner above (HQS_PRECOND_DC), starting from x on entry,
+ * fp64 inner products, stopping at ||r|| <= rel_tol ||rhs|| or after
+ * max_iter (<= HQS_MAX_ITERS) iterations; the host checks the residual each
+ * iteration (blocking).  Returns HQS_OK, HQS_ERR_NOT_CONVERGED or
+ * HQS_ERR_BREAKDOWN (HQS_ERR_UNSUPPORTED for HQS_PRECOND_DC where
+ * hqs_precond_apply3d is); info (host, optional) as for hqs_dc_solve.
+ * rhs and x distinct (nz, ny, nx). */
 HQS_API int hqs_dc_solve3d(hqs_plan3d plan, float a, float b, const hqs_c64* rhs, hqs_c64* x,
-                           int max_iter, double rel_tol, hqs_solve_info* info, void* stream);
+                           int max_iter, double rel_tol, int precond, hqs_solve_info* info,
+                           void* stream);
 
 /* Diagnostics (no counterpart in the paper): phase trace of the persistent
  * solve.  enable = 1 allocates a trace buffer on the plan (returns 0); later

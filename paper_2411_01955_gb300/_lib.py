@@ -134,7 +134,8 @@ _SIGS = {
     "hqs_adjoint3d": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "hqs_toeplitz_normal3d": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "hqs_dc_solve3d": (C.c_int, [C.c_void_p, C.c_float, C.c_float, C.c_void_p, C.c_void_p, C.c_int,
-                                 C.c_double, C.POINTER(SolveInfo), C.c_void_p]),
+                                 C.c_double, C.c_int, C.POINTER(SolveInfo), C.c_void_p]),
+    "hqs_precond_apply3d": (C.c_int, [C.c_void_p, C.c_float, C.c_float, C.c_void_p, C.c_void_p, C.c_void_p]),
 }
 
 
@@ -650,12 +651,19 @@ def plan3d_khat(plan: Plan3d, out, stream=None):
     return out
 
 
-def dc_solve3d(plan: Plan3d, a, b, rhs, x, max_iter=30, rel_tol=1e-4, stream=None, check=True) -> SolveInfo:
-    """Solves (a A^H A + b I) x = rhs in place (CG, blocking); returns SolveInfo."""
+def precond_apply3d(plan: Plan3d, a, b, r, z, stream=None):
+    _check(library().hqs_precond_apply3d(plan.handle, float(a), float(b), _ptr(r, torch.complex64, "r"),
+                                         _ptr(z, torch.complex64, "z"), _stream(stream)), "hqs_precond_apply3d")
+    return z
+
+
+def dc_solve3d(plan: Plan3d, a, b, rhs, x, max_iter=30, rel_tol=1e-4, precond=HQS_PRECOND_DC, stream=None,
+               check=True) -> SolveInfo:
+    """Solves (a A^H A + b I) x = rhs in place (PCG, blocking); returns SolveInfo."""
     info = SolveInfo()
     rc = library().hqs_dc_solve3d(plan.handle, float(a), float(b), _ptr(rhs, torch.complex64, "rhs"),
-                                  _ptr(x, torch.complex64, "x"), int(max_iter), float(rel_tol), C.byref(info),
-                                  _stream(stream))
+                                  _ptr(x, torch.complex64, "x"), int(max_iter), float(rel_tol), int(precond),
+                                  C.byref(info), _stream(stream))
     if check and rc not in (HQS_OK, HQS_ERR_NOT_CONVERGED):
         raise HqsError(rc, "hqs_dc_solve3d")
     info.rc = rc

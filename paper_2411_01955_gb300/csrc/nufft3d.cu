@@ -36,7 +36,7 @@ using namespace hqs;
 #define HQS3_KERNEL_W 8       // KB width used to grid the Toeplitz kernel
 
 struct Cg3 {
-    double rr, pq, alpha, beta, bnorm2, tol2;
+    double rr, rz, pq, alpha, beta, bnorm2, tol2;
     int it, done, status, max_iter;
 };
 
@@ -57,14 +57,17 @@ struct hqs_plan3d_s {
     int4* subs = nullptr;     // (bin, start, count, 0)
     float* khat = nullptr;    // [2nz][2ny][2nx], includes 1 / (8 Nvox)
     float2* tw = nullptr;     // twiddle bank
-    int tw_sizes[6] = {0, 0, 0, 0, 0, 0};
-    int tw_offs[6] = {0, 0, 0, 0, 0, 0};
+    int tw_sizes[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    int tw_offs[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    bool pc_ok = false;       // every axis has an n-point transform: DC preconditioner available
+    float* lam = nullptr;     // [nz][ny][nx] Chan symbol of the density preconditioner
     float2* bufA = nullptr;   // 8 Nvox L
     float2* bufB = nullptr;   // 4 Nvox L
     float2* bufC = nullptr;   // Nvox L
     float2* cg_r = nullptr;
     float2* cg_p = nullptr;
     float2* cg_q = nullptr;
+    float2* cg_z = nullptr;
     double* partials = nullptr;
     Cg3* cg = nullptr;
     Cg3* h_cg = nullptr;
@@ -388,6 +391,18 @@ struct MidKhat {
     }
 };
 
+// density-preconditioner multiply s^-1/2 / Nvox between the forward and
+// inverse z transforms of a single volume: b = ky*nx + kx
+struct MidPrecond {
+    const float* lam;
+    int64_t plane;   // ny * nx
+    float a, b, inv_nvox;
+    HQS_DEV float2 operator()(int64_t, int64_t bb, int p, float2 v) const {
+        const float sv = fmaxf(fmaf(a, fmaxf(lam[(int64_t)p * plane + bb], 0.f), b), 0.25f * b);
+        return cscale(v, rsqrtf(sv) * inv_nvox);
+    }
+};
+
 template <int N> constexpr size_t pass_smem() { return ((size_t)N * kLines + N) * sizeof(float2); }
 
 // One FFT pass over `nlines` lines (a = line / B, b = line % B), kLines per
@@ -425,7 +440,7 @@ __global__ void k_pass3(LD ld, ST st, MID mid, int64_t nlines, int64_t B, const 
 template <class F> int dispatch3(int n, F&& f) { return dispatch_fft_size(n, std::forward<F>(f)); }
 
 const float2* tw3(const hqs_plan3d_s* p, int N) {
-    for (int i = 0; i < 6; ++i)
+    for (int i = 0; i < 9; ++i)
         if (p->tw_sizes[i] == N) return p->tw + p->tw_offs[i];
     return nullptr;
 }
@@ -489,6 +504,36 @@ __global__ void k_kernel_deapod(float2* __restrict__ c, int Tx, int Ty, int Tz, 
     }
 }
 
+// Chan circulant column of the N^3 Toeplitz part (per axis d in {q, q - N},
+// weights (N - q)/N and q/N) from the 2N circulant column c.
+__global__ void k_chan3(const float2* __restrict__ c, int nx, int ny, int nz, float2* __restrict__ out) {
+    const int64_t total = (int64_t)nx * ny * nz;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int qx = (int)(e % nx);
+        const int64_t r = e / nx;
+        const int qy = (int)(r % ny), qz = (int)(r / ny);
+        float2 acc = make_float2(0.f, 0.f);
+        for (int sz = 0; sz < 2; ++sz) {
+            const int pz = sz ? qz + nz : qz;
+            const float wz = sz ? (float)qz / nz : (float)(nz - qz) / nz;
+            for (int sy = 0; sy < 2; ++sy) {
+                const int py = sy ? qy + ny : qy;
+                const float wy = sy ? (float)qy / ny : (float)(ny - qy) / ny;
+                for (int sx = 0; sx < 2; ++sx) {
+                    const int px = sx ? qx + nx : qx;
+                    const float wx = sx ? (float)qx / nx : (float)(nx - qx) / nx;
+                    const float2 v = c[((int64_t)pz * 2 * ny + py) * 2 * nx + px];
+                    const float w = wz * wy * wx;
+                    acc.x = fmaf(w, v.x, acc.x);
+                    acc.y = fmaf(w, v.y, acc.y);
+                }
+            }
+        }
+        out[e] = acc;
+    }
+}
+
 __global__ void k_real_part3(const float2* __restrict__ in, float* __restrict__ out, int64_t count, float s) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
          e += (int64_t)gridDim.x * blockDim.x)
@@ -497,7 +542,7 @@ __global__ void k_real_part3(const float2* __restrict__ in, float* __restrict__ 
 
 // ------------------------------------------------------------ CG kernels
 #define CG3_BLOCKS 1024
-enum { CG3_INIT = 0, CG3_ALPHA = 1, CG3_BETA = 2 };
+enum { CG3_INIT = 0, CG3_ALPHA = 1, CG3_RES = 2, CG3_RZ = 3, CG3_RZ_RR = 4 };
 
 HQS_DEV double block_sum(double v, double* sh) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -524,17 +569,16 @@ __global__ void k_dot3(const float2* __restrict__ a, const float2* __restrict__ 
     if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
-// r = rhs - q (q optional), p = r; partials: <r, r> (slot 0) and <rhs, rhs> (slot 1)
+// r = rhs - q; partials: <r, r> (slot 0) and <rhs, rhs> (slot 1)
 __global__ void k_cg3_init(const float2* __restrict__ rhs, const float2* __restrict__ q, float2* __restrict__ r,
-                           float2* __restrict__ p, int64_t count, double* __restrict__ part) {
+                           int64_t count, double* __restrict__ part) {
     __shared__ double sh[32];
     double rr = 0.0, bb = 0.0;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
          e += (int64_t)gridDim.x * blockDim.x) {
         const float2 b = rhs[e];
-        const float2 v = q ? csub(b, q[e]) : b;
+        const float2 v = csub(b, q[e]);
         r[e] = v;
-        p[e] = v;
         rr += (double)v.x * v.x + (double)v.y * v.y;
         bb += (double)b.x * b.x + (double)b.y * b.y;
     }
@@ -546,11 +590,18 @@ __global__ void k_cg3_init(const float2* __restrict__ rhs, const float2* __restr
     }
 }
 
+// CG scalars from fixed-order sums of the per-block partials:
+//   INIT  rr, ||rhs||^2, tolerance, done if converged at the start
+//   ALPHA alpha = rz / <p, q> (breakdown if <p, q> <= 0)
+//   RES   one more iteration: rr, history, convergence / iteration limit
+//   RZ    rz = <r, z>, beta = rz_new / rz_old (after the first)
+//   RZ_RR the same with z = r (no preconditioner): rz = rr
 __global__ void k_cg3_scalar(Cg3* cg, const double* __restrict__ part, int nparts, int mode, double* hist,
                              double rel_tol, int max_iter) {
     if (threadIdx.x != 0) return;
     double s = 0.0;
-    for (int i = 0; i < nparts; ++i) s += part[i];
+    if (mode != CG3_RZ_RR)
+        for (int i = 0; i < nparts; ++i) s += part[i];
     if (mode == CG3_INIT) {
         double bb = 0.0;
         for (int i = 0; i < nparts; ++i) bb += part[CG3_BLOCKS + i];
@@ -560,6 +611,7 @@ __global__ void k_cg3_scalar(Cg3* cg, const double* __restrict__ part, int npart
         cg->it = 0;
         cg->max_iter = max_iter;
         cg->status = HQS_OK;
+        cg->beta = 0.0;
         cg->done = (bb == 0.0 || s <= cg->tol2) ? 1 : 0;
         if (!cg->done && max_iter <= 0) {
             cg->done = 1;
@@ -577,10 +629,9 @@ __global__ void k_cg3_scalar(Cg3* cg, const double* __restrict__ part, int npart
             cg->alpha = 0.0;
             return;
         }
-        cg->alpha = cg->rr / s;
-    } else {
+        cg->alpha = cg->rz / s;
+    } else if (mode == CG3_RES) {
         cg->it += 1;
-        cg->beta = s / cg->rr;
         cg->rr = s;
         if (cg->it <= HQS_MAX_ITERS) hist[cg->it] = s;
         if (!isfinite(s)) {
@@ -592,6 +643,15 @@ __global__ void k_cg3_scalar(Cg3* cg, const double* __restrict__ part, int npart
             cg->done = 1;
             cg->status = HQS_ERR_NOT_CONVERGED;
         }
+    } else {
+        const double rz = mode == CG3_RZ_RR ? cg->rr : s;
+        if (!(rz > 0.0) || !isfinite(rz)) {
+            cg->done = 1;
+            cg->status = HQS_ERR_BREAKDOWN;
+            return;
+        }
+        cg->beta = cg->it > 0 ? rz / cg->rz : 0.0;
+        cg->rz = rz;
     }
 }
 
@@ -621,15 +681,21 @@ __global__ void k_cg3_update(float2* __restrict__ x, float2* __restrict__ r, con
     if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
-// p = r + beta p (after the BETA scalar step; skipped once done)
-__global__ void k_cg3_pupdate(float2* __restrict__ p, const float2* __restrict__ r, int64_t count,
+// p = z (first) or z + beta p; skipped once done
+__global__ void k_cg3_pupdate(float2* __restrict__ p, const float2* __restrict__ z, int64_t count,
                               const Cg3* __restrict__ cg) {
     if (cg->done) return;
+    const bool first = cg->it == 0;
     const float be = (float)cg->beta;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
          e += (int64_t)gridDim.x * blockDim.x) {
-        const float2 rv = r[e], pv = p[e];
-        p[e] = make_float2(fmaf(be, pv.x, rv.x), fmaf(be, pv.y, rv.y));
+        const float2 zv = z[e];
+        if (first) {
+            p[e] = zv;
+        } else {
+            const float2 pv = p[e];
+            p[e] = make_float2(fmaf(be, pv.x, zv.x), fmaf(be, pv.y, zv.y));
+        }
     }
 }
 
@@ -880,6 +946,46 @@ int toep3(hqs_plan3d_s* p, const float2* x, float2* out, float ca, float cb, con
     return HQS_OK;
 }
 
+// Chan symbol of the density preconditioner from the 2N circulant column c:
+// column on the N grid, FFT_N (x, y, z in place), real part.
+int build_lambda(hqs_plan3d_s* p, const float2* c, cudaStream_t s) {
+    const int nx = p->n[0], ny = p->n[1], nz = p->n[2];
+    const int64_t nvox = (int64_t)nx * ny * nz;
+    float2* col = p->cg_z;   // scratch volume (free until the first solve)
+    k_chan3<<<vec_blocks(nvox), 256, 0, s>>>(c, nx, ny, nz, col);
+    HQS_CUDA_TRY(cudaGetLastError());
+    const int64_t plane = (int64_t)ny * nx;
+    TRY3((run_pass<false, false, false>(p, nx, LdLine{col, {nx, 1}, nx}, StLine{col, {nx, 1}, nx, 0, nx},
+                                        (int64_t)nz * ny, 1, s)));
+    TRY3((run_pass<false, false, false>(p, ny, LdLine{col, {plane, nx}, ny}, StLine{col, {plane, nx}, ny, 0, ny},
+                                        (int64_t)nz * nx, nx, s)));
+    TRY3((run_pass<false, false, false>(p, nz, LdLine{col, {0, plane}, nz}, StLine{col, {0, plane}, nz, 0, nz},
+                                        plane, plane, s)));
+    k_real_part3<<<vec_blocks(nvox), 256, 0, s>>>(col, p->lam, nvox, 1.f);
+    HQS_CUDA_TRY(cudaGetLastError());
+    return HQS_OK;
+}
+
+// z = M^-1 r = IFFT_N(FFT_N(r) s^-1/2) for H = a A^H A + b I: x transform
+// into z, then y, z (with the symbol multiply and the inverse z), inverse y,
+// inverse x in place.
+int precond3(hqs_plan3d_s* p, float a, float b, const float2* r, float2* z, cudaStream_t s) {
+    const int nx = p->n[0], ny = p->n[1], nz = p->n[2];
+    const int64_t plane = (int64_t)ny * nx;
+    const int64_t nvox = plane * nz;
+    TRY3((run_pass<false, false, false>(p, nx, LdLine{r, {nx, 1}, nx}, StLine{z, {nx, 1}, nx, 0, nx},
+                                        (int64_t)nz * ny, 1, s)));
+    TRY3((run_pass<false, false, false>(p, ny, LdLine{z, {plane, nx}, ny}, StLine{z, {plane, nx}, ny, 0, ny},
+                                        (int64_t)nz * nx, nx, s)));
+    TRY3((run_pass<true, false, false>(p, nz, LdLine{z, {0, plane}, nz}, StLine{z, {0, plane}, nz, 0, nz}, plane,
+                                       plane, s, MidPrecond{p->lam, plane, a, b, (float)(1.0 / (double)nvox)})));
+    TRY3((run_pass<true, false, false>(p, ny, LdLine{z, {plane, nx}, ny}, StLine{z, {plane, nx}, ny, 0, ny},
+                                       (int64_t)nz * nx, nx, s)));
+    TRY3((run_pass<true, false, false>(p, nx, LdLine{z, {nx, 1}, nx}, StLine{z, {nx, 1}, nx, 0, nx},
+                                       (int64_t)nz * ny, 1, s)));
+    return HQS_OK;
+}
+
 // Khat from the gridded kernel: unit data spread on the 4N grid (width 8),
 // inverse transforms cropped to the 2N circulant, deapodised, FFT_2N.
 int build_khat(hqs_plan3d_s* p, const float* traj, cudaStream_t s) {
@@ -942,6 +1048,7 @@ int build_khat(hqs_plan3d_s* p, const float* traj, cudaStream_t s) {
         const double nvox = (double)p->n[0] * p->n[1] * p->n[2];
         k_kernel_deapod<<<vec_blocks(t3), 256, 0, s>>>(mid, T[0], T[1], T[2], ap[0], ap[1], ap[2],
                                                         (float)(1.0 / nvox));
+        if (p->pc_ok && (rc = build_lambda(p, mid, s)) != HQS_OK) break;
         // forward FFT of the circulant column, in place (x, y, z)
         const int64_t rowT = T[0], planeT = (int64_t)T[1] * T[0];
         if ((rc = run_pass<false, false, false>(p, T[0], LdLine{mid, {rowT, 1}, T[0]}, StLine{mid, {rowT, 1}, T[0], 0, T[0]},
@@ -974,6 +1081,9 @@ int plan3d_build(hqs_plan3d_s* p, const float* traj, const float2* smaps_user, c
     TRY3(alloc3(p, &p->cg_r, (size_t)nvox));
     TRY3(alloc3(p, &p->cg_p, (size_t)nvox));
     TRY3(alloc3(p, &p->cg_q, (size_t)nvox));
+    TRY3(alloc3(p, &p->cg_z, (size_t)nvox));
+    p->pc_ok = fft_size_supported(nx) && fft_size_supported(ny) && fft_size_supported(nz);
+    if (p->pc_ok) TRY3(alloc3(p, &p->lam, (size_t)nvox));
     TRY3(alloc3(p, &p->partials, (size_t)2 * CG3_BLOCKS));
     TRY3(alloc3(p, &p->cg, 1));
     TRY3(alloc3(p, &p->hist, HQS_MAX_ITERS + 1));
@@ -982,8 +1092,9 @@ int plan3d_build(hqs_plan3d_s* p, const float* traj, const float2* smaps_user, c
     {
         int ns = 0, total = 0;
         for (int a = 0; a < 3; ++a)
-            for (int m = 2; m <= 4; m += 2) {
+            for (int m = 1; m <= 4; m *= 2) {
                 const int N = m * p->n[a];
+                if (!fft_size_supported(N)) continue;
                 bool seen = false;
                 for (int k = 0; k < ns; ++k) seen |= p->tw_sizes[k] == N;
                 if (!seen) {
@@ -1089,21 +1200,45 @@ extern "C" int hqs_toeplitz_normal3d(hqs_plan3d p, const hqs_c64* x, hqs_c64* ou
                  (cudaStream_t)stream);
 }
 
+extern "C" int hqs_precond_apply3d(hqs_plan3d p, float a, float b, const hqs_c64* r, hqs_c64* z, void* stream) {
+    if (!p || !r || !z || !(b > 0.f)) return HQS_ERR_INVALID_ARG;
+    if (!p->pc_ok) return HQS_ERR_UNSUPPORTED;
+    return precond3(p, a, b, reinterpret_cast<const float2*>(r), reinterpret_cast<float2*>(z), (cudaStream_t)stream);
+}
+
 extern "C" int hqs_dc_solve3d(hqs_plan3d p, float a, float b, const hqs_c64* rhs_c, hqs_c64* x_c, int max_iter,
-                              double rel_tol, hqs_solve_info* info, void* stream) {
+                              double rel_tol, int precond, hqs_solve_info* info, void* stream) {
     if (!p || !rhs_c || !x_c || max_iter < 0 || max_iter > HQS_MAX_ITERS || !(rel_tol >= 0.0) ||
         reinterpret_cast<const void*>(rhs_c) == reinterpret_cast<const void*>(x_c))
         return HQS_ERR_INVALID_ARG;
+    if (precond != HQS_PRECOND_NONE && precond != HQS_PRECOND_DC) return HQS_ERR_INVALID_ARG;
+    const bool dc = precond == HQS_PRECOND_DC;
+    if (dc && (!p->pc_ok || !(b > 0.f))) return dc && !p->pc_ok ? HQS_ERR_UNSUPPORTED : HQS_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const float2* rhs = reinterpret_cast<const float2*>(rhs_c);
     float2* x = reinterpret_cast<float2*>(x_c);
     const int64_t nvox = (int64_t)p->n[0] * p->n[1] * p->n[2];
     const int nb = vec_blocks(nvox);
-    // q = H x for the initial residual
+    const float2* zsrc = dc ? p->cg_z : p->cg_r;
+    // z = M^-1 r (or r), rz = <r, z>, beta; p = z + beta p
+    auto precond_step = [&]() -> int {
+        if (dc) {
+            TRY3(precond3(p, a, b, p->cg_r, p->cg_z, s));
+            k_dot3<<<nb, 256, 0, s>>>(p->cg_r, p->cg_z, nvox, p->partials);
+            k_cg3_scalar<<<1, 32, 0, s>>>(p->cg, p->partials, nb, CG3_RZ, p->hist, rel_tol, max_iter);
+        } else {
+            k_cg3_scalar<<<1, 32, 0, s>>>(p->cg, p->partials, nb, CG3_RZ_RR, p->hist, rel_tol, max_iter);
+        }
+        k_cg3_pupdate<<<nb, 256, 0, s>>>(p->cg_p, zsrc, nvox, p->cg);
+        HQS_CUDA_TRY(cudaGetLastError());
+        return HQS_OK;
+    };
+    // r = rhs - H x
     TRY3(toep3(p, x, p->cg_q, a, b, x, s));
-    k_cg3_init<<<nb, 256, 0, s>>>(rhs, p->cg_q, p->cg_r, p->cg_p, nvox, p->partials);
+    k_cg3_init<<<nb, 256, 0, s>>>(rhs, p->cg_q, p->cg_r, nvox, p->partials);
     k_cg3_scalar<<<1, 32, 0, s>>>(p->cg, p->partials, nb, CG3_INIT, p->hist, rel_tol, max_iter);
     HQS_CUDA_TRY(cudaGetLastError());
+    TRY3(precond_step());
     for (int it = 0; it < max_iter; ++it) {
         HQS_CUDA_TRY(cudaMemcpyAsync(p->h_cg, p->cg, sizeof(Cg3), cudaMemcpyDeviceToHost, s));
         HQS_CUDA_TRY(cudaStreamSynchronize(s));
@@ -1112,9 +1247,9 @@ extern "C" int hqs_dc_solve3d(hqs_plan3d p, float a, float b, const hqs_c64* rhs
         k_dot3<<<nb, 256, 0, s>>>(p->cg_p, p->cg_q, nvox, p->partials);
         k_cg3_scalar<<<1, 32, 0, s>>>(p->cg, p->partials, nb, CG3_ALPHA, p->hist, rel_tol, max_iter);
         k_cg3_update<<<nb, 256, 0, s>>>(x, p->cg_r, p->cg_p, p->cg_q, nvox, p->cg, p->partials);
-        k_cg3_scalar<<<1, 32, 0, s>>>(p->cg, p->partials, nb, CG3_BETA, p->hist, rel_tol, max_iter);
-        k_cg3_pupdate<<<nb, 256, 0, s>>>(p->cg_p, p->cg_r, nvox, p->cg);
+        k_cg3_scalar<<<1, 32, 0, s>>>(p->cg, p->partials, nb, CG3_RES, p->hist, rel_tol, max_iter);
         HQS_CUDA_TRY(cudaGetLastError());
+        TRY3(precond_step());
     }
     HQS_CUDA_TRY(cudaMemcpyAsync(p->h_cg, p->cg, sizeof(Cg3), cudaMemcpyDeviceToHost, s));
     HQS_CUDA_TRY(cudaStreamSynchronize(s));

@@ -116,7 +116,8 @@ def test_dc_solve_3d_matches_oracle_cg():
     H = lambda v: nufft3d.normal(v, c["smaps"], K) + mu * v
     xo, io = solvers.pcg(H, rhs, np.zeros_like(rhs), max_iter=200, tol=1e-4)
     x = torch.zeros(c["shape"], dtype=torch.complex64, device="cuda")
-    info = hq().dc_solve3d(plan, 1.0, mu, to_dev(rhs), x, max_iter=200, rel_tol=1e-4)
+    info = hq().dc_solve3d(plan, 1.0, mu, to_dev(rhs), x, max_iter=200, rel_tol=1e-4,
+                           precond=hq().HQS_PRECOND_NONE)
     got = to_host(x)
     true_res = float(np.linalg.norm(rhs - H(got)) / np.linalg.norm(rhs))
     print(f"3D DC solve: {info.iterations} iterations (oracle {io['iters']}), recursion {info.rel_residual:.2e}, "
@@ -133,9 +134,61 @@ def test_dc_solve_3d_zero_rhs_and_start_at_solution():
     c = CASES["aniso"]()
     plan, _, _ = plan_of(c)
     x = torch.full(c["shape"], 1 + 1j, dtype=torch.complex64, device="cuda")
-    info = hq().dc_solve3d(plan, 1.0, 1e-2, torch.zeros_like(x), x, max_iter=10, rel_tol=1e-4)
+    info = hq().dc_solve3d(plan, 1.0, 1e-2, torch.zeros_like(x), x, max_iter=10, rel_tol=1e-4,
+                           precond=hq().HQS_PRECOND_NONE)
     assert info.rc == hq().HQS_OK and info.iterations == 0
     assert float(x.abs().max()) == 0.0
+    # nz = 8 has no 8-point transform: the density preconditioner is refused, not approximated
+    with pytest.raises(hq().HqsError) as e:
+        hq().dc_solve3d(plan, 1.0, 1e-2, torch.ones_like(x), x, max_iter=10, rel_tol=1e-4)
+    assert e.value.status == hq().HQS_ERR_UNSUPPORTED
+
+
+def pc_case():
+    # every axis a transform size (16, 32, 32), 4 coils, 16 planes of 8 x 256 samples
+    return q(synth.volume_case(4, (16, 32, 32), 4, 8, 256))
+
+
+def test_precond_3d_matches_oracle():
+    c = CASES["cube32"]()
+    plan, _, _ = plan_of(c)
+    lam = nufft3d.chan_symbol(nufft3d.kernel(c["traj"], c["shape"]), c["shape"])
+    r = synth.complex_noise(8, c["shape"]).astype(np.complex64).astype(np.complex128)
+    z = torch.empty(c["shape"], dtype=torch.complex64, device="cuda")
+    for a, b in ((1.0, 1e-2), (2.0, 0.5)):
+        hq().precond_apply3d(plan, a, b, to_dev(r), z)
+        e = rel(to_host(z), nufft3d.precond_apply(r, lam, a, b))
+        print(f"precond a={a} b={b}: {e:.2e}")
+        assert e <= 1e-5
+
+
+def test_dc_solve_3d_density_preconditioned_matches_oracle_pcg():
+    c = pc_case()
+    plan, _, _ = plan_of(c)
+    mu = 1e-2
+    kern = nufft3d.kernel(c["traj"], c["shape"])
+    K = nufft3d.khat(kern)
+    lam = nufft3d.chan_symbol(kern, c["shape"])
+    y = nufft3d.forward(c["x"], c["smaps"], c["traj"], c["W"], c["sigma"])
+    rhs = nufft3d.adjoint(y, c["smaps"], c["traj"], c["W"], c["sigma"])
+    rhs = rhs.astype(np.complex64).astype(np.complex128)
+    H = lambda v: nufft3d.normal(v, c["smaps"], K) + mu * v
+    z0 = np.zeros_like(rhs)
+    xo, io = solvers.pcg(H, rhs, z0, lambda v: nufft3d.precond_apply(v, lam, 1.0, mu), 200, 1e-4)
+    _, ip = solvers.pcg(H, rhs, z0, None, 200, 1e-4)
+    x = torch.zeros(c["shape"], dtype=torch.complex64, device="cuda")
+    info = hq().dc_solve3d(plan, 1.0, mu, to_dev(rhs), x, max_iter=200, rel_tol=1e-4)
+    got = to_host(x)
+    xp = torch.zeros_like(x)
+    plain = hq().dc_solve3d(plan, 1.0, mu, to_dev(rhs), xp, max_iter=200, rel_tol=1e-4,
+                            precond=hq().HQS_PRECOND_NONE)
+    true_res = float(np.linalg.norm(rhs - H(got)) / np.linalg.norm(rhs))
+    print(f"3D DC-PCG: {info.iterations} iterations (oracle {io['iters']}; plain CG {plain.iterations}, "
+          f"oracle {ip['iters']}), true residual {true_res:.2e}")
+    assert info.rc == hq().HQS_OK and info.rel_residual <= 1e-4 and true_res <= 2e-4
+    assert abs(info.iterations - io["iters"]) <= max(2, io["iters"] // 10)
+    assert abs(plain.iterations - ip["iters"]) <= max(2, ip["iters"] // 10)
+    assert info.iterations < plain.iterations
 
 
 def test_volume_edge_cases():
