@@ -13,6 +13,7 @@
 #pragma once
 
 #include <type_traits>
+#include <utility>
 
 #include "common.cuh"
 
@@ -108,6 +109,42 @@ template <bool INV> struct Dft<8, INV> {
         v[6] = csub(e[2], o2);
         v[3] = cadd(e[3], o3);
         v[7] = csub(e[3], o3);
+    }
+};
+
+// Radix 16 as 4 x 4 with twiddles: n = n1 + 4 n2, k = k1 + 4 k2,
+// X[k1 + 4 k2] = sum_n1 w4^(n1 k2) w16^(n1 k1) sum_n2 w4^(n2 k1) x[n1 + 4 n2].
+template <bool INV> struct Dft<16, INV> {
+    HQS_DEV static float2 tw(float2 v, float c, float s) {   // v * exp(-+ i theta), (c, s) = (cos, sin) theta
+        const float sn = INV ? s : -s;
+        return make_float2(v.x * c - v.y * sn, v.x * sn + v.y * c);
+    }
+    HQS_DEV static void run(float2* v) {
+        const float c1 = 0.92387953251128675613f, s1 = 0.38268343236508977173f;
+        float2 y[4][4];
+#pragma unroll
+        for (int n1 = 0; n1 < 4; ++n1) {
+            float2 t[4] = {v[n1], v[n1 + 4], v[n1 + 8], v[n1 + 12]};
+            Dft<4, INV>::run(t);
+#pragma unroll
+            for (int k1 = 0; k1 < 4; ++k1) y[n1][k1] = t[k1];
+        }
+        y[1][1] = tw(y[1][1], c1, s1);
+        y[1][2] = tw(y[1][2], kSqrtHalf, kSqrtHalf);
+        y[1][3] = tw(y[1][3], s1, c1);
+        y[2][1] = tw(y[2][1], kSqrtHalf, kSqrtHalf);
+        y[2][2] = mul_mi<INV>(y[2][2]);
+        y[2][3] = tw(y[2][3], -kSqrtHalf, kSqrtHalf);
+        y[3][1] = tw(y[3][1], s1, c1);
+        y[3][2] = tw(y[3][2], -kSqrtHalf, kSqrtHalf);
+        y[3][3] = tw(y[3][3], -c1, -s1);
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) {
+            float2 t[4] = {y[0][k1], y[1][k1], y[2][k1], y[3][k1]};
+            Dft<4, INV>::run(t);
+#pragma unroll
+            for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = t[k2];
+        }
     }
 };
 
@@ -396,6 +433,30 @@ HQS_FFT_SIZE(640, 40, ST(8, 1) ST(8, 8) ST(10, 64))
 HQS_FFT_SIZE(768, 24, ST(8, 1) ST(8, 8) ST(12, 64))
 #undef NN_
 #undef E_
+// Two-stage factorisations for the volume passes (fewer shared-memory round
+// trips per transform, more elements per thread); other sizes as above.
+template <int N> struct FftSizeV : FftSize<N> {};
+#define HQS_FFT_SIZE_V(NN, EE, ...)                                                   \
+    template <> struct FftSizeV<NN> {                                                 \
+        static constexpr int E = EE;                                                  \
+        static constexpr int TPL = NN / EE;                                           \
+        template <bool INV, bool ZIN, bool HOUT, class LD, class XF, class STF>       \
+        HQS_DEV static void run_io(float2* s, int t, bool act, const float2* tw, LD& ld, \
+                                   XF& xf, STF& stf) {                                \
+            __VA_ARGS__                                                               \
+        }                                                                             \
+    };
+#define NN_ 128
+#define E_ 16
+HQS_FFT_SIZE_V(128, 16, ST(8, 1) ST(16, 8))
+#undef NN_
+#undef E_
+#define NN_ 256
+#define E_ 16
+HQS_FFT_SIZE_V(256, 16, ST(16, 1) ST(16, 16))
+#undef NN_
+#undef E_
+#undef HQS_FFT_SIZE_V
 #undef ST
 #undef HQS_FFT_SIZE
 
@@ -430,9 +491,9 @@ HQS_DEV void block_fft(float2* s, int nlines, const float2* tw) {
 // shared memory, stf(line, pos, v) takes them instead of shared memory.  With
 // a loader the caller need not synchronise before (nothing is read from
 // shared memory); with a store hook the routine ends without a barrier.
-template <int N, bool INV, bool ZIN, bool HOUT, class LD, class XF, class STF>
-HQS_DEV void block_fft_io(float2* s, int nlines, const float2* tw, LD&& ld, XF&& xf, STF&& stf) {
-    constexpr int TPL = FftSize<N>::TPL;
+template <template <int> class TAB, int N, bool INV, bool ZIN, bool HOUT, class LD, class XF, class STF>
+HQS_DEV void block_fft_io_tab(float2* s, int nlines, const float2* tw, LD&& ld, XF&& xf, STF&& stf) {
+    constexpr int TPL = TAB<N>::TPL;
     const int lpg = blockDim.x / TPL;
     int tid;
     asm volatile("mov.u32 %0, %%tid.x;" : "=r"(tid));
@@ -452,7 +513,13 @@ HQS_DEV void block_fft_io(float2* s, int nlines, const float2* tw, LD&& ld, XF&&
         if constexpr (std::is_same_v<std::decay_t<STF>, NoIO>) return NoIO{};
         else return [&, line](int pos, float2 v) { stf(line, pos, v); };
     }();
-    FftSize<N>::template run_io<INV, ZIN, HOUT>(s + line, act ? t : 0, act, tw, bind_ld, bind_xf, bind_st);
+    TAB<N>::template run_io<INV, ZIN, HOUT>(s + line, act ? t : 0, act, tw, bind_ld, bind_xf, bind_st);
+}
+
+template <int N, bool INV, bool ZIN, bool HOUT, class LD, class XF, class STF>
+HQS_DEV void block_fft_io(float2* s, int nlines, const float2* tw, LD&& ld, XF&& xf, STF&& stf) {
+    block_fft_io_tab<FftSize, N, INV, ZIN, HOUT>(s, nlines, tw, std::forward<LD>(ld), std::forward<XF>(xf),
+                                                 std::forward<STF>(stf));
 }
 
 // Copies the N-point twiddle table into shared memory; the caller's barrier

@@ -349,34 +349,35 @@ struct LdToepX {
     }
 };
 
-// store positions o < count: dst[a*sA + o*sP + b] = line[pos(o)]
-// mode 0: pos = o; mode 1: centred crop (image n = count on grid G);
-// mode 2: circulant crop (count = 2h on grid G)
+// Output of the last stage, position pos of line (a, b): stored at
+// dst[a*sA + o*sP + b] for the output index o of pos, if o < count.
+// mode 0: o = pos; mode 1: centred crop (image n = count on grid G, pos =
+// i - n/2 mod G); mode 2: circulant crop (count = 2h, pos = o or o - 2h mod G).
+HQS_DEV int out_index(int pos, int count, int mode, int G) {
+    if (mode == 0) return pos < count ? pos : -1;
+    const int h = count >> 1;
+    if (mode == 1) return pos < h ? pos + h : (pos >= G - h ? pos - G + h : -1);
+    return pos < h ? pos : (pos >= G - h ? pos - G + 2 * h : -1);
+}
 struct StLine {
     float2* dst;
     Lines g;
     int count, mode, G;
-    HQS_DEV int pos(int o) const {
-        if (mode == 1) return centred_pos(o, count, G);
-        if (mode == 2) return circ_pos(o, count >> 1, G);
-        return o;
-    }
-    HQS_DEV void operator()(int64_t a, int64_t b, int li, int p0, int pst, const float2* s) const {
-        float2* d = dst + a * g.sA + b;
-        for (int o = p0; o < count; o += pst) d[(int64_t)o * g.sP] = s[pos(o) * kLines + li];
+    HQS_DEV void put(int64_t a, int64_t b, int pos, float2 v) const {
+        const int o = out_index(pos, count, mode, G);
+        if (o >= 0) dst[a * g.sA + (int64_t)o * g.sP + b] = v;
     }
 };
-// last pass with coil weighting: P[(a*nx + o)*L + b] = conj(S) * line[pos(o)]
+// last pass with coil weighting: P[(a*nx + o)*L + b] = conj(S) * v
 struct StCoil {
     float2* dst;
     const float2* S;
     int nx, L, centred, G;
-    HQS_DEV void operator()(int64_t a, int64_t b, int li, int p0, int pst, const float2* s) const {
-        for (int o = p0; o < nx; o += pst) {
-            const int p = centred ? centred_pos(o, nx, G) : o;
-            const int64_t e = (a * nx + o) * L + b;
-            dst[e] = cmulc(S[e], s[p * kLines + li]);
-        }
+    HQS_DEV void put(int64_t a, int64_t b, int pos, float2 v) const {
+        const int o = out_index(pos, nx, centred ? 1 : 0, G);
+        if (o < 0) return;
+        const int64_t e = (a * nx + o) * L + b;
+        dst[e] = cmulc(S[e], v);
     }
 };
 
@@ -404,37 +405,35 @@ struct MidPrecond {
 };
 
 template <int N> constexpr size_t pass_smem() { return ((size_t)N * kLines + N) * sizeof(float2); }
+template <int N> constexpr int pass_threads() { return ((kLines * FftSizeV<N>::TPL + 31) / 32) * 32; }
 
 // One FFT pass over `nlines` lines (a = line / B, b = line % B), kLines per
-// CTA: load (ld), transform (INV, ZIN, HOUT as in block_fft), and store (st).
-// With a MID functor the pass is FFT -> mid -> inverse FFT (HOUT applies to
-// the inverse).
+// CTA, with the two-stage volume transforms: the first stage loads through
+// ld (global memory), the last stage stores through st.put (global memory),
+// so shared memory holds only the data between stages.  INV, ZIN, HOUT as in
+// block_fft.  With a MID functor the pass is FFT -> mid (fused into the last
+// forward stage) -> inverse FFT, HOUT applying to the inverse.
 template <int N, bool INV, bool ZIN, bool HOUT, class LD, class ST, class MID>
 __global__ void k_pass3(LD ld, ST st, MID mid, int64_t nlines, int64_t B, const float2* __restrict__ twg) {
     extern __shared__ float2 s[];
     const float2* tw = stage_twiddles<N>(s + N * kLines, twg);
+    constexpr int TPL = FftSizeV<N>::TPL;
     const int64_t l0 = (int64_t)blockIdx.x * kLines;
     const int lines = (int)min((int64_t)kLines, nlines - l0);
-    const int pst = blockDim.x / lines;
-    const int li = threadIdx.x % lines, p0 = threadIdx.x / lines;
-    const int64_t line = l0 + li;
-    const int64_t a = line / B, b = line - a * B;
-    constexpr int NIN = ZIN ? N / 2 : N;
-    if (p0 < pst) {
-        for (int p = p0; p < NIN; p += pst) s[p * kLines + li] = ld(a, b, p);
-    }
-    __syncthreads();
+    const int ll = (int)(threadIdx.x % (blockDim.x / TPL));
+    const int64_t mine = l0 + (ll < lines ? ll : 0);
+    const int64_t a = mine / B, b = mine - a * B;
+    const int64_t a0 = l0 / B, b0 = l0 - a0 * B;
+    // threads without a line read line l0 (in bounds) and store nothing
+    auto load = [&](int, int pos, bool act) { return act ? ld(a, b, pos) : ld(a0, b0, pos); };
+    auto store = [&](int, int pos, float2 v) { st.put(a, b, pos, v); };
     if constexpr (std::is_same_v<MID, NoMid>) {
-        block_fft<N, INV, ZIN, HOUT>(s, lines, tw);
+        block_fft_io_tab<FftSizeV, N, INV, ZIN, HOUT>(s, lines, tw, load, NoIO{}, store);
     } else {
-        block_fft<N, false, ZIN, false>(s, lines, tw);
-        if (p0 < pst) {
-            for (int p = p0; p < N; p += pst) s[p * kLines + li] = mid(a, b, p, s[p * kLines + li]);
-        }
-        __syncthreads();
-        block_fft<N, true, false, HOUT>(s, lines, tw);
+        auto xf = [&](int, int pos, float2 v) { return mid(a, b, pos, v); };
+        block_fft_io_tab<FftSizeV, N, false, ZIN, false>(s, lines, tw, load, xf, NoIO{});
+        block_fft_io_tab<FftSizeV, N, true, false, HOUT>(s, lines, tw, NoIO{}, NoIO{}, store);
     }
-    if (p0 < pst) st(a, b, li, p0, pst, s);
 }
 
 template <class F> int dispatch3(int n, F&& f) { return dispatch_fft_size(n, std::forward<F>(f)); }
@@ -457,7 +456,7 @@ int run_pass(const hqs_plan3d_s* p, int N, LD ld, ST st, int64_t nlines, int64_t
         HQS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         const int64_t nblk = ceil_div64(nlines, kLines);
         if (nblk > 0x7fffffff) return HQS_ERR_INVALID_ARG;
-        kern<<<(unsigned)nblk, fft_threads<NN>(kLines), sm, s>>>(ld, st, mid, nlines, B, tw);
+        kern<<<(unsigned)nblk, pass_threads<NN>(), sm, s>>>(ld, st, mid, nlines, B, tw);
         HQS_CUDA_TRY(cudaGetLastError());
         return HQS_OK;
     });
