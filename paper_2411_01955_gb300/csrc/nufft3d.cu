@@ -24,6 +24,7 @@
 // over b.
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <vector>
 
 #include "fft.cuh"
@@ -72,6 +73,12 @@ struct hqs_plan3d_s {
     Cg3* cg = nullptr;
     Cg3* h_cg = nullptr;
     double* hist = nullptr;
+    const int* stop = nullptr;          // device flag: passes launched while set return at once
+    cudaStream_t cap_stream = nullptr;  // private stream the PCG iteration is captured on
+    cudaGraphExec_t iter_graph = nullptr;
+    float g_a = 0.f, g_b = 0.f;         // what the captured iteration was built for
+    int g_dc = -1;
+    const void* g_x = nullptr;
     size_t bytes = 0;
     std::vector<void*> allocs;
 };
@@ -85,14 +92,6 @@ HQS_DEV float kb_phi3(float t, float W, float beta) {
     return s >= 0.f ? cyl_bessel_i0f(beta * sqrtf(s)) : 0.f;
 }
 HQS_DEV int wrap(int i, int G) { return i < 0 ? i + G : (i >= G ? i - G : i); }
-// grid position of centred image index i (image size n on grid G)
-HQS_DEV int centred_pos(int i, int n, int G) {
-    const int c = i - (n >> 1);
-    return c >= 0 ? c : c + G;
-}
-// grid position of circulant index p in [0, 2h) (offset d = p or p - 2h) on grid G
-HQS_DEV int circ_pos(int p, int h, int G) { return p < h ? p : p - 2 * h + G; }
-
 // ------------------------------------------------------------ point setup
 __global__ void k_points3(const float* __restrict__ traj, int M, int Gx, int Gy, int Gz, int W, int TB,
                           int nbx, int nby, int4* __restrict__ rawi, float4* __restrict__ rawd,
@@ -414,7 +413,9 @@ template <int N> constexpr int pass_threads() { return ((kLines * FftSizeV<N>::T
 // block_fft.  With a MID functor the pass is FFT -> mid (fused into the last
 // forward stage) -> inverse FFT, HOUT applying to the inverse.
 template <int N, bool INV, bool ZIN, bool HOUT, class LD, class ST, class MID>
-__global__ void k_pass3(LD ld, ST st, MID mid, int64_t nlines, int64_t B, const float2* __restrict__ twg) {
+__global__ void k_pass3(LD ld, ST st, MID mid, int64_t nlines, int64_t B, const float2* __restrict__ twg,
+                        const int* stop) {
+    if (stop && *stop) return;
     extern __shared__ float2 s[];
     const float2* tw = stage_twiddles<N>(s + N * kLines, twg);
     constexpr int TPL = FftSizeV<N>::TPL;
@@ -456,7 +457,7 @@ int run_pass(const hqs_plan3d_s* p, int N, LD ld, ST st, int64_t nlines, int64_t
         HQS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         const int64_t nblk = ceil_div64(nlines, kLines);
         if (nblk > 0x7fffffff) return HQS_ERR_INVALID_ARG;
-        kern<<<(unsigned)nblk, pass_threads<NN>(), sm, s>>>(ld, st, mid, nlines, B, tw);
+        kern<<<(unsigned)nblk, pass_threads<NN>(), sm, s>>>(ld, st, mid, nlines, B, tw, p->stop);
         HQS_CUDA_TRY(cudaGetLastError());
         return HQS_OK;
     });
@@ -466,7 +467,8 @@ int run_pass(const hqs_plan3d_s* p, int N, LD ld, ST st, int64_t nlines, int64_t
 __global__ void k_coil_sum3(const float2* __restrict__ P, int L, int nx, int ny, int64_t nvox,
                             const float* __restrict__ apx, const float* __restrict__ apy,
                             const float* __restrict__ apz, float ca, float cb, const float2* z,
-                            float2* out) {
+                            float2* out, const int* stop) {
+    if (stop && *stop) return;
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nvox;
          v += (int64_t)gridDim.x * blockDim.x) {
         float2 a = make_float2(0.f, 0.f);
@@ -556,7 +558,8 @@ HQS_DEV double block_sum(double v, double* sh) {
 
 // partials[blk] = Re <a, b> over this block's grid-stride share (fp64)
 __global__ void k_dot3(const float2* __restrict__ a, const float2* __restrict__ b, int64_t count,
-                       double* __restrict__ part) {
+                       double* __restrict__ part, const int* stop) {
+    if (stop && *stop) return;
     __shared__ double sh[32];
     double acc = 0.0;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
@@ -595,15 +598,21 @@ __global__ void k_cg3_init(const float2* __restrict__ rhs, const float2* __restr
 //   RES   one more iteration: rr, history, convergence / iteration limit
 //   RZ    rz = <r, z>, beta = rz_new / rz_old (after the first)
 //   RZ_RR the same with z = r (no preconditioner): rz = rr
+// One warp: lane i sums partials i, i + 32, ... in order, then a butterfly
+// of shuffles (every lane ends with the same, run-to-run identical value).
+HQS_DEV double warp_fixed_sum(const double* part, int n) {
+    double v = 0.0;
+    for (int i = threadIdx.x; i < n; i += 32) v += part[i];
+    for (int m = 16; m > 0; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+    return v;
+}
+
 __global__ void k_cg3_scalar(Cg3* cg, const double* __restrict__ part, int nparts, int mode, double* hist,
                              double rel_tol, int max_iter) {
+    const double s = mode != CG3_RZ_RR ? warp_fixed_sum(part, nparts) : 0.0;
+    const double bb = mode == CG3_INIT ? warp_fixed_sum(part + CG3_BLOCKS, nparts) : 0.0;
     if (threadIdx.x != 0) return;
-    double s = 0.0;
-    if (mode != CG3_RZ_RR)
-        for (int i = 0; i < nparts; ++i) s += part[i];
     if (mode == CG3_INIT) {
-        double bb = 0.0;
-        for (int i = 0; i < nparts; ++i) bb += part[CG3_BLOCKS + i];
         cg->rr = s;
         cg->bnorm2 = bb;
         cg->tol2 = rel_tol * rel_tol * bb;
@@ -730,6 +739,8 @@ template <class T> int alloc3(hqs_plan3d_s* p, T** ptr, size_t count) {
 
 void plan3d_free(hqs_plan3d_s* p) {
     if (!p) return;
+    if (p->iter_graph) cudaGraphExecDestroy(p->iter_graph);
+    if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     for (void* v : p->allocs) cudaFree(v);
     if (p->h_cg) cudaFreeHost(p->h_cg);
     delete p;
@@ -912,7 +923,7 @@ int adj3(hqs_plan3d_s* p, const float2* y, float2* x, cudaStream_t s) {
                                        StCoil{p->bufC, p->smaps, nx, L, 1, Gx}, (int64_t)nz * ny * L, L, s)));
     const int64_t nvox = (int64_t)nx * ny * nz;
     k_coil_sum3<<<vec_blocks(nvox), 256, 0, s>>>(p->bufC, L, nx, ny, nvox, p->apod[0], p->apod[1], p->apod[2],
-                                                 p->scale, 0.f, nullptr, x);
+                                                 p->scale, 0.f, nullptr, x, p->stop);
     HQS_CUDA_TRY(cudaGetLastError());
     return HQS_OK;
 }
@@ -940,7 +951,7 @@ int toep3(hqs_plan3d_s* p, const float2* x, float2* out, float ca, float cb, con
                                       (int64_t)nz * ny * L, L, s)));
     const int64_t nvox = (int64_t)nx * ny * nz;
     k_coil_sum3<<<vec_blocks(nvox), 256, 0, s>>>(p->bufC, L, nx, ny, nvox, nullptr, nullptr, nullptr, ca, cb, z,
-                                                 out);
+                                                 out, p->stop);
     HQS_CUDA_TRY(cudaGetLastError());
     return HQS_OK;
 }
@@ -1199,6 +1210,76 @@ extern "C" int hqs_toeplitz_normal3d(hqs_plan3d p, const hqs_c64* x, hqs_c64* ou
                  (cudaStream_t)stream);
 }
 
+
+namespace {
+
+const int* done_flag(const hqs_plan3d_s* p) {
+    return reinterpret_cast<const int*>(reinterpret_cast<const char*>(p->cg) + offsetof(Cg3, done));
+}
+
+// z = M^-1 r (or r), rz = <r, z>, beta; p = z + beta p
+int pcg_precond_step(hqs_plan3d_s* p, float a, float b, bool dc, int nb, int64_t nvox, cudaStream_t s) {
+    if (dc) {
+        TRY3(precond3(p, a, b, p->cg_r, p->cg_z, s));
+        k_dot3<<<nb, 256, 0, s>>>(p->cg_r, p->cg_z, nvox, p->partials, p->stop);
+        k_cg3_scalar<<<1, 32, 0, s>>>(p->cg, p->partials, nb, CG3_RZ, p->hist, 0.0, 0);
+    } else {
+        k_cg3_scalar<<<1, 32, 0, s>>>(p->cg, p->partials, nb, CG3_RZ_RR, p->hist, 0.0, 0);
+    }
+    k_cg3_pupdate<<<nb, 256, 0, s>>>(p->cg_p, dc ? p->cg_z : p->cg_r, nvox, p->cg);
+    HQS_CUDA_TRY(cudaGetLastError());
+    return HQS_OK;
+}
+
+// one PCG iteration: q = H p, alpha, x and r updates, residual, preconditioner step
+int pcg_iteration(hqs_plan3d_s* p, float a, float b, bool dc, float2* x, int nb, int64_t nvox, cudaStream_t s) {
+    TRY3(toep3(p, p->cg_p, p->cg_q, a, b, p->cg_p, s));
+    k_dot3<<<nb, 256, 0, s>>>(p->cg_p, p->cg_q, nvox, p->partials, p->stop);
+    k_cg3_scalar<<<1, 32, 0, s>>>(p->cg, p->partials, nb, CG3_ALPHA, p->hist, 0.0, 0);
+    k_cg3_update<<<nb, 256, 0, s>>>(x, p->cg_r, p->cg_p, p->cg_q, nvox, p->cg, p->partials);
+    k_cg3_scalar<<<1, 32, 0, s>>>(p->cg, p->partials, nb, CG3_RES, p->hist, 0.0, 0);
+    HQS_CUDA_TRY(cudaGetLastError());
+    return pcg_precond_step(p, a, b, dc, nb, nvox, s);
+}
+
+// The iteration as a CUDA graph on the plan's capture stream, rebuilt when
+// (a, b, preconditioner, x) change.  Every kernel of it reads alpha, beta and
+// the done flag from the device, and returns at once once the solve is done,
+// so replays past convergence cost only their launches.
+int ensure_iteration_graph(hqs_plan3d_s* p, float a, float b, bool dc, float2* x, int nb, int64_t nvox) {
+    if (p->iter_graph && p->g_a == a && p->g_b == b && p->g_dc == (int)dc && p->g_x == x) return HQS_OK;
+    if (p->iter_graph) {
+        cudaGraphExecDestroy(p->iter_graph);
+        p->iter_graph = nullptr;
+    }
+    if (!p->cap_stream) HQS_CUDA_TRY(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+    HQS_CUDA_TRY(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeRelaxed));
+    const int rc = pcg_iteration(p, a, b, dc, x, nb, nvox, p->cap_stream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(p->cap_stream, &g);
+    if (rc != HQS_OK || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) hqs_note_cuda_error(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+        return rc != HQS_OK ? rc : HQS_ERR_CUDA;
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&p->iter_graph, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+        p->iter_graph = nullptr;
+        hqs_note_cuda_error(ei, "cudaGraphInstantiate", __FILE__, __LINE__);
+        return HQS_ERR_CUDA;
+    }
+    p->g_a = a;
+    p->g_b = b;
+    p->g_dc = (int)dc;
+    p->g_x = x;
+    return HQS_OK;
+}
+
+#define HQS3_GRAPH_CHUNK 4   // iterations replayed between host checks of the done flag
+
+}  // namespace
+
 extern "C" int hqs_precond_apply3d(hqs_plan3d p, float a, float b, const hqs_c64* r, hqs_c64* z, void* stream) {
     if (!p || !r || !z || !(b > 0.f)) return HQS_ERR_INVALID_ARG;
     if (!p->pc_ok) return HQS_ERR_UNSUPPORTED;
@@ -1218,37 +1299,24 @@ extern "C" int hqs_dc_solve3d(hqs_plan3d p, float a, float b, const hqs_c64* rhs
     float2* x = reinterpret_cast<float2*>(x_c);
     const int64_t nvox = (int64_t)p->n[0] * p->n[1] * p->n[2];
     const int nb = vec_blocks(nvox);
-    const float2* zsrc = dc ? p->cg_z : p->cg_r;
-    // z = M^-1 r (or r), rz = <r, z>, beta; p = z + beta p
-    auto precond_step = [&]() -> int {
-        if (dc) {
-            TRY3(precond3(p, a, b, p->cg_r, p->cg_z, s));
-            k_dot3<<<nb, 256, 0, s>>>(p->cg_r, p->cg_z, nvox, p->partials);
-            k_cg3_scalar<<<1, 32, 0, s>>>(p->cg, p->partials, nb, CG3_RZ, p->hist, rel_tol, max_iter);
-        } else {
-            k_cg3_scalar<<<1, 32, 0, s>>>(p->cg, p->partials, nb, CG3_RZ_RR, p->hist, rel_tol, max_iter);
-        }
-        k_cg3_pupdate<<<nb, 256, 0, s>>>(p->cg_p, zsrc, nvox, p->cg);
-        HQS_CUDA_TRY(cudaGetLastError());
-        return HQS_OK;
-    };
-    // r = rhs - H x
+    // r = rhs - H x: launched without the stop flag, which still holds the last solve's state
+    p->stop = nullptr;
     TRY3(toep3(p, x, p->cg_q, a, b, x, s));
     k_cg3_init<<<nb, 256, 0, s>>>(rhs, p->cg_q, p->cg_r, nvox, p->partials);
     k_cg3_scalar<<<1, 32, 0, s>>>(p->cg, p->partials, nb, CG3_INIT, p->hist, rel_tol, max_iter);
     HQS_CUDA_TRY(cudaGetLastError());
-    TRY3(precond_step());
-    for (int it = 0; it < max_iter; ++it) {
+    p->stop = done_flag(p);
+    int rc = pcg_precond_step(p, a, b, dc, nb, nvox, s);
+    if (rc == HQS_OK) rc = ensure_iteration_graph(p, a, b, dc, x, nb, nvox);
+    p->stop = nullptr;
+    if (rc != HQS_OK) return rc;
+    for (int it = 0; it < max_iter;) {
         HQS_CUDA_TRY(cudaMemcpyAsync(p->h_cg, p->cg, sizeof(Cg3), cudaMemcpyDeviceToHost, s));
         HQS_CUDA_TRY(cudaStreamSynchronize(s));
         if (p->h_cg->done) break;
-        TRY3(toep3(p, p->cg_p, p->cg_q, a, b, p->cg_p, s));
-        k_dot3<<<nb, 256, 0, s>>>(p->cg_p, p->cg_q, nvox, p->partials);
-        k_cg3_scalar<<<1, 32, 0, s>>>(p->cg, p->partials, nb, CG3_ALPHA, p->hist, rel_tol, max_iter);
-        k_cg3_update<<<nb, 256, 0, s>>>(x, p->cg_r, p->cg_p, p->cg_q, nvox, p->cg, p->partials);
-        k_cg3_scalar<<<1, 32, 0, s>>>(p->cg, p->partials, nb, CG3_RES, p->hist, rel_tol, max_iter);
-        HQS_CUDA_TRY(cudaGetLastError());
-        TRY3(precond_step());
+        const int chunk = std::min(HQS3_GRAPH_CHUNK, max_iter - it);
+        for (int k = 0; k < chunk; ++k) HQS_CUDA_TRY(cudaGraphLaunch(p->iter_graph, s));
+        it += chunk;
     }
     HQS_CUDA_TRY(cudaMemcpyAsync(p->h_cg, p->cg, sizeof(Cg3), cudaMemcpyDeviceToHost, s));
     HQS_CUDA_TRY(cudaStreamSynchronize(s));
