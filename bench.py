@@ -832,6 +832,10 @@ def run_learned320(args, rank, world, dist):
     print(json.dumps(line), flush=True)
 
 
+# DRAM bytes (read + write) of the six launches of one 64^3 x 16-coil A^H A, from one ncu capture
+VOL_AHA_TRAFFIC_BYTES = 514047488 + 190024704
+
+
 def vol_pass_bytes(shape, L):
     """Bytes the six launches of one 3D Toeplitz A^H A move by their pass
     structure (each FFT pass reads its input lines and writes its output):
@@ -929,7 +933,7 @@ def run_vol64(args, rank, world, dist):
         "forward_us": ms_f * 1e3 / K, "adjoint_us": ms_a * 1e3 / K, "aha_us": t_us,
         "aha_applies_per_s": K * world / (ms_t / 1e3),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": HBM_PEAK_GBS, "unit": "GB/s",
-                     "frac": achieved / HBM_PEAK_GBS, "traffic": None,
+                     "frac": achieved / HBM_PEAK_GBS, "traffic": VOL_AHA_TRAFFIC_BYTES,
                      "kernel": "the six launches of one A^H A (pass-structure bytes, measured peak)"},
         "e2e": {"value": nsol * world / (ms_e / 1e3), "unit": "solves/s",
                 "h2d_bytes_per_step": int(rhs.numel() * 8), "d2h_bytes_per_step": int(xs.numel() * 8)},
