@@ -199,6 +199,16 @@ def cpu_oracle_sample(n_iter=2):
     return t_it, t_plan
 
 
+def cpu_oracle_vol_sample(case):
+    """The FP64 oracle on the host cores: one 3D gridding forward + adjoint
+    (A^H(A x), W = 6) of one coil of the volume; returns seconds."""
+    from oracle import nufft3d
+    t0 = time.perf_counter()
+    y = nufft3d.forward(case["x"], case["smaps"][:1], case["traj"], 6, 2.0)
+    nufft3d.adjoint(y, case["smaps"][:1], case["traj"], 6, 2.0)
+    return time.perf_counter() - t0
+
+
 def threads_used():
     try:
         return len(os.sched_getaffinity(0))
@@ -916,6 +926,12 @@ def run_vol64(args, rank, world, dist):
     clocks = clk.stop()
     if rank != 0:
         return
+    cpu = None
+    if world == 1:
+        t_cpu = cpu_oracle_vol_sample(case)
+        cpu = {"value": 1.0 / (t_cpu * L), "unit": "A^H(A x) applies/s", "cores": threads_used(), "kind": "oracle",
+               "sample": "one coil of one 64^3 gridding forward + adjoint (oracle nufft3d, W=6, 524288 points), "
+                         f"{t_cpu:.1f} s, scaled to 16 coils; compare aha_applies_per_s"}
     nsol = max(1, K // 2)
     t_us = ms_t * 1e3 / K
     traffic = vol_pass_bytes(shape, L)
@@ -940,6 +956,7 @@ def run_vol64(args, rank, world, dist):
         # per solve: initial A^H A (6) + init + scalar + preconditioner step (5 + 3), then the
         # 18-kernel iteration graph replayed in chunks of 4 (replays past convergence return at once)
         "gpu_launches": nsol * (16 + 18 * 4 * math.ceil(info.iterations / 4)), "clocks": clocks,
+        "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)
 
