@@ -295,7 +295,9 @@ __global__ void __launch_bounds__(HQS3_SPREAD_WARPS * 32)
 }
 
 // ------------------------------------------------------------ FFT passes
-// Line (a, b) of a pass: element p at base + a*sA + p*sP + b.
+// Line (a, b) of a pass: element p at base + a*sA + p*sP + b.  Every
+// functor resolves its line once per thread (prepare(a, b) -> a small state,
+// in practice base pointers), so the per-element work is base + p*stride.
 struct Lines {
     int64_t sA, sP;
 };
@@ -305,19 +307,23 @@ struct LdLine {
     const float2* src;
     Lines g;
     int count;
-    HQS_DEV float2 operator()(int64_t a, int64_t b, int p) const {
-        return p < count ? src[a * g.sA + (int64_t)p * g.sP + b] : make_float2(0.f, 0.f);
+    struct St { const float2* p; };
+    HQS_DEV St prepare(int64_t a, int64_t b) const { return {src + a * g.sA + b}; }
+    HQS_DEV float2 operator()(const St& t, int p) const {
+        return p < count ? t.p[(int64_t)p * g.sP] : make_float2(0.f, 0.f);
     }
 };
-// centred placement: grid position p holds image index grid->image (n on G)
+// centred placement: grid position p holds image index p + n/2 (p < n/2) or p - G + n/2
 struct LdCentred {
     const float2* src;
     Lines g;
     int n, G;
-    HQS_DEV float2 operator()(int64_t a, int64_t b, int p) const {
+    struct St { const float2* p; };
+    HQS_DEV St prepare(int64_t a, int64_t b) const { return {src + a * g.sA + b}; }
+    HQS_DEV float2 operator()(const St& t, int p) const {
         const int h = n >> 1;
         const int i = p < h ? p + h : (p >= G - h ? p - G + h : -1);
-        return i >= 0 ? src[a * g.sA + (int64_t)i * g.sP + b] : make_float2(0.f, 0.f);
+        return i >= 0 ? t.p[(int64_t)i * g.sP] : make_float2(0.f, 0.f);
     }
 };
 // first forward pass of the NUFFT: S_l x / (phihat^3) at centred positions,
@@ -328,13 +334,16 @@ struct LdImageX {
     const float *apx, *apy, *apz;
     int nx, ny, G, L;
     float scale;
-    HQS_DEV float2 operator()(int64_t a, int64_t b, int p) const {
+    struct St { const float2* xr; const float2* sr; float f; };
+    HQS_DEV St prepare(int64_t a, int64_t b) const {
+        const int z = (int)(a / ny), yy = (int)(a - (int64_t)z * ny);
+        return {x + a * nx, S + a * nx * L + b, scale * apz[z] * apy[yy]};
+    }
+    HQS_DEV float2 operator()(const St& t, int p) const {
         const int h = nx >> 1;
         const int ix = p < h ? p + h : (p >= G - h ? p - G + h : -1);
         if (ix < 0) return make_float2(0.f, 0.f);
-        const int z = (int)(a / ny), yy = (int)(a - (int64_t)z * ny);
-        const int64_t v = a * nx + ix;
-        return cscale(cmul(S[v * L + b], x[v]), scale * apz[z] * apy[yy] * apx[ix]);
+        return cscale(cmul(t.sr[(int64_t)ix * L], t.xr[ix]), t.f * apx[ix]);
     }
 };
 // first pass of the Toeplitz product: S_l x in [0, n) (the upper half is zero)
@@ -342,10 +351,9 @@ struct LdToepX {
     const float2* x;
     const float2* S;
     int nx, L;
-    HQS_DEV float2 operator()(int64_t a, int64_t b, int p) const {
-        const int64_t v = a * nx + p;
-        return cmul(S[v * L + b], x[v]);
-    }
+    struct St { const float2* xr; const float2* sr; };
+    HQS_DEV St prepare(int64_t a, int64_t b) const { return {x + a * nx, S + a * nx * L + b}; }
+    HQS_DEV float2 operator()(const St& t, int p) const { return cmul(t.sr[(int64_t)p * L], t.xr[p]); }
 };
 
 // Output of the last stage, position pos of line (a, b): stored at
@@ -362,9 +370,11 @@ struct StLine {
     float2* dst;
     Lines g;
     int count, mode, G;
-    HQS_DEV void put(int64_t a, int64_t b, int pos, float2 v) const {
+    struct St { float2* p; };
+    HQS_DEV St prepare(int64_t a, int64_t b) const { return {dst + a * g.sA + b}; }
+    HQS_DEV void put(const St& t, int pos, float2 v) const {
         const int o = out_index(pos, count, mode, G);
-        if (o >= 0) dst[a * g.sA + (int64_t)o * g.sP + b] = v;
+        if (o >= 0) t.p[(int64_t)o * g.sP] = v;
     }
 };
 // last pass with coil weighting: P[(a*nx + o)*L + b] = conj(S) * v
@@ -372,23 +382,31 @@ struct StCoil {
     float2* dst;
     const float2* S;
     int nx, L, centred, G;
-    HQS_DEV void put(int64_t a, int64_t b, int pos, float2 v) const {
+    struct St { float2* d; const float2* s; };
+    HQS_DEV St prepare(int64_t a, int64_t b) const {
+        const int64_t e0 = a * nx * L + b;
+        return {dst + e0, S + e0};
+    }
+    HQS_DEV void put(const St& t, int pos, float2 v) const {
         const int o = out_index(pos, nx, centred ? 1 : 0, G);
         if (o < 0) return;
-        const int64_t e = (a * nx + o) * L + b;
-        dst[e] = cmulc(S[e], v);
+        const int64_t e = (int64_t)o * L;
+        t.d[e] = cmulc(t.s[e], v);
     }
 };
 
-struct NoMid {};
+struct NoMid {
+    struct St {};
+    HQS_DEV St prepare(int64_t, int64_t) const { return {}; }
+};
 // Khat multiply between the forward and inverse z transforms: b = (ky*Tx + kx)*L + l
 struct MidKhat {
     const float* khat;
     int64_t plane;   // Ty * Tx
     int L;
-    HQS_DEV float2 operator()(int64_t, int64_t b, int p, float2 v) const {
-        return cscale(v, khat[(int64_t)p * plane + b / L]);
-    }
+    struct St { const float* k; };
+    HQS_DEV St prepare(int64_t, int64_t b) const { return {khat + b / L}; }
+    HQS_DEV float2 operator()(const St& t, int p, float2 v) const { return cscale(v, t.k[(int64_t)p * plane]); }
 };
 
 // density-preconditioner multiply s^-1/2 / Nvox between the forward and
@@ -397,8 +415,10 @@ struct MidPrecond {
     const float* lam;
     int64_t plane;   // ny * nx
     float a, b, inv_nvox;
-    HQS_DEV float2 operator()(int64_t, int64_t bb, int p, float2 v) const {
-        const float sv = fmaxf(fmaf(a, fmaxf(lam[(int64_t)p * plane + bb], 0.f), b), 0.25f * b);
+    struct St { const float* l; };
+    HQS_DEV St prepare(int64_t, int64_t bb) const { return {lam + bb}; }
+    HQS_DEV float2 operator()(const St& t, int p, float2 v) const {
+        const float sv = fmaxf(fmaf(a, fmaxf(t.l[(int64_t)p * plane], 0.f), b), 0.25f * b);
         return cscale(v, rsqrtf(sv) * inv_nvox);
     }
 };
@@ -424,14 +444,17 @@ __global__ void k_pass3(LD ld, ST st, MID mid, int64_t nlines, int64_t B, const 
     const int ll = (int)(threadIdx.x % (blockDim.x / TPL));
     const int64_t mine = l0 + (ll < lines ? ll : 0);
     const int64_t a = mine / B, b = mine - a * B;
-    const int64_t a0 = l0 / B, b0 = l0 - a0 * B;
-    // threads without a line read line l0 (in bounds) and store nothing
-    auto load = [&](int, int pos, bool act) { return act ? ld(a, b, pos) : ld(a0, b0, pos); };
-    auto store = [&](int, int pos, float2 v) { st.put(a, b, pos, v); };
+    // threads without a line (ll >= lines) were given line l0 above: they read
+    // it (in bounds) and store nothing
+    const auto lds = ld.prepare(a, b);
+    const auto sts = st.prepare(a, b);
+    auto load = [&](int, int pos, bool) { return ld(lds, pos); };
+    auto store = [&](int, int pos, float2 v) { st.put(sts, pos, v); };
     if constexpr (std::is_same_v<MID, NoMid>) {
         block_fft_io_tab<FftSizeV, N, INV, ZIN, HOUT>(s, lines, tw, load, NoIO{}, store);
     } else {
-        auto xf = [&](int, int pos, float2 v) { return mid(a, b, pos, v); };
+        const auto mds = mid.prepare(a, b);
+        auto xf = [&](int, int pos, float2 v) { return mid(mds, pos, v); };
         block_fft_io_tab<FftSizeV, N, false, ZIN, false>(s, lines, tw, load, xf, NoIO{});
         block_fft_io_tab<FftSizeV, N, true, false, HOUT>(s, lines, tw, NoIO{}, NoIO{}, store);
     }
