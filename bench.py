@@ -843,7 +843,7 @@ def run_learned320(args, rank, world, dist):
 
 
 # DRAM bytes (read + write) of the six launches of one 64^3 x 16-coil A^H A, from one ncu capture
-VOL_AHA_TRAFFIC_BYTES = 514047488 + 190024704
+VOL_AHA_TRAFFIC_BYTES = 514025728 + 189041664
 
 
 def vol_pass_bytes(shape, L):
