@@ -13,7 +13,7 @@ which for P = Id is (A^H A + mu I) u = A^H y + mu x.  It is solved by PCG with
 a fixed number of iterations, warm-started at x_k.
 
 The default denoiser is separable complex Gaussian smoothing with periodic
-boundaries (a stand-in for the trained prior of Sec. 4.2).
+boundaries (a stand-in for the trained prior of Sec. 4.2), on images or volumes.
 """
 from __future__ import annotations
 
@@ -38,18 +38,19 @@ def gaussian_taps(s: float) -> np.ndarray:
 
 def gaussian_denoise(v, s: float) -> np.ndarray:
     """Separable Gaussian blur (std s pixels, radius ceil(3 s), periodic) of the
-    real and imaginary parts; identity when s < 0.1."""
+    real and imaginary parts of an image or a volume, one axis at a time from
+    the last (x) to the first; identity when s < 0.1."""
     v = np.asarray(v, dtype=np.complex128)
     if s < 0.1:
         return v.copy()
     g = gaussian_taps(s)
     r = (len(g) - 1) // 2
-    tmp = np.zeros_like(v)
-    for i, gi in enumerate(g):
-        tmp += gi * np.roll(v, -(i - r), axis=1)   # tmp[y, x] += g * v[y, x + (i - r)]
-    out = np.zeros_like(v)
-    for i, gi in enumerate(g):
-        out += gi * np.roll(tmp, -(i - r), axis=0)
+    out = v
+    for axis in reversed(range(v.ndim)):
+        acc = np.zeros_like(v)
+        for i, gi in enumerate(g):
+            acc += gi * np.roll(out, -(i - r), axis=axis)   # acc[.., n, ..] += g * out[.., n + (i - r), ..]
+        out = acc
     return out
 
 
@@ -59,12 +60,15 @@ def denoiser_std(sigma_k: float, sigma_0: float, kappa: float = 1.5) -> float:
 
 
 def hqs(apply_AHA, b0, x0, mu, sigma, K, k0=0, cg_iters=5, c0=1.0, c1=0.0,
-        denoiser=None, lam=None):
+        denoiser=None, lam=None, precond_apply=None):
     """Annealed PnP-HQS from iteration k0 to K; returns (x_K, u_{K-1}, history).
 
     denoiser(u, sigma_k) defaults to gaussian_denoise(u, 1.5*sigma_k/sigma_0)
     with sigma_0 = sigma[0]; lam is the circulant preconditioner symbol (None
-    for unpreconditioned CG)."""
+    for unpreconditioned CG), applied by precond_apply(v, lam, a, b) (default:
+    the 2D one of toeplitz; volumes pass nufft3d.precond_apply)."""
+    if precond_apply is None:
+        precond_apply = toeplitz.precond_apply
     if denoiser is None:
         s0 = float(sigma[0])
         denoiser = lambda u, sk: gaussian_denoise(u, denoiser_std(sk, s0))
@@ -79,7 +83,7 @@ def hqs(apply_AHA, b0, x0, mu, sigma, K, k0=0, cg_iters=5, c0=1.0, c1=0.0,
         H = lambda v, a=a, b=b: a * apply_AHA(v) + b * v
         Minv = None
         if lam is not None:
-            Minv = lambda v, a=a, b=b: toeplitz.precond_apply(v, lam, a, b)
+            Minv = lambda v, a=a, b=b: precond_apply(v, lam, a, b)
         u, _ = solvers.pcg(H, rhs, x, Minv, max_iter=cg_iters, tol=0.0)
         x = denoiser(u, float(sigma[k]))
         hist.append(x.copy())

@@ -9,7 +9,7 @@ import math
 import numpy as np
 import pytest
 
-from oracle import nudft, nufft3d, solvers, toeplitz
+from oracle import hqs, nudft, nufft3d, solvers, toeplitz
 import synth
 
 
@@ -208,3 +208,45 @@ def test_density_preconditioner_cuts_3d_iterations_on_stacked_spirals():
     _, i_plain = solvers.pcg(H, b0, z0, None, 300, 1e-4)
     _, i_dc = solvers.pcg(H, b0, z0, lambda v: nufft3d.precond_apply(v, lam, 1.0, mu), 300, 1e-4)
     assert i_dc["iters"] < 0.8 * i_plain["iters"], (i_dc["iters"], i_plain["iters"])
+
+
+# ------------------------------------------------------------ HQS on volumes
+def test_gaussian_denoise3d_matches_fft_convolution():
+    rng = np.random.default_rng(21)
+    shape, sd = (8, 10, 12), 1.3
+    v = rand_c(rng, shape)
+    g = hqs.gaussian_taps(sd)
+    r = (len(g) - 1) // 2
+    kern = np.zeros(shape)
+    for i in range(-r, r + 1):
+        for j in range(-r, r + 1):
+            for k in range(-r, r + 1):
+                kern[i % shape[0], j % shape[1], k % shape[2]] += g[i + r] * g[j + r] * g[k + r]
+    # out[n] = sum_d g(d) v[n + d]: correlation with the (symmetric) kernel
+    want = np.fft.ifftn(np.fft.fftn(v) * np.conj(np.fft.fftn(kern)))
+    assert rel(hqs.gaussian_denoise(v, sd), want) < 1e-13
+    assert rel(hqs.gaussian_denoise(v, 0.05), v) == 0.0
+
+
+def test_hqs_on_a_one_slice_volume_is_the_2d_run():
+    # every piece of the volumetric loop (normal operator, Chan preconditioner,
+    # Gaussian smoothing) reduces to its 2D counterpart on one slice
+    rng = np.random.default_rng(22)
+    ny, nx, L, M, K = 12, 16, 2, 300, 4
+    x = rand_c(rng, (ny, nx))
+    S = rand_c(rng, (L, ny, nx))
+    traj = rand_traj(rng, M)
+    y = nudft.forward(x, S, traj[:, :2]) + 0.05 * rand_c(rng, (L, M))
+    mu = np.geomspace(1e-1, 1e-2, K)
+    sg = np.geomspace(0.2, 0.05, K)
+    c2 = toeplitz.kernel(traj[:, :2], ny, nx)
+    K2, lam2 = toeplitz.khat(c2), toeplitz.chan_symbol(c2, ny, nx)
+    b2 = nudft.adjoint(y, S, traj[:, :2])
+    x2, _, _ = hqs.hqs(lambda v: toeplitz.normal(v, S, K2), b2, np.zeros((ny, nx)), mu, sg, K, cg_iters=4,
+                       lam=lam2)
+    c3 = nufft3d.kernel(traj, (1, ny, nx))
+    K3, lam3 = nufft3d.khat(c3), nufft3d.chan_symbol(c3, (1, ny, nx))
+    b3 = nufft3d.nudft_adjoint(y, S[:, None], traj)
+    x3, _, _ = hqs.hqs(lambda v: nufft3d.normal(v, S[:, None], K3), b3, np.zeros((1, ny, nx)), mu, sg, K,
+                       cg_iters=4, lam=lam3, precond_apply=nufft3d.precond_apply)
+    assert rel(x3[0], x2) < 1e-12
