@@ -398,7 +398,7 @@ HQS_API int hqs_debug_toeplitz_stage(hqs_plan plan, const hqs_c64* x, int precis
  * {8, 16, 32, 64, 128, 160, 192}; coils 1..64; kernel_width 4..8; oversamp
  * must be 2 (the NUFFT grid is then also the 2N Toeplitz grid).  Invalid
  * arguments return HQS_ERR_INVALID_ARG with *out = NULL.  The plan holds
- * about (13 L + 8) * 8 * nz*ny*nx bytes of device memory. */
+ * about (14 L + 13) * 8 * nz*ny*nx bytes of device memory. */
 HQS_API int hqs_plan3d_create(hqs_plan3d* out, const float* traj, int64_t M, int nz, int ny, int nx,
                               int coils, const hqs_c64* smaps, int kernel_width, float oversamp,
                               void* stream);
@@ -439,6 +439,30 @@ HQS_API int hqs_precond_apply3d(hqs_plan3d plan, float a, float b, const hqs_c64
 HQS_API int hqs_dc_solve3d(hqs_plan3d plan, float a, float b, const hqs_c64* rhs, hqs_c64* x,
                            int max_iter, double rel_tol, int precond, hqs_solve_info* info,
                            void* stream);
+
+/* Denoiser callback of hqs_run3d: D_sigma on a device (nz, ny, nx) volume,
+ * same contract as hqs_denoiser_fn. */
+typedef int (*hqs_denoiser3d_fn)(void* user, const hqs_c64* in, hqs_c64* out,
+                                 int nz, int ny, int nx, float sigma, void* stream);
+/* Built-in volume denoiser (stand-in for the trained prior of Sec. 4.2): the
+ * Gaussian smoothing of hqs_gaussian_denoise along x, then y, then z (std s
+ * voxels from hqs_gauss_params as there, radius ceil(3 s) <= 24, periodic);
+ * copies in to out when s < 0.1.  Uses stream-ordered scratch
+ * (cudaMallocAsync of 2 volumes).  Matches hqs_denoiser3d_fn. */
+HQS_API int hqs_gaussian_denoise3d(void* user, const hqs_c64* in, hqs_c64* out,
+                                   int nz, int ny, int nx, float sigma, void* stream);
+/* Annealed PnP-HQS of Sec. 3.3 on a volume, the steps of hqs_run: for
+ * k = k0..K-1, u_k from ((1 + c1 mu_k) A^H A + c0 mu_k I) u = A^H y +
+ * mu_k (c0 x_k + c1 A^H A x_k) by cg_iters PCG iterations (density
+ * preconditioner where hqs_precond_apply3d exists, plain CG otherwise)
+ * warm-started at x_k, then x_{k+1} = D_{sigma_k}(u_k).  mu, sigma: host
+ * arrays (mu_k > 0); y: (L, M) device; x: (nz, ny, nx) device, x_{k0} in,
+ * x_K out.  denoiser NULL: hqs_gaussian_denoise3d with `user` pointing to
+ * hqs_gauss_params (NULL: s = sigma).  Blocking (each CG iteration chunk is
+ * checked on the host); the callback runs on the calling thread. */
+HQS_API int hqs_run3d(hqs_plan3d plan, const hqs_c64* y, hqs_c64* x, const float* mu, const float* sigma,
+                      int K, int k0, int cg_iters, float c0, float c1, hqs_denoiser3d_fn denoiser,
+                      void* user, void* stream);
 
 /* Diagnostics (no counterpart in the paper): phase trace of the persistent
  * solve.  enable = 1 allocates a trace buffer on the plan (returns 0); later

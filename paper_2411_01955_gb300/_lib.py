@@ -53,6 +53,8 @@ class GaussParams(C.Structure):
 
 DENOISER_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int,
                           C.c_float, C.c_void_p)
+DENOISER3_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,
+                           C.c_float, C.c_void_p)
 
 _lock = threading.Lock()
 _lib = None
@@ -136,6 +138,11 @@ _SIGS = {
     "hqs_dc_solve3d": (C.c_int, [C.c_void_p, C.c_float, C.c_float, C.c_void_p, C.c_void_p, C.c_int,
                                  C.c_double, C.c_int, C.POINTER(SolveInfo), C.c_void_p]),
     "hqs_precond_apply3d": (C.c_int, [C.c_void_p, C.c_float, C.c_float, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "hqs_gaussian_denoise3d": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,
+                                         C.c_float, C.c_void_p]),
+    "hqs_run3d": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_float),
+                            C.c_int, C.c_int, C.c_int, C.c_float, C.c_float, C.c_void_p, C.c_void_p,
+                            C.c_void_p]),
 }
 
 
@@ -668,3 +675,45 @@ def dc_solve3d(plan: Plan3d, a, b, rhs, x, max_iter=30, rel_tol=1e-4, precond=HQ
         raise HqsError(rc, "hqs_dc_solve3d")
     info.rc = rc
     return info
+
+
+def gaussian_denoise3d(x, out, sigma, gauss=None, stream=None):
+    """Built-in volume denoiser; gauss=(kappa, sigma0) or None (s = sigma)."""
+    gp = GaussParams(float(gauss[0]), float(gauss[1])) if gauss is not None else None
+    nz, ny, nx = (int(v) for v in x.shape)
+    _check(library().hqs_gaussian_denoise3d(C.cast(C.pointer(gp), C.c_void_p) if gp is not None else None,
+                                            _ptr(x, torch.complex64, "x"), _ptr(out, torch.complex64, "out"),
+                                            nz, ny, nx, float(sigma), _stream(stream)), "hqs_gaussian_denoise3d")
+    return out
+
+
+def hqs_run3d(plan: Plan3d, y, x, mu, sigma, K=None, k0=0, cg_iters=5, c0=1.0, c1=0.0, denoiser=None,
+              gauss=None, stream=None):
+    """Annealed PnP-HQS on a volume; `denoiser` is None (built-in Gaussian
+    smoothing, optional gauss=(kappa, sigma0)) or a callable(in_tensor,
+    out_tensor, sigma) that enqueues work on the current stream and returns 0."""
+    lib = library()
+    K = len(mu) if K is None else int(K)
+    mu_c = (C.c_float * K)(*[float(v) for v in mu[:K]])
+    sg_c = (C.c_float * K)(*[float(v) for v in sigma[:K]])
+    user, cb, keep = None, None, []
+    if denoiser is None:
+        if gauss is not None:
+            gp = GaussParams(float(gauss[0]), float(gauss[1]))
+            keep.append(gp)
+            user = C.cast(C.pointer(gp), C.c_void_p)
+    else:
+        def _cb(_user, pin, pout, d, h, w, s, _stream_ptr):
+            try:
+                tin = _wrap_device(pin, (d, h, w))
+                tout = _wrap_device(pout, (d, h, w))
+                return int(denoiser(tin, tout, float(s)) or 0)
+            except Exception:
+                return 1
+        cb = DENOISER3_FN(_cb)
+        keep.append(cb)
+    rc = lib.hqs_run3d(plan.handle, _ptr(y, torch.complex64, "y"), _ptr(x, torch.complex64, "x"), mu_c, sg_c, K,
+                       int(k0), int(cg_iters), float(c0), float(c1),
+                       C.cast(cb, C.c_void_p) if cb is not None else None, user, _stream(stream))
+    _check(rc, "hqs_run3d")
+    return x

@@ -69,6 +69,10 @@ struct hqs_plan3d_s {
     float2* cg_p = nullptr;
     float2* cg_q = nullptr;
     float2* cg_z = nullptr;
+    float2* hqs_b0 = nullptr;   // A^H y of the outer loop
+    float2* hqs_rhs = nullptr;
+    float2* hqs_u = nullptr;
+    float2* hqs_w = nullptr;    // A^H A x for the P-metric prox (c1 != 0)
     double* partials = nullptr;
     Cg3* cg = nullptr;
     Cg3* h_cg = nullptr;
@@ -395,10 +399,7 @@ struct StCoil {
     }
 };
 
-struct NoMid {
-    struct St {};
-    HQS_DEV St prepare(int64_t, int64_t) const { return {}; }
-};
+struct NoMid {};
 // Khat multiply between the forward and inverse z transforms: b = (ky*Tx + kx)*L + l
 struct MidKhat {
     const float* khat;
@@ -562,6 +563,51 @@ __global__ void k_real_part3(const float2* __restrict__ in, float* __restrict__ 
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
          e += (int64_t)gridDim.x * blockDim.x)
         out[e] = in[e].x * s;
+}
+
+// ------------------------------------------------------------ Gaussian smoothing
+#define HQS3_BLUR_MAXR 24
+struct Taps3 {
+    int r;
+    float g[2 * HQS3_BLUR_MAXR + 1];
+};
+
+// One axis of the separable periodic blur: out[.., c, ..] = sum_i g[i] in[.., (c + i - r) mod n, ..],
+// the axis of length n with element stride `stride`; taps in order i = 0..2r.
+__global__ void k_blur3(const float2* __restrict__ in, float2* __restrict__ out, int n, int64_t stride,
+                        int64_t nvox, Taps3 t) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nvox;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)((v / stride) % n);
+        const float2* base = in + (v - (int64_t)c * stride);
+        float2 acc = make_float2(0.f, 0.f);
+        for (int i = 0; i <= 2 * t.r; ++i) {
+            int q = (c + i - t.r) % n;
+            if (q < 0) q += n;
+            const float2 w = base[(int64_t)q * stride];
+            acc.x = fmaf(t.g[i], w.x, acc.x);
+            acc.y = fmaf(t.g[i], w.y, acc.y);
+        }
+        out[v] = acc;
+    }
+}
+
+// out = u + cb v (+ cc w)
+__global__ void k_axpbypcz3(float2* __restrict__ out, const float2* __restrict__ u, const float2* __restrict__ v,
+                            float cb, const float2* __restrict__ w, float cc, int64_t count) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        float2 o = u[e];
+        const float2 vv = v[e];
+        o.x = fmaf(cb, vv.x, o.x);
+        o.y = fmaf(cb, vv.y, o.y);
+        if (w) {
+            const float2 ww = w[e];
+            o.x = fmaf(cc, ww.x, o.x);
+            o.y = fmaf(cc, ww.y, o.y);
+        }
+        out[e] = o;
+    }
 }
 
 // ------------------------------------------------------------ CG kernels
@@ -1115,6 +1161,10 @@ int plan3d_build(hqs_plan3d_s* p, const float* traj, const float2* smaps_user, c
     TRY3(alloc3(p, &p->cg_p, (size_t)nvox));
     TRY3(alloc3(p, &p->cg_q, (size_t)nvox));
     TRY3(alloc3(p, &p->cg_z, (size_t)nvox));
+    TRY3(alloc3(p, &p->hqs_b0, (size_t)nvox));
+    TRY3(alloc3(p, &p->hqs_rhs, (size_t)nvox));
+    TRY3(alloc3(p, &p->hqs_u, (size_t)nvox));
+    TRY3(alloc3(p, &p->hqs_w, (size_t)nvox));
     p->pc_ok = fft_size_supported(nx) && fft_size_supported(ny) && fft_size_supported(nz);
     if (p->pc_ok) TRY3(alloc3(p, &p->lam, (size_t)nvox));
     TRY3(alloc3(p, &p->partials, (size_t)2 * CG3_BLOCKS));
@@ -1366,5 +1416,80 @@ extern "C" int hqs_plan3d_get_info(hqs_plan3d p, int64_t* npoints, int* nsub, si
     if (npoints) *npoints = p->M;
     if (nsub) *nsub = p->nsub;
     if (device_bytes) *device_bytes = p->bytes;
+    return HQS_OK;
+}
+
+extern "C" int hqs_gaussian_denoise3d(void* user, const hqs_c64* in_c, hqs_c64* out_c, int nz, int ny, int nx,
+                                      float sigma, void* stream) {
+    if (!in_c || !out_c || nz <= 0 || ny <= 0 || nx <= 0 || !(sigma >= 0.f)) return HQS_ERR_INVALID_ARG;
+    float sd = sigma;
+    if (user) {
+        const hqs_gauss_params* gp = static_cast<const hqs_gauss_params*>(user);
+        if (gp->sigma0 > 0.f) sd = gp->kappa * sigma / gp->sigma0;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t nvox = (int64_t)nz * ny * nx;
+    const float2* in = reinterpret_cast<const float2*>(in_c);
+    float2* out = reinterpret_cast<float2*>(out_c);
+    if (sd < 0.1f) {
+        if (in != out) HQS_CUDA_TRY(cudaMemcpyAsync(out, in, nvox * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+        return HQS_OK;
+    }
+    Taps3 t;
+    t.r = (int)std::ceil(3.0 * (double)sd);
+    if (t.r > HQS3_BLUR_MAXR) return HQS_ERR_INVALID_ARG;
+    std::vector<double> g(2 * t.r + 1);
+    double sum = 0.0;
+    for (int i = -t.r; i <= t.r; ++i) {
+        g[i + t.r] = std::exp(-(double)i * i / (2.0 * (double)sd * (double)sd));
+        sum += g[i + t.r];
+    }
+    for (int i = 0; i <= 2 * t.r; ++i) t.g[i] = (float)(g[i] / sum);
+    // x, y, z passes through two stream-ordered scratch volumes
+    float2* tmp = nullptr;
+    HQS_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&tmp), 2 * nvox * sizeof(float2), st));
+    const int nb = vec_blocks(nvox);
+    k_blur3<<<nb, 256, 0, st>>>(in, tmp, nx, 1, nvox, t);
+    k_blur3<<<nb, 256, 0, st>>>(tmp, tmp + nvox, ny, nx, nvox, t);
+    k_blur3<<<nb, 256, 0, st>>>(tmp + nvox, out, nz, (int64_t)ny * nx, nvox, t);
+    const cudaError_t e = cudaGetLastError();
+    cudaFreeAsync(tmp, st);
+    HQS_CUDA_TRY(e);
+    return HQS_OK;
+}
+
+extern "C" int hqs_run3d(hqs_plan3d p, const hqs_c64* y, hqs_c64* x_c, const float* mu, const float* sigma, int K,
+                         int k0, int cg_iters, float c0, float c1, hqs_denoiser3d_fn denoiser, void* user,
+                         void* stream) {
+    if (!p || !x_c || (!y && p->M > 0) || !mu || !sigma || K < 0 || k0 < 0 || k0 > K || cg_iters < 0 ||
+        cg_iters > HQS_MAX_ITERS || !(c0 > 0.f))
+        return HQS_ERR_INVALID_ARG;
+    for (int k = k0; k < K; ++k)
+        if (!(mu[k] > 0.f) || !(sigma[k] >= 0.f) || !(1.f + c1 * mu[k] > 0.f)) return HQS_ERR_INVALID_ARG;
+    if (!denoiser) denoiser = hqs_gaussian_denoise3d;
+    cudaStream_t st = (cudaStream_t)stream;
+    float2* x = reinterpret_cast<float2*>(x_c);
+    const int nx = p->n[0], ny = p->n[1], nz = p->n[2];
+    const int64_t nvox = (int64_t)nx * ny * nz;
+    const int nb = vec_blocks(nvox);
+    TRY3(adj3(p, reinterpret_cast<const float2*>(y), p->hqs_b0, st));
+    const int precond = p->pc_ok ? HQS_PRECOND_DC : HQS_PRECOND_NONE;
+    for (int k = k0; k < K; ++k) {
+        const float m = mu[k];
+        const float a = 1.f + c1 * m, b = c0 * m;
+        // rhs = A^H y + mu (c0 x + c1 A^H A x); u starts at x
+        const float2* w = nullptr;
+        if (c1 != 0.f) {
+            TRY3(toep3(p, x, p->hqs_w, 1.f, 0.f, nullptr, st));
+            w = p->hqs_w;
+        }
+        k_axpbypcz3<<<nb, 256, 0, st>>>(p->hqs_rhs, p->hqs_b0, x, m * c0, w, m * c1, nvox);
+        HQS_CUDA_TRY(cudaMemcpyAsync(p->hqs_u, x, nvox * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+        const int rc = hqs_dc_solve3d(p, a, b, reinterpret_cast<const hqs_c64*>(p->hqs_rhs),
+                                      reinterpret_cast<hqs_c64*>(p->hqs_u), cg_iters, 0.0, precond, nullptr, stream);
+        if (rc != HQS_OK && rc != HQS_ERR_NOT_CONVERGED) return rc;
+        if (denoiser(user, reinterpret_cast<const hqs_c64*>(p->hqs_u), x_c, nz, ny, nx, sigma[k], stream) != 0)
+            return HQS_ERR_CALLBACK;
+    }
     return HQS_OK;
 }

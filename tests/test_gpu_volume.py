@@ -21,7 +21,7 @@ import pytest
 
 import synth
 from helpers import rel, to_dev, to_host
-from oracle import nufft3d, solvers
+from oracle import hqs as ohqs, nufft3d, solvers
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -270,3 +270,84 @@ def test_volume_benchmark_size_sampled():
     print(f"64^3 x 16 coils, {M} points: forward {ef:.2e}, adjoint {ea:.2e}, kernel {et:.2e}, "
           f"Toeplitz vs A^H(A x) {en:.2e}")
     assert ef <= 1e-4 and ea <= 1e-4 and et <= 1e-5 and en <= 1e-4
+
+
+# ------------------------------------------------------------------ HQS on volumes
+def test_gaussian_denoise3d_matches_oracle():
+    rng = np.random.default_rng(31)
+    v = (rng.normal(size=(8, 12, 16)) + 1j * rng.normal(size=(8, 12, 16))).astype(np.complex64)
+    out = torch.empty(v.shape, dtype=torch.complex64, device="cuda")
+    for s_, gauss in ((1.3, None), (0.6, (1.5, 0.3)), (0.05, None)):
+        hq().gaussian_denoise3d(to_dev(v), out, s_, gauss=gauss)
+        sd = s_ if gauss is None else gauss[0] * s_ / gauss[1]
+        e = rel(to_host(out), ohqs.gaussian_denoise(v.astype(np.complex128), sd))
+        assert e <= 1e-6, (s_, e)
+    # in place
+    x = to_dev(v)
+    hq().gaussian_denoise3d(x, x, 1.3)
+    assert rel(to_host(x), ohqs.gaussian_denoise(v.astype(np.complex128), 1.3)) <= 1e-6
+
+
+def test_hqs_run3d_matches_oracle():
+    """Annealed HQS on a volume, 6 outer x 5 PCG iterations, mu 1e-1 -> 1e-3,
+    Gaussian smoothing.  As for the 2D run, truncated warm-started CG amplifies
+    rounding, so the bounds are derived from the oracle's own sensitivity:
+    each step (started from the oracle's x_k) within max(1e-5, 4 d_k), d_k the
+    oracle's one-step deviation when A^H y and x_k are perturbed by 2^-22
+    relative (four float32 unit roundoffs: the GPU's gridded Toeplitz kernel
+    adds ~1e-7 to the FP32 rounding); the whole run within 4x the oracle's
+    deviation under the same perturbation of A^H y."""
+    c = pc_case()
+    plan, _, _ = plan_of(c)
+    K, cg = 6, 5
+    kern = nufft3d.kernel(c["traj"], c["shape"])
+    Kh, lam = nufft3d.khat(kern), nufft3d.chan_symbol(kern, c["shape"])
+    y = nufft3d.forward(c["x"], c["smaps"], c["traj"], c["W"], c["sigma"])
+    y = (y + 0.02 * np.abs(y).max() * synth.complex_noise(7, y.shape)).astype(np.complex64).astype(np.complex128)
+    mu = np.geomspace(1e-1, 1e-3, K).astype(np.float32)
+    sigma = mu.copy()
+    mu64, sg64 = mu.astype(np.float64), sigma.astype(np.float64)
+    b0 = nufft3d.adjoint(y, c["smaps"], c["traj"], c["W"], c["sigma"])
+    AHA = lambda v: nufft3d.normal(v, c["smaps"], Kh)
+    run = lambda b, x0, k1, k0=0: ohqs.hqs(AHA, b, x0, mu64, sg64, k1, k0=k0, cg_iters=cg, lam=lam,
+                                           precond_apply=nufft3d.precond_apply)
+    want, _, hist = run(b0, np.zeros(c["shape"]), K)
+    rng = np.random.default_rng(0)
+    eps = 2.0 ** -22
+    xk = np.zeros(c["shape"], dtype=np.complex128)
+    for k in range(K):
+        xg = to_dev(xk)
+        hq().hqs_run3d(plan, to_dev(y), xg, mu, sigma, K=k + 1, k0=k, cg_iters=cg, gauss=(1.5, float(sigma[0])))
+        step, _, _ = run(b0, xk, k + 1, k)
+        pstep, _, _ = run(b0 * (1 + eps * rng.normal(size=b0.shape)), xk * (1 + eps * rng.normal(size=xk.shape)),
+                          k + 1, k)
+        tol_k = max(1e-5, 4 * rel(pstep, step))
+        assert rel(to_host(xg), step) <= tol_k, (k, rel(to_host(xg), step), tol_k)
+        xk = hist[k].astype(np.complex64).astype(np.complex128)
+    x = torch.zeros(c["shape"], dtype=torch.complex64, device="cuda")
+    hq().hqs_run3d(plan, to_dev(y), x, mu, sigma, K=K, cg_iters=cg, gauss=(1.5, float(sigma[0])))
+    pert, _, _ = run(b0 * (1 + eps * rng.normal(size=b0.shape)), np.zeros(c["shape"]), K)
+    bound = max(1e-5, 4 * rel(pert, want))
+    err = rel(to_host(x), want)
+    print(f"3D HQS {K}x{cg}: rel error to the oracle {err:.2e} (bound {bound:.2e}); "
+          f"to the ground truth {rel(to_host(x), c['x']):.3f}")
+    assert err <= bound, (err, bound)
+
+
+def test_hqs_run3d_callback_and_failure():
+    c = CASES["aniso"]()
+    plan, _, _ = plan_of(c)
+    y = to_dev(synth.complex_noise(2, (c["L"], c["traj"].shape[0])))
+    calls = []
+
+    def shrink(tin, tout, s):
+        calls.append((tuple(tin.shape), s))
+        tout.copy_(tin * 0.5)
+        return 0
+
+    x = torch.zeros(c["shape"], dtype=torch.complex64, device="cuda")
+    hq().hqs_run3d(plan, y, x, [0.1, 0.05], [1.0, 0.5], cg_iters=3, denoiser=shrink)
+    assert calls == [(c["shape"], 1.0), (c["shape"], 0.5)]
+    with pytest.raises(hq().HqsError) as ei:
+        hq().hqs_run3d(plan, y, x, [0.1], [1.0], cg_iters=3, denoiser=lambda a, b, s: 7)
+    assert ei.value.status == hq().HQS_ERR_CALLBACK
