@@ -89,7 +89,7 @@ def parse():
     ap.add_argument("--mode", default="batched", choices=["batched", "fused", "plain"])
     ap.add_argument("--group", type=int, default=64, help="slices per batched launch (at most 64)")
     ap.add_argument("--workload", default="dc320",
-                    choices=["dc320", "batch64", "mixed320", "hqs320", "learned320", "vol64"])
+                    choices=["dc320", "batch64", "mixed320", "hqs320", "learned320", "vol64", "vol128"])
     return ap.parse_args()
 
 
@@ -858,17 +858,20 @@ def vol_pass_bytes(shape, L):
 
 
 def run_vol64(args, rank, world, dist):
-    """Volumetric operator at 64^3 x 16 coils (stack of 64 VD spirals, 8 x 1024
-    samples each): forward / adjoint / Toeplitz A^H A per call and DC solves
-    (CG, mu 1e-2, 1e-4) per second; every rank runs its own volume."""
+    """Volumetric operator at 64^3 (vol64: stack of 64 VD spirals, 8 x 1024
+    samples each) or 128^3 (vol128: 128 spirals of 16 x 1024), 16 coils:
+    forward / adjoint / Toeplitz A^H A per call, DC solves (PCG, mu 1e-2,
+    1e-4) per second and one annealed HQS run; every rank runs its own volume."""
     import torch
     import paper_2411_01955_gb300 as hq
     import synth
 
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
-    shape, L = (64, 64, 64), 16
-    case = synth.volume_case(rank, shape, L, 8, 1024)
+    big = args.workload == "vol128"
+    nv = 128 if big else 64
+    shape, L = (nv, nv, nv), 16
+    case = synth.volume_case(rank, shape, L, 16 if big else 8, 1024)
     traj = torch.from_numpy(case["traj"]).cuda()
     smaps = torch.from_numpy(case["smaps"].astype(np.complex64)).cuda()
     plan = hq.plan3d_create(traj, shape, smaps, 6, 2.0)
@@ -923,11 +926,21 @@ def run_vol64(args, rank, world, dist):
         solve()
         h_x.copy_(xs, non_blocking=True)
     ms_e = timed(solve_e2e, max(1, K // 2))
+    # annealed HQS on the volume: 10 outer steps x 5 PCG iterations, mu 1e-1 -> 1e-3,
+    # built-in Gaussian smoothing (A^H y, 10 DC steps, 10 denoiser calls per run)
+    mu_h = np.geomspace(1e-1, 1e-3, 10).astype(np.float32)
+    xh = torch.zeros_like(x)
+
+    def hqs_run():
+        xh.zero_()
+        hq.hqs_run3d(plan, y, xh, mu_h, mu_h, cg_iters=5, gauss=(1.5, float(mu_h[0])))
+    hqs_run()
+    ms_h = timed(hqs_run, max(1, K // 5))
     clocks = clk.stop()
     if rank != 0:
         return
     cpu = None
-    if world == 1:
+    if world == 1 and not big:
         t_cpu = cpu_oracle_vol_sample(case)
         cpu = {"value": 1.0 / (t_cpu * L), "unit": "A^H(A x) applies/s", "cores": threads_used(), "kind": "oracle",
                "sample": "one coil of one 64^3 gridding forward + adjoint (oracle nufft3d, W=6, 524288 points), "
@@ -936,20 +949,24 @@ def run_vol64(args, rank, world, dist):
     t_us = ms_t * 1e3 / K
     traffic = vol_pass_bytes(shape, L)
     achieved = traffic / (t_us * 1e-6) / 1e9
+    npts = case["traj"].shape[0]
     line = {
-        "metric": "3D DC solves/s to 1e-4 at 64^3, 16 coils (PCG on the 2N^3 Toeplitz A^H A)",
+        "metric": f"3D DC solves/s to 1e-4 at {nv}^3, 16 coils (PCG on the 2N^3 Toeplitz A^H A)",
         "value": nsol * world / (ms_s / 1e3), "unit": "solves/s", "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": ms_s / nsol, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic (seeded ellipsoid phantom, Gaussian-bump coil maps, stack of VD spirals)",
-        "config": {"workload": "64x64x64, 16 coils, stack of 64 spirals x 8 x 1024 (524288 points), KB W=6, "
-                               "sigma=2, mu=1e-2, rel. residual 1e-4, PCG with the 3D density preconditioner",
-                   "l2": "grids (268 MB per Toeplitz pass) larger than L2, no flush"},
+        "config": {"workload": f"{nv}x{nv}x{nv}, 16 coils, stack of {nv} spirals x {16 if big else 8} x 1024 "
+                               f"({npts} points), KB W=6, sigma=2, mu=1e-2, rel. residual 1e-4, PCG with the 3D "
+                               "density preconditioner",
+                   "l2": f"grids ({(2 * nv) ** 3 // 2 * L * 8 // 2 ** 20} MB per Toeplitz pass) larger than L2, "
+                         "no flush"},
         "cg_iterations": info.iterations, "plain_cg_iterations": plain.iterations,
         "plain_cg_solves_per_s": max(1, K // 2) * world / (ms_plain / 1e3), "precond_us": ms_pc * 1e3 / K,
         "forward_us": ms_f * 1e3 / K, "adjoint_us": ms_a * 1e3 / K, "aha_us": t_us,
         "aha_applies_per_s": K * world / (ms_t / 1e3),
+        "hqs_10x5_ms": ms_h / max(1, K // 5),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": HBM_PEAK_GBS, "unit": "GB/s",
-                     "frac": achieved / HBM_PEAK_GBS, "traffic": VOL_AHA_TRAFFIC_BYTES,
+                     "frac": achieved / HBM_PEAK_GBS, "traffic": None if big else VOL_AHA_TRAFFIC_BYTES,
                      "kernel": "the six launches of one A^H A (pass-structure bytes, measured peak)"},
         "e2e": {"value": nsol * world / (ms_e / 1e3), "unit": "solves/s",
                 "h2d_bytes_per_step": int(rhs.numel() * 8), "d2h_bytes_per_step": int(xs.numel() * 8)},
@@ -998,7 +1015,7 @@ def main():
         run_hqs320(args, rank, world, dist)
     elif args.workload == "learned320":
         run_learned320(args, rank, world, dist)
-    elif args.workload == "vol64":
+    elif args.workload in ("vol64", "vol128"):
         run_vol64(args, rank, world, dist)
     else:
         run_ours(args, rank, world, dist)
