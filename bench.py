@@ -842,19 +842,22 @@ def run_learned320(args, rank, world, dist):
     print(json.dumps(line), flush=True)
 
 
-# DRAM bytes (read + write) of the six launches of one 64^3 x 16-coil A^H A, from one ncu capture
-VOL_AHA_TRAFFIC_BYTES = 514025728 + 189041664
+# DRAM bytes (read + write) of the launches of one 64^3 x 16-coil A^H A, from one ncu capture of
+# the current kernels (None until re-measured after a change)
+VOL_AHA_TRAFFIC_BYTES = None
 
 
 def vol_pass_bytes(shape, L):
-    """Bytes the six launches of one 3D Toeplitz A^H A move by their pass
+    """Bytes the launches of one 3D Toeplitz A^H A move by their pass
     structure (each FFT pass reads its input lines and writes its output):
     with U = Nvox L 8 bytes, x-FFT 1U (maps) + 2U, y-FFT 2U + 4U, z-FFT with
-    Khat 4U + 4U, inverse y 4U + 2U, inverse x 2U + 1U (maps) + 1U, coil sum
-    1U; plus x and out (8 Nvox each) and Khat (32 Nvox)."""
+    Khat 4U + 4U, inverse y 4U + 2U, inverse x 2U + 1U (maps); then, with the
+    coil sum fused into the inverse x pass (L divides 16), nothing more, else
+    1U written and read back by the separate coil sum; plus x and out (8 Nvox
+    each) and Khat (32 Nvox)."""
     nvox = shape[0] * shape[1] * shape[2]
     U = nvox * L * 8
-    return 28 * U + 16 * nvox + 32 * nvox
+    return (26 if 16 % L == 0 else 28) * U + 16 * nvox + 32 * nvox
 
 
 def run_vol64(args, rank, world, dist):
@@ -967,7 +970,7 @@ def run_vol64(args, rank, world, dist):
         "hqs_10x5_ms": ms_h / max(1, K // 5),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": HBM_PEAK_GBS, "unit": "GB/s",
                      "frac": achieved / HBM_PEAK_GBS, "traffic": None if big else VOL_AHA_TRAFFIC_BYTES,
-                     "kernel": "the six launches of one A^H A (pass-structure bytes, measured peak)"},
+                     "kernel": "the five launches of one A^H A (pass-structure bytes, measured peak)"},
         "e2e": {"value": nsol * world / (ms_e / 1e3), "unit": "solves/s",
                 "h2d_bytes_per_step": int(rhs.numel() * 8), "d2h_bytes_per_step": int(xs.numel() * 8)},
         # per solve: initial A^H A (6) + init + scalar + preconditioner step (5 + 3), then the

@@ -371,6 +371,7 @@ HQS_DEV int out_index(int pos, int count, int mode, int G) {
     return pos < h ? pos : (pos >= G - h ? pos - G + 2 * h : -1);
 }
 struct StLine {
+    static constexpr bool kReduce = false;
     float2* dst;
     Lines g;
     int count, mode, G;
@@ -383,6 +384,7 @@ struct StLine {
 };
 // last pass with coil weighting: P[(a*nx + o)*L + b] = conj(S) * v
 struct StCoil {
+    static constexpr bool kReduce = false;
     float2* dst;
     const float2* S;
     int nx, L, centred, G;
@@ -396,6 +398,55 @@ struct StCoil {
         if (o < 0) return;
         const int64_t e = (int64_t)o * L;
         t.d[e] = cmulc(t.s[e], v);
+    }
+};
+
+// Last x pass with the coil sum fused: the CTA's kLines lines are kLines / L
+// whole rows (a = z*ny + y) of all L coils (L divides kLines), so after the
+// transform the row's output is reduced over the coils from shared memory:
+// out[a*nx + o] = ca * f(a, o) * sum_l conj(S_l) line_l[pos(o)] + cb * z[a*nx + o],
+// f the deapodisation (apx etc., or 1 without), pos(o) = o or the centred crop.
+// A half-warp per output column, lane j = (row j / L, coil j % L), shuffles
+// over the coil lanes.
+struct StCoilSum {
+    static constexpr bool kReduce = true;
+    float2* out;
+    const float2* S;
+    const float2* z;
+    const float *apx, *apy, *apz;
+    int nx, ny, L, centred, G;
+    float ca, cb;
+    HQS_DEV void reduce(int64_t l0, const float2* s) const {
+        const int hw = threadIdx.x >> 4, nhw = blockDim.x >> 4;
+        const int j = threadIdx.x & 15;
+        const int r = j / L, l = j - r * L;
+        const int64_t a = l0 / L + r;
+        for (int base = 0; base < nx; base += nhw) {
+            const int o = base + hw;
+            float2 v = make_float2(0.f, 0.f);
+            if (o < nx) {
+                const int pos = centred ? (o - (nx >> 1) >= 0 ? o - (nx >> 1) : o - (nx >> 1) + G) : o;
+                v = cmulc(S[(a * nx + o) * L + l], s[pos * kLines + j]);
+            }
+            for (int m = L >> 1; m > 0; m >>= 1) {
+                v.x += __shfl_xor_sync(0xffffffffu, v.x, m);
+                v.y += __shfl_xor_sync(0xffffffffu, v.y, m);
+            }
+            if (o < nx && l == 0) {
+                float f = ca;
+                if (apx) {
+                    const int zz = (int)(a / ny), yy = (int)(a - (int64_t)zz * ny);
+                    f *= apz[zz] * apy[yy] * apx[o];
+                }
+                float2 w = cscale(v, f);
+                if (z) {
+                    const float2 zv = z[a * nx + o];
+                    w.x = fmaf(cb, zv.x, w.x);
+                    w.y = fmaf(cb, zv.y, w.y);
+                }
+                out[a * nx + o] = w;
+            }
+        }
     }
 };
 
@@ -448,8 +499,14 @@ __global__ void k_pass3(LD ld, ST st, MID mid, int64_t nlines, int64_t B, const 
     // threads without a line (ll >= lines) were given line l0 above: they read
     // it (in bounds) and store nothing
     const auto lds = ld.prepare(a, b);
-    const auto sts = st.prepare(a, b);
     auto load = [&](int, int pos, bool) { return ld(lds, pos); };
+    if constexpr (ST::kReduce) {
+        static_assert(std::is_same_v<MID, NoMid>, "the coil-sum store ends a plain pass");
+        block_fft_io_tab<FftSizeV, N, INV, ZIN, HOUT>(s, lines, tw, load, NoIO{}, NoIO{});   // ends with a barrier
+        st.reduce(l0, s);
+        return;
+    } else {
+    const auto sts = st.prepare(a, b);
     auto store = [&](int, int pos, float2 v) { st.put(sts, pos, v); };
     if constexpr (std::is_same_v<MID, NoMid>) {
         block_fft_io_tab<FftSizeV, N, INV, ZIN, HOUT>(s, lines, tw, load, NoIO{}, store);
@@ -458,6 +515,7 @@ __global__ void k_pass3(LD ld, ST st, MID mid, int64_t nlines, int64_t B, const 
         auto xf = [&](int, int pos, float2 v) { return mid(mds, pos, v); };
         block_fft_io_tab<FftSizeV, N, false, ZIN, false>(s, lines, tw, load, xf, NoIO{});
         block_fft_io_tab<FftSizeV, N, true, false, HOUT>(s, lines, tw, NoIO{}, NoIO{}, store);
+    }
     }
 }
 
@@ -987,7 +1045,15 @@ int adj3(hqs_plan3d_s* p, const float2* y, float2* x, cudaStream_t s) {
     TRY3((run_pass<true, false, false>(p, Gy, LdLine{p->bufB, {plane, row}, Gy},
                                        StLine{p->bufA, {(int64_t)ny * row, row}, ny, 1, Gy}, (int64_t)nz * row,
                                        row, s)));
-    // x: conj(S_l) per coil, [nz][ny][nx][L] in bufC
+    // x: conj(S_l) coil sum and deapodisation fused where the CTA holds whole rows,
+    // else per coil into bufC and a separate sum
+    if (kLines % L == 0) {
+        TRY3((run_pass<true, false, false>(
+            p, Gx, LdLine{p->bufA, {row, L}, Gx},
+            StCoilSum{x, p->smaps, nullptr, p->apod[0], p->apod[1], p->apod[2], nx, ny, L, 1, Gx, p->scale, 0.f},
+            (int64_t)nz * ny * L, L, s)));
+        return HQS_OK;
+    }
     TRY3((run_pass<true, false, false>(p, Gx, LdLine{p->bufA, {row, L}, Gx},
                                        StCoil{p->bufC, p->smaps, nx, L, 1, Gx}, (int64_t)nz * ny * L, L, s)));
     const int64_t nvox = (int64_t)nx * ny * nz;
@@ -1015,7 +1081,14 @@ int toep3(hqs_plan3d_s* p, const float2* x, float2* out, float ca, float cb, con
     TRY3((run_pass<true, false, true>(p, Ty, LdLine{p->bufB, {plane, row}, Ty},
                                       StLine{p->bufA, {(int64_t)ny * row, row}, ny, 0, Ty}, (int64_t)nz * row, row,
                                       s)));
-    // x inverse: conj(S_l) per coil in bufC
+    // x inverse with the conj(S_l) coil sum fused (whole rows per CTA), else per coil in bufC + sum
+    if (kLines % L == 0) {
+        TRY3((run_pass<true, false, true>(
+            p, Tx, LdLine{p->bufA, {row, L}, Tx},
+            StCoilSum{out, p->smaps, z, nullptr, nullptr, nullptr, nx, ny, L, 0, Tx, ca, cb},
+            (int64_t)nz * ny * L, L, s)));
+        return HQS_OK;
+    }
     TRY3((run_pass<true, false, true>(p, Tx, LdLine{p->bufA, {row, L}, Tx}, StCoil{p->bufC, p->smaps, nx, L, 0, Tx},
                                       (int64_t)nz * ny * L, L, s)));
     const int64_t nvox = (int64_t)nx * ny * nz;
