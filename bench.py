@@ -973,9 +973,10 @@ def run_vol64(args, rank, world, dist):
                      "kernel": "the five launches of one A^H A (pass-structure bytes, measured peak)"},
         "e2e": {"value": nsol * world / (ms_e / 1e3), "unit": "solves/s",
                 "h2d_bytes_per_step": int(rhs.numel() * 8), "d2h_bytes_per_step": int(xs.numel() * 8)},
-        # per solve: initial A^H A (6) + init + scalar + preconditioner step (5 + 3), then the
-        # 18-kernel iteration graph replayed in chunks of 4 (replays past convergence return at once)
-        "gpu_launches": nsol * (16 + 18 * 4 * math.ceil(info.iterations / 4)), "clocks": clocks,
+        # per solve: initial A^H A (5: coil sum fused at 16 coils) + init + scalar + preconditioner
+        # step (5 + 3), then the 17-kernel iteration graph replayed in chunks of 4 (replays past
+        # convergence return at once)
+        "gpu_launches": nsol * (15 + 17 * 4 * math.ceil(info.iterations / 4)), "clocks": clocks,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)
