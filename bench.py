@@ -844,7 +844,7 @@ def run_learned320(args, rank, world, dist):
 
 # DRAM bytes (read + write) of the launches of one 64^3 x 16-coil A^H A, from one ncu capture of
 # the current kernels (None until re-measured after a change)
-VOL_AHA_TRAFFIC_BYTES = None
+VOL_AHA_TRAFFIC_BYTES = 480437760 + 181145600
 
 
 def vol_pass_bytes(shape, L):
