@@ -29,6 +29,7 @@ __all__ = [
     "complex_noise", "noise_scale_snr", "noise_scale_image_rule",
     "mu_schedule_geometric", "paper_schedule", "tiny_case", "brain_case",
     "odd_case", "phantom3d", "coil_maps3d", "traj_stack_of_spirals", "volume_case",
+    "traj_spiral_frames", "dynamic_phantom",
 ]
 
 
@@ -307,3 +308,34 @@ def volume_case(seed: int = 0, shape=(64, 64, 64), L: int = 16, n_interleaves: i
     traj = traj_stack_of_spirals(nz, n_interleaves, n_samples, max(ny, nx))
     return dict(shape=tuple(shape), L=L, W=W, sigma=2.0, x=phantom3d(seed, shape),
                 smaps=coil_maps3d(seed, shape, L), traj=traj)
+
+
+# ----------------------------------------------------------------- 2D + time
+def traj_spiral_frames(n_frames: int, n_interleaves: int, n_samples: int, n: int,
+                       accel: float = 8.0):
+    """Per-frame trajectories of a dynamic (2D + time) acquisition: frame t
+    holds the traj_spiral pattern rotated by t times the golden angle, so
+    consecutive frames sample complementary k-space.  List of float32 (M, 2)."""
+    base = traj_spiral(n_interleaves, n_samples, n, accel).astype(np.float64)
+    kxy = base[:, 0] + 1j * base[:, 1]
+    golden = math.pi * (3.0 - math.sqrt(5.0))
+    out = []
+    for t in range(n_frames):
+        r = kxy * np.exp(1j * golden * t)
+        out.append(np.stack([_wrap_pi(r.real), _wrap_pi(r.imag)], axis=1).astype(np.float32))
+    return out
+
+
+def dynamic_phantom(seed: int, n: int, n_frames: int) -> np.ndarray:
+    """Frames (T, n, n) complex128: the phantom of `seed` plus a bright disc
+    (radius 0.12, amplitude 0.5) moving on a circle of radius 0.25 half-FOV
+    units, one turn over the T frames."""
+    base = phantom(seed, n)
+    c = _grid_coords(n)
+    X, Y = np.meshgrid(c, c, indexing="xy")
+    out = np.empty((n_frames, n, n), dtype=np.complex128)
+    for t in range(n_frames):
+        ang = 2 * math.pi * t / n_frames
+        disc = ((X - 0.25 * math.cos(ang)) ** 2 + (Y - 0.25 * math.sin(ang)) ** 2) <= 0.12 ** 2
+        out[t] = base + 0.5 * disc
+    return out
