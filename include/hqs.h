@@ -464,6 +464,15 @@ HQS_API int hqs_run3d(hqs_plan3d plan, const hqs_c64* y, hqs_c64* x, const float
                       int K, int k0, int cg_iters, float c0, float c1, hqs_denoiser3d_fn denoiser,
                       void* user, void* stream);
 
+/* Diagnostics (no counterpart in the paper): phase trace of the batched
+ * solve (hqs_batch_dc_solve), same protocol as hqs_debug_phase_trace below:
+ * enable = 1 allocates the buffer (returns 0); enable = 0 synchronises
+ * `stream` and copies up to max_out globaltimer stamps (ns) of the last
+ * batched solve to out (host): the start, one stamp after every grid
+ * barrier, and the end.  Returns the number of stamps. */
+HQS_API int hqs_batch_debug_trace(hqs_batch batch, int enable, unsigned long long* out, int max_out,
+                                  void* stream);
+
 /* Diagnostics (no counterpart in the paper): phase trace of the persistent
  * solve.  enable = 1 allocates a trace buffer on the plan (returns 0); later
  * calls with enable = 0 synchronise `stream` and copy up to max_out

@@ -126,6 +126,7 @@ _SIGS = {
                                             C.c_void_p, C.c_void_p]),
     "hqs_debug_phase_trace": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_ulonglong), C.c_int,
                                         C.c_void_p]),
+    "hqs_batch_debug_trace": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_ulonglong), C.c_int, C.c_void_p]),
     "hqs_plan3d_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_int,
                                     C.c_int, C.c_void_p, C.c_int, C.c_float, C.c_void_p]),
     "hqs_plan3d_destroy": (None, [C.c_void_p]),
@@ -567,6 +568,15 @@ class Batch:
         _check(library().hqs_batch_dc_solve(self.handle, rp, xp, float(a), float(b), int(max_iter),
                                             float(rel_tol), _stream(stream)), "hqs_batch_dc_solve")
         return xs
+
+    def debug_trace(self, enable=False, stream=None):
+        """enable=True arms the batched solve's phase trace; enable=False
+        returns the globaltimer stamps (ns) of the last batched solve."""
+        buf = (C.c_ulonglong * 4096)()
+        rc = library().hqs_batch_debug_trace(self.handle, 1 if enable else 0, buf, 4096, _stream(stream))
+        if rc < 0:
+            raise HqsError(rc, "hqs_batch_debug_trace")
+        return [buf[i] for i in range(rc)]
 
     def dc_info(self, stream=None):
         """Per slice (iterations, relative residual, status) of the last batched solve."""

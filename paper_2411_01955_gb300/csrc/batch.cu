@@ -484,6 +484,8 @@ struct DcBatchArgs {
     int* status;            // [ns] HQS_OK / HQS_ERR_NOT_CONVERGED / HQS_ERR_BREAKDOWN
     unsigned* bar;
     unsigned* err;
+    unsigned long long* trace;   // optional: globaltimer stamp at the start, after each grid barrier, at the end
+    int trace_max;
 };
 
 __global__ void __launch_bounds__(HQS_BATCH_BD, 2) k_pcg_batch(DcBatchArgs B) {
@@ -498,9 +500,16 @@ __global__ void __launch_bounds__(HQS_BATCH_BD, 2) k_pcg_batch(DcBatchArgs B) {
     const int ns = B.ns, G = gridDim.x, bid = blockIdx.x;
     const float a = B.a, bcoef = B.b;
     const float2* twN = nullptr;
-#define BB_BARRIER()                                \
-    do {                                            \
-        if (!grid_barrier(B.bar, B.err)) return;    \
+    // optional phase trace, kept by thread 0 of CTA 0 (count in shared memory: no registers)
+    __shared__ int ntr;
+    if (B.trace && bid == 0 && threadIdx.x == 0) {
+        ntr = 0;
+        if (B.trace_max > 0) B.trace[ntr++] = global_ns();
+    }
+#define BB_BARRIER()                                                                         \
+    do {                                                                                     \
+        if (!grid_barrier(B.bar, B.err)) return;                                             \
+        if (B.trace && bid == 0 && threadIdx.x == 0 && ntr < B.trace_max) B.trace[ntr++] = global_ns(); \
     } while (0)
 #define FOR_ITEMS(list, ...)                                                               \
     {                                                                                      \
@@ -710,6 +719,10 @@ __global__ void __launch_bounds__(HQS_BATCH_BD, 2) k_pcg_batch(DcBatchArgs B) {
             B.iters[i] = its[i];
             B.status[i] = stat[i];
         }
+    if (B.trace && bid == 0 && threadIdx.x == 0) {
+        if (ntr < B.trace_max) B.trace[ntr++] = global_ns();
+        B.trace[B.trace_max] = ntr;
+    }
 #undef BB_BARRIER
 #undef FOR_ITEMS
 #undef STAGE_TWN
@@ -751,6 +764,7 @@ struct hqs_batch_s {
     int* d_iters = nullptr;
     int* d_status = nullptr;
     std::vector<const void*> dc_key;
+    unsigned long long* d_trace = nullptr;   // optional phase trace of the batched solve
 };
 
 static void batch_free(hqs_batch_s* b) {
@@ -774,6 +788,7 @@ static void batch_free(hqs_batch_s* b) {
     cudaFree(b->d_slices_dc);
     cudaFree(b->d_iters);
     cudaFree(b->d_status);
+    cudaFree(b->d_trace);
     delete b;
 }
 
@@ -1024,6 +1039,8 @@ extern "C" int hqs_batch_dc_solve(hqs_batch b, const hqs_c64* const* rhs, hqs_c6
     A.status = b->d_status;
     A.bar = b->d_bar;
     A.err = b->d_err;
+    A.trace = b->d_trace;
+    A.trace_max = b->d_trace ? HQS_TRACE_MAX : 0;
     const size_t sm = kBatchSmemF2 * sizeof(float2);
     HQS_CUDA_TRY(cudaFuncSetAttribute(k_pcg_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     int per_sm = 0, nsm = 0;
@@ -1053,4 +1070,22 @@ extern "C" int hqs_batch_dc_info(hqs_batch b, int* iterations, double* rel_resid
         if (status) status[i] = stt[i];
     }
     return (err & HQS_DEVERR_TIMEOUT) ? HQS_ERR_TIMEOUT : HQS_OK;
+}
+
+extern "C" int hqs_batch_debug_trace(hqs_batch b, int enable, unsigned long long* out, int max_out, void* stream) {
+    if (!b) return HQS_ERR_INVALID_ARG;
+    if (enable && !b->d_trace) {
+        HQS_CUDA_TRY(cudaMalloc(&b->d_trace, (HQS_TRACE_MAX + 1) * sizeof(unsigned long long)));
+        HQS_CUDA_TRY(cudaMemset(b->d_trace, 0, (HQS_TRACE_MAX + 1) * sizeof(unsigned long long)));
+        return 0;
+    }
+    if (!b->d_trace) return 0;
+    std::vector<unsigned long long> h(HQS_TRACE_MAX + 1);
+    HQS_CUDA_TRY(cudaMemcpyAsync(h.data(), b->d_trace, h.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                 (cudaStream_t)stream));
+    HQS_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    const int cnt = (int)std::min<unsigned long long>(h[HQS_TRACE_MAX], HQS_TRACE_MAX);
+    if (out)
+        for (int i = 0; i < cnt && i < max_out; ++i) out[i] = h[i];
+    return cnt;
 }
