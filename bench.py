@@ -76,7 +76,7 @@ ADJ_BYTES = (_Y + _PTS + _G2L) + (_G2L + _ROWS) + (_ROWS + _S + 320 * 320 * 8)
 # the kernel has changed since the last capture.
 PERSISTENT_TRAFFIC_BYTES = 16408576 + 2208768
 # The same for one k_pcg_batch launch (all 16 slices of a default step); None until captured.
-BATCH_TRAFFIC_BYTES = 49036934144 + 32612910080
+BATCH_TRAFFIC_BYTES = 49290943744 + 32896723968
 
 
 def parse():
@@ -88,6 +88,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="batched", choices=["batched", "fused", "plain"])
     ap.add_argument("--group", type=int, default=64, help="slices per batched launch (at most 64)")
+    ap.add_argument("--phase-trace", action="store_true",
+                    help="batched dc320: add the per-phase time of one traced batched solve to the line")
     ap.add_argument("--workload", default="dc320",
                     choices=["dc320", "batch64", "mixed320", "hqs320", "learned320", "vol64", "vol128"])
     return ap.parse_args()
@@ -408,6 +410,9 @@ def run_ours(args, rank, world, dist):
     h2d = sum(int(y.numel()) * 8 for y in ys)
     d2h = sum(int(x.numel()) * 8 for x in xs)
 
+    phases = None
+    if args.phase_trace and args.mode == "batched":
+        phases = batch_phase_trace(batches[0], [rhss[i] for i in groups[0]], [xs[i] for i in groups[0]], hq)
     if rank != 0:
         return
     # roofline of the persistent solve: FP32 ALU work per launch / duration
@@ -460,7 +465,32 @@ def run_ours(args, rank, world, dist):
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
     }
+    if phases is not None:
+        line["phase_trace_us"] = phases
     print(json.dumps(line), flush=True)
+
+
+BATCH_PHASES = ["p_update", "rows_fwd", "cols", "rows_adj", "epilogue", "update_pc_rows", "pc_cols_rz"]
+
+
+def batch_phase_trace(bt, rhs, xs, hq):
+    """One batched solve with the kernel's phase trace armed (outside the timed
+    region): mean microseconds per CG iteration of each phase between grid
+    barriers, over all iterations of the launch, plus the set-up phases."""
+    for x in xs:
+        x.zero_()
+    bt.debug_trace(True)
+    bt.dc_solve(rhs, xs, 1.0, MU, max_iter=MAX_ITER, rel_tol=TOL)
+    st = bt.debug_trace(False)
+    d = np.diff(np.array(st, dtype=np.float64)) / 1e3
+    body = d[3:-1]
+    out = {"setup": [round(float(v), 1) for v in d[:3]], "iterations": int(math.ceil(len(body) / 7))}
+    for k, name in enumerate(BATCH_PHASES):
+        v = body[k::7]
+        if len(v):
+            out[name] = round(float(np.mean(v)), 1)
+    out["total_ms"] = round(float((st[-1] - st[0]) / 1e6), 3)
+    return out
 
 
 def make_batch64(rank=0, count=64):
