@@ -249,8 +249,10 @@ __global__ void __launch_bounds__(HQS3_SPREAD_WARPS * 32)
     __syncthreads();   // loc and wts are read by other threads below
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ox = bx * TB - W / 2, oy = by * TB - W / 2, oz = bz * TB - W / 2;
-    constexpr int W2 = W * W;
-    const int E = W2 << lcs;     // (cell, coil) entries of one footprint plane
+    // lane -> (x tap b, coil l) of a footprint row; W * LC <= 32 (LC = 4 needs W <= 6,
+    // the launcher uses LC <= 2 above that)
+    const bool has_tap = lane < (W << lcs);
+    const int lb = lane >> lcs, ll = lane & ((1 << lcs) - 1);
     for (int ch = blockIdx.y; ch < nchunk; ch += gridDim.y) {
         const int l0 = ch * LC;
         const int lines = min(LC, L - l0);
@@ -265,19 +267,21 @@ __global__ void __launch_bounds__(HQS3_SPREAD_WARPS * 32)
         for (int i = 0; i < cnt; ++i) {
             const int4 c0 = loc[i];
             const int c = ((warp - c0.z) % HQS3_SPREAD_WARPS + HQS3_SPREAD_WARPS) % HQS3_SPREAD_WARPS;
-            if (c < W) {
+            if (c < W && has_tap) {
+                // this lane's (b, l): the value times the z and x weights once, then down
+                // the W rows of the plane
                 const float* wv = wts + i * 3 * W;
-                const float wz = wv[2 * W + c];
-                float2* plane = patch + (((c0.z + c) * P + c0.y) * P + c0.x) * LC;
-                for (int e = lane; e < E; e += 32) {
-                    const int l = e & (LC - 1), cell = e >> lcs;
-                    const int a = cell / W, b = cell - a * W;
-                    const float w = wz * wv[W + a] * wv[b];
-                    const float2 v = vals[(i << lcs) + l];
-                    float2* dst = plane + ((a * P + b) << lcs) + l;
+                const float wzx = wv[2 * W + c] * wv[lb];
+                const float2 v = vals[(i << lcs) + ll];
+                const float2 t = make_float2(v.x * wzx, v.y * wzx);
+                float2* col = patch + ((((c0.z + c) * P + c0.y) * P + c0.x + lb) << lcs) + ll;
+#pragma unroll
+                for (int a = 0; a < W; ++a) {
+                    const float wy = wv[W + a];
+                    float2* dst = col + ((a * P) << lcs);
                     float2 acc = *dst;
-                    acc.x = fmaf(w, v.x, acc.x);
-                    acc.y = fmaf(w, v.y, acc.y);
+                    acc.x = fmaf(wy, t.x, acc.x);
+                    acc.y = fmaf(wy, t.y, acc.y);
                     *dst = acc;
                 }
             }
@@ -983,8 +987,9 @@ int spread3(const Points3& pts, const float2* y, int64_t M, const int G[3], int 
     return dispatch_w3(W, [&]<int WW>() {
         const int P = HQS3_TILE + WW - 1;
         const size_t cell_bytes = (size_t)P * P * P * sizeof(float2);
-        // coils per chunk: 4, or 2 where a 4-coil patch would exceed 72 KB, or 1 for one coil
-        int lcs = cell_bytes * 4 <= 72 * 1024 ? 2 : 1;
+        // coils per chunk: 4, or 2 where a 4-coil patch would exceed 72 KB or the
+        // W x 4 (tap, coil) lanes a warp (W > 6), or 1 for one coil
+        int lcs = (cell_bytes * 4 <= 72 * 1024 && WW <= 6) ? 2 : 1;
         while (lcs > 0 && (1 << (lcs - 1)) >= L) --lcs;
         const int nch = ceil_div(L, 1 << lcs);
         const size_t sm = HQS3_MAXPTS * sizeof(int4) + HQS3_MAXPTS * 3 * WW * sizeof(float) +
