@@ -42,3 +42,29 @@ def test_invalid_arguments_are_rejected_without_a_gpu():
                                ctypes.c_float(2.0), None) == -1
     assert lib.hqs_plan_create(None, None, ctypes.c_int64(0), 32, 32, 4, None, 4, ctypes.c_float(2.0), None) == -1
     assert lib.hqs_forward(None, None, None, None) == -1
+
+
+def test_volume_arguments_are_rejected_without_a_gpu():
+    """The volumetric plan validates sizes, widths, oversampling and pointers
+    before any CUDA call; the operators reject a null plan."""
+    from paper_2411_01955_gb300 import build
+    lib = ctypes.CDLL(build.build())
+    h = ctypes.c_void_p(123)
+    fake = ctypes.c_void_p(0x1000)   # never dereferenced: validation fails first
+    two = ctypes.c_float(2.0)
+    # sizes: 24 (48 is no transform size), 4 (too small), odd; width 3 and 9; oversampling 1.5; coils 0
+    for nz, ny, nx in [(8, 16, 24), (4, 16, 16), (8, 15, 16)]:
+        assert lib.hqs_plan3d_create(ctypes.byref(h), None, ctypes.c_int64(0), nz, ny, nx, 2, fake, 6, two,
+                                     None) == -1
+        assert h.value is None
+        h = ctypes.c_void_p(123)
+    for L, W, sg in [(2, 3, 2.0), (2, 9, 2.0), (2, 6, 1.5), (0, 6, 2.0)]:
+        assert lib.hqs_plan3d_create(ctypes.byref(h), None, ctypes.c_int64(0), 8, 16, 16, L, fake, W,
+                                     ctypes.c_float(sg), None) == -1
+    # points without a trajectory, maps missing, no output handle
+    assert lib.hqs_plan3d_create(ctypes.byref(h), None, ctypes.c_int64(10), 8, 16, 16, 2, fake, 6, two, None) == -1
+    assert lib.hqs_plan3d_create(ctypes.byref(h), None, ctypes.c_int64(0), 8, 16, 16, 2, None, 6, two, None) == -1
+    assert lib.hqs_plan3d_create(None, None, ctypes.c_int64(0), 8, 16, 16, 2, fake, 6, two, None) == -1
+    for fn in ("hqs_forward3d", "hqs_adjoint3d", "hqs_toeplitz_normal3d"):
+        assert getattr(lib, fn)(None, fake, fake, None) == -1
+    assert lib.hqs_precond_apply3d(None, ctypes.c_float(1.0), ctypes.c_float(0.1), fake, fake, None) == -1
