@@ -250,3 +250,33 @@ def test_hqs_on_a_one_slice_volume_is_the_2d_run():
     x3, _, _ = hqs.hqs(lambda v: nufft3d.normal(v, S[:, None], K3), b3, np.zeros((1, ny, nx)), mu, sg, K,
                        cg_iters=4, lam=lam3, precond_apply=nufft3d.precond_apply)
     assert rel(x3[0], x2) < 1e-12
+
+
+def test_hqs3d_fixed_point_linear_shrink_prop1():
+    # Proposition 1 on a volume: D(v) = v/(1+tau) is the prox of (tau/2)||.||^2, so with
+    # P = Id and constant mu the u-iterate converges to u* solving
+    # (A^H A + mu tau/(1+tau) I) u = A^H y, and x* = u*/(1+tau); the system is formed
+    # densely from the exact NUDFT and solved by the library solver
+    rng = np.random.default_rng(23)
+    shape, L, M = (4, 6, 6), 2, 120
+    nvox = int(np.prod(shape))
+    S = rand_c(rng, (L,) + shape)
+    traj = rand_traj(rng, M)
+    y = rand_c(rng, (L, M))
+    c = nufft3d.kernel(traj, shape)
+    Kh, lam = nufft3d.khat(c), nufft3d.chan_symbol(c, shape)
+    AHA = lambda v: nufft3d.normal(v, S, Kh)
+    b0 = nufft3d.nudft_adjoint(y, S, traj)
+    mu, tau, K = 0.05, 0.5, 150
+    D = lambda u, s: u / (1 + tau)
+    # more inner CG iterations than unknowns: every DC step is solved exactly
+    x, u, _ = hqs.hqs(AHA, b0, np.zeros(shape), [mu] * K, [1.0] * K, K, cg_iters=nvox + 16, denoiser=D, lam=lam,
+                      precond_apply=nufft3d.precond_apply)
+    H = np.zeros((nvox, nvox), dtype=np.complex128)
+    for i in range(nvox):
+        e = np.zeros(nvox, dtype=np.complex128)
+        e[i] = 1
+        H[:, i] = (nufft3d.nudft_normal(e.reshape(shape), S, traj) + mu * tau / (1 + tau) * e.reshape(shape)).ravel()
+    ustar = np.linalg.solve(H, b0.ravel()).reshape(shape)
+    assert rel(u, ustar) < 1e-8
+    assert rel(x, ustar / (1 + tau)) < 1e-8
