@@ -779,6 +779,27 @@ def run_hqs320(args, rank, world, dist):
         ms = max_over_ranks(e0.elapsed_time(e1), dist)
         res["pgd_" + name] = {"pgd_runs_per_s": whole_job_rate(B * args.steps, world, ms),
                               "ms_per_run": ms / (B * args.steps), "c0": c0, "c1": c1}
+    # the two other pieces of a reconstruction run here: S-map estimation from the
+    # 20 x 20 Hamming-windowed k-space centre (once per scan) and the GPU conv denoiser
+    # D_sigma (once per outer step in place of the Gaussian smoothing)
+    from paper_2411_01955_gb300 import learned
+    smaps_out = torch.empty((L, n, n), dtype=torch.complex64, device="cuda")
+    net = hq.Net()
+    net.set_params(learned.initial_params(0))
+    den_out = torch.empty_like(xs[0])
+
+    def timed_ms(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return max_over_ranks(e0.elapsed_time(e1), dist) / reps
+    smaps_ms = timed_ms(lambda: hq.estimate_smaps(traj, ys[0], n, smaps_out), max(args.steps, 3))
+    denoise_ms = timed_ms(lambda: net.denoise(xs[0], den_out, 0.05), 10 * max(args.steps, 3))
     clocks = clk.stop()
     if rank != 0:
         return
@@ -791,6 +812,7 @@ def run_hqs320(args, rank, world, dist):
                                "mu 1e-1 -> 1e-3, Gaussian smoothing denoiser, DC-preconditioned CG",
                    "batch_per_gpu": B, "alpha": alpha},
         "metrics": res, "clocks": clocks,
+        "smaps_estimation_ms": smaps_ms, "conv_denoiser_ms": denoise_ms,
     }
     print(json.dumps(line), flush=True)
 
