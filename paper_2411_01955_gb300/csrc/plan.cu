@@ -424,7 +424,7 @@ static int plan_build(hqs_plan_s* p, const float* traj, const float2* smaps_user
 
         // Toeplitz kernel, its FFT (Khat, real, scaled by 1/n2^2) and the density symbol
         dim3 gg(ceil_div(n2, 64), ceil_div(n2, 64));
-        if (M > 0) {
+        if (M > 0 && !p->nufft_only) {
             k_toeplitz_kernel<<<gg, 256, 0, s>>>(phase, M, n, n2, 1.0 / ((double)n * n), cbuf);
         } else if (cudaMemsetAsync(cbuf, 0, (size_t)n2 * n2 * sizeof(float2), s)) {
             rc = HQS_ERR_CUDA;
@@ -448,6 +448,11 @@ static int plan_build(hqs_plan_s* p, const float* traj, const float2* smaps_user
 extern "C" int hqs_plan_create(hqs_plan* out, const float* traj, int64_t M, int ny, int nx,
                                int coils, const hqs_c64* smaps, int kernel_width, float oversamp,
                                void* stream) {
+    return plan_create_internal(out, traj, M, ny, nx, coils, smaps, kernel_width, oversamp, stream, false);
+}
+
+int plan_create_internal(hqs_plan* out, const float* traj, int64_t M, int ny, int nx, int coils,
+                         const hqs_c64* smaps, int kernel_width, float oversamp, void* stream, bool nufft_only) {
     if (!out) return HQS_ERR_INVALID_ARG;
     *out = nullptr;
     if (ny != nx || ny <= 0 || coils <= 0 || coils > 64 || M < 0 || M > (int64_t)1 << 30)
@@ -473,6 +478,7 @@ extern "C" int hqs_plan_create(hqs_plan* out, const float* traj, int64_t M, int 
     p->beta = M_PI * sqrt(bsq * bsq - 0.8);
     p->M = M;
     p->scale = (float)(1.0 / ny);
+    p->nufft_only = nufft_only;
     int rc = plan_build(p, traj, reinterpret_cast<const float2*>(smaps), (cudaStream_t)stream);
     if (rc != HQS_OK) {
         plan_free(p);

@@ -48,6 +48,7 @@ struct hqs_plan_s {
     int tile = 16, nbx = 0, nsub = 0;
     int q_rows = 8;     // lines per CTA in the single-image FFT passes
     int fused_grid = 0; // cap on the persistent solver's CTAs (0: occupancy limit)
+    bool nufft_only = false; // internal plans that only grid (no Toeplitz kernel, density symbol zero)
     int pc_lines = 4;   // preconditioner lines per item in the persistent solver (1..16)
 
     // constant tables and plan data (device)
@@ -93,6 +94,11 @@ struct hqs_plan_s {
 };
 
 const float2* plan_twiddles(const hqs_plan_s* p, int N);
+// hqs_plan_create; with nufft_only the plan serves hqs_forward / hqs_adjoint only:
+// its Toeplitz kernel and density symbol are left zero (for internal helpers such as
+// the S-map estimation, which grids one coil at a time)
+int plan_create_internal(hqs_plan* out, const float* traj, int64_t M, int ny, int nx, int coils,
+                         const hqs_c64* smaps, int kernel_width, float oversamp, void* stream, bool nufft_only);
 void mixed_free(hqs_plan_s* p);
 
 // launchers implemented in the kernel translation units

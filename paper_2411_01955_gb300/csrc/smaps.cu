@@ -81,8 +81,9 @@ extern "C" int hqs_estimate_smaps(const float* traj, int64_t M, const hqs_c64* y
             break;
         }
         k_fill_one<<<ceil_div(count, 256), 256, 0, st>>>(ones, count);
-        rc = hqs_plan_create(&plan, traj, M, n, n, 1, reinterpret_cast<const hqs_c64*>(ones), kernel_width, oversamp,
-                             stream);
+        // a gridding-only plan: the estimate needs the adjoint, not the Toeplitz kernel
+        rc = plan_create_internal(&plan, traj, M, n, n, 1, reinterpret_cast<const hqs_c64*>(ones), kernel_width,
+                                  oversamp, stream, true);
         if (rc != HQS_OK) break;
         float2* out = reinterpret_cast<float2*>(smaps);
         const float2* yy = reinterpret_cast<const float2*>(y);
