@@ -50,6 +50,8 @@ import numpy as np
 
 METRIC = "A^H A applies/s and DC solves/s to 1e-4 residual at 320², 16 coils vs plain PCG"
 UNIT = "solves/s"
+WORKLOAD = ("brain-sized DC solve: 320x320, 16 coils, spiral 16x2048 (32768 pts), KB W=6, sigma=2, mu=1e-2, "
+            "rel. residual 1e-4, DC-preconditioned CG")
 MU = 1e-2
 TOL = 1e-4
 MAX_ITER = 200
@@ -57,8 +59,31 @@ MAX_ITER = 200
 # a run so the shapes are timed on the GPU that runs it).
 TUNE_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), ".bench_tune_cache.json")
 
-# Measured copy bandwidth of the GB300s (MEASURED_PEAKS.json, hbm_gbs).
-HBM_PEAK_GBS = 6768.8
+
+
+def read_peaks():
+    """Roofline denominators: the measured HBM copy bandwidth and BF16 GEMM
+    rates in MEASURED_PEAKS.json at the repository root, or the earlier
+    GB300 measurement (6.8 TB/s, 1.9 / 1.7 PFLOP/s) when that file is absent."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return {"hbm_gbs": float(p["hbm_gbs"]), "bf16_tflops": float(p["bf16_tflops"]),
+                "bf16_tflops_sustained": float(p.get("bf16_tflops_sustained", p["bf16_tflops"])),
+                "source": "measured"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
+
+
+PEAKS = read_peaks()
+HBM_PEAK_GBS = PEAKS["hbm_gbs"]
+# FP32 ALU peak from the unit counts: 152 SMs x 128 FP32 lanes x 2 flop (FMA) per clock
+FP32_LANES = 152 * 128
+
+
+def fp32_peak_tflops(sm_mhz: float) -> float:
+    return FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
 # Algorithmic bytes of one forward / adjoint at 320^2, 16 coils, G = 640, M = 32768
 # (complex64 = 8 B): forward = x + S (fused apodise/coil/pad/row-FFT pass) + grid
 # write, column FFT read + write, interpolation read + points + y write;
@@ -178,27 +203,38 @@ def make_slices(B, rank=0):
     return n, L, traj, slices
 
 
-def cpu_oracle_sample(n_iter=2):
-    """The FP64 oracle on the host cores: plan (Toeplitz kernel, density
-    symbol) for one slice, then n_iter preconditioned CG iterations; returns
-    seconds per CG iteration and the plan time."""
-    import synth
-    from oracle import nufft, solvers, toeplitz
-    n, L, traj, sl = make_slices(1)
-    s = sl[0]
-    t0 = time.perf_counter()
-    c = toeplitz.kernel(traj, n, n)
-    Kh = toeplitz.khat(c)
-    lam = toeplitz.chan_symbol(c, n, n)
-    t_plan = time.perf_counter() - t0
-    AHA = lambda v: toeplitz.normal(v, s["smaps"], Kh)
-    rhs = AHA(s["x"])
-    H = lambda v: AHA(v) + MU * v
-    Minv = lambda v: toeplitz.precond_apply(v, lam, 1.0, MU)
-    t0 = time.perf_counter()
-    solvers.pcg(H, rhs, np.zeros((n, n)), Minv, max_iter=n_iter, tol=0.0)
-    t_it = (time.perf_counter() - t0) / (n_iter + 1)   # +1: the initial residual apply
-    return t_it, t_plan
+class OracleStep:
+    """One step of the benchmark's workload in the FP64 oracle, for one slice
+    (the first slice of the GPU step, the same seeded inputs): rhs = A^H y +
+    mu z by the gridding adjoint, then DC-preconditioned CG from zero to
+    relative residual 1e-4, counting its iterations.  Setting up (the
+    Toeplitz kernel and density symbol, y and z) is not timed."""
+
+    def __init__(self):
+        from oracle import hqs as ohqs
+        from oracle import nufft, toeplitz
+        self.nufft, self.toeplitz = nufft, toeplitz
+        n, L, traj, sl = make_slices(1)
+        s = sl[0]
+        self.n, self.traj, self.S = n, traj, s["smaps"]
+        t0 = time.perf_counter()
+        c = toeplitz.kernel(traj, n, n)
+        self.Kh, self.lam = toeplitz.khat(c), toeplitz.chan_symbol(c, n, n)
+        self.t_plan = time.perf_counter() - t0
+        y = nufft.forward(s["x"], self.S, traj, 6, 2.0)
+        sd = math.sqrt(1e-4 * float(np.max(np.sum(np.abs(self.S * s["x"]) ** 2, axis=0))))
+        self.y = y + sd * s["noise"]
+        self.z = ohqs.gaussian_denoise(nufft.adjoint(self.y, self.S, traj, 6, 2.0), 1.0)
+
+    def __call__(self):
+        """Runs one step; returns (seconds, CG iterations)."""
+        from oracle import solvers
+        t0 = time.perf_counter()
+        rhs = self.nufft.adjoint(self.y, self.S, self.traj, 6, 2.0) + MU * self.z
+        H = lambda v: self.toeplitz.normal(v, self.S, self.Kh) + MU * v
+        M = lambda v: self.toeplitz.precond_apply(v, self.lam, 1.0, MU)
+        _, info = solvers.pcg(H, rhs, np.zeros((self.n, self.n)), M, max_iter=MAX_ITER, tol=TOL)
+        return time.perf_counter() - t0, info["iters"]
 
 
 def cpu_oracle_vol_sample(case):
@@ -220,23 +256,28 @@ def threads_used():
 
 # --------------------------------------------------------------- reference arm
 def run_reference(args, rank, world):
+    """The oracle arm: each step is one full oracle step of one slice
+    (OracleStep), W untimed, K timed; rank 0 alone runs under torchrun."""
     if rank != 0:
         return
-    iters_needed = 18   # DC-PCG iterations to 1e-4 at this workload (GPU path, same recursion)
-    times = []
+    step = OracleStep()
     for _ in range(args.warmup):
-        cpu_oracle_sample(1)
+        step()
+    times, iters = [], []
     for _ in range(args.steps):
-        t_it, _ = cpu_oracle_sample(1)
-        times.append(t_it)
-    t_solve = float(np.mean(times)) * iters_needed
-    value = 1.0 / t_solve
-    sample = (f"per step: 1 preconditioned CG iteration of the FP64 oracle (plus its initial "
-              f"residual apply) on one 320x320x16 slice, extrapolated to {iters_needed} iterations")
+        t, it = step()
+        times.append(t)
+        iters.append(it)
+    t_step = float(np.mean(times))
+    value = 1.0 / t_step
+    sample = (f"per step: one FP64 oracle step of slice 0 (gridding adjoint for A^H y + mu z, then "
+              f"DC-preconditioned CG to 1e-4: {np.mean(iters):.1f} iterations), measured, not extrapolated; "
+              f"oracle plan {step.t_plan:.1f} s once, untimed")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_solve * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": "brain-sized DC solve, 320x320, 16 coils, spiral 16x2048, W=6, sigma=2, mu=1e-2, tol 1e-4", "batch": 1},
+            "data": "synthetic", "config": {"workload": WORKLOAD, "batch": 1},
+            "oracle_cg_iterations": float(np.mean(iters)),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads_used(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -389,8 +430,21 @@ def run_ours(args, rank, world, dist):
     ms_adj = timed(adjoints, reps)
     fwd_per_s = B * reps * world / (ms_fwd / 1e3)
     adj_per_s = B * reps * world / (ms_adj / 1e3)
-    # measured FP32 FMA throughput: the ALU roofline's denominator
-    fp32_peak = hq.probe_fp32_peak()
+    # the solutions themselves, not only the CG recursion: true relative residual
+    # ||rhs - (A^H A + mu I) x|| / ||rhs|| of every slice with the library's operator
+    for i in range(B):
+        hq.adjoint_axpy(plans[i], ys[i], MU, zs[i], rhss[i])
+    solve_all(args.mode)
+    true_res = []
+    for i in range(B):
+        hq.toeplitz_normal(plans[i], xs[i], outs[i])
+        r = rhss[i] - (outs[i] + MU * xs[i])
+        true_res.append(float(torch.linalg.vector_norm(r) / torch.linalg.vector_norm(rhss[i])))
+    assert max(true_res) <= 1.5 * TOL, max(true_res)
+
+    # the precision variant (BF16x3 / FP16x3 tensor-core Toeplitz passes): A^H A
+    # time, per-stage DC solves to 1e-4 and their distance to the FP32 solutions
+    mixed = mixed_precision_summary(hq, plans[:4], rhss[:4], xs[:4], timed)
 
     # end to end through the public API with host buffers: H2D of y, D2H of x
     y_host = [y.cpu().pin_memory() for y in ys]
@@ -415,15 +469,20 @@ def run_ours(args, rank, world, dist):
         phases = batch_phase_trace(batches[0], [rhss[i] for i in groups[0]], [xs[i] for i in groups[0]], hq)
     if rank != 0:
         return
-    # roofline of the persistent solve: FP32 ALU work per launch / duration
+    # roofline of the dominant kernel (the batched or persistent solve): its
+    # algorithmic FP32 work per launch / duration against the ALU peak of the unit
+    # counts at the maximum SM clock; beside it the same launch's compulsory bytes
+    # against the measured HBM bandwidth
     flops_iter = aha_flops(n, L) + precond_flops(n) + 12 * 8 * n * n
     flops_launch = flops_iter * mean_iters * solves_per_launch
     achieved = flops_launch / (solve_ms / 1e3) / 1e12
     sm_max = clocks.get("sm_max_mhz") or 2070.0
-    nominal = 152 * 128 * 2 * sm_max * 1e6 / 1e12
-    peak = fp32_peak
-    cpu_t_it, cpu_plan = cpu_oracle_sample(1)
-    cpu_value = 1.0 / (cpu_t_it * mean_iters)
+    peak = fp32_peak_tflops(sm_max)
+    bytes_launch = iter_bytes(n, L) * mean_iters * solves_per_launch
+    hbm_achieved = bytes_launch / (solve_ms / 1e3) / 1e9
+    step0 = OracleStep()
+    cpu_t, cpu_iters = step0()
+    cpu_value = 1.0 / cpu_t
     # per step: spread, column IFFT, row IFFT + axpy per slice, then the solve launch(es)
     launches_per_step = 3 * B + (len(groups) if args.mode == "batched" else B)
     line = {
@@ -431,8 +490,7 @@ def run_ours(args, rank, world, dist):
         "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded ellipse phantoms, Gaussian-bump coil maps, VD spiral)",
-        "config": {"workload": "brain-sized DC solve: 320x320, 16 coils, spiral 16x2048 (32768 pts), "
-                               "KB W=6, sigma=2, mu=1e-2, rel. residual 1e-4, DC-preconditioned CG",
+        "config": {"workload": WORKLOAD,
                    "batch_per_gpu": B, "solver": args.mode,
                    "slices_per_launch": len(groups[0]) if args.mode == "batched" else 1, "parallelism": f"replicas x{world}",
                    "tuning": {"spread_tile": tuned.spread_tile, "pc_lines": tuned.pc_lines,
@@ -449,18 +507,24 @@ def run_ours(args, rank, world, dist):
         "plain_pcg_solves_per_s": plain_value,
         "speedup_vs_plain_pcg": value / plain_value,
         "mean_cg_iterations": mean_iters,
+        "true_rel_residual_max": max(true_res),
+        "mixed_precision": mixed,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
                      "traffic": BATCH_TRAFFIC_BYTES if args.mode == "batched" else PERSISTENT_TRAFFIC_BYTES,
                      "kernel": (f"k_pcg_batch ({len(groups[0])} slices per launch)" if args.mode == "batched"
                                 else "k_pcg_persistent<640,320>"),
-                     "peak_source": "measured: FP32 FMA probe (hqs_probe_fp32_peak, 8 independent chains per "
-                                    "thread, full occupancy) on this GPU after the timed region",
-                     "nominal": nominal},
+                     "flops_per_launch": flops_launch, "launch_ms": solve_ms,
+                     "peak_source": f"unit counts: 152 SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz "
+                                    f"(maximum SM clock)",
+                     "hbm": {"achieved": hbm_achieved, "peak": HBM_PEAK_GBS, "unit": "GB/s",
+                             "frac": hbm_achieved / HBM_PEAK_GBS, "bytes_per_launch": bytes_launch,
+                             "bytes": "compulsory per slice-iteration: x, S, Khat and the output of A^H A "
+                                      "plus 8 vector passes", "peak_source": PEAKS["source"]}},
         "cpu_baseline": {"value": cpu_value, "unit": UNIT, "cores": threads_used(), "kind": "oracle",
-                         "sample": f"1 FP64 oracle PCG iteration (+ initial residual) on one slice, "
-                                   f"scaled to {mean_iters:.1f} iterations per solve; oracle plan "
-                                   f"{cpu_plan:.1f} s not included"},
+                         "sample": f"one FP64 oracle step of slice 0 (gridding adjoint for A^H y + mu z, "
+                                   f"DC-preconditioned CG to 1e-4 in {cpu_iters} iterations), measured; "
+                                   f"oracle plan {step0.t_plan:.1f} s once, untimed"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
@@ -687,7 +751,7 @@ def run_mixed320(args, rank, world, dist):
     # tensor-pipe work of one mixed A^H A: 4 real GEMMs x 3 products
     gemm_flops = 3 * 2 * (L * n * 4 * n * 2 * n + L * 2 * n * 4 * n * 2 * n + L * 2 * n * 2 * n * 4 * n
                           + n * L * 2 * n * 4 * n)
-    peak = 1880.3
+    peak = PEAKS["bf16_tflops"]
     for name in ("bf16x3", "fp16x3"):
         res[name]["tensor_tflops"] = gemm_flops / (res[name]["aha_us"] * 1e-6) / 1e12
         res[name]["tensor_frac_of_measured_bf16_peak"] = res[name]["tensor_tflops"] / peak
@@ -1051,10 +1115,55 @@ def precond_flops(n):
     return 2 * 2 * n * fft_flops(n) + 6 * n * n
 
 
+def iter_bytes(n, L):
+    """Compulsory HBM bytes of one CG iteration of one slice: the A^H A apply's
+    x, coil maps, Khat and output (complex64 images and maps, real Khat on the
+    2n grid) and 8 passes over complex64 n x n vectors (p, q, x, r, z)."""
+    img = n * n * 8
+    return img + L * img + (2 * n) * (2 * n) * 4 + img + 8 * img
+
+
+def mixed_precision_summary(hq, plans, rhss, xs_fp32, timed):
+    """A^H A microseconds and per-stage DC solves to 1e-4 in BF16x3 and FP16x3
+    (tensor-core DFT-GEMM Toeplitz passes, fp64 CG scalars) on a few slices,
+    with each solution's relative distance to the FP32 path's solution."""
+    import torch
+    out = {}
+    outs = [torch.empty_like(x) for x in xs_fp32]
+    for name, prec in (("fp32", hq.HQS_PREC_FP32), ("bf16x3", hq.HQS_PREC_BF16X3), ("fp16x3", hq.HQS_PREC_FP16X3)):
+        def applies():
+            for p, r, o in zip(plans, rhss, outs):
+                hq.toeplitz_normal(p, r, o, precision=prec)
+        xs = [torch.zeros_like(x) for x in xs_fp32]
+
+        def solves():
+            for p, r, x in zip(plans, rhss, xs):
+                hq.dc_solve(p, 1.0, MU, r, x, max_iter=MAX_ITER, rel_tol=TOL, precision=prec,
+                            mode=hq.HQS_SOLVE_X0_ZERO, want_info=False)
+        applies()
+        reps = 5
+        ms_a = timed(applies, reps)
+        its = [hq.dc_solve(p, 1.0, MU, r, x, max_iter=MAX_ITER, rel_tol=TOL, precision=prec,
+                           mode=hq.HQS_SOLVE_X0_ZERO).iterations for p, r, x in zip(plans, rhss, xs)]
+        ms_s = timed(solves, 1)
+        diff = max(float(torch.linalg.vector_norm(x - x0) / torch.linalg.vector_norm(x0))
+                   for x, x0 in zip(xs, xs_fp32))
+        out[name] = {"aha_us": ms_a * 1e3 / (reps * len(plans)),
+                     "dc_solves_per_s": len(plans) / (ms_s / 1e3),
+                     "mean_cg_iterations": float(np.mean(its)),
+                     "rel_diff_vs_fp32_solution": diff}
+    return out
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
+    if args.gpus != world:
+        print(f"bench.py: --gpus {args.gpus} but WORLD_SIZE is {world}; launch N > 1 with "
+              f"python -m torch.distributed.run --nproc-per-node {args.gpus} bench.py --gpus {args.gpus}",
+              file=sys.stderr)
+        sys.exit(2)
     dist = None
     if world > 1:
         import torch.distributed as td

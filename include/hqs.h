@@ -188,9 +188,13 @@ HQS_API int hqs_precond_apply(hqs_plan plan, float a, float b, const hqs_c64* r,
  *   hqs_precond_apply, with the density symbol lam given by the caller.
  *   r, z: (n, n) complex device; lam: (n, n) float device; b > 0;
  *   n in {16, 32, 64, 128, 256, 320, 384}: larger n returns HQS_ERR_INVALID_ARG.
- * The first call on a device sets up (looks up the arrays' device addresses,
- * fills the twiddle tables and synchronises `stream` once); make that first
- * call before any stream capture.  All calls on a device share the scratch
+ * The first call on a device sets up: it looks up the arrays' device
+ * addresses, loads the kernels of every supported n (so that no later call,
+ * for any n, loads code), fills the twiddle tables and synchronises `stream`
+ * once.  Make that first call before any stream capture.  A device reset
+ * (cudaDeviceReset) makes a new context; the next call detects it by the
+ * context's id and sets up again, so that call too must come before any
+ * capture.  All calls on a device share the scratch
  * array and it keeps the last call's contents: calls that overlap on the GPU
  * (for instance on two streams) race on it.  Nothing in it needs to start at
  * zero: the row pass overwrites the whole n x n region before it is read. */
@@ -351,11 +355,6 @@ HQS_API int hqs_power_iteration(hqs_plan plan, int iters, double* lam_max, void*
 
 HQS_API const char* hqs_status_string(int status);
 
-/* Measured FP32 FMA throughput of the current GPU in TFLOP/s (no counterpart
- * in the paper: the denominator of the ALU roofline of the L2-resident
- * persistent solve).  BLOCKING on `stream`: 4 launches of 8 independent FMA
- * chains per thread at full occupancy, median of the last 3. */
-HQS_API int hqs_probe_fp32_peak(double* tflops, void* stream);
 
 /* Tuning knobs (no counterpart in the paper), set per plan by the autotuner:
  *   HQS_TUNE_FUSED_GRID  cap on the persistent solve's CTAs (0 = all resident)

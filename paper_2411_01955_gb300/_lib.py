@@ -85,7 +85,6 @@ _SIGS = {
                                        C.c_float, C.c_void_p]),
     "hqs_power_iteration": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_void_p]),
     "hqs_status_string": (C.c_char_p, [C.c_int]),
-    "hqs_probe_fp32_peak": (C.c_int, [C.POINTER(C.c_double), C.c_void_p]),
     "hqs_estimate_smaps": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,
                                      C.c_float, C.c_float, C.c_float, C.c_void_p, C.c_void_p]),
     "hqs_plan_set_tuning": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
@@ -182,13 +181,6 @@ def estimate_smaps(traj, y, n, out, dcf=None, kernel_width=6, oversamp=2.0, widt
                                         float(thresh), _ptr(out, torch.complex64, "smaps"), _stream(stream)),
            "hqs_estimate_smaps")
     return out
-
-
-def probe_fp32_peak(stream=None) -> float:
-    """Measured FP32 FMA throughput of the current GPU, TFLOP/s."""
-    v = C.c_double()
-    _check(library().hqs_probe_fp32_peak(C.byref(v), _stream(stream)), "hqs_probe_fp32_peak")
-    return v.value
 
 
 def status_string(status: int) -> str:
@@ -420,10 +412,31 @@ def plan_set_tuning(plan: Plan, key: int, value: int):
     _check(library().hqs_plan_set_tuning(plan.handle, int(key), int(value)), "hqs_plan_set_tuning")
 
 
+NOALLOC_SIZES = (16, 32, 64, 128, 256, 320, 384)
+
+
+def _noalloc_check(r, lam, z) -> int:
+    """Shapes and types of hqs_precond_apply_noalloc's arguments, checked before
+    any launch: the C entry point takes n alone and cannot check the buffers."""
+    if r.dim() != 2 or r.shape[0] != r.shape[1]:
+        raise ValueError(f"r must be (n, n), got {tuple(r.shape)}")
+    n = int(r.shape[0])
+    if n not in NOALLOC_SIZES:
+        raise ValueError(f"n = {n} is not one of {NOALLOC_SIZES}")
+    for t, name, dt in ((r, "r", torch.complex64), (lam, "lam", torch.float32), (z, "z", torch.complex64)):
+        if tuple(t.shape) != (n, n):
+            raise ValueError(f"{name} must be ({n}, {n}), got {tuple(t.shape)}")
+        if t.dtype != dt:
+            raise TypeError(f"{name} must be {dt}, got {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    return n
+
+
 def precond_apply_noalloc(r, lam, a, b, z, stream=None):
     """Preconditioner apply without any device allocation (no plan): scratch
     lives in a static device array, n <= 384; the density symbol lam is given."""
-    n = int(r.shape[-1])
+    n = _noalloc_check(r, lam, z)
     _check(library().hqs_precond_apply_noalloc(_ptr(r, torch.complex64, "r"),
                                                _ptr(lam, torch.float32, "lam"), n, float(a),
                                                float(b), _ptr(z, torch.complex64, "z"),

@@ -269,29 +269,77 @@ __global__ void k_noalloc_twiddles(float2* tw) {
 
 struct NoallocDevice {
     bool ready = false;
-    float2* spectrum = nullptr;   // device address of g_noalloc_spectrum
-    float2* twiddles = nullptr;   // device address of g_noalloc_twiddles
+    unsigned long long ctx_id = 0;   // context the addresses below belong to
+    float2* spectrum = nullptr;      // device address of g_noalloc_spectrum
+    float2* twiddles = nullptr;      // device address of g_noalloc_twiddles
 };
 static std::mutex g_noalloc_mu;
 static NoallocDevice g_noalloc_dev[HQS_NOALLOC_MAX_DEVICES];
 
-// Once per device, with that device current: resolve the arrays' device
-// addresses (their names are only host stand-ins in host code) and fill the
-// twiddle tables; the caller's stream is synchronised once so that later
-// calls on any stream see the tables.
+// The current context's process-unique id (the driver's cuCtxGetId, reached
+// through the runtime's entry-point query so that no libcuda link is needed).
+// A device reset makes a new context with a new id, so a cache entry keyed by
+// it is never reused for the reloaded module.
+typedef int (*ctx_get_id_fn)(void* ctx, unsigned long long* id);
+static int noalloc_context_id(unsigned long long* id) {
+    static ctx_get_id_fn fn = nullptr;
+    if (!fn) {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        HQS_CUDA_TRY(cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q));
+        if (q != cudaDriverEntryPointSuccess || !f) return HQS_ERR_CUDA;
+        fn = reinterpret_cast<ctx_get_id_fn>(f);
+    }
+    return fn(nullptr, id) == 0 ? HQS_OK : HQS_ERR_CUDA;
+}
+
+// Loads the three pass kernels for one size and sets their shared-memory
+// limit, so that no later call loads code (which may allocate device memory
+// under lazy module loading).
+template <int N>
+static int noalloc_prepare_size() {
+    const int sm = (int)((N * kLines + N) * sizeof(float2));
+    cudaFuncAttributes fa;
+    HQS_CUDA_TRY(cudaFuncGetAttributes(&fa, k_pc_rows_fwd<N>));
+    HQS_CUDA_TRY(cudaFuncGetAttributes(&fa, k_pc_cols<N>));
+    HQS_CUDA_TRY(cudaFuncGetAttributes(&fa, k_pc_rows_inv<N>));
+    HQS_CUDA_TRY(cudaFuncSetAttribute(k_pc_rows_fwd<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    HQS_CUDA_TRY(cudaFuncSetAttribute(k_pc_cols<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    HQS_CUDA_TRY(cudaFuncSetAttribute(k_pc_rows_inv<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    return HQS_OK;
+}
+
+// Once per device and context, with that device current: resolve the arrays'
+// device addresses (their names are only host stand-ins in host code), load
+// every kernel this entry point launches, and fill the twiddle tables; the
+// caller's stream is synchronised once so that later calls on any stream see
+// the tables.
 static int noalloc_setup(int dev, cudaStream_t st, NoallocDevice** out) {
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
     NoallocDevice& d = g_noalloc_dev[dev];
-    if (!d.ready) {
-        void* spec = nullptr;
-        void* tw = nullptr;
-        HQS_CUDA_TRY(cudaGetSymbolAddress(&spec, g_noalloc_spectrum));
+    void* spec = nullptr;
+    void* tw = nullptr;
+    // the lookup also makes the runtime's context current (after a device reset: a new one)
+    HQS_CUDA_TRY(cudaGetSymbolAddress(&spec, g_noalloc_spectrum));
+    unsigned long long ctx = 0;
+    int rc = noalloc_context_id(&ctx);
+    if (rc != HQS_OK) return rc;
+    if (!d.ready || d.ctx_id != ctx) {
+        d.ready = false;
         HQS_CUDA_TRY(cudaGetSymbolAddress(&tw, g_noalloc_twiddles));
+        if ((rc = noalloc_prepare_size<16>()) != HQS_OK) return rc;
+        if ((rc = noalloc_prepare_size<32>()) != HQS_OK) return rc;
+        if ((rc = noalloc_prepare_size<64>()) != HQS_OK) return rc;
+        if ((rc = noalloc_prepare_size<128>()) != HQS_OK) return rc;
+        if ((rc = noalloc_prepare_size<256>()) != HQS_OK) return rc;
+        if ((rc = noalloc_prepare_size<320>()) != HQS_OK) return rc;
+        if ((rc = noalloc_prepare_size<384>()) != HQS_OK) return rc;
         k_noalloc_twiddles<<<ceil_div(HQS_NOALLOC_TW_TOTAL, 256), 256, 0, st>>>(static_cast<float2*>(tw));
         HQS_CUDA_TRY(cudaGetLastError());
         HQS_CUDA_TRY(cudaStreamSynchronize(st));
         d.spectrum = static_cast<float2*>(spec);
         d.twiddles = static_cast<float2*>(tw);
+        d.ctx_id = ctx;
         d.ready = true;
     }
     *out = &d;
@@ -306,9 +354,6 @@ static int precond_noalloc_impl(const NoallocDevice& d, float a, float b, const 
     const int th = fft_threads<N>(Q);
     const size_t sm = (size_t)(N * kLines + N) * sizeof(float2);
     const int nb = ceil_div(N, Q);
-    HQS_CUDA_TRY(cudaFuncSetAttribute(k_pc_rows_fwd<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    HQS_CUDA_TRY(cudaFuncSetAttribute(k_pc_cols<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    HQS_CUDA_TRY(cudaFuncSetAttribute(k_pc_rows_inv<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     k_pc_rows_fwd<N><<<nb, th, sm, st>>>(r, d.spectrum, Q, tw, nullptr);
     k_pc_cols<N><<<nb, th, sm, st>>>(d.spectrum, Q, lam, a, b, tw, nullptr, nullptr);
     k_pc_rows_inv<N><<<nb, th, sm, st>>>(d.spectrum, z, Q, tw, nullptr);

@@ -68,3 +68,36 @@ def test_volume_arguments_are_rejected_without_a_gpu():
     for fn in ("hqs_forward3d", "hqs_adjoint3d", "hqs_toeplitz_normal3d"):
         assert getattr(lib, fn)(None, fake, fake, None) == -1
     assert lib.hqs_precond_apply3d(None, ctypes.c_float(1.0), ctypes.c_float(0.1), fake, fake, None) == -1
+
+
+def test_noalloc_wrapper_checks_shapes_before_any_launch():
+    """hqs_precond_apply_noalloc takes n alone, so the binding is the only
+    guard of the buffers' sizes: a non-square r, or a symbol or output of
+    another size or type, is rejected before the library is called (CPU
+    tensors here: the check runs before the device-pointer check).  The C
+    entry point itself rejects unsupported n before any CUDA call."""
+    import pytest
+    torch = pytest.importorskip("torch")
+    import paper_2411_01955_gb300 as hq
+    from paper_2411_01955_gb300 import build
+    c64, f32 = torch.complex64, torch.float32
+    ok_r, ok_l = torch.zeros((64, 64), dtype=c64), torch.zeros((64, 64), dtype=f32)
+    bad = [
+        (torch.zeros((64, 128), dtype=c64), ok_l, ok_r.clone()),       # non-square r
+        (torch.zeros((2, 64, 64), dtype=c64), ok_l, ok_r.clone()),     # batched r
+        (torch.zeros((48, 48), dtype=c64), torch.zeros((48, 48), dtype=f32), torch.zeros((48, 48), dtype=c64)),
+        (ok_r, torch.zeros((32, 32), dtype=f32), ok_r.clone()),        # smaller symbol
+        (ok_r, ok_l, torch.zeros((32, 64), dtype=c64)),                # smaller output
+        (ok_r, ok_l.to(torch.float64), ok_r.clone()),                  # symbol of another type
+        (ok_r, ok_l, torch.zeros((64, 64), dtype=torch.complex128)),   # output of another type
+    ]
+    for r, lam, z in bad:
+        with pytest.raises((ValueError, TypeError)):
+            hq.precond_apply_noalloc(r, lam, 1.0, 0.1, z)
+    lib = ctypes.CDLL(build.build())
+    fake = ctypes.c_void_p(0x1000)   # never dereferenced: validation fails first
+    for n in (0, 8, 48, 512, 1024):
+        assert lib.hqs_precond_apply_noalloc(fake, fake, n, ctypes.c_float(1.0), ctypes.c_float(0.1),
+                                             fake, None) == -1
+    assert lib.hqs_precond_apply_noalloc(fake, fake, 64, ctypes.c_float(1.0), ctypes.c_float(0.0),
+                                         fake, None) == -1

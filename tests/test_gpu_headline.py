@@ -1,0 +1,209 @@
+"""GPU parity at the benchmarked size, against the FP64 oracle.
+
+The brain-sized workload: 320 x 320 image, 16 coils, variable-density spiral
+of 16 interleaves x 2048 samples (32768 points), Kaiser-Bessel width 6,
+oversampling 2 (Eq. (1) with the gridding parameters of the benchmark).  Its
+transforms are the ones the smaller cases never reach: 640-point lines
+(radix 5 and the prime-factor 10 and 40 stages) on the NUFFT grid and the
+Toeplitz grid, 320-point lines in the preconditioner; the 384 x 384 slices of
+the batched workload add 768-point lines.  The batched solve is checked in the
+launch configuration the benchmark times: 16 slices of one trajectory, one
+plan each, in one cooperative launch.
+
+Bars: relative L2 <= 1e-5 for a single operator (float32 path against the
+float64 oracle at equal parameters); for iterated results (CG, HQS) the bound
+is max(1e-5, 4 d), d the oracle's own deviation when its right-hand side is
+perturbed by the float32 unit roundoff 2^-24, as in the smaller tests.
+"""
+import numpy as np
+import pytest
+
+import oracle_jobs as jobs
+import synth
+from helpers import make_plan, quantised, rel, to_dev, to_host
+from oracle import nufft, toeplitz
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+MU = 1e-2
+
+
+def hq():
+    import paper_2411_01955_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def brain():
+    """Slice 0 of the benchmark (seed 0): its plan, and the oracle's Toeplitz
+    kernel spectrum and density symbol."""
+    case = quantised(synth.brain_case(0))
+    plan, _, _ = make_plan(case)
+    Kh, lam = jobs.slice_operators(case["traj"], case["n"])
+    return case, plan, Kh, lam
+
+
+def test_brain_forward_matches_oracle(brain):
+    case, plan, _, _ = brain
+    y = torch.empty((case["L"], case["traj"].shape[0]), dtype=torch.complex64, device="cuda")
+    hq().forward(plan, to_dev(case["x"]), y)
+    want = nufft.forward(case["x"], case["smaps"], case["traj"], case["W"], case["sigma"])
+    err = rel(to_host(y), want)
+    print(f"320^2 x 16 forward: {err:.2e}")
+    assert err <= TOL
+
+
+def test_brain_adjoint_matches_oracle(brain):
+    case, plan, _, _ = brain
+    yv = jobs.c64(case["noise"])
+    x = torch.empty((case["n"], case["n"]), dtype=torch.complex64, device="cuda")
+    hq().adjoint(plan, to_dev(yv), x)
+    want = nufft.adjoint(yv, case["smaps"], case["traj"], case["W"], case["sigma"])
+    err = rel(to_host(x), want)
+    print(f"320^2 x 16 adjoint: {err:.2e}")
+    assert err <= TOL
+    # the fused right-hand side A^H y + mu z of the benchmark's step
+    z = case["x"]
+    hq().adjoint_axpy(plan, to_dev(yv), MU, to_dev(z), x)
+    assert rel(to_host(x), want + MU * z) <= TOL
+
+
+def test_brain_toeplitz_normal_matches_oracle(brain):
+    case, plan, Kh, _ = brain
+    out = torch.empty((case["n"], case["n"]), dtype=torch.complex64, device="cuda")
+    hq().toeplitz_normal(plan, to_dev(case["x"]), out)
+    want = toeplitz.normal(case["x"], case["smaps"], Kh)
+    err = rel(to_host(out), want)
+    print(f"320^2 x 16 A^H A: {err:.2e}")
+    assert err <= TOL
+
+
+def test_brain_precond_apply_matches_oracle(brain):
+    case, plan, _, lam = brain
+    r = case["x"]
+    z = torch.empty((case["n"], case["n"]), dtype=torch.complex64, device="cuda")
+    for a, b in [(1.0, MU), (0.8, 0.05)]:
+        hq().precond_apply(plan, a, b, to_dev(r), z)
+        assert rel(to_host(z), toeplitz.precond_apply(r, lam, a, b)) <= TOL, (a, b)
+
+
+@pytest.mark.parametrize("mode", ["plain", "fused"])
+def test_brain_pcg_fixed_iterations_match_oracle(brain, mode):
+    """5 DC-preconditioned CG iterations from zero: the per-stage solve
+    (k_toep_* passes on 640-point lines) and the persistent solve
+    (k_pcg_persistent<640, 320>) follow the oracle's recursion."""
+    case, plan, Kh, lam = brain
+    rhs = jobs.normal_rhs(case["smaps"], Kh, MU, case["x"])
+    want, hist, dev = jobs.pcg_fixed(case["smaps"], Kh, lam, MU, rhs, 5, seed=1)
+    tol = max(TOL, 4 * dev)
+    flag = hq().HQS_SOLVE_FUSED if mode == "fused" else hq().HQS_SOLVE_PLAIN
+    x = torch.zeros((case["n"], case["n"]), dtype=torch.complex64, device="cuda")
+    info = hq().dc_solve(plan, 1.0, MU, to_dev(rhs), x, max_iter=5, rel_tol=0.0, mode=flag)
+    err = rel(to_host(x), want)
+    print(f"320^2 x 16 {mode} PCG, 5 iterations: {err:.2e} (bound {tol:.2e})")
+    assert info.iterations == 5 and info.status == 0
+    assert err <= tol
+    assert np.allclose(np.array(info.history()), hist, rtol=1e-4, atol=0)
+    # to the benchmark's tolerance: the fp64 true residual of the GPU's solution
+    xs = torch.zeros_like(x)
+    inf = hq().dc_solve(plan, 1.0, MU, to_dev(rhs), xs, max_iter=200, rel_tol=1e-4, mode=flag)
+    tr = jobs.true_residual(case["smaps"], Kh, MU, rhs, to_host(xs))
+    print(f"320^2 x 16 {mode} PCG to 1e-4: {inf.iterations} iterations, true residual {tr:.2e}")
+    assert inf.status == 0 and tr <= 1.2e-4
+
+
+def test_brain_batched_solve_16_slices_matches_oracle():
+    """k_pcg_batch as the benchmark launches it: 16 slices of the spiral
+    workload (seeds 0-15, one plan each, one trajectory), one cooperative
+    launch.  5 fixed iterations against the oracle's PCG per slice; then to
+    1e-4, every slice's fp64 true residual and its iteration count against
+    the per-slice persistent solve (within one)."""
+    n, L, B = 320, 16, 16
+    traj = synth.traj_spiral(16, 2048, n)
+    cases = [quantised(dict(n=n, L=L, W=6, sigma=2.0, x=synth.phantom(s, n), smaps=synth.coil_maps(s, n, L),
+                            traj=traj)) for s in range(B)]
+    Kh, lam = jobs.slice_operators(cases[0]["traj"], n)
+    with jobs.pool(B) as ex:
+        rhs_np = list(ex.map(jobs.normal_rhs, [c["smaps"] for c in cases], [Kh] * B, [MU] * B,
+                             [c["x"] for c in cases]))
+        fut = [ex.submit(jobs.pcg_fixed, c["smaps"], Kh, lam, MU, b, 5, 10 + i)
+               for i, (c, b) in enumerate(zip(cases, rhs_np))]
+        plans = [make_plan(c)[0] for c in cases]
+        batch = hq().Batch(plans, max_outer=1)
+        rhs = [to_dev(b) for b in rhs_np]
+        xs = [torch.full((n, n), 2.0 - 1j, dtype=torch.complex64, device="cuda") for _ in range(B)]
+        batch.dc_solve(rhs, xs, 1.0, MU, max_iter=5, rel_tol=0.0)
+        info = batch.dc_info()
+        got = [to_host(x) for x in xs]
+        oracle = [f.result() for f in fut]
+        for i, ((want, _, dev), g) in enumerate(zip(oracle, got)):
+            tol = max(TOL, 4 * dev)
+            print(f"batched slice {i}, 5 iterations: {rel(g, want):.2e} (bound {tol:.2e})")
+            assert info[i][0] == 5 and info[i][2] == 0
+            assert rel(g, want) <= tol, (i, rel(g, want), tol)
+        # to tolerance
+        for x in xs:
+            x.zero_()
+        batch.dc_solve(rhs, xs, 1.0, MU, max_iter=200, rel_tol=1e-4)
+        info = batch.dc_info()
+        sols = [to_host(x) for x in xs]
+        tres = list(ex.map(jobs.true_residual, [c["smaps"] for c in cases], [Kh] * B, [MU] * B, rhs_np, sols))
+    for i in range(B):
+        xf = torch.zeros((n, n), dtype=torch.complex64, device="cuda")
+        inf = hq().dc_solve(plans[i], 1.0, MU, rhs[i], xf, max_iter=200, rel_tol=1e-4, mode=hq().HQS_SOLVE_FUSED)
+        its, rr, st = info[i]
+        print(f"batched slice {i} to 1e-4: {its} iterations (per-slice {inf.iterations}), "
+              f"true residual {tres[i]:.2e}")
+        assert st == 0 and rr <= 1e-4 and abs(its - inf.iterations) <= 1
+        assert tres[i] <= 1.2e-4
+
+
+def mixed_size_cases():
+    """A 384^2 slice (768-point lines; 12 coils, 48 radial spokes x 768) and
+    a 320^2 slice of the spiral workload, as the batched workload mixes them."""
+    return [
+        quantised(dict(n=384, L=12, W=6, sigma=2.0, x=synth.phantom(41, 384), smaps=synth.coil_maps(41, 384, 12),
+                       traj=synth.traj_radial(48, 768))),
+        quantised(dict(n=320, L=16, W=6, sigma=2.0, x=synth.phantom(42, 320), smaps=synth.coil_maps(42, 320, 16),
+                       traj=synth.traj_spiral(16, 2048, 320))),
+    ]
+
+
+def test_batched_384_and_320_hqs_and_solve_match_oracle():
+    """Batched annealed HQS (3 outer x 3 CG iterations, Gaussian smoothing)
+    and 5 fixed iterations of the batched DC solve on a 384^2 and a 320^2
+    slice in one launch each, every slice against the oracle."""
+    cases = mixed_size_cases()
+    K, cg = 3, 3
+    mu = np.array([0.1, 0.03, 0.01], dtype=np.float32)
+    sigma = mu.copy()
+    ys = []
+    for i, c in enumerate(cases):
+        y = nufft.forward(c["x"], c["smaps"], c["traj"], c["W"], c["sigma"])
+        y = y + 0.01 * np.sqrt(np.mean(np.abs(y) ** 2)) * synth.complex_noise(50 + i, y.shape)
+        ys.append(jobs.c64(y))
+    with jobs.pool(4) as ex:
+        f_hqs = [ex.submit(jobs.hqs_slice, c, y, mu.astype(np.float64), sigma.astype(np.float64), K, cg, 60 + i)
+                 for i, (c, y) in enumerate(zip(cases, ys))]
+        f_dc = [ex.submit(jobs.dc_slice, c, MU, 5, 70 + i) for i, c in enumerate(cases)]
+        plans = [make_plan(c)[0] for c in cases]
+        batch = hq().Batch(plans, max_outer=4)
+        xs = [torch.zeros((c["n"], c["n"]), dtype=torch.complex64, device="cuda") for c in cases]
+        batch.run([to_dev(y) for y in ys], xs, mu, sigma, cg_iters=cg, use_graph=False)
+        got = [to_host(x) for x in xs]
+        for c, g, f in zip(cases, got, f_hqs):
+            want, dev = f.result()
+            tol = max(TOL, 4 * dev)
+            print(f"batched HQS {c['n']}^2 x {c['L']}: {rel(g, want):.2e} (bound {tol:.2e})")
+            assert rel(g, want) <= tol
+        dc = [f.result() for f in f_dc]
+    xs = [torch.zeros((c["n"], c["n"]), dtype=torch.complex64, device="cuda") for c in cases]
+    batch.dc_solve([to_dev(r) for r, _, _, _ in dc], xs, 1.0, MU, max_iter=5, rel_tol=0.0)
+    info = batch.dc_info()
+    for c, x, (_, want, _, dev), inf in zip(cases, xs, dc, info):
+        tol = max(TOL, 4 * dev)
+        err = rel(to_host(x), want)
+        print(f"batched DC solve {c['n']}^2 x {c['L']}, 5 iterations: {err:.2e} (bound {tol:.2e})")
+        assert inf[0] == 5 and inf[2] == 0 and err <= tol

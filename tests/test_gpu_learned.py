@@ -15,6 +15,29 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-5
+EPS = 2.0 ** -24
+
+
+def rounding_model(params, rng):
+    """The network's float32 rounding as a perturbation of its parameters.
+
+    A float32 dot product of K terms equals the exact dot product of slightly
+    perturbed weights, |dw| <= K u |w| in the worst case and about sqrt(K) u |w|
+    for rounding errors of random sign (Higham, Accuracy and Stability of
+    Numerical Algorithms, sec. 3.1 and 2.8), u = 2^-24.  Each 3x3 layer sums
+    K = 9 Cin products plus its bias, so every parameter of that layer is
+    perturbed by a relative sqrt(K) u with a random sign.  The learned path's
+    bound is then four times the oracle's deviation under this perturbation
+    (and a 2^-24 perturbation of its input), like the other iterated or
+    composed results in this suite; ReLU and the input scaling add no error
+    of their own beyond this model."""
+    out = []
+    for W, b in params:
+        K = 9 * W.shape[1] + 1
+        d = EPS * math.sqrt(K)
+        out.append((W * (1 + d * rng.choice([-1.0, 1.0], size=W.shape)),
+                    b * (1 + d * rng.choice([-1.0, 1.0], size=b.shape))))
+    return out
 
 
 def hq():
@@ -160,7 +183,13 @@ def test_learned_precond_apply_matches_oracle():
     z = torch.empty((n, n), dtype=torch.complex64, device="cuda")
     hq().learned_precond_apply(plan, 1.0, 0.05, to_dev(r), z)
     want = convnet.learned_precond(r, lam, 1.0, 0.05, params)
-    assert rel(to_host(z), want) <= 1e-4
+    rng = np.random.default_rng(11)
+    dev = rel(convnet.learned_precond(r * (1 + EPS * rng.normal(size=r.shape)), lam, 1.0, 0.05,
+                                      rounding_model(params, rng)), want)
+    tol = max(TOL, 4 * dev)
+    err = rel(to_host(z), want)
+    print(f"learned preconditioner apply: {err:.2e} (bound {tol:.2e})")
+    assert err <= tol
     hq().plan_set_net(plan, None)
 
 
@@ -181,11 +210,19 @@ def test_learned_fcg_iterates_match_oracle():
     H = lambda v: toeplitz.normal(v, case["smaps"], Kh) + mu * v
     B = lambda v: convnet.learned_precond(v, lam, 1.0, mu, params)
     want, winfo = solvers.fcg(H, rhs, np.zeros((n, n)), B, None, max_iter=4, tol=0.0)
+    rng = np.random.default_rng(12)
+    pp = rounding_model(params, rng)
+    Bp = lambda v: convnet.learned_precond(v, lam, 1.0, mu, pp)
+    pert, _ = solvers.fcg(H, rhs * (1 + EPS * rng.normal(size=rhs.shape)), np.zeros((n, n)), Bp, None,
+                          max_iter=4, tol=0.0)
+    tol = max(TOL, 4 * rel(pert, want))
     x = torch.zeros((n, n), dtype=torch.complex64, device="cuda")
     info = hq().dc_solve(plan, 1.0, mu, to_dev(rhs), x, max_iter=4, rel_tol=0.0,
                          precond=hq().HQS_PRECOND_LEARNED)
     assert info.iterations == 4 and not info.fallback and not winfo["fallback"]
-    assert rel(to_host(x), want) <= 1e-4
+    err = rel(to_host(x), want)
+    print(f"learned flexible CG, 4 iterations: {err:.2e} (bound {tol:.2e})")
+    assert err <= tol
     assert np.allclose(np.array(info.history()), winfo["res_hist"], rtol=1e-3, atol=0)
     hq().plan_set_net(plan, None)
 

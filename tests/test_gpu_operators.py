@@ -309,6 +309,59 @@ def test_hqs_run_matches_oracle_tiny_config():
     assert rel(to_host(xa), to_host(x)) <= bound
 
 
+@pytest.mark.parametrize("metric", ["f1", "chebyshev"])
+def test_hqs_run_pmetric_matches_oracle(metric):
+    """Annealed HQS in the P-metrics of Sec. 3.4 (10 outer x 5 CG iterations,
+    Gaussian smoothing, the 64^2 workload): P = c0 I + c1 A^H A with
+    (c0, c1) = (2, -alpha) (F-1) and (4, -10 alpha / 3) (Chebyshev), alpha =
+    1 / ||A^H A|| from the oracle's power iteration.  The prox solves
+    ((1 + c1 mu) A^H A + c0 mu I) u = A^H y + mu (c0 x + c1 A^H A x), so this
+    checks the extra A^H A x term of the right-hand side and the solve's
+    coefficients against the oracle.  Bounds derived as in the P = Id test:
+    each step from the oracle's x_k within max(1e-5, 4 d_k), the whole run
+    within 4x the oracle's deviation under a 2^-24 perturbation of A^H y."""
+    case = quantised(synth.tiny_case(0))
+    plan, _, _ = make_plan(case)
+    n, K = case["n"], case["K"]
+    Kh, lam = oracle_toeplitz(case)
+    AHA = lambda v: toeplitz.normal(v, case["smaps"], Kh)
+    lmax = solvers.power_iteration(AHA, (n, n), iters=300, rtol=1e-12)
+    alpha = 1.0 / lmax
+    c0, c1 = {"f1": (2.0, -alpha), "chebyshev": (4.0, -10.0 * alpha / 3.0)}[metric]
+    c1 = float(np.float32(c1))     # the value the library receives
+    y = nufft.forward(case["x"], case["smaps"], case["traj"], case["W"], case["sigma"])
+    sd = synth.noise_scale_snr(float(np.sum(np.abs(y) ** 2)), y.size, case["snr_db"])
+    y = (y + sd * case["noise"]).astype(np.complex64).astype(np.complex128)
+    mu = case["mu"].astype(np.float32)
+    sigma = mu.copy()
+    mu64, sg64 = mu.astype(np.float64), sigma.astype(np.float64)
+    b0 = nufft.adjoint(y, case["smaps"], case["traj"], case["W"], case["sigma"])
+    cg = case["cg_iters"]
+    run = lambda b, x0, k1, k0=0: ohqs.hqs(AHA, b, x0, mu64, sg64, k1, k0=k0, cg_iters=cg, c0=c0, c1=c1, lam=lam)
+    want, _, hist = run(b0, np.zeros((n, n)), K)
+    gauss = (1.5, float(sigma[0]))
+    rng = np.random.default_rng(4)
+    eps = 2.0 ** -24
+    xk = np.zeros((n, n), dtype=np.complex128)
+    for k in range(K):
+        xg = to_dev(xk)
+        hq().hqs_run(plan, to_dev(y), xg, mu, sigma, K=k + 1, k0=k, cg_iters=cg, c0=c0, c1=c1, gauss=gauss)
+        step, _, _ = run(b0, xk, k + 1, k)
+        pstep, _, _ = run(b0 * (1 + eps * rng.normal(size=b0.shape)), xk * (1 + eps * rng.normal(size=xk.shape)),
+                          k + 1, k)
+        tol_k = max(TOL, 4 * rel(pstep, step))
+        err = rel(to_host(xg), step)
+        assert err <= tol_k, (metric, k, err, tol_k)
+        xk = hist[k].astype(np.complex64).astype(np.complex128)
+    x = torch.zeros((n, n), dtype=torch.complex64, device="cuda")
+    hq().hqs_run(plan, to_dev(y), x, mu, sigma, K=K, cg_iters=cg, c0=c0, c1=c1)
+    pert, _, _ = run(b0 * (1 + eps * rng.normal(size=b0.shape)), np.zeros((n, n)), K)
+    bound = 4 * rel(pert, want)
+    err = rel(to_host(x), want)
+    print(f"HQS {metric}: whole run {err:.2e} (bound {bound:.2e})")
+    assert err <= max(TOL, bound), (err, bound)
+
+
 def test_hqs_denoiser_callback_and_failure():
     case = quantised(synth.tiny_case(0))
     plan, _, _ = make_plan(case)
@@ -366,14 +419,6 @@ def test_fused_line_balanced_passes(grid):
                         mode=hq().HQS_SOLVE_FUSED | hq().HQS_SOLVE_X0_ZERO)
     assert inf.status == 0
     assert np.linalg.norm(rhs - H(to_host(xf))) / np.linalg.norm(rhs) <= 1.2e-4
-
-
-def test_fp32_peak_probe_is_plausible():
-    """The measured FP32 FMA rate sits below the unit-count bound (152 SMs x
-    128 lanes x 2 flop x at most 2.1 GHz = 81.7 TFLOP/s) and well above a
-    small fraction of it."""
-    t = hq().probe_fp32_peak()
-    assert 20.0 < t < 82.0, t
 
 
 @pytest.mark.parametrize("metric", ["id", "f1", "chebyshev"])
