@@ -81,12 +81,32 @@ def test_brain_toeplitz_normal_matches_oracle(brain):
 
 
 def test_brain_precond_apply_matches_oracle(brain):
+    """The density-compensation preconditioner with the plan's own symbol.
+
+    The plan computes the symbol lam by a float32 2D FFT of the Chan column,
+    whose error (rounding of random sign) is about u sqrt(log2 N^2) ||lam|| in
+    L2, u = 2^-24.  Where a lam + b is small (the spiral's gaps at b = mu =
+    1e-2) s^-1/2 amplifies that error, so the bound is four times the
+    oracle's deviation when its symbol carries such an error (and r a 2^-24
+    perturbation), at least 1e-5.  The apply itself, given the oracle's
+    symbol, is held to 1e-5 at every size by the allocation-free entry
+    point's test."""
+    import math
     case, plan, _, lam = brain
-    r = case["x"]
-    z = torch.empty((case["n"], case["n"]), dtype=torch.complex64, device="cuda")
+    n, r = case["n"], case["x"]
+    rng = np.random.default_rng(2)
+    eps = 2.0 ** -24
+    z = torch.empty((n, n), dtype=torch.complex64, device="cuda")
     for a, b in [(1.0, MU), (0.8, 0.05)]:
+        want = toeplitz.precond_apply(r, lam, a, b)
+        d = rng.normal(size=lam.shape)
+        d *= eps * math.sqrt(math.log2(n * n)) * np.linalg.norm(lam) / np.linalg.norm(d)
+        dev = rel(toeplitz.precond_apply(r * (1 + eps * rng.normal(size=r.shape)), lam + d, a, b), want)
+        tol = max(TOL, 4 * dev)
         hq().precond_apply(plan, a, b, to_dev(r), z)
-        assert rel(to_host(z), toeplitz.precond_apply(r, lam, a, b)) <= TOL, (a, b)
+        err = rel(to_host(z), want)
+        print(f"320^2 preconditioner a={a} b={b}: {err:.2e} (bound {tol:.2e})")
+        assert err <= tol, (a, b, err, tol)
 
 
 @pytest.mark.parametrize("mode", ["plain", "fused"])
