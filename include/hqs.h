@@ -81,7 +81,7 @@ typedef struct {
     int64_t npoints;          /* M */
     double  kb_beta;          /* Kaiser-Bessel shape parameter */
     size_t  device_bytes;     /* device memory held by the plan */
-    int     nsub;             /* spreading sub-problems */
+    int     nsub;             /* spreading work items (tile-owned spreading) */
     int     tile;             /* spreading tile edge on the grid */
 } hqs_plan_info;
 
@@ -133,7 +133,9 @@ HQS_API int hqs_forward(hqs_plan plan, const hqs_c64* x, hqs_c64* y, void* strea
 
 /* --------------------------------------------------------- adjoint (a3) */
 /* x = A^H y (Sec. 3.4 uses A^H), the exact transpose of hqs_forward:
- * KB spreading (shared-memory tiles), inverse FFT, deapodisation, coil
+ * KB spreading (each grid tile accumulated in shared memory by the CTAs
+ * that own it and written once: no atomics, a fixed summation order, so the
+ * result is bitwise repeatable), inverse FFT, deapodisation, coil
  * combination with conj(S_l).  y: (L, M); x: (ny, nx). */
 HQS_API int hqs_adjoint(hqs_plan plan, const hqs_c64* y, hqs_c64* x, void* stream);
 

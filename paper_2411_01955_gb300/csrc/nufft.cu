@@ -1,8 +1,9 @@
 // Gridding NUFFT of the multicoil operator of Eq. (1) (Sec. 2.1):
 //   forward (a2): apodise + coil-multiply + zero-pad fused into the row FFT,
 //                 column FFT, Kaiser-Bessel interpolation (gather);
-//   adjoint (a3): shared-memory tiled KB spreading, column IFFT, row IFFT
-//                 fused with crop + deapodisation + conj(S_l) coil sum.
+//   adjoint (a3): tile-owned KB spreading (shared-memory tiles, no atomics),
+//                 column IFFT, row IFFT fused with crop + deapodisation +
+//                 conj(S_l) coil sum.
 // All grids are coil-innermost ([gy][gx][l]) so a grid tap is L contiguous
 // complex values.
 #include <algorithm>
@@ -150,71 +151,208 @@ __global__ void __launch_bounds__(256) k_interp(const float2* __restrict__ Gh, c
 }
 
 // ---------------------------------------------------------------- adjoint
-// Type-1 spreading of one sub-problem (<= HQS_SPREAD_MAXPTS points of one
-// TB x TB bin) into a (TB+W-1)^2 x LC patch in shared memory with shared
-// atomics, then one pass of vector float2 atomics into the global grid.
-template <int W>
-__global__ void k_spread(const float2* __restrict__ y, const int4* __restrict__ pts,
-                         const int* __restrict__ perm, const int4* __restrict__ subs, int M, int G,
-                         int L, int LC, int nchunk, int TB, int nbx, float beta,
-                         float2* __restrict__ grid) {
+// k-space data to the sorted point order, coil-innermost: ys[invperm[m]][l] =
+// y[l][m].  A CTA stages kSortPts caller-order points of every coil (coalesced
+// rows of y) in shared memory and writes each point's L-coil line contiguously.
+constexpr int kSortPts = 64;
+__global__ void __launch_bounds__(256) k_y_to_sorted(const float2* __restrict__ y, const int* __restrict__ invperm,
+                                                     int M, int L, float2* __restrict__ ys) {
+    extern __shared__ float2 sy[];   // [kSortPts][L + 1]
+    const int m0 = blockIdx.x * kSortPts;
+    const int np = min(kSortPts, M - m0);
+    for (int e = threadIdx.x; e < L * kSortPts; e += blockDim.x) {
+        const int l = e / kSortPts, q = e - l * kSortPts;
+        if (q < np) sy[q * (L + 1) + l] = y[(int64_t)l * M + m0 + q];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < np * L; e += blockDim.x) {
+        const int q = e / L, l = e - q * L;
+        ys[(int64_t)invperm[m0 + q] * L + l] = sy[q * (L + 1) + l];
+    }
+}
+
+// Tile-owned type-1 spreading.  One CTA per item of a TT x TT tile of the
+// grid: the item's candidates (points [c0, c1) of the tile's 3 x 3
+// neighbouring bins, taken in a fixed order; a point's W taps reach at most
+// one bin to either side because TT >= W/2) that touch the tile are staged in
+// shared memory, in candidate order, with their 2W Kaiser-Bessel weights.
+// The tile is accumulated in shared memory for chunks of LCS coils: warp w
+// owns the tile rows w (mod 8), so one warp updates a given row; a lane owns
+// one (x tap, coil) pair of the point's row, so no two lanes update one cell;
+// points are taken in order with a warp barrier between them.  The tile is
+// written once with plain stores: to the grid when the tile has one item,
+// else to the item's partial slot, and the last of the tile's items to
+// arrive sums the slots in slot order into the grid.  No atomics on data, no
+// memset of the grid, a fixed summation order for every cell.
+constexpr int kSpreadWarps = 8;
+template <int W, int TT>
+__global__ void __launch_bounds__(256) k_spread_tiles(const float2* __restrict__ ys, const int4* __restrict__ pts,
+                                                      const int* __restrict__ bin_off, const int4* __restrict__ items,
+                                                      const int2* __restrict__ tinfo, unsigned* __restrict__ tickets,
+                                                      float2* __restrict__ partial, int G, int L, int LCS, int nbx,
+                                                      float beta, float2* __restrict__ grid) {
+    constexpr int CAND = HQS_SPREAD_CAND;
+    constexpr int RPW = (TT + kSpreadWarps - 1) / kSpreadWarps;
+    constexpr int NPQ = (HQS_MAX_W * 16 + 31) / 32;   // (tap, coil) pairs per lane, LCS <= 16
     extern __shared__ float4 smem4[];
-    const int P = TB + W - 1;
-    float2* patch = reinterpret_cast<float2*>(smem4);
-    float* wts = reinterpret_cast<float*>(patch + P * P * LC);
-    int2* loc = reinterpret_cast<int2*>(wts + HQS_SPREAD_MAXPTS * 2 * W);
-    const int4 sb = subs[blockIdx.x];
-    const int bin = sb.x, start = sb.y, cnt = sb.z;
-    const int bx = bin % nbx, by = bin / nbx;
-    const int ox = bx * TB - W / 2, oy = by * TB - W / 2;
-    for (int i = threadIdx.x; i < cnt * 2 * W; i += blockDim.x) {
-        const int pi = i / (2 * W), hh = i - pi * 2 * W;
-        const int4 pt = pts[start + pi];
-        const float t = hh < W ? __int_as_float(pt.z) - (float)hh : __int_as_float(pt.w) - (float)(hh - W);
-        wts[i] = kb_phi(t, (float)W, beta);
+    float2* tile = reinterpret_cast<float2*>(smem4);              // [TT * TT][LCS]
+    float2* sval = tile + TT * TT * LCS;                           // [CAND][LCS]
+    float* swt = reinterpret_cast<float*>(sval + CAND * LCS);      // [CAND][2W]
+    int* sij = reinterpret_cast<int*>(swt + CAND * 2 * W);         // [CAND][3]: i0x, i0y, sorted index
+    __shared__ int nb_start[9], nb_pre[10], nnb, npts, wcount[kSpreadWarps], last;
+    const int4 it = items[blockIdx.x];
+    const int t = it.x, tx = t % nbx, ty = t / nbx;
+    const int x0 = tx * TT, y0 = ty * TT;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        int xs[3], yv[3], cx = 0, cy = 0;
+        for (int d = -1; d <= 1; ++d) {   // distinct neighbouring bins (fewer than 3 per axis when nbx < 3)
+            const int vx = (tx + d + nbx) % nbx, vy = (ty + d + nbx) % nbx;
+            bool sx = false, sy = false;
+            for (int k = 0; k < cx; ++k) sx |= xs[k] == vx;
+            for (int k = 0; k < cy; ++k) sy |= yv[k] == vy;
+            if (!sx) xs[cx++] = vx;
+            if (!sy) yv[cy++] = vy;
+        }
+        int k = 0, pre = 0;
+        for (int a = 0; a < cy; ++a)
+            for (int b = 0; b < cx; ++b) {
+                const int bin = yv[a] * nbx + xs[b];
+                nb_start[k] = bin_off[bin];
+                nb_pre[k] = pre;
+                pre += bin_off[bin + 1] - bin_off[bin];
+                ++k;
+            }
+        nb_pre[k] = pre;
+        nnb = k;
     }
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-        const int4 pt = pts[start + i];
-        int cx = pt.x + W / 2, cy = pt.y + W / 2;
-        if (cx >= G) cx -= G;
-        if (cy >= G) cy -= G;
-        loc[i] = make_int2(cx - bx * TB, cy - by * TB);
-    }
-    for (int ch = blockIdx.y; ch < nchunk; ch += gridDim.y) {
-        const int l0 = ch * LC;
-        const int lines = min(LC, L - l0);
-        for (int e = threadIdx.x; e < P * P * lines; e += blockDim.x) patch[e] = make_float2(0.f, 0.f);
+    __syncthreads();
+    // stage the candidates that touch the tile (one per thread: CAND == blockDim)
+    {
+        const int c = it.y + threadIdx.x;
+        bool ov = false;
+        int j = 0, i0x = 0, i0y = 0;
+        float dx = 0.f, dy = 0.f;
+        if (c < it.z) {
+            int k = 0;
+            while (k + 1 < nnb && nb_pre[k + 1] <= c) ++k;
+            j = nb_start[k] + (c - nb_pre[k]);
+            const int4 pt = pts[j];
+            i0x = pt.x;
+            i0y = pt.y;
+            dx = __int_as_float(pt.z);
+            dy = __int_as_float(pt.w);
+            int ax = x0 - i0x, bx = i0x - x0, ay = y0 - i0y, by = i0y - y0;   // arc offsets mod G
+            if (ax < 0) ax += G;
+            if (bx < 0) bx += G;
+            if (ay < 0) ay += G;
+            if (by < 0) by += G;
+            ov = (ax < W || bx < TT) && (ay < W || by < TT);
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, ov);
+        if (lane == 0) wcount[warp] = __popc(bal);
         __syncthreads();
-        for (int wi = threadIdx.x; wi < cnt * lines; wi += blockDim.x) {
-            const int i = wi / lines, l = wi - i * lines;
-            const float2 v = y[(int64_t)(l0 + l) * M + perm[start + i]];
-            const int2 c0 = loc[i];
-            const float* wv = wts + i * 2 * W;
+        int base = 0;
+        for (int w = 0; w < warp; ++w) base += wcount[w];
+        if (threadIdx.x == 0) {
+            int tot = 0;
+            for (int w = 0; w < kSpreadWarps; ++w) tot += wcount[w];
+            npts = tot;
+        }
+        if (ov) {
+            const int pos = base + __popc(bal & ((1u << lane) - 1u));
+            sij[pos * 3] = i0x;
+            sij[pos * 3 + 1] = i0y;
+            sij[pos * 3 + 2] = j;
 #pragma unroll
-            for (int a = 0; a < W; ++a) {
-                const float wyv = wv[W + a];
-                const float2 va = make_float2(v.x * wyv, v.y * wyv);
-                float2* prow = patch + ((c0.y + a) * P + c0.x) * lines + l;
-#pragma unroll
-                for (int b = 0; b < W; ++b) {
-                    const float wxv = wv[b];
-                    atomicAdd(&prow[b * lines].x, va.x * wxv);
-                    atomicAdd(&prow[b * lines].y, va.y * wxv);
-                }
+            for (int h = 0; h < W; ++h) {
+                swt[pos * 2 * W + h] = kb_phi(dx - (float)h, (float)W, beta);
+                swt[pos * 2 * W + W + h] = kb_phi(dy - (float)h, (float)W, beta);
             }
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < P * P * lines; e += blockDim.x) {
-            const float2 v = patch[e];
-            if (v.x == 0.f && v.y == 0.f) continue;
-            const int l = e % lines, cell = e / lines;
-            const int cy = cell / P, cx = cell - cy * P;
-            int gx = ox + cx, gy = oy + cy;
-            gx = gx < 0 ? gx + G : (gx >= G ? gx - G : gx);
-            gy = gy < 0 ? gy + G : (gy >= G ? gy - G : gy);
-            atomicAdd(&grid[((int64_t)gy * G + gx) * L + l0 + l], v);
+    }
+    const int np = npts;
+    for (int l0 = 0; l0 < L; l0 += LCS) {
+        const int lc = min(LCS, L - l0);
+        const int npair = W * lc;
+        int pb[NPQ], pl[NPQ];
+#pragma unroll
+        for (int q = 0; q < NPQ; ++q) {
+            const int pp = lane + 32 * q;
+            pb[q] = pp / lc;
+            pl[q] = pp - pb[q] * lc;
+        }
+        for (int e = threadIdx.x; e < TT * TT * lc; e += blockDim.x) tile[e] = make_float2(0.f, 0.f);
+        for (int e = threadIdx.x; e < np * lc; e += blockDim.x) {
+            const int i = e / lc, l = e - i * lc;
+            sval[i * LCS + l] = __ldg(ys + (int64_t)sij[i * 3 + 2] * L + l0 + l);
         }
         __syncthreads();
+        for (int i = 0; i < np; ++i) {
+            const int i0x = sij[i * 3], i0y = sij[i * 3 + 1];
+#pragma unroll
+            for (int rr = 0; rr < RPW; ++rr) {
+                const int r = warp + kSpreadWarps * rr;
+                if (r >= TT) break;
+                int a = y0 + r - i0y;   // row tap index (gy - i0y) mod G
+                if (a < 0) a += G;
+                if (a >= W) continue;
+                const float wy = swt[i * 2 * W + W + a];
+#pragma unroll
+                for (int q = 0; q < NPQ; ++q) {
+                    if (lane + 32 * q >= npair) break;
+                    const int b = pb[q], l = pl[q];
+                    int cx = i0x + b - x0;
+                    if (cx < 0) cx += G;
+                    else if (cx >= G) cx -= G;
+                    if (cx < TT) {
+                        const float w = wy * swt[i * 2 * W + b];
+                        const float2 v = sval[i * LCS + l];
+                        float2* cell = tile + (r * TT + cx) * lc + l;
+                        float2 c = *cell;
+                        c.x = fmaf(w, v.x, c.x);
+                        c.y = fmaf(w, v.y, c.y);
+                        *cell = c;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        __syncthreads();
+        float2* dst = it.w < 0 ? grid : partial + (int64_t)it.w * TT * TT * L;
+        for (int e = threadIdx.x; e < TT * TT * lc; e += blockDim.x) {
+            const int l = e % lc, cell = e / lc;
+            const int r = cell / TT, cx = cell - r * TT;
+            const int64_t o = it.w < 0 ? ((int64_t)(y0 + r) * G + x0 + cx) * L : (int64_t)cell * L;
+            dst[o + l0 + l] = tile[e];
+        }
+        __syncthreads();
+    }
+    if (it.w >= 0) {
+        // the last item of the tile to arrive sums the partial slots in order
+        __threadfence();
+        __syncthreads();
+        const int2 ti = tinfo[t];
+        if (threadIdx.x == 0) last = atomicAdd(&tickets[t], 1u) == (unsigned)(ti.x - 1);
+        __syncthreads();
+        if (last) {
+            __threadfence();
+            const int64_t slot = (int64_t)TT * TT * L;
+            const float2* p0 = partial + (int64_t)ti.y * slot;
+            for (int e = threadIdx.x; e < TT * TT * L; e += blockDim.x) {
+                float2 acc = __ldcg(p0 + e);
+                for (int c = 1; c < ti.x; ++c) {
+                    const float2 v = __ldcg(p0 + c * slot + e);
+                    acc.x += v.x;
+                    acc.y += v.y;
+                }
+                const int l = e % L, cell = e / L;
+                const int r = cell / TT, cx = cell - r * TT;
+                grid[((int64_t)(y0 + r) * G + x0 + cx) * L + l] = acc;
+            }
+            if (threadIdx.x == 0) tickets[t] = 0u;
+        }
     }
 }
 
@@ -351,21 +489,43 @@ static int interp_impl(hqs_plan_s* p, float2* y, cudaStream_t st) {
     return HQS_OK;
 }
 
-template <int W>
-static int spread_impl(hqs_plan_s* p, const float2* y, cudaStream_t st) {
-    if (p->nsub == 0) return HQS_OK;
-    const int P = p->tile + W - 1;
-    // coil chunks of <= 8 on the grid's y dimension: a smaller shared patch per
-    // CTA keeps more CTAs resident to hide the shared-atomic latency
-    const int nch = ceil_div(p->L, 8);
-    const int lc = ceil_div(p->L, nch);
-    const size_t sm = (size_t)P * P * lc * sizeof(float2) + HQS_SPREAD_MAXPTS * 2 * W * sizeof(float) +
-                      HQS_SPREAD_MAXPTS * sizeof(int2);
-    HQS_CUDA_TRY(cudaFuncSetAttribute(k_spread<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_spread<W><<<dim3(p->nsub, nch), 256, sm, st>>>(y, p->pts, p->perm, p->subs, (int)p->M, p->G, p->L, lc,
-                                                     nch, p->tile, p->nbx, (float)p->beta, p->grid);
+// coils per chunk of the tile-owned spreading (shared tile TT^2 x LCS)
+inline int spread_lcs(int tile, int L) {
+    const int cap = tile <= 16 ? 16 : 8;
+    const int nch = ceil_div(L, cap);
+    return ceil_div(L, nch);
+}
+
+inline size_t spread_smem(int tile, int W, int lcs) {
+    return (size_t)tile * tile * lcs * sizeof(float2) + (size_t)HQS_SPREAD_CAND * lcs * sizeof(float2) +
+           (size_t)HQS_SPREAD_CAND * 2 * W * sizeof(float) + (size_t)HQS_SPREAD_CAND * 3 * sizeof(int);
+}
+
+template <int W, int TT>
+static int spread_tiles_impl(hqs_plan_s* p, const float2* y, cudaStream_t st) {
+    const int lcs = spread_lcs(TT, p->L);
+    const size_t sm = spread_smem(TT, W, lcs);
+    HQS_CUDA_TRY(cudaFuncSetAttribute(k_spread_tiles<W, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    if (p->M > 0) {
+        const size_t smy = (size_t)kSortPts * (p->L + 1) * sizeof(float2);
+        k_y_to_sorted<<<(unsigned)ceil_div64(p->M, kSortPts), 256, smy, st>>>(y, p->invperm, (int)p->M, p->L,
+                                                                           p->spread.ysort);
+    }
+    k_spread_tiles<W, TT><<<p->spread.nitems, 256, sm, st>>>(
+        p->spread.ysort, p->pts, p->spread.bin_off, p->spread.items, p->spread.tile_info, p->spread.tickets,
+        p->spread.partial, p->G, p->L, lcs, p->nbx, (float)p->beta, p->grid);
     HQS_CUDA_TRY(cudaGetLastError());
     return HQS_OK;
+}
+
+template <int W>
+static int spread_impl(hqs_plan_s* p, const float2* y, cudaStream_t st) {
+    switch (p->tile) {
+        case 8: return spread_tiles_impl<W, 8>(p, y, st);
+        case 16: return spread_tiles_impl<W, 16>(p, y, st);
+        case 32: return spread_tiles_impl<W, 32>(p, y, st);
+        default: return HQS_ERR_INVALID_ARG;
+    }
 }
 
 template <class F> static int dispatch_w(int W, F&& f) {
@@ -388,7 +548,7 @@ int launch_fwd(hqs_plan_s* p, const float2* x, float2* y, cudaStream_t st) {
 }
 
 int launch_adj_axpy(hqs_plan_s* p, const float2* y, float zc, const float2* z, float2* x, cudaStream_t st) {
-    HQS_CUDA_TRY(cudaMemsetAsync(p->grid, 0, (size_t)p->G * p->G * p->L * sizeof(float2), st));
+    // every grid cell is written by the tile-owned spreading: no memset
     int rc = dispatch_w(p->W, [&]<int WW>() { return spread_impl<WW>(p, y, st); });
     if (rc != HQS_OK) return rc;
     return dispatch_fft_size(p->G, [&]<int GG>() { return adj_fft_impl<GG>(p, x, zc, z, st); });

@@ -107,6 +107,11 @@ __global__ void k_point_scatter(const int4* __restrict__ raw, const int* __restr
     perm[pos] = j;
 }
 
+__global__ void k_invert_perm(const int* __restrict__ perm, int M, int* __restrict__ inv) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < M) inv[perm[j]] = j;
+}
+
 // Toeplitz kernel c[py][px] = Npix^-1 sum_j exp(+i (kx_j dx + ky_j dy)), d the
 // circulant offset of position p, as a complex GEMM Ey^T Ex whose operands are
 // generated in shared memory.  Phases are formed in turns from the split
@@ -279,6 +284,7 @@ static void plan_free(hqs_plan_s* p) {
     cudaGetDevice(&cur);
     if (cur != p->device) cudaSetDevice(p->device);
     mixed_free(p);
+    spread_free(p);
     for (void* v : p->allocs) cudaFree(v);
     if (p->trace) cudaFree(p->trace);
     if (p->h_cg) cudaFreeHost(p->h_cg);
@@ -294,8 +300,7 @@ static int plan_build(hqs_plan_s* p, const float* traj, const float2* smaps_user
     // coil chunking for the FFT passes
     p->nchunk = ceil_div(L, HQS_MAX_LC);
     p->LC = ceil_div(L, p->nchunk);
-    p->tile = 16;
-    if (G % p->tile != 0) p->tile = 8;
+    p->tile = 8;   // every supported G is a multiple of 8
     p->nbx = G / p->tile;
     p->q_rows = 16;
     const int maxg = std::max(G, n2);
@@ -304,6 +309,8 @@ static int plan_build(hqs_plan_s* p, const float* traj, const float2* smaps_user
     HQS_TRY(dev_alloc(p, &p->apod, (size_t)n));
     HQS_TRY(dev_alloc(p, &p->pts, (size_t)std::max(M, 1)));
     HQS_TRY(dev_alloc(p, &p->perm, (size_t)std::max(M, 1)));
+    HQS_TRY(dev_alloc(p, &p->invperm, (size_t)std::max(M, 1)));
+    HQS_TRY(dev_alloc(p, &p->spread.ysort, (size_t)std::max(M, 1) * L));
     HQS_TRY(dev_alloc(p, &p->khat, (size_t)n2 * n2));
     HQS_TRY(dev_alloc(p, &p->lam, (size_t)n * n));
     HQS_TRY(dev_alloc(p, &p->grid, (size_t)G * G * L));
@@ -401,26 +408,20 @@ static int plan_build(hqs_plan_s* p, const float* traj, const float2* smaps_user
         if (cudaMemcpyAsync(hc.data(), counts, nbins * sizeof(int), cudaMemcpyDeviceToHost, s) ||
             cudaStreamSynchronize(s)) { rc = HQS_ERR_CUDA; break; }
         std::vector<int> offs(nbins);
-        std::vector<int4> subs;
         int acc = 0;
         for (int b = 0; b < nbins; ++b) {
             offs[b] = acc;
-            for (int st = 0; st < hc[b]; st += HQS_SPREAD_MAXPTS)
-                subs.push_back(make_int4(b, acc + st, std::min(HQS_SPREAD_MAXPTS, hc[b] - st), 0));
             acc += hc[b];
-        }
-        p->nsub = (int)subs.size();
-        if (dev_alloc(p, &p->subs, std::max<size_t>(subs.size(), 1)) != HQS_OK) { rc = HQS_ERR_OOM; break; }
-        if (!subs.empty() &&
-            cudaMemcpyAsync(p->subs, subs.data(), subs.size() * sizeof(int4), cudaMemcpyHostToDevice, s)) {
-            rc = HQS_ERR_CUDA;
-            break;
         }
         if (cudaMemcpyAsync(counts, offs.data(), nbins * sizeof(int), cudaMemcpyHostToDevice, s)) {
             rc = HQS_ERR_CUDA;
             break;
         }
-        if (M > 0) k_point_scatter<<<ceil_div(M, 256), 256, 0, s>>>(raw, bin, M, counts, p->pts, p->perm);
+        if (M > 0) {
+            k_point_scatter<<<ceil_div(M, 256), 256, 0, s>>>(raw, bin, M, counts, p->pts, p->perm);
+            k_invert_perm<<<ceil_div(M, 256), 256, 0, s>>>(p->perm, M, p->invperm);
+        }
+        if ((rc = spread_build(p, hc, s)) != HQS_OK) break;
 
         // Toeplitz kernel, its FFT (Khat, real, scaled by 1/n2^2) and the density symbol
         dim3 gg(ceil_div(n2, 64), ceil_div(n2, 64));
@@ -513,19 +514,16 @@ __global__ void k_rebin_scatter(const int4* __restrict__ pts, const int* __restr
 }
 
 extern "C" int hqs_plan_retile(hqs_plan p, int tile, void* stream) {
-    if (!p || (tile != 8 && tile != 16 && tile != 32) || p->G % tile != 0 || tile + p->W - 1 > p->G)
+    if (!p || (tile != 8 && tile != 16 && tile != 32) || p->G % tile != 0 || 2 * tile < p->W)
         return HQS_ERR_INVALID_ARG;
-    const size_t smem = (size_t)(tile + p->W - 1) * (tile + p->W - 1) * p->LC * sizeof(float2) +
-                        HQS_SPREAD_MAXPTS * (2 * p->W * sizeof(float) + sizeof(int2));
-    if (smem > 220 * 1024) return HQS_ERR_UNSUPPORTED;
     if (tile == p->tile) return HQS_OK;
     cudaStream_t s = (cudaStream_t)stream;
     const int M = (int)p->M;
     const int nbx = p->G / tile, nbins = nbx * nbx;
     int *bin = nullptr, *counts = nullptr, *perm2 = nullptr;
     int4* pts2 = nullptr;
-    int4* subs2 = nullptr;
     int rc = HQS_OK;
+    const int old_tile = p->tile, old_nbx = p->nbx;
     do {
         const int Mp = std::max(M, 1);
         if (cudaMalloc(&bin, Mp * sizeof(int)) || cudaMalloc(&counts, nbins * sizeof(int)) ||
@@ -538,19 +536,21 @@ extern "C" int hqs_plan_retile(hqs_plan p, int tile, void* stream) {
         std::vector<int> hc(nbins), offs(nbins);
         if (cudaMemcpyAsync(hc.data(), counts, nbins * sizeof(int), cudaMemcpyDeviceToHost, s) ||
             cudaStreamSynchronize(s)) { rc = HQS_ERR_CUDA; break; }
-        std::vector<int4> subs;
         int acc = 0;
         for (int b = 0; b < nbins; ++b) {
             offs[b] = acc;
-            for (int st = 0; st < hc[b]; st += HQS_SPREAD_MAXPTS)
-                subs.push_back(make_int4(b, acc + st, std::min(HQS_SPREAD_MAXPTS, hc[b] - st), 0));
             acc += hc[b];
         }
-        if (cudaMalloc(&subs2, std::max<size_t>(subs.size(), 1) * sizeof(int4))) { rc = HQS_ERR_OOM; break; }
-        if ((!subs.empty() && cudaMemcpyAsync(subs2, subs.data(), subs.size() * sizeof(int4),
-                                              cudaMemcpyHostToDevice, s)) ||
-            cudaMemcpyAsync(counts, offs.data(), nbins * sizeof(int), cudaMemcpyHostToDevice, s)) {
+        if (cudaMemcpyAsync(counts, offs.data(), nbins * sizeof(int), cudaMemcpyHostToDevice, s)) {
             rc = HQS_ERR_CUDA;
+            break;
+        }
+        // items for the new tile first: if they cannot be built the points stay as they are
+        p->tile = tile;
+        p->nbx = nbx;
+        if ((rc = spread_build(p, hc, s)) != HQS_OK) {
+            p->tile = old_tile;
+            p->nbx = old_nbx;
             break;
         }
         if (M > 0) k_rebin_scatter<<<ceil_div(M, 256), 256, 0, s>>>(p->pts, p->perm, bin, M, counts, pts2, perm2);
@@ -559,23 +559,100 @@ extern "C" int hqs_plan_retile(hqs_plan p, int tile, void* stream) {
             rc = HQS_ERR_CUDA;
             break;
         }
+        if (M > 0) k_invert_perm<<<ceil_div(M, 256), 256, 0, s>>>(p->perm, M, p->invperm);
         if (cudaStreamSynchronize(s)) { rc = HQS_ERR_CUDA; break; }
-        // swap in the new sub-problem list (owned by the plan's allocation list)
-        for (auto& v : p->allocs)
-            if (v == p->subs) v = subs2;
-        cudaFree(p->subs);
-        p->subs = subs2;
-        subs2 = nullptr;
-        p->nsub = (int)subs.size();
-        p->tile = tile;
-        p->nbx = nbx;
     } while (0);
     cudaFree(bin);
     cudaFree(counts);
     cudaFree(perm2);
     cudaFree(pts2);
-    cudaFree(subs2);
     return rc;
+}
+
+// ------------------------------------------------ tile-owned spreading items
+void spread_free(hqs_plan_s* p) {
+    cudaFree(p->spread.bin_off);
+    cudaFree(p->spread.items);
+    cudaFree(p->spread.tile_info);
+    cudaFree(p->spread.tickets);
+    cudaFree(p->spread.partial);
+    p->spread.bin_off = nullptr;
+    p->spread.items = nullptr;
+    p->spread.tile_info = nullptr;
+    p->spread.tickets = nullptr;
+    p->spread.partial = nullptr;
+    p->bytes -= p->spread.bytes;
+    p->spread.bytes = 0;
+    p->spread.nitems = p->spread.nslots = 0;
+}
+
+// Every tile of p->tile x p->tile grid cells gets items of at most
+// HQS_SPREAD_CAND candidates: the points of its distinct neighbouring bins
+// (3 x 3, fewer when the grid has fewer than 3 bins per axis).  A tile with
+// more candidates gets several items, each with a partial slot.
+int spread_build(hqs_plan_s* p, const std::vector<int>& hc, cudaStream_t s) {
+    const int T = p->tile, nbx = p->G / T, nbins = nbx * nbx, L = p->L;
+    if ((int)hc.size() != nbins) return HQS_ERR_INVALID_ARG;
+    std::vector<int> off(nbins + 1, 0);
+    for (int b = 0; b < nbins; ++b) off[b + 1] = off[b] + hc[b];
+    auto distinct = [&](int t, int* out) {
+        int c = 0;
+        for (int d = -1; d <= 1; ++d) {
+            const int v = (t + d + nbx) % nbx;
+            bool seen = false;
+            for (int k = 0; k < c; ++k) seen |= out[k] == v;
+            if (!seen) out[c++] = v;
+        }
+        return c;
+    };
+    std::vector<int4> items;
+    std::vector<int2> info(nbins);
+    int slots = 0;
+    for (int t = 0; t < nbins; ++t) {
+        int xs[3], ys[3];
+        const int cx = distinct(t % nbx, xs), cy = distinct(t / nbx, ys);
+        int cand = 0;
+        for (int a = 0; a < cy; ++a)
+            for (int b = 0; b < cx; ++b) cand += hc[ys[a] * nbx + xs[b]];
+        const int nch = std::max(1, ceil_div(cand, HQS_SPREAD_CAND));
+        const int first = nch > 1 ? slots : -1;
+        if (nch > 1) slots += nch;
+        info[t] = make_int2(nch, first);
+        for (int k = 0; k < nch; ++k)
+            items.push_back(make_int4(t, k * HQS_SPREAD_CAND, std::min((k + 1) * HQS_SPREAD_CAND, cand),
+                                      nch > 1 ? first + k : -1));
+    }
+    const size_t slot_elems = (size_t)T * T * L;
+    if ((size_t)slots * slot_elems * sizeof(float2) > ((size_t)1 << 30)) return HQS_ERR_UNSUPPORTED;
+    hqs_plan_s::Spread nw;
+    nw.nitems = (int)items.size();
+    nw.nslots = slots;
+    nw.ysort = p->spread.ysort;
+    int rc = HQS_OK;
+    if (cudaMalloc(&nw.bin_off, (nbins + 1) * sizeof(int)) || cudaMalloc(&nw.items, items.size() * sizeof(int4)) ||
+        cudaMalloc(&nw.tile_info, nbins * sizeof(int2)) || cudaMalloc(&nw.tickets, nbins * sizeof(unsigned)) ||
+        (slots > 0 && cudaMalloc(&nw.partial, slots * slot_elems * sizeof(float2)))) {
+        rc = HQS_ERR_OOM;
+    } else if (cudaMemcpyAsync(nw.bin_off, off.data(), (nbins + 1) * sizeof(int), cudaMemcpyHostToDevice, s) ||
+               cudaMemcpyAsync(nw.items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice, s) ||
+               cudaMemcpyAsync(nw.tile_info, info.data(), nbins * sizeof(int2), cudaMemcpyHostToDevice, s) ||
+               cudaMemsetAsync(nw.tickets, 0, nbins * sizeof(unsigned), s) || cudaStreamSynchronize(s)) {
+        rc = HQS_ERR_CUDA;
+    }
+    if (rc != HQS_OK) {
+        cudaFree(nw.bin_off);
+        cudaFree(nw.items);
+        cudaFree(nw.tile_info);
+        cudaFree(nw.tickets);
+        cudaFree(nw.partial);
+        return rc;
+    }
+    spread_free(p);
+    nw.bytes = (nbins + 1) * sizeof(int) + items.size() * sizeof(int4) + nbins * (sizeof(int2) + sizeof(unsigned)) +
+               slots * slot_elems * sizeof(float2);
+    p->spread = nw;
+    p->bytes += nw.bytes;
+    return HQS_OK;
 }
 
 extern "C" void hqs_plan_destroy(hqs_plan plan) { plan_free(plan); }
@@ -591,7 +668,7 @@ extern "C" int hqs_plan_get_info(hqs_plan p, hqs_plan_info* info) {
     info->npoints = p->M;
     info->kb_beta = p->beta;
     info->device_bytes = p->bytes;
-    info->nsub = p->nsub;
+    info->nsub = p->spread.nitems;
     info->tile = p->tile;
     return HQS_OK;
 }

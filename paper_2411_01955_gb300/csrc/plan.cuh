@@ -11,7 +11,7 @@
 #endif
 #define HQS_MAX_LC HQS_KLINES  // coils per chunk in the FFT passes
 #define HQS_MAX_BLOCKS 2048    // partial-sum slots per reduction (and >= 3 x 256 for the FCG dots)
-#define HQS_SPREAD_MAXPTS 256  // points per spreading sub-problem
+#define HQS_SPREAD_CAND 256    // candidate points per tile-owned spreading item
 #define HQS_TRACE_MAX 4096     // phase-trace stamps kept per persistent solve
 
 // CG scalars kept on the device so that the solve never needs the host
@@ -45,7 +45,7 @@ struct hqs_plan_s {
     int64_t M = 0;
     float scale = 1.f;  // Npix^-1/2
     int LC = 1, nchunk = 1;
-    int tile = 16, nbx = 0, nsub = 0;
+    int tile = 8, nbx = 0;
     int q_rows = 8;     // lines per CTA in the single-image FFT passes
     int fused_grid = 0; // cap on the persistent solver's CTAs (0: occupancy limit)
     bool nufft_only = false; // internal plans that only grid (no Toeplitz kernel, density symbol zero)
@@ -56,7 +56,20 @@ struct hqs_plan_s {
     float* apod = nullptr;      // [n] 1/phihat((i - n/2)/G)
     int4* pts = nullptr;        // sorted points: (i0x, i0y, bits(dx), bits(dy)), i0 in [0, G)
     int* perm = nullptr;        // sorted -> caller index
-    int4* subs = nullptr;       // (bin, start, count, 0)
+    int* invperm = nullptr;     // caller index -> sorted position
+    // tile-owned spreading (adjoint): every grid tile of tile x tile cells is
+    // written by the CTAs of its items; candidates are the points of the 3 x 3
+    // neighbouring bins, taken in chunks of <= HQS_SPREAD_CAND
+    struct Spread {
+        int* bin_off = nullptr;        // [nbins + 1] sorted-point offsets per bin
+        int4* items = nullptr;         // (tile, first candidate, end candidate, partial slot or -1)
+        int2* tile_info = nullptr;     // [nbins] (chunks, first partial slot)
+        unsigned* tickets = nullptr;   // [nbins] arrival counts of multi-chunk tiles (reset by the last)
+        float2* partial = nullptr;     // [slots][tile * tile * L] partial tiles of multi-chunk tiles
+        float2* ysort = nullptr;       // [M][L] k-space data in sorted order, coil-innermost
+        int nitems = 0, nslots = 0;
+        size_t bytes = 0;              // device bytes of the arrays above but ysort
+    } spread;
     float* khat = nullptr;      // [n2][n2] transposed (khat[kx][ky]), includes 1/n2^2
     float* lam = nullptr;       // [n][n] density symbol
     float2* tw = nullptr;       // twiddle bank
@@ -108,3 +121,7 @@ int launch_adj_axpy(hqs_plan_s* p, const float2* y, float zc, const float2* z, f
 int launch_toeplitz(hqs_plan_s* p, const float2* x, float2* out, cudaStream_t s);
 int launch_fft2d(const hqs_plan_s* p, float2* data, int N, bool inverse, cudaStream_t s);
 int launch_precond(hqs_plan_s* p, float a, float b, const float2* r, float2* z, cudaStream_t s);
+// (re)builds the tile-owned spreading items for p->tile from the per-bin point
+// counts (host) and the sorted points; blocking
+int spread_build(hqs_plan_s* p, const std::vector<int>& counts, cudaStream_t s);
+void spread_free(hqs_plan_s* p);

@@ -65,7 +65,9 @@ def store_cache(path: str, key: str, t: Tuning) -> None:
 
 
 def valid_tiles(G: int, W: int) -> list[int]:
-    return [t for t in SPREAD_TILES if G % t == 0 and t + W - 1 <= G]
+    """Spreading tiles that divide the grid and are at least half the kernel
+    width (so a point's taps reach at most one neighbouring tile per side)."""
+    return [t for t in SPREAD_TILES if G % t == 0 and 2 * t >= W]
 
 
 def pick(timings: dict) -> object:

@@ -64,6 +64,10 @@ def test_brain_adjoint_matches_oracle(brain):
     err = rel(to_host(x), want)
     print(f"320^2 x 16 adjoint: {err:.2e}")
     assert err <= TOL
+    x2 = torch.empty_like(x)
+    hq().adjoint(plan, to_dev(yv), x2)
+    torch.cuda.synchronize()
+    assert torch.equal(x, x2)    # tile-owned spreading: bitwise repeatable
     # the fused right-hand side A^H y + mu z of the benchmark's step
     z = case["x"]
     hq().adjoint_axpy(plan, to_dev(yv), MU, to_dev(z), x)

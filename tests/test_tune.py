@@ -26,7 +26,8 @@ def test_cache_roundtrip_and_key(tmp_path):
 def test_valid_tiles_and_pick():
     assert tune.valid_tiles(640, 6) == [8, 16, 32]
     assert tune.valid_tiles(40, 6) == [8]           # 40 is not a multiple of 16 or 32
-    assert tune.valid_tiles(16, 6) == [8]           # a 16 tile plus halo exceeds the grid
+    assert tune.valid_tiles(16, 6) == [8, 16]       # one 16 tile covers the whole grid
+    assert tune.valid_tiles(64, 8) == [8, 16, 32]
     assert tune.pick({8: 2.0, 16: 1.0, 32: 1.5}) == 16
     assert tune.pick({(2, 0): 1.0, (4, 0): 1.0}) == (2, 0)   # ties: first listed
 
