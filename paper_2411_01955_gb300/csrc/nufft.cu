@@ -175,30 +175,30 @@ __global__ void __launch_bounds__(256) k_y_to_sorted(const float2* __restrict__ 
 // grid: the item's candidates (points [c0, c1) of the tile's 3 x 3
 // neighbouring bins, taken in a fixed order; a point's W taps reach at most
 // one bin to either side because TT >= W/2) that touch the tile are staged in
-// shared memory, in candidate order, with their 2W Kaiser-Bessel weights.
-// The tile is accumulated in shared memory for chunks of LCS coils: warp w
-// owns the tile rows w (mod 8), so one warp updates a given row; a lane owns
-// one (x tap, coil) pair of the point's row, so no two lanes update one cell;
-// points are taken in order with a warp barrier between them.  The tile is
-// written once with plain stores: to the grid when the tile has one item,
-// else to the item's partial slot, and the last of the tile's items to
-// arrive sums the slots in slot order into the grid.  No atomics on data, no
-// memset of the grid, a fixed summation order for every cell.
+// shared memory, in candidate order, with their plan-time Kaiser-Bessel
+// weights, their first tap relative to the tile and their k-space values.
+// Warp w owns the tile rows w (mod 8); for one row and a chunk of LCS coils a
+// lane owns the (cell, coil) pairs p = lane + 32 k of the row and keeps their
+// sums in registers while it walks the staged points in order, so no two
+// threads ever update one cell and every cell is summed in the same order.
+// The row is then written once with plain stores: to the grid when the tile
+// has one item, else to the item's partial slot, and the last of the tile's
+// items to arrive sums the slots in slot order into the grid.  No atomics on
+// data and no memset of the grid.
 constexpr int kSpreadWarps = 8;
 template <int W, int TT>
 __global__ void __launch_bounds__(256) k_spread_tiles(const float2* __restrict__ ys, const int4* __restrict__ pts,
-                                                      const int* __restrict__ bin_off, const int4* __restrict__ items,
-                                                      const int2* __restrict__ tinfo, unsigned* __restrict__ tickets,
-                                                      float2* __restrict__ partial, int G, int L, int LCS, int nbx,
-                                                      float beta, float2* __restrict__ grid) {
+                                                      const float* __restrict__ kbw, const int* __restrict__ bin_off,
+                                                      const int4* __restrict__ items, const int2* __restrict__ tinfo,
+                                                      unsigned* __restrict__ tickets, float2* __restrict__ partial,
+                                                      int G, int L, int LCS, int nbx, float2* __restrict__ grid) {
     constexpr int CAND = HQS_SPREAD_CAND;
-    constexpr int RPW = (TT + kSpreadWarps - 1) / kSpreadWarps;
-    constexpr int NPQ = (HQS_MAX_W * 16 + 31) / 32;   // (tap, coil) pairs per lane, LCS <= 16
+    constexpr int NK = (TT * 16 + 31) / 32;   // (cell, coil) pairs of a row per lane, LCS <= 16
     extern __shared__ float4 smem4[];
-    float2* tile = reinterpret_cast<float2*>(smem4);              // [TT * TT][LCS]
-    float2* sval = tile + TT * TT * LCS;                           // [CAND][LCS]
+    float2* sval = reinterpret_cast<float2*>(smem4);              // [CAND][LCS]
     float* swt = reinterpret_cast<float*>(sval + CAND * LCS);      // [CAND][2W]
-    int* sij = reinterpret_cast<int*>(swt + CAND * 2 * W);         // [CAND][3]: i0x, i0y, sorted index
+    int2* soff = reinterpret_cast<int2*>(swt + CAND * 2 * W);      // [CAND]: first tap - tile origin (x, y)
+    int* sidx = reinterpret_cast<int*>(soff + CAND);               // [CAND]: sorted point index
     __shared__ int nb_start[9], nb_pre[10], nnb, npts, wcount[kSpreadWarps], last;
     const int4 it = items[blockIdx.x];
     const int t = it.x, tx = t % nbx, ty = t / nbx;
@@ -227,27 +227,25 @@ __global__ void __launch_bounds__(256) k_spread_tiles(const float2* __restrict__
         nnb = k;
     }
     __syncthreads();
-    // stage the candidates that touch the tile (one per thread: CAND == blockDim)
+    // stage the candidates that touch the tile, in candidate order (CAND == blockDim)
     {
         const int c = it.y + threadIdx.x;
         bool ov = false;
-        int j = 0, i0x = 0, i0y = 0;
-        float dx = 0.f, dy = 0.f;
+        int j = 0, ox = 0, oy = 0;
         if (c < it.z) {
             int k = 0;
             while (k + 1 < nnb && nb_pre[k + 1] <= c) ++k;
             j = nb_start[k] + (c - nb_pre[k]);
             const int4 pt = pts[j];
-            i0x = pt.x;
-            i0y = pt.y;
-            dx = __int_as_float(pt.z);
-            dy = __int_as_float(pt.w);
-            int ax = x0 - i0x, bx = i0x - x0, ay = y0 - i0y, by = i0y - y0;   // arc offsets mod G
-            if (ax < 0) ax += G;
-            if (bx < 0) bx += G;
-            if (ay < 0) ay += G;
-            if (by < 0) by += G;
-            ov = (ax < W || bx < TT) && (ay < W || by < TT);
+            // first tap relative to the tile, on the periodic grid: in [0, TT) when the
+            // taps start inside the tile, in [-(W-1), 0) when they start left of it
+            ox = pt.x - x0;
+            oy = pt.y - y0;
+            if (ox < 0) ox += G;
+            if (oy < 0) oy += G;
+            if (ox >= TT) ox -= G;
+            if (oy >= TT) oy -= G;
+            ov = ox > -W && oy > -W;
         }
         const unsigned bal = __ballot_sync(0xffffffffu, ov);
         if (lane == 0) wcount[warp] = __popc(bal);
@@ -261,71 +259,60 @@ __global__ void __launch_bounds__(256) k_spread_tiles(const float2* __restrict__
         }
         if (ov) {
             const int pos = base + __popc(bal & ((1u << lane) - 1u));
-            sij[pos * 3] = i0x;
-            sij[pos * 3 + 1] = i0y;
-            sij[pos * 3 + 2] = j;
-#pragma unroll
-            for (int h = 0; h < W; ++h) {
-                swt[pos * 2 * W + h] = kb_phi(dx - (float)h, (float)W, beta);
-                swt[pos * 2 * W + W + h] = kb_phi(dy - (float)h, (float)W, beta);
-            }
+            soff[pos] = make_int2(ox, oy);
+            sidx[pos] = j;
         }
         __syncthreads();
     }
     const int np = npts;
+    for (int e = threadIdx.x; e < np * 2 * W; e += blockDim.x) {
+        const int i = e / (2 * W), h = e - i * (2 * W);
+        swt[e] = __ldg(kbw + (int64_t)sidx[i] * 2 * W + h);
+    }
     for (int l0 = 0; l0 < L; l0 += LCS) {
         const int lc = min(LCS, L - l0);
-        const int npair = W * lc;
-        int pb[NPQ], pl[NPQ];
-#pragma unroll
-        for (int q = 0; q < NPQ; ++q) {
-            const int pp = lane + 32 * q;
-            pb[q] = pp / lc;
-            pl[q] = pp - pb[q] * lc;
-        }
-        for (int e = threadIdx.x; e < TT * TT * lc; e += blockDim.x) tile[e] = make_float2(0.f, 0.f);
         for (int e = threadIdx.x; e < np * lc; e += blockDim.x) {
             const int i = e / lc, l = e - i * lc;
-            sval[i * LCS + l] = __ldg(ys + (int64_t)sij[i * 3 + 2] * L + l0 + l);
+            sval[i * LCS + l] = __ldg(ys + (int64_t)sidx[i] * L + l0 + l);
         }
         __syncthreads();
-        for (int i = 0; i < np; ++i) {
-            const int i0x = sij[i * 3], i0y = sij[i * 3 + 1];
+        const int npair = TT * lc;
+        int px[NK], pl[NK];
 #pragma unroll
-            for (int rr = 0; rr < RPW; ++rr) {
-                const int r = warp + kSpreadWarps * rr;
-                if (r >= TT) break;
-                int a = y0 + r - i0y;   // row tap index (gy - i0y) mod G
-                if (a < 0) a += G;
-                if (a >= W) continue;
+        for (int k = 0; k < NK; ++k) {
+            const int pp = lane + 32 * k;
+            px[k] = pp / lc;
+            pl[k] = pp - px[k] * lc;
+        }
+        float2* dst = it.w < 0 ? grid : partial + (int64_t)it.w * TT * TT * L;
+        for (int r = warp; r < TT; r += kSpreadWarps) {
+            float2 acc[NK];
+#pragma unroll
+            for (int k = 0; k < NK; ++k) acc[k] = make_float2(0.f, 0.f);
+            for (int i = 0; i < np; ++i) {
+                const int2 o = soff[i];
+                // the point's row tap for this row (the wrap matters only when the tile is
+                // the whole grid: there a footprint can leave its right edge and re-enter)
+                int a = r - o.y;
+                a += a < 0 ? G : 0;
+                if ((unsigned)a >= (unsigned)W) continue;
                 const float wy = swt[i * 2 * W + W + a];
 #pragma unroll
-                for (int q = 0; q < NPQ; ++q) {
-                    if (lane + 32 * q >= npair) break;
-                    const int b = pb[q], l = pl[q];
-                    int cx = i0x + b - x0;
-                    if (cx < 0) cx += G;
-                    else if (cx >= G) cx -= G;
-                    if (cx < TT) {
-                        const float w = wy * swt[i * 2 * W + b];
-                        const float2 v = sval[i * LCS + l];
-                        float2* cell = tile + (r * TT + cx) * lc + l;
-                        float2 c = *cell;
-                        c.x = fmaf(w, v.x, c.x);
-                        c.y = fmaf(w, v.y, c.y);
-                        *cell = c;
-                    }
+                for (int k = 0; k < NK; ++k) {
+                    int b = px[k] - o.x;
+                    b += b < 0 ? G : 0;
+                    const int bc = min(max(b, 0), W - 1);
+                    float w = swt[i * 2 * W + bc];
+                    w = ((unsigned)b < (unsigned)W) ? w * wy : 0.f;
+                    const float2 v = sval[i * LCS + pl[k]];
+                    acc[k].x = fmaf(w, v.x, acc[k].x);
+                    acc[k].y = fmaf(w, v.y, acc[k].y);
                 }
             }
-            __syncwarp();
-        }
-        __syncthreads();
-        float2* dst = it.w < 0 ? grid : partial + (int64_t)it.w * TT * TT * L;
-        for (int e = threadIdx.x; e < TT * TT * lc; e += blockDim.x) {
-            const int l = e % lc, cell = e / lc;
-            const int r = cell / TT, cx = cell - r * TT;
-            const int64_t o = it.w < 0 ? ((int64_t)(y0 + r) * G + x0 + cx) * L : (int64_t)cell * L;
-            dst[o + l0 + l] = tile[e];
+            const int64_t rowo = it.w < 0 ? ((int64_t)(y0 + r) * G + x0) * L : (int64_t)r * TT * L;
+#pragma unroll
+            for (int k = 0; k < NK; ++k)
+                if (lane + 32 * k < npair) dst[rowo + (int64_t)px[k] * L + l0 + pl[k]] = acc[k];
         }
         __syncthreads();
     }
@@ -489,22 +476,42 @@ static int interp_impl(hqs_plan_s* p, float2* y, cudaStream_t st) {
     return HQS_OK;
 }
 
+// Kaiser-Bessel weights of every sorted point: kbw[j][h] = phi(dx_j - h),
+// kbw[j][W + h] = phi(dy_j - h), h < W (a plan-time table of the spreading).
+__global__ void k_point_weights(const int4* __restrict__ pts, int M, int W, float beta, float* __restrict__ kbw) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= (int64_t)M * 2 * W) return;
+    const int j = (int)(e / (2 * W)), h = (int)(e - (int64_t)j * 2 * W);
+    const int4 pt = pts[j];
+    const float t = h < W ? __int_as_float(pt.z) - (float)h : __int_as_float(pt.w) - (float)(h - W);
+    kbw[e] = kb_phi(t, (float)W, beta);
+}
+
+int launch_point_weights(hqs_plan_s* p, cudaStream_t st) {
+    if (p->M == 0) return HQS_OK;
+    const int64_t cnt = p->M * 2 * p->W;
+    k_point_weights<<<(unsigned)ceil_div64(cnt, 256), 256, 0, st>>>(p->pts, (int)p->M, p->W, (float)p->beta,
+                                                                     p->spread.kbw);
+    HQS_CUDA_TRY(cudaGetLastError());
+    return HQS_OK;
+}
+
 // coils per chunk of the tile-owned spreading (shared tile TT^2 x LCS)
 inline int spread_lcs(int tile, int L) {
-    const int cap = tile <= 16 ? 16 : 8;
-    const int nch = ceil_div(L, cap);
+    (void)tile;
+    const int nch = ceil_div(L, 16);
     return ceil_div(L, nch);
 }
 
-inline size_t spread_smem(int tile, int W, int lcs) {
-    return (size_t)tile * tile * lcs * sizeof(float2) + (size_t)HQS_SPREAD_CAND * lcs * sizeof(float2) +
-           (size_t)HQS_SPREAD_CAND * 2 * W * sizeof(float) + (size_t)HQS_SPREAD_CAND * 3 * sizeof(int);
+inline size_t spread_smem(int W, int lcs) {
+    return (size_t)HQS_SPREAD_CAND * lcs * sizeof(float2) + (size_t)HQS_SPREAD_CAND * 2 * W * sizeof(float) +
+           (size_t)HQS_SPREAD_CAND * (sizeof(int2) + sizeof(int));
 }
 
 template <int W, int TT>
 static int spread_tiles_impl(hqs_plan_s* p, const float2* y, cudaStream_t st) {
     const int lcs = spread_lcs(TT, p->L);
-    const size_t sm = spread_smem(TT, W, lcs);
+    const size_t sm = spread_smem(W, lcs);
     HQS_CUDA_TRY(cudaFuncSetAttribute(k_spread_tiles<W, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     if (p->M > 0) {
         const size_t smy = (size_t)kSortPts * (p->L + 1) * sizeof(float2);
@@ -512,8 +519,8 @@ static int spread_tiles_impl(hqs_plan_s* p, const float2* y, cudaStream_t st) {
                                                                            p->spread.ysort);
     }
     k_spread_tiles<W, TT><<<p->spread.nitems, 256, sm, st>>>(
-        p->spread.ysort, p->pts, p->spread.bin_off, p->spread.items, p->spread.tile_info, p->spread.tickets,
-        p->spread.partial, p->G, p->L, lcs, p->nbx, (float)p->beta, p->grid);
+        p->spread.ysort, p->pts, p->spread.kbw, p->spread.bin_off, p->spread.items, p->spread.tile_info,
+        p->spread.tickets, p->spread.partial, p->G, p->L, lcs, p->nbx, p->grid);
     HQS_CUDA_TRY(cudaGetLastError());
     return HQS_OK;
 }

@@ -311,6 +311,7 @@ static int plan_build(hqs_plan_s* p, const float* traj, const float2* smaps_user
     HQS_TRY(dev_alloc(p, &p->perm, (size_t)std::max(M, 1)));
     HQS_TRY(dev_alloc(p, &p->invperm, (size_t)std::max(M, 1)));
     HQS_TRY(dev_alloc(p, &p->spread.ysort, (size_t)std::max(M, 1) * L));
+    HQS_TRY(dev_alloc(p, &p->spread.kbw, (size_t)std::max(M, 1) * 2 * p->W));
     HQS_TRY(dev_alloc(p, &p->khat, (size_t)n2 * n2));
     HQS_TRY(dev_alloc(p, &p->lam, (size_t)n * n));
     HQS_TRY(dev_alloc(p, &p->grid, (size_t)G * G * L));
@@ -421,6 +422,7 @@ static int plan_build(hqs_plan_s* p, const float* traj, const float2* smaps_user
             k_point_scatter<<<ceil_div(M, 256), 256, 0, s>>>(raw, bin, M, counts, p->pts, p->perm);
             k_invert_perm<<<ceil_div(M, 256), 256, 0, s>>>(p->perm, M, p->invperm);
         }
+        if ((rc = launch_point_weights(p, s)) != HQS_OK) break;
         if ((rc = spread_build(p, hc, s)) != HQS_OK) break;
 
         // Toeplitz kernel, its FFT (Khat, real, scaled by 1/n2^2) and the density symbol
@@ -560,6 +562,7 @@ extern "C" int hqs_plan_retile(hqs_plan p, int tile, void* stream) {
             break;
         }
         if (M > 0) k_invert_perm<<<ceil_div(M, 256), 256, 0, s>>>(p->perm, M, p->invperm);
+        if ((rc = launch_point_weights(p, s)) != HQS_OK) break;
         if (cudaStreamSynchronize(s)) { rc = HQS_ERR_CUDA; break; }
     } while (0);
     cudaFree(bin);
@@ -628,6 +631,7 @@ int spread_build(hqs_plan_s* p, const std::vector<int>& hc, cudaStream_t s) {
     nw.nitems = (int)items.size();
     nw.nslots = slots;
     nw.ysort = p->spread.ysort;
+    nw.kbw = p->spread.kbw;
     int rc = HQS_OK;
     if (cudaMalloc(&nw.bin_off, (nbins + 1) * sizeof(int)) || cudaMalloc(&nw.items, items.size() * sizeof(int4)) ||
         cudaMalloc(&nw.tile_info, nbins * sizeof(int2)) || cudaMalloc(&nw.tickets, nbins * sizeof(unsigned)) ||

@@ -67,6 +67,7 @@ struct hqs_plan_s {
         unsigned* tickets = nullptr;   // [nbins] arrival counts of multi-chunk tiles (reset by the last)
         float2* partial = nullptr;     // [slots][tile * tile * L] partial tiles of multi-chunk tiles
         float2* ysort = nullptr;       // [M][L] k-space data in sorted order, coil-innermost
+        float* kbw = nullptr;          // [M][2W] Kaiser-Bessel weights of the sorted points (x taps, y taps)
         int nitems = 0, nslots = 0;
         size_t bytes = 0;              // device bytes of the arrays above but ysort
     } spread;
@@ -124,4 +125,5 @@ int launch_precond(hqs_plan_s* p, float a, float b, const float2* r, float2* z, 
 // (re)builds the tile-owned spreading items for p->tile from the per-bin point
 // counts (host) and the sorted points; blocking
 int spread_build(hqs_plan_s* p, const std::vector<int>& counts, cudaStream_t s);
+int launch_point_weights(hqs_plan_s* p, cudaStream_t s);   // spread.kbw from the sorted points
 void spread_free(hqs_plan_s* p);
