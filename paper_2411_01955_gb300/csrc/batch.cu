@@ -511,10 +511,17 @@ __global__ void __launch_bounds__(HQS_BATCH_BD, 2) k_pcg_batch(DcBatchArgs B) {
         if (!grid_barrier(B.bar, B.err)) return;                                             \
         if (B.trace && bid == 0 && threadIdx.x == 0 && ntr < B.trace_max) B.trace[ntr++] = global_ns(); \
     } while (0)
+    // Each phase deals its items in the opposite slice order to the phase before, so
+    // that it starts on the slices whose data the previous phase touched last (still
+    // in L2 when the batch's intermediates do not all fit).
+    int pdir = 0;
 #define FOR_ITEMS(list, ...)                                                               \
     {                                                                                      \
         const int* off_ = B.off + (list) * (ns + 1);                                       \
-        for (int g_ = bid; g_ < off_[ns]; g_ += G) {                                       \
+        const int tot_ = off_[ns];                                                         \
+        pdir ^= 1;                                                                         \
+        for (int k_ = bid; k_ < tot_; k_ += G) {                                           \
+            const int g_ = pdir ? tot_ - 1 - k_ : k_;                                      \
             const int si = find_slice(off_, ns, g_);                                       \
             if (!active[si]) continue;                                                     \
             const int it_ = g_ - off_[si];                                                 \

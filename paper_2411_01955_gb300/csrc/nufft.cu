@@ -186,7 +186,12 @@ __global__ void __launch_bounds__(256) k_y_to_sorted(const float2* __restrict__ 
 // items to arrive sums the slots in slot order into the grid.  No atomics on
 // data and no memset of the grid.
 constexpr int kSpreadWarps = 8;
-template <int W, int TT>
+// FULL16: every coil chunk has exactly 16 coils (L a multiple of 16).  Then lane
+// (h, l) = (lane / 16, lane % 16) owns coil l of the cells x = h + 2 k of a row,
+// and each staged point's x weights over the tile row are tabulated once
+// (wrow[i][h][k], zero outside the footprint), so a cell update is one
+// multiply-add pair on registers.
+template <int W, int TT, bool FULL16>
 __global__ void __launch_bounds__(256) k_spread_tiles(const float2* __restrict__ ys, const int4* __restrict__ pts,
                                                       const float* __restrict__ kbw, const int* __restrict__ bin_off,
                                                       const int4* __restrict__ items, const int2* __restrict__ tinfo,
@@ -199,6 +204,7 @@ __global__ void __launch_bounds__(256) k_spread_tiles(const float2* __restrict__
     float* swt = reinterpret_cast<float*>(sval + CAND * LCS);      // [CAND][2W]
     int2* soff = reinterpret_cast<int2*>(swt + CAND * 2 * W);      // [CAND]: first tap - tile origin (x, y)
     int* sidx = reinterpret_cast<int*>(soff + CAND);               // [CAND]: sorted point index
+    float* wrow = reinterpret_cast<float*>(sidx + CAND);           // FULL16: [CAND][2][TT / 2]
     __shared__ int nb_start[9], nb_pre[10], nnb, npts, wcount[kSpreadWarps], last;
     const int4 it = items[blockIdx.x];
     const int t = it.x, tx = t % nbx, ty = t / nbx;
@@ -269,7 +275,54 @@ __global__ void __launch_bounds__(256) k_spread_tiles(const float2* __restrict__
         const int i = e / (2 * W), h = e - i * (2 * W);
         swt[e] = __ldg(kbw + (int64_t)sidx[i] * 2 * W + h);
     }
-    for (int l0 = 0; l0 < L; l0 += LCS) {
+    if constexpr (FULL16) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < np * TT; e += blockDim.x) {
+            const int i = e / TT, x = e - i * TT;
+            int b = x - soff[i].x;
+            b += b < 0 ? G : 0;
+            wrow[i * TT + (x & 1) * (TT / 2) + (x >> 1)] = (unsigned)b < (unsigned)W ? swt[i * 2 * W + b] : 0.f;
+        }
+        const int h = lane >> 4, l = lane & 15;
+        for (int l0 = 0; l0 < L; l0 += 16) {
+            for (int e = threadIdx.x; e < np * 16; e += blockDim.x) {
+                const int i = e >> 4, ll = e & 15;
+                sval[i * 16 + ll] = __ldg(ys + (int64_t)sidx[i] * L + l0 + ll);
+            }
+            __syncthreads();
+            float2* dst = it.w < 0 ? grid : partial + (int64_t)it.w * TT * TT * L;
+            for (int r = warp; r < TT; r += kSpreadWarps) {
+                float2 acc[TT / 2];
+#pragma unroll
+                for (int k = 0; k < TT / 2; ++k) acc[k] = make_float2(0.f, 0.f);
+                for (int i = 0; i < np; ++i) {
+                    int a = r - soff[i].y;
+                    a += a < 0 ? G : 0;
+                    if ((unsigned)a >= (unsigned)W) continue;
+                    const float wy = swt[i * 2 * W + W + a];
+                    float2 v = sval[i * 16 + l];
+                    v.x *= wy;
+                    v.y *= wy;
+                    const float4* wr = reinterpret_cast<const float4*>(wrow + i * TT + h * (TT / 2));
+#pragma unroll
+                    for (int k4 = 0; k4 < TT / 8; ++k4) {
+                        const float4 w4 = wr[k4];
+                        const float wk[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            acc[4 * k4 + q].x = fmaf(wk[q], v.x, acc[4 * k4 + q].x);
+                            acc[4 * k4 + q].y = fmaf(wk[q], v.y, acc[4 * k4 + q].y);
+                        }
+                    }
+                }
+                const int64_t rowo = it.w < 0 ? ((int64_t)(y0 + r) * G + x0) * L : (int64_t)r * TT * L;
+#pragma unroll
+                for (int k = 0; k < TT / 2; ++k) dst[rowo + (int64_t)(h + 2 * k) * L + l0 + l] = acc[k];
+            }
+            __syncthreads();
+        }
+    }
+    for (int l0 = 0; !FULL16 && l0 < L; l0 += LCS) {
         const int lc = min(LCS, L - l0);
         for (int e = threadIdx.x; e < np * lc; e += blockDim.x) {
             const int i = e / lc, l = e - i * lc;
@@ -503,22 +556,24 @@ inline int spread_lcs(int tile, int L) {
     return ceil_div(L, nch);
 }
 
-inline size_t spread_smem(int W, int lcs) {
+inline size_t spread_smem(int W, int lcs, int tile) {
     return (size_t)HQS_SPREAD_CAND * lcs * sizeof(float2) + (size_t)HQS_SPREAD_CAND * 2 * W * sizeof(float) +
-           (size_t)HQS_SPREAD_CAND * (sizeof(int2) + sizeof(int));
+           (size_t)HQS_SPREAD_CAND * (sizeof(int2) + sizeof(int)) + (size_t)HQS_SPREAD_CAND * tile * sizeof(float);
 }
 
 template <int W, int TT>
 static int spread_tiles_impl(hqs_plan_s* p, const float2* y, cudaStream_t st) {
     const int lcs = spread_lcs(TT, p->L);
-    const size_t sm = spread_smem(W, lcs);
-    HQS_CUDA_TRY(cudaFuncSetAttribute(k_spread_tiles<W, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    const bool full16 = p->L % 16 == 0;
+    const size_t sm = spread_smem(W, lcs, full16 ? TT : 0);
+    auto kern = full16 ? k_spread_tiles<W, TT, true> : k_spread_tiles<W, TT, false>;
+    HQS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     if (p->M > 0) {
         const size_t smy = (size_t)kSortPts * (p->L + 1) * sizeof(float2);
         k_y_to_sorted<<<(unsigned)ceil_div64(p->M, kSortPts), 256, smy, st>>>(y, p->invperm, (int)p->M, p->L,
                                                                            p->spread.ysort);
     }
-    k_spread_tiles<W, TT><<<p->spread.nitems, 256, sm, st>>>(
+    kern<<<p->spread.nitems, 256, sm, st>>>(
         p->spread.ysort, p->pts, p->spread.kbw, p->spread.bin_off, p->spread.items, p->spread.tile_info,
         p->spread.tickets, p->spread.partial, p->G, p->L, lcs, p->nbx, p->grid);
     HQS_CUDA_TRY(cudaGetLastError());

@@ -625,6 +625,9 @@ int spread_build(hqs_plan_s* p, const std::vector<int>& hc, cudaStream_t s) {
             items.push_back(make_int4(t, k * HQS_SPREAD_CAND, std::min((k + 1) * HQS_SPREAD_CAND, cand),
                                       nch > 1 ? first + k : -1));
     }
+    // heaviest items first: the long ones start at once instead of at the end
+    std::stable_sort(items.begin(), items.end(),
+                     [](const int4& u, const int4& v) { return u.z - u.y > v.z - v.y; });
     const size_t slot_elems = (size_t)T * T * L;
     if ((size_t)slots * slot_elems * sizeof(float2) > ((size_t)1 << 30)) return HQS_ERR_UNSUPPORTED;
     hqs_plan_s::Spread nw;
