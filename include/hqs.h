@@ -362,10 +362,19 @@ HQS_API const char* hqs_status_string(int status);
  *   HQS_TUNE_FUSED_GRID  cap on the persistent solve's CTAs (0 = all resident)
  *   HQS_TUNE_PC_LINES    preconditioner rows/columns per work item (1..16)
  *   HQS_TUNE_SPREAD_TILE spreading tile edge (8, 16 or 32): re-bins the
- *                        plan's points (hqs_plan_retile on the default stream) */
+ *                        plan's points (hqs_plan_retile on the default stream)
+ * and one test hook for the failure path of the persistent solve:
+ *   HQS_TUNE_DEBUG_BARRIER_SKIP  1 arms it for the next HQS_SOLVE_FUSED solve
+ *                        only: that solve's last CTA leaves before the first
+ *                        grid barrier and the barrier waits are cut to about
+ *                        10 ms, so the others' waits run out and the solve
+ *                        returns HQS_ERR_TIMEOUT (no result); the barrier
+ *                        words are reset at every launch, so the next solve
+ *                        on the plan runs normally. */
 #define HQS_TUNE_FUSED_GRID   1
 #define HQS_TUNE_PC_LINES     2
 #define HQS_TUNE_SPREAD_TILE  3
+#define HQS_TUNE_DEBUG_BARRIER_SKIP 4
 HQS_API int hqs_plan_set_tuning(hqs_plan plan, int key, int value);
 /* Re-sorts the plan's points into tile x tile spreading bins (8, 16, 32);
  * BLOCKING on `stream`.  The result of hqs_adjoint does not depend on the tile

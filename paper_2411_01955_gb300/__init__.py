@@ -18,5 +18,6 @@ from ._lib import (  # noqa: F401
     last_solve_info, hqs_run, gaussian_denoise, power_iteration, status_string,
     debug_phase_trace, plan_set_tuning, precond_apply_noalloc,
     Net, plan_set_net, learned_precond_apply, Batch, plan_retile, toeplitz_stage, pgd_run, estimate_smaps, HQS_TUNE_SPREAD_TILE, HQS_TUNE_FUSED_GRID, HQS_TUNE_PC_LINES,
+    HQS_TUNE_DEBUG_BARRIER_SKIP,
     Plan3d, plan3d_create, forward3d, adjoint3d, toeplitz_normal3d, plan3d_khat, dc_solve3d, precond_apply3d, gaussian_denoise3d, hqs_run3d,
 )

@@ -22,6 +22,7 @@ HQS_PRECOND_NONE, HQS_PRECOND_DC, HQS_PRECOND_LEARNED = 0, 1, 2
 HQS_SOLVE_PLAIN, HQS_SOLVE_FUSED = 0, 1
 HQS_SOLVE_X0_ZERO = 16
 HQS_TUNE_FUSED_GRID, HQS_TUNE_PC_LINES, HQS_TUNE_SPREAD_TILE = 1, 2, 3
+HQS_TUNE_DEBUG_BARRIER_SKIP = 4
 HQS_MAX_ITERS = 512
 
 _PKG = os.path.dirname(os.path.abspath(__file__))

@@ -47,6 +47,8 @@ struct FusedArgs {
     unsigned* err;
     unsigned long long* trace;  // optional: globaltimer stamp after each barrier
     int trace_max;
+    int skip_cta;               // test hook: this CTA leaves before the first barrier (-1: none)
+    long long barrier_limit;    // grid barrier wait limit, SM clock cycles
 };
 
 
@@ -179,6 +181,7 @@ __global__ void __launch_bounds__(FftSize<N2>::TPL * kLines,
     const ToepArgs& A = F.A;
     const int n = A.n, nch = A.nchunk;
     const int G = gridDim.x, bid = blockIdx.x;
+    if (bid == F.skip_cta) return;   // test hook: the others' first barrier wait runs out
     const int count = n * n;
     const int npc = (n + F.Q - 1) / F.Q;
     float2* twN = s + (size_t)N2 * kLines + N + N2;
@@ -193,7 +196,7 @@ __global__ void __launch_bounds__(FftSize<N2>::TPL * kLines,
     if (lead && F.trace && F.trace_max > 0) F.trace[ntrace++] = global_ns();
 #define BARRIER()                                                            \
     do {                                                                     \
-        if (!grid_barrier(F.bar, F.err)) return;                             \
+        if (!grid_barrier(F.bar, F.err, F.barrier_limit)) return;            \
         if (lead && F.trace && ntrace < F.trace_max) F.trace[ntrace++] = global_ns(); \
     } while (0)
 
@@ -404,6 +407,11 @@ static int pcg_fused_impl(hqs_plan_s* p, float a, float b, const float2* rhs, fl
     int grid = std::min(per_sm * nsm, N2 * p->nchunk);
     grid = std::min(grid, HQS_MAX_BLOCKS);
     if (p->fused_grid > 0) grid = std::min(grid, p->fused_grid);
+    // test hook (one-shot): the last CTA leaves at once and the waits are cut to
+    // about 10 ms, so the solve ends with HQS_ERR_TIMEOUT instead of a result
+    F.skip_cta = p->debug_barrier_skip ? grid - 1 : -1;
+    F.barrier_limit = p->debug_barrier_skip ? 20000000ll : HQS_BARRIER_LIMIT_CYCLES;
+    p->debug_barrier_skip = 0;
     HQS_CUDA_TRY(cudaMemsetAsync(p->barrier, 0, 2 * sizeof(unsigned), st));
     HQS_CUDA_TRY(cudaMemsetAsync(p->dev_err, 0, sizeof(unsigned), st));
     void* args[] = {&F};
@@ -457,6 +465,10 @@ extern "C" int hqs_plan_set_tuning(hqs_plan p, int key, int value) {
             return HQS_OK;
         case HQS_TUNE_SPREAD_TILE:
             return hqs_plan_retile(p, value, nullptr);
+        case HQS_TUNE_DEBUG_BARRIER_SKIP:
+            if (value != 0 && value != 1) return HQS_ERR_INVALID_ARG;
+            p->debug_barrier_skip = value;
+            return HQS_OK;
         default:
             return HQS_ERR_INVALID_ARG;
     }

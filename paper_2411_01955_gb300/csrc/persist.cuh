@@ -14,8 +14,9 @@ HQS_DEV unsigned long long global_ns() {
 }
 
 // Grid-wide barrier (cooperative launch: all CTAs are resident).  Returns
-// false when the wait exceeded its limit or another CTA reported an error.
-HQS_DEV bool grid_barrier(unsigned* bar, unsigned* err) {
+// false when the wait exceeded `limit` SM clock cycles (about a second by
+// default) or another CTA reported an error.
+HQS_DEV bool grid_barrier(unsigned* bar, unsigned* err, long long limit = HQS_BARRIER_LIMIT_CYCLES) {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -35,7 +36,7 @@ HQS_DEV bool grid_barrier(unsigned* bar, unsigned* err) {
                     ok = 0;
                     break;
                 }
-                if (clock64() - t0 > HQS_BARRIER_LIMIT_CYCLES) {
+                if (clock64() - t0 > limit) {
                     atomicOr(err, HQS_DEVERR_TIMEOUT);
                     ok = 0;
                     break;

@@ -50,6 +50,7 @@ struct hqs_plan_s {
     int fused_grid = 0; // cap on the persistent solver's CTAs (0: occupancy limit)
     bool nufft_only = false; // internal plans that only grid (no Toeplitz kernel, density symbol zero)
     int pc_lines = 4;   // preconditioner lines per item in the persistent solver (1..16)
+    int debug_barrier_skip = 0;  // test hook for the next persistent solve (HQS_TUNE_DEBUG_BARRIER_SKIP)
 
     // constant tables and plan data (device)
     float2* smaps = nullptr;    // [n][n][L]

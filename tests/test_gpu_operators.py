@@ -414,6 +414,33 @@ def test_power_iteration_matches_oracle():
     assert abs(got / want - 1) < 1e-3
 
 
+def test_fused_solve_reports_a_barrier_timeout_and_recovers():
+    """The persistent solve's failure path, made to happen without a GPU
+    fault: with the test hook armed, one CTA leaves before the first grid
+    barrier, the others' bounded waits (cut to about 10 ms) run out, and the
+    solve returns HQS_ERR_TIMEOUT; the next solve on the same plan runs
+    normally and matches a solve on a fresh plan bit for bit."""
+    case = quantised(synth.tiny_case(0))
+    plan, _, _ = make_plan(case)
+    n, mu = case["n"], 1e-2
+    rhs = to_dev(nufft.adjoint(case["noise"], case["smaps"], case["traj"], case["W"], case["sigma"]))
+    fused = hq().HQS_SOLVE_FUSED | hq().HQS_SOLVE_X0_ZERO
+    hq().plan_set_tuning(plan, hq().HQS_TUNE_DEBUG_BARRIER_SKIP, 1)
+    x = torch.zeros((n, n), dtype=torch.complex64, device="cuda")
+    info = hq().dc_solve(plan, 1.0, mu, rhs, x, max_iter=50, rel_tol=1e-4, mode=fused, check=False)
+    assert info.rc == hq().HQS_ERR_TIMEOUT and info.status == hq().HQS_ERR_TIMEOUT
+    x2 = torch.zeros_like(x)
+    info2 = hq().dc_solve(plan, 1.0, mu, rhs, x2, max_iter=50, rel_tol=1e-4, mode=fused)
+    assert info2.status == 0 and info2.rel_residual <= 1e-4
+    plan_b, _, _ = make_plan(case)
+    x3 = torch.zeros_like(x)
+    hq().dc_solve(plan_b, 1.0, mu, rhs, x3, max_iter=50, rel_tol=1e-4, mode=fused)
+    torch.cuda.synchronize()
+    assert torch.equal(x2, x3)
+    with pytest.raises(hq().HqsError):
+        hq().plan_set_tuning(plan, hq().HQS_TUNE_DEBUG_BARRIER_SKIP, 2)
+
+
 @pytest.mark.parametrize("grid", [0, 37, 100])
 def test_fused_line_balanced_passes(grid):
     """16 coils: the persistent solve deals (row, coil) and (column, coil)
