@@ -247,6 +247,15 @@ def cpu_oracle_vol_sample(case):
     return time.perf_counter() - t0
 
 
+def tests_module(name):
+    """A helper module of the test suite (tests/ is not a package)."""
+    import importlib
+    tdir = os.path.join(ROOT, "tests")
+    if tdir not in sys.path:
+        sys.path.insert(0, tdir)
+    return importlib.import_module(name)
+
+
 def threads_used():
     try:
         return len(os.sched_getaffinity(0))
@@ -846,7 +855,7 @@ def run_hqs320(args, rank, world, dist):
     # the two other pieces of a reconstruction run here: S-map estimation from the
     # 20 x 20 Hamming-windowed k-space centre (once per scan) and the GPU conv denoiser
     # D_sigma (once per outer step in place of the Gaussian smoothing)
-    from paper_2411_01955_gb300 import learned
+    learned = tests_module("learned_training")
     smaps_out = torch.empty((L, n, n), dtype=torch.complex64, device="cuda")
     net = hq.Net()
     net.set_params(learned.initial_params(0))
@@ -890,7 +899,7 @@ def run_learned320(args, rank, world, dist):
     import time as _time
     import torch
     import paper_2411_01955_gb300 as hq
-    from paper_2411_01955_gb300 import learned
+    learned = tests_module("learned_training")
     import synth
 
     dev = int(os.environ.get("LOCAL_RANK", "0"))

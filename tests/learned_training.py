@@ -1,4 +1,7 @@
-"""Training data and training loop for the learned CG preconditioner.
+"""Training data and training loop for the learned CG preconditioner (test
+and benchmark infrastructure: the tests and the learned-preconditioner
+benchmark workload train networks with it; the product library itself only
+runs the network's forward, backward and Adam kernels).
 
 Pairs come from the plain solver (Sec. 3.4's data-consistency system with
 P = Id): for a right-hand side b, x* is solved to a tight tolerance with
@@ -14,7 +17,7 @@ from __future__ import annotations
 import numpy as np
 import torch
 
-from . import _lib as hq
+import paper_2411_01955_gb300 as hq
 
 
 LAYERS = ((2, 32), (32, 32), (32, 32), (32, 2))   # (in, out) channels of the 3x3 convolutions

@@ -122,7 +122,7 @@ def make_slices(seeds, n=128, L=8):
 
 
 def test_learned_fcg_trains_converges_and_falls_back():
-    from paper_2411_01955_gb300 import learned
+    import learned_training as learned
     mu = 1e-2
     train_slices = make_slices(range(1000, 1006))
     test_slices = make_slices(range(5000, 5002))
@@ -249,7 +249,7 @@ def test_residual_trained_net_in_flexible_cg():
     DC-PCG residuals, the network lowers it on held-out slices below the DC
     preconditioner's; flexible CG with it converges (falling back if it
     stalls), and its iteration count is reported beside DC-PCG's."""
-    from paper_2411_01955_gb300 import learned
+    import learned_training as learned
     mu = 1e-2
     train_slices = make_slices(range(1000, 1008))
     test_slices = make_slices(range(5000, 5003))
@@ -306,7 +306,7 @@ def test_trained_net_denoiser_and_hqs_with_it():
     """Trained on synthetic phantoms (noise std 0.02-0.2 per part, images
     scaled to max 1), the conv denoiser lowers the held-out error well below
     the noisy input's; annealed HQS runs with it as the native denoiser."""
-    from paper_2411_01955_gb300 import learned
+    import learned_training as learned
     n = 128
     def imgs(seeds):
         out = []

@@ -427,14 +427,14 @@ def test_fused_solve_reports_a_barrier_timeout_and_recovers():
     fused = hq().HQS_SOLVE_FUSED | hq().HQS_SOLVE_X0_ZERO
     hq().plan_set_tuning(plan, hq().HQS_TUNE_DEBUG_BARRIER_SKIP, 1)
     x = torch.zeros((n, n), dtype=torch.complex64, device="cuda")
-    info = hq().dc_solve(plan, 1.0, mu, rhs, x, max_iter=50, rel_tol=1e-4, mode=fused, check=False)
+    info = hq().dc_solve(plan, 1.0, mu, rhs, x, max_iter=300, rel_tol=1e-4, mode=fused, check=False)
     assert info.rc == hq().HQS_ERR_TIMEOUT and info.status == hq().HQS_ERR_TIMEOUT
     x2 = torch.zeros_like(x)
-    info2 = hq().dc_solve(plan, 1.0, mu, rhs, x2, max_iter=50, rel_tol=1e-4, mode=fused)
+    info2 = hq().dc_solve(plan, 1.0, mu, rhs, x2, max_iter=300, rel_tol=1e-4, mode=fused)
     assert info2.status == 0 and info2.rel_residual <= 1e-4
     plan_b, _, _ = make_plan(case)
     x3 = torch.zeros_like(x)
-    hq().dc_solve(plan_b, 1.0, mu, rhs, x3, max_iter=50, rel_tol=1e-4, mode=fused)
+    hq().dc_solve(plan_b, 1.0, mu, rhs, x3, max_iter=300, rel_tol=1e-4, mode=fused)
     torch.cuda.synchronize()
     assert torch.equal(x2, x3)
     with pytest.raises(hq().HqsError):
