@@ -116,7 +116,8 @@ def parse():
     ap.add_argument("--phase-trace", action="store_true",
                     help="batched dc320: add the per-phase time of one traced batched solve to the line")
     ap.add_argument("--workload", default="dc320",
-                    choices=["dc320", "batch64", "mixed320", "hqs320", "learned320", "vol64", "vol128"])
+                    choices=["dc320", "batch64", "mixed320", "mixedsizes", "hqs320", "learned320", "vol64",
+                             "vol128"])
     return ap.parse_args()
 
 
@@ -555,14 +556,20 @@ def batch_phase_trace(bt, rhs, xs, hq):
     bt.debug_trace(True)
     bt.dc_solve(rhs, xs, 1.0, MU, max_iter=MAX_ITER, rel_tol=TOL)
     st = bt.debug_trace(False)
+    its = [it for it, _, _ in bt.dc_info()]
     d = np.diff(np.array(st, dtype=np.float64)) / 1e3
     body = d[3:-1]
-    out = {"setup": [round(float(v), 1) for v in d[:3]], "iterations": int(math.ceil(len(body) / 7))}
+    nit = int(math.ceil(len(body) / 7))
+    out = {"setup": [round(float(v), 1) for v in d[:3]], "iterations": nit}
     for k, name in enumerate(BATCH_PHASES):
         v = body[k::7]
         if len(v):
             out[name] = round(float(np.mean(v)), 1)
     out["total_ms"] = round(float((st[-1] - st[0]) / 1e6), 3)
+    # per batched iteration: its time and the number of slices still iterating
+    out["per_iteration_us"] = [round(float(np.sum(body[7 * k:7 * k + 7])), 1) for k in range(nit)]
+    out["active_slices"] = [sum(1 for i in its if i > k) for k in range(nit)]
+    out["slice_iterations"] = its
     return out
 
 
@@ -775,6 +782,51 @@ def run_mixed320(args, rank, world, dist):
         "precisions": res, "gemm_flops_per_aha": gemm_flops,
         "gpu_launches_per_mixed_aha": 6, "clocks": clocks,
     }
+    print(json.dumps(line), flush=True)
+
+
+def run_mixed_sizes(args, rank, world, dist):
+    """A^H A microseconds per apply with the Toeplitz passes as FP32 in-house
+    FFTs and as BF16x3 / FP16x3 tensor-core DFT-GEMMs, over the image sizes
+    the DFT-GEMM path supports (n a multiple of 64, <= 384), 16 coils, a
+    variable-density spiral scaled with n; CUDA events over 50 applies."""
+    import torch
+    import paper_2411_01955_gb300 as hq
+    import synth
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    L = 16
+    rows = {}
+    clk = ClockSampler(dev)
+    clk.start()
+    for n in (64, 128, 256, 320, 384):
+        traj = torch.from_numpy(synth.traj_spiral(16, max(256, int(2048 * n / 320)), n)).cuda()
+        smaps = torch.from_numpy(synth.coil_maps(0, n, L).astype(np.complex64)).cuda()
+        plan = hq.plan_create(traj, n, n, smaps, 6, 2.0)
+        x = torch.from_numpy(synth.phantom(0, n).astype(np.complex64)).cuda()
+        y = torch.empty_like(x)
+        row = {}
+        for name, prec in (("fp32", hq.HQS_PREC_FP32), ("bf16x3", hq.HQS_PREC_BF16X3), ("fp16x3", hq.HQS_PREC_FP16X3)):
+            for _ in range(max(args.warmup, 3)):
+                hq.toeplitz_normal(plan, x, y, precision=prec)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(50):
+                hq.toeplitz_normal(plan, x, y, precision=prec)
+            e1.record()
+            torch.cuda.synchronize()
+            row[name] = e0.elapsed_time(e1) * 1e3 / 50
+        rows[n] = row
+        plan.close()
+    clocks = clk.stop()
+    if rank != 0:
+        return
+    line = {"metric": "A^H A microseconds per apply: FP32 in-house FFTs vs BF16x3 / FP16x3 DFT-GEMMs, 16 coils",
+            "value": rows[320]["bf16x3"] / rows[320]["fp32"], "unit": "BF16x3 / FP32 time at 320^2",
+            "n_gpus": world, "higher_is_better": False, "data": "synthetic (seeded phantoms, coil maps, VD spiral)",
+            "config": {"workload": "image sizes 64-384, 16 coils, spiral 16 interleaves scaled with n, W 6, sigma 2"},
+            "aha_us": {str(k): v for k, v in rows.items()}, "clocks": clocks}
     print(json.dumps(line), flush=True)
 
 
@@ -1185,6 +1237,8 @@ def main():
         run_batch64(args, rank, world, dist)
     elif args.workload == "mixed320":
         run_mixed320(args, rank, world, dist)
+    elif args.workload == "mixedsizes":
+        run_mixed_sizes(args, rank, world, dist)
     elif args.workload == "hqs320":
         run_hqs320(args, rank, world, dist)
     elif args.workload == "learned320":
