@@ -100,6 +100,111 @@ __global__ void k_fwd_cols(const float2* __restrict__ U, int n, int L, int LC, i
     }
 }
 
+// ---- passes with the image in the lower half of each line (G = 2n, 16-coil chunks)
+// With G = 2n the centred placement p = (i - n/2) mod G of pixel i is the circular
+// shift by n/2 of position q = i, so FFT_G of the centred line is i^k times the FFT of
+// the line holding the image in its lower half [0, n), and the centred output pixels
+// of an inverse transform are the lower half of the inverse of (-i)^k X[k].  The first
+// forward stage then skips the zero half and reads straight from global memory, the
+// last inverse stage skips the discarded half, and stores go straight to global
+// memory (the I/O hooks of block_fft_io, which need every thread to own a line).
+HQS_DEV float2 mul_ipow(float2 v, int k) {   // v * i^k, k >= 0
+    switch (k & 3) {
+        case 0: return v;
+        case 1: return make_float2(-v.y, v.x);
+        case 2: return make_float2(-v.x, -v.y);
+        default: return make_float2(v.y, -v.x);
+    }
+}
+HQS_DEV float2 mul_mipow(float2 v, int k) { return mul_ipow(v, 4 - (k & 3)); }   // v * (-i)^k
+
+template <int G>
+__global__ void k_fwd_rows_h(const float2* __restrict__ x, const float2* __restrict__ smaps,
+                             const float* __restrict__ apod, int n, int L, float scale,
+                             const float2* __restrict__ twg, float2* __restrict__ U) {
+    extern __shared__ float2 s[];
+    const float2* tw = stage_twiddles<G>(s + G * kLines, twg);
+    const int iy = blockIdx.x, l0 = blockIdx.y * kLines;
+    const float ay = apod[iy] * scale;
+    const float2* xr = x + (int64_t)iy * n;
+    const float2* sm = smaps + (int64_t)iy * n * L + l0;
+    float2* dst = U + (int64_t)iy * G * L + l0;
+    __syncthreads();
+    block_fft_io<G, false, true, false>(
+        s, kLines, tw,
+        [&](int line, int q, bool) { return cscale(cmul(__ldg(sm + (int64_t)q * L + line), __ldg(xr + q)), ay * __ldg(apod + q)); },
+        NoIO{}, [&](int line, int k, float2 v) { dst[(int64_t)k * L + line] = mul_ipow(v, k); });
+}
+
+template <int G>
+__global__ void k_fwd_cols_h(const float2* __restrict__ U, int n, int L, const float2* __restrict__ twg,
+                             float2* __restrict__ Gh) {
+    extern __shared__ float2 s[];
+    const float2* tw = stage_twiddles<G>(s + G * kLines, twg);
+    const int gx = blockIdx.x, l0 = blockIdx.y * kLines;
+    const int64_t rs = (int64_t)G * L;
+    const float2* col = U + (int64_t)gx * L + l0;
+    float2* dst = Gh + (int64_t)gx * L + l0;
+    __syncthreads();
+    block_fft_io<G, false, true, false>(
+        s, kLines, tw, [&](int line, int q, bool) { return __ldg(col + q * rs + line); }, NoIO{},
+        [&](int line, int k, float2 v) { dst[k * rs + line] = mul_ipow(v, k); });
+}
+
+template <int G>
+__global__ void k_adj_cols_h(const float2* __restrict__ Hg, int n, int L, const float2* __restrict__ twg,
+                             float2* __restrict__ V) {
+    extern __shared__ float2 s[];
+    const float2* tw = stage_twiddles<G>(s + G * kLines, twg);
+    const int gx = blockIdx.x, l0 = blockIdx.y * kLines;
+    const int64_t rs = (int64_t)G * L;
+    const float2* col = Hg + (int64_t)gx * L + l0;
+    float2* dst = V + (int64_t)gx * L + l0;
+    __syncthreads();
+    block_fft_io<G, true, false, true>(
+        s, kLines, tw, [&](int line, int p, bool) { return mul_mipow(__ldg(col + p * rs + line), p); }, NoIO{},
+        [&](int line, int q, float2 v) { dst[q * rs + line] = v; });
+}
+
+template <int G>
+__global__ void k_adj_rows_h(const float2* __restrict__ V, const float2* __restrict__ smaps,
+                             const float* __restrict__ apod, int n, int L, int nchunk, float scale,
+                             const float2* __restrict__ twg, float2* x, float2* __restrict__ part, float zc,
+                             const float2* z) {
+    extern __shared__ float2 s[];
+    const float2* tw = stage_twiddles<G>(s + G * kLines, twg);
+    const int iy = blockIdx.x, l0 = blockIdx.y * kLines;
+    const float2* src = V + (int64_t)iy * G * L + l0;
+    __syncthreads();
+    block_fft_io<G, true, false, true>(
+        s, kLines, tw, [&](int line, int p, bool) { return mul_mipow(__ldg(src + (int64_t)p * L + line), p); },
+        NoIO{}, NoIO{});
+    const float ay = apod[iy] * scale;
+    for (int ix = threadIdx.x; ix < n; ix += blockDim.x) {
+        const float4* s4 = reinterpret_cast<const float4*>(smaps + ((int64_t)iy * n + ix) * L + l0);
+        float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int h = 0; h < kLines / 2; ++h) {
+            const float4 sv = __ldg(s4 + h);
+            const float2 g0 = s[ix * kLines + 2 * h], g1 = s[ix * kLines + 2 * h + 1];
+            a.x += sv.x * g0.x + sv.y * g0.y + sv.z * g1.x + sv.w * g1.y;
+            a.y += sv.x * g0.y - sv.y * g0.x + sv.z * g1.y - sv.w * g1.x;
+        }
+        if (nchunk == 1) {
+            const int64_t e = (int64_t)iy * n + ix;
+            float2 v = cscale(a, ay * apod[ix]);
+            if (z) {
+                const float2 zv = z[e];
+                v.x = fmaf(zc, zv.x, v.x);
+                v.y = fmaf(zc, zv.y, v.y);
+            }
+            x[e] = v;
+        } else {
+            part[((int64_t)blockIdx.y * n + iy) * n + ix] = a;
+        }
+    }
+}
+
 // Type-2 interpolation: 16 lanes per point (lane = coil, looping over coils
 // beyond 16), the 2W separable weights computed once per point by lanes
 // 0..2W-1 and broadcast with shuffles.
@@ -488,11 +593,22 @@ __global__ void k_adj_chunk_sum(const float2* __restrict__ part, const float* __
 }
 
 // ---------------------------------------------------------------- launchers
+// the lower-half passes apply when G = 2n and every coil chunk has 16 coils
+inline bool half_passes(const hqs_plan_s* p) { return p->G == 2 * p->n && p->LC == kLines && p->L % kLines == 0; }
+
 template <int G>
 static int fwd_fft_impl(hqs_plan_s* p, const float2* x, cudaStream_t st) {
     const float2* tw = plan_twiddles(p, G);
     const int th = fft_threads<G>(p->LC);
     const size_t sm = nufft_smem_floats2<G>() * sizeof(float2);
+    if (half_passes(p)) {
+        HQS_CUDA_TRY(cudaFuncSetAttribute(k_fwd_rows_h<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        HQS_CUDA_TRY(cudaFuncSetAttribute(k_fwd_cols_h<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_fwd_rows_h<G><<<dim3(p->n, p->nchunk), th, sm, st>>>(x, p->smaps, p->apod, p->n, p->L, p->scale, tw, p->work);
+        k_fwd_cols_h<G><<<dim3(G, p->nchunk), th, sm, st>>>(p->work, p->n, p->L, tw, p->grid);
+        HQS_CUDA_TRY(cudaGetLastError());
+        return HQS_OK;
+    }
     HQS_CUDA_TRY(cudaFuncSetAttribute(k_fwd_rows<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     HQS_CUDA_TRY(cudaFuncSetAttribute(k_fwd_cols<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     k_fwd_rows<G><<<dim3(p->n, p->nchunk), th, sm, st>>>(x, p->smaps, p->apod, p->n, p->L, p->LC,
@@ -507,6 +623,18 @@ static int adj_fft_impl(hqs_plan_s* p, float2* x, float zc, const float2* z, cud
     const float2* tw = plan_twiddles(p, G);
     const int th = fft_threads<G>(p->LC);
     const size_t sm = nufft_smem_floats2<G>() * sizeof(float2);
+    if (half_passes(p)) {
+        HQS_CUDA_TRY(cudaFuncSetAttribute(k_adj_cols_h<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        HQS_CUDA_TRY(cudaFuncSetAttribute(k_adj_rows_h<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_adj_cols_h<G><<<dim3(G, p->nchunk), th, sm, st>>>(p->grid, p->n, p->L, tw, p->work);
+        k_adj_rows_h<G><<<dim3(p->n, p->nchunk), th, sm, st>>>(p->work, p->smaps, p->apod, p->n, p->L, p->nchunk,
+                                                               p->scale, tw, x, p->chunk_buf, zc, z);
+        if (p->nchunk > 1)
+            k_adj_chunk_sum<<<std::min(ceil_div(p->n * p->n, 256), 1024), 256, 0, st>>>(
+                p->chunk_buf, p->apod, p->n, p->nchunk, p->scale, x, zc, z);
+        HQS_CUDA_TRY(cudaGetLastError());
+        return HQS_OK;
+    }
     HQS_CUDA_TRY(cudaFuncSetAttribute(k_adj_cols<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     HQS_CUDA_TRY(cudaFuncSetAttribute(k_adj_rows<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     k_adj_cols<G><<<dim3(G, p->nchunk), th, sm, st>>>(p->grid, p->n, p->L, p->LC, p->nchunk, tw, p->work);

@@ -29,10 +29,14 @@ def cases():
         "odd_w6": dict(synth.odd_case(1, n=32, L=5, M=301, W=6)),
         # 20 coils: two coil chunks in every FFT pass; odd kernel width
         "l20_w5": dict(synth.odd_case(2, n=32, L=20, M=400, W=5)),
+        # 16 and 32 coils with G = 2n: the NUFFT passes with the image in the lower half
+        # of each line (one and two 16-coil chunks)
+        "l16": dict(synth.odd_case(5, n=64, L=16, M=900, W=6)),
+        "l32_w4": dict(synth.odd_case(6, n=32, L=32, M=500, W=4)),
     }
 
 
-@pytest.fixture(scope="module", params=["tiny", "odd", "odd_w6", "l20_w5"])
+@pytest.fixture(scope="module", params=["tiny", "odd", "odd_w6", "l20_w5", "l16", "l32_w4"])
 def case(request):
     return quantised(cases()[request.param])
 
