@@ -108,15 +108,17 @@ __global__ void k_fwd_cols(const float2* __restrict__ U, int n, int L, int LC, i
 // forward stage then skips the zero half and reads straight from global memory, the
 // last inverse stage skips the discarded half, and stores go straight to global
 // memory (the I/O hooks of block_fft_io, which need every thread to own a line).
-HQS_DEV float2 mul_ipow(float2 v, int k) {   // v * i^k, k >= 0
-    switch (k & 3) {
-        case 0: return v;
-        case 1: return make_float2(-v.y, v.x);
-        case 2: return make_float2(-v.x, -v.y);
-        default: return make_float2(v.y, -v.x);
-    }
+// v * i^k and v * (-i)^k, k >= 0, with selects (k differs from lane to lane: no branches)
+HQS_DEV float2 mul_ipow(float2 v, int k) {
+    const bool odd = k & 1, neg = k & 2;
+    const float re = odd ? -v.y : v.x, im = odd ? v.x : v.y;
+    return neg ? make_float2(-re, -im) : make_float2(re, im);
 }
-HQS_DEV float2 mul_mipow(float2 v, int k) { return mul_ipow(v, 4 - (k & 3)); }   // v * (-i)^k
+HQS_DEV float2 mul_mipow(float2 v, int k) {
+    const bool odd = k & 1, neg = k & 2;
+    const float re = odd ? v.y : v.x, im = odd ? -v.x : v.y;
+    return neg ? make_float2(-re, -im) : make_float2(re, im);
+}
 
 template <int G>
 __global__ void k_fwd_rows_h(const float2* __restrict__ x, const float2* __restrict__ smaps,
@@ -255,6 +257,57 @@ __global__ void __launch_bounds__(256) k_interp(const float2* __restrict__ Gh, c
     }
 }
 
+// Type-2 interpolation for 16-coil chunks: 8 lanes per point, lane q owning coils
+// (2q, 2q+1) of a chunk, so one float4 load per lane reads a tap's 16 coils as one
+// 128-byte line; the 2W weights come from the plan's table; the result goes to the
+// sorted order, coil-innermost (one 128-byte store per point and chunk), and
+// k_y_from_sorted puts it in the caller's (coil, point) order.
+template <int W>
+__global__ void __launch_bounds__(256) k_interp16(const float2* __restrict__ Gh, const int4* __restrict__ pts,
+                                                  const float* __restrict__ kbw, int M, int G, int L,
+                                                  float2* __restrict__ ys) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t j = t >> 3;
+    const int q = threadIdx.x & 7;
+    if (j >= M) return;
+    const int4 pt = pts[j];
+    float wx[W], wy[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        wx[w] = __ldg(kbw + j * 2 * W + w);
+        wy[w] = __ldg(kbw + j * 2 * W + W + w);
+    }
+    int gxs[W];
+#pragma unroll
+    for (int b = 0; b < W; ++b) {
+        const int gx = pt.x + b;
+        gxs[b] = gx >= G ? gx - G : gx;
+    }
+    for (int l0 = 0; l0 < L; l0 += 16) {
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int a = 0; a < W; ++a) {
+            int gy = pt.y + a;
+            if (gy >= G) gy -= G;
+            const float4* row = reinterpret_cast<const float4*>(Gh + (int64_t)gy * G * L + l0) + q;
+            float4 ra = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int b = 0; b < W; ++b) {
+                const float4 g = __ldg(row + (int64_t)gxs[b] * (L / 2));
+                ra.x = fmaf(wx[b], g.x, ra.x);
+                ra.y = fmaf(wx[b], g.y, ra.y);
+                ra.z = fmaf(wx[b], g.z, ra.z);
+                ra.w = fmaf(wx[b], g.w, ra.w);
+            }
+            acc.x = fmaf(wy[a], ra.x, acc.x);
+            acc.y = fmaf(wy[a], ra.y, acc.y);
+            acc.z = fmaf(wy[a], ra.z, acc.z);
+            acc.w = fmaf(wy[a], ra.w, acc.w);
+        }
+        reinterpret_cast<float4*>(ys + j * L + l0)[q] = acc;
+    }
+}
+
 // ---------------------------------------------------------------- adjoint
 // k-space data to the sorted point order, coil-innermost: ys[invperm[m]][l] =
 // y[l][m].  A CTA stages kSortPts caller-order points of every coil (coalesced
@@ -273,6 +326,24 @@ __global__ void __launch_bounds__(256) k_y_to_sorted(const float2* __restrict__ 
     for (int e = threadIdx.x; e < np * L; e += blockDim.x) {
         const int q = e / L, l = e - q * L;
         ys[(int64_t)invperm[m0 + q] * L + l] = sy[q * (L + 1) + l];
+    }
+}
+
+// The reverse copy for the forward operator: y[l][m] = ys[invperm[m]][l], each
+// point's L-coil line read contiguously, each coil's kSortPts points written as one run.
+__global__ void __launch_bounds__(256) k_y_from_sorted(const float2* __restrict__ ys, const int* __restrict__ invperm,
+                                                       int M, int L, float2* __restrict__ y) {
+    extern __shared__ float2 sy[];   // [kSortPts][L + 1]
+    const int m0 = blockIdx.x * kSortPts;
+    const int np = min(kSortPts, M - m0);
+    for (int e = threadIdx.x; e < np * L; e += blockDim.x) {
+        const int q = e / L, l = e - q * L;
+        sy[q * (L + 1) + l] = ys[(int64_t)invperm[m0 + q] * L + l];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < L * kSortPts; e += blockDim.x) {
+        const int l = e / kSortPts, q = e - l * kSortPts;
+        if (q < np) y[(int64_t)l * M + m0 + q] = sy[q * (L + 1) + l];
     }
 }
 
@@ -650,6 +721,16 @@ static int adj_fft_impl(hqs_plan_s* p, float2* x, float zc, const float2* z, cud
 template <int W>
 static int interp_impl(hqs_plan_s* p, float2* y, cudaStream_t st) {
     if (p->M == 0) return HQS_OK;
+    if (p->L % 16 == 0) {
+        const int64_t threads8 = p->M * 8;
+        k_interp16<W><<<(unsigned)ceil_div64(threads8, 256), 256, 0, st>>>(p->grid, p->pts, p->spread.kbw, (int)p->M,
+                                                                         p->G, p->L, p->spread.ysort);
+        const size_t smy = (size_t)kSortPts * (p->L + 1) * sizeof(float2);
+        k_y_from_sorted<<<(unsigned)ceil_div64(p->M, kSortPts), 256, smy, st>>>(p->spread.ysort, p->invperm,
+                                                                             (int)p->M, p->L, y);
+        HQS_CUDA_TRY(cudaGetLastError());
+        return HQS_OK;
+    }
     const int64_t threads = p->M * 16;
     k_interp<W><<<(unsigned)ceil_div64(threads, 256), 256, 0, st>>>(p->grid, p->pts, p->perm, (int)p->M,
                                                                     p->G, p->L, (float)p->beta, y);
