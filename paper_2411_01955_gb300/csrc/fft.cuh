@@ -460,6 +460,120 @@ HQS_FFT_SIZE_V(256, 16, ST(16, 1) ST(16, 16))
 #undef ST
 #undef HQS_FFT_SIZE
 
+// ------------------------------------------------ forward x factor x inverse pair
+// A forward transform, a pointwise factor and the inverse transform of the same
+// line, with the inverse taking the forward's radices in reverse order.  Then the
+// forward's last Stockham stage (radix R after P = N / R) reads and writes the
+// positions i + r N/R, i < N/R, and the inverse's first stage (radix R, P = 1) reads
+// exactly those positions: the two stages and the factor run on the same registers,
+// with no shared-memory round trip and no barrier between them.
+template <int N, int E, int R, class XF>
+HQS_DEV void fft_mid_stage(float2* s, int t, bool act, const float2* __restrict__ tw, XF& xf) {
+    constexpr int st = kLines;
+    constexpr int TPL = N / E;
+    constexpr int NB = N / R;   // also P, the product of the forward's earlier radices
+    constexpr int BPT = E / R;
+    static_assert(E % R == 0 && NB == TPL * BPT, "butterfly split");
+    float2 v[E];
+#pragma unroll
+    for (int b = 0; b < BPT; ++b) {
+        const int i = t + b * TPL;
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[b * R + r] = s[(i + r * NB) * st];
+    }
+    __syncthreads();
+    if (act) {
+#pragma unroll
+        for (int b = 0; b < BPT; ++b) {
+            const int i = t + b * TPL;   // < NB = P, so i mod P = i
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[b * R + r] = cmul(v[b * R + r], tw[r * i]);
+            Dft<R, false>::run(&v[b * R]);
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[b * R + r] = xf(i + r * NB, v[b * R + r]);
+            Dft<R, true>::run(&v[b * R]);
+#pragma unroll
+            for (int r = 0; r < R; ++r) s[(i * R + r) * st] = v[b * R + r];
+        }
+    }
+    __syncthreads();
+}
+
+// Stage tables of the pair: forward head stages (the first with the zero upper
+// half and the loader), the middle radix, inverse tail stages in reverse order
+// (the last keeping the lower half only, through the store hook).
+template <int N> struct FftPair;
+
+#define HQS_FFT_PAIR(NN, EE, RM, HEAD, TAIL)                                                      \
+    template <> struct FftPair<NN> {                                                              \
+        static constexpr int E = EE;                                                              \
+        static constexpr int TPL = NN / EE;                                                       \
+        template <class LD, class XF, class STF>                                                  \
+        HQS_DEV static void run(float2* s, int t, bool act, const float2* tw, LD& ld, XF& xf,     \
+                                STF& stf) {                                                       \
+            NoIO nio;                                                                             \
+            HEAD                                                                                  \
+            fft_mid_stage<NN, EE, RM>(s, t, act, tw, xf);                                         \
+            TAIL                                                                                  \
+        }                                                                                         \
+    };
+#define FH(R, P) fft_stage_io<NN_, E_, R, P, false, P == 1, false, P == 1, false>(s, t, act, tw, ld, nio, nio);
+#define FT(R, P) fft_stage_io<NN_, E_, R, P, true, false, P * R == NN_, false, P * R == NN_>(s, t, act, tw, nio, nio, stf);
+
+#define NN_ 16
+#define E_ 4
+HQS_FFT_PAIR(16, 4, 4, FH(4, 1), FT(4, 4))
+#undef NN_
+#undef E_
+#define NN_ 32
+#define E_ 8
+HQS_FFT_PAIR(32, 8, 4, FH(8, 1), FT(8, 4))
+#undef NN_
+#undef E_
+#define NN_ 64
+#define E_ 8
+HQS_FFT_PAIR(64, 8, 8, FH(8, 1), FT(8, 8))
+#undef NN_
+#undef E_
+#define NN_ 128
+#define E_ 8
+HQS_FFT_PAIR(128, 8, 4, FH(8, 1) FH(4, 8), FT(4, 4) FT(8, 16))
+#undef NN_
+#undef E_
+#define NN_ 256
+#define E_ 8
+HQS_FFT_PAIR(256, 8, 4, FH(8, 1) FH(8, 8), FT(8, 4) FT(8, 32))
+#undef NN_
+#undef E_
+#define NN_ 320
+#define E_ 40
+HQS_FFT_PAIR(320, 40, 40, FH(8, 1), FT(8, 40))
+#undef NN_
+#undef E_
+#define NN_ 384
+#define E_ 24
+HQS_FFT_PAIR(384, 24, 6, FH(8, 1) FH(8, 8), FT(8, 6) FT(8, 48))
+#undef NN_
+#undef E_
+#define NN_ 512
+#define E_ 16
+HQS_FFT_PAIR(512, 16, 8, FH(8, 1) FH(8, 8), FT(8, 8) FT(8, 64))
+#undef NN_
+#undef E_
+#define NN_ 640
+#define E_ 40
+HQS_FFT_PAIR(640, 40, 10, FH(8, 1) FH(8, 8), FT(8, 10) FT(8, 80))
+#undef NN_
+#undef E_
+#define NN_ 768
+#define E_ 24
+HQS_FFT_PAIR(768, 24, 12, FH(8, 1) FH(8, 8), FT(8, 12) FT(8, 96))
+#undef NN_
+#undef E_
+#undef FH
+#undef FT
+#undef HQS_FFT_PAIR
+
 // Transform `nlines` (<= kLines) lines held at s[pos * kLines + line] with the
 // whole CTA: thread (line = tid % lpg, t = tid / lpg) owns E elements of one
 // line, lpg = blockDim.x / TPL >= nlines (launch with fft_threads).  The
@@ -514,6 +628,26 @@ HQS_DEV void block_fft_io_tab(float2* s, int nlines, const float2* tw, LD&& ld, 
         else return [&, line](int pos, float2 v) { stf(line, pos, v); };
     }();
     TAB<N>::template run_io<INV, ZIN, HOUT>(s + line, act ? t : 0, act, tw, bind_ld, bind_xf, bind_st);
+}
+
+// The forward x factor x inverse pair (FftPair) with the same hooks: ld feeds the
+// forward's first stage (upper half zero), xf(line, pos, v) is the factor, stf
+// takes the inverse's lower half.
+template <int N, class LD, class XF, class STF>
+HQS_DEV void block_fft_pair(float2* s, int nlines, const float2* tw, LD&& ld, XF&& xf, STF&& stf) {
+    constexpr int TPL = FftPair<N>::TPL;
+    static_assert(FftPair<N>::E == FftSize<N>::E, "same thread layout as the single transforms");
+    const int lpg = blockDim.x / TPL;
+    int tid;
+    asm volatile("mov.u32 %0, %%tid.x;" : "=r"(tid));
+    const int ll = tid % lpg;
+    const int t = tid / lpg;
+    const bool act = (ll < nlines) && (t < TPL);
+    const int line = act ? ll : 0;
+    auto bind_ld = [&, line, act](int pos) { return ld(line, pos, act); };
+    auto bind_xf = [&, line](int pos, float2 v) { return xf(line, pos, v); };
+    auto bind_st = [&, line](int pos, float2 v) { stf(line, pos, v); };
+    FftPair<N>::run(s + line, act ? t : 0, act, tw, bind_ld, bind_xf, bind_st);
 }
 
 template <int N, bool INV, bool ZIN, bool HOUT, class LD, class XF, class STF>

@@ -66,13 +66,13 @@ HQS_DEV void toep_cols_item(const ToepArgs& A, int kx, int ch, float2* s) {
     const int64_t rs = (int64_t)N2 * L;
     const float* kh = A.khat + (int64_t)kx * N2;   // Khat stored transposed: column kx contiguous
     __syncthreads();
-    // column straight into the first stage (zero-padded upper half), * Khat in
-    // the last forward stage, IFFT, first n rows straight back to T
-    block_fft_io<N2, false, true, false>(
+    // column straight into the first stage (zero-padded upper half), * Khat between
+    // the last forward and the first inverse stage (on registers), IFFT, first n rows
+    // straight back to T
+    block_fft_pair<N2>(
         s, lines, tw, [&](int line, int p, bool) { return __ldcg(col + line + p * rs); },
-        [&](int, int p, float2 v) { return cscale(v, __ldg(kh + p)); }, NoIO{});
-    block_fft_io<N2, true, false, true>(s, lines, tw, NoIO{}, NoIO{},
-                                        [&](int line, int p, float2 v) { col[line + p * rs] = v; });
+        [&](int, int p, float2 v) { return cscale(v, __ldg(kh + p)); },
+        [&](int line, int p, float2 v) { col[line + p * rs] = v; });
     __syncthreads();
 }
 
