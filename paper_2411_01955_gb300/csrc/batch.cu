@@ -25,7 +25,6 @@ using namespace hqs;
 #define HQS_BATCH_MAX 64
 #define HQS_BATCH_BD 256
 #define HQS_BATCH_MAXR 24
-#define HQS_BATCH_Q 8   // preconditioner lines per item: Q x TPL(n) <= block size for every n
 
 namespace {
 
@@ -116,10 +115,14 @@ HQS_DEV void z_and_p_rows(const BatchSlice& S, int r0, float beta, bool first, f
     __syncthreads();
 }
 
+// preconditioner lines per item: as many n-point lines as the CTA holds (<= 16)
+template <int N> constexpr int batch_pq() {
+    return (HQS_BATCH_BD / FftSize<N>::TPL) < kLines ? HQS_BATCH_BD / FftSize<N>::TPL : kLines;
+}
+
 template <int N>
 HQS_DEV double pc_rows(const BatchSlice& S, int r0, float alpha, bool update, float2* s, const float2* twN) {
-    static_assert(HQS_BATCH_Q * FftSize<N>::TPL <= HQS_BATCH_BD, "a preconditioner item needs more threads");
-    const int lines = min(HQS_BATCH_Q, N - r0);
+    const int lines = min(batch_pq<N>(), N - r0);
     double rr = 0.0;
     for (int e = threadIdx.x; e < lines * N; e += blockDim.x) {
         const int q_ = e / N, ix = e - q_ * N;
@@ -150,29 +153,21 @@ HQS_DEV double pc_rows(const BatchSlice& S, int r0, float alpha, bool update, fl
 
 template <int N>
 HQS_DEV double pc_cols(const BatchSlice& S, int c0, float a, float b, float2* s, const float2* twN) {
-    static_assert(HQS_BATCH_Q * FftSize<N>::TPL <= HQS_BATCH_BD, "a preconditioner item needs more threads");
-    const int lines = min(HQS_BATCH_Q, N - c0);
-    for (int e = threadIdx.x; e < N * lines; e += blockDim.x) {
-        const int pos = e / lines, q_ = e - pos * lines;
-        s[pos * kLines + q_] = __ldcg(S.pcb + (size_t)pos * N + c0 + q_);
-    }
-    __syncthreads();
-    block_fft<N, false>(s, lines, twN);
+    const int lines = min(batch_pq<N>(), N - c0);
+    // column FFT, * s^-1/2 (accumulating <r, z> = sum s^-1/2 |r_hat|^2), column IFFT as
+    // one forward x factor x inverse pair, loads and stores straight from / to pcb
     double acc = 0.0;
-    for (int e = threadIdx.x; e < N * lines; e += blockDim.x) {
-        const int pos = e / lines, q_ = e - pos * lines;
-        const float l = S.lam[(size_t)pos * N + c0 + q_];
-        const float m = rsqrtf(fmaxf(fmaf(a, fmaxf(l, 0.f), b), 0.25f * b));
-        const float2 v = s[pos * kLines + q_];
-        acc += (double)(m * (v.x * v.x + v.y * v.y));
-        s[pos * kLines + q_] = cscale(v, m);
-    }
-    __syncthreads();
-    block_fft<N, true>(s, lines, twN);
-    for (int e = threadIdx.x; e < N * lines; e += blockDim.x) {
-        const int pos = e / lines, q_ = e - pos * lines;
-        S.pcb[(size_t)pos * N + c0 + q_] = s[pos * kLines + q_];
-    }
+    float2* col = S.pcb + c0;
+    const float* lcol = S.lam + c0;
+    block_fft_pair<N, false, false>(
+        s, lines, twN, [&](int line, int pos, bool) { return __ldcg(col + (size_t)pos * N + line); },
+        [&](int line, int pos, float2 v) {
+            const float l = __ldg(lcol + (size_t)pos * N + line);
+            const float m = rsqrtf(fmaxf(fmaf(a, fmaxf(l, 0.f), b), 0.25f * b));
+            acc += (double)(m * (v.x * v.x + v.y * v.y));
+            return cscale(v, m);
+        },
+        [&](int line, int pos, float2 v) { col[(size_t)pos * N + line] = v; });
     __syncthreads();
     return acc;
 }
@@ -332,14 +327,14 @@ __global__ void __launch_bounds__(HQS_BATCH_BD, 2) k_hqs_batch(BatchArgs B) {
         // preconditioner of the initial residual
         FOR_ITEMS(BL_PC, {
             STAGE_TWN(S, si);
-            HQS_BATCH_DISPATCH(S.A.n, (pc_rows<N>(S, it_ * HQS_BATCH_Q, 0.f, false, s, twN)));
+            HQS_BATCH_DISPATCH(S.A.n, (pc_rows<N>(S, it_ * batch_pq<N>(), 0.f, false, s, twN)));
         });
         BB_BARRIER();
         CLEAR_ACC();
         FOR_ITEMS(BL_PC, {
             STAGE_TWN(S, si);
             double v = 0.0;
-            HQS_BATCH_DISPATCH(S.A.n, (v = pc_cols<N>(S, it_ * HQS_BATCH_Q, 1.f, bcoef, s, twN)));
+            HQS_BATCH_DISPATCH(S.A.n, (v = pc_cols<N>(S, it_ * batch_pq<N>(), 1.f, bcoef, s, twN)));
             v = cta_sum(v, red);
             if (threadIdx.x == 0) acc[0][si] += v;
         });
@@ -405,7 +400,7 @@ __global__ void __launch_bounds__(HQS_BATCH_BD, 2) k_hqs_batch(BatchArgs B) {
             FOR_ITEMS(BL_PC, {
                 STAGE_TWN(S, si);
                 double v = 0.0;
-                HQS_BATCH_DISPATCH(S.A.n, (v = pc_rows<N>(S, it_ * HQS_BATCH_Q, (float)alphas[si], true, s, twN)));
+                HQS_BATCH_DISPATCH(S.A.n, (v = pc_rows<N>(S, it_ * batch_pq<N>(), (float)alphas[si], true, s, twN)));
                 v = cta_sum(v, red);
                 if (threadIdx.x == 0) acc[1][si] += v;
             });
@@ -418,7 +413,7 @@ __global__ void __launch_bounds__(HQS_BATCH_BD, 2) k_hqs_batch(BatchArgs B) {
             FOR_ITEMS(BL_PC, {
                 STAGE_TWN(S, si);
                 double v = 0.0;
-                HQS_BATCH_DISPATCH(S.A.n, (v = pc_cols<N>(S, it_ * HQS_BATCH_Q, 1.f, bcoef, s, twN)));
+                HQS_BATCH_DISPATCH(S.A.n, (v = pc_cols<N>(S, it_ * batch_pq<N>(), 1.f, bcoef, s, twN)));
                 v = cta_sum(v, red);
                 if (threadIdx.x == 0) acc[0][si] += v;
             });
@@ -586,14 +581,14 @@ __global__ void __launch_bounds__(HQS_BATCH_BD, 2) k_pcg_batch(DcBatchArgs B) {
     // preconditioner of the initial residual, <r, z>
     FOR_ITEMS(BL_PC, {
         STAGE_TWN(S, si);
-        HQS_BATCH_DISPATCH(S.A.n, (pc_rows<N>(S, it_ * HQS_BATCH_Q, 0.f, false, s, twN)));
+        HQS_BATCH_DISPATCH(S.A.n, (pc_rows<N>(S, it_ * batch_pq<N>(), 0.f, false, s, twN)));
     });
     BB_BARRIER();
     CLEAR_ACC();
     FOR_ITEMS(BL_PC, {
         STAGE_TWN(S, si);
         double v = 0.0;
-        HQS_BATCH_DISPATCH(S.A.n, (v = pc_cols<N>(S, it_ * HQS_BATCH_Q, a, bcoef, s, twN)));
+        HQS_BATCH_DISPATCH(S.A.n, (v = pc_cols<N>(S, it_ * batch_pq<N>(), a, bcoef, s, twN)));
         v = cta_sum(v, red);
         if (threadIdx.x == 0) acc[0][si] += v;
     });
@@ -668,7 +663,7 @@ __global__ void __launch_bounds__(HQS_BATCH_BD, 2) k_pcg_batch(DcBatchArgs B) {
         FOR_ITEMS(BL_PC, {
             STAGE_TWN(S, si);
             double v = 0.0;
-            HQS_BATCH_DISPATCH(S.A.n, (v = pc_rows<N>(S, it_ * HQS_BATCH_Q, (float)alphas[si], true, s, twN)));
+            HQS_BATCH_DISPATCH(S.A.n, (v = pc_rows<N>(S, it_ * batch_pq<N>(), (float)alphas[si], true, s, twN)));
             v = cta_sum(v, red);
             if (threadIdx.x == 0) acc[1][si] += v;
         });
@@ -699,7 +694,7 @@ __global__ void __launch_bounds__(HQS_BATCH_BD, 2) k_pcg_batch(DcBatchArgs B) {
         FOR_ITEMS(BL_PC, {
             STAGE_TWN(S, si);
             double v = 0.0;
-            HQS_BATCH_DISPATCH(S.A.n, (v = pc_cols<N>(S, it_ * HQS_BATCH_Q, a, bcoef, s, twN)));
+            HQS_BATCH_DISPATCH(S.A.n, (v = pc_cols<N>(S, it_ * batch_pq<N>(), a, bcoef, s, twN)));
             v = cta_sum(v, red);
             if (threadIdx.x == 0) acc[0][si] += v;
         });
@@ -801,6 +796,18 @@ static void batch_free(hqs_batch_s* b) {
 
 extern "C" void hqs_batch_destroy(hqs_batch b) { batch_free(b); }
 
+
+// preconditioner lines per item for a slice of size n (host side of batch_pq)
+static int batch_pq_host(int n) {
+    switch (n) {
+        case 64: return batch_pq<64>();
+        case 128: return batch_pq<128>();
+        case 256: return batch_pq<256>();
+        case 320: return batch_pq<320>();
+        default: return batch_pq<384>();
+    }
+}
+
 extern "C" int hqs_batch_create(hqs_batch* out, hqs_plan* plans, int n, int max_outer) {
     if (!out || !plans || n <= 0 || n > HQS_BATCH_MAX || max_outer <= 0 || max_outer > 4096)
         return HQS_ERR_INVALID_ARG;
@@ -852,7 +859,7 @@ extern "C" int hqs_batch_create(hqs_batch* out, hqs_plan* plans, int n, int max_
         S.q = p->cg_q;
         S.pcb = p->pc_buf;
         const int zq = dispatch_fft_size(p->n, [&]<int NN>() { return batch_zq<NN>(); });
-        const int cnt[BL_N] = {p->n * nch, 2 * p->n * nch, ceil_div(p->n, HQS_BATCH_Q), p->n,
+        const int cnt[BL_N] = {p->n * nch, 2 * p->n * nch, ceil_div(p->n, batch_pq_host(p->n)), p->n,
                                ceil_div(p->n, 32) * ceil_div(p->n, 32), nch > 1 ? p->n : 0, ceil_div(p->n, zq)};
         for (int l = 0; l < BL_N; ++l) off[(size_t)l * (n + 1) + i + 1] = off[(size_t)l * (n + 1) + i] + cnt[l];
     }

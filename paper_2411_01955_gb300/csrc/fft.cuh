@@ -499,16 +499,16 @@ HQS_DEV void fft_mid_stage(float2* s, int t, bool act, const float2* __restrict_
     __syncthreads();
 }
 
-// Stage tables of the pair: forward head stages (the first with the zero upper
-// half and the loader), the middle radix, inverse tail stages in reverse order
-// (the last keeping the lower half only, through the store hook).
+// Stage tables of the pair: forward head stages (the first with the loader and,
+// with ZIN, the zero upper half), the middle radix, inverse tail stages in reverse
+// order (the last through the store hook, keeping the lower half only with HOUT).
 template <int N> struct FftPair;
 
 #define HQS_FFT_PAIR(NN, EE, RM, HEAD, TAIL)                                                      \
     template <> struct FftPair<NN> {                                                              \
         static constexpr int E = EE;                                                              \
         static constexpr int TPL = NN / EE;                                                       \
-        template <class LD, class XF, class STF>                                                  \
+        template <bool ZIN_, bool HOUT_, class LD, class XF, class STF>                           \
         HQS_DEV static void run(float2* s, int t, bool act, const float2* tw, LD& ld, XF& xf,     \
                                 STF& stf) {                                                       \
             NoIO nio;                                                                             \
@@ -517,8 +517,8 @@ template <int N> struct FftPair;
             TAIL                                                                                  \
         }                                                                                         \
     };
-#define FH(R, P) fft_stage_io<NN_, E_, R, P, false, P == 1, false, P == 1, false>(s, t, act, tw, ld, nio, nio);
-#define FT(R, P) fft_stage_io<NN_, E_, R, P, true, false, P * R == NN_, false, P * R == NN_>(s, t, act, tw, nio, nio, stf);
+#define FH(R, P) fft_stage_io<NN_, E_, R, P, false, ZIN_ && P == 1, false, P == 1, false>(s, t, act, tw, ld, nio, nio);
+#define FT(R, P) fft_stage_io<NN_, E_, R, P, true, false, HOUT_ && P * R == NN_, false, P * R == NN_>(s, t, act, tw, nio, nio, stf);
 
 #define NN_ 16
 #define E_ 4
@@ -631,9 +631,9 @@ HQS_DEV void block_fft_io_tab(float2* s, int nlines, const float2* tw, LD&& ld, 
 }
 
 // The forward x factor x inverse pair (FftPair) with the same hooks: ld feeds the
-// forward's first stage (upper half zero), xf(line, pos, v) is the factor, stf
-// takes the inverse's lower half.
-template <int N, class LD, class XF, class STF>
+// forward's first stage (upper half zero with ZIN), xf(line, pos, v) is the
+// factor, stf takes the inverse's output (its lower half only with HOUT).
+template <int N, bool ZIN, bool HOUT, class LD, class XF, class STF>
 HQS_DEV void block_fft_pair(float2* s, int nlines, const float2* tw, LD&& ld, XF&& xf, STF&& stf) {
     constexpr int TPL = FftPair<N>::TPL;
     static_assert(FftPair<N>::E == FftSize<N>::E, "same thread layout as the single transforms");
@@ -647,7 +647,7 @@ HQS_DEV void block_fft_pair(float2* s, int nlines, const float2* tw, LD&& ld, XF
     auto bind_ld = [&, line, act](int pos) { return ld(line, pos, act); };
     auto bind_xf = [&, line](int pos, float2 v) { return xf(line, pos, v); };
     auto bind_st = [&, line](int pos, float2 v) { stf(line, pos, v); };
-    FftPair<N>::run(s + line, act ? t : 0, act, tw, bind_ld, bind_xf, bind_st);
+    FftPair<N>::template run<ZIN, HOUT>(s + line, act ? t : 0, act, tw, bind_ld, bind_xf, bind_st);
 }
 
 template <int N, bool INV, bool ZIN, bool HOUT, class LD, class XF, class STF>

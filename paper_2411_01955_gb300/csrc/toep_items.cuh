@@ -69,7 +69,7 @@ HQS_DEV void toep_cols_item(const ToepArgs& A, int kx, int ch, float2* s) {
     // column straight into the first stage (zero-padded upper half), * Khat between
     // the last forward and the first inverse stage (on registers), IFFT, first n rows
     // straight back to T
-    block_fft_pair<N2>(
+    block_fft_pair<N2, true, true>(
         s, lines, tw, [&](int line, int p, bool) { return __ldcg(col + line + p * rs); },
         [&](int, int p, float2 v) { return cscale(v, __ldg(kh + p)); },
         [&](int line, int p, float2 v) { col[line + p * rs] = v; });
