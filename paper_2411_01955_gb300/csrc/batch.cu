@@ -491,9 +491,21 @@ __global__ void __launch_bounds__(HQS_BATCH_BD, 2) k_pcg_batch(DcBatchArgs B) {
     __shared__ double rzs[HQS_BATCH_MAX], alphas[HQS_BATCH_MAX], betas[HQS_BATCH_MAX];
     __shared__ double bbs[HQS_BATCH_MAX], rrs[HQS_BATCH_MAX];
     __shared__ int active[HQS_BATCH_MAX], its[HQS_BATCH_MAX], stat[HQS_BATCH_MAX];
-    __shared__ int nact;
+    __shared__ int nact, tw_cur;
     const int ns = B.ns, G = gridDim.x, bid = blockIdx.x;
     const float a = B.a, bcoef = B.b;
+    // the 2n-point twiddles of the Toeplitz items stay in a fixed shared region after
+    // the largest transform buffer and its image row, restaged only when the size changes
+    float2* twT = s + (size_t)768 * kLines + 384;
+    if (threadIdx.x == 0) tw_cur = 0;
+#define STAGE_TW2(AA)                                                                    \
+    if (tw_cur != 2 * (AA).n) {                                                          \
+        __syncthreads();                                                                 \
+        for (int i_ = threadIdx.x; i_ < 2 * (AA).n; i_ += blockDim.x) twT[i_] = (AA).tw[i_]; \
+        __syncthreads();                                                                 \
+        if (threadIdx.x == 0) tw_cur = 2 * (AA).n;                                       \
+        __syncthreads();                                                                 \
+    }
     const float2* twN = nullptr;
     // optional phase trace, kept by thread 0 of CTA 0 (count in shared memory: no registers)
     __shared__ int ntr;
@@ -616,19 +628,23 @@ __global__ void __launch_bounds__(HQS_BATCH_BD, 2) k_pcg_batch(DcBatchArgs B) {
         // q = a A^H A p + b p, <p, q>
         FOR_ITEMS(BL_ROWS, {
             const int n = S.A.n, ch = it_ / n, iy = it_ - ch * n;
-            HQS_BATCH_DISPATCH(n, (toep_rows_fwd_item<N2, HQS_BATCH_BD>(S.A, iy, ch, S.p, nullptr, 0.f, false, s)));
+            STAGE_TW2(S.A);
+            HQS_BATCH_DISPATCH(n, (toep_rows_fwd_item<N2, HQS_BATCH_BD>(S.A, iy, ch, S.p, nullptr, 0.f, false, s,
+                                                                        nullptr, twT)));
         });
         BB_BARRIER();
         FOR_ITEMS(BL_COLS, {
             const int n = S.A.n, N2v = 2 * n, ch = it_ / N2v, kx = it_ - ch * N2v;
-            HQS_BATCH_DISPATCH(n, (toep_cols_item<N2, HQS_BATCH_BD>(S.A, kx, ch, s)));
+            STAGE_TW2(S.A);
+            HQS_BATCH_DISPATCH(n, (toep_cols_item<N2, HQS_BATCH_BD>(S.A, kx, ch, s, twT)));
         });
         BB_BARRIER();
         CLEAR_ACC();
         FOR_ITEMS(BL_ROWS, {
             const int n = S.A.n, ch = it_ / n, iy = it_ - ch * n;
             double v = 0.0;
-            HQS_BATCH_DISPATCH(n, (v = toep_rows_adj_item<N2, HQS_BATCH_BD>(S.A, iy, ch, S.q, S.p, a, bcoef, 1, s)));
+            STAGE_TW2(S.A);
+            HQS_BATCH_DISPATCH(n, (v = toep_rows_adj_item<N2, HQS_BATCH_BD>(S.A, iy, ch, S.q, S.p, a, bcoef, 1, s, twT)));
             v = cta_sum(v, red);
             if (threadIdx.x == 0) acc[0][si] += v;
         });
@@ -729,6 +745,7 @@ __global__ void __launch_bounds__(HQS_BATCH_BD, 2) k_pcg_batch(DcBatchArgs B) {
 #undef FOR_ITEMS
 #undef STAGE_TWN
 #undef CLEAR_ACC
+#undef STAGE_TW2
 #undef COUNT_ACTIVE
 }
 

@@ -19,16 +19,18 @@ template <int N2> constexpr size_t toep_smem_floats2(int n) { return (size_t)N2 
 // P1: v = src (or p = src + beta p when fused, single chunk only), S_l v,
 // zero-pad to N2, FFT along x.
 // src_row, when given, is the row already in shared memory (the persistent
-// solver rebuilds z there); otherwise the row is read from src.  Vectors
+// solver rebuilds z there); otherwise the row is read from src.  tws, when given,
+// holds the 2n-point twiddles already staged in shared memory (else this item
+// stages them after the image row).  Vectors
 // written by other CTAs earlier in the same launch are read with ld.global.cg
 // (L2), never from a possibly stale L1 line.
 template <int N2, int BD = FftSize<N2>::TPL * kLines>
 HQS_DEV void toep_rows_fwd_item(const ToepArgs& A, int iy, int ch, const float2* __restrict__ src,
                                 float2* __restrict__ pvec, float beta, bool fuse, float2* s,
-                                const float2* src_row = nullptr) {
+                                const float2* src_row = nullptr, const float2* tws = nullptr) {
     const int n = A.n, L = A.L;
     float2* rowv = s + N2 * kLines;
-    const float2* tw = stage_twiddles<N2>(rowv + n, A.tw);
+    const float2* tw = tws ? tws : stage_twiddles<N2>(rowv + n, A.tw);
     for (int ix = threadIdx.x; ix < n; ix += blockDim.x) {
         const int64_t e = (int64_t)iy * n + ix;
         float2 v = src_row ? src_row[ix] : __ldcg(src + e);
@@ -57,9 +59,9 @@ HQS_DEV void toep_rows_fwd_item(const ToepArgs& A, int iy, int ch, const float2*
 
 // P2: column kx: zero-pad, FFT along y, * Khat, IFFT, keep the first n rows.
 template <int N2, int BD = FftSize<N2>::TPL * kLines>
-HQS_DEV void toep_cols_item(const ToepArgs& A, int kx, int ch, float2* s) {
+HQS_DEV void toep_cols_item(const ToepArgs& A, int kx, int ch, float2* s, const float2* tws = nullptr) {
     const int n = A.n, L = A.L;
-    const float2* tw = stage_twiddles<N2>(s + N2 * kLines + n, A.tw);
+    const float2* tw = tws ? tws : stage_twiddles<N2>(s + N2 * kLines + n, A.tw);
     const int l0 = ch * A.LC;
     const int lines = min(A.LC, L - l0);
     float2* col = A.T + (int64_t)kx * L + l0;
@@ -94,9 +96,9 @@ HQS_DEV float2 toep_epilogue(float2 v, int64_t e, const float2* __restrict__ pve
 template <int N2, int BD = FftSize<N2>::TPL * kLines>
 HQS_DEV double toep_rows_adj_item(const ToepArgs& A, int iy, int ch, float2* __restrict__ out,
                                   const float2* __restrict__ pvec, float a, float b, int mode,
-                                  float2* s) {
+                                  float2* s, const float2* tws = nullptr) {
     const int n = A.n, L = A.L;
-    const float2* tw = stage_twiddles<N2>(s + N2 * kLines + n, A.tw);
+    const float2* tw = tws ? tws : stage_twiddles<N2>(s + N2 * kLines + n, A.tw);
     const int l0 = ch * A.LC;
     const int lines = min(A.LC, L - l0);
     const float2* src = A.T + (int64_t)iy * N2 * L + l0;
