@@ -577,11 +577,13 @@ void spread_free(hqs_plan_s* p) {
     cudaFree(p->spread.bin_off);
     cudaFree(p->spread.items);
     cudaFree(p->spread.tile_info);
+    cudaFree(p->spread.tile_nb);
     cudaFree(p->spread.tickets);
     cudaFree(p->spread.partial);
     p->spread.bin_off = nullptr;
     p->spread.items = nullptr;
     p->spread.tile_info = nullptr;
+    p->spread.tile_nb = nullptr;
     p->spread.tickets = nullptr;
     p->spread.partial = nullptr;
     p->bytes -= p->spread.bytes;
@@ -609,14 +611,19 @@ int spread_build(hqs_plan_s* p, const std::vector<int>& hc, cudaStream_t s) {
         return c;
     };
     std::vector<int4> items;
-    std::vector<int2> info(nbins);
+    std::vector<int2> info(nbins), nbt((size_t)nbins * 10, make_int2(0, 0));
     int slots = 0;
     for (int t = 0; t < nbins; ++t) {
         int xs[3], ys[3];
         const int cx = distinct(t % nbx, xs), cy = distinct(t / nbx, ys);
-        int cand = 0;
+        int cand = 0, k = 0;
         for (int a = 0; a < cy; ++a)
-            for (int b = 0; b < cx; ++b) cand += hc[ys[a] * nbx + xs[b]];
+            for (int b = 0; b < cx; ++b, ++k) {
+                const int bin = ys[a] * nbx + xs[b];
+                nbt[(size_t)t * 10 + k] = make_int2(off[bin], cand);
+                cand += hc[bin];
+            }
+        nbt[(size_t)t * 10 + 9] = make_int2(k, cand);
         const int nch = std::max(1, ceil_div(cand, HQS_SPREAD_CAND));
         const int first = nch > 1 ? slots : -1;
         if (nch > 1) slots += nch;
@@ -638,11 +645,13 @@ int spread_build(hqs_plan_s* p, const std::vector<int>& hc, cudaStream_t s) {
     int rc = HQS_OK;
     if (cudaMalloc(&nw.bin_off, (nbins + 1) * sizeof(int)) || cudaMalloc(&nw.items, items.size() * sizeof(int4)) ||
         cudaMalloc(&nw.tile_info, nbins * sizeof(int2)) || cudaMalloc(&nw.tickets, nbins * sizeof(unsigned)) ||
+        cudaMalloc(&nw.tile_nb, (size_t)nbins * 10 * sizeof(int2)) ||
         (slots > 0 && cudaMalloc(&nw.partial, slots * slot_elems * sizeof(float2)))) {
         rc = HQS_ERR_OOM;
     } else if (cudaMemcpyAsync(nw.bin_off, off.data(), (nbins + 1) * sizeof(int), cudaMemcpyHostToDevice, s) ||
                cudaMemcpyAsync(nw.items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice, s) ||
                cudaMemcpyAsync(nw.tile_info, info.data(), nbins * sizeof(int2), cudaMemcpyHostToDevice, s) ||
+               cudaMemcpyAsync(nw.tile_nb, nbt.data(), (size_t)nbins * 10 * sizeof(int2), cudaMemcpyHostToDevice, s) ||
                cudaMemsetAsync(nw.tickets, 0, nbins * sizeof(unsigned), s) || cudaStreamSynchronize(s)) {
         rc = HQS_ERR_CUDA;
     }
@@ -650,12 +659,13 @@ int spread_build(hqs_plan_s* p, const std::vector<int>& hc, cudaStream_t s) {
         cudaFree(nw.bin_off);
         cudaFree(nw.items);
         cudaFree(nw.tile_info);
+        cudaFree(nw.tile_nb);
         cudaFree(nw.tickets);
         cudaFree(nw.partial);
         return rc;
     }
     spread_free(p);
-    nw.bytes = (nbins + 1) * sizeof(int) + items.size() * sizeof(int4) + nbins * (sizeof(int2) + sizeof(unsigned)) +
+    nw.bytes = (nbins + 1) * sizeof(int) + items.size() * sizeof(int4) + nbins * (11 * sizeof(int2) + sizeof(unsigned)) +
                slots * slot_elems * sizeof(float2);
     p->spread = nw;
     p->bytes += nw.bytes;

@@ -65,6 +65,8 @@ struct hqs_plan_s {
         int* bin_off = nullptr;        // [nbins + 1] sorted-point offsets per bin
         int4* items = nullptr;         // (tile, first candidate, end candidate, partial slot or -1)
         int2* tile_info = nullptr;     // [nbins] (chunks, first partial slot)
+        int2* tile_nb = nullptr;       // [nbins][10]: (first point, candidate prefix) of each distinct
+                                       // neighbouring bin in candidate order, entry 9 = (bins, candidates)
         unsigned* tickets = nullptr;   // [nbins] arrival counts of multi-chunk tiles (reset by the last)
         float2* partial = nullptr;     // [slots][tile * tile * L] partial tiles of multi-chunk tiles
         float2* ysort = nullptr;       // [M][L] k-space data in sorted order, coil-innermost
