@@ -362,13 +362,11 @@ __global__ void __launch_bounds__(256) k_y_from_sorted(const float2* __restrict_
 // items to arrive sums the slots in slot order into the grid.  No atomics on
 // data and no memset of the grid.
 constexpr int kSpreadWarps = 8;
-// FULL16: every coil chunk has exactly 16 coils (L a multiple of 16).  Then each
-// thread loads its own candidate's weights and first 16 coil values right away
-// into the candidate's slot (one round of global loads per item), the compaction
-// keeps only a list of slots, lane (h, l) = (lane / 16, lane % 16) owns coil l of
-// the cells x = h + 2 k of a row, and each staged point's x weights over the tile
-// row are tabulated once (wrow[i][h][k], zero outside the footprint), so a cell
-// update is one multiply-add pair on registers.
+// FULL16: every coil chunk has exactly 16 coils (L a multiple of 16).  Then lane
+// (h, l) = (lane / 16, lane % 16) owns coil l of the cells x = h + 2 k of a row,
+// and each staged point's x weights over the tile row are tabulated once
+// (wrow[i][h][k], zero outside the footprint), so a cell update is one
+// multiply-add pair on registers.
 template <int W, int TT, bool FULL16>
 __global__ void __launch_bounds__(256) k_spread_tiles(const float2* __restrict__ ys, const int4* __restrict__ pts,
                                                       const float* __restrict__ kbw, const int2* __restrict__ tile_nb,
@@ -384,22 +382,22 @@ __global__ void __launch_bounds__(256) k_spread_tiles(const float2* __restrict__
     int* sidx = reinterpret_cast<int*>(soff + CAND);               // [CAND]: sorted point index
     float* wrow = reinterpret_cast<float*>(sidx + CAND);           // FULL16: [CAND][2][TT / 2]
     __shared__ int2 nbs[10];
-    __shared__ int cidx[CAND];
     __shared__ int npts, wcount[kSpreadWarps], last;
     const int4 it = items[blockIdx.x];
     const int t = it.x, tx = t % nbx, ty = t / nbx;
     const int x0 = tx * TT, y0 = ty * TT;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // the tile's distinct neighbouring bins: (first point, candidate prefix), entry 9 = (bins, total)
+    // the tile's distinct neighbouring bins from the plan: (first point, candidate
+    // prefix) in candidate order, entry 9 = (bins, candidates)
     if (threadIdx.x < 10) nbs[threadIdx.x] = tile_nb[(int64_t)t * 10 + threadIdx.x];
     __syncthreads();
     // stage the candidates that touch the tile, in candidate order (CAND == blockDim)
     {
-        const int nnb = nbs[9].x;
         const int c = it.y + threadIdx.x;
         bool ov = false;
         int j = 0, ox = 0, oy = 0;
         if (c < it.z) {
+            const int nnb = nbs[9].x;
             int k = 0;
             while (k + 1 < nnb && nbs[k + 1].y <= c) ++k;
             j = nbs[k].x + (c - nbs[k].y);
@@ -414,19 +412,6 @@ __global__ void __launch_bounds__(256) k_spread_tiles(const float2* __restrict__
             if (oy >= TT) oy -= G;
             ov = ox > -W && oy > -W;
         }
-        if constexpr (FULL16) {
-            if (ov) {   // the slot of this candidate: its weights and first 16 coil values
-                const int slot = threadIdx.x;
-                soff[slot] = make_int2(ox, oy);
-                sidx[slot] = j;
-#pragma unroll
-                for (int h = 0; h < 2 * W; ++h) swt[slot * 2 * W + h] = __ldg(kbw + (int64_t)j * 2 * W + h);
-                const float4* src = reinterpret_cast<const float4*>(ys + (int64_t)j * L);
-                float4* dstv = reinterpret_cast<float4*>(sval + slot * 16);
-#pragma unroll
-                for (int h = 0; h < 8; ++h) dstv[h] = __ldg(src + h);
-            }
-        }
         const unsigned bal = __ballot_sync(0xffffffffu, ov);
         if (lane == 0) wcount[warp] = __popc(bal);
         __syncthreads();
@@ -439,32 +424,29 @@ __global__ void __launch_bounds__(256) k_spread_tiles(const float2* __restrict__
         }
         if (ov) {
             const int pos = base + __popc(bal & ((1u << lane) - 1u));
-            if constexpr (FULL16) {
-                cidx[pos] = threadIdx.x;
-            } else {
-                soff[pos] = make_int2(ox, oy);
-                sidx[pos] = j;
-            }
+            soff[pos] = make_int2(ox, oy);
+            sidx[pos] = j;
         }
         __syncthreads();
     }
     const int np = npts;
+    for (int e = threadIdx.x; e < np * 2 * W; e += blockDim.x) {
+        const int i = e / (2 * W), h = e - i * (2 * W);
+        swt[e] = __ldg(kbw + (int64_t)sidx[i] * 2 * W + h);
+    }
     if constexpr (FULL16) {
+        __syncthreads();
         for (int e = threadIdx.x; e < np * TT; e += blockDim.x) {
             const int i = e / TT, x = e - i * TT;
-            const int c = cidx[i];
-            int b = x - soff[c].x;
+            int b = x - soff[i].x;
             b += b < 0 ? G : 0;
-            wrow[i * TT + (x & 1) * (TT / 2) + (x >> 1)] = (unsigned)b < (unsigned)W ? swt[c * 2 * W + b] : 0.f;
+            wrow[i * TT + (x & 1) * (TT / 2) + (x >> 1)] = (unsigned)b < (unsigned)W ? swt[i * 2 * W + b] : 0.f;
         }
         const int h = lane >> 4, l = lane & 15;
         for (int l0 = 0; l0 < L; l0 += 16) {
-            if (l0 > 0) {   // later 16-coil chunks: reload the staged points' values
-                __syncthreads();
-                for (int e = threadIdx.x; e < np * 16; e += blockDim.x) {
-                    const int c = cidx[e >> 4], ll = e & 15;
-                    sval[c * 16 + ll] = __ldg(ys + (int64_t)sidx[c] * L + l0 + ll);
-                }
+            for (int e = threadIdx.x; e < np * 16; e += blockDim.x) {
+                const int i = e >> 4, ll = e & 15;
+                sval[i * 16 + ll] = __ldg(ys + (int64_t)sidx[i] * L + l0 + ll);
             }
             __syncthreads();
             float2* dst = it.w < 0 ? grid : partial + (int64_t)it.w * TT * TT * L;
@@ -473,14 +455,11 @@ __global__ void __launch_bounds__(256) k_spread_tiles(const float2* __restrict__
 #pragma unroll
                 for (int k = 0; k < TT / 2; ++k) acc[k] = make_float2(0.f, 0.f);
                 for (int i = 0; i < np; ++i) {
-                    const int c = cidx[i];
-                    // the point's row tap for this row (the wrap matters only when the tile is
-                    // the whole grid: there a footprint can leave its right edge and re-enter)
-                    int a = r - soff[c].y;
+                    int a = r - soff[i].y;
                     a += a < 0 ? G : 0;
                     if ((unsigned)a >= (unsigned)W) continue;
-                    const float wy = swt[c * 2 * W + W + a];
-                    float2 v = sval[c * 16 + l];
+                    const float wy = swt[i * 2 * W + W + a];
+                    float2 v = sval[i * 16 + l];
                     v.x *= wy;
                     v.y *= wy;
                     const float4* wr = reinterpret_cast<const float4*>(wrow + i * TT + h * (TT / 2));
@@ -499,58 +478,55 @@ __global__ void __launch_bounds__(256) k_spread_tiles(const float2* __restrict__
 #pragma unroll
                 for (int k = 0; k < TT / 2; ++k) dst[rowo + (int64_t)(h + 2 * k) * L + l0 + l] = acc[k];
             }
+            __syncthreads();
+        }
+    }
+    for (int l0 = 0; !FULL16 && l0 < L; l0 += LCS) {
+        const int lc = min(LCS, L - l0);
+        for (int e = threadIdx.x; e < np * lc; e += blockDim.x) {
+            const int i = e / lc, l = e - i * lc;
+            sval[i * LCS + l] = __ldg(ys + (int64_t)sidx[i] * L + l0 + l);
         }
         __syncthreads();
-    } else {
-        for (int e = threadIdx.x; e < np * 2 * W; e += blockDim.x) {
-            const int i = e / (2 * W), hh = e - i * (2 * W);
-            swt[e] = __ldg(kbw + (int64_t)sidx[i] * 2 * W + hh);
+        const int npair = TT * lc;
+        int px[NK], pl[NK];
+#pragma unroll
+        for (int k = 0; k < NK; ++k) {
+            const int pp = lane + 32 * k;
+            px[k] = pp / lc;
+            pl[k] = pp - px[k] * lc;
         }
-        for (int l0 = 0; l0 < L; l0 += LCS) {
-            const int lc = min(LCS, L - l0);
-            for (int e = threadIdx.x; e < np * lc; e += blockDim.x) {
-                const int i = e / lc, ll = e - i * lc;
-                sval[i * LCS + ll] = __ldg(ys + (int64_t)sidx[i] * L + l0 + ll);
-            }
-            __syncthreads();
-            const int npair = TT * lc;
-            int px[NK], pl[NK];
+        float2* dst = it.w < 0 ? grid : partial + (int64_t)it.w * TT * TT * L;
+        for (int r = warp; r < TT; r += kSpreadWarps) {
+            float2 acc[NK];
 #pragma unroll
-            for (int k = 0; k < NK; ++k) {
-                const int pp = lane + 32 * k;
-                px[k] = pp / lc;
-                pl[k] = pp - px[k] * lc;
-            }
-            float2* dst = it.w < 0 ? grid : partial + (int64_t)it.w * TT * TT * L;
-            for (int r = warp; r < TT; r += kSpreadWarps) {
-                float2 acc[NK];
+            for (int k = 0; k < NK; ++k) acc[k] = make_float2(0.f, 0.f);
+            for (int i = 0; i < np; ++i) {
+                const int2 o = soff[i];
+                // the point's row tap for this row (the wrap matters only when the tile is
+                // the whole grid: there a footprint can leave its right edge and re-enter)
+                int a = r - o.y;
+                a += a < 0 ? G : 0;
+                if ((unsigned)a >= (unsigned)W) continue;
+                const float wy = swt[i * 2 * W + W + a];
 #pragma unroll
-                for (int k = 0; k < NK; ++k) acc[k] = make_float2(0.f, 0.f);
-                for (int i = 0; i < np; ++i) {
-                    const int2 o = soff[i];
-                    int a = r - o.y;
-                    a += a < 0 ? G : 0;
-                    if ((unsigned)a >= (unsigned)W) continue;
-                    const float wy = swt[i * 2 * W + W + a];
-#pragma unroll
-                    for (int k = 0; k < NK; ++k) {
-                        int b = px[k] - o.x;
-                        b += b < 0 ? G : 0;
-                        const int bc = min(max(b, 0), W - 1);
-                        float w = swt[i * 2 * W + bc];
-                        w = ((unsigned)b < (unsigned)W) ? w * wy : 0.f;
-                        const float2 v = sval[i * LCS + pl[k]];
-                        acc[k].x = fmaf(w, v.x, acc[k].x);
-                        acc[k].y = fmaf(w, v.y, acc[k].y);
-                    }
+                for (int k = 0; k < NK; ++k) {
+                    int b = px[k] - o.x;
+                    b += b < 0 ? G : 0;
+                    const int bc = min(max(b, 0), W - 1);
+                    float w = swt[i * 2 * W + bc];
+                    w = ((unsigned)b < (unsigned)W) ? w * wy : 0.f;
+                    const float2 v = sval[i * LCS + pl[k]];
+                    acc[k].x = fmaf(w, v.x, acc[k].x);
+                    acc[k].y = fmaf(w, v.y, acc[k].y);
                 }
-                const int64_t rowo = it.w < 0 ? ((int64_t)(y0 + r) * G + x0) * L : (int64_t)r * TT * L;
-#pragma unroll
-                for (int k = 0; k < NK; ++k)
-                    if (lane + 32 * k < npair) dst[rowo + (int64_t)px[k] * L + l0 + pl[k]] = acc[k];
             }
-            __syncthreads();
+            const int64_t rowo = it.w < 0 ? ((int64_t)(y0 + r) * G + x0) * L : (int64_t)r * TT * L;
+#pragma unroll
+            for (int k = 0; k < NK; ++k)
+                if (lane + 32 * k < npair) dst[rowo + (int64_t)px[k] * L + l0 + pl[k]] = acc[k];
         }
+        __syncthreads();
     }
     if (it.w >= 0) {
         // the last item of the tile to arrive sums the partial slots in order
