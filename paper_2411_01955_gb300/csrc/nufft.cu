@@ -435,6 +435,11 @@ __global__ void __launch_bounds__(256) k_spread_tiles(const float2* __restrict__
         swt[e] = __ldg(kbw + (int64_t)sidx[i] * 2 * W + h);
     }
     if constexpr (FULL16) {
+        // the first chunk's values load together with the weights (one latency round)
+        for (int e = threadIdx.x; e < np * 16; e += blockDim.x) {
+            const int i = e >> 4, ll = e & 15;
+            sval[i * 16 + ll] = __ldg(ys + (int64_t)sidx[i] * L + ll);
+        }
         __syncthreads();
         for (int e = threadIdx.x; e < np * TT; e += blockDim.x) {
             const int i = e / TT, x = e - i * TT;
@@ -444,9 +449,11 @@ __global__ void __launch_bounds__(256) k_spread_tiles(const float2* __restrict__
         }
         const int h = lane >> 4, l = lane & 15;
         for (int l0 = 0; l0 < L; l0 += 16) {
-            for (int e = threadIdx.x; e < np * 16; e += blockDim.x) {
-                const int i = e >> 4, ll = e & 15;
-                sval[i * 16 + ll] = __ldg(ys + (int64_t)sidx[i] * L + l0 + ll);
+            if (l0 > 0) {   // later 16-coil chunks
+                for (int e = threadIdx.x; e < np * 16; e += blockDim.x) {
+                    const int i = e >> 4, ll = e & 15;
+                    sval[i * 16 + ll] = __ldg(ys + (int64_t)sidx[i] * L + l0 + ll);
+                }
             }
             __syncthreads();
             float2* dst = it.w < 0 ? grid : partial + (int64_t)it.w * TT * TT * L;
