@@ -101,7 +101,7 @@ ADJ_BYTES = (_Y + _PTS + _G2L) + (_G2L + _ROWS) + (_ROWS + _S + 320 * 320 * 8)
 # the kernel has changed since the last capture.
 PERSISTENT_TRAFFIC_BYTES = 16408576 + 2208768
 # The same for one k_pcg_batch launch (all 16 slices of a default step); None until captured.
-BATCH_TRAFFIC_BYTES = 45362993664 + 31120549632
+BATCH_TRAFFIC_BYTES = 44440873472 + 30583470080
 
 
 def parse():
