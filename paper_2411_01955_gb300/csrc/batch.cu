@@ -234,9 +234,22 @@ __global__ void __launch_bounds__(HQS_BATCH_BD, 2) k_hqs_batch(BatchArgs B) {
     __shared__ double acc[2][HQS_BATCH_MAX];
     __shared__ double tot[2][HQS_BATCH_MAX];
     __shared__ double rzs[HQS_BATCH_MAX], alphas[HQS_BATCH_MAX], betas[HQS_BATCH_MAX];
-    __shared__ int sl_cache;
+    __shared__ int sl_cache, tw_cur;
     const int ns = B.ns, G = gridDim.x, bid = blockIdx.x;
     const float2* twN = nullptr;   // n-point twiddles of the current slice (global)
+    // the 2n-point twiddles of the Toeplitz items stay in the shared region after the
+    // largest lines buffer and its image row (the blur and preconditioner items use
+    // less than the lines buffer), restaged only when the slice size changes
+    float2* twT = s + (size_t)768 * kLines + 384;
+    if (threadIdx.x == 0) tw_cur = 0;
+#define STAGE_TW2(AA)                                                                    \
+    if (tw_cur != 2 * (AA).n) {                                                          \
+        __syncthreads();                                                                 \
+        for (int i_ = threadIdx.x; i_ < 2 * (AA).n; i_ += blockDim.x) twT[i_] = (AA).tw[i_]; \
+        __syncthreads();                                                                 \
+        if (threadIdx.x == 0) tw_cur = 2 * (AA).n;                                       \
+        __syncthreads();                                                                 \
+    }
 #define BB_BARRIER()                                \
     do {                                            \
         if (!grid_barrier(B.bar, B.err)) return;    \
@@ -275,17 +288,21 @@ __global__ void __launch_bounds__(HQS_BATCH_BD, 2) k_hqs_batch(BatchArgs B) {
         // q = H u
         FOR_ITEMS(BL_ROWS, {
             const int n = S.A.n, ch = it_ / n, iy = it_ - ch * n;
-            HQS_BATCH_DISPATCH(n, (toep_rows_fwd_item<N2, HQS_BATCH_BD>(S.A, iy, ch, S.u, nullptr, 0.f, false, s)));
+            STAGE_TW2(S.A);
+            HQS_BATCH_DISPATCH(n, (toep_rows_fwd_item<N2, HQS_BATCH_BD>(S.A, iy, ch, S.u, nullptr, 0.f, false, s,
+                                                                        nullptr, twT)));
         });
         BB_BARRIER();
         FOR_ITEMS(BL_COLS, {
             const int n = S.A.n, N2v = 2 * n, ch = it_ / N2v, kx = it_ - ch * N2v;
-            HQS_BATCH_DISPATCH(n, (toep_cols_item<N2, HQS_BATCH_BD>(S.A, kx, ch, s)));
+            STAGE_TW2(S.A);
+            HQS_BATCH_DISPATCH(n, (toep_cols_item<N2, HQS_BATCH_BD>(S.A, kx, ch, s, twT)));
         });
         BB_BARRIER();
         FOR_ITEMS(BL_ROWS, {
             const int n = S.A.n, ch = it_ / n, iy = it_ - ch * n;
-            HQS_BATCH_DISPATCH(n, (toep_rows_adj_item<N2, HQS_BATCH_BD>(S.A, iy, ch, S.q, S.u, 1.f, bcoef, 1, s)));
+            STAGE_TW2(S.A);
+            HQS_BATCH_DISPATCH(n, (toep_rows_adj_item<N2, HQS_BATCH_BD>(S.A, iy, ch, S.q, S.u, 1.f, bcoef, 1, s, twT)));
         });
         BB_BARRIER();
         FOR_ITEMS(BL_EPI, {   // several coil chunks: fixed-order chunk sum + epilogue
@@ -357,19 +374,23 @@ __global__ void __launch_bounds__(HQS_BATCH_BD, 2) k_hqs_batch(BatchArgs B) {
             BB_BARRIER();
             FOR_ITEMS(BL_ROWS, {
                 const int n = S.A.n, ch = it_ / n, iy = it_ - ch * n;
-                HQS_BATCH_DISPATCH(n, (toep_rows_fwd_item<N2, HQS_BATCH_BD>(S.A, iy, ch, S.p, nullptr, 0.f, false, s)));
+                STAGE_TW2(S.A);
+                HQS_BATCH_DISPATCH(n, (toep_rows_fwd_item<N2, HQS_BATCH_BD>(S.A, iy, ch, S.p, nullptr, 0.f, false, s,
+                                                                            nullptr, twT)));
             });
             BB_BARRIER();
             FOR_ITEMS(BL_COLS, {
                 const int n = S.A.n, N2v = 2 * n, ch = it_ / N2v, kx = it_ - ch * N2v;
-                HQS_BATCH_DISPATCH(n, (toep_cols_item<N2, HQS_BATCH_BD>(S.A, kx, ch, s)));
+                STAGE_TW2(S.A);
+            HQS_BATCH_DISPATCH(n, (toep_cols_item<N2, HQS_BATCH_BD>(S.A, kx, ch, s, twT)));
             });
             BB_BARRIER();
             CLEAR_ACC();
             FOR_ITEMS(BL_ROWS, {
                 const int n = S.A.n, ch = it_ / n, iy = it_ - ch * n;
                 double v = 0.0;
-                HQS_BATCH_DISPATCH(n, (v = toep_rows_adj_item<N2, HQS_BATCH_BD>(S.A, iy, ch, S.q, S.p, 1.f, bcoef, 1, s)));
+                STAGE_TW2(S.A);
+                HQS_BATCH_DISPATCH(n, (v = toep_rows_adj_item<N2, HQS_BATCH_BD>(S.A, iy, ch, S.q, S.p, 1.f, bcoef, 1, s, twT)));
                 v = cta_sum(v, red);
                 if (threadIdx.x == 0) acc[0][si] += v;
             });
@@ -455,6 +476,7 @@ __global__ void __launch_bounds__(HQS_BATCH_BD, 2) k_hqs_batch(BatchArgs B) {
 #undef BB_BARRIER
 #undef FOR_ITEMS
 #undef STAGE_TWN
+#undef STAGE_TW2
 #undef CLEAR_ACC
 }
 
