@@ -574,13 +574,11 @@ extern "C" int hqs_plan_retile(hqs_plan p, int tile, void* stream) {
 
 // ------------------------------------------------ tile-owned spreading items
 void spread_free(hqs_plan_s* p) {
-    cudaFree(p->spread.bin_off);
     cudaFree(p->spread.items);
     cudaFree(p->spread.tile_info);
     cudaFree(p->spread.tile_nb);
     cudaFree(p->spread.tickets);
     cudaFree(p->spread.partial);
-    p->spread.bin_off = nullptr;
     p->spread.items = nullptr;
     p->spread.tile_info = nullptr;
     p->spread.tile_nb = nullptr;
@@ -643,20 +641,18 @@ int spread_build(hqs_plan_s* p, const std::vector<int>& hc, cudaStream_t s) {
     nw.ysort = p->spread.ysort;
     nw.kbw = p->spread.kbw;
     int rc = HQS_OK;
-    if (cudaMalloc(&nw.bin_off, (nbins + 1) * sizeof(int)) || cudaMalloc(&nw.items, items.size() * sizeof(int4)) ||
+    if (cudaMalloc(&nw.items, items.size() * sizeof(int4)) ||
         cudaMalloc(&nw.tile_info, nbins * sizeof(int2)) || cudaMalloc(&nw.tickets, nbins * sizeof(unsigned)) ||
         cudaMalloc(&nw.tile_nb, (size_t)nbins * 10 * sizeof(int2)) ||
         (slots > 0 && cudaMalloc(&nw.partial, slots * slot_elems * sizeof(float2)))) {
         rc = HQS_ERR_OOM;
-    } else if (cudaMemcpyAsync(nw.bin_off, off.data(), (nbins + 1) * sizeof(int), cudaMemcpyHostToDevice, s) ||
-               cudaMemcpyAsync(nw.items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice, s) ||
+    } else if (cudaMemcpyAsync(nw.items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice, s) ||
                cudaMemcpyAsync(nw.tile_info, info.data(), nbins * sizeof(int2), cudaMemcpyHostToDevice, s) ||
                cudaMemcpyAsync(nw.tile_nb, nbt.data(), (size_t)nbins * 10 * sizeof(int2), cudaMemcpyHostToDevice, s) ||
                cudaMemsetAsync(nw.tickets, 0, nbins * sizeof(unsigned), s) || cudaStreamSynchronize(s)) {
         rc = HQS_ERR_CUDA;
     }
     if (rc != HQS_OK) {
-        cudaFree(nw.bin_off);
         cudaFree(nw.items);
         cudaFree(nw.tile_info);
         cudaFree(nw.tile_nb);
@@ -665,7 +661,7 @@ int spread_build(hqs_plan_s* p, const std::vector<int>& hc, cudaStream_t s) {
         return rc;
     }
     spread_free(p);
-    nw.bytes = (nbins + 1) * sizeof(int) + items.size() * sizeof(int4) + nbins * (11 * sizeof(int2) + sizeof(unsigned)) +
+    nw.bytes = items.size() * sizeof(int4) + nbins * (11 * sizeof(int2) + sizeof(unsigned)) +
                slots * slot_elems * sizeof(float2);
     p->spread = nw;
     p->bytes += nw.bytes;

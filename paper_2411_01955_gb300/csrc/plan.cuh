@@ -62,7 +62,6 @@ struct hqs_plan_s {
     // written by the CTAs of its items; candidates are the points of the 3 x 3
     // neighbouring bins, taken in chunks of <= HQS_SPREAD_CAND
     struct Spread {
-        int* bin_off = nullptr;        // [nbins + 1] sorted-point offsets per bin
         int4* items = nullptr;         // (tile, first candidate, end candidate, partial slot or -1)
         int2* tile_info = nullptr;     // [nbins] (chunks, first partial slot)
         int2* tile_nb = nullptr;       // [nbins][10]: (first point, candidate prefix) of each distinct
