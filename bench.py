@@ -455,6 +455,10 @@ def run_ours(args, rank, world, dist):
     # the precision variant (BF16x3 / FP16x3 tensor-core Toeplitz passes): A^H A
     # time, per-stage DC solves to 1e-4 and their distance to the FP32 solutions
     mixed = mixed_precision_summary(hq, plans[:4], rhss[:4], xs[:4], timed)
+    # the learned preconditioner on this workload's shapes, compact (outside the
+    # timed regions): 2 training seeds x 16 iterates, 200 Adam steps, 2 held-out seeds
+    learned = learned_summary(hq, range(1000, 1002), range(5000, 5002), steps=200)
+    learned = {k: v for k, v in learned.items() if k != "held_out"}
 
     # end to end through the public API with host buffers: H2D of y, D2H of x
     y_host = [y.cpu().pin_memory() for y in ys]
@@ -519,6 +523,7 @@ def run_ours(args, rank, world, dist):
         "mean_cg_iterations": mean_iters,
         "true_rel_residual_max": max(true_res),
         "mixed_precision": mixed,
+        "learned_precond": learned,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
                      "traffic": BATCH_TRAFFIC_BYTES if args.mode == "batched" else PERSISTENT_TRAFFIC_BYTES,
@@ -924,7 +929,12 @@ def run_hqs320(args, rank, world, dist):
         torch.cuda.synchronize()
         return max_over_ranks(e0.elapsed_time(e1), dist) / reps
     smaps_ms = timed_ms(lambda: hq.estimate_smaps(traj, ys[0], n, smaps_out), max(args.steps, 3))
+    # the network's 32 -> 32 layers on the tensor cores (the default) and on the FP32 cores
     denoise_ms = timed_ms(lambda: net.denoise(xs[0], den_out, 0.05), 10 * max(args.steps, 3))
+    net.set_precision(hq.HQS_PREC_FP32)
+    denoise_fp32_ms = timed_ms(lambda: net.denoise(xs[0], den_out, 0.05), 10 * max(args.steps, 3))
+    net.set_precision(hq.HQS_PREC_BF16X3)
+    net.status()
     clocks = clk.stop()
     if rank != 0:
         return
@@ -937,25 +947,22 @@ def run_hqs320(args, rank, world, dist):
                                "mu 1e-1 -> 1e-3, Gaussian smoothing denoiser, DC-preconditioned CG",
                    "batch_per_gpu": B, "alpha": alpha},
         "metrics": res, "clocks": clocks,
-        "smaps_estimation_ms": smaps_ms, "conv_denoiser_ms": denoise_ms,
+        "smaps_estimation_ms": smaps_ms, "conv_denoiser_ms": denoise_ms, "conv_denoiser_fp32_layers_ms": denoise_fp32_ms,
     }
     print(json.dumps(line), flush=True)
 
 
-def run_learned320(args, rank, world, dist):
+def learned_summary(hq, train_seeds, held_seeds, steps, iterates=16):
     """Learned preconditioner at 320^2 x 16 coils: the network is trained on the
-    GPU (library kernels) on DC-PCG iterates of training seeds 1000+ (mu
-    log-uniform in [1e-3, 1e-1]), then flexible CG with it and DC-PCG solve
-    held-out seeds 5000+ to relative residual 1e-4: iterations, solve time,
-    fallback counts."""
+    GPU (library kernels; its 32 -> 32 layers on the tensor cores) on DC-PCG
+    iterates of training seeds 1000+ (mu log-uniform in [1e-3, 1e-1]), then
+    flexible CG with it and DC-PCG solve held-out seeds 5000+ to relative
+    residual 1e-4: iterations, solve time, fallback counts."""
     import time as _time
     import torch
-    import paper_2411_01955_gb300 as hq
     learned = tests_module("learned_training")
     import synth
 
-    dev = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(dev)
     n, L = 320, 16
     traj_np = synth.traj_spiral(16, 2048, n)
     traj = torch.from_numpy(traj_np).cuda()
@@ -972,17 +979,18 @@ def run_learned320(args, rank, world, dist):
         return plan, rhs
     t0 = _time.time()
     examples = []
-    for seed in range(1000, 1000 + args.batch):
+    for seed in train_seeds:
         plan, rhs = slice_(seed)
         mu = float(10 ** rng.uniform(-3, -1))
-        for r, e in learned.solve_pairs(plan, rhs, mu, iterates=16):
+        for r, e in learned.solve_pairs(plan, rhs, mu, iterates=iterates):
             examples.append(learned.network_example(plan, mu, r, e))
     net = hq.Net()
     net.set_params(learned.initial_params(0))   # zero last layer: the untrained network is DC-PCG
-    losses = learned.train(net, examples, steps=400, batch=16, crop=64, lr=1e-3)
+    losses = learned.train(net, examples, steps=steps, batch=16, crop=64, lr=1e-3)
+    torch.cuda.synchronize()
     train_s = _time.time() - t0
     rows = []
-    for seed in range(5000, 5000 + 4):
+    for seed in held_seeds:
         plan, rhs = slice_(seed)
         mu = float(10 ** rng.uniform(-3, -1))
         out = {}
@@ -1001,20 +1009,41 @@ def run_learned320(args, rank, world, dist):
                          "rel_residual": info.rel_residual}
         hq.plan_set_net(plan, None)
         rows.append({"seed": seed, "mu": mu, **out})
+    net.status()
+    return {
+        "learned_iterations": float(np.mean([r["learned"]["iterations"] for r in rows])),
+        "dc_iterations": float(np.mean([r["dc"]["iterations"] for r in rows])),
+        "learned_solves_per_s": 1e3 / float(np.mean([r["learned"]["ms"] for r in rows])),
+        "dc_solves_per_s": 1e3 / float(np.mean([r["dc"]["ms"] for r in rows])),
+        "learned_fallbacks": int(sum(r["learned"]["fallback"] for r in rows)),
+        "train_pairs": len(examples), "train_steps": steps, "train_seconds": train_s,
+        "train_loss_first_last": [losses[0], float(np.mean(losses[-20:]))],
+        "held_out": rows,
+    }
+
+
+def run_learned320(args, rank, world, dist):
+    """The learned-preconditioner summary at full size: args.batch training
+    seeds x 16 DC-PCG iterates, 400 Adam steps on 64 x 64 crops, 4 held-out
+    seeds."""
+    import torch
+    import paper_2411_01955_gb300 as hq
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    res = learned_summary(hq, range(1000, 1000 + args.batch), range(5000, 5004), steps=400)
     if rank != 0:
         return
     line = {
         "metric": "DC solves to 1e-4 at 320^2, 16 coils: learned-preconditioned flexible CG vs DC-PCG",
-        "value": float(np.mean([r["learned"]["iterations"] for r in rows])), "unit": "CG iterations (mean)",
+        "value": res["learned_iterations"], "unit": "CG iterations (mean)",
         "n_gpus": world, "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded ellipse phantoms, Gaussian-bump coil maps, VD spiral)",
         "config": {"workload": "320x320, 16 coils, spiral 16x2048, KB W=6, sigma=2, mu log-uniform [1e-3, 1e-1]; "
                                f"training: {args.batch} seeds x 16 DC-PCG iterates, 400 Adam steps on 64x64 crops",
-                   "train_pairs": len(examples)},
-        "dc_mean_iterations": float(np.mean([r["dc"]["iterations"] for r in rows])),
-        "learned_fallbacks": int(sum(r["learned"]["fallback"] for r in rows)),
-        "train_seconds": train_s, "train_loss_first_last": [losses[0], float(np.mean(losses[-20:]))],
-        "held_out": rows,
+                   "train_pairs": res["train_pairs"]},
+        "dc_mean_iterations": res["dc_iterations"],
+        **{k: v for k, v in res.items() if k not in ("learned_iterations", "dc_iterations", "train_pairs")},
     }
     print(json.dumps(line), flush=True)
 

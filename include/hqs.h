@@ -236,6 +236,18 @@ HQS_API int hqs_last_solve_info(hqs_plan plan, hqs_solve_info* info, void* strea
 HQS_API int hqs_net_create(hqs_net* out);                  /* parameters zero */
 HQS_API void hqs_net_destroy(hqs_net net);
 HQS_API int hqs_net_num_params(void);
+/* Arithmetic of the two 32 -> 32 layers (their forward and input-gradient
+ * convolutions; the other layers and every weight gradient stay FP32):
+ * HQS_PREC_BF16X3 (the default) runs them as implicit GEMMs on the tcgen05
+ * tensor cores with BF16 hi/lo split operands (hi*hi + lo*hi + hi*lo, FP32
+ * accumulation; each product within 3 * 2^-16 of its exact value, relative),
+ * HQS_PREC_FP32 on the FP32 cores.  HQS_PREC_FP16X3: HQS_ERR_UNSUPPORTED. */
+HQS_API int hqs_net_set_precision(hqs_net net, int precision);
+/* Blocks on `stream`; HQS_ERR_TIMEOUT when a tensor-core convolution of this
+ * network gave up waiting for its MMAs (a bounded wait; the output of that
+ * launch is incomplete) since the last check, which clears the flag.  The loss
+ * of hqs_net_gradient / hqs_net_train_step and the learned solve check it too. */
+HQS_API int hqs_net_status(hqs_net net, void* stream);
 HQS_API int hqs_net_set_params(hqs_net net, const float* host, int count);  /* resets Adam */
 HQS_API int hqs_net_get_params(hqs_net net, float* host, int count);
 HQS_API int hqs_net_forward(hqs_net net, const float* x, float* y, int N, int H, int W, void* stream);

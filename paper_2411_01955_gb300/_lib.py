@@ -94,6 +94,8 @@ _SIGS = {
     "hqs_net_create": (C.c_int, [C.POINTER(C.c_void_p)]),
     "hqs_net_destroy": (None, [C.c_void_p]),
     "hqs_net_num_params": (C.c_int, []),
+    "hqs_net_set_precision": (C.c_int, [C.c_void_p, C.c_int]),
+    "hqs_net_status": (C.c_int, [C.c_void_p, C.c_void_p]),
     "hqs_net_set_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "hqs_net_get_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "hqs_net_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,
@@ -454,6 +456,16 @@ class Net:
         _check(library().hqs_net_create(C.byref(h)), "hqs_net_create")
         self.handle = h
         self.num_params = library().hqs_net_num_params()
+
+    def set_precision(self, precision):
+        """HQS_PREC_BF16X3 (default: the 32 -> 32 layers on the tensor cores) or
+        HQS_PREC_FP32."""
+        _check(library().hqs_net_set_precision(self.handle, int(precision)), "hqs_net_set_precision")
+
+    def status(self, stream=None):
+        """Raises HqsError(HQS_ERR_TIMEOUT) if a tensor-core convolution gave up a
+        wait since the last check."""
+        _check(library().hqs_net_status(self.handle, _stream(stream)), "hqs_net_status")
 
     def set_params(self, vec):
         import numpy as np

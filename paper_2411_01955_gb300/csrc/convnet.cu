@@ -13,7 +13,10 @@
 #include <cstdio>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "net.cuh"
+#include "tc.cuh"
 
 #define CONV_TILE 16
 
@@ -124,6 +127,183 @@ __global__ void __launch_bounds__(256) k_conv3x3_wgrad(const float* __restrict__
     }
 }
 
+// ------------------------------------------------ tensor-core 3x3 conv, 32 -> 32
+// The hidden layers as an implicit GEMM on the tcgen05 tensor cores:
+//   D[pixel][o] = sum over (tap, i) of A[pixel][tap * 32 + i] B[o][tap * 32 + i],
+//   A[pixel][tap * 32 + i] = x[i][pixel shifted by tap] (zero outside the image),
+// M = 128 pixels of the flattened (sample, row, column) index per tile, N = 32
+// output channels, K = 9 taps x 32 channels = 288 (18 steps of 16).  Both
+// operands are split into BF16 hi + lo parts, v = hi + lo + O(2^-16 |v|), and
+// multiplied as hi*hi + lo*hi + hi*lo with FP32 accumulation in TMEM; the dropped
+// lo*lo term and the split residuals leave each product within 3 * 2^-16 of
+// its exact value (relative).  A (the tile's im2col) and B (the weights, staged
+// once per CTA) sit in shared memory K-major with the 128-byte swizzle; K chunk
+// j holds taps 2j and 2j + 1 (64 BF16 = one 128-byte row), the last chunk tap 8
+// only (its second half is never read: the last chunk takes two K steps).
+// One CTA of 512 threads per SM walks the tiles; thread (m, q) gathers pixel
+// m's channels 8q..8q+7 for all nine taps, one elected thread issues the MMAs,
+// and warp w reads TMEM lanes 32 (w mod 4).. (its quarter) for output channels
+// 8 (w / 4)..8 (w / 4) + 7.
+constexpr int kTcC = 32, kTcM = 128, kTcChunks = 5, kTcThreads = 512;
+constexpr uint32_t kTcA = kTcM * 128, kTcB = kTcC * 128;   // bytes of one K chunk of A / B
+constexpr size_t kTcSmem = 2 * (size_t)kTcChunks * (kTcA + kTcB) + 16 + 1024;
+constexpr long long kTcWaitCycles = 2000000000ll;
+
+// byte offset of the 16-byte unit `unit` of row `row` in a 128-byte-swizzled,
+// K-major operand chunk (8-row groups of 1024 bytes)
+__device__ __forceinline__ uint32_t sw128_off(int row, int unit) {
+    return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((unit ^ (row & 7)) << 4));
+}
+
+// 8 consecutive K elements of one operand row as BF16 hi and lo units
+__device__ __forceinline__ void put_split_unit(uint8_t* hi, uint8_t* lo, uint32_t off, const float* v) {
+    uint32_t a[4], b[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * t]), h1 = __float2bfloat16_rn(v[2 * t + 1]);
+        const __nv_bfloat16 l0 = __float2bfloat16_rn(v[2 * t] - __bfloat162float(h0));
+        const __nv_bfloat16 l1 = __float2bfloat16_rn(v[2 * t + 1] - __bfloat162float(h1));
+        a[t] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+        b[t] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+    }
+    *reinterpret_cast<uint4*>(hi + off) = make_uint4(a[0], a[1], a[2], a[3]);
+    *reinterpret_cast<uint4*>(lo + off) = make_uint4(b[0], b[1], b[2], b[3]);
+}
+
+// MODE as k_conv3x3 (CONV_FWD / CONV_FWD_RELU with bias, CONV_DGRAD_MASK with
+// the layer's weights flipped and transposed and the ReLU mask of its input)
+template <int MODE>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_conv3x3_tc(const float* __restrict__ x, const float* __restrict__ W, const float* __restrict__ bias,
+                 const float* __restrict__ mask, float* __restrict__ y, int N, int H, int Wd,
+                 unsigned* __restrict__ err) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint8_t* a_hi = sm;
+    uint8_t* a_lo = a_hi + kTcChunks * kTcA;
+    uint8_t* b_hi = a_lo + kTcChunks * kTcA;
+    uint8_t* b_lo = b_hi + kTcChunks * kTcB;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(b_lo + kTcChunks * kTcB);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 1);
+    __shared__ int s_fail;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int HW = H * Wd;
+    const long long total = (long long)N * HW;
+    const long long ntiles = (total + kTcM - 1) / kTcM;
+
+    if (tid == 0) {
+        tc::mbar_init(bar, 1);
+        s_fail = 0;
+        tc::fence_mbar_init();
+    }
+    if (warp == 0) tc::tmem_alloc(tmem_slot, 32);
+    // B[o][tap * 32 + i]: 32 rows x 9 taps x 4 units of 8 channels
+    for (int u = tid; u < kTcC * 9 * 4; u += blockDim.x) {
+        const int q = u & 3, tap = (u >> 2) % 9, o = (u >> 2) / 9;
+        float v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int i = 8 * q + e;
+            v[e] = MODE == CONV_DGRAD_MASK ? W[((size_t)i * kTcC + o) * 9 + (8 - tap)]   // layer W[o = i][i = o]
+                                           : W[((size_t)o * kTcC + i) * 9 + tap];
+        }
+        put_split_unit(b_hi + (tap >> 1) * kTcB, b_lo + (tap >> 1) * kTcB, sw128_off(o, (tap & 1) * 4 + q), v);
+    }
+    tc::fence_proxy_async_smem();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int m = tid & (kTcM - 1), q = tid >> 7;
+    const int g = warp & 3, cb = warp >> 2;
+    uint32_t phase = 0;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        // im2col of pixel m, channels 8q..8q+7, all nine taps
+        {
+            const long long P = t * kTcM + m;
+            const bool in = P < total;
+            int n = 0, py = 0, px = 0;
+            if (in) {
+                n = (int)(P / HW);
+                const int rem = (int)(P - (long long)n * HW);
+                py = rem / Wd;
+                px = rem - py * Wd;
+            }
+            const float* xb = x + ((size_t)n * kTcC + 8 * q) * HW;
+            float v[9][8];
+#pragma unroll
+            for (int tap = 0; tap < 9; ++tap) {
+                const int yy = py + tap / 3 - 1, xx = px + tap % 3 - 1;
+                const bool ok = in && yy >= 0 && yy < H && xx >= 0 && xx < Wd;
+                const float* src = xb + (ok ? yy * Wd + xx : 0);
+#pragma unroll
+                for (int e = 0; e < 8; ++e) v[tap][e] = ok ? __ldg(src + (size_t)e * HW) : 0.f;
+            }
+#pragma unroll
+            for (int tap = 0; tap < 9; ++tap)
+                put_split_unit(a_hi + (tap >> 1) * kTcA, a_lo + (tap >> 1) * kTcA, sw128_off(m, (tap & 1) * 4 + q),
+                               v[tap]);
+        }
+        tc::fence_proxy_async_smem();
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+        if (tid == 0) {
+            const uint32_t idesc = tc::idesc_f16(kTcM, kTcC, false);
+            const uint32_t ah = tc::smem_u32(a_hi), al = tc::smem_u32(a_lo);
+            const uint32_t bh = tc::smem_u32(b_hi), bl = tc::smem_u32(b_lo);
+            uint32_t acc = 0;
+            for (int j = 0; j < kTcChunks; ++j) {
+                const int steps = j + 1 < kTcChunks ? 4 : 2;
+                for (int k = 0; k < steps; ++k) {
+                    const uint32_t ao = j * kTcA + k * 32, bo = j * kTcB + k * 32;
+                    tc::mma_f16(tmem, tc::sdesc_sw128(ah + ao), tc::sdesc_sw128(bh + bo), idesc, acc);
+                    tc::mma_f16(tmem, tc::sdesc_sw128(al + ao), tc::sdesc_sw128(bh + bo), idesc, 1u);
+                    tc::mma_f16(tmem, tc::sdesc_sw128(ah + ao), tc::sdesc_sw128(bl + bo), idesc, 1u);
+                    acc = 1u;
+                }
+            }
+            tc::mma_commit(bar);
+        }
+        const bool ok = tc::mbar_wait(bar, phase, kTcWaitCycles, &s_fail);
+        phase ^= 1u;
+        if (!ok) {
+            atomicOr(err, HQS_DEVERR_TIMEOUT);
+            s_fail = 1;
+        }
+        __syncthreads();
+        if (s_fail) break;
+        tc::fence_after();
+        // epilogue: TMEM lane quarter g = pixels 32 g + lane, channels 8 cb..8 cb + 7
+        float d[8];
+        tc::tmem_ld8(tmem + ((uint32_t)(32 * g) << 16) + 8 * cb, d);
+        const long long P = t * kTcM + 32 * g + lane;
+        if (P < total) {
+            const int n = (int)(P / HW);
+            const int rem = (int)(P - (long long)n * HW);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int co = 8 * cb + e;
+                const size_t idx = ((size_t)n * kTcC + co) * HW + rem;
+                float v = d[e];
+                if (MODE != CONV_DGRAD_MASK) v += __ldg(bias + co);
+                if (MODE == CONV_FWD_RELU) v = fmaxf(v, 0.f);
+                if (MODE == CONV_DGRAD_MASK) v = mask[idx] > 0.f ? v : 0.f;
+                y[idx] = v;
+            }
+        }
+        // the next tile rewrites A and D only after every thread is done with both
+        tc::fence_before();
+        __syncthreads();
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after();
+        tc::tmem_dealloc(tmem, 32);
+    }
+}
+
 // out[k] = sum over t of part[t][k] (fixed order), accumulated in fp64.
 __global__ void k_sum_tiles(const float* __restrict__ part, int ntiles, int count, float* __restrict__ out) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -197,6 +377,25 @@ int conv_launch(const float* x, const float* W, const float* b, const float* mas
     return HQS_OK;
 }
 
+// the 32 -> 32 layers on the tensor cores: one 512-thread CTA per SM walking the
+// 128-pixel tiles
+template <int MODE>
+int conv_tc_launch(const float* x, const float* W, const float* b, const float* mask, float* y, int N, int H,
+                   int Wd, unsigned* err, cudaStream_t st) {
+    static int sms[64] = {0};
+    int dev = 0;
+    HQS_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return HQS_ERR_UNSUPPORTED;
+    if (!sms[dev]) HQS_CUDA_TRY(cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev));
+    HQS_CUDA_TRY(cudaFuncSetAttribute(k_conv3x3_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)kTcSmem));
+    const long long tiles = ((long long)N * H * Wd + kTcM - 1) / kTcM;
+    const int grid = (int)std::min<long long>(tiles, sms[dev]);
+    k_conv3x3_tc<MODE><<<grid, kTcThreads, kTcSmem, st>>>(x, W, b, mask, y, N, H, Wd, err);
+    HQS_CUDA_TRY(cudaGetLastError());
+    return HQS_OK;
+}
+
 template <int CIN, int COUT>
 int wgrad_launch(const float* a, const float* dz, float* part, float* grad, int N, int H, int Wd,
                  cudaStream_t st) {
@@ -259,10 +458,15 @@ int net_forward(hqs_net_s* net, const float* x, float* out, int N, int H, int Wd
     const int Hd = HQS_NET_HIDDEN;
     HQS_TRY_RC((conv_launch<2, HQS_NET_HIDDEN, CONV_FWD_RELU>(x, P + layer_offset(0), P + layer_offset(0) + Hd * 2 * 9,
                                                               nullptr, net->act[0], N, H, Wd, st)));
-    HQS_TRY_RC((conv_launch<HQS_NET_HIDDEN, HQS_NET_HIDDEN, CONV_FWD_RELU>(
-        net->act[0], P + layer_offset(1), P + layer_offset(1) + Hd * Hd * 9, nullptr, net->act[1], N, H, Wd, st)));
-    HQS_TRY_RC((conv_launch<HQS_NET_HIDDEN, HQS_NET_HIDDEN, CONV_FWD_RELU>(
-        net->act[1], P + layer_offset(2), P + layer_offset(2) + Hd * Hd * 9, nullptr, net->act[2], N, H, Wd, st)));
+    for (int l = 1; l <= 2; ++l) {
+        const float* Wl = P + layer_offset(l);
+        if (net->precision == HQS_PREC_BF16X3)
+            HQS_TRY_RC((conv_tc_launch<CONV_FWD_RELU>(net->act[l - 1], Wl, Wl + Hd * Hd * 9, nullptr, net->act[l], N,
+                                                      H, Wd, net->dev_err, st)));
+        else
+            HQS_TRY_RC((conv_launch<HQS_NET_HIDDEN, HQS_NET_HIDDEN, CONV_FWD_RELU>(
+                net->act[l - 1], Wl, Wl + Hd * Hd * 9, nullptr, net->act[l], N, H, Wd, st)));
+    }
     HQS_TRY_RC((conv_launch<HQS_NET_HIDDEN, 2, CONV_FWD>(net->act[2], P + layer_offset(3),
                                                          P + layer_offset(3) + 2 * Hd * 9, nullptr,
                                                          out ? out : net->act[3], N, H, Wd, st)));
@@ -281,18 +485,18 @@ static int net_backprop(hqs_net_s* net, const float* x, int N, int H, int Wd, cu
     HQS_TRY_RC((conv_launch<2, HQS_NET_HIDDEN, CONV_DGRAD_MASK>(dz, P + layer_offset(3), nullptr, net->act[2], da, N,
                                                                 H, Wd, st)));
     std::swap(dz, da);
-    // layer 3
-    HQS_TRY_RC((wgrad_launch<HQS_NET_HIDDEN, HQS_NET_HIDDEN>(net->act[1], dz, net->part, G + layer_offset(2), N, H,
-                                                             Wd, st)));
-    HQS_TRY_RC((conv_launch<HQS_NET_HIDDEN, HQS_NET_HIDDEN, CONV_DGRAD_MASK>(dz, P + layer_offset(2), nullptr,
-                                                                             net->act[1], da, N, H, Wd, st)));
-    std::swap(dz, da);
-    // layer 2
-    HQS_TRY_RC((wgrad_launch<HQS_NET_HIDDEN, HQS_NET_HIDDEN>(net->act[0], dz, net->part, G + layer_offset(1), N, H,
-                                                             Wd, st)));
-    HQS_TRY_RC((conv_launch<HQS_NET_HIDDEN, HQS_NET_HIDDEN, CONV_DGRAD_MASK>(dz, P + layer_offset(1), nullptr,
-                                                                             net->act[0], da, N, H, Wd, st)));
-    std::swap(dz, da);
+    // layers 3 and 2 (H -> H)
+    for (int l = 2; l >= 1; --l) {
+        HQS_TRY_RC((wgrad_launch<HQS_NET_HIDDEN, HQS_NET_HIDDEN>(net->act[l - 1], dz, net->part, G + layer_offset(l),
+                                                                 N, H, Wd, st)));
+        if (net->precision == HQS_PREC_BF16X3)
+            HQS_TRY_RC((conv_tc_launch<CONV_DGRAD_MASK>(dz, P + layer_offset(l), nullptr, net->act[l - 1], da, N, H,
+                                                        Wd, net->dev_err, st)));
+        else
+            HQS_TRY_RC((conv_launch<HQS_NET_HIDDEN, HQS_NET_HIDDEN, CONV_DGRAD_MASK>(
+                dz, P + layer_offset(l), nullptr, net->act[l - 1], da, N, H, Wd, st)));
+        std::swap(dz, da);
+    }
     // layer 1 (2 -> H)
     HQS_TRY_RC((wgrad_launch<2, HQS_NET_HIDDEN>(x, dz, net->part, G + layer_offset(0), N, H, Wd, st)));
     return HQS_OK;
@@ -328,11 +532,23 @@ static int adam_update(hqs_net_s* net, float lr, cudaStream_t st) {
     return HQS_OK;
 }
 
+// HQS_ERR_TIMEOUT when a tensor-core convolution of this network gave up a wait
+// since the last check (the flag is cleared); blocks on the stream
+int net_check(hqs_net_s* net, cudaStream_t st) {
+    unsigned e = 0;
+    HQS_CUDA_TRY(cudaMemcpyAsync(&e, net->dev_err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    HQS_CUDA_TRY(cudaStreamSynchronize(st));
+    if (!e) return HQS_OK;
+    HQS_CUDA_TRY(cudaMemsetAsync(net->dev_err, 0, sizeof(unsigned), st));
+    HQS_CUDA_TRY(cudaStreamSynchronize(st));
+    return HQS_ERR_TIMEOUT;
+}
+
 static int read_loss(hqs_net_s* net, int N, double* loss, cudaStream_t st) {
     if (!loss) return HQS_OK;
     std::vector<double> h(N);
     HQS_CUDA_TRY(cudaMemcpyAsync(h.data(), net->loss_n, N * sizeof(double), cudaMemcpyDeviceToHost, st));
-    HQS_CUDA_TRY(cudaStreamSynchronize(st));
+    HQS_TRY_RC(net_check(net, st));
     double s = 0.0;
     for (double v : h) s += v;
     *loss = s / N;
@@ -350,6 +566,8 @@ extern "C" int hqs_net_create(hqs_net* out) {
     if (e == cudaSuccess) e = cudaMalloc(&net->grads, np * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&net->m, np * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&net->v, np * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&net->dev_err, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(net->dev_err, 0, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(net->params, 0, np * sizeof(float));
     if (e == cudaSuccess) e = cudaMemset(net->m, 0, np * sizeof(float));
     if (e == cudaSuccess) e = cudaMemset(net->v, 0, np * sizeof(float));
@@ -368,6 +586,7 @@ extern "C" void hqs_net_destroy(hqs_net net) {
     cudaFree(net->grads);
     cudaFree(net->m);
     cudaFree(net->v);
+    cudaFree(net->dev_err);
     for (float* b : net->act) cudaFree(b);
     cudaFree(net->dbuf[0]);
     cudaFree(net->dbuf[1]);
@@ -380,6 +599,18 @@ extern "C" void hqs_net_destroy(hqs_net net) {
 }
 
 extern "C" int hqs_net_num_params(void) { return net_num_params(); }
+
+extern "C" int hqs_net_set_precision(hqs_net net, int precision) {
+    if (!net) return HQS_ERR_INVALID_ARG;
+    if (precision != HQS_PREC_FP32 && precision != HQS_PREC_BF16X3) return HQS_ERR_UNSUPPORTED;
+    net->precision = precision;
+    return HQS_OK;
+}
+
+extern "C" int hqs_net_status(hqs_net net, void* stream) {
+    if (!net) return HQS_ERR_INVALID_ARG;
+    return net_check(net, (cudaStream_t)stream);
+}
 
 extern "C" int hqs_net_set_params(hqs_net net, const float* host, int count) {
     if (!net || !host || count != net_num_params()) return HQS_ERR_INVALID_ARG;

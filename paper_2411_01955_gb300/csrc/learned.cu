@@ -345,7 +345,7 @@ int fcg_learned(hqs_plan_s* p, float a, float b, const float2* rhs, float2* x, i
     HQS_CUDA_TRY(cudaMemcpyAsync(p->hist, hist.data(), hist.size() * sizeof(double), cudaMemcpyHostToDevice, st));
     HQS_CUDA_TRY(cudaMemsetAsync(p->dev_err, 0, sizeof(unsigned), st));
     HQS_CUDA_TRY(cudaStreamSynchronize(st));
-    return HQS_OK;
+    return p->net ? net_check(p->net, st) : HQS_OK;
 }
 
 extern "C" int hqs_plan_set_net(hqs_plan p, hqs_net net) {

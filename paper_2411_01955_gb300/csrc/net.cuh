@@ -12,6 +12,10 @@ struct hqs_net_s {
     float* m = nullptr;        // Adam moments
     float* v = nullptr;
     int adam_t = 0;
+    // HQS_PREC_BF16X3: the 32 -> 32 layers' forward and input-gradient convolutions
+    // on the tensor cores; HQS_PREC_FP32: every convolution on the FP32 cores
+    int precision = HQS_PREC_BF16X3;
+    unsigned* dev_err = nullptr;   // HQS_DEVERR_* bits of the tensor-core convolutions
     // activations and gradient scratch, grown on demand
     float* act[4] = {nullptr, nullptr, nullptr, nullptr};
     float* dbuf[2] = {nullptr, nullptr};
@@ -28,3 +32,4 @@ struct hqs_net_s {
 
 int net_num_params();
 int net_forward(hqs_net_s* net, const float* x, float* out, int N, int H, int Wd, cudaStream_t st);
+int net_check(hqs_net_s* net, cudaStream_t st);

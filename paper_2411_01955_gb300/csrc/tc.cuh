@@ -110,6 +110,22 @@ HQS_DEV void mma_commit(uint64_t* bar) {
                  : "memory");
 }
 
+// Makes this thread's generic-proxy shared-memory writes visible to the async
+// proxy (the tensor core's operand reads); each writer executes it before the
+// barrier that precedes the MMA issue.
+HQS_DEV void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 8 consecutive 32-bit TMEM columns of this thread's lane (32x32b shape).
+HQS_DEV void tmem_ld8(uint32_t taddr, float* v) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // 16 consecutive 32-bit TMEM columns of this thread's lane (32x32b shape).
 HQS_DEV void tmem_ld16(uint32_t taddr, float* v) {
     uint32_t r[16];

@@ -18,23 +18,33 @@ TOL = 1e-5
 EPS = 2.0 ** -24
 
 
-def rounding_model(params, rng):
-    """The network's float32 rounding as a perturbation of its parameters.
+TC_PRODUCT = 3 * 2.0 ** -16
+
+
+def rounding_model(params, rng, tensor_cores=True):
+    """The network's rounding as a perturbation of its parameters.
 
     A float32 dot product of K terms equals the exact dot product of slightly
     perturbed weights, |dw| <= K u |w| in the worst case and about sqrt(K) u |w|
     for rounding errors of random sign (Higham, Accuracy and Stability of
     Numerical Algorithms, sec. 3.1 and 2.8), u = 2^-24.  Each 3x3 layer sums
     K = 9 Cin products plus its bias, so every parameter of that layer is
-    perturbed by a relative sqrt(K) u with a random sign.  The learned path's
-    bound is then four times the oracle's deviation under this perturbation
-    (and a 2^-24 perturbation of its input), like the other iterated or
-    composed results in this suite; ReLU and the input scaling add no error
-    of their own beyond this model."""
+    perturbed by a relative sqrt(K) u with a random sign.  With the tensor
+    cores (the default precision) the two 32 -> 32 layers multiply BF16 hi/lo
+    splits: v = hi + lo + r with |r| <= 2^-16 |v| (two roundings to 8
+    significant bits), and hi*hi + lo*hi + hi*lo misses lo*lo + r_a b + a r_b,
+    at most 3 * 2^-16 |a b| per product; as a weight perturbation that is a
+    relative 3 * 2^-16 per weight (random sign) on top of the FP32
+    accumulation's sqrt(K) u.  The learned path's bound is then four times the
+    oracle's deviation under this perturbation (and a 2^-24 perturbation of its
+    input), like the other iterated or composed results in this suite; ReLU
+    and the input scaling add no error of their own beyond this model."""
     out = []
-    for W, b in params:
+    for li, (W, b) in enumerate(params):
         K = 9 * W.shape[1] + 1
         d = EPS * math.sqrt(K)
+        if tensor_cores and W.shape[0] == W.shape[1] == 32:
+            d += TC_PRODUCT
         out.append((W * (1 + d * rng.choice([-1.0, 1.0], size=W.shape)),
                     b * (1 + d * rng.choice([-1.0, 1.0], size=b.shape))))
     return out
@@ -59,31 +69,88 @@ def f32(params):
             for W, b in params]
 
 
-def test_net_forward_and_gradient_match_oracle():
+def grad_vector(wgrads):
+    return np.concatenate([np.concatenate([dW.ravel(), db.ravel()]) for dW, db in wgrads])
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("shape", [(2, 2, 20, 19), (2, 2, 160, 100)])
+def test_net_forward_and_gradient_match_oracle(precision, shape):
+    """Forward pass, loss and parameter gradient against the FP64 oracle: FP32
+    convolutions within 1e-5, the tensor-core 32 -> 32 layers within the bound
+    their BF16 split derives (rounding_model); 20 x 19 images leave partial
+    16 x 16 tiles and a partial 128-pixel tile, 2 x 160 x 100 gives 250
+    128-pixel tiles (more than one per SM)."""
     rng = np.random.default_rng(0)
     params = f32(random_params(1))
     net = hq().Net()
+    tc = precision == "bf16x3"
+    net.set_precision(hq().HQS_PREC_BF16X3 if tc else hq().HQS_PREC_FP32)
     assert net.num_params == convnet.num_params() == 19682
     net.set_params(convnet.flatten(params))
     assert np.array_equal(net.get_params(), convnet.flatten(params).astype(np.float32))
-    # odd spatial sizes: partial 16x16 tiles on both axes
-    x = rng.normal(size=(2, 2, 20, 19)).astype(np.float32)
-    t = rng.normal(size=(2, 2, 20, 19)).astype(np.float32)
+    x = rng.normal(size=shape).astype(np.float32)
+    t = rng.normal(size=shape).astype(np.float32)
     xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
     out = net.forward(xd).cpu().numpy()
     want, _ = convnet.forward(params, x.astype(np.float64))
-    assert rel(out, want) <= TOL
-    g, loss = net.gradient(xd, td)
     wloss, wgrads = convnet.loss_and_grad(params, x.astype(np.float64), t.astype(np.float64))
-    wg = np.concatenate([np.concatenate([dW.ravel(), db.ravel()]) for dW, db in wgrads])
-    assert abs(loss / wloss - 1) <= TOL
-    assert rel(g.cpu().numpy(), wg) <= TOL
+    wg = grad_vector(wgrads)
+    # the bound: the oracle under the rounding model of the chosen precision
+    prng = np.random.default_rng(21)
+    pp = rounding_model(params, prng, tensor_cores=tc)
+    xp = x.astype(np.float64) * (1 + EPS * prng.normal(size=x.shape))
+    pout, _ = convnet.forward(pp, xp)
+    ploss, pgrads = convnet.loss_and_grad(pp, xp, t.astype(np.float64))
+    pg = grad_vector(pgrads)
+    tol_out = max(TOL, 4 * rel(pout, want))
+    tol_loss = max(TOL, 4 * abs(ploss / wloss - 1))
+    tol_g = max(TOL, 4 * rel(pg, wg))
+    if not tc:
+        tol_out = tol_loss = tol_g = TOL
+    g, loss = net.gradient(xd, td)
+    err_out, err_loss, err_g = rel(out, want), abs(loss / wloss - 1), rel(g.cpu().numpy(), wg)
+    print(f"{precision} {shape}: forward {err_out:.2e} (bound {tol_out:.2e}), loss {err_loss:.2e} "
+          f"({tol_loss:.2e}), gradient {err_g:.2e} ({tol_g:.2e})")
+    assert err_out <= tol_out
+    assert err_loss <= tol_loss
+    assert err_g <= tol_g
     # per layer as well (a wrong layer offset would hide in the global norm)
     k = 0
-    for dW, db in wgrads:
+    for (dW, db), (pW, pb) in zip(wgrads, pgrads):
         m = dW.size + db.size
-        assert rel(g.cpu().numpy()[k:k + m], wg[k:k + m]) <= 1e-4
+        bound = max(1e-4, 4 * rel(pg[k:k + m], wg[k:k + m])) if tc else 1e-4
+        assert rel(g.cpu().numpy()[k:k + m], wg[k:k + m]) <= bound
         k += m
+    net.status()
+
+
+def test_tensor_core_layers_against_fp32_layers():
+    """The same network in both precisions on a 320 x 320 image (800 tiles of
+    128 pixels): the tensor-core forward stays within the BF16 split's bound of
+    the FP32 one, and the network's error flag stays clear."""
+    rng = np.random.default_rng(4)
+    params = f32(random_params(2))
+    x = torch.from_numpy(rng.normal(size=(1, 2, 320, 320)).astype(np.float32)).cuda()
+    outs = {}
+    for prec in (hq().HQS_PREC_FP32, hq().HQS_PREC_BF16X3):
+        net = hq().Net()
+        net.set_precision(prec)
+        net.set_params(convnet.flatten(params))
+        outs[prec] = net.forward(x).cpu().numpy().astype(np.float64)
+        net.status()
+    with pytest.raises(hq().HqsError):
+        hq().Net().set_precision(hq().HQS_PREC_FP16X3)
+    # bound from the oracle on a 64 x 64 crop (the error is per pixel, so the
+    # relative L2 bound carries over to the whole image)
+    crop = x[:, :, :64, :64].cpu().numpy().astype(np.float64)
+    want, _ = convnet.forward(params, crop)
+    prng = np.random.default_rng(22)
+    pout, _ = convnet.forward(rounding_model(params, prng, tensor_cores=True), crop)
+    bound = 8 * rel(pout, want)
+    err = rel(outs[hq().HQS_PREC_BF16X3], outs[hq().HQS_PREC_FP32])
+    print(f"tensor-core vs FP32 layers at 320^2: {err:.2e} (bound {bound:.2e})")
+    assert 0 < err <= bound
 
 
 def test_adam_step_matches_its_definition():
@@ -292,10 +359,15 @@ def test_net_denoiser_matches_oracle_forward():
     for sigma in (0.3, 0.05):
         out = torch.empty((40, 40), dtype=torch.complex64, device="cuda")
         net.denoise(to_dev(v), out, sigma)
-        inp = np.stack([v.real, v.imag])[None] / np.float32(sigma)
-        y, _ = convnet.forward(params, inp.astype(np.float32).astype(np.float64))
+        inp = (np.stack([v.real, v.imag])[None] / np.float32(sigma)).astype(np.float32).astype(np.float64)
+        y, _ = convnet.forward(params, inp)
         want = v - sigma * (y[0, 0] + 1j * y[0, 1])
-        assert rel(to_host(out), want) <= 1e-5
+        # bound: the oracle under the tensor-core rounding model (the default precision)
+        yp, _ = convnet.forward(rounding_model(params, np.random.default_rng(23)), inp)
+        tol = max(1e-5, 4 * rel(v - sigma * (yp[0, 0] + 1j * yp[0, 1]), want))
+        err = rel(to_host(out), want)
+        print(f"net denoiser, sigma {sigma}: {err:.2e} (bound {tol:.2e})")
+        assert err <= tol
     # sigma = 0 copies
     out = torch.empty((40, 40), dtype=torch.complex64, device="cuda")
     net.denoise(to_dev(v), out, 0.0)
