@@ -9,6 +9,7 @@
 // channels, fused with the ReLU mask of the layer input; the weight gradient
 // is reduced per 16x16 tile and then over tiles in a fixed order.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <vector>
@@ -128,35 +129,49 @@ __global__ void __launch_bounds__(256) k_conv3x3_wgrad(const float* __restrict__
 }
 
 // ------------------------------------------------ tensor-core 3x3 conv, 32 -> 32
-// The hidden layers as an implicit GEMM on the tcgen05 tensor cores:
-//   D[pixel][o] = sum over (tap, i) of A[pixel][tap * 32 + i] B[o][tap * 32 + i],
-//   A[pixel][tap * 32 + i] = x[i][pixel shifted by tap] (zero outside the image),
-// M = 128 pixels of the flattened (sample, row, column) index per tile, N = 32
-// output channels, K = 9 taps x 32 channels = 288 (18 steps of 16).  Both
-// operands are split into BF16 hi + lo parts, v = hi + lo + O(2^-16 |v|), and
-// multiplied as hi*hi + lo*hi + hi*lo with FP32 accumulation in TMEM; the dropped
-// lo*lo term and the split residuals leave each product within 3 * 2^-16 of
-// its exact value (relative).  A (the tile's im2col) and B (the weights, staged
-// once per CTA) sit in shared memory K-major with the 128-byte swizzle; K chunk
-// j holds taps 2j and 2j + 1 (64 BF16 = one 128-byte row), the last chunk tap 8
-// only (its second half is never read: the last chunk takes two K steps).
-// One CTA of 512 threads per SM walks the tiles; thread (m, q) gathers pixel
-// m's channels 8q..8q+7 for all nine taps, one elected thread issues the MMAs,
-// and warp w reads TMEM lanes 32 (w mod 4).. (its quarter) for output channels
-// 8 (w / 4)..8 (w / 4) + 7.
-constexpr int kTcC = 32, kTcM = 128, kTcChunks = 5, kTcThreads = 512;
-constexpr uint32_t kTcA = kTcM * 128, kTcB = kTcC * 128;   // bytes of one K chunk of A / B
-constexpr size_t kTcSmem = 2 * (size_t)kTcChunks * (kTcA + kTcB) + 16 + 1024;
+// The hidden layers as implicit GEMMs on the tcgen05 tensor cores.  One output
+// tile is 128 pixels of one image row (x0..x0+127 of row y), M = 128, with the
+// 32 output channels as N and the 9 taps x 32 input channels as K:
+//   D[m][o] = sum over taps (dy, dx) and channels i of X[i][y+dy][x0+m+dx] W[o][i][tap].
+// Every operand is split into BF16 hi + lo parts, v = hi + lo + r with
+// |r| <= 2^-16 |v|, and multiplied as hi*hi + hi*lo + lo*hi with FP32
+// accumulation (each product within 3 * 2^-16 of its exact value, relative).
+//
+// Shared memory holds three staged input rows (y-1, y, y+1) in a ring, each as
+// 130 pixel rows (x0-1..x0+128, zero outside the image) of 128 bytes =
+// [32 channels hi | 32 channels lo] BF16, K-major with the 128-byte swizzle.
+// A tap's A operand is then a view of the ring: the row buffer of y+dy started
+// dx+1 pixel rows in, so no im2col copy exists; a CTA walks a vertical run of output
+// rows and stages one new input row per tile, fetched into registers while the
+// tensor cores work on the previous tile.  The weights are staged once per CTA
+// as 5 chunks of two taps: 64 rows (32 output channels hi, then lo) x 128 bytes.
+// Per 16-channel K step and tap two MMAs run: A_hi x [W_hi; W_lo] (N = 64) into
+// TMEM columns 0..63 and A_lo x W_hi (N = 32) into columns 64..95; the epilogue
+// adds the three 32-column blocks.
+constexpr int kTcC = 32, kTcM = 128, kTcThreads = 256;
+constexpr int kTcRowPx = kTcM + 2;                          // staged pixels of an input row
+constexpr uint32_t kTcRowBytes = 17408;                     // 130 rows x 128 B, rounded up to 1 KB
+constexpr uint32_t kTcBChunk = 64 * 128;                    // two taps of W: 64 rows x 128 B
+constexpr size_t kTcSmem = 3 * (size_t)kTcRowBytes + 5 * (size_t)kTcBChunk + 16 + 1024;
+constexpr int kTcRowUnits = 4 * kTcRowPx;                   // (pixel, 8-channel unit) pairs of a row
+constexpr int kTcPer = (kTcRowUnits + kTcThreads - 1) / kTcThreads;
 constexpr long long kTcWaitCycles = 2000000000ll;
 
 // byte offset of the 16-byte unit `unit` of row `row` in a 128-byte-swizzled,
-// K-major operand chunk (8-row groups of 1024 bytes)
+// K-major operand region that starts on a 1 KB boundary
 __device__ __forceinline__ uint32_t sw128_off(int row, int unit) {
     return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((unit ^ (row & 7)) << 4));
 }
 
-// 8 consecutive K elements of one operand row as BF16 hi and lo units
-__device__ __forceinline__ void put_split_unit(uint8_t* hi, uint8_t* lo, uint32_t off, const float* v) {
+// descriptor of a view starting at any 128-byte row of a region written with
+// the swizzle of its absolute shared-memory addresses: the tensor core applies
+// the XOR pattern to the absolute address bits, so the base offset field stays
+// 0 (measured on sm_103a for every start row phase 0..7; with the phase in that
+// field the reads come out permuted)
+__device__ __forceinline__ uint64_t sdesc_view(uint32_t saddr) { return tc::sdesc_sw128(saddr); }
+
+// 8 channels of one operand row, split: hi into unit `uh`, lo into unit `ul`
+__device__ __forceinline__ void put_split(uint8_t* base, int row, int uh, int ul, const float* v) {
     uint32_t a[4], b[4];
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
@@ -166,38 +181,62 @@ __device__ __forceinline__ void put_split_unit(uint8_t* hi, uint8_t* lo, uint32_
         a[t] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
         b[t] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
     }
-    *reinterpret_cast<uint4*>(hi + off) = make_uint4(a[0], a[1], a[2], a[3]);
-    *reinterpret_cast<uint4*>(lo + off) = make_uint4(b[0], b[1], b[2], b[3]);
+    *reinterpret_cast<uint4*>(base + sw128_off(row, uh)) = make_uint4(a[0], a[1], a[2], a[3]);
+    *reinterpret_cast<uint4*>(base + sw128_off(row, ul)) = make_uint4(b[0], b[1], b[2], b[3]);
+}
+
+// input row yy of sample plane xn (channel stride HW), pixels x0-1..x0+128:
+// this thread's (pixel, 8-channel unit) pairs idx = tid + k * kTcThreads
+__device__ __forceinline__ void fetch_row(const float* __restrict__ xn, int HW, int H, int Wd, int yy, int x0,
+                                          float (&v)[kTcPer][8]) {
+#pragma unroll
+    for (int k = 0; k < kTcPer; ++k) {
+        const int idx = threadIdx.x + k * kTcThreads;
+        const int q = idx / kTcRowPx, pl = idx - q * kTcRowPx;
+        const int xx = x0 - 1 + pl;
+        const bool ok = idx < kTcRowUnits && yy >= 0 && yy < H && xx >= 0 && xx < Wd;
+        const float* src = xn + (ok ? (size_t)8 * q * HW + (size_t)yy * Wd + xx : 0);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[k][e] = ok ? __ldg(src + (size_t)e * HW) : 0.f;
+    }
+}
+
+__device__ __forceinline__ void put_row(uint8_t* buf, const float (&v)[kTcPer][8]) {
+#pragma unroll
+    for (int k = 0; k < kTcPer; ++k) {
+        const int idx = threadIdx.x + k * kTcThreads;
+        if (idx < kTcRowUnits) {
+            const int q = idx / kTcRowPx, pl = idx - q * kTcRowPx;
+            put_split(buf, pl, q, 4 + q, v[k]);
+        }
+    }
 }
 
 // MODE as k_conv3x3 (CONV_FWD / CONV_FWD_RELU with bias, CONV_DGRAD_MASK with
-// the layer's weights flipped and transposed and the ReLU mask of its input)
+// the layer's weights flipped and transposed and the ReLU mask of its input).
+// Work unit u = (sample, 128-column strip, run of `rows` output rows).
 template <int MODE>
-__global__ void __launch_bounds__(kTcThreads, 1)
+__global__ void __launch_bounds__(kTcThreads, 2)
     k_conv3x3_tc(const float* __restrict__ x, const float* __restrict__ W, const float* __restrict__ bias,
-                 const float* __restrict__ mask, float* __restrict__ y, int N, int H, int Wd,
-                 unsigned* __restrict__ err) {
+                 const float* __restrict__ mask, float* __restrict__ y, int N, int H, int Wd, int strips,
+                 int rows, int runs, unsigned* __restrict__ err) {
     extern __shared__ uint8_t smem_raw[];
-    uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    uint8_t* a_hi = sm;
-    uint8_t* a_lo = a_hi + kTcChunks * kTcA;
-    uint8_t* b_hi = a_lo + kTcChunks * kTcA;
-    uint8_t* b_lo = b_hi + kTcChunks * kTcB;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(b_lo + kTcChunks * kTcB);
+    uint8_t* ring = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint8_t* bsm = ring + 3 * kTcRowBytes;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(bsm + 5 * kTcBChunk);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 1);
     __shared__ int s_fail;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int HW = H * Wd;
-    const long long total = (long long)N * HW;
-    const long long ntiles = (total + kTcM - 1) / kTcM;
+    const int units = N * strips * runs;
 
     if (tid == 0) {
         tc::mbar_init(bar, 1);
         s_fail = 0;
         tc::fence_mbar_init();
     }
-    if (warp == 0) tc::tmem_alloc(tmem_slot, 32);
-    // B[o][tap * 32 + i]: 32 rows x 9 taps x 4 units of 8 channels
+    if (warp == 0) tc::tmem_alloc(tmem_slot, 128);
+    // W: chunk tap / 2, units (tap & 1) * 4 + q of row o (hi) and row 32 + o (lo)
     for (int u = tid; u < kTcC * 9 * 4; u += blockDim.x) {
         const int q = u & 3, tap = (u >> 2) % 9, o = (u >> 2) / 9;
         float v[8];
@@ -207,100 +246,105 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             v[e] = MODE == CONV_DGRAD_MASK ? W[((size_t)i * kTcC + o) * 9 + (8 - tap)]   // layer W[o = i][i = o]
                                            : W[((size_t)o * kTcC + i) * 9 + tap];
         }
-        put_split_unit(b_hi + (tap >> 1) * kTcB, b_lo + (tap >> 1) * kTcB, sw128_off(o, (tap & 1) * 4 + q), v);
+        uint8_t* cb = bsm + (tap >> 1) * kTcBChunk;
+        const int un = (tap & 1) * 4 + q;
+        // hi into row o, lo into row 32 + o (same unit)
+        uint32_t a[4], b[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * t]), h1 = __float2bfloat16_rn(v[2 * t + 1]);
+            const __nv_bfloat16 l0 = __float2bfloat16_rn(v[2 * t] - __bfloat162float(h0));
+            const __nv_bfloat16 l1 = __float2bfloat16_rn(v[2 * t + 1] - __bfloat162float(h1));
+            a[t] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+            b[t] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+        }
+        *reinterpret_cast<uint4*>(cb + sw128_off(o, un)) = make_uint4(a[0], a[1], a[2], a[3]);
+        *reinterpret_cast<uint4*>(cb + sw128_off(32 + o, un)) = make_uint4(b[0], b[1], b[2], b[3]);
     }
     tc::fence_proxy_async_smem();
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
     const uint32_t tmem = *tmem_slot;
-    const int m = tid & (kTcM - 1), q = tid >> 7;
-    const int g = warp & 3, cb = warp >> 2;
+    const uint32_t ring_s = tc::smem_u32(ring), b_s = tc::smem_u32(bsm);
+    const int g = warp & 3, h = warp >> 2;   // TMEM lane quarter, 16-channel half
     uint32_t phase = 0;
-    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        // im2col of pixel m, channels 8q..8q+7, all nine taps
-        {
-            const long long P = t * kTcM + m;
-            const bool in = P < total;
-            int n = 0, py = 0, px = 0;
-            if (in) {
-                n = (int)(P / HW);
-                const int rem = (int)(P - (long long)n * HW);
-                py = rem / Wd;
-                px = rem - py * Wd;
-            }
-            const float* xb = x + ((size_t)n * kTcC + 8 * q) * HW;
-            float v[9][8];
-#pragma unroll
-            for (int tap = 0; tap < 9; ++tap) {
-                const int yy = py + tap / 3 - 1, xx = px + tap % 3 - 1;
-                const bool ok = in && yy >= 0 && yy < H && xx >= 0 && xx < Wd;
-                const float* src = xb + (ok ? yy * Wd + xx : 0);
-#pragma unroll
-                for (int e = 0; e < 8; ++e) v[tap][e] = ok ? __ldg(src + (size_t)e * HW) : 0.f;
-            }
-#pragma unroll
-            for (int tap = 0; tap < 9; ++tap)
-                put_split_unit(a_hi + (tap >> 1) * kTcA, a_lo + (tap >> 1) * kTcA, sw128_off(m, (tap & 1) * 4 + q),
-                               v[tap]);
+    for (int u = blockIdx.x; u < units && !s_fail; u += gridDim.x) {
+        const int n = u / (strips * runs);
+        const int rest = u - n * strips * runs;
+        const int strip = rest / runs, run = rest - strip * runs;
+        const int x0 = strip * kTcM, ya = run * rows, yb = min(H, ya + rows);
+        const float* xn = x + (size_t)n * kTcC * HW;
+        float pre[kTcPer][8];
+        for (int r = 0; r < 3; ++r) {
+            fetch_row(xn, HW, H, Wd, ya - 1 + r, x0, pre);
+            put_row(ring + r * kTcRowBytes, pre);
         }
         tc::fence_proxy_async_smem();
         tc::fence_before();
         __syncthreads();
         tc::fence_after();
-        if (tid == 0) {
-            const uint32_t idesc = tc::idesc_f16(kTcM, kTcC, false);
-            const uint32_t ah = tc::smem_u32(a_hi), al = tc::smem_u32(a_lo);
-            const uint32_t bh = tc::smem_u32(b_hi), bl = tc::smem_u32(b_lo);
-            uint32_t acc = 0;
-            for (int j = 0; j < kTcChunks; ++j) {
-                const int steps = j + 1 < kTcChunks ? 4 : 2;
-                for (int k = 0; k < steps; ++k) {
-                    const uint32_t ao = j * kTcA + k * 32, bo = j * kTcB + k * 32;
-                    tc::mma_f16(tmem, tc::sdesc_sw128(ah + ao), tc::sdesc_sw128(bh + bo), idesc, acc);
-                    tc::mma_f16(tmem, tc::sdesc_sw128(al + ao), tc::sdesc_sw128(bh + bo), idesc, 1u);
-                    tc::mma_f16(tmem, tc::sdesc_sw128(ah + ao), tc::sdesc_sw128(bl + bo), idesc, 1u);
-                    acc = 1u;
+        for (int yy = ya; yy < yb; ++yy) {
+            const int s0 = (yy - ya) % 3;   // ring slot of row yy - 1; yy and yy + 1 follow
+            if (tid == 0) {
+                const uint32_t id64 = tc::idesc_f16(kTcM, 64, false), id32 = tc::idesc_f16(kTcM, 32, false);
+                uint32_t acc = 0;
+#pragma unroll 1
+                for (int tap = 0; tap < 9; ++tap) {
+                    const int slot = (s0 + tap / 3) % 3, dx = tap % 3;
+                    const uint32_t a = ring_s + slot * kTcRowBytes + dx * 128;
+                    const uint32_t b = b_s + (tap >> 1) * kTcBChunk + (tap & 1) * 64;
+#pragma unroll
+                    for (int ks = 0; ks < 2; ++ks) {
+                        tc::mma_f16(tmem, sdesc_view(a + ks * 32), sdesc_view(b + ks * 32), id64, acc);
+                        tc::mma_f16(tmem + 64, sdesc_view(a + 64 + ks * 32), sdesc_view(b + ks * 32), id32, acc);
+                        acc = 1u;
+                    }
+                }
+                tc::mma_commit(bar);
+            }
+            const bool more = yy + 1 < yb;
+            if (more) fetch_row(xn, HW, H, Wd, yy + 2, x0, pre);   // the next tile's new row
+            const bool ok = tc::mbar_wait(bar, phase, kTcWaitCycles, &s_fail);
+            phase ^= 1u;
+            if (!ok) {
+                atomicOr(err, HQS_DEVERR_TIMEOUT);
+                s_fail = 1;
+            }
+            __syncthreads();
+            if (s_fail) break;
+            tc::fence_after();
+            // epilogue: pixels x0 + 32 g + lane, channels 16 h..16 h + 15
+            float d0[16], d1[16], d2[16];
+            const uint32_t tl = tmem + ((uint32_t)(32 * g) << 16) + 16 * h;
+            tc::tmem_ld16(tl, d0);
+            tc::tmem_ld16(tl + 32, d1);
+            tc::tmem_ld16(tl + 64, d2);
+            const int xx = x0 + 32 * g + lane;
+            if (xx < Wd) {
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    const int co = 16 * h + e;
+                    const size_t idx = ((size_t)n * kTcC + co) * HW + (size_t)yy * Wd + xx;
+                    float v = (d0[e] + d1[e]) + d2[e];
+                    if (MODE != CONV_DGRAD_MASK) v += __ldg(bias + co);
+                    if (MODE == CONV_FWD_RELU) v = fmaxf(v, 0.f);
+                    if (MODE == CONV_DGRAD_MASK) v = mask[idx] > 0.f ? v : 0.f;
+                    y[idx] = v;
                 }
             }
-            tc::mma_commit(bar);
+            if (more) put_row(ring + s0 * kTcRowBytes, pre);   // row yy + 2 replaces row yy - 1
+            tc::fence_proxy_async_smem();
+            tc::fence_before();
+            __syncthreads();
+            tc::fence_after();
         }
-        const bool ok = tc::mbar_wait(bar, phase, kTcWaitCycles, &s_fail);
-        phase ^= 1u;
-        if (!ok) {
-            atomicOr(err, HQS_DEVERR_TIMEOUT);
-            s_fail = 1;
-        }
-        __syncthreads();
-        if (s_fail) break;
-        tc::fence_after();
-        // epilogue: TMEM lane quarter g = pixels 32 g + lane, channels 8 cb..8 cb + 7
-        float d[8];
-        tc::tmem_ld8(tmem + ((uint32_t)(32 * g) << 16) + 8 * cb, d);
-        const long long P = t * kTcM + 32 * g + lane;
-        if (P < total) {
-            const int n = (int)(P / HW);
-            const int rem = (int)(P - (long long)n * HW);
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const int co = 8 * cb + e;
-                const size_t idx = ((size_t)n * kTcC + co) * HW + rem;
-                float v = d[e];
-                if (MODE != CONV_DGRAD_MASK) v += __ldg(bias + co);
-                if (MODE == CONV_FWD_RELU) v = fmaxf(v, 0.f);
-                if (MODE == CONV_DGRAD_MASK) v = mask[idx] > 0.f ? v : 0.f;
-                y[idx] = v;
-            }
-        }
-        // the next tile rewrites A and D only after every thread is done with both
-        tc::fence_before();
-        __syncthreads();
     }
     tc::fence_before();
     __syncthreads();
     if (warp == 0) {
         tc::fence_after();
-        tc::tmem_dealloc(tmem, 32);
+        tc::tmem_dealloc(tmem, 128);
     }
 }
 
@@ -377,8 +421,8 @@ int conv_launch(const float* x, const float* W, const float* b, const float* mas
     return HQS_OK;
 }
 
-// the 32 -> 32 layers on the tensor cores: one 512-thread CTA per SM walking the
-// 128-pixel tiles
+// the 32 -> 32 layers on the tensor cores: units of (sample, 128-column strip,
+// run of output rows), the runs sized so that the units fill two CTAs per SM
 template <int MODE>
 int conv_tc_launch(const float* x, const float* W, const float* b, const float* mask, float* y, int N, int H,
                    int Wd, unsigned* err, cudaStream_t st) {
@@ -389,9 +433,15 @@ int conv_tc_launch(const float* x, const float* W, const float* b, const float* 
     if (!sms[dev]) HQS_CUDA_TRY(cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev));
     HQS_CUDA_TRY(cudaFuncSetAttribute(k_conv3x3_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)kTcSmem));
-    const long long tiles = ((long long)N * H * Wd + kTcM - 1) / kTcM;
-    const int grid = (int)std::min<long long>(tiles, sms[dev]);
-    k_conv3x3_tc<MODE><<<grid, kTcThreads, kTcSmem, st>>>(x, W, b, mask, y, N, H, Wd, err);
+    const int slots = 2 * sms[dev];
+    const int strips = ceil_div(Wd, kTcM);
+    const long long row_tiles = (long long)N * strips * H;
+    const int rows = (int)std::min<long long>(H, std::max<long long>(1, (row_tiles + slots - 1) / slots));
+    const int runs = ceil_div(H, rows);
+    const long long units = (long long)N * strips * runs;
+    if (units > INT_MAX) return HQS_ERR_UNSUPPORTED;
+    const int grid = (int)std::min<long long>(units, slots);
+    k_conv3x3_tc<MODE><<<grid, kTcThreads, kTcSmem, st>>>(x, W, b, mask, y, N, H, Wd, strips, rows, runs, err);
     HQS_CUDA_TRY(cudaGetLastError());
     return HQS_OK;
 }
