@@ -327,12 +327,16 @@ HQS_API int hqs_pgd_run(hqs_plan plan, const hqs_c64* y, hqs_c64* x, const float
  * at a time (its workspace is used).  hqs_batch_create allocates;
  * hqs_batch_run enqueues on `stream` the per-slice adjoints and the
  * persistent kernel, recorded once into a CUDA graph and replayed when
- * use_graph != 0 (re-recorded when y/x pointers, K, k0, cg_iters or c0
+ * use_graph != 0 (re-recorded when y/x pointers, K, k0, cg_iters, c0 or c1
  * change; mu, sigma may change freely); it synchronises `stream` first.
  * y[i]: (L_i, M_i) device; x[i]: (n_i, n_i) device, x_{k0} in, x_K out.
- * c1 != 0 (F-1 / Chebyshev metrics) returns HQS_ERR_UNSUPPORTED here (use
- * hqs_run).  hqs_batch_status synchronises and reports, per slice, the
- * relative CG residual of the last data-consistency step. */
+ * c0, c1: the metric P = c0 I + c1 A^H A of Sec. 3.4, shared by every slice
+ * (as in hqs_run: each step solves ((1 + c1 mu_k) A^H A + c0 mu_k I) u =
+ * A^H y + mu_k (c0 x_k + c1 A^H A x_k)); for the F-1 and Chebyshev metrics
+ * take alpha from the slice with the largest ||A^H A|| (hqs_power_iteration),
+ * which keeps P positive definite for every slice.  hqs_batch_status
+ * synchronises and reports, per slice, the relative CG residual of the last
+ * data-consistency step. */
 HQS_API int hqs_batch_create(hqs_batch* out, hqs_plan* plans, int n, int max_outer);
 HQS_API void hqs_batch_destroy(hqs_batch batch);
 HQS_API int hqs_batch_run(hqs_batch batch, const hqs_c64* const* y, hqs_c64* const* x,

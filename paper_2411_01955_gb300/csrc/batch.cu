@@ -1,9 +1,12 @@
 // Batched annealed PnP-HQS over slices of uneven size (a9): one persistent
 // cooperative launch runs, for every slice s and outer iteration k
-// (Sec. 3.3, P = Id in the metric of Sec. 3.4),
-//   u = x_k;  rhs = A^H y + mu_k c0 x_k;  cg_iters DC-preconditioned CG
-//   iterations on (A^H A + c0 mu_k I) u = rhs from u;  x_{k+1} = G_{s_k} u
+// (Sec. 3.3, the prox in the metric P = c0 I + c1 A^H A of Sec. 3.4),
+//   u = x_k;  rhs = A^H y + mu_k (c0 x_k + c1 A^H A x_k);  cg_iters DC-
+//   preconditioned CG iterations on ((1 + c1 mu_k) A^H A + c0 mu_k I) u = rhs
+//   from u;  x_{k+1} = G_{s_k} u
 // with the Gaussian-smoothing denoiser of std s_k = kappa sigma_k / sigma_0.
+// The CG start u = x_k needs A^H A x_k anyway (for H u), so the c1 term of the
+// right-hand side costs no extra operator apply.
 // The work items of all slices (rows, columns, preconditioner row blocks,
 // denoiser tiles) are dealt to the CTAs together in every phase, so slices of
 // 256^2, 320^2 and 384^2 with 8-20 coils share the GPU without per-slice
@@ -50,7 +53,7 @@ struct BatchArgs {
     int ns;
     const int* off;      // [BL_N][ns + 1] prefix item counts
     int K, k0, cg_iters;
-    float c0;
+    float c0, c1;
     const float* mu;     // [K]
     const float* taps;   // [K][2 MAXR + 1], normalised
     const int* radius;   // [K], -1: identity
@@ -254,6 +257,13 @@ __global__ void __launch_bounds__(HQS_BATCH_BD, 2) k_hqs_batch(BatchArgs B) {
     do {                                            \
         if (!grid_barrier(B.bar, B.err)) return;    \
     } while (0)
+    // the chunk epilogue reads what the row-adjoint pass wrote: its barrier is needed
+    // only when some slice has several coil chunks
+    const bool has_epi = B.off[BL_EPI * (ns + 1) + ns] > 0;
+#define EPI_BARRIER()                   \
+    do {                                \
+        if (has_epi) BB_BARRIER();      \
+    } while (0)
 #define FOR_ITEMS(list, ...)                                                               \
     {                                                                                      \
         const int* off_ = B.off + (list) * (ns + 1);                                       \
@@ -273,7 +283,10 @@ __global__ void __launch_bounds__(HQS_BATCH_BD, 2) k_hqs_batch(BatchArgs B) {
     (void)sl_cache;
     for (int k = B.k0; k < B.K; ++k) {
         const float muk = B.mu[k];
-        const float bcoef = B.c0 * muk;
+        const float acoef = 1.0f + B.c1 * muk, bcoef = B.c0 * muk;
+        // with c1 != 0 the first operator pass keeps v = A^H A u (epilogue mode 0);
+        // the residual phase forms H u = a v + b u and the rhs term mu c1 v
+        const int mode0 = B.c1 != 0.f ? 0 : 1;
         // PREP: u = x, rhs = A^H y + mu c0 x
         FOR_ITEMS(BL_IMG, {
             const int n = S.A.n;
@@ -302,9 +315,10 @@ __global__ void __launch_bounds__(HQS_BATCH_BD, 2) k_hqs_batch(BatchArgs B) {
         FOR_ITEMS(BL_ROWS, {
             const int n = S.A.n, ch = it_ / n, iy = it_ - ch * n;
             STAGE_TW2(S.A);
-            HQS_BATCH_DISPATCH(n, (toep_rows_adj_item<N2, HQS_BATCH_BD>(S.A, iy, ch, S.q, S.u, 1.f, bcoef, 1, s, twT)));
+            HQS_BATCH_DISPATCH(n, (toep_rows_adj_item<N2, HQS_BATCH_BD>(S.A, iy, ch, S.q, S.u, acoef, bcoef, mode0, s,
+                                                                        twT)));
         });
-        BB_BARRIER();
+        EPI_BARRIER();
         FOR_ITEMS(BL_EPI, {   // several coil chunks: fixed-order chunk sum + epilogue
             const int n = S.A.n, cnt = n * n;
             for (int ix = threadIdx.x; ix < n; ix += blockDim.x) {
@@ -312,19 +326,30 @@ __global__ void __launch_bounds__(HQS_BATCH_BD, 2) k_hqs_batch(BatchArgs B) {
                 float2 v = make_float2(0.f, 0.f);
                 for (int c = 0; c < S.A.nchunk; ++c) v = cadd(v, __ldcg(S.A.chunk + (size_t)c * cnt + e));
                 double dummy = 0.0;
-                S.q[e] = toep_epilogue(v, e, S.u, 1.f, bcoef, 1, dummy);
+                S.q[e] = toep_epilogue(v, e, S.u, acoef, bcoef, mode0, dummy);
             }
         });
         BB_BARRIER();
-        // r = rhs - q; ||r||^2, ||rhs||^2 per slice
+        // r = rhs - q; ||r||^2, ||rhs||^2 per slice (c1 != 0: q holds v = A^H A u;
+        // rhs += mu c1 v and q = a v + b u, in the epilogue's arithmetic)
         CLEAR_ACC();
         FOR_ITEMS(BL_IMG, {
             const int n = S.A.n;
             double a1 = 0.0, a2 = 0.0;
             for (int ix = threadIdx.x; ix < n; ix += blockDim.x) {
                 const size_t e = (size_t)it_ * n + ix;
-                const float2 bv = __ldcg(S.rhs + e);
-                const float2 v = csub(bv, __ldcg(S.q + e));
+                float2 bv = __ldcg(S.rhs + e);
+                float2 qv = __ldcg(S.q + e);
+                if (mode0 == 0) {
+                    const float mc1 = muk * B.c1;
+                    bv.x = fmaf(mc1, qv.x, bv.x);
+                    bv.y = fmaf(mc1, qv.y, bv.y);
+                    S.rhs[e] = bv;
+                    double dummy = 0.0;
+                    qv = toep_epilogue(qv, e, S.u, acoef, bcoef, 1, dummy);
+                    S.q[e] = qv;
+                }
+                const float2 v = csub(bv, qv);
                 S.r[e] = v;
                 a1 += (double)v.x * v.x + (double)v.y * v.y;
                 a2 += (double)bv.x * bv.x + (double)bv.y * bv.y;
@@ -351,7 +376,7 @@ __global__ void __launch_bounds__(HQS_BATCH_BD, 2) k_hqs_batch(BatchArgs B) {
         FOR_ITEMS(BL_PC, {
             STAGE_TWN(S, si);
             double v = 0.0;
-            HQS_BATCH_DISPATCH(S.A.n, (v = pc_cols<N>(S, it_ * batch_pq<N>(), 1.f, bcoef, s, twN)));
+            HQS_BATCH_DISPATCH(S.A.n, (v = pc_cols<N>(S, it_ * batch_pq<N>(), acoef, bcoef, s, twN)));
             v = cta_sum(v, red);
             if (threadIdx.x == 0) acc[0][si] += v;
         });
@@ -390,11 +415,12 @@ __global__ void __launch_bounds__(HQS_BATCH_BD, 2) k_hqs_batch(BatchArgs B) {
                 const int n = S.A.n, ch = it_ / n, iy = it_ - ch * n;
                 double v = 0.0;
                 STAGE_TW2(S.A);
-                HQS_BATCH_DISPATCH(n, (v = toep_rows_adj_item<N2, HQS_BATCH_BD>(S.A, iy, ch, S.q, S.p, 1.f, bcoef, 1, s, twT)));
+                HQS_BATCH_DISPATCH(n, (v = toep_rows_adj_item<N2, HQS_BATCH_BD>(S.A, iy, ch, S.q, S.p, acoef, bcoef, 1, s,
+                                                                                 twT)));
                 v = cta_sum(v, red);
                 if (threadIdx.x == 0) acc[0][si] += v;
             });
-            BB_BARRIER();
+            EPI_BARRIER();
             FOR_ITEMS(BL_EPI, {
                 const int n = S.A.n, cnt = n * n;
                 double v = 0.0;
@@ -402,7 +428,7 @@ __global__ void __launch_bounds__(HQS_BATCH_BD, 2) k_hqs_batch(BatchArgs B) {
                     const size_t e = (size_t)it_ * n + ix;
                     float2 w = make_float2(0.f, 0.f);
                     for (int c = 0; c < S.A.nchunk; ++c) w = cadd(w, __ldcg(S.A.chunk + (size_t)c * cnt + e));
-                    S.q[e] = toep_epilogue(w, e, S.p, 1.f, bcoef, 1, v);
+                    S.q[e] = toep_epilogue(w, e, S.p, acoef, bcoef, 1, v);
                 }
                 v = cta_sum(v, red);
                 if (threadIdx.x == 0) acc[0][si] += v;
@@ -434,7 +460,7 @@ __global__ void __launch_bounds__(HQS_BATCH_BD, 2) k_hqs_batch(BatchArgs B) {
             FOR_ITEMS(BL_PC, {
                 STAGE_TWN(S, si);
                 double v = 0.0;
-                HQS_BATCH_DISPATCH(S.A.n, (v = pc_cols<N>(S, it_ * batch_pq<N>(), 1.f, bcoef, s, twN)));
+                HQS_BATCH_DISPATCH(S.A.n, (v = pc_cols<N>(S, it_ * batch_pq<N>(), acoef, bcoef, s, twN)));
                 v = cta_sum(v, red);
                 if (threadIdx.x == 0) acc[0][si] += v;
             });
@@ -474,6 +500,7 @@ __global__ void __launch_bounds__(HQS_BATCH_BD, 2) k_hqs_batch(BatchArgs B) {
         BB_BARRIER();
     }
 #undef BB_BARRIER
+#undef EPI_BARRIER
 #undef FOR_ITEMS
 #undef STAGE_TWN
 #undef STAGE_TW2
@@ -539,6 +566,17 @@ __global__ void __launch_bounds__(HQS_BATCH_BD, 2) k_pcg_batch(DcBatchArgs B) {
     do {                                                                                     \
         if (!grid_barrier(B.bar, B.err)) return;                                             \
         if (B.trace && bid == 0 && threadIdx.x == 0 && ntr < B.trace_max) B.trace[ntr++] = global_ns(); \
+    } while (0)
+    // the chunk epilogue reads what the row-adjoint pass wrote: its barrier is needed
+    // only when some slice has several coil chunks (the trace keeps the stamp)
+    const bool has_epi = B.off[BL_EPI * (ns + 1) + ns] > 0;
+#define EPI_BARRIER()                                                                        \
+    do {                                                                                     \
+        if (has_epi) {                                                                       \
+            BB_BARRIER();                                                                    \
+        } else if (B.trace && bid == 0 && threadIdx.x == 0 && ntr < B.trace_max) {           \
+            B.trace[ntr++] = global_ns();                                                    \
+        }                                                                                    \
     } while (0)
     // Each phase deals its items in the opposite slice order to the phase before, so
     // that it starts on the slices whose data the previous phase touched last (still
@@ -670,7 +708,7 @@ __global__ void __launch_bounds__(HQS_BATCH_BD, 2) k_pcg_batch(DcBatchArgs B) {
             v = cta_sum(v, red);
             if (threadIdx.x == 0) acc[0][si] += v;
         });
-        BB_BARRIER();
+        EPI_BARRIER();
         FOR_ITEMS(BL_EPI, {   // several coil chunks: fixed-order chunk sum + epilogue
             const int n = S.A.n, cnt = n * n;
             double v = 0.0;
@@ -764,6 +802,7 @@ __global__ void __launch_bounds__(HQS_BATCH_BD, 2) k_pcg_batch(DcBatchArgs B) {
         B.trace[B.trace_max] = ntr;
     }
 #undef BB_BARRIER
+#undef EPI_BARRIER
 #undef FOR_ITEMS
 #undef STAGE_TWN
 #undef CLEAR_ACC
@@ -796,7 +835,7 @@ struct hqs_batch_s {
     cudaGraphExec_t exec = nullptr;
     std::vector<const void*> key;  // y / x pointers the graph was recorded with
     int key_K = -1, key_k0 = -1, key_cg = -1;
-    float key_c0 = 0.f;
+    float key_c0 = 0.f, key_c1 = 0.f;
     std::vector<float2*> chunks;   // per-slice coil-chunk partial sums
     // batched data-consistency solve: its own slice table (u = x, rhs = the
     // caller's), rebuilt when the caller's pointers change
@@ -933,7 +972,7 @@ extern "C" int hqs_batch_create(hqs_batch* out, hqs_plan* plans, int n, int max_
 
 // Everything one batch step enqueues (recorded into the graph).
 static int batch_enqueue(hqs_batch_s* b, const hqs_c64* const* y, hqs_c64* const* x, int K, int k0, int cg_iters,
-                         float c0, cudaStream_t st) {
+                         float c0, float c1, cudaStream_t st) {
     const int n = b->ns;
     for (int i = 0; i < n; ++i)
         HQS_TRY_RC(launch_adj(b->plans[i], reinterpret_cast<const float2*>(y[i]), b->plans[i]->img_b0, st));
@@ -951,6 +990,7 @@ static int batch_enqueue(hqs_batch_s* b, const hqs_c64* const* y, hqs_c64* const
     A.k0 = k0;
     A.cg_iters = cg_iters;
     A.c0 = c0;
+    A.c1 = c1;
     A.mu = b->d_mu;
     A.taps = b->d_taps;
     A.radius = b->d_radius;
@@ -968,9 +1008,8 @@ extern "C" int hqs_batch_run(hqs_batch b, const hqs_c64* const* y, hqs_c64* cons
                              const float* sigma, int K, int k0, int cg_iters, float c0, float c1,
                              const hqs_gauss_params* gauss, int use_graph, void* stream) {
     if (!b || !y || !x || !mu || !sigma || K <= 0 || K > b->K || k0 < 0 || k0 >= K || cg_iters < 1 ||
-        cg_iters > HQS_MAX_ITERS || !(c0 > 0.f))
+        cg_iters > HQS_MAX_ITERS || !(c0 > 0.f) || !(c1 == c1))
         return HQS_ERR_INVALID_ARG;
-    if (c1 != 0.f) return HQS_ERR_UNSUPPORTED;
     for (int i = 0; i < b->ns; ++i)
         if (!x[i] || (!y[i] && b->plans[i]->M > 0)) return HQS_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
@@ -1006,19 +1045,20 @@ extern "C" int hqs_batch_run(hqs_batch b, const hqs_c64* const* y, hqs_c64* cons
         for (int i = -r; i <= r; ++i) sum += gg[i + r] = std::exp(-(double)i * i / (2.0 * sd * sd));
         for (int i = 0; i <= 2 * r; ++i) g[i] = (float)(gg[i] / sum);
     }
-    if (!use_graph) return batch_enqueue(b, y, x, K, k0, cg_iters, c0, st);
+    if (!use_graph) return batch_enqueue(b, y, x, K, k0, cg_iters, c0, c1, st);
     std::vector<const void*> key;
     for (int i = 0; i < b->ns; ++i) {
         key.push_back(y[i]);
         key.push_back(x[i]);
     }
-    if (!b->exec || key != b->key || K != b->key_K || k0 != b->key_k0 || cg_iters != b->key_cg || c0 != b->key_c0) {
+    if (!b->exec || key != b->key || K != b->key_K || k0 != b->key_k0 || cg_iters != b->key_cg || c0 != b->key_c0 ||
+        c1 != b->key_c1) {
         if (b->exec) cudaGraphExecDestroy(b->exec);
         if (b->graph) cudaGraphDestroy(b->graph);
         b->exec = nullptr;
         b->graph = nullptr;
         HQS_CUDA_TRY(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
-        const int rc = batch_enqueue(b, y, x, K, k0, cg_iters, c0, b->cap);
+        const int rc = batch_enqueue(b, y, x, K, k0, cg_iters, c0, c1, b->cap);
         cudaGraph_t g = nullptr;
         const cudaError_t e = cudaStreamEndCapture(b->cap, &g);
         if (rc != HQS_OK) {
@@ -1033,6 +1073,7 @@ extern "C" int hqs_batch_run(hqs_batch b, const hqs_c64* const* y, hqs_c64* cons
         b->key_k0 = k0;
         b->key_cg = cg_iters;
         b->key_c0 = c0;
+        b->key_c1 = c1;
     }
     HQS_CUDA_TRY(cudaGraphLaunch(b->exec, st));
     return HQS_OK;

@@ -86,14 +86,67 @@ def test_batched_hqs_matches_oracle_per_slice_and_graph_replay():
         assert rel(d, g) <= tol
 
 
-def test_batched_hqs_rejects_unsupported_metric():
-    slices = build(slice_cases()[:1])
+@pytest.mark.parametrize("metric", ["f1", "chebyshev"])
+def test_batched_hqs_pmetric_matches_oracle(metric):
+    """The batched HQS in the F-1 and Chebyshev metrics of Sec. 3.4 (P = c0 I +
+    c1 A^H A, shared by the slices, alpha = 1 / the largest ||A^H A|| of the
+    batch): every slice matches the oracle's hqs(..., c0, c1), whose prox solves
+    ((1 + c1 mu) A^H A + c0 mu I) u = A^H y + mu (c0 x + c1 A^H A x) with a
+    fixed number of DC-preconditioned CG iterations.  Three slices: 64^2 radial,
+    128^2 with 20 coils (two coil chunks, the chunk epilogue) and 64^2 spiral.
+    Bound as in the P = Id test: 4x the oracle's own deviation under a 2^-24
+    relative perturbation of A^H y (at least 1e-5)."""
+    from oracle import solvers
+    slices = build(slice_cases()[:3])
+    K, cg = 3, 3
+    mu = np.array([0.1, 0.03, 0.01], dtype=np.float32)
+    sigma = mu.copy()
+    ops = []
+    lmax = 0.0
+    for case, _, y in slices:
+        n = case["n"]
+        c = toeplitz.kernel(case["traj"], n, n)
+        Kh, lam = toeplitz.khat(c), toeplitz.chan_symbol(c, n, n)
+        AHA = lambda v, S=case["smaps"], Kh=Kh: toeplitz.normal(v, S, Kh)
+        b0 = nufft.adjoint(y, case["smaps"], case["traj"], case["W"], case["sigma"])
+        ops.append((AHA, lam, b0))
+        lmax = max(lmax, solvers.power_iteration(AHA, (n, n), iters=200, rtol=1e-10))
+    alpha = 1.0 / lmax
+    c0, c1 = {"f1": (2.0, -alpha), "chebyshev": (4.0, -10.0 * alpha / 3.0)}[metric]
+    c1 = float(np.float32(c1))     # the value the library receives
     batch = hq().Batch([p for _, p, _ in slices], max_outer=4)
     ys = [to_dev(y) for _, _, y in slices]
-    xs = [torch.zeros((64, 64), dtype=torch.complex64, device="cuda")]
-    with pytest.raises(hq().HqsError) as ei:
-        batch.run(ys, xs, [0.1], [0.1], c1=-0.5)
-    assert ei.value.status == hq().HQS_ERR_UNSUPPORTED
+    xs = [torch.zeros((c["n"], c["n"]), dtype=torch.complex64, device="cuda") for c, _, _ in slices]
+    batch.run(ys, xs, mu, sigma, cg_iters=cg, c0=c0, c1=c1, use_graph=False)
+    res = batch.status()
+    rng = np.random.default_rng(1)
+    mu64, sg64 = mu.astype(np.float64), sigma.astype(np.float64)
+    tols, direct = [], []
+    for (case, _, _), (AHA, lam, b0), x, r in zip(slices, ops, xs, res):
+        n = case["n"]
+        run = lambda b: ohqs.hqs(AHA, b, np.zeros((n, n)), mu64, sg64, K, cg_iters=cg, c0=c0, c1=c1, lam=lam)[0]
+        want = run(b0)
+        pert = run(b0 * (1 + 2.0 ** -24 * rng.normal(size=b0.shape)))
+        tol = max(1e-5, 4 * rel(pert, want))
+        got = to_host(x)
+        assert rel(got, want) <= tol, (metric, n, case["L"], rel(got, want), tol)
+        assert 0.0 < r < 1.0
+        tols.append(tol)
+        direct.append(got)
+    # the graph records c0 and c1 with the rest: after a replay in the Id metric,
+    # the metric's call is re-recorded and agrees with its direct launch
+    for x in xs:
+        x.zero_()
+    batch.run(ys, xs, mu, sigma, cg_iters=cg, use_graph=True)
+    id_run = [to_host(x) for x in xs]
+    for x in xs:
+        x.zero_()
+    batch.run(ys, xs, mu, sigma, cg_iters=cg, c0=c0, c1=c1, use_graph=True)
+    torch.cuda.synchronize()
+    for x, g, gi, tol in zip(xs, direct, id_run, tols):
+        d = to_host(x)
+        assert rel(d, g) <= tol
+        assert rel(gi, g) > 10 * tol      # the Id metric gives a different iterate
 
 
 def test_batched_dc_solve_matches_oracle_and_per_slice_solves():
