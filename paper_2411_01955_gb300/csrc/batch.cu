@@ -232,7 +232,7 @@ HQS_DEV void blur_tile(const BatchSlice& S, int tile, const float* g, int r, flo
 constexpr size_t kBatchSmemF2 = (size_t)768 * kLines + 384 + 768;
 
 __global__ void __launch_bounds__(HQS_BATCH_BD, 2) k_hqs_batch(BatchArgs B) {
-    extern __shared__ float2 s[];
+    extern __shared__ __align__(16) float2 s[];
     __shared__ double red[33];
     __shared__ double acc[2][HQS_BATCH_MAX];
     __shared__ double tot[2][HQS_BATCH_MAX];
@@ -533,7 +533,7 @@ struct DcBatchArgs {
 };
 
 __global__ void __launch_bounds__(HQS_BATCH_BD, 2) k_pcg_batch(DcBatchArgs B) {
-    extern __shared__ float2 s[];
+    extern __shared__ __align__(16) float2 s[];
     __shared__ double red[33];
     __shared__ double acc[2][HQS_BATCH_MAX];
     __shared__ double tot[2][HQS_BATCH_MAX];

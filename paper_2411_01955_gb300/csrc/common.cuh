@@ -24,6 +24,14 @@ HQS_DEV float2 cfma(float2 a, float2 b, float2 acc) {   // acc + a*b
     acc.y = fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y));
     return acc;
 }
+// 16-byte asynchronous copy global -> shared through L2 (cp.async.cg; both
+// addresses 16-byte aligned), and the wait for every copy this thread issued.
+HQS_DEV void cp_async16(void* smem_dst, const void* gmem_src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+HQS_DEV void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // multiply by -i (forward) or +i (inverse)
 template <bool INV> HQS_DEV float2 mul_mi(float2 a) {
     return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);

@@ -481,6 +481,9 @@ HQS_DEV void fft_mid_stage(float2* s, int t, bool act, const float2* __restrict_
 #pragma unroll
         for (int r = 0; r < R; ++r) v[b * R + r] = s[(i + r * NB) * st];
     }
+    // a factor the caller fetched with cp.async before the transform is complete
+    // after this thread's wait and the barrier (a no-op when nothing is pending)
+    cp_async_wait_all();
     __syncthreads();
     if (act) {
 #pragma unroll

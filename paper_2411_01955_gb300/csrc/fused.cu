@@ -175,7 +175,7 @@ template <int N2, int N>
 __global__ void __launch_bounds__(FftSize<N2>::TPL * kLines,
                                   (512 / (FftSize<N2>::TPL * kLines)) > 1 ? 512 / (FftSize<N2>::TPL * kLines) : 1)
     k_pcg_persistent(FusedArgs F) {
-    extern __shared__ float2 s[];
+    extern __shared__ __align__(16) float2 s[];
     __shared__ double red[33];
     constexpr int BD = FftSize<N2>::TPL * kLines;   // == blockDim.x
     const ToepArgs& A = F.A;

@@ -67,26 +67,31 @@ HQS_DEV void toep_cols_item(const ToepArgs& A, int kx, int ch, float2* s, const 
     float2* col = A.T + (int64_t)kx * L + l0;
     const int64_t rs = (int64_t)N2 * L;
     const float* kh = A.khat + (int64_t)kx * N2;   // Khat stored transposed: column kx contiguous
+    // the column of Khat (N2 floats) goes to the image-row region asynchronously while
+    // the forward stages run; the pair's middle stage waits for it before its barrier
+    float* khs = reinterpret_cast<float*>(s + N2 * kLines);
+    for (int c = threadIdx.x; c < N2 / 4; c += blockDim.x) cp_async16(khs + 4 * c, kh + 4 * c);
     __syncthreads();
     // column straight into the first stage (zero-padded upper half), * Khat between
     // the last forward and the first inverse stage (on registers), IFFT, first n rows
     // straight back to T
     block_fft_pair<N2, true, true>(
         s, lines, tw, [&](int line, int p, bool) { return __ldcg(col + line + p * rs); },
-        [&](int, int p, float2 v) { return cscale(v, __ldg(kh + p)); },
+        [&](int, int p, float2 v) { return cscale(v, khs[p]); },
         [&](int line, int p, float2 v) { col[line + p * rs] = v; });
     __syncthreads();
 }
 
 // CG epilogue on one pixel: mode 0 returns v = A^H A p; mode 1 returns
 // q = a v + b p and adds Re<p, q> to part.
+HQS_DEV float2 toep_epilogue_pv(float2 v, float2 pv, float a, float b, double& part) {
+    v = make_float2(fmaf(a, v.x, b * pv.x), fmaf(a, v.y, b * pv.y));
+    part += (double)pv.x * v.x + (double)pv.y * v.y;
+    return v;
+}
 HQS_DEV float2 toep_epilogue(float2 v, int64_t e, const float2* __restrict__ pvec, float a, float b,
                              int mode, double& part) {
-    if (mode == 1) {
-        const float2 pv = __ldcg(pvec + e);
-        v = make_float2(fmaf(a, v.x, b * pv.x), fmaf(a, v.y, b * pv.y));
-        part += (double)pv.x * v.x + (double)pv.y * v.y;
-    }
+    if (mode == 1) v = toep_epilogue_pv(v, __ldcg(pvec + e), a, b, part);
     return v;
 }
 
@@ -102,21 +107,49 @@ HQS_DEV double toep_rows_adj_item(const ToepArgs& A, int iy, int ch, float2* __r
     const int l0 = ch * A.LC;
     const int lines = min(A.LC, L - l0);
     const float2* src = A.T + (int64_t)iy * N2 * L + l0;
+    const float2* sm = A.smaps + (int64_t)iy * n * L + l0;
+    // A full chunk of 16 coils (every thread of the CTA owns a line position): the
+    // row's maps go with cp.async to the upper half of the lines buffer once the
+    // last stage has read it (that stage writes the lower half only), so their
+    // latency overlaps the stage; with one chunk and mode 1 the row of pvec (when
+    // 16-byte aligned) goes to the image-row region at the start.  Callers declare
+    // the dynamic shared memory 16-byte aligned.
+    const bool fast = lines == kLines && (int)blockDim.x == kLines * FftSize<N2>::TPL;
+    const bool pre_p = mode == 1 && A.nchunk == 1 && ((uintptr_t)pvec & 15u) == 0;
+    float2* msm = s + (int64_t)n * kLines;   // upper half: [n][kLines]
+    float2* prow = s + N2 * kLines;          // image-row region: [n]
+    if (pre_p)
+        for (int c = threadIdx.x; c < n / 2; c += blockDim.x) cp_async16(prow + 2 * c, pvec + (int64_t)iy * n + 2 * c);
+    bool issued = false;
     __syncthreads();
     // row straight from T into the first stage; only the first n columns are kept
     block_fft_io<N2, true, false, true>(
-        s, lines, tw, [&](int line, int p, bool) { return __ldcg(src + (int64_t)p * L + line); }, NoIO{}, NoIO{});
-    const float2* sm = A.smaps + (int64_t)iy * n * L + l0;
+        s, lines, tw, [&](int line, int p, bool) { return __ldcg(src + (int64_t)p * L + line); },
+        [&](int, int, float2 v) {
+            if (fast && !issued) {
+                issued = true;
+                for (int e = threadIdx.x; e < n * (kLines / 2); e += blockDim.x) {
+                    const int ix = e / (kLines / 2), h = e - ix * (kLines / 2);
+                    cp_async16(msm + ix * kLines + 2 * h, sm + (int64_t)ix * L + 2 * h);
+                }
+            }
+            return v;
+        },
+        NoIO{});
+    if (fast || pre_p) {
+        cp_async_wait_all();
+        __syncthreads();
+    }
     double part = 0.0;
     for (int ix = threadIdx.x; ix < n; ix += blockDim.x) {
         float2 acc = make_float2(0.f, 0.f);
         const float2* smx = sm + (int64_t)ix * L;
-        if (lines == kLines) {
+        if (fast) {
             // a full chunk of 16 coils is 128 contiguous, 16-byte aligned bytes
-            const float4* s4 = reinterpret_cast<const float4*>(smx);
+            const float4* s4 = reinterpret_cast<const float4*>(msm + ix * kLines);
             float4 sv4[kLines / 2];
 #pragma unroll
-            for (int h = 0; h < kLines / 2; ++h) sv4[h] = __ldg(s4 + h);
+            for (int h = 0; h < kLines / 2; ++h) sv4[h] = s4[h];
 #pragma unroll
             for (int h = 0; h < kLines / 2; ++h) {
                 const float2 g0 = s[ix * kLines + 2 * h], g1 = s[ix * kLines + 2 * h + 1];
@@ -133,7 +166,7 @@ HQS_DEV double toep_rows_adj_item(const ToepArgs& A, int iy, int ch, float2* __r
         }
         const int64_t e = (int64_t)iy * n + ix;
         if (A.nchunk == 1)
-            out[e] = toep_epilogue(acc, e, pvec, a, b, mode, part);
+            out[e] = pre_p ? toep_epilogue_pv(acc, prow[ix], a, b, part) : toep_epilogue(acc, e, pvec, a, b, mode, part);
         else
             A.chunk[(int64_t)ch * n * n + e] = acc;
     }

@@ -25,7 +25,7 @@ template <int N2>
 __global__ void k_toep_rows_fwd(ToepArgs A, const float2* __restrict__ src, float2* __restrict__ pvec,
                                 int fuse, const CgScalars* __restrict__ cg) {
     if (cg && cg->done) return;
-    extern __shared__ float2 s[];
+    extern __shared__ __align__(16) float2 s[];
     const float beta = (fuse && cg) ? (float)cg->beta : 0.f;
     toep_rows_fwd_item<N2>(A, blockIdx.x, blockIdx.y, src, pvec, beta, fuse != 0, s);
 }
@@ -33,7 +33,7 @@ __global__ void k_toep_rows_fwd(ToepArgs A, const float2* __restrict__ src, floa
 template <int N2>
 __global__ void k_toep_cols(ToepArgs A, const CgScalars* __restrict__ cg) {
     if (cg && cg->done) return;
-    extern __shared__ float2 s[];
+    extern __shared__ __align__(16) float2 s[];
     toep_cols_item<N2>(A, blockIdx.x, blockIdx.y, s);
 }
 
@@ -42,7 +42,7 @@ __global__ void k_toep_rows_adj(ToepArgs A, float2* __restrict__ out, const floa
                                 float a, float b, int mode, double* __restrict__ part,
                                 const CgScalars* __restrict__ cg) {
     if (cg && cg->done) return;
-    extern __shared__ float2 s[];
+    extern __shared__ __align__(16) float2 s[];
     __shared__ double red[32];
     const double v = toep_rows_adj_item<N2>(A, blockIdx.x, blockIdx.y, out, pvec, a, b, mode, s);
     if (part && A.nchunk == 1) {
