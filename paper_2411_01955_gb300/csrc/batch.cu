@@ -88,8 +88,10 @@ HQS_DEV void put_slice_partials(double* part, int ns, const double* acc) {
 
 // ---- per-size item bodies (BD = HQS_BATCH_BD)
 // z rows per item in the p-update phase: as many n-point lines as the CTA holds
+// (up to 2 kLines: 32 lines of 320 points fill the 256 threads, so the 16 slices'
+// items of this phase fit in one round of the grid)
 template <int N> constexpr int batch_zq() {
-    return (HQS_BATCH_BD / FftSize<N>::TPL) < kLines ? HQS_BATCH_BD / FftSize<N>::TPL : kLines;
+    return (HQS_BATCH_BD / FftSize<N>::TPL) < 2 * kLines ? HQS_BATCH_BD / FftSize<N>::TPL : 2 * kLines;
 }
 
 // rows [r0, r0 + lines): z = IFFT_N(pc spectrum rows) / N^2, p = z + beta p
@@ -99,15 +101,15 @@ HQS_DEV void z_and_p_rows(const BatchSlice& S, int r0, float beta, bool first, f
     const int lines = min(batch_zq<N>(), n - r0);
     for (int e = threadIdx.x; e < lines * N; e += blockDim.x) {
         const int q = e / N, pos = e - q * N;
-        s[pos * kLines + q] = __ldcg(S.pcb + (size_t)(r0 + q) * N + pos);
+        s[line_elem<N>(pos, q)] = __ldcg(S.pcb + (size_t)(r0 + q) * N + pos);
     }
     __syncthreads();
-    block_fft<N, true>(s, lines, twN);
+    block_fft<N, true, false, false, true>(s, lines, twN);
     const float sc = 1.0f / ((float)N * (float)N);
     for (int e2 = threadIdx.x; e2 < lines * n; e2 += blockDim.x) {
         const int q = e2 / n, ix = e2 - q * n;
         const size_t e = (size_t)(r0 + q) * n + ix;
-        float2 v = cscale(s[ix * kLines + q], sc);
+        float2 v = cscale(s[line_elem<N>(ix, q)], sc);
         if (!first && beta != 0.f) {
             const float2 pv = __ldcg(S.p + e);
             v.x = fmaf(beta, pv.x, v.x);
@@ -118,9 +120,9 @@ HQS_DEV void z_and_p_rows(const BatchSlice& S, int r0, float beta, bool first, f
     __syncthreads();
 }
 
-// preconditioner lines per item: as many n-point lines as the CTA holds (<= 16)
+// preconditioner lines per item: as many n-point lines as the CTA holds (<= 2 kLines)
 template <int N> constexpr int batch_pq() {
-    return (HQS_BATCH_BD / FftSize<N>::TPL) < kLines ? HQS_BATCH_BD / FftSize<N>::TPL : kLines;
+    return (HQS_BATCH_BD / FftSize<N>::TPL) < 2 * kLines ? HQS_BATCH_BD / FftSize<N>::TPL : 2 * kLines;
 }
 
 template <int N>
@@ -142,13 +144,13 @@ HQS_DEV double pc_rows(const BatchSlice& S, int r0, float alpha, bool update, fl
             S.r[idx] = rv;
         }
         rr += (double)rv.x * rv.x + (double)rv.y * rv.y;
-        s[ix * kLines + q_] = rv;
+        s[line_elem<N>(ix, q_)] = rv;
     }
     __syncthreads();
-    block_fft<N, false>(s, lines, twN);
+    block_fft<N, false, false, false, true>(s, lines, twN);
     for (int e = threadIdx.x; e < lines * N; e += blockDim.x) {
         const int q_ = e / N, pos = e - q_ * N;
-        S.pcb[(size_t)(r0 + q_) * N + pos] = s[pos * kLines + q_];
+        S.pcb[(size_t)(r0 + q_) * N + pos] = s[line_elem<N>(pos, q_)];
     }
     __syncthreads();
     return rr;
@@ -162,7 +164,7 @@ HQS_DEV double pc_cols(const BatchSlice& S, int c0, float a, float b, float2* s,
     double acc = 0.0;
     float2* col = S.pcb + c0;
     const float* lcol = S.lam + c0;
-    block_fft_pair<N, false, false>(
+    block_fft_pair<N, false, false, true>(
         s, lines, twN, [&](int line, int pos, bool) { return __ldcg(col + (size_t)pos * N + line); },
         [&](int line, int pos, float2 v) {
             const float l = __ldg(lcol + (size_t)pos * N + line);
@@ -230,6 +232,10 @@ HQS_DEV void blur_tile(const BatchSlice& S, int tile, const float* g, int r, flo
 // of the preconditioner FFTs are read from global memory (L1), which keeps two
 // CTAs resident per SM.
 constexpr size_t kBatchSmemF2 = (size_t)768 * kLines + 384 + 768;
+// the preconditioner items' lines (up to 2 kLines per item) fit the lines buffer
+static_assert(2 * 64 * kLines <= 768 * kLines && 2 * 320 * kLines <= 768 * kLines &&
+                  batch_pq<384>() <= kLines && batch_pq<128>() <= kLines && batch_pq<256>() <= kLines,
+              "preconditioner items exceed the lines buffer");
 
 __global__ void __launch_bounds__(HQS_BATCH_BD, 2) k_hqs_batch(BatchArgs B) {
     extern __shared__ __align__(16) float2 s[];

@@ -577,13 +577,23 @@ HQS_FFT_PAIR(768, 24, 12, FH(8, 1) FH(8, 8), FT(8, 12) FT(8, 96))
 #undef FT
 #undef HQS_FFT_PAIR
 
-// Transform `nlines` (<= kLines) lines held at s[pos * kLines + line] with the
+// Element (pos, line) of a CTA's line buffer of N-point lines: lines [0, kLines)
+// at s[pos * kLines + line], lines [kLines, 2 kLines) in a second block of
+// N * kLines elements after the first (same stride), so short lines can fill a
+// CTA with up to 2 kLines lines.
+template <int N> HQS_DEV int line_elem(int pos, int line) {
+    return line < kLines ? pos * kLines + line : N * kLines + pos * kLines + (line - kLines);
+}
+template <int N> HQS_DEV float2* line_base(float2* s, int line) { return s + line_elem<N>(0, line); }
+
+// Transform `nlines` (<= kLines; <= 2 kLines with WIDE, lines held at
+// s[line_elem<N>(pos, line)]) lines held at s[pos * kLines + line] with the
 // whole CTA: thread (line = tid % lpg, t = tid / lpg) owns E elements of one
 // line, lpg = blockDim.x / TPL >= nlines (launch with fft_threads).  The
 // caller synchronises before (after filling s); this routine ends with a
 // barrier.  (A loop over line groups here doubles register use, so the launch
 // shape covers every line at once instead.)
-template <int N, bool INV, bool ZIN = false, bool HOUT = false>
+template <int N, bool INV, bool ZIN = false, bool HOUT = false, bool WIDE = false>
 HQS_DEV void block_fft(float2* s, int nlines, const float2* tw) {
     constexpr int TPL = FftSize<N>::TPL;
     const int lpg = blockDim.x / TPL;
@@ -596,7 +606,8 @@ HQS_DEV void block_fft(float2* s, int nlines, const float2* tw) {
     const int ll = tid % lpg;
     const int t = tid / lpg;
     const bool act = (ll < nlines) && (t < TPL);
-    FftSize<N>::template run<INV, ZIN, HOUT>(s + (act ? ll : 0), act ? t : 0, act, tw);
+    float2* base = WIDE ? line_base<N>(s, act ? ll : 0) : s + (act ? ll : 0);
+    FftSize<N>::template run<INV, ZIN, HOUT>(base, act ? t : 0, act, tw);
 }
 
 // block_fft with I/O hooks (see fft_stage_io).  The hooks receive this
@@ -635,8 +646,9 @@ HQS_DEV void block_fft_io_tab(float2* s, int nlines, const float2* tw, LD&& ld, 
 
 // The forward x factor x inverse pair (FftPair) with the same hooks: ld feeds the
 // forward's first stage (upper half zero with ZIN), xf(line, pos, v) is the
-// factor, stf takes the inverse's output (its lower half only with HOUT).
-template <int N, bool ZIN, bool HOUT, class LD, class XF, class STF>
+// factor, stf takes the inverse's output (its lower half only with HOUT).  WIDE:
+// up to 2 kLines lines, the buffer laid out as line_elem<N>.
+template <int N, bool ZIN, bool HOUT, bool WIDE = false, class LD, class XF, class STF>
 HQS_DEV void block_fft_pair(float2* s, int nlines, const float2* tw, LD&& ld, XF&& xf, STF&& stf) {
     constexpr int TPL = FftPair<N>::TPL;
     static_assert(FftPair<N>::E == FftSize<N>::E, "same thread layout as the single transforms");
@@ -650,7 +662,8 @@ HQS_DEV void block_fft_pair(float2* s, int nlines, const float2* tw, LD&& ld, XF
     auto bind_ld = [&, line, act](int pos) { return ld(line, pos, act); };
     auto bind_xf = [&, line](int pos, float2 v) { return xf(line, pos, v); };
     auto bind_st = [&, line](int pos, float2 v) { stf(line, pos, v); };
-    FftPair<N>::template run<ZIN, HOUT>(s + line, act ? t : 0, act, tw, bind_ld, bind_xf, bind_st);
+    FftPair<N>::template run<ZIN, HOUT>(WIDE ? line_base<N>(s, line) : s + line, act ? t : 0, act, tw, bind_ld, bind_xf,
+                                        bind_st);
 }
 
 template <int N, bool INV, bool ZIN, bool HOUT, class LD, class XF, class STF>
