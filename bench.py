@@ -26,6 +26,9 @@ coils, radial (48-96 spokes x 2n) or spiral (12-24 interleaves x 1024-4096)
 trajectories, in one persistent launch replayed from a CUDA graph after the
 spreading tile and solve shapes were picked by the autotuner; it reports
 slices/s, the batch latency, and the same HQS run slice by slice beside it.
+The default line carries a compact run of it (2 timed steps, `batch64_hqs`),
+beside the precision variant (`mixed_precision`) and the learned
+preconditioner (`learned_precond`), all outside the timed region.
 
 With N > 1 (torchrun) every rank solves its own batch (replicas, weak
 scaling); the timed region is bracketed by barriers and the slowest rank's
@@ -459,6 +462,9 @@ def run_ours(args, rank, world, dist):
     # timed regions): 2 training seeds x 16 iterates, 200 Adam steps, 2 held-out seeds
     learned = learned_summary(hq, range(1000, 1002), range(5000, 5002), steps=200)
     learned = {k: v for k, v in learned.items() if k != "held_out"}
+    # the uneven batch (64 slices of 256^2-384^2, annealed HQS 20 x 5 in one
+    # graph-replayed persistent launch), compact: 2 timed steps, outside the timed region
+    batch64, _, _, _ = batch64_summary(hq, 2, 3, rank, world, dist)
 
     # end to end through the public API with host buffers: H2D of y, D2H of x
     y_host = [y.cpu().pin_memory() for y in ys]
@@ -524,6 +530,7 @@ def run_ours(args, rank, world, dist):
         "true_rel_residual_max": max(true_res),
         "mixed_precision": mixed,
         "learned_precond": learned,
+        "batch64_hqs": batch64,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
                      "traffic": BATCH_TRAFFIC_BYTES if args.mode == "batched" else PERSISTENT_TRAFFIC_BYTES,
@@ -600,18 +607,19 @@ def make_batch64(rank=0, count=64):
     return out
 
 
-def run_batch64(args, rank, world, dist):
+def batch64_summary(hq, steps, warmup, rank, world, dist, count=64):
+    """The uneven-batch workload (64 slices, n in {256, 320, 384}, 8-20 coils,
+    radial or spiral, annealed HQS 20 x 5 in one graph-replayed persistent
+    launch): slices/s, per-step latency and the same work slice by slice through
+    hqs_run.  Returns (summary dict, clocks, timed ms, slices)."""
     import torch
-    import paper_2411_01955_gb300 as hq
     from paper_2411_01955_gb300 import tune
     import synth
 
-    dev = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(dev)
     K, CG = 20, 5
     mu = synth.mu_schedule_geometric(1e-1, 1e-3, K).astype(np.float32)
     sigma = mu.copy()
-    sl = make_batch64(rank)
+    sl = make_batch64(rank, count)
     plans, ys, xs = [], [], []
     tuned = {}
     for s in sl:
@@ -641,28 +649,27 @@ def run_batch64(args, rank, world, dist):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def timed(fn, steps):
+    def timed(fn, steps_):
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(steps):
+        for _ in range(steps_):
             fn()
         e1.record(stream)
         barrier()
-        ms = e0.elapsed_time(e1)
-        return max_over_ranks(ms, dist)
+        ms_ = e0.elapsed_time(e1)
+        return max_over_ranks(ms_, dist)
 
-    for _ in range(max(args.warmup, 3)):
+    for _ in range(max(warmup, 3)):
         step()
     res = batch.status()
-    clk = ClockSampler(dev)
+    clk = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     clk.start()
-    ms = timed(step, args.steps)
+    ms = timed(step, steps)
     clocks = clk.stop()
-    value = whole_job_rate(len(sl) * args.steps, world, ms)
     # per-step latency (every slice of a step finishes with the step's one launch)
     lat = []
-    for _ in range(max(args.steps, 5)):
+    for _ in range(max(steps, 5)):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         step()
@@ -677,10 +684,34 @@ def run_batch64(args, rank, world, dist):
     batch.close()
     per_slice()
     ms_seq = timed(per_slice, 1)
+    summary = {
+        "slices_per_s": whole_job_rate(len(sl) * steps, world, ms),
+        "batch_latency_ms": ms / steps,
+        "slice_latency_ms_p50_p95": [float(np.percentile(lat, 50)), float(np.percentile(lat, 95))],
+        "per_slice_hqs_run_slices_per_s": len(sl) * world / (ms_seq / 1e3),
+        "speedup_vs_per_slice": (ms_seq) / (ms / steps),
+        "max_final_rel_residual_sq": float(max(res)),
+        "sizes": {str(k): sum(1 for s in sl if s["n"] == k) for k in (256, 320, 384)},
+        "points": int(sum(s["traj"].shape[0] for s in sl)),
+        "coils": int(sum(s["L"] for s in sl)),
+        "spread_tiles_picked": {str(k): v for k, v in sorted(tuned.items())},
+    }
+    for p in plans:
+        p.close()
+    return summary, clocks, ms, sl
+
+
+def run_batch64(args, rank, world, dist):
+    import torch
+    import paper_2411_01955_gb300 as hq
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    summ, clocks, ms, sl = batch64_summary(hq, args.steps, args.warmup, rank, world, dist)
     if rank != 0:
         return
     line = {
-        "metric": "batched annealed HQS slices/s (64 uneven slices, 20 x 5 CG)", "value": value,
+        "metric": "batched annealed HQS slices/s (64 uneven slices, 20 x 5 CG)", "value": summ["slices_per_s"],
         "unit": "slices/s", "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32",
@@ -688,16 +719,14 @@ def run_batch64(args, rank, world, dist):
         "config": {"workload": "64 slices, n in {256,320,384}, 8-20 coils, radial 48-96 spokes x 2n or "
                                "spiral 12-24 x 1024-4096, KB W=6, sigma=2, HQS 20 outer x 5 CG, "
                                "mu 1e-1 -> 1e-3, Gaussian denoiser; one graph-replayed persistent launch",
-                   "sizes": {str(k): sum(1 for s in sl if s["n"] == k) for k in (256, 320, 384)},
-                   "points": int(sum(s["traj"].shape[0] for s in sl)),
-                   "coils": int(sum(s["L"] for s in sl)),
-                   "spread_tiles_picked": {str(k): v for k, v in sorted(tuned.items())},
+                   "sizes": summ["sizes"], "points": summ["points"], "coils": summ["coils"],
+                   "spread_tiles_picked": summ["spread_tiles_picked"],
                    "l2": "inputs larger than L2 (64 distinct slices), no flush"},
-        "batch_latency_ms": ms / args.steps,
-        "slice_latency_ms_p50_p95": [float(np.percentile(lat, 50)), float(np.percentile(lat, 95))],
-        "per_slice_hqs_run_slices_per_s": len(sl) * world / (ms_seq / 1e3),
-        "speedup_vs_per_slice": (ms_seq) / (ms / args.steps),
-        "max_final_rel_residual_sq": float(max(res)),
+        "batch_latency_ms": summ["batch_latency_ms"],
+        "slice_latency_ms_p50_p95": summ["slice_latency_ms_p50_p95"],
+        "per_slice_hqs_run_slices_per_s": summ["per_slice_hqs_run_slices_per_s"],
+        "speedup_vs_per_slice": summ["speedup_vs_per_slice"],
+        "max_final_rel_residual_sq": summ["max_final_rel_residual_sq"],
         "gpu_launches": (len(sl) * 3 + 1) * args.steps,
         "clocks": clocks,
     }

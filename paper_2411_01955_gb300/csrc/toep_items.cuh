@@ -108,13 +108,15 @@ HQS_DEV double toep_rows_adj_item(const ToepArgs& A, int iy, int ch, float2* __r
     const int lines = min(A.LC, L - l0);
     const float2* src = A.T + (int64_t)iy * N2 * L + l0;
     const float2* sm = A.smaps + (int64_t)iy * n * L + l0;
-    // A full chunk of 16 coils (every thread of the CTA owns a line position): the
-    // row's maps go with cp.async to the upper half of the lines buffer once the
-    // last stage has read it (that stage writes the lower half only), so their
-    // latency overlaps the stage; with one chunk and mode 1 the row of pvec (when
-    // 16-byte aligned) goes to the image-row region at the start.  Callers declare
-    // the dynamic shared memory 16-byte aligned.
-    const bool fast = lines == kLines && (int)blockDim.x == kLines * FftSize<N2>::TPL;
+    // Maps in 16-byte pieces (an even number of coils at an even offset): the row's
+    // maps of the chunk go with cp.async to the upper half of the lines buffer
+    // ([n][kLines], `lines` used per pixel) once the last stage has read it (that
+    // stage writes the lower half only), issued by the stage's active threads, so
+    // their latency overlaps the stage; with one chunk and mode 1 the row of pvec
+    // (when 16-byte aligned) goes to the image-row region at the start.  Callers
+    // declare the dynamic shared memory 16-byte aligned.
+    constexpr int TPL = FftSize<N2>::TPL;
+    const bool pre_m = (lines % 2) == 0 && (L % 2) == 0 && (l0 % 2) == 0;
     const bool pre_p = mode == 1 && A.nchunk == 1 && ((uintptr_t)pvec & 15u) == 0;
     float2* msm = s + (int64_t)n * kLines;   // upper half: [n][kLines]
     float2* prow = s + N2 * kLines;          // image-row region: [n]
@@ -125,26 +127,29 @@ HQS_DEV double toep_rows_adj_item(const ToepArgs& A, int iy, int ch, float2* __r
     // row straight from T into the first stage; only the first n columns are kept
     block_fft_io<N2, true, false, true>(
         s, lines, tw, [&](int line, int p, bool) { return __ldcg(src + (int64_t)p * L + line); },
-        [&](int, int, float2 v) {
-            if (fast && !issued) {
+        [&](int line, int, float2 v) {
+            if (pre_m && !issued) {
                 issued = true;
-                for (int e = threadIdx.x; e < n * (kLines / 2); e += blockDim.x) {
-                    const int ix = e / (kLines / 2), h = e - ix * (kLines / 2);
+                // active threads: (line < lines, t < TPL), numbered t * lines + line
+                const int me = (int)(threadIdx.x / (blockDim.x / TPL)) * lines + line;
+                const int per = lines / 2;
+                for (int e = me; e < n * per; e += lines * TPL) {
+                    const int ix = e / per, h = e - ix * per;
                     cp_async16(msm + ix * kLines + 2 * h, sm + (int64_t)ix * L + 2 * h);
                 }
             }
             return v;
         },
         NoIO{});
-    if (fast || pre_p) {
+    if (pre_m || pre_p) {
         cp_async_wait_all();
         __syncthreads();
     }
     double part = 0.0;
     for (int ix = threadIdx.x; ix < n; ix += blockDim.x) {
         float2 acc = make_float2(0.f, 0.f);
-        const float2* smx = sm + (int64_t)ix * L;
-        if (fast) {
+        const float2* smx = pre_m ? msm + ix * kLines : sm + (int64_t)ix * L;
+        if (pre_m && lines == kLines) {
             // a full chunk of 16 coils is 128 contiguous, 16-byte aligned bytes
             const float4* s4 = reinterpret_cast<const float4*>(msm + ix * kLines);
             float4 sv4[kLines / 2];
