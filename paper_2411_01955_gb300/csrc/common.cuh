@@ -32,6 +32,19 @@ HQS_DEV void cp_async16(void* smem_dst, const void* gmem_src) {
 }
 HQS_DEV void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// Programmatic dependent launch (kernels launched with launch_pdl): the
+// kernel lets the next kernel of the stream launch its CTAs early and waits
+// until the previous kernel of the stream has completed and its memory is
+// visible; both are no-ops without a programmatic dependency.  A kernel entered
+// this way touches no global memory before the wait.
+HQS_DEV void griddep_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+HQS_DEV void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+#define HQS_PDL_ENTRY()              \
+    do {                             \
+        griddep_launch_dependents(); \
+        griddep_wait();              \
+    } while (0)
+
 // multiply by -i (forward) or +i (inverse)
 template <bool INV> HQS_DEV float2 mul_mi(float2 a) {
     return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
@@ -53,6 +66,25 @@ void hqs_note_cuda_error(cudaError_t e, const char* what, const char* file, int 
 #define HQS_DEVERR_TIMEOUT   1u
 #define HQS_DEVERR_BREAKDOWN 2u
 #define HQS_DEVERR_BOUNDS    4u
+
+// Launch with programmatic stream serialisation: the kernel's CTAs may start
+// while the previous kernel of the stream finishes (the kernel begins with
+// HQS_PDL_ENTRY), which hides the launch gap between the passes of an operator.
+template <class... KArgs, class... Args>
+static inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                     Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
 
 // ---------------------------------------------------------------- math
 static inline int ceil_div(int a, int b) { return (a + b - 1) / b; }

@@ -42,6 +42,7 @@ template <int G>
 __global__ void k_fwd_rows(const float2* __restrict__ x, const float2* __restrict__ smaps,
                            const float* __restrict__ apod, int n, int L, int LC, int nchunk,
                            float scale, const float2* __restrict__ twg, float2* __restrict__ U) {
+    HQS_PDL_ENTRY();
     extern __shared__ float2 s[];
     const float2* tw = stage_twiddles<G>(s + G * kLines, twg);
     const int iy = blockIdx.x;
@@ -75,6 +76,7 @@ __global__ void k_fwd_rows(const float2* __restrict__ x, const float2* __restric
 template <int G>
 __global__ void k_fwd_cols(const float2* __restrict__ U, int n, int L, int LC, int nchunk,
                            const float2* __restrict__ twg, float2* __restrict__ Gh) {
+    HQS_PDL_ENTRY();
     extern __shared__ float2 s[];
     const float2* tw = stage_twiddles<G>(s + G * kLines, twg);
     const int gx = blockIdx.x;
@@ -124,6 +126,7 @@ template <int G>
 __global__ void k_fwd_rows_h(const float2* __restrict__ x, const float2* __restrict__ smaps,
                              const float* __restrict__ apod, int n, int L, float scale,
                              const float2* __restrict__ twg, float2* __restrict__ U) {
+    HQS_PDL_ENTRY();
     extern __shared__ float2 s[];
     const float2* tw = stage_twiddles<G>(s + G * kLines, twg);
     const int iy = blockIdx.x, l0 = blockIdx.y * kLines;
@@ -141,6 +144,7 @@ __global__ void k_fwd_rows_h(const float2* __restrict__ x, const float2* __restr
 template <int G>
 __global__ void k_fwd_cols_h(const float2* __restrict__ U, int n, int L, const float2* __restrict__ twg,
                              float2* __restrict__ Gh) {
+    HQS_PDL_ENTRY();
     extern __shared__ float2 s[];
     const float2* tw = stage_twiddles<G>(s + G * kLines, twg);
     const int gx = blockIdx.x, l0 = blockIdx.y * kLines;
@@ -156,6 +160,7 @@ __global__ void k_fwd_cols_h(const float2* __restrict__ U, int n, int L, const f
 template <int G>
 __global__ void k_adj_cols_h(const float2* __restrict__ Hg, int n, int L, const float2* __restrict__ twg,
                              float2* __restrict__ V) {
+    HQS_PDL_ENTRY();
     extern __shared__ float2 s[];
     const float2* tw = stage_twiddles<G>(s + G * kLines, twg);
     const int gx = blockIdx.x, l0 = blockIdx.y * kLines;
@@ -173,6 +178,7 @@ __global__ void k_adj_rows_h(const float2* __restrict__ V, const float2* __restr
                              const float* __restrict__ apod, int n, int L, int nchunk, float scale,
                              const float2* __restrict__ twg, float2* x, float2* __restrict__ part, float zc,
                              const float2* z) {
+    HQS_PDL_ENTRY();
     extern __shared__ float2 s[];
     const float2* tw = stage_twiddles<G>(s + G * kLines, twg);
     const int iy = blockIdx.x, l0 = blockIdx.y * kLines;
@@ -214,6 +220,7 @@ template <int W>
 __global__ void __launch_bounds__(256) k_interp(const float2* __restrict__ Gh, const int4* __restrict__ pts,
                                                 const int* __restrict__ perm, int M, int G, int L,
                                                 float beta, float2* __restrict__ y) {
+    HQS_PDL_ENTRY();
     const int j = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 4);
     const int h = threadIdx.x & 15;
     const int base = threadIdx.x & 16;
@@ -266,6 +273,7 @@ template <int W>
 __global__ void __launch_bounds__(256) k_interp16(const float2* __restrict__ Gh, const int4* __restrict__ pts,
                                                   const float* __restrict__ kbw, int M, int G, int L,
                                                   float2* __restrict__ ys) {
+    HQS_PDL_ENTRY();
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t j = t >> 3;
     const int q = threadIdx.x & 7;
@@ -315,6 +323,7 @@ __global__ void __launch_bounds__(256) k_interp16(const float2* __restrict__ Gh,
 constexpr int kSortPts = 64;
 __global__ void __launch_bounds__(256) k_y_to_sorted(const float2* __restrict__ y, const int* __restrict__ invperm,
                                                      int M, int L, float2* __restrict__ ys) {
+    HQS_PDL_ENTRY();
     extern __shared__ float2 sy[];   // [kSortPts][L + 1]
     const int m0 = blockIdx.x * kSortPts;
     const int np = min(kSortPts, M - m0);
@@ -333,6 +342,7 @@ __global__ void __launch_bounds__(256) k_y_to_sorted(const float2* __restrict__ 
 // point's L-coil line read contiguously, each coil's kSortPts points written as one run.
 __global__ void __launch_bounds__(256) k_y_from_sorted(const float2* __restrict__ ys, const int* __restrict__ invperm,
                                                        int M, int L, float2* __restrict__ y) {
+    HQS_PDL_ENTRY();
     extern __shared__ float2 sy[];   // [kSortPts][L + 1]
     const int m0 = blockIdx.x * kSortPts;
     const int np = min(kSortPts, M - m0);
@@ -373,6 +383,7 @@ __global__ void __launch_bounds__(256) k_spread_tiles(const float2* __restrict__
                                                       const int4* __restrict__ items, const int2* __restrict__ tinfo,
                                                       unsigned* __restrict__ tickets, float2* __restrict__ partial,
                                                       int G, int L, int LCS, int nbx, float2* __restrict__ grid) {
+    HQS_PDL_ENTRY();
     constexpr int CAND = HQS_SPREAD_CAND;
     constexpr int NK = (TT * 16 + 31) / 32;   // (cell, coil) pairs of a row per lane, LCS <= 16
     extern __shared__ float4 smem4[];
@@ -566,6 +577,7 @@ __global__ void __launch_bounds__(256) k_spread_tiles(const float2* __restrict__
 template <int G>
 __global__ void k_adj_cols(const float2* __restrict__ Hg, int n, int L, int LC, int nchunk,
                            const float2* __restrict__ twg, float2* __restrict__ V) {
+    HQS_PDL_ENTRY();
     extern __shared__ float2 s[];
     const float2* tw = stage_twiddles<G>(s + G * kLines, twg);
     const int gx = blockIdx.x;
@@ -596,6 +608,7 @@ __global__ void k_adj_rows(const float2* __restrict__ V, const float2* __restric
                            const float* __restrict__ apod, int n, int L, int LC, int nchunk,
                            float scale, const float2* __restrict__ twg, float2* x,
                            float2* __restrict__ part, float zc, const float2* z) {
+    HQS_PDL_ENTRY();
     extern __shared__ float2 s[];
     const float2* tw = stage_twiddles<G>(s + G * kLines, twg);
     const int iy = blockIdx.x;
@@ -638,6 +651,7 @@ __global__ void k_adj_rows(const float2* __restrict__ V, const float2* __restric
 
 __global__ void k_adj_chunk_sum(const float2* __restrict__ part, const float* __restrict__ apod, int n,
                                 int nchunk, float scale, float2* x, float zc, const float2* z) {
+    HQS_PDL_ENTRY();
     const int count = n * n;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x) {
         float2 a = make_float2(0.f, 0.f);
@@ -665,16 +679,18 @@ static int fwd_fft_impl(hqs_plan_s* p, const float2* x, cudaStream_t st) {
     if (half_passes(p)) {
         HQS_CUDA_TRY(cudaFuncSetAttribute(k_fwd_rows_h<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         HQS_CUDA_TRY(cudaFuncSetAttribute(k_fwd_cols_h<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_fwd_rows_h<G><<<dim3(p->n, p->nchunk), th, sm, st>>>(x, p->smaps, p->apod, p->n, p->L, p->scale, tw, p->work);
-        k_fwd_cols_h<G><<<dim3(G, p->nchunk), th, sm, st>>>(p->work, p->n, p->L, tw, p->grid);
+        HQS_CUDA_TRY(launch_pdl(k_fwd_rows_h<G>, dim3(p->n, p->nchunk), th, sm, st, x, p->smaps, p->apod, p->n, p->L,
+                                p->scale, tw, p->work));
+        HQS_CUDA_TRY(launch_pdl(k_fwd_cols_h<G>, dim3(G, p->nchunk), th, sm, st, p->work, p->n, p->L, tw, p->grid));
         HQS_CUDA_TRY(cudaGetLastError());
         return HQS_OK;
     }
     HQS_CUDA_TRY(cudaFuncSetAttribute(k_fwd_rows<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     HQS_CUDA_TRY(cudaFuncSetAttribute(k_fwd_cols<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_fwd_rows<G><<<dim3(p->n, p->nchunk), th, sm, st>>>(x, p->smaps, p->apod, p->n, p->L, p->LC,
-                                                         p->nchunk, p->scale, tw, p->work);
-    k_fwd_cols<G><<<dim3(G, p->nchunk), th, sm, st>>>(p->work, p->n, p->L, p->LC, p->nchunk, tw, p->grid);
+    HQS_CUDA_TRY(launch_pdl(k_fwd_rows<G>, dim3(p->n, p->nchunk), th, sm, st, x, p->smaps, p->apod, p->n, p->L, p->LC,
+                            p->nchunk, p->scale, tw, p->work));
+    HQS_CUDA_TRY(launch_pdl(k_fwd_cols<G>, dim3(G, p->nchunk), th, sm, st, p->work, p->n, p->L, p->LC, p->nchunk, tw,
+                            p->grid));
     HQS_CUDA_TRY(cudaGetLastError());
     return HQS_OK;
 }
@@ -687,23 +703,24 @@ static int adj_fft_impl(hqs_plan_s* p, float2* x, float zc, const float2* z, cud
     if (half_passes(p)) {
         HQS_CUDA_TRY(cudaFuncSetAttribute(k_adj_cols_h<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         HQS_CUDA_TRY(cudaFuncSetAttribute(k_adj_rows_h<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_adj_cols_h<G><<<dim3(G, p->nchunk), th, sm, st>>>(p->grid, p->n, p->L, tw, p->work);
-        k_adj_rows_h<G><<<dim3(p->n, p->nchunk), th, sm, st>>>(p->work, p->smaps, p->apod, p->n, p->L, p->nchunk,
-                                                               p->scale, tw, x, p->chunk_buf, zc, z);
+        HQS_CUDA_TRY(launch_pdl(k_adj_cols_h<G>, dim3(G, p->nchunk), th, sm, st, p->grid, p->n, p->L, tw, p->work));
+        HQS_CUDA_TRY(launch_pdl(k_adj_rows_h<G>, dim3(p->n, p->nchunk), th, sm, st, p->work, p->smaps, p->apod, p->n,
+                                p->L, p->nchunk, p->scale, tw, x, p->chunk_buf, zc, z));
         if (p->nchunk > 1)
-            k_adj_chunk_sum<<<std::min(ceil_div(p->n * p->n, 256), 1024), 256, 0, st>>>(
-                p->chunk_buf, p->apod, p->n, p->nchunk, p->scale, x, zc, z);
+            HQS_CUDA_TRY(launch_pdl(k_adj_chunk_sum, dim3(std::min(ceil_div(p->n * p->n, 256), 1024)), dim3(256), 0, st,
+                                    p->chunk_buf, p->apod, p->n, p->nchunk, p->scale, x, zc, z));
         HQS_CUDA_TRY(cudaGetLastError());
         return HQS_OK;
     }
     HQS_CUDA_TRY(cudaFuncSetAttribute(k_adj_cols<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     HQS_CUDA_TRY(cudaFuncSetAttribute(k_adj_rows<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_adj_cols<G><<<dim3(G, p->nchunk), th, sm, st>>>(p->grid, p->n, p->L, p->LC, p->nchunk, tw, p->work);
-    k_adj_rows<G><<<dim3(p->n, p->nchunk), th, sm, st>>>(p->work, p->smaps, p->apod, p->n, p->L, p->LC,
-                                                         p->nchunk, p->scale, tw, x, p->chunk_buf, zc, z);
+    HQS_CUDA_TRY(launch_pdl(k_adj_cols<G>, dim3(G, p->nchunk), th, sm, st, p->grid, p->n, p->L, p->LC, p->nchunk, tw,
+                            p->work));
+    HQS_CUDA_TRY(launch_pdl(k_adj_rows<G>, dim3(p->n, p->nchunk), th, sm, st, p->work, p->smaps, p->apod, p->n, p->L,
+                            p->LC, p->nchunk, p->scale, tw, x, p->chunk_buf, zc, z));
     if (p->nchunk > 1)
-        k_adj_chunk_sum<<<std::min(ceil_div(p->n * p->n, 256), 1024), 256, 0, st>>>(
-            p->chunk_buf, p->apod, p->n, p->nchunk, p->scale, x, zc, z);
+        HQS_CUDA_TRY(launch_pdl(k_adj_chunk_sum, dim3(std::min(ceil_div(p->n * p->n, 256), 1024)), dim3(256), 0, st,
+                                p->chunk_buf, p->apod, p->n, p->nchunk, p->scale, x, zc, z));
     HQS_CUDA_TRY(cudaGetLastError());
     return HQS_OK;
 }
@@ -713,17 +730,17 @@ static int interp_impl(hqs_plan_s* p, float2* y, cudaStream_t st) {
     if (p->M == 0) return HQS_OK;
     if (p->L % 16 == 0) {
         const int64_t threads8 = p->M * 8;
-        k_interp16<W><<<(unsigned)ceil_div64(threads8, 256), 256, 0, st>>>(p->grid, p->pts, p->spread.kbw, (int)p->M,
-                                                                         p->G, p->L, p->spread.ysort);
+        HQS_CUDA_TRY(launch_pdl(k_interp16<W>, dim3((unsigned)ceil_div64(threads8, 256)), dim3(256), 0, st, p->grid,
+                                p->pts, p->spread.kbw, (int)p->M, p->G, p->L, p->spread.ysort));
         const size_t smy = (size_t)kSortPts * (p->L + 1) * sizeof(float2);
-        k_y_from_sorted<<<(unsigned)ceil_div64(p->M, kSortPts), 256, smy, st>>>(p->spread.ysort, p->invperm,
-                                                                             (int)p->M, p->L, y);
+        HQS_CUDA_TRY(launch_pdl(k_y_from_sorted, dim3((unsigned)ceil_div64(p->M, kSortPts)), dim3(256), smy, st,
+                                p->spread.ysort, p->invperm, (int)p->M, p->L, y));
         HQS_CUDA_TRY(cudaGetLastError());
         return HQS_OK;
     }
     const int64_t threads = p->M * 16;
-    k_interp<W><<<(unsigned)ceil_div64(threads, 256), 256, 0, st>>>(p->grid, p->pts, p->perm, (int)p->M,
-                                                                    p->G, p->L, (float)p->beta, y);
+    HQS_CUDA_TRY(launch_pdl(k_interp<W>, dim3((unsigned)ceil_div64(threads, 256)), dim3(256), 0, st, p->grid, p->pts,
+                            p->perm, (int)p->M, p->G, p->L, (float)p->beta, y));
     HQS_CUDA_TRY(cudaGetLastError());
     return HQS_OK;
 }
@@ -769,12 +786,12 @@ static int spread_tiles_impl(hqs_plan_s* p, const float2* y, cudaStream_t st) {
     HQS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     if (p->M > 0) {
         const size_t smy = (size_t)kSortPts * (p->L + 1) * sizeof(float2);
-        k_y_to_sorted<<<(unsigned)ceil_div64(p->M, kSortPts), 256, smy, st>>>(y, p->invperm, (int)p->M, p->L,
-                                                                           p->spread.ysort);
+        HQS_CUDA_TRY(launch_pdl(k_y_to_sorted, dim3((unsigned)ceil_div64(p->M, kSortPts)), dim3(256), smy, st, y,
+                                p->invperm, (int)p->M, p->L, p->spread.ysort));
     }
-    kern<<<p->spread.nitems, 256, sm, st>>>(
-        p->spread.ysort, p->pts, p->spread.kbw, p->spread.tile_nb, p->spread.items, p->spread.tile_info,
-        p->spread.tickets, p->spread.partial, p->G, p->L, lcs, p->nbx, p->grid);
+    HQS_CUDA_TRY(launch_pdl(kern, dim3(p->spread.nitems), dim3(256), sm, st, p->spread.ysort, p->pts, p->spread.kbw,
+                            p->spread.tile_nb, p->spread.items, p->spread.tile_info, p->spread.tickets,
+                            p->spread.partial, p->G, p->L, lcs, p->nbx, p->grid));
     HQS_CUDA_TRY(cudaGetLastError());
     return HQS_OK;
 }

@@ -24,6 +24,7 @@ using namespace hqs;
 template <int N2>
 __global__ void k_toep_rows_fwd(ToepArgs A, const float2* __restrict__ src, float2* __restrict__ pvec,
                                 int fuse, const CgScalars* __restrict__ cg) {
+    HQS_PDL_ENTRY();
     if (cg && cg->done) return;
     extern __shared__ __align__(16) float2 s[];
     const float beta = (fuse && cg) ? (float)cg->beta : 0.f;
@@ -32,6 +33,7 @@ __global__ void k_toep_rows_fwd(ToepArgs A, const float2* __restrict__ src, floa
 
 template <int N2>
 __global__ void k_toep_cols(ToepArgs A, const CgScalars* __restrict__ cg) {
+    HQS_PDL_ENTRY();
     if (cg && cg->done) return;
     extern __shared__ __align__(16) float2 s[];
     toep_cols_item<N2>(A, blockIdx.x, blockIdx.y, s);
@@ -41,6 +43,7 @@ template <int N2>
 __global__ void k_toep_rows_adj(ToepArgs A, float2* __restrict__ out, const float2* __restrict__ pvec,
                                 float a, float b, int mode, double* __restrict__ part,
                                 const CgScalars* __restrict__ cg) {
+    HQS_PDL_ENTRY();
     if (cg && cg->done) return;
     extern __shared__ __align__(16) float2 s[];
     __shared__ double red[32];
@@ -56,6 +59,7 @@ __global__ void k_toep_rows_adj(ToepArgs A, float2* __restrict__ out, const floa
 __global__ void k_toep_chunk_epilogue(ToepArgs A, float2* __restrict__ out, const float2* __restrict__ pvec,
                                       float a, float b, int mode, double* __restrict__ part,
                                       const CgScalars* __restrict__ cg) {
+    HQS_PDL_ENTRY();
     if (cg && cg->done) return;
     __shared__ double red[32];
     const int count = A.n * A.n;
@@ -271,11 +275,12 @@ static int toep_impl(hqs_plan_s* p, const float2* src, float2* pvec, int fuse, f
         src = pvec;
         fuse = 0;
     }
-    k_toep_rows_fwd<N2><<<grows, th, sm, st>>>(A, src, pvec, fuse, cg);
-    k_toep_cols<N2><<<gcols, th, sm, st>>>(A, cg);
-    k_toep_rows_adj<N2><<<grows, th, sm, st>>>(A, out, pmul, a, b, mode, part, cg);
+    HQS_CUDA_TRY(launch_pdl(k_toep_rows_fwd<N2>, grows, th, sm, st, A, src, pvec, fuse, cg));
+    HQS_CUDA_TRY(launch_pdl(k_toep_cols<N2>, gcols, th, sm, st, A, cg));
+    HQS_CUDA_TRY(launch_pdl(k_toep_rows_adj<N2>, grows, th, sm, st, A, out, pmul, a, b, mode, part, cg));
     if (p->nchunk > 1)
-        k_toep_chunk_epilogue<<<toep_partial_count(p), 256, 0, st>>>(A, out, pmul, a, b, mode, part, cg);
+        HQS_CUDA_TRY(launch_pdl(k_toep_chunk_epilogue, dim3(toep_partial_count(p)), dim3(256), 0, st, A, out, pmul, a,
+                                b, mode, part, cg));
     HQS_CUDA_TRY(cudaGetLastError());
     return HQS_OK;
 }
