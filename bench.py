@@ -102,9 +102,10 @@ ADJ_BYTES = (_Y + _PTS + _G2L) + (_G2L + _ROWS) + (_ROWS + _S + 320 * 320 * 8)
 # DRAM bytes (read + write) of one k_pcg_persistent<640,320> launch from an ncu
 # capture of the current kernel (profiles/pcg_persistent_320x16.md); None while
 # the kernel has changed since the last capture.
-PERSISTENT_TRAFFIC_BYTES = 16408576 + 2208768
-# The same for one k_pcg_batch launch (all 16 slices of a default step); None until captured.
-BATCH_TRAFFIC_BYTES = 44440873472 + 30583470080
+PERSISTENT_TRAFFIC_BYTES = None
+# The same for one k_pcg_batch launch (all 16 slices of a default step), from the
+# capture in profiles/pcg_batch_320x16_16slices.md; None until captured.
+BATCH_TRAFFIC_BYTES = 45479788544 + 31168711424
 
 
 def parse():
