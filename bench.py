@@ -426,6 +426,16 @@ def run_ours(args, rank, world, dist):
         applies()
     ms_aha = timed(applies, reps)
     aha_per_s = B * reps * world / (ms_aha / 1e3)
+    # the same applies batched: one launch of hqs_batch_toeplitz_normal per slice group
+    aha_batched_per_s = None
+    if batches:
+        def applies_batched():
+            for g, bt in zip(groups, batches):
+                bt.toeplitz_normal([zs[i] for i in g], [outs[i] for i in g])
+        for _ in range(3):
+            applies_batched()
+        ms_ahab = timed(applies_batched, reps)
+        aha_batched_per_s = B * reps * world / (ms_ahab / 1e3)
 
     # forward A and adjoint A^H of the NUFFT (each slice its own plan and data)
     xs_img = [torch.from_numpy(s["x"].astype(np.complex64)).cuda() for s in sl]
@@ -518,6 +528,7 @@ def run_ours(args, rank, world, dist):
                               "fused_grid": tuned.fused_grid},
                    "l2": "inputs larger than L2 (batch of distinct slices), no flush"},
         "aha_applies_per_s": aha_per_s,
+        "aha_applies_per_s_batched": aha_batched_per_s,
         "forward_per_s": fwd_per_s,
         "adjoint_per_s": adj_per_s,
         "nufft_hbm": {"unit": "GB/s", "peak": HBM_PEAK_GBS,

@@ -357,6 +357,17 @@ HQS_API int hqs_batch_dc_solve(hqs_batch batch, const hqs_c64* const* rhs, hqs_c
                                int max_iter, double rel_tol, void* stream);
 HQS_API int hqs_batch_dc_info(hqs_batch batch, int* iterations, double* rel_residual, int* status,
                               void* stream);
+/* Batched normal operator (Sec. 3.4's A^H A, A = F_Omega (x) S_l): out[i] =
+ * A_i^H A_i x[i] for every slice i of the batch in one cooperative launch, by
+ * the same exact 2N Toeplitz passes as hqs_toeplitz_normal (FP32), each pass
+ * dealing the work items of all slices to all CTAs.  x[i], out[i]: device
+ * (n_i x n_i) complex64 of the i-th plan, caller-owned; out[i] may equal x[i].
+ * Enqueued on `stream`; synchronises it first when the pointers differ from the
+ * last call.  Uses the plans' workspaces: calls on one batch (and on its plans)
+ * run in stream order.  A grid barrier that runs out of time is reported by the
+ * next hqs_batch_status / hqs_batch_dc_info (HQS_ERR_TIMEOUT). */
+HQS_API int hqs_batch_toeplitz_normal(hqs_batch batch, const hqs_c64* const* x, hqs_c64* const* out,
+                                      void* stream);
 
 /* Built-in denoiser (stand-in for the trained prior of Sec. 4.2): separable
  * Gaussian blur of real and imaginary parts, std s pixels (see

@@ -124,6 +124,7 @@ _SIGS = {
                                      C.c_float, C.c_int, C.c_double, C.c_void_p]),
     "hqs_batch_dc_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_int),
                                     C.c_void_p]),
+    "hqs_batch_toeplitz_normal": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_void_p]),
     "hqs_precond_apply_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_float, C.c_float,
                                             C.c_void_p, C.c_void_p]),
     "hqs_debug_phase_trace": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_ulonglong), C.c_int,
@@ -594,6 +595,20 @@ class Batch:
         _check(library().hqs_batch_dc_solve(self.handle, rp, xp, float(a), float(b), int(max_iter),
                                             float(rel_tol), _stream(stream)), "hqs_batch_dc_solve")
         return xs
+
+    def toeplitz_normal(self, xs, outs, stream=None):
+        """out_i = A_i^H A_i x_i for every slice in one launch."""
+        n = len(self.plans)
+        if len(xs) != n or len(outs) != n:
+            raise ValueError("one x and one out per slice")
+        for p, x, o in zip(self.plans, xs, outs):
+            if tuple(x.shape) != (p.ny, p.nx) or tuple(o.shape) != (p.ny, p.nx):
+                raise ValueError(f"x and out must be ({p.ny}, {p.nx})")
+        xp = (C.c_void_p * n)(*[_ptr(x, torch.complex64, "x") for x in xs])
+        op = (C.c_void_p * n)(*[_ptr(o, torch.complex64, "out") for o in outs])
+        _check(library().hqs_batch_toeplitz_normal(self.handle, xp, op, _stream(stream)),
+               "hqs_batch_toeplitz_normal")
+        return outs
 
     def debug_trace(self, enable=False, stream=None):
         """enable=True arms the batched solve's phase trace; enable=False

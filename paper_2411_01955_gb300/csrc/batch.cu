@@ -818,6 +818,84 @@ __global__ void __launch_bounds__(HQS_BATCH_BD, 2) k_pcg_batch(DcBatchArgs B) {
 
 }  // namespace
 
+// Batched normal operator: out_i = A_i^H A_i x_i for every slice of a batch in
+// one cooperative launch (Sec. 3.4's A^H A, the Toeplitz form of the per-stage
+// operator): the three Toeplitz passes, each dealing the items of all slices to
+// all CTAs, with a grid barrier between passes (and the fixed-order coil-chunk
+// sum when a slice has several chunks).  The per-slice arithmetic is that of
+// the per-stage passes.
+struct AhaBatchArgs {
+    const BatchSlice* sl;   // u = caller's x, q = caller's out
+    int ns;
+    const int* off;
+    unsigned* bar;
+    unsigned* err;
+};
+
+__global__ void __launch_bounds__(HQS_BATCH_BD, 2) k_aha_batch(AhaBatchArgs B) {
+    extern __shared__ __align__(16) float2 s[];
+    __shared__ int tw_cur;
+    const int ns = B.ns, G = gridDim.x, bid = blockIdx.x;
+    float2* twT = s + (size_t)768 * kLines + 384;
+    if (threadIdx.x == 0) tw_cur = 0;
+    __syncthreads();
+#define STAGE_TW2(AA)                                                                    \
+    if (tw_cur != 2 * (AA).n) {                                                          \
+        __syncthreads();                                                                 \
+        for (int i_ = threadIdx.x; i_ < 2 * (AA).n; i_ += blockDim.x) twT[i_] = (AA).tw[i_]; \
+        __syncthreads();                                                                 \
+        if (threadIdx.x == 0) tw_cur = 2 * (AA).n;                                       \
+        __syncthreads();                                                                 \
+    }
+#define AB_BARRIER()                                \
+    do {                                            \
+        if (!grid_barrier(B.bar, B.err)) return;    \
+    } while (0)
+#define FOR_ITEMS(list, ...)                                                               \
+    {                                                                                      \
+        const int* off_ = B.off + (list) * (ns + 1);                                       \
+        for (int g_ = bid; g_ < off_[ns]; g_ += G) {                                       \
+            const int si = find_slice(off_, ns, g_);                                       \
+            const int it_ = g_ - off_[si];                                                 \
+            const BatchSlice& S = B.sl[si];                                                \
+            __VA_ARGS__;                                                                   \
+        }                                                                                  \
+    }
+    FOR_ITEMS(BL_ROWS, {
+        const int n = S.A.n, ch = it_ / n, iy = it_ - ch * n;
+        STAGE_TW2(S.A);
+        HQS_BATCH_DISPATCH(n, (toep_rows_fwd_item<N2, HQS_BATCH_BD>(S.A, iy, ch, S.u, nullptr, 0.f, false, s, nullptr,
+                                                                    twT)));
+    });
+    AB_BARRIER();
+    FOR_ITEMS(BL_COLS, {
+        const int n = S.A.n, N2v = 2 * n, ch = it_ / N2v, kx = it_ - ch * N2v;
+        STAGE_TW2(S.A);
+        HQS_BATCH_DISPATCH(n, (toep_cols_item<N2, HQS_BATCH_BD>(S.A, kx, ch, s, twT)));
+    });
+    AB_BARRIER();
+    FOR_ITEMS(BL_ROWS, {
+        const int n = S.A.n, ch = it_ / n, iy = it_ - ch * n;
+        STAGE_TW2(S.A);
+        HQS_BATCH_DISPATCH(n, (toep_rows_adj_item<N2, HQS_BATCH_BD>(S.A, iy, ch, S.q, nullptr, 1.f, 0.f, 0, s, twT)));
+    });
+    if (B.off[BL_EPI * (ns + 1) + ns] > 0) {   // several coil chunks: fixed-order chunk sum
+        AB_BARRIER();
+        FOR_ITEMS(BL_EPI, {
+            const int n = S.A.n, cnt = n * n;
+            for (int ix = threadIdx.x; ix < n; ix += blockDim.x) {
+                const size_t e = (size_t)it_ * n + ix;
+                float2 v = make_float2(0.f, 0.f);
+                for (int c = 0; c < S.A.nchunk; ++c) v = cadd(v, __ldcg(S.A.chunk + (size_t)c * cnt + e));
+                S.q[e] = v;
+            }
+        });
+    }
+#undef AB_BARRIER
+#undef FOR_ITEMS
+#undef STAGE_TW2
+}
+
 struct hqs_batch_s {
     int device = 0;
     int ns = 0;
@@ -851,6 +929,10 @@ struct hqs_batch_s {
     int* d_status = nullptr;
     std::vector<const void*> dc_key;
     unsigned long long* d_trace = nullptr;   // optional phase trace of the batched solve
+    // batched A^H A: its own slice table (u = x, q = out), rebuilt when the pointers change
+    std::vector<BatchSlice> ap_host;
+    BatchSlice* d_slices_ap = nullptr;
+    std::vector<const void*> ap_key;
 };
 
 static void batch_free(hqs_batch_s* b) {
@@ -875,6 +957,7 @@ static void batch_free(hqs_batch_s* b) {
     cudaFree(b->d_iters);
     cudaFree(b->d_status);
     cudaFree(b->d_trace);
+    cudaFree(b->d_slices_ap);
     delete b;
 }
 
@@ -966,8 +1049,9 @@ extern "C" int hqs_batch_create(hqs_batch* out, hqs_plan* plans, int n, int max_
         cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking))
         return fail(HQS_ERR_OOM);
     b->dc_host = hs;
+    b->ap_host = hs;
     if (cudaMalloc(&b->d_slices_dc, n * sizeof(BatchSlice)) || cudaMalloc(&b->d_iters, n * sizeof(int)) ||
-        cudaMalloc(&b->d_status, n * sizeof(int)))
+        cudaMalloc(&b->d_status, n * sizeof(int)) || cudaMalloc(&b->d_slices_ap, n * sizeof(BatchSlice)))
         return fail(HQS_ERR_OOM);
     if (cudaMemcpy(b->d_slices, hs.data(), n * sizeof(BatchSlice), cudaMemcpyHostToDevice) ||
         cudaMemcpy(b->d_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice))
@@ -1150,6 +1234,48 @@ extern "C" int hqs_batch_dc_solve(hqs_batch b, const hqs_c64* const* rhs, hqs_c6
     const int grid = std::min(b->grid, per_sm * nsm);   // d_part holds b->grid partials per slot
     void* args[] = {&A};
     HQS_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_pcg_batch, dim3(grid), dim3(HQS_BATCH_BD), args, sm, st));
+    return HQS_OK;
+}
+
+extern "C" int hqs_batch_toeplitz_normal(hqs_batch b, const hqs_c64* const* x, hqs_c64* const* out, void* stream) {
+    if (!b || !x || !out) return HQS_ERR_INVALID_ARG;
+    for (int i = 0; i < b->ns; ++i)
+        if (!x[i] || !out[i]) return HQS_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<const void*> key;
+    for (int i = 0; i < b->ns; ++i) {
+        key.push_back(x[i]);
+        key.push_back(out[i]);
+    }
+    if (key != b->ap_key) {
+        // a previous apply may still read the table
+        HQS_CUDA_TRY(cudaStreamSynchronize(st));
+        for (int i = 0; i < b->ns; ++i) {
+            b->ap_host[i].u = const_cast<float2*>(reinterpret_cast<const float2*>(x[i]));
+            b->ap_host[i].q = reinterpret_cast<float2*>(out[i]);
+            b->ap_host[i].x = nullptr;
+        }
+        HQS_CUDA_TRY(cudaMemcpy(b->d_slices_ap, b->ap_host.data(), b->ns * sizeof(BatchSlice),
+                                cudaMemcpyHostToDevice));
+        b->ap_key = key;
+    }
+    HQS_CUDA_TRY(cudaMemsetAsync(b->d_bar, 0, 2 * sizeof(unsigned), st));
+    HQS_CUDA_TRY(cudaMemsetAsync(b->d_err, 0, sizeof(unsigned), st));
+    AhaBatchArgs A;
+    A.sl = b->d_slices_ap;
+    A.ns = b->ns;
+    A.off = b->d_off;
+    A.bar = b->d_bar;
+    A.err = b->d_err;
+    const size_t sm = kBatchSmemF2 * sizeof(float2);
+    HQS_CUDA_TRY(cudaFuncSetAttribute(k_aha_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    int per_sm = 0, nsm = 0;
+    HQS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_aha_batch, HQS_BATCH_BD, sm));
+    HQS_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->device));
+    if (per_sm < 1) return HQS_ERR_UNSUPPORTED;
+    const int grid = per_sm * nsm;
+    void* args[] = {&A};
+    HQS_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_aha_batch, dim3(grid), dim3(HQS_BATCH_BD), args, sm, st));
     return HQS_OK;
 }
 
