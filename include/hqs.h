@@ -368,6 +368,19 @@ HQS_API int hqs_batch_dc_info(hqs_batch batch, int* iterations, double* rel_resi
  * next hqs_batch_status / hqs_batch_dc_info (HQS_ERR_TIMEOUT). */
 HQS_API int hqs_batch_toeplitz_normal(hqs_batch batch, const hqs_c64* const* x, hqs_c64* const* out,
                                       void* stream);
+/* Batched NUFFT operators (Eq. (1) and its adjoint, the same gridding as
+ * hqs_forward / hqs_adjoint_axpy): y[i] = A_i x[i], and x[i] = A_i^H y[i] +
+ * zc z[i] (z NULL, or z[i] NULL: no axpy term), for every slice i.  The
+ * slices whose grid is 2n with 16-coil chunks run their row and column FFT
+ * passes together, one launch per pass and grid size; spreading,
+ * interpolation and the other slices' passes run per slice.  y[i]: (L_i, M_i),
+ * x[i], z[i]: (n_i, n_i), device complex64, caller-owned.  Enqueued on
+ * `stream`; synchronises it first when the image pointers differ from the last
+ * call.  Uses the plans' workspaces: calls on one batch (and on its plans) run
+ * in stream order. */
+HQS_API int hqs_batch_forward(hqs_batch batch, const hqs_c64* const* x, hqs_c64* const* y, void* stream);
+HQS_API int hqs_batch_adjoint_axpy(hqs_batch batch, const hqs_c64* const* y, float zc, const hqs_c64* const* z,
+                                   hqs_c64* const* x, void* stream);
 
 /* Built-in denoiser (stand-in for the trained prior of Sec. 4.2): separable
  * Gaussian blur of real and imaginary parts, std s pixels (see

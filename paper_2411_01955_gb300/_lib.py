@@ -125,6 +125,9 @@ _SIGS = {
     "hqs_batch_dc_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_int),
                                     C.c_void_p]),
     "hqs_batch_toeplitz_normal": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_void_p]),
+    "hqs_batch_forward": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_void_p]),
+    "hqs_batch_adjoint_axpy": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.c_float, C.POINTER(C.c_void_p),
+                                         C.POINTER(C.c_void_p), C.c_void_p]),
     "hqs_precond_apply_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_float, C.c_float,
                                             C.c_void_p, C.c_void_p]),
     "hqs_debug_phase_trace": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_ulonglong), C.c_int,
@@ -609,6 +612,45 @@ class Batch:
         _check(library().hqs_batch_toeplitz_normal(self.handle, xp, op, _stream(stream)),
                "hqs_batch_toeplitz_normal")
         return outs
+
+    def _check_images(self, xs, what):
+        if len(xs) != len(self.plans):
+            raise ValueError(f"one {what} per slice")
+        for p, x in zip(self.plans, xs):
+            if tuple(x.shape) != (p.ny, p.nx):
+                raise ValueError(f"{what} must be ({p.ny}, {p.nx})")
+
+    def _check_kspace(self, ys):
+        if len(ys) != len(self.plans):
+            raise ValueError("one y per slice")
+        for p, y in zip(self.plans, ys):
+            if tuple(y.shape) != (p.coils, p.npoints):
+                raise ValueError(f"y must be ({p.coils}, {p.npoints})")
+
+    def forward(self, xs, ys, stream=None):
+        """y_i = A_i x_i for every slice (the FFT passes of like slices batched)."""
+        self._check_images(xs, "x")
+        self._check_kspace(ys)
+        n = len(self.plans)
+        xp = (C.c_void_p * n)(*[_ptr(x, torch.complex64, "x") for x in xs])
+        yp = (C.c_void_p * n)(*[_ptr(y, torch.complex64, "y") for y in ys])
+        _check(library().hqs_batch_forward(self.handle, xp, yp, _stream(stream)), "hqs_batch_forward")
+        return ys
+
+    def adjoint_axpy(self, ys, zc, zs, xs, stream=None):
+        """x_i = A_i^H y_i + zc z_i for every slice (zs None: no axpy term)."""
+        self._check_kspace(ys)
+        self._check_images(xs, "x")
+        n = len(self.plans)
+        yp = (C.c_void_p * n)(*[_ptr(y, torch.complex64, "y") for y in ys])
+        xp = (C.c_void_p * n)(*[_ptr(x, torch.complex64, "x") for x in xs])
+        zp = None
+        if zs is not None:
+            self._check_images(zs, "z")
+            zp = (C.c_void_p * n)(*[_ptr(z, torch.complex64, "z") for z in zs])
+        _check(library().hqs_batch_adjoint_axpy(self.handle, yp, float(zc), zp, xp, _stream(stream)),
+               "hqs_batch_adjoint_axpy")
+        return xs
 
     def debug_trace(self, enable=False, stream=None):
         """enable=True arms the batched solve's phase trace; enable=False

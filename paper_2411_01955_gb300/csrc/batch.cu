@@ -933,6 +933,14 @@ struct hqs_batch_s {
     std::vector<BatchSlice> ap_host;
     BatchSlice* d_slices_ap = nullptr;
     std::vector<const void*> ap_key;
+    // batched forward / adjoint: the lower-half passes' argument tables of the slices
+    // that take them, grouped by grid size (rebuilt when the pointers change)
+    struct HalfGroup {
+        int G, n, maxchunk, first, count;
+    };
+    void* d_half[2] = {nullptr, nullptr};   // [0] forward, [1] adjoint
+    std::vector<HalfGroup> half_groups[2];
+    std::vector<const void*> half_key[2];
 };
 
 static void batch_free(hqs_batch_s* b) {
@@ -958,6 +966,8 @@ static void batch_free(hqs_batch_s* b) {
     cudaFree(b->d_status);
     cudaFree(b->d_trace);
     cudaFree(b->d_slices_ap);
+    cudaFree(b->d_half[0]);
+    cudaFree(b->d_half[1]);
     delete b;
 }
 
@@ -1276,6 +1286,97 @@ extern "C" int hqs_batch_toeplitz_normal(hqs_batch b, const hqs_c64* const* x, h
     const int grid = per_sm * nsm;
     void* args[] = {&A};
     HQS_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_aha_batch, dim3(grid), dim3(HQS_BATCH_BD), args, sm, st));
+    return HQS_OK;
+}
+
+// Argument tables of the batched lower-half passes (dir 0: forward x -> grid,
+// dir 1: adjoint grid -> x with the axpy term z), grouped by grid size in slice
+// order; uploaded when the image pointers differ from the last call.
+static int half_tables(hqs_batch_s* b, int dir, const float2* const* xin, float2* const* xout,
+                       const float2* const* z, cudaStream_t st) {
+    std::vector<const void*> key;
+    for (int i = 0; i < b->ns; ++i) {
+        key.push_back(xin ? (const void*)xin[i] : nullptr);
+        key.push_back(xout ? (const void*)xout[i] : nullptr);
+        key.push_back(z ? (const void*)z[i] : nullptr);
+    }
+    if (b->d_half[dir] && key == b->half_key[dir]) return HQS_OK;
+    // a previous call may still read the table
+    HQS_CUDA_TRY(cudaStreamSynchronize(st));
+    const size_t sz = half_args_bytes();
+    if (!b->d_half[dir]) HQS_CUDA_TRY(cudaMalloc(&b->d_half[dir], sz * b->ns));
+    std::vector<unsigned char> host(sz * b->ns);
+    std::vector<hqs_batch_s::HalfGroup> groups;
+    std::vector<int> done(b->ns, 0);
+    int slot = 0;
+    for (int i = 0; i < b->ns; ++i) {
+        const hqs_plan_s* p = b->plans[i];
+        if (done[i] || !plan_half_passes(p)) continue;
+        hqs_batch_s::HalfGroup g{p->G, p->n, 0, slot, 0};
+        for (int j = i; j < b->ns; ++j) {
+            const hqs_plan_s* q = b->plans[j];
+            if (done[j] || !plan_half_passes(q) || q->G != p->G) continue;
+            fill_half_args(q, xin ? xin[j] : nullptr, xout ? xout[j] : nullptr, z ? z[j] : nullptr,
+                           host.data() + sz * slot);
+            g.maxchunk = std::max(g.maxchunk, q->nchunk);
+            ++g.count;
+            ++slot;
+            done[j] = 1;
+        }
+        groups.push_back(g);
+    }
+    if (slot > 0) HQS_CUDA_TRY(cudaMemcpy(b->d_half[dir], host.data(), sz * slot, cudaMemcpyHostToDevice));
+    b->half_groups[dir] = groups;
+    b->half_key[dir] = key;
+    return HQS_OK;
+}
+
+extern "C" int hqs_batch_adjoint_axpy(hqs_batch b, const hqs_c64* const* y, float zc, const hqs_c64* const* z,
+                                      hqs_c64* const* x, void* stream) {
+    if (!b || !y || !x || !(zc == zc)) return HQS_ERR_INVALID_ARG;
+    for (int i = 0; i < b->ns; ++i)
+        if (!x[i] || (!y[i] && b->plans[i]->M > 0)) return HQS_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    auto X = reinterpret_cast<float2* const*>(x);
+    auto Z = reinterpret_cast<const float2* const*>(z);
+    HQS_TRY_RC(half_tables(b, 1, nullptr, X, Z, st));
+    // spreading per slice (the others take their whole per-slice adjoint)
+    for (int i = 0; i < b->ns; ++i) {
+        hqs_plan_s* p = b->plans[i];
+        const float2* yi = reinterpret_cast<const float2*>(y[i]);
+        if (plan_half_passes(p))
+            HQS_TRY_RC(launch_spread(p, yi, st));
+        else
+            HQS_TRY_RC(launch_adj_axpy(p, yi, zc, Z ? Z[i] : nullptr, X[i], st));
+    }
+    const size_t sz = half_args_bytes();
+    for (const auto& g : b->half_groups[1])
+        HQS_TRY_RC(launch_half_group(g.G, g.n, g.maxchunk, g.count,
+                                     static_cast<unsigned char*>(b->d_half[1]) + sz * g.first, 1, zc, st));
+    for (int i = 0; i < b->ns; ++i)
+        if (plan_half_passes(b->plans[i])) HQS_TRY_RC(launch_adj_chunks(b->plans[i], X[i], zc, Z ? Z[i] : nullptr, st));
+    return HQS_OK;
+}
+
+extern "C" int hqs_batch_forward(hqs_batch b, const hqs_c64* const* x, hqs_c64* const* y, void* stream) {
+    if (!b || !x || !y) return HQS_ERR_INVALID_ARG;
+    for (int i = 0; i < b->ns; ++i)
+        if (!x[i] || (!y[i] && b->plans[i]->M > 0)) return HQS_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    auto Xin = reinterpret_cast<const float2* const*>(x);
+    auto Y = reinterpret_cast<float2* const*>(y);
+    HQS_TRY_RC(half_tables(b, 0, Xin, nullptr, nullptr, st));
+    const size_t sz = half_args_bytes();
+    for (const auto& g : b->half_groups[0])
+        HQS_TRY_RC(launch_half_group(g.G, g.n, g.maxchunk, g.count,
+                                     static_cast<unsigned char*>(b->d_half[0]) + sz * g.first, 0, 0.f, st));
+    for (int i = 0; i < b->ns; ++i) {
+        hqs_plan_s* p = b->plans[i];
+        if (plan_half_passes(p))
+            HQS_TRY_RC(launch_interp(p, Y[i], st));
+        else
+            HQS_TRY_RC(launch_fwd(p, Xin[i], Y[i], st));
+    }
     return HQS_OK;
 }
 

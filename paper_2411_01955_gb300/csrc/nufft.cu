@@ -7,6 +7,7 @@
 // All grids are coil-innermost ([gy][gx][l]) so a grid tap is L contiguous
 // complex values.
 #include <algorithm>
+#include <cstring>
 
 #include "fft.cuh"
 #include "plan.cuh"
@@ -122,18 +123,31 @@ HQS_DEV float2 mul_mipow(float2 v, int k) {
     return neg ? make_float2(-re, -im) : make_float2(re, im);
 }
 
-template <int G>
-__global__ void k_fwd_rows_h(const float2* __restrict__ x, const float2* __restrict__ smaps,
-                             const float* __restrict__ apod, int n, int L, float scale,
-                             const float2* __restrict__ twg, float2* __restrict__ U) {
-    HQS_PDL_ENTRY();
-    extern __shared__ float2 s[];
-    const float2* tw = stage_twiddles<G>(s + G * kLines, twg);
-    const int iy = blockIdx.x, l0 = blockIdx.y * kLines;
-    const float ay = apod[iy] * scale;
-    const float2* xr = x + (int64_t)iy * n;
-    const float2* sm = smaps + (int64_t)iy * n * L + l0;
-    float2* dst = U + (int64_t)iy * G * L + l0;
+// Arguments of the lower-half FFT passes of one plan (G = 2n, chunks of 16 coils),
+// for the single-slice launches and, in a table over slices, the batched ones.
+struct HalfArgs {
+    const float2* x;       // forward: image
+    float2* xo;            // adjoint: image (out)
+    const float2* z;       // adjoint: xo = A^H y + zc z when z is given
+    float zc;
+    const float2* smaps;   // [n][n][L]
+    const float* apod;     // [n]
+    const float2* tw;      // G-point twiddles
+    float2* work;          // [n][G][L]
+    float2* grid;          // [G][G][L]
+    float2* part;          // [nchunk][n][n] coil-chunk sums (nchunk > 1)
+    int n, L, nchunk;
+    float scale;
+};
+
+template <int G> HQS_DEV void fwd_rows_h_item(const HalfArgs& A, int iy, int ch, float2* s) {
+    const float2* tw = stage_twiddles<G>(s + G * kLines, A.tw);
+    const int n = A.n, L = A.L, l0 = ch * kLines;
+    const float ay = A.apod[iy] * A.scale;
+    const float2* xr = A.x + (int64_t)iy * n;
+    const float2* sm = A.smaps + (int64_t)iy * n * L + l0;
+    const float* apod = A.apod;
+    float2* dst = A.work + (int64_t)iy * G * L + l0;
     __syncthreads();
     block_fft_io<G, false, true, false>(
         s, kLines, tw,
@@ -141,81 +155,104 @@ __global__ void k_fwd_rows_h(const float2* __restrict__ x, const float2* __restr
         NoIO{}, [&](int line, int k, float2 v) { dst[(int64_t)k * L + line] = mul_ipow(v, k); });
 }
 
-template <int G>
-__global__ void k_fwd_cols_h(const float2* __restrict__ U, int n, int L, const float2* __restrict__ twg,
-                             float2* __restrict__ Gh) {
-    HQS_PDL_ENTRY();
-    extern __shared__ float2 s[];
-    const float2* tw = stage_twiddles<G>(s + G * kLines, twg);
-    const int gx = blockIdx.x, l0 = blockIdx.y * kLines;
+template <int G> HQS_DEV void fwd_cols_h_item(const HalfArgs& A, int gx, int ch, float2* s) {
+    const float2* tw = stage_twiddles<G>(s + G * kLines, A.tw);
+    const int L = A.L, l0 = ch * kLines;
     const int64_t rs = (int64_t)G * L;
-    const float2* col = U + (int64_t)gx * L + l0;
-    float2* dst = Gh + (int64_t)gx * L + l0;
+    const float2* col = A.work + (int64_t)gx * L + l0;
+    float2* dst = A.grid + (int64_t)gx * L + l0;
     __syncthreads();
     block_fft_io<G, false, true, false>(
         s, kLines, tw, [&](int line, int q, bool) { return __ldg(col + q * rs + line); }, NoIO{},
         [&](int line, int k, float2 v) { dst[k * rs + line] = mul_ipow(v, k); });
 }
 
-template <int G>
-__global__ void k_adj_cols_h(const float2* __restrict__ Hg, int n, int L, const float2* __restrict__ twg,
-                             float2* __restrict__ V) {
-    HQS_PDL_ENTRY();
-    extern __shared__ float2 s[];
-    const float2* tw = stage_twiddles<G>(s + G * kLines, twg);
-    const int gx = blockIdx.x, l0 = blockIdx.y * kLines;
+template <int G> HQS_DEV void adj_cols_h_item(const HalfArgs& A, int gx, int ch, float2* s) {
+    const float2* tw = stage_twiddles<G>(s + G * kLines, A.tw);
+    const int L = A.L, l0 = ch * kLines;
     const int64_t rs = (int64_t)G * L;
-    const float2* col = Hg + (int64_t)gx * L + l0;
-    float2* dst = V + (int64_t)gx * L + l0;
+    const float2* col = A.grid + (int64_t)gx * L + l0;
+    float2* dst = A.work + (int64_t)gx * L + l0;
     __syncthreads();
     block_fft_io<G, true, false, true>(
         s, kLines, tw, [&](int line, int p, bool) { return mul_mipow(__ldg(col + p * rs + line), p); }, NoIO{},
         [&](int line, int q, float2 v) { dst[q * rs + line] = v; });
 }
 
-template <int G>
-__global__ void k_adj_rows_h(const float2* __restrict__ V, const float2* __restrict__ smaps,
-                             const float* __restrict__ apod, int n, int L, int nchunk, float scale,
-                             const float2* __restrict__ twg, float2* x, float2* __restrict__ part, float zc,
-                             const float2* z) {
-    HQS_PDL_ENTRY();
-    extern __shared__ float2 s[];
-    const float2* tw = stage_twiddles<G>(s + G * kLines, twg);
-    const int iy = blockIdx.x, l0 = blockIdx.y * kLines;
-    const float2* src = V + (int64_t)iy * G * L + l0;
+// The row's coil maps go with cp.async to the upper half of the lines buffer once
+// the last stage has read it (that stage keeps the lower half only), so their
+// latency overlaps the stage instead of following the transform.
+template <int G> HQS_DEV void adj_rows_h_item(const HalfArgs& A, int iy, int ch, float2* s) {
+    const float2* tw = stage_twiddles<G>(s + G * kLines, A.tw);
+    const int n = A.n, L = A.L, l0 = ch * kLines;
+    const float2* src = A.work + (int64_t)iy * G * L + l0;
+    const float2* sm = A.smaps + (int64_t)iy * n * L + l0;
+    float2* msm = s + (int64_t)n * kLines;   // upper half: [n][kLines]
+    bool issued = false;
     __syncthreads();
     block_fft_io<G, true, false, true>(
         s, kLines, tw, [&](int line, int p, bool) { return mul_mipow(__ldg(src + (int64_t)p * L + line), p); },
-        NoIO{}, NoIO{});
-    const float ay = apod[iy] * scale;
+        [&](int, int, float2 v) {
+            if (!issued) {   // every thread owns a line position (16 lines, blockDim = 16 TPL)
+                issued = true;
+                for (int e = threadIdx.x; e < n * (kLines / 2); e += blockDim.x) {
+                    const int ix = e / (kLines / 2), h = e - ix * (kLines / 2);
+                    cp_async16(msm + ix * kLines + 2 * h, sm + (int64_t)ix * L + 2 * h);
+                }
+            }
+            return v;
+        },
+        NoIO{});
+    cp_async_wait_all();
+    __syncthreads();
+    const float ay = A.apod[iy] * A.scale;
     for (int ix = threadIdx.x; ix < n; ix += blockDim.x) {
-        const float4* s4 = reinterpret_cast<const float4*>(smaps + ((int64_t)iy * n + ix) * L + l0);
+        const float4* s4 = reinterpret_cast<const float4*>(msm + ix * kLines);
         float2 a = make_float2(0.f, 0.f);
 #pragma unroll
         for (int h = 0; h < kLines / 2; ++h) {
-            const float4 sv = __ldg(s4 + h);
+            const float4 sv = s4[h];
             const float2 g0 = s[ix * kLines + 2 * h], g1 = s[ix * kLines + 2 * h + 1];
             a.x += sv.x * g0.x + sv.y * g0.y + sv.z * g1.x + sv.w * g1.y;
             a.y += sv.x * g0.y - sv.y * g0.x + sv.z * g1.y - sv.w * g1.x;
         }
-        if (nchunk == 1) {
+        if (A.nchunk == 1) {
             const int64_t e = (int64_t)iy * n + ix;
-            float2 v = cscale(a, ay * apod[ix]);
-            if (z) {
-                const float2 zv = z[e];
-                v.x = fmaf(zc, zv.x, v.x);
-                v.y = fmaf(zc, zv.y, v.y);
+            float2 v = cscale(a, ay * A.apod[ix]);
+            if (A.z) {
+                const float2 zv = A.z[e];
+                v.x = fmaf(A.zc, zv.x, v.x);
+                v.y = fmaf(A.zc, zv.y, v.y);
             }
-            x[e] = v;
+            A.xo[e] = v;
         } else {
-            part[((int64_t)blockIdx.y * n + iy) * n + ix] = a;
+            A.part[((int64_t)ch * n + iy) * n + ix] = a;
         }
     }
 }
 
-// Type-2 interpolation: 16 lanes per point (lane = coil, looping over coils
-// beyond 16), the 2W separable weights computed once per point by lanes
-// 0..2W-1 and broadcast with shuffles.
+// single slice: grid (rows or columns, chunks); batched: grid (rows or columns,
+// largest chunk count, slices), the slice's arguments from a device table
+#define HQS_HALF_KERNELS(NAME)                                                            \
+    template <int G> __global__ void k_##NAME(HalfArgs A) {                               \
+        HQS_PDL_ENTRY();                                                                  \
+        extern __shared__ __align__(16) float2 s[];                                       \
+        NAME##_item<G>(A, blockIdx.x, blockIdx.y, s);                                     \
+    }                                                                                     \
+    template <int G> __global__ void k_##NAME##_b(const HalfArgs* __restrict__ tab, float zc) { \
+        HQS_PDL_ENTRY();                                                                  \
+        extern __shared__ __align__(16) float2 s[];                                       \
+        HalfArgs A = tab[blockIdx.z];                                                     \
+        A.zc = zc;                                                                        \
+        if ((int)blockIdx.y >= A.nchunk) return;                                          \
+        NAME##_item<G>(A, blockIdx.x, blockIdx.y, s);                                     \
+    }
+HQS_HALF_KERNELS(fwd_rows_h)
+HQS_HALF_KERNELS(fwd_cols_h)
+HQS_HALF_KERNELS(adj_cols_h)
+HQS_HALF_KERNELS(adj_rows_h)
+#undef HQS_HALF_KERNELS
+
 template <int W>
 __global__ void __launch_bounds__(256) k_interp(const float2* __restrict__ Gh, const int4* __restrict__ pts,
                                                 const int* __restrict__ perm, int M, int G, int L,
@@ -671,6 +708,25 @@ __global__ void k_adj_chunk_sum(const float2* __restrict__ part, const float* __
 // the lower-half passes apply when G = 2n and every coil chunk has 16 coils
 inline bool half_passes(const hqs_plan_s* p) { return p->G == 2 * p->n && p->LC == kLines && p->L % kLines == 0; }
 
+static HalfArgs half_args(const hqs_plan_s* p, const float2* x, float2* xo, float zc, const float2* z) {
+    HalfArgs A;
+    A.x = x;
+    A.xo = xo;
+    A.z = z;
+    A.zc = zc;
+    A.smaps = p->smaps;
+    A.apod = p->apod;
+    A.tw = plan_twiddles(p, p->G);
+    A.work = p->work;
+    A.grid = p->grid;
+    A.part = p->chunk_buf;
+    A.n = p->n;
+    A.L = p->L;
+    A.nchunk = p->nchunk;
+    A.scale = p->scale;
+    return A;
+}
+
 template <int G>
 static int fwd_fft_impl(hqs_plan_s* p, const float2* x, cudaStream_t st) {
     const float2* tw = plan_twiddles(p, G);
@@ -679,9 +735,9 @@ static int fwd_fft_impl(hqs_plan_s* p, const float2* x, cudaStream_t st) {
     if (half_passes(p)) {
         HQS_CUDA_TRY(cudaFuncSetAttribute(k_fwd_rows_h<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         HQS_CUDA_TRY(cudaFuncSetAttribute(k_fwd_cols_h<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        HQS_CUDA_TRY(launch_pdl(k_fwd_rows_h<G>, dim3(p->n, p->nchunk), th, sm, st, x, p->smaps, p->apod, p->n, p->L,
-                                p->scale, tw, p->work));
-        HQS_CUDA_TRY(launch_pdl(k_fwd_cols_h<G>, dim3(G, p->nchunk), th, sm, st, p->work, p->n, p->L, tw, p->grid));
+        const HalfArgs A = half_args(p, x, nullptr, 0.f, nullptr);
+        HQS_CUDA_TRY(launch_pdl(k_fwd_rows_h<G>, dim3(p->n, p->nchunk), th, sm, st, A));
+        HQS_CUDA_TRY(launch_pdl(k_fwd_cols_h<G>, dim3(G, p->nchunk), th, sm, st, A));
         HQS_CUDA_TRY(cudaGetLastError());
         return HQS_OK;
     }
@@ -703,9 +759,9 @@ static int adj_fft_impl(hqs_plan_s* p, float2* x, float zc, const float2* z, cud
     if (half_passes(p)) {
         HQS_CUDA_TRY(cudaFuncSetAttribute(k_adj_cols_h<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         HQS_CUDA_TRY(cudaFuncSetAttribute(k_adj_rows_h<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        HQS_CUDA_TRY(launch_pdl(k_adj_cols_h<G>, dim3(G, p->nchunk), th, sm, st, p->grid, p->n, p->L, tw, p->work));
-        HQS_CUDA_TRY(launch_pdl(k_adj_rows_h<G>, dim3(p->n, p->nchunk), th, sm, st, p->work, p->smaps, p->apod, p->n,
-                                p->L, p->nchunk, p->scale, tw, x, p->chunk_buf, zc, z));
+        const HalfArgs A = half_args(p, nullptr, x, zc, z);
+        HQS_CUDA_TRY(launch_pdl(k_adj_cols_h<G>, dim3(G, p->nchunk), th, sm, st, A));
+        HQS_CUDA_TRY(launch_pdl(k_adj_rows_h<G>, dim3(p->n, p->nchunk), th, sm, st, A));
         if (p->nchunk > 1)
             HQS_CUDA_TRY(launch_pdl(k_adj_chunk_sum, dim3(std::min(ceil_div(p->n * p->n, 256), 1024)), dim3(256), 0, st,
                                     p->chunk_buf, p->apod, p->n, p->nchunk, p->scale, x, zc, z));
@@ -830,6 +886,57 @@ int launch_adj_axpy(hqs_plan_s* p, const float2* y, float zc, const float2* z, f
     int rc = dispatch_w(p->W, [&]<int WW>() { return spread_impl<WW>(p, y, st); });
     if (rc != HQS_OK) return rc;
     return dispatch_fft_size(p->G, [&]<int GG>() { return adj_fft_impl<GG>(p, x, zc, z, st); });
+}
+
+// ---- the passes of several plans in one launch per pass (batched operators)
+bool plan_half_passes(const hqs_plan_s* p) { return half_passes(p); }
+size_t half_args_bytes() { return sizeof(HalfArgs); }
+void fill_half_args(const hqs_plan_s* p, const float2* x, float2* xo, const float2* z, void* dst) {
+    const HalfArgs A = half_args(p, x, xo, 0.f, z);
+    std::memcpy(dst, &A, sizeof(HalfArgs));
+}
+
+// `count` plans with grid G = 2n and 16-coil chunks whose arguments are the
+// consecutive HalfArgs at d_tab: the forward's row and column passes (adjoint 0)
+// or the adjoint's column and row passes (adjoint 1), grid (lines, chunks, plans)
+int launch_half_group(int G, int n, int maxchunk, int count, const void* d_tab, int adjoint, float zc,
+                      cudaStream_t st) {
+    return dispatch_fft_size(G, [&]<int GG>() -> int {
+        if constexpr (GG % 2 != 0 || GG < 32) {
+            return HQS_ERR_UNSUPPORTED;
+        } else {
+            const int th = fft_threads<GG>(kLines);
+            const size_t sm = nufft_smem_floats2<GG>() * sizeof(float2);
+            const HalfArgs* tab = static_cast<const HalfArgs*>(d_tab);
+            if (adjoint) {
+                HQS_CUDA_TRY(cudaFuncSetAttribute(k_adj_cols_h_b<GG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+                HQS_CUDA_TRY(cudaFuncSetAttribute(k_adj_rows_h_b<GG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+                HQS_CUDA_TRY(launch_pdl(k_adj_cols_h_b<GG>, dim3(GG, maxchunk, count), th, sm, st, tab, zc));
+                HQS_CUDA_TRY(launch_pdl(k_adj_rows_h_b<GG>, dim3(n, maxchunk, count), th, sm, st, tab, zc));
+            } else {
+                HQS_CUDA_TRY(cudaFuncSetAttribute(k_fwd_rows_h_b<GG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+                HQS_CUDA_TRY(cudaFuncSetAttribute(k_fwd_cols_h_b<GG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+                HQS_CUDA_TRY(launch_pdl(k_fwd_rows_h_b<GG>, dim3(n, maxchunk, count), th, sm, st, tab, zc));
+                HQS_CUDA_TRY(launch_pdl(k_fwd_cols_h_b<GG>, dim3(GG, maxchunk, count), th, sm, st, tab, zc));
+            }
+            HQS_CUDA_TRY(cudaGetLastError());
+            return HQS_OK;
+        }
+    });
+}
+
+// the parts of the operators outside the lower-half passes, per plan
+int launch_spread(hqs_plan_s* p, const float2* y, cudaStream_t st) {
+    return dispatch_w(p->W, [&]<int WW>() { return spread_impl<WW>(p, y, st); });
+}
+int launch_interp(hqs_plan_s* p, float2* y, cudaStream_t st) {
+    return dispatch_w(p->W, [&]<int WW>() { return interp_impl<WW>(p, y, st); });
+}
+int launch_adj_chunks(hqs_plan_s* p, float2* x, float zc, const float2* z, cudaStream_t st) {
+    if (p->nchunk <= 1) return HQS_OK;
+    HQS_CUDA_TRY(launch_pdl(k_adj_chunk_sum, dim3(std::min(ceil_div(p->n * p->n, 256), 1024)), dim3(256), 0, st,
+                            p->chunk_buf, p->apod, p->n, p->nchunk, p->scale, x, zc, z));
+    return HQS_OK;
 }
 
 int launch_adj(hqs_plan_s* p, const float2* y, float2* x, cudaStream_t st) {

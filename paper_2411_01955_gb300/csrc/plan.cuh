@@ -121,6 +121,16 @@ void mixed_free(hqs_plan_s* p);
 int launch_fwd(hqs_plan_s* p, const float2* x, float2* y, cudaStream_t s);
 int launch_adj(hqs_plan_s* p, const float2* y, float2* x, cudaStream_t s);
 int launch_adj_axpy(hqs_plan_s* p, const float2* y, float zc, const float2* z, float2* x, cudaStream_t s);
+// batched operators (csrc/nufft.cu): per-plan pieces and the lower-half passes of
+// a group of plans (G = 2n, 16-coil chunks) in one launch per pass
+bool plan_half_passes(const hqs_plan_s* p);
+size_t half_args_bytes();
+void fill_half_args(const hqs_plan_s* p, const float2* x, float2* xo, const float2* z, void* dst);
+int launch_half_group(int G, int n, int maxchunk, int count, const void* d_tab, int adjoint, float zc,
+                      cudaStream_t s);
+int launch_spread(hqs_plan_s* p, const float2* y, cudaStream_t s);
+int launch_interp(hqs_plan_s* p, float2* y, cudaStream_t s);
+int launch_adj_chunks(hqs_plan_s* p, float2* x, float zc, const float2* z, cudaStream_t s);
 int launch_toeplitz(hqs_plan_s* p, const float2* x, float2* out, cudaStream_t s);
 int launch_fft2d(const hqs_plan_s* p, float2* data, int N, bool inverse, cudaStream_t s);
 int launch_precond(hqs_plan_s* p, float a, float b, const float2* r, float2* z, cudaStream_t s);

@@ -184,6 +184,30 @@ def test_brain_batched_solve_16_slices_matches_oracle():
         assert tres[i] <= 1.2e-4
 
 
+def test_brain_batched_toeplitz_normal_16_slices_matches_oracle():
+    """hqs_batch_toeplitz_normal as the benchmark launches it
+    (`aha_applies_per_s_batched`): 16 slices of the spiral workload, one plan
+    each, in one cooperative launch; every slice's A^H A x against the FP64
+    oracle's Toeplitz normal operator at the single-operator bar."""
+    n, L, B = 320, 16, 16
+    traj = synth.traj_spiral(16, 2048, n)
+    cases = [quantised(dict(n=n, L=L, W=6, sigma=2.0, x=synth.phantom(s, n), smaps=synth.coil_maps(s, n, L),
+                            traj=traj)) for s in range(B)]
+    Kh, _ = jobs.slice_operators(traj, n)
+    with jobs.pool(B) as ex:
+        fut = list(ex.map(jobs.normal_rhs, [c["smaps"] for c in cases], [Kh] * B, [0.0] * B,
+                          [c["x"] for c in cases]))
+        plans = [make_plan(c)[0] for c in cases]
+        batch = hq().Batch(plans, max_outer=1)
+        xs = [to_dev(c["x"]) for c in cases]
+        outs = [torch.empty_like(x) for x in xs]
+        batch.toeplitz_normal(xs, outs)
+        got = [to_host(o) for o in outs]
+    for i, (g, want) in enumerate(zip(got, fut)):
+        print(f"batched A^H A, slice {i}: {rel(g, want):.2e}")
+        assert rel(g, want) <= TOL, (i, rel(g, want))
+
+
 def mixed_size_cases():
     """A 384^2 slice (768-point lines; 12 coils, 48 radial spokes x 768) and
     a 320^2 slice of the spiral workload, as the batched workload mixes them."""
