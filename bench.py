@@ -6,7 +6,8 @@ with A^H A applies per second and the per-stage (plain) PCG path beside it.
 A step is one DC solve for each slice of a batch of B slices: A^H y
 (adjoint NUFFT), rhs = A^H y + mu z, and the preconditioned CG solve of
 (A^H A + mu I) x = rhs, each slice with its own phantom and coil maps (one
-plan per slice).  By default (--mode batched) the B solves run in one
+plan per slice).  By default (--mode batched) the B right-hand sides come from
+the batched adjoint (hqs_batch_adjoint_axpy) and the B solves run in one
 cooperative launch (hqs_batch_dc_solve), each slice to its own tolerance;
 --mode fused launches the persistent solve once per slice, --mode plain
 the per-stage PCG.  The batch's resident inputs exceed the 129 MB L2, so no
