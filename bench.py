@@ -104,9 +104,10 @@ ADJ_BYTES = (_Y + _PTS + _G2L) + (_G2L + _ROWS) + (_ROWS + _S + 320 * 320 * 8)
 # capture of the current kernel (profiles/pcg_persistent_320x16.md); None while
 # the kernel has changed since the last capture.
 PERSISTENT_TRAFFIC_BYTES = None
-# The same for one k_pcg_batch launch (all 16 slices of a default step), from the
-# capture in profiles/pcg_batch_320x16_16slices.md; None until captured.
-BATCH_TRAFFIC_BYTES = 45479788544 + 31168711424
+# The same for the batched solves of one default step (two concurrent k_pcg_batch
+# launches of 8 slices: the sum of both launches' bytes, each captured alone), from
+# profiles/pcg_batch_320x16_16slices.md; None until captured.
+BATCH_TRAFFIC_BYTES = None
 
 
 def parse():
@@ -118,6 +119,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="batched", choices=["batched", "fused", "plain"])
     ap.add_argument("--group", type=int, default=64, help="slices per batched launch (at most 64)")
+    ap.add_argument("--streams", type=int, default=2,
+                    help="batched mode: the slices split into this many groups, each its own batched "
+                         "launch on its own stream with an equal share of the resident CTAs")
     ap.add_argument("--phase-trace", action="store_true",
                     help="batched dc320: add the per-phase time of one traced batched solve to the line")
     ap.add_argument("--workload", default="dc320",
@@ -335,15 +339,39 @@ def run_ours(args, rank, world, dist):
         zs.append(z)
         rhss.append(torch.empty_like(x))
         xs.append(torch.zeros_like(x))
-    G_ = max(1, min(args.group, B))
+    nstreams = max(1, args.streams) if args.mode == "batched" else 1
+    G_ = max(1, min(args.group, math.ceil(B / nstreams), B))
     groups = [list(range(i, min(i + G_, B))) for i in range(0, B, G_)]
     batches = [hq.Batch([plans[i] for i in g], max_outer=1) for g in groups] if args.mode == "batched" else []
     stream = torch.cuda.current_stream()
+    # concurrent groups: each batched launch gets an equal share of the CTAs the batch
+    # kernels keep resident (two per SM), so the launches run side by side and one
+    # launch's grid barriers do not idle the other's CTAs
+    gstreams = [torch.cuda.Stream() for _ in groups] if len(groups) > 1 else [stream]
+    if len(groups) > 1:
+        cap = 2 * torch.cuda.get_device_properties(dev).multi_processor_count // len(groups)
+        for bt in batches:
+            bt.set_grid(cap)
+
+    def on_group_streams(fn):
+        # fn(group index, stream) on each group's stream, ordered after and before the main stream
+        if len(gstreams) == 1:
+            for k in range(len(groups)):
+                fn(k, stream)
+            return
+        for gs in gstreams:
+            gs.wait_stream(stream)
+        for k, gs in enumerate(gstreams):
+            with torch.cuda.stream(gs):
+                fn(k, gs)
+        for gs in gstreams:
+            stream.wait_stream(gs)
 
     def solve_all(mode_):
         if mode_ == "batched":
-            for g, bt in zip(groups, batches):
-                bt.dc_solve([rhss[i] for i in g], [xs[i] for i in g], 1.0, MU, max_iter=MAX_ITER, rel_tol=TOL)
+            on_group_streams(lambda k, gs: batches[k].dc_solve(
+                [rhss[i] for i in groups[k]], [xs[i] for i in groups[k]], 1.0, MU, max_iter=MAX_ITER, rel_tol=TOL,
+                stream=gs))
             return
         flag = hq.HQS_SOLVE_FUSED if mode_ == "fused" else hq.HQS_SOLVE_PLAIN
         for i in range(B):
@@ -353,12 +381,17 @@ def run_ours(args, rank, world, dist):
     def step(mode_=args.mode, ys_=None):
         yy = ys if ys_ is None else ys_
         if mode_ == "batched":
-            # A^H y + mu z of every slice of a group: the FFT passes batched
-            for g, bt in zip(groups, batches):
-                bt.adjoint_axpy([yy[i] for i in g], MU, [zs[i] for i in g], [rhss[i] for i in g])
-        else:
-            for i in range(B):
-                hq.adjoint_axpy(plans[i], yy[i], MU, zs[i], rhss[i])
+            # per group on its stream: A^H y + mu z of its slices (the FFT passes
+            # batched), then its batched solve
+            def grp(k, gs):
+                g = groups[k]
+                batches[k].adjoint_axpy([yy[i] for i in g], MU, [zs[i] for i in g], [rhss[i] for i in g], stream=gs)
+                batches[k].dc_solve([rhss[i] for i in g], [xs[i] for i in g], 1.0, MU, max_iter=MAX_ITER,
+                                    rel_tol=TOL, stream=gs)
+            on_group_streams(grp)
+            return
+        for i in range(B):
+            hq.adjoint_axpy(plans[i], yy[i], MU, zs[i], rhss[i])
         solve_all(mode_)
 
     def barrier():
@@ -416,8 +449,15 @@ def run_ours(args, rank, world, dist):
         e_solve.append((e0, e1))
     torch.cuda.synchronize()
     launch_ms = float(np.mean([a.elapsed_time(b) for a, b in e_solve[1:]]))
-    solves_per_launch = len(groups[0]) if args.mode == "batched" else 1
-    solve_ms = launch_ms / (len(groups) if args.mode == "batched" else B)   # per launch
+    # the unit of the roofline: the concurrent batched launches of all groups together,
+    # else one launch
+    concurrent = args.mode == "batched" and len(gstreams) > 1
+    if args.mode == "batched":
+        solves_per_launch = B if concurrent else len(groups[0])
+        solve_ms = launch_ms if concurrent else launch_ms / len(groups)
+    else:
+        solves_per_launch = 1
+        solve_ms = launch_ms / B
     mean_iters = float(np.mean(iters))
 
     # plain PCG (per-stage launches, host-checked residual) and A^H A applies/s
@@ -437,8 +477,8 @@ def run_ours(args, rank, world, dist):
     aha_batched_per_s = None
     if batches:
         def applies_batched():
-            for g, bt in zip(groups, batches):
-                bt.toeplitz_normal([zs[i] for i in g], [outs[i] for i in g])
+            on_group_streams(lambda k, gs: batches[k].toeplitz_normal(
+                [zs[i] for i in groups[k]], [outs[i] for i in groups[k]], stream=gs))
         for _ in range(3):
             applies_batched()
         ms_ahab = timed(applies_batched, reps)
@@ -465,12 +505,12 @@ def run_ours(args, rank, world, dist):
     fwd_batched_per_s = adj_batched_per_s = None
     if batches:
         def forwards_b():
-            for g, bt in zip(groups, batches):
-                bt.forward([xs_img[i] for i in g], [ys_out[i] for i in g])
+            on_group_streams(lambda k, gs: batches[k].forward(
+                [xs_img[i] for i in groups[k]], [ys_out[i] for i in groups[k]], stream=gs))
 
         def adjoints_b():
-            for g, bt in zip(groups, batches):
-                bt.adjoint_axpy([ys[i] for i in g], 0.0, None, [outs[i] for i in g])
+            on_group_streams(lambda k, gs: batches[k].adjoint_axpy(
+                [ys[i] for i in groups[k]], 0.0, None, [outs[i] for i in groups[k]], stream=gs))
         forwards_b()
         adjoints_b()
         fwd_batched_per_s = B * reps * world / (timed(forwards_b, reps) / 1e3)
@@ -554,7 +594,9 @@ def run_ours(args, rank, world, dist):
         "data": "synthetic (seeded ellipse phantoms, Gaussian-bump coil maps, VD spiral)",
         "config": {"workload": WORKLOAD,
                    "batch_per_gpu": B, "solver": args.mode,
-                   "slices_per_launch": len(groups[0]) if args.mode == "batched" else 1, "parallelism": f"replicas x{world}",
+                   "slices_per_launch": len(groups[0]) if args.mode == "batched" else 1,
+                   "concurrent_launches": len(gstreams) if args.mode == "batched" else 1,
+                   "parallelism": f"replicas x{world}",
                    "tuning": {"spread_tile": tuned.spread_tile, "pc_lines": tuned.pc_lines,
                               "fused_grid": tuned.fused_grid},
                    "l2": "inputs larger than L2 (batch of distinct slices), no flush"},
@@ -579,8 +621,10 @@ def run_ours(args, rank, world, dist):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
                      "traffic": BATCH_TRAFFIC_BYTES if args.mode == "batched" else PERSISTENT_TRAFFIC_BYTES,
-                     "kernel": (f"k_pcg_batch ({len(groups[0])} slices per launch)" if args.mode == "batched"
-                                else "k_pcg_persistent<640,320>"),
+                     "kernel": ((f"k_pcg_batch ({len(groups)} concurrent launches of {len(groups[0])} slices, "
+                                 f"each on {2 * torch.cuda.get_device_properties(dev).multi_processor_count // len(groups)} CTAs)"
+                                 if concurrent else f"k_pcg_batch ({len(groups[0])} slices per launch)")
+                                if args.mode == "batched" else "k_pcg_persistent<640,320>"),
                      "flops_per_launch": flops_launch, "launch_ms": solve_ms,
                      "peak_source": f"unit counts: 152 SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz "
                                     f"(maximum SM clock)",

@@ -338,6 +338,12 @@ HQS_API int hqs_pgd_run(hqs_plan plan, const hqs_c64* y, hqs_c64* x, const float
  * synchronises and reports, per slice, the relative CG residual of the last
  * data-consistency step. */
 HQS_API int hqs_batch_create(hqs_batch* out, hqs_plan* plans, int n, int max_outer);
+/* Caps the CTAs of the batch's cooperative launches (0, the default: every CTA
+ * the kernel keeps resident, two per SM).  With a cap of one CTA per SM, two
+ * batches launched on two streams can run side by side, each CTA's grid
+ * barriers independent of the other batch's.  No counterpart in the paper: a
+ * launch-shape setting. */
+HQS_API int hqs_batch_set_grid(hqs_batch batch, int ctas);
 HQS_API void hqs_batch_destroy(hqs_batch batch);
 HQS_API int hqs_batch_run(hqs_batch batch, const hqs_c64* const* y, hqs_c64* const* x,
                           const float* mu, const float* sigma, int K, int k0, int cg_iters,

@@ -125,6 +125,7 @@ _SIGS = {
     "hqs_batch_dc_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_int),
                                     C.c_void_p]),
     "hqs_batch_toeplitz_normal": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_void_p]),
+    "hqs_batch_set_grid": (C.c_int, [C.c_void_p, C.c_int]),
     "hqs_batch_forward": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_void_p]),
     "hqs_batch_adjoint_axpy": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.c_float, C.POINTER(C.c_void_p),
                                          C.POINTER(C.c_void_p), C.c_void_p]),
@@ -598,6 +599,10 @@ class Batch:
         _check(library().hqs_batch_dc_solve(self.handle, rp, xp, float(a), float(b), int(max_iter),
                                             float(rel_tol), _stream(stream)), "hqs_batch_dc_solve")
         return xs
+
+    def set_grid(self, ctas):
+        """Caps the CTAs of the batch's cooperative launches (0: all resident)."""
+        _check(library().hqs_batch_set_grid(self.handle, int(ctas)), "hqs_batch_set_grid")
 
     def toeplitz_normal(self, xs, outs, stream=None):
         """out_i = A_i^H A_i x_i for every slice in one launch."""

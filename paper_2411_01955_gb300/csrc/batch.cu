@@ -913,12 +913,13 @@ struct hqs_batch_s {
     float* h_mu = nullptr;        // pinned staging (read when the graph replays)
     float* h_taps = nullptr;
     int* h_radius = nullptr;
-    int grid = 0;
+    int grid = 0;        // CTAs of a launch: every resident CTA of the kernel
+    int grid_cap = 0;    // hqs_batch_set_grid: at most this many (0: no cap)
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     std::vector<const void*> key;  // y / x pointers the graph was recorded with
-    int key_K = -1, key_k0 = -1, key_cg = -1;
+    int key_K = -1, key_k0 = -1, key_cg = -1, key_grid = -1;
     float key_c0 = 0.f, key_c1 = 0.f;
     std::vector<float2*> chunks;   // per-slice coil-chunk partial sums
     // batched data-consistency solve: its own slice table (u = x, rhs = the
@@ -972,6 +973,19 @@ static void batch_free(hqs_batch_s* b) {
 }
 
 extern "C" void hqs_batch_destroy(hqs_batch b) { batch_free(b); }
+
+// CTAs of one cooperative launch of a batch kernel: every CTA the kernel keeps
+// resident (at most b->grid, the partial-sum slots), or the caller's cap
+static int batch_grid(const hqs_batch_s* b, int resident) {
+    const int g = std::min(b->grid, resident);
+    return b->grid_cap > 0 ? std::min(g, b->grid_cap) : g;
+}
+
+extern "C" int hqs_batch_set_grid(hqs_batch b, int ctas) {
+    if (!b || ctas < 0) return HQS_ERR_INVALID_ARG;
+    b->grid_cap = ctas;
+    return HQS_OK;
+}
 
 
 // preconditioner lines per item for a slice of size n (host side of batch_pq)
@@ -1099,7 +1113,7 @@ static int batch_enqueue(hqs_batch_s* b, const hqs_c64* const* y, hqs_c64* const
     A.bar = b->d_bar;
     A.err = b->d_err;
     void* args[] = {&A};
-    HQS_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_hqs_batch, dim3(b->grid), dim3(HQS_BATCH_BD), args,
+    HQS_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_hqs_batch, dim3(batch_grid(b, b->grid)), dim3(HQS_BATCH_BD), args,
                                              kBatchSmemF2 * sizeof(float2), st));
     return HQS_OK;
 }
@@ -1152,7 +1166,7 @@ extern "C" int hqs_batch_run(hqs_batch b, const hqs_c64* const* y, hqs_c64* cons
         key.push_back(x[i]);
     }
     if (!b->exec || key != b->key || K != b->key_K || k0 != b->key_k0 || cg_iters != b->key_cg || c0 != b->key_c0 ||
-        c1 != b->key_c1) {
+        c1 != b->key_c1 || b->grid_cap != b->key_grid) {
         if (b->exec) cudaGraphExecDestroy(b->exec);
         if (b->graph) cudaGraphDestroy(b->graph);
         b->exec = nullptr;
@@ -1174,6 +1188,7 @@ extern "C" int hqs_batch_run(hqs_batch b, const hqs_c64* const* y, hqs_c64* cons
         b->key_cg = cg_iters;
         b->key_c0 = c0;
         b->key_c1 = c1;
+        b->key_grid = b->grid_cap;
     }
     HQS_CUDA_TRY(cudaGraphLaunch(b->exec, st));
     return HQS_OK;
@@ -1241,7 +1256,7 @@ extern "C" int hqs_batch_dc_solve(hqs_batch b, const hqs_c64* const* rhs, hqs_c6
     HQS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_batch, HQS_BATCH_BD, sm));
     HQS_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->device));
     if (per_sm < 1) return HQS_ERR_UNSUPPORTED;
-    const int grid = std::min(b->grid, per_sm * nsm);   // d_part holds b->grid partials per slot
+    const int grid = batch_grid(b, per_sm * nsm);   // d_part holds b->grid partials per slot
     void* args[] = {&A};
     HQS_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_pcg_batch, dim3(grid), dim3(HQS_BATCH_BD), args, sm, st));
     return HQS_OK;
@@ -1283,7 +1298,7 @@ extern "C" int hqs_batch_toeplitz_normal(hqs_batch b, const hqs_c64* const* x, h
     HQS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_aha_batch, HQS_BATCH_BD, sm));
     HQS_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->device));
     if (per_sm < 1) return HQS_ERR_UNSUPPORTED;
-    const int grid = per_sm * nsm;
+    const int grid = batch_grid(b, per_sm * nsm);
     void* args[] = {&A};
     HQS_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_aha_batch, dim3(grid), dim3(HQS_BATCH_BD), args, sm, st));
     return HQS_OK;
