@@ -231,6 +231,64 @@ def test_batched_forward_and_adjoint_match_oracle_and_per_slice():
         batch.forward(xs[:-1], ys[:-1])
 
 
+def test_batched_solves_side_by_side_on_capped_grids():
+    """hqs_batch_set_grid: two batches with their launches capped at 152 and 76
+    CTAs, solving on two streams at once, solve every slice to the tolerance with
+    the iteration count of one uncapped batch of all slices (within 15 %: the
+    fp64 reductions are split over fewer CTAs), and a capped A^H A equals the
+    uncapped one bit for bit (no reduction across CTAs)."""
+    slices = build(slice_cases())
+    plans = [p for _, p, _ in slices]
+    rng = np.random.default_rng(5)
+    rhs = [to_dev((rng.normal(size=(c["n"], c["n"])) + 1j * rng.normal(size=(c["n"], c["n"]))).astype(np.complex64))
+           for c, _, _ in slices]
+    one = hq().Batch(plans, max_outer=1)
+    xs1 = [torch.zeros_like(r) for r in rhs]
+    one.dc_solve(rhs, xs1, 1.0, 1e-2, max_iter=200, rel_tol=1e-4)
+    info1 = one.dc_info()
+    outs1 = [torch.empty_like(r) for r in rhs]
+    one.toeplitz_normal(rhs, outs1)
+    ref = [to_host(x) for x in xs1]
+    aha = [to_host(o) for o in outs1]
+    one.close()
+    parts = [[0, 1], [2, 3, 4]]
+    bs = [hq().Batch([plans[i] for i in g], max_outer=1) for g in parts]
+    bs[0].set_grid(152)
+    bs[1].set_grid(76)
+    xs2 = [torch.zeros_like(r) for r in rhs]
+    sts = [torch.cuda.Stream(), torch.cuda.Stream()]
+    main = torch.cuda.current_stream()
+    for s_ in sts:
+        s_.wait_stream(main)
+    for b, g, s_ in zip(bs, parts, sts):
+        with torch.cuda.stream(s_):
+            b.dc_solve([rhs[i] for i in g], [xs2[i] for i in g], 1.0, 1e-2, max_iter=200, rel_tol=1e-4, stream=s_)
+    for s_ in sts:
+        main.wait_stream(s_)
+    info2 = bs[0].dc_info() + bs[1].dc_info()
+    for i, (a, b) in enumerate(zip(info1, info2)):
+        assert a[2] == 0 and b[2] == 0 and iterations_agree(a[0], b[0]), (i, a, b)
+        # both runs reach the tolerance on the CG recursion; their true residuals (by
+        # the library's float32 operator: the recursion drifts from them by the
+        # operator's rounding, here on random right-hand sides) agree, and so do the
+        # solutions, to the accuracy that tolerance allows
+        assert a[1] <= 1e-4 and b[1] <= 1e-4, (i, a, b)
+        tres = []
+        for x in (xs1[i], xs2[i]):
+            hx = torch.empty_like(x)
+            hq().toeplitz_normal(plans[i], x, hx)
+            tres.append(float(torch.linalg.vector_norm(rhs[i] - hx - 1e-2 * x) / torch.linalg.vector_norm(rhs[i])))
+        assert max(tres) <= 3e-4 and abs(tres[0] - tres[1]) <= 1e-4, (i, tres)
+        assert rel(to_host(xs2[i]), ref[i]) <= 1e-2, (i, rel(to_host(xs2[i]), ref[i]))
+    outs2 = [torch.empty_like(r) for r in rhs]
+    for b, g in zip(bs, parts):
+        b.toeplitz_normal([rhs[i] for i in g], [outs2[i] for i in g])
+    for o, w in zip(outs2, aha):
+        assert np.array_equal(to_host(o), w)
+    with pytest.raises(hq().HqsError):
+        bs[0].set_grid(-1)
+
+
 def test_batched_dc_solve_matches_oracle_and_per_slice_solves():
     """One launch, DC-preconditioned CG for every slice: 5 fixed iterations
     match the oracle's PCG per slice within max(1e-5, 4x the oracle's own
