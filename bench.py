@@ -107,7 +107,7 @@ PERSISTENT_TRAFFIC_BYTES = None
 # The same for the batched solves of one default step (two concurrent k_pcg_batch
 # launches of 8 slices: the sum of both launches' bytes, each captured alone), from
 # profiles/pcg_batch_320x16_16slices.md; None until captured.
-BATCH_TRAFFIC_BYTES = None
+BATCH_TRAFFIC_BYTES = 19029755136 + 13915506944 + 20309124608 + 14937506560
 
 
 def parse():
