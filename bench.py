@@ -6,15 +6,18 @@ with A^H A applies per second and the per-stage (plain) PCG path beside it.
 A step is one DC solve for each slice of a batch of B slices: A^H y
 (adjoint NUFFT), rhs = A^H y + mu z, and the preconditioned CG solve of
 (A^H A + mu I) x = rhs, each slice with its own phantom and coil maps (one
-plan per slice).  By default (--mode batched) the B right-hand sides come from
-the batched adjoint (hqs_batch_adjoint_axpy) and the B solves run in one
-cooperative launch (hqs_batch_dc_solve), each slice to its own tolerance;
+plan per slice).  By default (--mode batched) the B slices form --streams
+groups (2), each a batch on its own stream whose cooperative launches take an
+equal share of the resident CTAs (hqs_batch_set_grid), so the groups run side by
+side; per group the right-hand sides come from the batched adjoint
+(hqs_batch_adjoint_axpy) and the solves run in one cooperative launch
+(hqs_batch_dc_solve), each slice to its own tolerance;
 --mode fused launches the persistent solve once per slice, --mode plain
 the per-stage PCG.  The batch's resident inputs exceed the 129 MB L2, so no
 explicit flush is needed between steps.  Inputs are synthetic (seeded
 ellipse phantoms, Gaussian-bump coil maps, spiral trajectory).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B] [--mode batched|fused|plain]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B] [--mode batched|fused|plain] [--streams S]
                   [--impl ours|reference]
   python bench.py --workload batch64     # 64 uneven slices, batched HQS 20 x 5
   python bench.py --workload mixed320    # A^H A and DC solves at FP32 / BF16x3 / FP16x3
