@@ -6,9 +6,10 @@ oversampling 2 (Eq. (1) with the gridding parameters of the benchmark).  Its
 transforms are the ones the smaller cases never reach: 640-point lines
 (radix 5 and the prime-factor 10 and 40 stages) on the NUFFT grid and the
 Toeplitz grid, 320-point lines in the preconditioner; the 384 x 384 slices of
-the batched workload add 768-point lines.  The batched solve is checked in the
-launch configuration the benchmark times: 16 slices of one trajectory, one
-plan each, in one cooperative launch.
+the batched workload add 768-point lines.  The batched solve and the batched
+A^H A are checked in the launch configuration the benchmark times: 16 slices
+of one trajectory, one plan each, as two batches of 8 whose cooperative
+launches (one CTA per SM each) run side by side on two streams.
 
 Bars: relative L2 <= 1e-5 for a single operator (float32 path against the
 float64 oracle at equal parameters); for iterated results (CG, HQS) the bound
@@ -138,12 +139,27 @@ def test_brain_pcg_fixed_iterations_match_oracle(brain, mode):
     assert inf.status == 0 and tr <= 1.2e-4
 
 
+def _side_by_side(batches, groups, fn):
+    """fn(batch, group, stream) for each batch on its own stream, as the
+    benchmark runs its two groups, ordered after and before the current stream."""
+    main = torch.cuda.current_stream()
+    sts = [torch.cuda.Stream() for _ in batches]
+    for s_ in sts:
+        s_.wait_stream(main)
+    for b, g, s_ in zip(batches, groups, sts):
+        with torch.cuda.stream(s_):
+            fn(b, g, s_)
+    for s_ in sts:
+        main.wait_stream(s_)
+
+
 def test_brain_batched_solve_16_slices_matches_oracle():
     """k_pcg_batch as the benchmark launches it: 16 slices of the spiral
-    workload (seeds 0-15, one plan each, one trajectory), one cooperative
-    launch.  5 fixed iterations against the oracle's PCG per slice; then to
-    1e-4, every slice's fp64 true residual and its iteration count against
-    the per-slice persistent solve (within 15 %, helpers.iterations_agree)."""
+    workload (seeds 0-15, one plan each, one trajectory) as two batches of 8,
+    each launch capped at one CTA per SM, side by side on two streams.  5 fixed
+    iterations against the oracle's PCG per slice; then to 1e-4, every slice's
+    fp64 true residual and its iteration count against the per-slice persistent
+    solve (within 15 %, helpers.iterations_agree)."""
     n, L, B = 320, 16, 16
     traj = synth.traj_spiral(16, 2048, n)
     cases = [quantised(dict(n=n, L=L, W=6, sigma=2.0, x=synth.phantom(s, n), smaps=synth.coil_maps(s, n, L),
@@ -155,11 +171,16 @@ def test_brain_batched_solve_16_slices_matches_oracle():
         fut = [ex.submit(jobs.pcg_fixed, c["smaps"], Kh, lam, MU, b, 5, 10 + i)
                for i, (c, b) in enumerate(zip(cases, rhs_np))]
         plans = [make_plan(c)[0] for c in cases]
-        batch = hq().Batch(plans, max_outer=1)
+        groups = [list(range(0, 8)), list(range(8, 16))]
+        batches = [hq().Batch([plans[i] for i in g], max_outer=1) for g in groups]
+        cap = 2 * torch.cuda.get_device_properties(0).multi_processor_count // 2
+        for b in batches:
+            b.set_grid(cap)
         rhs = [to_dev(b) for b in rhs_np]
         xs = [torch.full((n, n), 2.0 - 1j, dtype=torch.complex64, device="cuda") for _ in range(B)]
-        batch.dc_solve(rhs, xs, 1.0, MU, max_iter=5, rel_tol=0.0)
-        info = batch.dc_info()
+        _side_by_side(batches, groups, lambda b, g, st: b.dc_solve([rhs[i] for i in g], [xs[i] for i in g], 1.0, MU,
+                                                                 max_iter=5, rel_tol=0.0, stream=st))
+        info = batches[0].dc_info() + batches[1].dc_info()
         got = [to_host(x) for x in xs]
         oracle = [f.result() for f in fut]
         for i, ((want, _, dev), g) in enumerate(zip(oracle, got)):
@@ -170,8 +191,9 @@ def test_brain_batched_solve_16_slices_matches_oracle():
         # to tolerance
         for x in xs:
             x.zero_()
-        batch.dc_solve(rhs, xs, 1.0, MU, max_iter=200, rel_tol=1e-4)
-        info = batch.dc_info()
+        _side_by_side(batches, groups, lambda b, g, st: b.dc_solve([rhs[i] for i in g], [xs[i] for i in g], 1.0, MU,
+                                                                 max_iter=200, rel_tol=1e-4, stream=st))
+        info = batches[0].dc_info() + batches[1].dc_info()
         sols = [to_host(x) for x in xs]
         tres = list(ex.map(jobs.true_residual, [c["smaps"] for c in cases], [Kh] * B, [MU] * B, rhs_np, sols))
     for i in range(B):
@@ -187,8 +209,8 @@ def test_brain_batched_solve_16_slices_matches_oracle():
 def test_brain_batched_toeplitz_normal_16_slices_matches_oracle():
     """hqs_batch_toeplitz_normal as the benchmark launches it
     (`aha_applies_per_s_batched`): 16 slices of the spiral workload, one plan
-    each, in one cooperative launch; every slice's A^H A x against the FP64
-    oracle's Toeplitz normal operator at the single-operator bar."""
+    each, as two capped batches of 8 side by side; every slice's A^H A x against
+    the FP64 oracle's Toeplitz normal operator at the single-operator bar."""
     n, L, B = 320, 16, 16
     traj = synth.traj_spiral(16, 2048, n)
     cases = [quantised(dict(n=n, L=L, W=6, sigma=2.0, x=synth.phantom(s, n), smaps=synth.coil_maps(s, n, L),
@@ -198,10 +220,15 @@ def test_brain_batched_toeplitz_normal_16_slices_matches_oracle():
         fut = list(ex.map(jobs.normal_rhs, [c["smaps"] for c in cases], [Kh] * B, [0.0] * B,
                           [c["x"] for c in cases]))
         plans = [make_plan(c)[0] for c in cases]
-        batch = hq().Batch(plans, max_outer=1)
+        groups = [list(range(0, 8)), list(range(8, 16))]
+        batches = [hq().Batch([plans[i] for i in g], max_outer=1) for g in groups]
+        cap = 2 * torch.cuda.get_device_properties(0).multi_processor_count // 2
+        for b in batches:
+            b.set_grid(cap)
         xs = [to_dev(c["x"]) for c in cases]
         outs = [torch.empty_like(x) for x in xs]
-        batch.toeplitz_normal(xs, outs)
+        _side_by_side(batches, groups, lambda b, g, st: b.toeplitz_normal([xs[i] for i in g], [outs[i] for i in g],
+                                                                        stream=st))
         got = [to_host(o) for o in outs]
     for i, (g, want) in enumerate(zip(got, fut)):
         print(f"batched A^H A, slice {i}: {rel(g, want):.2e}")
