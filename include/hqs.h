@@ -341,8 +341,9 @@ HQS_API int hqs_batch_create(hqs_batch* out, hqs_plan* plans, int n, int max_out
 /* Caps the CTAs of the batch's cooperative launches (0, the default: every CTA
  * the kernel keeps resident, two per SM).  With a cap of one CTA per SM, two
  * batches launched on two streams can run side by side, each CTA's grid
- * barriers independent of the other batch's.  No counterpart in the paper: a
- * launch-shape setting. */
+ * barriers independent of the other batch's.  Results are unchanged up to the
+ * order of the per-CTA fp64 partial sums.  No counterpart in the paper: a
+ * launch-shape setting.  ctas < 0 or a NULL batch: HQS_ERR_INVALID_ARG. */
 HQS_API int hqs_batch_set_grid(hqs_batch batch, int ctas);
 HQS_API void hqs_batch_destroy(hqs_batch batch);
 HQS_API int hqs_batch_run(hqs_batch batch, const hqs_c64* const* y, hqs_c64* const* x,
@@ -371,7 +372,8 @@ HQS_API int hqs_batch_dc_info(hqs_batch batch, int* iterations, double* rel_resi
  * Enqueued on `stream`; synchronises it first when the pointers differ from the
  * last call.  Uses the plans' workspaces: calls on one batch (and on its plans)
  * run in stream order.  A grid barrier that runs out of time is reported by the
- * next hqs_batch_status / hqs_batch_dc_info (HQS_ERR_TIMEOUT). */
+ * next hqs_batch_status / hqs_batch_dc_info (HQS_ERR_TIMEOUT).  A NULL batch,
+ * array or pointer: HQS_ERR_INVALID_ARG, nothing enqueued. */
 HQS_API int hqs_batch_toeplitz_normal(hqs_batch batch, const hqs_c64* const* x, hqs_c64* const* out,
                                       void* stream);
 /* Batched NUFFT operators (Eq. (1) and its adjoint, the same gridding as
@@ -383,7 +385,8 @@ HQS_API int hqs_batch_toeplitz_normal(hqs_batch batch, const hqs_c64* const* x, 
  * x[i], z[i]: (n_i, n_i), device complex64, caller-owned.  Enqueued on
  * `stream`; synchronises it first when the image pointers differ from the last
  * call.  Uses the plans' workspaces: calls on one batch (and on its plans) run
- * in stream order. */
+ * in stream order.  A NULL batch, array or image pointer (or a NULL y[i] of a
+ * plan with points): HQS_ERR_INVALID_ARG, nothing enqueued. */
 HQS_API int hqs_batch_forward(hqs_batch batch, const hqs_c64* const* x, hqs_c64* const* y, void* stream);
 HQS_API int hqs_batch_adjoint_axpy(hqs_batch batch, const hqs_c64* const* y, float zc, const hqs_c64* const* z,
                                    hqs_c64* const* x, void* stream);
