@@ -36,6 +36,7 @@ enum BatchList { BL_ROWS = 0, BL_COLS = 1, BL_PC = 2, BL_IMG = 3, BL_BLUR = 4, B
 
 struct BatchSlice {
     ToepArgs A;
+    int colcap;   // > 0: column items of colcap flattened (column, coil) lines; 0: one column per chunk
     const float2* twN;
     const float* lam;
     const float2* b0;
@@ -315,7 +316,12 @@ __global__ void __launch_bounds__(HQS_BATCH_BD, 2) k_hqs_batch(BatchArgs B) {
         FOR_ITEMS(BL_COLS, {
             const int n = S.A.n, N2v = 2 * n, ch = it_ / N2v, kx = it_ - ch * N2v;
             STAGE_TW2(S.A);
-            HQS_BATCH_DISPATCH(n, (toep_cols_item<N2, HQS_BATCH_BD>(S.A, kx, ch, s, twT)));
+            if (S.colcap > 0) {
+                const int f0 = it_ * S.colcap, nl = min(S.colcap, N2v * S.A.L - f0);
+                HQS_BATCH_DISPATCH(n, (toep_cols_flat_item<N2, HQS_BATCH_BD>(S.A, f0, nl, s, twT)));
+            } else {
+                HQS_BATCH_DISPATCH(n, (toep_cols_item<N2, HQS_BATCH_BD>(S.A, kx, ch, s, twT)));
+            }
         });
         BB_BARRIER();
         FOR_ITEMS(BL_ROWS, {
@@ -413,7 +419,12 @@ __global__ void __launch_bounds__(HQS_BATCH_BD, 2) k_hqs_batch(BatchArgs B) {
             FOR_ITEMS(BL_COLS, {
                 const int n = S.A.n, N2v = 2 * n, ch = it_ / N2v, kx = it_ - ch * N2v;
                 STAGE_TW2(S.A);
-            HQS_BATCH_DISPATCH(n, (toep_cols_item<N2, HQS_BATCH_BD>(S.A, kx, ch, s, twT)));
+                if (S.colcap > 0) {
+                    const int f0 = it_ * S.colcap, nl = min(S.colcap, N2v * S.A.L - f0);
+                    HQS_BATCH_DISPATCH(n, (toep_cols_flat_item<N2, HQS_BATCH_BD>(S.A, f0, nl, s, twT)));
+                } else {
+                    HQS_BATCH_DISPATCH(n, (toep_cols_item<N2, HQS_BATCH_BD>(S.A, kx, ch, s, twT)));
+                }
             });
             BB_BARRIER();
             CLEAR_ACC();
@@ -702,7 +713,12 @@ __global__ void __launch_bounds__(HQS_BATCH_BD, 2) k_pcg_batch(DcBatchArgs B) {
         FOR_ITEMS(BL_COLS, {
             const int n = S.A.n, N2v = 2 * n, ch = it_ / N2v, kx = it_ - ch * N2v;
             STAGE_TW2(S.A);
-            HQS_BATCH_DISPATCH(n, (toep_cols_item<N2, HQS_BATCH_BD>(S.A, kx, ch, s, twT)));
+            if (S.colcap > 0) {
+                const int f0 = it_ * S.colcap, nl = min(S.colcap, N2v * S.A.L - f0);
+                HQS_BATCH_DISPATCH(n, (toep_cols_flat_item<N2, HQS_BATCH_BD>(S.A, f0, nl, s, twT)));
+            } else {
+                HQS_BATCH_DISPATCH(n, (toep_cols_item<N2, HQS_BATCH_BD>(S.A, kx, ch, s, twT)));
+            }
         });
         BB_BARRIER();
         CLEAR_ACC();
@@ -871,7 +887,12 @@ __global__ void __launch_bounds__(HQS_BATCH_BD, 2) k_aha_batch(AhaBatchArgs B) {
     FOR_ITEMS(BL_COLS, {
         const int n = S.A.n, N2v = 2 * n, ch = it_ / N2v, kx = it_ - ch * N2v;
         STAGE_TW2(S.A);
-        HQS_BATCH_DISPATCH(n, (toep_cols_item<N2, HQS_BATCH_BD>(S.A, kx, ch, s, twT)));
+        if (S.colcap > 0) {
+            const int f0 = it_ * S.colcap, nl = min(S.colcap, N2v * S.A.L - f0);
+            HQS_BATCH_DISPATCH(n, (toep_cols_flat_item<N2, HQS_BATCH_BD>(S.A, f0, nl, s, twT)));
+        } else {
+            HQS_BATCH_DISPATCH(n, (toep_cols_item<N2, HQS_BATCH_BD>(S.A, kx, ch, s, twT)));
+        }
     });
     AB_BARRIER();
     FOR_ITEMS(BL_ROWS, {
@@ -1049,8 +1070,13 @@ extern "C" int hqs_batch_create(hqs_batch* out, hqs_plan* plans, int n, int max_
         S.p = p->cg_p;
         S.q = p->cg_q;
         S.pcb = p->pc_buf;
+        // column items: with chunks of fewer than lcmax coils, items of lcmax flattened
+        // (column, coil) lines instead of one column per chunk
+        const bool pack = S.A.LC < lcmax;
+        S.colcap = pack ? lcmax : 0;
+        const int ncols = pack ? ceil_div(2 * p->n * p->L, lcmax) : 2 * p->n * nch;
         const int zq = dispatch_fft_size(p->n, [&]<int NN>() { return batch_zq<NN>(); });
-        const int cnt[BL_N] = {p->n * nch, 2 * p->n * nch, ceil_div(p->n, batch_pq_host(p->n)), p->n,
+        const int cnt[BL_N] = {p->n * nch, ncols, ceil_div(p->n, batch_pq_host(p->n)), p->n,
                                ceil_div(p->n, 32) * ceil_div(p->n, 32), nch > 1 ? p->n : 0, ceil_div(p->n, zq)};
         for (int l = 0; l < BL_N; ++l) off[(size_t)l * (n + 1) + i + 1] = off[(size_t)l * (n + 1) + i] + cnt[l];
     }

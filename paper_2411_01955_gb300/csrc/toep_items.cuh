@@ -82,6 +82,34 @@ HQS_DEV void toep_cols_item(const ToepArgs& A, int kx, int ch, float2* s, const 
     __syncthreads();
 }
 
+// P2 over nl consecutive (column, coil) lines of the flattened index f = kx L + l
+// (f0 .. f0 + nl - 1, nl <= kLines): the data of line f at position p is
+// T[f + p N2 L], so an item's lines are contiguous whichever columns they belong
+// to, and chunks of fewer than kLines coils need not leave threads idle.  Khat of
+// the item's first column is staged with cp.async; a line of a later column reads
+// its Khat through L1.
+template <int N2, int BD = FftSize<N2>::TPL * kLines>
+HQS_DEV void toep_cols_flat_item(const ToepArgs& A, int f0, int nl, float2* s, const float2* tws = nullptr) {
+    const int n = A.n, L = A.L;
+    const float2* tw = tws ? tws : stage_twiddles<N2>(s + N2 * kLines + n, A.tw);
+    float2* col = A.T + f0;
+    const int64_t rs = (int64_t)N2 * L;
+    const int kx0 = f0 / L;
+    const float* kh0 = A.khat + (int64_t)kx0 * N2;
+    const float* khat = A.khat;
+    float* khs = reinterpret_cast<float*>(s + N2 * kLines);
+    for (int c = threadIdx.x; c < N2 / 4; c += blockDim.x) cp_async16(khs + 4 * c, kh0 + 4 * c);
+    __syncthreads();
+    block_fft_pair<N2, true, true>(
+        s, nl, tw, [&](int line, int p, bool) { return __ldcg(col + line + p * rs); },
+        [&](int line, int p, float2 v) {
+            const int kx = (f0 + line) / L;
+            return cscale(v, kx == kx0 ? khs[p] : __ldg(khat + (int64_t)kx * N2 + p));
+        },
+        [&](int line, int p, float2 v) { col[line + p * rs] = v; });
+    __syncthreads();
+}
+
 // CG epilogue on one pixel: mode 0 returns v = A^H A p; mode 1 returns
 // q = a v + b p and adds Re<p, q> to part.
 HQS_DEV float2 toep_epilogue_pv(float2 v, float2 pv, float a, float b, double& part) {
