@@ -192,6 +192,42 @@ def test_density_symbols_are_one_on_full_cartesian():
     assert rel(toeplitz.precond_apply(v, lam, 2.0, 0.5), v / math.sqrt(2.5)) < 1e-13
 
 
+def _dft_matrix(ny, nx):
+    # E[k, m] = exp(-2 pi i (ky my / ny + kx mx / nx)), k and m flattened row-major (y, x)
+    my, mx = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    return np.exp(-2j * np.pi * (np.outer(my.ravel(), my.ravel()) / ny + np.outer(mx.ravel(), mx.ravel()) / nx))
+
+
+def test_precond_apply_is_inverse_square_root_of_its_circulant():
+    # Brute force on a 5 x 4 grid with a random, partly negative symbol (frequency ky
+    # along axis 0, in DFT order): two applies followed by the dense circulant whose
+    # eigenvalues are a max(lam, 0) + b give v back.  A transposed or mirrored symbol
+    # (lam[-k]), a dropped clamp or a full instead of a square-root inverse fails.
+    rng = np.random.default_rng(29)
+    ny, nx = 5, 4
+    lam = rng.uniform(-0.5, 3.0, size=(ny, nx))
+    E = _dft_matrix(ny, nx)
+    C = E.conj().T @ np.diag((0.7 * np.maximum(lam, 0.0) + 0.2).ravel()) @ E / (ny * nx)
+    v = rand_c(rng, (ny, nx))
+    z = toeplitz.precond_apply(toeplitz.precond_apply(v, lam, 0.7, 0.2), lam, 0.7, 0.2)
+    assert rel((C @ z.ravel()).reshape(ny, nx), v) < 1e-13
+
+
+def test_precond_apply_floor_on_plane_waves():
+    # Plane waves are the circulant's eigenvectors.  With a < 0 the symbol
+    # a lam + b falls below b / 4 where lam is large: there the multiplier is the
+    # floor's (b / 4)^(-1/2) = 2 / sqrt(b); where lam < 0 it is b^(-1/2).
+    ny, nx = 6, 5
+    lam = np.full((ny, nx), 0.5)
+    lam[2, 3], lam[4, 1] = 10.0, -3.0
+    a, b = -0.1, 0.4
+    my, mx = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    for (ky, kx), want in (((2, 3), 2.0 / math.sqrt(b)), ((4, 1), 1.0 / math.sqrt(b)),
+                           ((0, 0), 1.0 / math.sqrt(a * 0.5 + b))):
+        e = np.exp(2j * np.pi * (ky * my / ny + kx * mx / nx))
+        assert rel(toeplitz.precond_apply(e, lam, a, b), want * e) < 1e-13
+
+
 def test_chan_circulant_averages_wrapped_diagonals():
     # T. Chan (1988): the Frobenius-optimal circulant approximation of a matrix
     # has first column c[q] = mean over n of T[(n + q) mod N, n].  Build the
