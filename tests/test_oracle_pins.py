@@ -149,6 +149,18 @@ def test_nufft_vs_nudft_error_bound_and_monotone_in_width():
     assert ea <= 2e-3
 
 
+def test_nufft_rectangular_image_against_nudft():
+    # ny != nx: a per-axis quantity (grid size, apodisation, tap table) applied to the
+    # wrong axis changes the result or its shape
+    rng = np.random.default_rng(31)
+    ny, nx, L, M = 24, 16, 2, 300
+    x, S = rand_c(rng, (ny, nx)), rand_c(rng, (L, ny, nx))
+    traj = rng.uniform(-math.pi, math.pi, size=(M, 2))
+    y = rand_c(rng, (L, M))
+    assert rel(nufft.forward(x, S, traj, 6, 2.0), nudft.forward(x, S, traj)) < 1e-4
+    assert rel(nufft.adjoint(y, S, traj, 6, 2.0), nudft.adjoint(y, S, traj)) < 1e-4
+
+
 def test_nufft_odd_shapes_and_hot_centre():
     c = synth.odd_case(0)
     ex = nudft.forward(c["x"], c["smaps"], c["traj"])
@@ -318,6 +330,28 @@ def test_fcg_with_linear_preconditioner_matches_pcg():
     assert i3["fallback"] and rel(x3, x1) < 1e-8
 
 
+def test_fcg_fallback_continues_from_the_current_iterate():
+    # B is the DC preconditioner for its first three calls (so three flexible-CG
+    # iterations equal three PCG iterations) and then returns -r (<z, r> < 0): the
+    # fallback is DC-PCG started at x_3 for the remaining iterations
+    P = small_problem(18)
+    n, mu = P["n"], 1e-2
+    H = lambda v: P["AHA"](v) + mu * v
+    Minv = lambda v: toeplitz.precond_apply(v, P["lam"], 1.0, mu)
+    calls = [0]
+
+    def B(v):
+        calls[0] += 1
+        return Minv(v) if calls[0] <= 3 else -v
+
+    x0 = 0.3 * synth.phantom(5, n)
+    x, info = solvers.fcg(H, P["b0"], x0, B, Minv, max_iter=12, tol=0.0)
+    x3, _ = solvers.pcg(H, P["b0"], x0, Minv, max_iter=3, tol=0.0)
+    want, _ = solvers.pcg(H, P["b0"], x3, Minv, max_iter=9, tol=0.0)
+    assert info["fallback"] and info["iters"] == 12
+    assert rel(x, want) < 1e-10
+
+
 def test_pcg_zero_rhs_and_converged_start():
     P = small_problem(11)
     n = P["n"]
@@ -353,6 +387,82 @@ def test_gaussian_denoiser_matches_fft_convolution():
     assert rel(hqs.gaussian_denoise(v, s), want) < 1e-13
     assert np.allclose(hqs.gaussian_denoise(v, 0.05), v)
     assert abs(hqs.gaussian_denoise(v, 2.0).sum() - v.sum()) < 1e-10
+
+
+@pytest.mark.parametrize("s", [2.0, 3.0, 4.0])
+def test_gaussian_taps_variance_of_the_truncated_normal(s):
+    # taps sampled from a normal of std s and cut at +-3 s: their variance is the
+    # truncated normal's, s^2 (1 - 6 phi(3) / (2 Phi(3) - 1)) = 0.97334 s^2 (the
+    # sampling at integer offsets changes it by far less than the tolerance here)
+    g = hqs.gaussian_taps(s)
+    r = (len(g) - 1) // 2
+    i = np.arange(-r, r + 1)
+    assert r == 3 * s and abs(g.sum() - 1.0) < 1e-15
+    var = float(np.sum(g * i * i))
+    pdf3 = math.exp(-4.5) / math.sqrt(2 * math.pi)
+    want = s * s * (1 - 6 * pdf3 / math.erf(3 / math.sqrt(2)))
+    assert abs(var / want - 1) < 0.03
+
+
+def test_denoiser_std_tracks_the_noise_level():
+    # the blur is kappa = 1.5 px at the first noise level and scales with sigma_k
+    assert abs(hqs.denoiser_std(0.2, 0.2) - 1.5) < 1e-15
+    assert abs(hqs.denoiser_std(0.05, 0.2) - 0.375) < 1e-15
+
+
+def test_hqs_and_pgd_closed_form_when_AHA_is_identity():
+    # With A^H A = I every prox system is ((1 + (c0 + c1) mu_k)) u = b0 + mu_k (c0 + c1) x,
+    # solved exactly by the first CG step, and a PGD step is x - gamma_k (c0 + c1)(x - b0);
+    # with the shrink D(u, s) = u / (1 + s) both loops are scalar recursions per pixel,
+    # so each step's mu_k, sigma_k, gamma_k and the metric enter visibly.
+    rng = np.random.default_rng(33)
+    b0, x0 = rand_c(rng, (6, 6)), rand_c(rng, (6, 6))
+    I = lambda v: v
+    D = lambda u, s: u / (1 + s)
+    mu = [0.3, 0.1, 0.05, 0.02]
+    sig = [0.4, 0.2, 0.1, 0.05]
+    gam = [0.2, 0.15, 0.1, 0.05]
+    for c0, c1 in [(1.0, 0.0), (2.0, -0.4), (4.0, -10 * 0.4 / 3)]:
+        c = c0 + c1
+        x, u, _ = hqs.hqs(I, b0, x0, mu, sig, 4, cg_iters=3, c0=c0, c1=c1, denoiser=D)
+        want = x0
+        for m, sg in zip(mu, sig):
+            want = (b0 + m * c * want) / (1 + c * m) / (1 + sg)
+        assert rel(x, want) < 1e-13
+        xp = hqs.pgd(I, b0, x0, gam, sig, 4, c0=c0, c1=c1, denoiser=D)
+        want = x0
+        for g, sg in zip(gam, sig):
+            want = (want - g * c * (want - b0)) / (1 + sg)
+        assert rel(xp, want) < 1e-13
+
+
+def test_hqs_warm_start_keeps_a_consistent_solution():
+    # noise-free data b0 = A^H A x_t and x_0 = x_t: x_t solves every prox system, so
+    # warm-started CG leaves it in place (three iterations could not reach it from 0)
+    P = small_problem(34)
+    n = P["n"]
+    xt = synth.phantom(34, n)
+    b0 = P["AHA"](xt)
+    x, u, _ = hqs.hqs(P["AHA"], b0, xt, [0.05, 0.02], [1.0, 1.0], 2, cg_iters=3,
+                      denoiser=lambda v, s: v, lam=P["lam"])
+    assert rel(x, xt) < 1e-10 and rel(u, xt) < 1e-10
+
+
+def test_pgd_fixed_point_in_the_f1_metric():
+    # P = 2 I - alpha A^H A, D(v) = v / (1 + tau): the PGD limit solves
+    # (tau I + gamma P A^H A) x = gamma P A^H y
+    P = small_problem(35)
+    n, tau, K = P["n"], 0.5, 300
+    lmax = solvers.power_iteration(P["AHA"], (n, n), iters=500, rtol=1e-12)
+    alpha = 1.0 / lmax
+    gamma = 0.9 / (2.0 * lmax)
+    D = lambda u, s: u / (1 + tau)
+    x = hqs.pgd(P["AHA"], P["b0"], np.zeros((n, n)), [gamma] * K, [1.0] * K, K, c0=2.0, c1=-alpha,
+                denoiser=D)
+    Pm = lambda v: 2.0 * v - alpha * P["AHA"](v)
+    Hd = dense_matrix(lambda v: tau * v + gamma * Pm(P["AHA"](v)), n)
+    want = np.linalg.solve(Hd, (gamma * Pm(P["b0"])).ravel()).reshape(n, n)
+    assert rel(x, want) < 1e-8
 
 
 def test_hqs_fixed_point_linear_shrink_prop1():
@@ -508,6 +618,21 @@ def test_learned_preconditioner_starts_as_dc_preconditioner():
     assert rel(z, toeplitz.precond_apply(r, P["lam"], 1.0, 0.05)) < 1e-15
 
 
+def test_learned_preconditioner_is_positively_homogeneous():
+    # the network sees zdc / s, which does not change when r is scaled, and its output
+    # is scaled back by s: z(c r) = c z(r) for c > 0, whatever the weights and biases
+    P = small_problem(24)
+    rng = np.random.default_rng(24)
+    vec = convnet.flatten(convnet.init_params(1))
+    vec = vec + 0.05 * rng.normal(size=vec.shape)          # last layer and biases non-zero
+    params = convnet.unflatten(vec)
+    r = P["b0"]
+    z1 = convnet.learned_precond(r, P["lam"], 1.0, 0.05, params)
+    z2 = convnet.learned_precond(3.7 * r, P["lam"], 1.0, 0.05, params)
+    assert rel(z1, toeplitz.precond_apply(r, P["lam"], 1.0, 0.05)) > 1e-3
+    assert rel(z2, 3.7 * z1) < 1e-13
+
+
 # ------------------------------------------------------------------ S-maps (Sec. 4.1)
 def test_smaps_window_closed_form():
     from oracle import smaps
@@ -517,6 +642,9 @@ def test_smaps_window_closed_form():
     traj = np.stack([us * 2 * np.pi / n, np.zeros_like(us)], axis=1)
     w = smaps.hamming_centre(traj, n, 20)
     assert np.allclose(w, [1.0, 0.54, 0.54, 0.08, 0.08, 0.0], atol=1e-12)
+    # separable: off the axes the weight is the product of the two axes' values
+    pts = np.array([[5.0, 5.0], [-5.0, 10.0], [0.0, 12.0], [0.0, -5.0]]) * 2 * np.pi / n
+    assert np.allclose(smaps.hamming_centre(pts, n, 20), [0.54 ** 2, 0.54 * 0.08, 0.0, 0.54], atol=1e-12)
 
 
 def test_smaps_estimate_normalised_masked_and_phase_covariant():

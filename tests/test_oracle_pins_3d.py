@@ -195,6 +195,22 @@ def test_chan3d_symbol_is_one_on_full_cartesian_sampling():
     assert rel(nufft3d.precond_apply(v, lam, 2.0, 0.5), v / math.sqrt(2.5)) < 1e-13
 
 
+def test_precond3d_floor_and_clamp_on_plane_waves():
+    # plane waves are the 3D circulant's eigenvectors: where lam < 0 the multiplier is
+    # b^(-1/2) (the clamp), where a lam + b < b / 4 (a < 0) it is 2 / sqrt(b) (the floor),
+    # elsewhere (a lam + b)^(-1/2); frequency kz is the first axis
+    nz, ny, nx = 3, 4, 5
+    lam = np.full((nz, ny, nx), 0.5)
+    lam[1, 2, 3], lam[2, 0, 4] = 10.0, -3.0
+    mz, my, mx = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    for a, b, k, want in ((-0.1, 0.4, (1, 2, 3), 2.0 / math.sqrt(0.4)),
+                          (0.7, 0.2, (2, 0, 4), 1.0 / math.sqrt(0.2)),
+                          (0.7, 0.2, (1, 2, 3), 1.0 / math.sqrt(7.2)),
+                          (0.7, 0.2, (0, 3, 1), 1.0 / math.sqrt(0.55))):
+        e = np.exp(2j * np.pi * (k[0] * mz / nz + k[1] * my / ny + k[2] * mx / nx))
+        assert rel(nufft3d.precond_apply(e, lam, a, b), want * e) < 1e-13
+
+
 def test_density_preconditioner_cuts_3d_iterations_on_stacked_spirals():
     # the design property the preconditioner is chosen for (not a parity pin)
     c = synth.volume_case(3, (8, 32, 32), 4, 8, 256)
