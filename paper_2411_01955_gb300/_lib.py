@@ -579,6 +579,10 @@ class Batch:
     def run(self, ys, xs, mu, sigma, K=None, k0=0, cg_iters=5, c0=1.0, c1=0.0, gauss=None,
             use_graph=True, stream=None):
         K = len(mu) if K is None else int(K)
+        if K > min(len(mu), len(sigma)):
+            raise ValueError("mu and sigma need K entries")
+        self._check_kspace(ys)
+        self._check_images(xs, "x")
         n = len(self.plans)
         yp = (C.c_void_p * n)(*[_ptr(y, torch.complex64, "y") for y in ys])
         xp = (C.c_void_p * n)(*[_ptr(x, torch.complex64, "x") for x in xs])
@@ -593,6 +597,8 @@ class Batch:
 
     def dc_solve(self, rhs, xs, a, b, max_iter=200, rel_tol=1e-4, stream=None):
         """Solves (a A^H A + b I) x_i = rhs_i for every slice from x_i = 0 in one launch."""
+        self._check_images(rhs, "rhs")
+        self._check_images(xs, "x")
         n = len(self.plans)
         rp = (C.c_void_p * n)(*[_ptr(r, torch.complex64, "rhs") for r in rhs])
         xp = (C.c_void_p * n)(*[_ptr(x, torch.complex64, "x") for x in xs])
@@ -646,12 +652,13 @@ class Batch:
         """x_i = A_i^H y_i + zc z_i for every slice (zs None: no axpy term)."""
         self._check_kspace(ys)
         self._check_images(xs, "x")
+        if zs is not None:
+            self._check_images(zs, "z")
         n = len(self.plans)
         yp = (C.c_void_p * n)(*[_ptr(y, torch.complex64, "y") for y in ys])
         xp = (C.c_void_p * n)(*[_ptr(x, torch.complex64, "x") for x in xs])
         zp = None
         if zs is not None:
-            self._check_images(zs, "z")
             zp = (C.c_void_p * n)(*[_ptr(z, torch.complex64, "z") for z in zs])
         _check(library().hqs_batch_adjoint_axpy(self.handle, yp, float(zc), zp, xp, _stream(stream)),
                "hqs_batch_adjoint_axpy")

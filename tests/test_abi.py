@@ -101,3 +101,34 @@ def test_noalloc_wrapper_checks_shapes_before_any_launch():
                                              fake, None) == -1
     assert lib.hqs_precond_apply_noalloc(fake, fake, 64, ctypes.c_float(1.0), ctypes.c_float(0.0),
                                          fake, None) == -1
+
+
+def test_batch_wrappers_check_counts_and_shapes_before_any_launch():
+    # the C side cannot see tensor sizes, so the binding rejects a missing slice or a
+    # wrongly sized image / k-space array before it touches a pointer (CPU tensors
+    # reach the check; a launch would need CUDA ones)
+    import pytest
+    torch = pytest.importorskip("torch")
+    import types
+    import paper_2411_01955_gb300 as hq
+    c64 = torch.complex64
+    plans = [types.SimpleNamespace(ny=32, nx=32, coils=4, npoints=100),
+             types.SimpleNamespace(ny=64, nx=64, coils=2, npoints=300)]
+    bt = object.__new__(hq.Batch)
+    bt.plans, bt.handle = plans, None
+    img = [torch.zeros((32, 32), dtype=c64), torch.zeros((64, 64), dtype=c64)]
+    ksp = [torch.zeros((4, 100), dtype=c64), torch.zeros((2, 300), dtype=c64)]
+    small = [img[0], torch.zeros((32, 32), dtype=c64)]
+    calls = [
+        lambda: bt.dc_solve(img[:1], img, 1.0, 0.1),
+        lambda: bt.dc_solve(img, small, 1.0, 0.1),
+        lambda: bt.run(ksp, small, [0.1], [0.1]),
+        lambda: bt.run([ksp[0], torch.zeros((2, 200), dtype=c64)], img, [0.1], [0.1]),
+        lambda: bt.run(ksp, img, [0.1, 0.1], [0.1], K=2),
+        lambda: bt.toeplitz_normal(img, small),
+        lambda: bt.forward(img, ksp[:1]),
+        lambda: bt.adjoint_axpy(ksp, 0.1, small, img),
+    ]
+    for call in calls:
+        with pytest.raises(ValueError):
+            call()
