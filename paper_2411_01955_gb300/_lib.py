@@ -212,6 +212,36 @@ def _ptr(t, dtype=None, name="tensor"):
     return C.c_void_p(t.data_ptr())
 
 
+def _need(t, n, name):
+    # the C entry points size every buffer from the plan, so a tensor holding fewer
+    # (or more) elements than the plan implies is rejected here, before any launch
+    if t is not None and t.numel() != n:
+        raise ValueError(f"{name} must hold {n} elements, got {t.numel()} (shape {tuple(t.shape)})")
+
+
+def _image_elems(plan):
+    if hasattr(plan, "ny"):
+        return plan.ny * plan.nx
+    nz, ny, nx = plan.shape
+    return nz * ny * nx
+
+
+def _need_image(plan, **named):
+    for name, t in named.items():
+        _need(t, _image_elems(plan), name)
+
+
+def _need_kspace(plan, **named):
+    for name, t in named.items():
+        _need(t, plan.coils * plan.npoints, name)
+
+
+def _need_schedule(K, **named):
+    for name, v in named.items():
+        if len(v) < K:
+            raise ValueError(f"{name} needs K = {K} entries, got {len(v)}")
+
+
 def _stream(stream=None):
     s = stream if stream is not None else torch.cuda.current_stream()
     return C.c_void_p(s.cuda_stream)
@@ -243,9 +273,11 @@ class Plan:
 
 def plan_create(traj, ny, nx, smaps, kernel_width=6, oversamp=2.0, stream=None) -> Plan:
     """traj (M, 2) float32 CUDA; smaps (L, ny, nx) complex64 CUDA."""
+    M = int(traj.shape[0])
+    _need(traj, 2 * M, "traj")
+    _need(smaps, int(smaps.shape[0]) * int(ny) * int(nx), "smaps")
     lib = library()
     h = C.c_void_p()
-    M = int(traj.shape[0])
     rc = lib.hqs_plan_create(C.byref(h), _ptr(traj, torch.float32, "traj"), M, int(ny), int(nx),
                              int(smaps.shape[0]), _ptr(smaps, torch.complex64, "smaps"),
                              int(kernel_width), float(oversamp), _stream(stream))
@@ -254,12 +286,16 @@ def plan_create(traj, ny, nx, smaps, kernel_width=6, oversamp=2.0, stream=None) 
 
 
 def forward(plan: Plan, x, y, stream=None):
+    _need_image(plan, x=x)
+    _need_kspace(plan, y=y)
     _check(library().hqs_forward(plan.handle, _ptr(x, torch.complex64, "x"),
                                  _ptr(y, torch.complex64, "y"), _stream(stream)), "hqs_forward")
     return y
 
 
 def adjoint(plan: Plan, y, x, stream=None):
+    _need_kspace(plan, y=y)
+    _need_image(plan, x=x)
     _check(library().hqs_adjoint(plan.handle, _ptr(y, torch.complex64, "y"),
                                  _ptr(x, torch.complex64, "x"), _stream(stream)), "hqs_adjoint")
     return x
@@ -267,6 +303,8 @@ def adjoint(plan: Plan, y, x, stream=None):
 
 def adjoint_axpy(plan: Plan, y, c, z, x, stream=None):
     """x = A^H y + c z (the HQS data-consistency right-hand side)."""
+    _need_kspace(plan, y=y)
+    _need_image(plan, z=z, x=x)
     _check(library().hqs_adjoint_axpy(plan.handle, _ptr(y, torch.complex64, "y"), float(c),
                                       _ptr(z, torch.complex64, "z"), _ptr(x, torch.complex64, "x"),
                                       _stream(stream)), "hqs_adjoint_axpy")
@@ -274,6 +312,7 @@ def adjoint_axpy(plan: Plan, y, c, z, x, stream=None):
 
 
 def toeplitz_normal(plan: Plan, x, out, precision=HQS_PREC_FP32, stream=None):
+    _need_image(plan, x=x, out=out)
     _check(library().hqs_toeplitz_normal(plan.handle, _ptr(x, torch.complex64, "x"),
                                          _ptr(out, torch.complex64, "out"), int(precision),
                                          _stream(stream)), "hqs_toeplitz_normal")
@@ -281,6 +320,7 @@ def toeplitz_normal(plan: Plan, x, out, precision=HQS_PREC_FP32, stream=None):
 
 
 def precond_apply(plan: Plan, a, b, r, z, stream=None):
+    _need_image(plan, r=r, z=z)
     _check(library().hqs_precond_apply(plan.handle, float(a), float(b), _ptr(r, torch.complex64, "r"),
                                        _ptr(z, torch.complex64, "z"), _stream(stream)),
            "hqs_precond_apply")
@@ -291,6 +331,7 @@ def dc_solve(plan: Plan, a, b, rhs, x, max_iter=30, rel_tol=1e-4, precond=HQS_PR
              mode=HQS_SOLVE_PLAIN, precision=HQS_PREC_FP32, want_info=True, stream=None,
              check=True):
     """Solves (a A^H A + b I) x = rhs in place; returns SolveInfo (or None)."""
+    _need_image(plan, rhs=rhs, x=x)
     info = SolveInfo() if want_info else None
     rc = library().hqs_dc_solve(plan.handle, float(a), float(b), _ptr(rhs, torch.complex64, "rhs"),
                                 _ptr(x, torch.complex64, "x"), int(max_iter), float(rel_tol),
@@ -322,8 +363,11 @@ def hqs_run(plan: Plan, y, x, mu, sigma, K=None, k0=0, cg_iters=5, c0=1.0, c1=0.
     """Annealed PnP-HQS; `denoiser` is None (built-in Gaussian smoothing, with
     optional gauss=(kappa, sigma0)) or a callable(in_tensor, out_tensor, sigma)
     that enqueues work on the current stream and returns 0 on success."""
+    _need_kspace(plan, y=y)
+    _need_image(plan, x=x)
     lib = library()
     K = len(mu) if K is None else int(K)
+    _need_schedule(K, mu=mu, sigma=sigma)
     mu_c = (C.c_float * K)(*[float(v) for v in mu[:K]])
     sg_c = (C.c_float * K)(*[float(v) for v in sigma[:K]])
     user = None
@@ -361,7 +405,10 @@ def hqs_run(plan: Plan, y, x, mu, sigma, K=None, k0=0, cg_iters=5, c0=1.0, c1=0.
 def pgd_run(plan: Plan, y, x, gamma, sigma, K=None, c0=1.0, c1=0.0, gauss=None, stream=None):
     """PnP-PGD with the gradient step in the metric P = c0 I + c1 A^H A and the
     built-in Gaussian smoothing denoiser (optional gauss=(kappa, sigma0))."""
+    _need_kspace(plan, y=y)
+    _need_image(plan, x=x)
     K = len(gamma) if K is None else int(K)
+    _need_schedule(K, gamma=gamma, sigma=sigma)
     g_c = (C.c_float * max(K, 1))(*[float(v) for v in gamma[:K]])
     s_c = (C.c_float * max(K, 1))(*[float(v) for v in sigma[:K]])
     user, keep = None, []
@@ -379,6 +426,8 @@ def gaussian_denoise(x, out, sigma, gauss=None, stream=None):
     if gauss is not None:
         gp = GaussParams(float(gauss[0]), float(gauss[1]))
     ny, nx = x.shape[-2], x.shape[-1]
+    _need(x, int(ny) * int(nx), "x")
+    _need(out, int(ny) * int(nx), "out")
     _check(library().hqs_gaussian_denoise(C.cast(C.pointer(gp), C.c_void_p) if gp else None,
                                           _ptr(x, torch.complex64, "x"),
                                           _ptr(out, torch.complex64, "out"), int(ny), int(nx),
@@ -406,6 +455,7 @@ def debug_phase_trace(plan: Plan, enable=False, stream=None):
 def toeplitz_stage(plan: Plan, x, precision: int, stage: int, out, stream=None):
     """Intermediate of the mixed-precision A^H A after DFT-GEMM pass `stage`
     (1..3, complex64, natural layout; 4 = the result)."""
+    _need_image(plan, x=x)
     _check(library().hqs_debug_toeplitz_stage(plan.handle, _ptr(x, torch.complex64, "x"), int(precision),
                                               int(stage), _ptr(out, torch.complex64, "out"),
                                               _stream(stream)), "hqs_debug_toeplitz_stage")
@@ -558,6 +608,7 @@ def plan_set_net(plan: Plan, net):
 
 
 def learned_precond_apply(plan: Plan, a, b, r, z, stream=None):
+    _need_image(plan, r=r, z=z)
     _check(library().hqs_learned_precond_apply(plan.handle, float(a), float(b),
                                                _ptr(r, torch.complex64, "r"),
                                                _ptr(z, torch.complex64, "z"), _stream(stream)),
@@ -728,8 +779,10 @@ class Plan3d:
 def plan3d_create(traj, shape, smaps, kernel_width=6, oversamp=2.0, stream=None) -> Plan3d:
     """traj (M, 3) float32 CUDA; shape (nz, ny, nx); smaps (L, nz, ny, nx) complex64 CUDA."""
     nz, ny, nx = (int(v) for v in shape)
-    h = C.c_void_p()
     M = int(traj.shape[0])
+    _need(traj, 3 * M, "traj")
+    _need(smaps, int(smaps.shape[0]) * nz * ny * nx, "smaps")
+    h = C.c_void_p()
     rc = library().hqs_plan3d_create(C.byref(h), _ptr(traj, torch.float32, "traj"), M, nz, ny, nx,
                                      int(smaps.shape[0]), _ptr(smaps, torch.complex64, "smaps"),
                                      int(kernel_width), float(oversamp), _stream(stream))
@@ -738,18 +791,23 @@ def plan3d_create(traj, shape, smaps, kernel_width=6, oversamp=2.0, stream=None)
 
 
 def forward3d(plan: Plan3d, x, y, stream=None):
+    _need_image(plan, x=x)
+    _need_kspace(plan, y=y)
     _check(library().hqs_forward3d(plan.handle, _ptr(x, torch.complex64, "x"), _ptr(y, torch.complex64, "y"),
                                    _stream(stream)), "hqs_forward3d")
     return y
 
 
 def adjoint3d(plan: Plan3d, y, x, stream=None):
+    _need_kspace(plan, y=y)
+    _need_image(plan, x=x)
     _check(library().hqs_adjoint3d(plan.handle, _ptr(y, torch.complex64, "y"), _ptr(x, torch.complex64, "x"),
                                    _stream(stream)), "hqs_adjoint3d")
     return x
 
 
 def toeplitz_normal3d(plan: Plan3d, x, out, stream=None):
+    _need_image(plan, x=x, out=out)
     _check(library().hqs_toeplitz_normal3d(plan.handle, _ptr(x, torch.complex64, "x"),
                                            _ptr(out, torch.complex64, "out"), _stream(stream)),
            "hqs_toeplitz_normal3d")
@@ -758,12 +816,14 @@ def toeplitz_normal3d(plan: Plan3d, x, out, stream=None):
 
 def plan3d_khat(plan: Plan3d, out, stream=None):
     """Khat (2nz, 2ny, 2nx) float32, scaled by 1 / (8 nz ny nx)."""
+    _need(out, 8 * _image_elems(plan), "out")
     _check(library().hqs_plan3d_get_khat(plan.handle, _ptr(out, torch.float32, "out"), _stream(stream)),
            "hqs_plan3d_get_khat")
     return out
 
 
 def precond_apply3d(plan: Plan3d, a, b, r, z, stream=None):
+    _need_image(plan, r=r, z=z)
     _check(library().hqs_precond_apply3d(plan.handle, float(a), float(b), _ptr(r, torch.complex64, "r"),
                                          _ptr(z, torch.complex64, "z"), _stream(stream)), "hqs_precond_apply3d")
     return z
@@ -772,6 +832,7 @@ def precond_apply3d(plan: Plan3d, a, b, r, z, stream=None):
 def dc_solve3d(plan: Plan3d, a, b, rhs, x, max_iter=30, rel_tol=1e-4, precond=HQS_PRECOND_DC, stream=None,
                check=True) -> SolveInfo:
     """Solves (a A^H A + b I) x = rhs in place (PCG, blocking); returns SolveInfo."""
+    _need_image(plan, rhs=rhs, x=x)
     info = SolveInfo()
     rc = library().hqs_dc_solve3d(plan.handle, float(a), float(b), _ptr(rhs, torch.complex64, "rhs"),
                                   _ptr(x, torch.complex64, "x"), int(max_iter), float(rel_tol), int(precond),
@@ -786,6 +847,7 @@ def gaussian_denoise3d(x, out, sigma, gauss=None, stream=None):
     """Built-in volume denoiser; gauss=(kappa, sigma0) or None (s = sigma)."""
     gp = GaussParams(float(gauss[0]), float(gauss[1])) if gauss is not None else None
     nz, ny, nx = (int(v) for v in x.shape)
+    _need(out, nz * ny * nx, "out")
     _check(library().hqs_gaussian_denoise3d(C.cast(C.pointer(gp), C.c_void_p) if gp is not None else None,
                                             _ptr(x, torch.complex64, "x"), _ptr(out, torch.complex64, "out"),
                                             nz, ny, nx, float(sigma), _stream(stream)), "hqs_gaussian_denoise3d")
@@ -797,8 +859,11 @@ def hqs_run3d(plan: Plan3d, y, x, mu, sigma, K=None, k0=0, cg_iters=5, c0=1.0, c
     """Annealed PnP-HQS on a volume; `denoiser` is None (built-in Gaussian
     smoothing, optional gauss=(kappa, sigma0)) or a callable(in_tensor,
     out_tensor, sigma) that enqueues work on the current stream and returns 0."""
+    _need_kspace(plan, y=y)
+    _need_image(plan, x=x)
     lib = library()
     K = len(mu) if K is None else int(K)
+    _need_schedule(K, mu=mu, sigma=sigma)
     mu_c = (C.c_float * K)(*[float(v) for v in mu[:K]])
     sg_c = (C.c_float * K)(*[float(v) for v in sigma[:K]])
     user, cb, keep = None, None, []

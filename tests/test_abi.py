@@ -132,3 +132,45 @@ def test_batch_wrappers_check_counts_and_shapes_before_any_launch():
     for call in calls:
         with pytest.raises(ValueError):
             call()
+
+
+def test_plan_wrappers_check_element_counts_before_any_launch():
+    # every single-plan entry point sizes its buffers from the plan: a tensor holding
+    # another number of elements, or a schedule shorter than K, is rejected before a
+    # pointer reaches the library
+    import types
+    import pytest
+    torch = pytest.importorskip("torch")
+    import paper_2411_01955_gb300 as hq
+    c64 = torch.complex64
+    p2 = types.SimpleNamespace(ny=16, nx=16, coils=3, npoints=50, handle=None)
+    p3 = types.SimpleNamespace(shape=(4, 8, 8), coils=2, npoints=40, handle=None)
+    img, ksp = torch.zeros((16, 16), dtype=c64), torch.zeros((3, 50), dtype=c64)
+    vol, ksp3 = torch.zeros((4, 8, 8), dtype=c64), torch.zeros((2, 40), dtype=c64)
+    small, big = torch.zeros((16, 8), dtype=c64), torch.zeros((3, 51), dtype=c64)
+    calls = [
+        lambda: hq.forward(p2, small, ksp),
+        lambda: hq.forward(p2, img, big),
+        lambda: hq.adjoint(p2, big, img),
+        lambda: hq.adjoint_axpy(p2, ksp, 0.1, small, img),
+        lambda: hq.toeplitz_normal(p2, img, small),
+        lambda: hq.precond_apply(p2, 1.0, 0.1, small, img),
+        lambda: hq.dc_solve(p2, 1.0, 0.1, img, small),
+        lambda: hq.hqs_run(p2, big, img, [0.1], [0.1]),
+        lambda: hq.hqs_run(p2, ksp, img, [0.1, 0.1], [0.1]),
+        lambda: hq.pgd_run(p2, ksp, small, [0.1], [0.1]),
+        lambda: hq.learned_precond_apply(p2, 1.0, 0.1, img, small),
+        lambda: hq.gaussian_denoise(img, small, 1.0),
+        lambda: hq.plan_create(torch.zeros((50, 3)), 16, 16, torch.zeros((3, 16, 16), dtype=c64)),
+        lambda: hq.forward3d(p3, vol[:2], ksp3),
+        lambda: hq.adjoint3d(p3, ksp, vol),
+        lambda: hq.toeplitz_normal3d(p3, vol, small),
+        lambda: hq.plan3d_khat(p3, torch.zeros((4, 8, 8))),
+        lambda: hq.precond_apply3d(p3, 1.0, 0.1, vol, vol[1:]),
+        lambda: hq.dc_solve3d(p3, 1.0, 0.1, vol[:, :4], vol),
+        lambda: hq.hqs_run3d(p3, ksp3, vol, [0.1, 0.1], [0.1], K=2),
+        lambda: hq.gaussian_denoise3d(vol, vol[:3], 1.0),
+    ]
+    for call in calls:
+        with pytest.raises(ValueError):
+            call()
