@@ -109,8 +109,9 @@ ADJ_BYTES = (_Y + _PTS + _G2L) + (_G2L + _ROWS) + (_ROWS + _S + 320 * 320 * 8)
 PERSISTENT_TRAFFIC_BYTES = None
 # The same for the batched solves of one default step (two concurrent k_pcg_batch
 # launches of 8 slices: the sum of both launches' bytes, each captured alone), from
-# profiles/pcg_batch_320x16_16slices.md; None until captured.
-BATCH_TRAFFIC_BYTES = 19029755136 + 13915506944 + 20309124608 + 14937506560
+# profiles/pcg_batch_320x16_16slices.md; None while the kernel has changed since the
+# last capture (the 68.2 GB there predate the column items over flattened lines).
+BATCH_TRAFFIC_BYTES = None
 
 
 def parse():
