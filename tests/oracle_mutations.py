@@ -37,6 +37,7 @@ M = [
     ("nudft.py", "Ex, Ey = _axis_matrices(traj, ny, nx, +1.0)", "Ex, Ey = _axis_matrices(traj, ny, nx, -1.0)", "adjoint sign"),
     ("nudft.py", "Ex = np.exp(sign * 1j * np.outer(k[:, 0], centred(nx)))", "Ex = np.exp(sign * 1j * np.outer(k[:, 1], centred(nx)))", "kx/ky swap"),
     ("nudft.py", "x += np.conj(smaps[l]) * img", "x += smaps[l] * img", "nudft adjoint conj"),
+    ("nudft.py", "    Ex, Ey = _axis_matrices(traj, ny, nx, -1.0)\n", "    Ex, Ey = _axis_matrices(traj, nx, ny, -1.0)\n", "forward axes swapped"),
     # nufft
     ("nufft.py", "i0 = np.ceil(u - W / 2.0)", "i0 = np.floor(u - W / 2.0)", "tap origin"),
     ("nufft.py", "return 1.0 / kb.phihat(centred(n) / G, W, b)", "return 1.0 / kb.phihat(centred(n) / n, W, b)", "apodisation scale"),
@@ -57,6 +58,7 @@ M = [
     ("toeplitz.py", "return np.fft.fft2(chan_column(c, ny, nx)).real", "return np.fft.ifft2(chan_column(c, ny, nx)).real", "chan symbol fft"),
     ("toeplitz.py", "dy = np.arange(ny) - ny // 2", "dy = np.arange(ny) - (ny - 1) // 2", "strang centring"),
     ("toeplitz.py", "return 1.0 / np.sqrt(np.maximum(s, 0.25 * b))", "return 1.0 / np.sqrt(np.maximum(s, 0.5 * b))", "precond floor"),
+    ("toeplitz.py", "    c[ny, :] = 0.0\n", "    c[ny - 1, :] = 0.0\n", "kernel zeroed row off by one"),
     # solvers
     ("solvers.py", "        beta = rz_new / rz\n", "        beta = rz / rz_new\n", "pcg beta inverted"),
     ("solvers.py", "        r = r - alpha * q\n        it += 1\n        hist.append(float(np.linalg.norm(r)) / bnorm)\n        if hist[-1] <= tol:\n            status = \"ok\"",
@@ -92,11 +94,17 @@ M = [
     ("convnet.py", "    mh = m / (1 - b1 ** t)", "    mh = m", "adam bias correction"),
     ("convnet.py", "    return zdc + s * (out[0, 0] + 1j * out[0, 1])", "    return zdc + (out[0, 0] + 1j * out[0, 1])", "learned scale"),
     ("convnet.py", "        h = z if li == len(params) - 1 else np.maximum(z, 0.0)", "        h = np.maximum(z, 0.0)", "relu on last layer"),
+    ("convnet.py", "    s = math.sqrt(float(np.mean(np.abs(zdc) ** 2)))", "    s = float(np.mean(np.abs(zdc)))", "learned scale mean abs"),
+    ("convnet.py", "    v = b2 * v + (1 - b2) * grad * grad", "    v = b2 * v + (1 - b2) * np.abs(grad)", "adam second moment"),
+    ("convnet.py", "    return vec - lr * mh / (np.sqrt(vh) + eps), m, v", "    return vec - lr * mh / np.sqrt(vh + eps), m, v", "adam eps placement"),
+    ("convnet.py", "    return dW, dz.sum(axis=(0, 2, 3))", "    return dW, dz.sum(axis=(0, 2, 3)) / dz.shape[0]", "bias grad scale"),
     # smaps
     ("smaps.py", "0.54 + 0.46 * np.cos(2.0 * np.pi * u / width)", "0.54 + 0.46 * np.cos(np.pi * u / width)", "hamming period"),
     ("smaps.py", "    return h[:, 0] * h[:, 1]", "    return h[:, 0]", "hamming separable"),
     ("smaps.py", "    rss = np.sqrt(np.sum(np.abs(c) ** 2, axis=0))", "    rss = np.sum(np.abs(c), axis=0)", "rss norm"),
     ("smaps.py", "        w = w * np.asarray(dcf, dtype=np.float64)", "        w = w / np.asarray(dcf, dtype=np.float64)", "dcf inverted"),
+    ("smaps.py", "    u = np.asarray(traj, dtype=np.float64) * n / (2.0 * np.pi)", "    u = np.asarray(traj, dtype=np.float64) * n / np.pi", "window units"),
+    ("smaps.py", "    mask = rss >= thresh * rss.max()", "    mask = rss >= thresh", "mask threshold absolute"),
     # nufft3d
     ("nufft3d.py", "    Ez = np.exp(sign * 1j * np.outer(k[:, 2], centred(nz)))   # (M, nz)", "    Ez = np.exp(sign * 1j * np.outer(k[:, 2], centred(nx)))   # (M, nz)", "3d nudft z uses nx"),
     ("nufft3d.py", "        sy = np.einsum(\"zyj,jy->zj\", sx, Ey)           # sum over n_y", "        sy = np.einsum(\"zyj,jy->zj\", sx, np.conj(Ey))           # sum over n_y", "3d nudft y sign"),

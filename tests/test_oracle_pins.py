@@ -591,7 +591,13 @@ def test_convnet_gradient_matches_finite_differences():
     layers = [(p[0].shape[1], p[0].shape[0]) for p in params]
     vec = convnet.flatten(params)
     h = 1e-6
-    for k in rng.choice(vec.size, size=25, replace=False):
+    # 25 random parameters and every bias (a handful among the weights)
+    biases, k0 = [], 0
+    for W, b in params:
+        k0 += W.size
+        biases += list(range(k0, k0 + b.size))
+        k0 += b.size
+    for k in list(rng.choice(vec.size, size=25, replace=False)) + biases:
         vp, vm = vec.copy(), vec.copy()
         vp[k] += h
         vm[k] -= h
@@ -631,6 +637,20 @@ def test_learned_preconditioner_is_positively_homogeneous():
     z2 = convnet.learned_precond(3.7 * r, P["lam"], 1.0, 0.05, params)
     assert rel(z1, toeplitz.precond_apply(r, P["lam"], 1.0, 0.05)) > 1e-3
     assert rel(z2, 3.7 * z1) < 1e-13
+
+
+def test_learned_preconditioner_scale_is_the_rms_of_the_dc_output():
+    # last layer: zero weights and bias (c, 0), so net(.) = c + 0i everywhere and
+    # z - zdc = s c: s must be the root-mean-square of zdc over the complex pixels
+    P = small_problem(25)
+    params = convnet.init_params(2)
+    W4, b4 = params[-1]
+    params[-1] = (np.zeros_like(W4), np.array([0.7, 0.0]))
+    r = P["b0"]
+    zdc = toeplitz.precond_apply(r, P["lam"], 1.0, 0.05)
+    z = convnet.learned_precond(r, P["lam"], 1.0, 0.05, params)
+    s = math.sqrt(float(np.sum(zdc.real ** 2 + zdc.imag ** 2)) / zdc.size)
+    assert rel(z - zdc, np.full(zdc.shape, 0.7 * s)) < 1e-13
 
 
 # ------------------------------------------------------------------ S-maps (Sec. 4.1)
